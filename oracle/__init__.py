@@ -1,0 +1,331 @@
+"""FP64 brute-force CPU oracle for the SPH neighbour sums -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It never imports the CUDA package and
+the CUDA package never imports it; the two share only the seeded input
+generators (``paper_1508_00115_gb300/inputs.py``, which holds none of the
+method's arithmetic).
+
+What each function follows (Theuns et al. 2015, "Swift: task-based
+hydrodynamics and gravity for cosmological simulations"):
+
+* :func:`density_at_h`, :func:`solve_h` -- Sec. 2, Eq. 1 (density), the
+  smoothing-length criterion in the sentence after Eq. 2, and the velocity
+  divergence / curl estimates the viscosity switch needs.
+* :func:`ghost` -- Sec. 2: equation of state and "density before pressure
+  gradient"; the grad-h factor of the Gadget-2 formulation the paper adopts.
+* :func:`force` -- Sec. 2, Eq. 2 in the Gadget-2 form, with artificial
+  viscosity.
+* :func:`step` -- Sec. 2, "particles are marched forward in time": a
+  kick-drift-kick leapfrog (the integrator is not named in the paper).
+
+The arithmetic lives in ``sph_oracle.c`` (plain C, FP64, OpenMP over targets,
+``-ffp-contract=off``); this file only marshals arrays and composes the step.
+Parity pins: ``tests/test_oracle_pins.py`` (no function here is unpinned).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sph_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+FOUR_PI_3 = 4.0 * np.pi / 3.0
+
+
+def build(force: bool = False) -> str:
+    """Compile sph_oracle.c into oracle/_build/liboracle.so (gcc, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC",
+           "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i64 = ctypes.c_int64
+        d = ctypes.c_double
+        lib.orc_w.restype = d
+        lib.orc_w.argtypes = [d]
+        lib.orc_dw.restype = d
+        lib.orc_dw.argtypes = [d]
+        lib.orc_wrap.restype = None
+        lib.orc_wrap.argtypes = [i64, d, P]
+        lib.orc_cell_key.restype = i64
+        lib.orc_cell_key.argtypes = [d, d, d, d, i64]
+        lib.orc_hash_id.restype = ctypes.c_uint64
+        lib.orc_hash_id.argtypes = [ctypes.c_uint64]
+        lib.orc_density_at_h.restype = ctypes.c_int
+        lib.orc_density_at_h.argtypes = [i64, d] + [P] * 8 + [i64, P, P, P, P, P]
+        lib.orc_solve_h.restype = ctypes.c_int
+        lib.orc_solve_h.argtypes = ([i64, d] + [P] * 7 + [P, d, d, d, i64, P, P]
+                                    + [P, P, P, P, P])
+        lib.orc_ghost.restype = None
+        lib.orc_ghost.argtypes = [i64] + [P] * 6 + [d, ctypes.c_int] + [P] * 4
+        lib.orc_force.restype = ctypes.c_int
+        lib.orc_force.argtypes = ([i64, d] + [P] * 7 + [P] * 6 + [d, i64, P]
+                                  + [P] * 6)
+        lib.orc_num_threads.restype = ctypes.c_int
+        lib.orc_num_threads.argtypes = []
+        _lib = lib
+        return lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+def w(q: float) -> float:
+    """Cubic-spline shape w(q), support q <= 1 (normalised: int 4 pi q^2 w = 1)."""
+    return float(_load().orc_w(float(q)))
+
+
+def dw(q: float) -> float:
+    """dw/dq of the cubic-spline shape."""
+    return float(_load().orc_dw(float(q)))
+
+
+def hash_id(i: int) -> int:
+    """splitmix64 finaliser of a particle id (neighbour-set fingerprint term)."""
+    return int(_load().orc_hash_id(ctypes.c_uint64(int(i))))
+
+
+def wrap(x: np.ndarray, box: float) -> np.ndarray:
+    """Periodic wrap into [0, box) (FP64)."""
+    out = _f64(x).copy()
+    _load().orc_wrap(out.size, float(box), _p(out))
+    return out
+
+
+def cell_keys(x, y, z, box: float, nc: int) -> np.ndarray:
+    """Linear cell key (iz*nc+iy)*nc+ix of each wrapped position."""
+    lib = _load()
+    return np.array([lib.orc_cell_key(float(a), float(b), float(c), float(box), int(nc))
+                     for a, b, c in zip(x, y, z)], dtype=np.int64)
+
+
+@dataclass
+class State:
+    """Particle state, FP64 SoA.  ``box`` is the periodic box side."""
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    vx: np.ndarray
+    vy: np.ndarray
+    vz: np.ndarray
+    m: np.ndarray
+    u: np.ndarray
+    h: np.ndarray
+    box: float = 1.0
+    ids: np.ndarray | None = field(default=None)
+
+    @property
+    def n(self) -> int:
+        return int(self.x.size)
+
+    def copy(self) -> "State":
+        return State(*(np.array(getattr(self, k), dtype=np.float64) for k in
+                       ("x", "y", "z", "vx", "vy", "vz", "m", "u", "h")),
+                     box=self.box,
+                     ids=None if self.ids is None else self.ids.copy())
+
+    def _arrs(self):
+        return [_f64(getattr(self, k)) for k in ("x", "y", "z", "vx", "vy", "vz", "m")]
+
+
+def _targets(n, targets):
+    if targets is None:
+        return None, n
+    t = np.ascontiguousarray(targets, dtype=np.int64)
+    return t, int(t.size)
+
+
+def _ids(s: State):
+    if s.ids is None:
+        return None
+    return np.ascontiguousarray(s.ids, dtype=np.uint64)
+
+
+def density_at_h(s: State, h=None, targets=None) -> dict:
+    """Eq. 1 and companions at the given smoothing lengths (default s.h).
+
+    Returns dict of arrays over targets: rho, nw, dnw_dh, drho_dh, divv, curl (n,3),
+    curl_abs, n_ngb, ngb_hash.
+    """
+    lib = _load()
+    h = _f64(s.h if h is None else h)
+    t, nt = _targets(s.n, targets)
+    out = np.zeros((nt, 8))
+    nngb = np.zeros(nt, dtype=np.int64)
+    hh = np.zeros(nt, dtype=np.uint64)
+    arrs = s._arrs()
+    ids = _ids(s)
+    lib.orc_density_at_h(s.n, float(s.box), *[_p(a) for a in arrs], _p(h), nt, _p(t),
+                         _p(ids), _p(out), _p(nngb), _p(hh))
+    return _density_dict(out, nngb, hh)
+
+
+def _density_dict(out, nngb, hh):
+    curl = out[:, 5:8].copy()
+    return dict(rho=out[:, 0].copy(), nw=out[:, 1].copy(), dnw_dh=out[:, 2].copy(),
+                drho_dh=out[:, 3].copy(), divv=out[:, 4].copy(), curl=curl,
+                curl_abs=np.sqrt((curl * curl).sum(axis=1)), n_ngb=nngb, ngb_hash=hh)
+
+
+def solve_h(s: State, h_guess=None, n_ngb: float = 48.0, tol: float = 1e-12,
+            h_max: float | None = None, targets=None) -> dict:
+    """Smoothing lengths with N_w(h) = n_ngb (Newton + bisection), plus the density
+    sums at the solved h.  Returns the density_at_h dict plus 'h' and 'iters'."""
+    lib = _load()
+    hg = _f64(s.h if h_guess is None else h_guess)
+    t, nt = _targets(s.n, targets)
+    if h_max is None:
+        h_max = s.box / 2.0
+    hout = np.zeros(nt)
+    iters = np.zeros(nt, dtype=np.int32)
+    out = np.zeros((nt, 8))
+    nngb = np.zeros(nt, dtype=np.int64)
+    hh = np.zeros(nt, dtype=np.uint64)
+    arrs = s._arrs()
+    ids = _ids(s)
+    bad = lib.orc_solve_h(s.n, float(s.box), *[_p(a) for a in arrs], _p(hg), float(n_ngb),
+                          float(tol), float(h_max), nt, _p(t), _p(ids), _p(hout), _p(iters),
+                          _p(out), _p(nngb), _p(hh))
+    if bad:
+        raise RuntimeError(f"oracle: {bad} smoothing lengths exceed h_max={h_max}")
+    d = _density_dict(out, nngb, hh)
+    d["h"] = hout
+    d["iters"] = iters
+    return d
+
+
+def ghost(rho, drho_dh, divv, curl_abs, u, h, gamma: float = 5.0 / 3.0,
+          use_balsara: bool = True) -> dict:
+    """P, c, f (grad-h) and Balsara B per particle."""
+    lib = _load()
+    arrs = [_f64(a) for a in (rho, drho_dh, divv, curl_abs, u, h)]
+    n = arrs[0].size
+    P, c, f, B = (np.zeros(n) for _ in range(4))
+    lib.orc_ghost(n, *[_p(a) for a in arrs], float(gamma), int(bool(use_balsara)),
+                  _p(P), _p(c), _p(f), _p(B))
+    return dict(P=P, c=c, f=f, B=B)
+
+
+def force(s: State, h, rho, P, c, f, B, alpha: float = 0.8, targets=None) -> dict:
+    """Pressure-gradient + viscosity sums (Gadget-2 form of Eq. 2).  Per-particle
+    inputs are full-length arrays; outputs are over targets."""
+    lib = _load()
+    t, nt = _targets(s.n, targets)
+    ins = [_f64(a) for a in (h, rho, P, c, f, B)]
+    ax, ay, az, dudt, vsig = (np.zeros(nt) for _ in range(5))
+    npairs = np.zeros(nt, dtype=np.int64)
+    arrs = s._arrs()
+    lib.orc_force(s.n, float(s.box), *[_p(a) for a in arrs], *[_p(a) for a in ins],
+                  float(alpha), nt, _p(t), _p(ax), _p(ay), _p(az), _p(dudt), _p(vsig),
+                  _p(npairs))
+    return dict(a=np.stack([ax, ay, az], axis=1), dudt=dudt, vsig=vsig, n_pairs=npairs)
+
+
+@dataclass
+class Params:
+    gamma: float = 5.0 / 3.0
+    n_ngb: float = 48.0
+    alpha: float = 0.8
+    cfl: float = 0.1
+    use_balsara: bool = True
+    h_tol: float = 1e-12
+
+
+def hydro(s: State, p: Params = Params(), h_guess=None) -> dict:
+    """Density (with h solve), ghost and force for every particle."""
+    d = solve_h(s, h_guess=h_guess, n_ngb=p.n_ngb, tol=p.h_tol)
+    g = ghost(d["rho"], d["drho_dh"], d["divv"], d["curl_abs"], s.u, d["h"], p.gamma,
+              p.use_balsara)
+    fr = force(s, d["h"], d["rho"], g["P"], g["c"], g["f"], g["B"], p.alpha)
+    out = dict(d)
+    out.update(g)
+    out.update(fr)
+    return out
+
+
+def cfl_dt(h, vsig, cfl: float = 0.1) -> float:
+    """dt = C_CFL min_i h_i / vsig_i over particles with vsig_i > 0."""
+    h = _f64(h)
+    v = _f64(vsig)
+    ok = v > 0
+    return float(cfl * np.min(h[ok] / v[ok])) if ok.any() else float("inf")
+
+
+def conserved(s: State) -> dict:
+    """Total momentum, kinetic and thermal energy (FP64)."""
+    mv = np.array([np.sum(s.m * s.vx), np.sum(s.m * s.vy), np.sum(s.m * s.vz)])
+    ek = float(np.sum(0.5 * s.m * (s.vx ** 2 + s.vy ** 2 + s.vz ** 2)))
+    eu = float(np.sum(s.m * s.u))
+    return dict(momentum=mv, e_kin=ek, e_th=eu, e_tot=ek + eu)
+
+
+def step(s: State, acc: dict, dt: float, p: Params = Params()) -> tuple[State, dict, int]:
+    """One kick-drift-kick step.  ``acc`` holds the hydro result at the start of the
+    step (keys a, dudt, h).  The hydro pass at the end of the drift sees velocities
+    and internal energies predicted to the synchronised time,
+    v_pred = v_half + a_old dt/2 and u_pred = u_half + (du/dt)_old dt/2 (the
+    Gadget-2 prediction; the paper names no integrator).  Internal energy is floored
+    at 0 after each kick and prediction; the number of floored values is returned.
+    Returns (new state, new hydro, floors)."""
+    n2 = s.copy()
+    a = acc["a"]
+    floors = 0
+    half = 0.5 * dt
+    n2.vx = n2.vx + a[:, 0] * half
+    n2.vy = n2.vy + a[:, 1] * half
+    n2.vz = n2.vz + a[:, 2] * half
+    n2.u = n2.u + acc["dudt"] * half
+    floors += int(np.sum(n2.u < 0))
+    n2.u = np.maximum(n2.u, 0.0)
+    n2.x = wrap(n2.x + n2.vx * dt, s.box)
+    n2.y = wrap(n2.y + n2.vy * dt, s.box)
+    n2.z = wrap(n2.z + n2.vz * dt, s.box)
+    pred = n2.copy()
+    pred.vx = n2.vx + a[:, 0] * half
+    pred.vy = n2.vy + a[:, 1] * half
+    pred.vz = n2.vz + a[:, 2] * half
+    pred.u = np.maximum(n2.u + acc["dudt"] * half, 0.0)
+    res = hydro(pred, p, h_guess=acc["h"])
+    n2.h = res["h"].copy()
+    a2 = res["a"]
+    n2.vx = n2.vx + a2[:, 0] * half
+    n2.vy = n2.vy + a2[:, 1] * half
+    n2.vz = n2.vz + a2[:, 2] * half
+    n2.u = n2.u + res["dudt"] * half
+    floors += int(np.sum(n2.u < 0))
+    n2.u = np.maximum(n2.u, 0.0)
+    return n2, res, floors
