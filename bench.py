@@ -1,0 +1,378 @@
+"""Benchmark of the SPH hot path on GB300: KDK steps of the Sedov-Taylor workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one pass of the whole hot path over the particle set: kick, drift,
+cell binning (wrap, key, radix sort, permute), density with the smoothing-length
+iteration, force, kick, and the global reductions (CFL dt, conserved sums).
+Workload: Sedov-Taylor blast on a 128^3 jittered lattice (2,097,152 particles),
+the configuration the throughput is quoted on; inputs resident in HBM.
+
+Prints ONE JSON line (rank 0).  value = particles advanced per second over all
+ranks; the device time is taken with CUDA events on the library's stream,
+bracketed by a barrier and synchronisations, max over ranks.  Under torchrun each
+rank steps its own replica (the path does not shard across GPUs here).
+
+--impl reference times the FP64 brute-force oracle on this host's cores on a
+bounded sample of the same workload (the oracle is the only other
+implementation of this path), extrapolated to particles/s.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SPH step particles/s & pair interactions/s, learned-h+batched vs plain, 1 GB300"
+UNIT = "particles/s"
+# Algorithmic FP32 operations per accepted pair (FMA = 2, add/mul/div/rsqrt = 1,
+# Kahan compensation included; rejected distance tests are NOT counted).
+FLOP_DENSITY_PAIR = 69
+FLOP_FORCE_PAIR = 86
+L2_BYTES = 129e6
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def fp32_peak_tflops(sms: int, peaks: dict) -> tuple[float, str]:
+    """Plain FP32 ALU peak: SMs x 128 lanes x 2 FLOP (FMA) x max SM clock."""
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, f"{sms} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.lines: list[str] = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, pw, reasons = [], [], [], set()
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+                pw.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _gpu_id(dev: int) -> str:
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[dev] if vis else str(dev)
+
+
+def _traffic(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    from paper_1508_00115_gb300 import build as b
+    path = os.path.join(ROOT, "profiles", f"{kernel}_sedov128.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    src = None
+    val = None
+    for line in text.splitlines():
+        if line.startswith("source_digest:"):
+            src = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            val = float(line.split(":", 1)[1].split()[0])
+    if src is None or val is None or src != b._digest():
+        return None
+    return val
+
+
+def workload(seed: int = 2):
+    from paper_1508_00115_gb300 import inputs
+    return inputs.sedov(128, seed=seed)
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+
+def oracle_sample(d: dict, n_force: int, seed: int = 5) -> dict:
+    """Time the FP64 oracle on a bounded sample of the workload: n_force random
+    targets get the full path (h solve + density for them and for every particle
+    within 1.5 h of them, then the force sum), each brute-forced against all N.
+    particles/s = 1 / (T_density/S_density + T_force/S_force)."""
+    import oracle
+    n = d["x"].size
+    s = oracle.State(**{k: d[k] for k in ("x", "y", "z", "vx", "vy", "vz", "m", "u", "h")})
+    rng = np.random.default_rng(seed)
+    tf = rng.choice(n, n_force, replace=False)
+    R = 1.5 * float(np.max(d["h"]))
+    near = []
+    for i in tf:  # sample selection (not timed): everything that can be a neighbour
+        dx = s.x - s.x[i]; dx -= np.rint(dx)
+        dy = s.y - s.y[i]; dy -= np.rint(dy)
+        dz = s.z - s.z[i]; dz -= np.rint(dz)
+        near.append(np.nonzero(dx * dx + dy * dy + dz * dz < R * R)[0])
+    td = np.unique(np.concatenate([tf] + near))
+    t0 = time.perf_counter()
+    r = oracle.solve_h(s, targets=td)
+    t1 = time.perf_counter()
+    h = np.full(n, 1e-30)
+    rho = np.ones(n); P = np.zeros(n); c = np.zeros(n); f = np.ones(n); B = np.zeros(n)
+    g = oracle.ghost(r["rho"], r["drho_dh"], r["divv"], r["curl_abs"], s.u[td], r["h"])
+    h[td] = r["h"]; rho[td] = r["rho"]; P[td] = g["P"]; c[td] = g["c"]; f[td] = g["f"]
+    B[td] = g["B"]
+    t2 = time.perf_counter()
+    oracle.force(s, h, rho, P, c, f, B, targets=tf)
+    t3 = time.perf_counter()
+    td_s, tf_s = t1 - t0, t3 - t2
+    per = td_s / td.size + tf_s / tf.size
+    return {"value": 1.0 / per, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": (f"{td.size} density/h-solve targets + {tf.size} force targets of the "
+                       f"{n}-particle Sedov 128^3 state, each brute-forced against all N "
+                       f"(FP64, OpenMP); {td_s:.1f} s + {tf_s:.1f} s"),
+            "seconds": td_s + tf_s}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if world > 1 and rank != 0:
+        return
+    d = workload()
+    vals = []
+    info = None
+    for k in range(args.warmup + args.steps):
+        info = oracle_sample(d, n_force=8, seed=100 + k)
+        if k >= args.warmup:
+            vals.append(info["value"])
+    v = float(np.median(vals)) if vals else 0.0
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": "sedov-taylor 128^3 jittered lattice (2097152 particles), "
+                                  "bounded oracle sample per step", "n_particles": int(d["x"].size)},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+                            "sample": info["sample"]},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ GPU path
+
+
+def run_ours(args):
+    import torch
+    from paper_1508_00115_gb300 import binding
+
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    binding.lib()
+    d = workload()
+    n = int(d["x"].size)
+    stream = torch.cuda.Stream()
+    ctx = binding.Context(n, device=local, stream=stream.cuda_stream, flags=binding.SPH_FLAG_TIMING)
+    parts = binding.Particles(d)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        ctx.step(parts)
+    ctx.reset_stats()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(_gpu_id(local)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    floors = 0
+    for _ in range(args.steps):
+        _, cons = ctx.step(parts)
+        floors += cons["u_floors"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    st = ctx.stats()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    sec = ms / 1e3
+    value = world * n * args.steps / sec
+    pairs = st["density_pairs"] + st["force_pairs"]
+
+    # roofline of the dominant pair kernel (plain FP32 ALU bound)
+    props = torch.cuda.get_device_properties(local)
+    peaks = _peaks()
+    peak, peak_how = fp32_peak_tflops(props.multi_processor_count, peaks)
+    kernels = {
+        "density": (st["t_density_ms"], st["density_pairs"] * FLOP_DENSITY_PAIR,
+                    st["density_passes"]),
+        "force": (st["t_force_ms"], st["force_pairs"] * FLOP_FORCE_PAIR, st["force_passes"]),
+    }
+    dom = max(kernels, key=lambda k: kernels[k][0])
+    t_ms, flops, launches = kernels[dom]
+    achieved = flops / (t_ms / 1e3) / 1e12 if t_ms > 0 else 0.0
+    traffic = _traffic(dom)
+    roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic,
+                "peak_source": f"derived: {peak_how} (FP32 non-tensor; MEASURED_PEAKS.json "
+                               "holds HBM and bf16 only)",
+                "launches": launches, "avg_launch_ms": t_ms / max(launches, 1),
+                "other_kernel": {k: {"ms_total": v[0], "tflops": (v[1] / (v[0] / 1e3) / 1e12
+                                                                   if v[0] > 0 else 0)}
+                                 for k, v in kernels.items() if k != dom}}
+
+    # end to end through the public C-ABI with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        ctx_h = binding.Context(n, device=local, stream=stream.cuda_stream)
+        hp = binding.Particles(d, device="cpu", pin=True)
+        for _ in range(max(1, args.warmup)):
+            ctx_h.step_host(hp)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx_h.step_host(hp)
+        t_e2e = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([t_e2e], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
+        e2e = {"value": world * n * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": n * (6 * 8 + 8 * 4),
+               "d2h_bytes_per_step": n * (6 * 8 + 14 * 4 + 4)}
+        ctx_h.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(d, n_force=args.cpu_force_targets)
+        cpu.pop("seconds", None)
+
+    work_mb = n * (6 * 8 + 14 * 4 + 4 + 3 * 16 + 4 + 8 + 8 + 16) / 1e6
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "dtype_detail": "FP32 pair arithmetic with compensated sums; FP64 positions, "
+                           "kicks/drifts, wrap and global reductions",
+           "data": "synthetic",
+           "config": {"workload": "sedov-taylor 128^3 jittered lattice, KDK step: cells + "
+                                  "density/h-iteration + force + kicks (plain path)",
+                      "n_particles": n, "n_ngb": 48, "h_tol": float(ctx.params.h_tol),
+                      "l2": f"inputs larger than L2 (~{work_mb:.0f} MB resident per step > 129 MB)",
+                      "parallelism": f"replicas x{world}"},
+           "pair_interactions_per_s": world * pairs / sec,
+           "per_step": {"density_pairs": st["density_pairs"] / args.steps,
+                        "force_pairs": st["force_pairs"] / args.steps,
+                        "density_passes": st["density_passes"] / args.steps,
+                        "density_targets": st["density_targets"] / args.steps,
+                        "density_candidates": st["density_candidates"] / args.steps,
+                        "force_candidates": st["force_candidates"] / args.steps,
+                        "rebuilds": st["rebuilds"] / args.steps,
+                        "t_density_ms": st["t_density_ms"] / args.steps,
+                        "t_force_ms": st["t_force_ms"] / args.steps,
+                        "t_build_ms": st["t_build_ms"] / args.steps,
+                        "u_floors": floors / args.steps},
+           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": int(st["kernel_launches"]), "clocks": clocks}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-force-targets", type=int, default=48)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

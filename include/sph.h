@@ -1,0 +1,199 @@
+/*
+ * sph.h -- C-ABI of libsph, the GB300-native SPH neighbour-interaction path.
+ *
+ * The operations follow Theuns, Chalk, Schaller & Gonnet 2015, "Swift:
+ * task-based hydrodynamics and gravity for cosmological simulations":
+ *   - cubic cells no smaller than the smoothing length, so that every neighbour
+ *     of a particle lies in its own cell or an adjacent one (Sec. 3.1);
+ *   - the density sum, Eq. 1, with h_i set so that a given weighted number of
+ *     neighbours contributes (Sec. 2, after Eq. 2);
+ *   - the pressure-gradient sum, Eq. 2, in the Gadget-2 form the paper adopts
+ *     (Sec. 2), with signal-velocity artificial viscosity;
+ *   - marching particles forward in time (Sec. 2).
+ *
+ * Conventions
+ *   - Every pointer inside sph_particles is a DEVICE pointer owned by the caller
+ *     (except for sph_step_host, which takes HOST pointers).  The library never
+ *     frees caller memory.  Arrays are structure-of-arrays, length n, contiguous.
+ *   - The library owns its scratch (cell arrays, sort buffers, packed FP32
+ *     copies); it allocates it in sph_init / on first use and frees it in
+ *     sph_destroy.
+ *   - Every call enqueues its work on the stream given to sph_init and returns
+ *     after the last launch, EXCEPT where a call documents a host read (the
+ *     cell-grid size in sph_build_cells, the convergence count in sph_density,
+ *     the time step in sph_step).
+ *   - Calls return an sph_status.  No exception, abort or exit crosses the ABI.
+ *     sph_last_error() gives a one-line message for the last failure.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_ERR_INVALID_ARG = 1,    /* null pointer, n < 0, bad parameter value      */
+    SPH_ERR_CUDA = 2,           /* a CUDA runtime call failed (message kept)     */
+    SPH_ERR_NOT_CONVERGED = 3,  /* h iteration hit max_h_iter; results valid for */
+                                /* converged particles, last iterate for others  */
+    SPH_ERR_H_EXCEEDS_CELL = 4, /* some h > box/3: no periodic cell grid with at */
+                                /* least 3 cells per side can hold the support   */
+    SPH_ERR_TIMEOUT = 5,        /* a bounded device-side wait ran out            */
+    SPH_ERR_NAN = 6,            /* a non-finite input or result was detected     */
+    SPH_ERR_STATE = 7           /* call order violated (e.g. force before        */
+                                /* density on the current positions)             */
+} sph_status;
+
+typedef struct sph_ctx sph_ctx; /* opaque, library-owned */
+
+/* Flags for sph_params.flags */
+#define SPH_FLAG_TIMING 1u /* record CUDA events around the pair kernels */
+#define SPH_FLAG_NGB_HASH 2u /* density pass also writes a neighbour-set hash */
+
+typedef struct {
+    int64_t n;           /* particles; 0 <= n < 2^31                                  */
+    double box_size;     /* periodic box side L (> 0)                                */
+    float gamma;         /* adiabatic index of the ideal-gas EOS, P = (gamma-1) rho u */
+    float n_ngb;         /* target weighted neighbour number N_ngb (Sec. 2)           */
+    float h_tol;         /* converged when |N_w/N_ngb - 1| <= h_tol                   */
+    float alpha_visc;    /* artificial-viscosity strength alpha                      */
+    float cfl;           /* dt = cfl * min_i h_i / vsig_i                            */
+    float cell_factor;   /* cell side >= cell_factor * max h  (>= 1)                  */
+    int32_t max_h_iter;  /* cap on density passes per sph_density call               */
+    int32_t use_balsara; /* 1: viscosity scaled by the Balsara switch                */
+    int32_t kernel;      /* 0: cubic spline (the only kernel)                        */
+    uint32_t flags;      /* SPH_FLAG_*                                               */
+} sph_params;
+
+/*
+ * Particle arrays (caller-owned, device).  Inputs: x..h.  Outputs of the density
+ * pass: h (converged), rho, P, c, f, divv, curl, n_ngb.  Outputs of the force pass:
+ * ax, ay, az, dudt, vsig.  Units: box units for lengths, caller units otherwise.
+ *   x, y, z    absolute positions (FP64), wrapped into [0, L) by sph_build_cells
+ *   vx, vy, vz velocities (FP64)
+ *   m          mass; u specific internal energy; h smoothing length = kernel
+ *              support radius (W = 0 beyond h); on input h is the initial guess
+ *   rho        density, Eq. 1 (self term included)
+ *   P, c       pressure and sound speed from the ideal-gas EOS
+ *   f          grad-h factor [1 + h/(3 rho) d rho/dh]^-1
+ *   divv, curl velocity divergence and |curl| (SPH estimates at h_i)
+ *   n_ngb      number of j != i with r_ij < h_i
+ *   ax, ay, az hydrodynamic acceleration (pressure + viscosity)
+ *   dudt       rate of change of u
+ *   vsig       max signal velocity over the neighbours of i
+ */
+typedef struct {
+    double *x, *y, *z;
+    double *vx, *vy, *vz;
+    float *m, *u, *h;
+    float *rho, *P, *c, *f, *divv, *curl;
+    int32_t *n_ngb;
+    float *ax, *ay, *az, *dudt, *vsig;
+} sph_particles;
+
+/* Global quantities after a step (FP64 reductions, deterministic order). */
+typedef struct {
+    double momentum[3]; /* sum m v                                   */
+    double e_kin;       /* sum m v^2 / 2                             */
+    double e_th;        /* sum m u                                   */
+    double dt_next;     /* cfl * min h/vsig from the new force pass  */
+    int64_t u_floors;   /* kicks that drove u below 0 (clamped to 0) */
+} sph_conserved;
+
+/* Counters since the last sph_reset_stats (sph_get_stats synchronises the stream). */
+typedef struct {
+    int32_t nc;                /* cells per side of the current grid                 */
+    int32_t rebuilds;          /* cell rebuilds forced by h growing past the cell    */
+    int64_t n_cells;           /* nc^3                                               */
+    double cell_size;          /* L / nc                                             */
+    int64_t density_passes;    /* density-kernel launches                            */
+    int64_t force_passes;      /* force-kernel launches                              */
+    int64_t density_pairs;     /* directed pairs (i, j != i) with r_ij < h_i, summed */
+                               /* over every density pass actually run               */
+    int64_t density_targets;   /* active targets summed over density passes         */
+    int64_t force_pairs;       /* directed pairs with r_ij < max(h_i, h_j)           */
+    int64_t density_candidates;/* pair distance tests executed in density passes    */
+    int64_t force_candidates;  /* pair distance tests executed in force passes      */
+    double t_density_ms;       /* summed device time of density launches (TIMING)   */
+    double t_force_ms;         /* summed device time of force launches (TIMING)     */
+    double t_build_ms;         /* summed device time of cell builds (TIMING)        */
+    int64_t kernel_launches;   /* libsph kernels launched                           */
+} sph_stats;
+
+/* Fill *p with the defaults: gamma 5/3, n_ngb 48, h_tol 1e-4, alpha 0.8, cfl 0.1,
+ * cell_factor 1.1, max_h_iter 30, use_balsara 1, kernel 0, flags 0, box 1. */
+int sph_default_params(sph_params *p);
+
+/* Create a context for up to p->n particles on CUDA device `device`, enqueuing on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  *ctx is set
+ * to NULL on failure. */
+int sph_init(sph_ctx **ctx, const sph_params *p, int device, void *cuda_stream);
+
+/* Change the particle count (reallocates scratch if it grows). */
+int sph_set_n(sph_ctx *ctx, int64_t n);
+
+/* Sec. 3.1 cells: wrap positions into [0, L), choose nc = floor(L / (cell_factor *
+ * max h)) (>= 3), key each particle by its cell ((iz*nc+iy)*nc+ix with
+ * ix = floor(x * nc/L)), stable LSD radix sort by key, and permute x..h, vx..vz,
+ * m, u IN PLACE into cell order.  The composite permutation since the first build
+ * (or since sph_reset_ids) is kept: sph_get_permutation.  Host read: max h.
+ * Errors: SPH_ERR_H_EXCEEDS_CELL if max h > L/3. */
+int sph_build_cells(sph_ctx *ctx, sph_particles *parts);
+
+/* Eq. 1 with the smoothing-length iteration: starting from parts->h, Newton steps
+ * on N_w(h) = n_ngb (step clamped to [h/2, 2h]) re-running only unconverged
+ * particles, until all satisfy |N_w/N_ngb - 1| <= h_tol or max_h_iter passes ran.
+ * Rebuilds the cells (permuting the arrays again) if some h outgrows its cell.
+ * Writes h, rho, P, c, f, divv, curl, n_ngb.  *iters_out (may be NULL) = passes
+ * run.  Requires sph_build_cells on the current positions.  Host read: the
+ * unconverged count after each pass. */
+int sph_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out);
+
+/* Eq. 2 (Gadget-2 form) with artificial viscosity over pairs r_ij < max(h_i, h_j).
+ * Writes ax, ay, az, dudt, vsig.  Requires sph_density on the current state. */
+int sph_force(sph_ctx *ctx, sph_particles *parts);
+
+/* One kick-drift-kick step (Sec. 2 "marched forward in time"): kick v, u by dt/2
+ * with the current a, du/dt; drift x by dt (FP64) and wrap; rebuild cells; density
+ * and force on v, u predicted to the end of the step; kick by dt/2 with the new
+ * rates; u is floored at 0.  If no force pass ran on the current state, one runs
+ * first.  dt <= 0 selects the CFL step from the current vsig.  *dt_used and *out
+ * (either may be NULL) receive the step taken and the conserved quantities.
+ * Host read: dt and the reductions. */
+int sph_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_used, sph_conserved *out);
+
+/* sph_step on HOST arrays (pinned memory recommended): copies x..h, vx..vz, m, u,
+ * ax, ay, az, dudt, vsig to library-owned device buffers, steps, and copies every
+ * array of *host_parts back (in the new cell order).  Includes the copies in the
+ * call; synchronises the stream before returning. */
+int sph_step_host(sph_ctx *ctx, sph_particles *host_parts, double dt, double *dt_used,
+                  sph_conserved *out);
+
+/* Composite permutation: dev_perm[k] (device, int64, length n) = index, in the
+ * arrays given to the first sph_build_cells, of the particle now in slot k. */
+int sph_get_permutation(sph_ctx *ctx, int64_t *dev_perm);
+
+/* Forget the permutation: the next build numbers particles 0..n-1 afresh. */
+int sph_reset_ids(sph_ctx *ctx);
+
+/* Cell key of every slot (device, int32, length n) for the current grid. */
+int sph_get_cell_keys(sph_ctx *ctx, int32_t *dev_keys);
+
+/* Neighbour-set hash of the last density pass (needs SPH_FLAG_NGB_HASH): device,
+ * uint64, length n: sum over j != i with r_ij < h_i of splitmix64(perm id of j). */
+int sph_get_ngb_hash(sph_ctx *ctx, uint64_t *dev_hash);
+
+int sph_get_stats(sph_ctx *ctx, sph_stats *s);
+int sph_reset_stats(sph_ctx *ctx);
+const char *sph_last_error(const sph_ctx *ctx);
+void sph_destroy(sph_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_H */

@@ -1,0 +1,322 @@
+"""ctypes binding of libsph (include/sph.h): argument marshalling only.
+
+Every step of the SPH path runs in the CUDA kernels of ``libsph.so``; this module
+only turns torch CUDA tensors into the pointer structs the C-ABI takes.  There is
+no CPU fallback: if the library is missing or cannot load, :func:`lib` raises.
+
+The C entry points are exposed under their C names (``sph_init``,
+``sph_build_cells``, ``sph_density``, ``sph_force``, ``sph_step``, ...);
+:class:`Context` and :class:`Particles` are small conveniences on top.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SPH_OK = 0
+SPH_ERR_INVALID_ARG = 1
+SPH_ERR_CUDA = 2
+SPH_ERR_NOT_CONVERGED = 3
+SPH_ERR_H_EXCEEDS_CELL = 4
+SPH_ERR_TIMEOUT = 5
+SPH_ERR_NAN = 6
+SPH_ERR_STATE = 7
+SPH_FLAG_TIMING = 1
+SPH_FLAG_NGB_HASH = 2
+
+_NAMES = {0: "SPH_OK", 1: "SPH_ERR_INVALID_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_NOT_CONVERGED",
+          4: "SPH_ERR_H_EXCEEDS_CELL", 5: "SPH_ERR_TIMEOUT", 6: "SPH_ERR_NAN", 7: "SPH_ERR_STATE"}
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "sph.h")
+
+
+class SphError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class sph_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("box_size", ctypes.c_double), ("gamma", ctypes.c_float),
+                ("n_ngb", ctypes.c_float), ("h_tol", ctypes.c_float), ("alpha_visc", ctypes.c_float),
+                ("cfl", ctypes.c_float), ("cell_factor", ctypes.c_float),
+                ("max_h_iter", ctypes.c_int32), ("use_balsara", ctypes.c_int32),
+                ("kernel", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+_PFIELDS = ["x", "y", "z", "vx", "vy", "vz", "m", "u", "h", "rho", "P", "c", "f", "divv", "curl",
+            "n_ngb", "ax", "ay", "az", "dudt", "vsig"]
+
+
+class sph_particles(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in _PFIELDS]
+
+
+class sph_conserved(ctypes.Structure):
+    _fields_ = [("momentum", ctypes.c_double * 3), ("e_kin", ctypes.c_double),
+                ("e_th", ctypes.c_double), ("dt_next", ctypes.c_double),
+                ("u_floors", ctypes.c_int64)]
+
+
+class sph_stats(ctypes.Structure):
+    _fields_ = [("nc", ctypes.c_int32), ("rebuilds", ctypes.c_int32), ("n_cells", ctypes.c_int64),
+                ("cell_size", ctypes.c_double), ("density_passes", ctypes.c_int64),
+                ("force_passes", ctypes.c_int64), ("density_pairs", ctypes.c_int64),
+                ("density_targets", ctypes.c_int64), ("force_pairs", ctypes.c_int64),
+                ("density_candidates", ctypes.c_int64), ("force_candidates", ctypes.c_int64),
+                ("t_density_ms", ctypes.c_double), ("t_force_ms", ctypes.c_double),
+                ("t_build_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib(build_if_missing: bool = True):
+    """Load libsph.so (building it with nvcc first when asked).  Raises when the
+    library cannot be built or loaded -- there is no other implementation."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libsph.so not built ({path}); run paper_1508_00115_gb300.build")
+        L = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        C = ctypes.c_int
+        sig = {
+            "sph_default_params": (C, [ctypes.POINTER(sph_params)]),
+            "sph_init": (C, [ctypes.POINTER(P), ctypes.POINTER(sph_params), C, P]),
+            "sph_set_n": (C, [P, ctypes.c_int64]),
+            "sph_build_cells": (C, [P, ctypes.POINTER(sph_particles)]),
+            "sph_density": (C, [P, ctypes.POINTER(sph_particles), ctypes.POINTER(ctypes.c_int32)]),
+            "sph_force": (C, [P, ctypes.POINTER(sph_particles)]),
+            "sph_step": (C, [P, ctypes.POINTER(sph_particles), ctypes.c_double,
+                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(sph_conserved)]),
+            "sph_step_host": (C, [P, ctypes.POINTER(sph_particles), ctypes.c_double,
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(sph_conserved)]),
+            "sph_get_permutation": (C, [P, P]),
+            "sph_reset_ids": (C, [P]),
+            "sph_get_cell_keys": (C, [P, P]),
+            "sph_get_ngb_hash": (C, [P, P]),
+            "sph_get_stats": (C, [P, ctypes.POINTER(sph_stats)]),
+            "sph_reset_stats": (C, [P]),
+            "sph_last_error": (ctypes.c_char_p, [P]),
+            "sph_destroy": (None, [P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def header_symbols() -> list[str]:
+    """Entry points declared in include/sph.h."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(sph_\w+)\s*\(", text,
+                                 flags=re.M)))
+
+
+# ------------------------------------------------------------------ C names
+
+
+def sph_default_params() -> sph_params:
+    p = sph_params()
+    lib().sph_default_params(ctypes.byref(p))
+    return p
+
+
+def _check(rc: int, ctx=None, allow=()):
+    if rc != SPH_OK and rc not in allow:
+        msg = lib().sph_last_error(ctx).decode() if ctx else ""
+        raise SphError(rc, msg)
+    return rc
+
+
+def sph_init(params: sph_params, device: int = 0, stream: int | None = None):
+    h = ctypes.c_void_p()
+    rc = lib().sph_init(ctypes.byref(h), ctypes.byref(params), int(device),
+                        ctypes.c_void_p(stream or 0))
+    if rc != SPH_OK:
+        raise SphError(rc, "sph_init failed (check parameters / device)")
+    return h
+
+
+def sph_build_cells(ctx, parts: sph_particles) -> int:
+    return _check(lib().sph_build_cells(ctx, ctypes.byref(parts)), ctx)
+
+
+def sph_density(ctx, parts: sph_particles, allow_not_converged: bool = False) -> int:
+    it = ctypes.c_int32(0)
+    allow = (SPH_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    _check(lib().sph_density(ctx, ctypes.byref(parts), ctypes.byref(it)), ctx, allow)
+    return int(it.value)
+
+
+def sph_force(ctx, parts: sph_particles) -> int:
+    return _check(lib().sph_force(ctx, ctypes.byref(parts)), ctx)
+
+
+def sph_step(ctx, parts: sph_particles, dt: float = 0.0):
+    used = ctypes.c_double(0)
+    cons = sph_conserved()
+    _check(lib().sph_step(ctx, ctypes.byref(parts), float(dt), ctypes.byref(used),
+                          ctypes.byref(cons)), ctx)
+    return float(used.value), _cons_dict(cons)
+
+
+def sph_step_host(ctx, parts: sph_particles, dt: float = 0.0):
+    used = ctypes.c_double(0)
+    cons = sph_conserved()
+    _check(lib().sph_step_host(ctx, ctypes.byref(parts), float(dt), ctypes.byref(used),
+                               ctypes.byref(cons)), ctx)
+    return float(used.value), _cons_dict(cons)
+
+
+def _cons_dict(c: sph_conserved) -> dict:
+    return dict(momentum=np.array(list(c.momentum)), e_kin=c.e_kin, e_th=c.e_th,
+                e_tot=c.e_kin + c.e_th, dt_next=c.dt_next, u_floors=int(c.u_floors))
+
+
+def sph_get_stats(ctx) -> dict:
+    s = sph_stats()
+    _check(lib().sph_get_stats(ctx, ctypes.byref(s)), ctx)
+    return {k: getattr(s, k) for k, _ in sph_stats._fields_}
+
+
+def sph_reset_stats(ctx) -> int:
+    return _check(lib().sph_reset_stats(ctx), ctx)
+
+
+def sph_destroy(ctx) -> None:
+    if ctx:
+        lib().sph_destroy(ctx)
+
+
+# ------------------------------------------------------------ conveniences
+
+
+class Particles:
+    """Caller-owned device SoA (torch CUDA tensors) in the layout of sph_particles."""
+
+    F64 = ("x", "y", "z", "vx", "vy", "vz")
+    F32 = ("m", "u", "h", "rho", "P", "c", "f", "divv", "curl", "ax", "ay", "az", "dudt", "vsig")
+
+    def __init__(self, d: dict, device: str = "cuda", pin: bool = False):
+        import torch
+        n = int(np.asarray(d["x"]).size)
+        self.n = n
+        self.t = {}
+        for k in self.F64:
+            self.t[k] = self._mk(d.get(k), n, torch.float64, device, pin)
+        for k in self.F32:
+            self.t[k] = self._mk(d.get(k), n, torch.float32, device, pin)
+        self.t["n_ngb"] = self._mk(d.get("n_ngb"), n, torch.int32, device, pin)
+
+    @staticmethod
+    def _mk(v, n, dtype, device, pin):
+        import torch
+        if device == "cpu":
+            t = torch.zeros(n, dtype=dtype, pin_memory=pin)
+            if v is not None:
+                t.copy_(torch.as_tensor(np.asarray(v)).to(dtype))
+            return t
+        if v is None:
+            return torch.zeros(n, dtype=dtype, device=device)
+        return torch.as_tensor(np.asarray(v)).to(dtype).to(device)
+
+    def struct(self) -> sph_particles:
+        p = sph_particles()
+        for k in _PFIELDS:
+            setattr(p, k, ctypes.c_void_p(self.t[k].data_ptr()))
+        return p
+
+    def numpy(self) -> dict:
+        return {k: v.detach().cpu().numpy() for k, v in self.t.items()}
+
+
+class Context:
+    """Owns an sph_ctx; methods mirror the C entry points."""
+
+    def __init__(self, n: int, device: int = 0, stream=None, **overrides):
+        import torch
+        self.params = sph_default_params()
+        self.params.n = int(n)
+        for k, v in overrides.items():
+            setattr(self.params, k, v)
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.stream = stream
+        self.h = sph_init(self.params, device, stream)
+
+    def build_cells(self, parts: Particles):
+        self._p = parts.struct()
+        return sph_build_cells(self.h, self._p)
+
+    def density(self, parts: Particles, allow_not_converged=False) -> int:
+        return sph_density(self.h, parts.struct(), allow_not_converged)
+
+    def force(self, parts: Particles):
+        return sph_force(self.h, parts.struct())
+
+    def step(self, parts: Particles, dt: float = 0.0):
+        return sph_step(self.h, parts.struct(), dt)
+
+    def step_host(self, parts: Particles, dt: float = 0.0):
+        return sph_step_host(self.h, parts.struct(), dt)
+
+    def permutation(self) -> np.ndarray:
+        import torch
+        n = int(self.params.n)
+        t = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
+        _check(lib().sph_get_permutation(self.h, ctypes.c_void_p(t.data_ptr())), self.h)
+        torch.cuda.synchronize()
+        return t[:n].cpu().numpy()
+
+    def cell_keys(self) -> np.ndarray:
+        import torch
+        n = int(self.params.n)
+        t = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        _check(lib().sph_get_cell_keys(self.h, ctypes.c_void_p(t.data_ptr())), self.h)
+        torch.cuda.synchronize()
+        return t[:n].cpu().numpy()
+
+    def ngb_hash(self) -> np.ndarray:
+        import torch
+        n = int(self.params.n)
+        t = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
+        _check(lib().sph_get_ngb_hash(self.h, ctypes.c_void_p(t.data_ptr())), self.h)
+        torch.cuda.synchronize()
+        return t[:n].cpu().numpy().view(np.uint64)
+
+    def stats(self) -> dict:
+        return sph_get_stats(self.h)
+
+    def reset_stats(self):
+        return sph_reset_stats(self.h)
+
+    def last_error(self) -> str:
+        return lib().sph_last_error(self.h).decode()
+
+    def close(self):
+        if self.h:
+            sph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,513 @@
+// sph_api.cu -- the extern "C" entry points of libsph (declared in include/sph.h):
+// argument checks, scratch ownership, and the host-side ordering of the passes
+// (cells -> density with the h iteration -> force -> time step), which in the
+// paper's design is expressed as task dependencies (Theuns et al. 2015, Sec. 3.1:
+// densities must be known before pressure gradients).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+int red_scratch_doubles();  // sph_integrate.cu
+
+int fail(sph_ctx *ctx, int code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_fail(sph_ctx *ctx, cudaError_t e, const char *what)
+{
+    char buf[512];
+    snprintf(buf, sizeof buf, "CUDA error in %s: %s", what, cudaGetErrorString(e));
+    if (ctx) ctx->err = buf;
+    return SPH_ERR_CUDA;
+}
+
+void timer_begin(sph_ctx *ctx, int kind, cudaEvent_t *out_end)
+{
+    *out_end = nullptr;
+    if (!(ctx->p.flags & SPH_FLAG_TIMING)) return;
+    Timer t;
+    if (!ctx->free_timers.empty()) {
+        t = ctx->free_timers.back();
+        ctx->free_timers.pop_back();
+    } else {
+        if (cudaEventCreate(&t.a) != cudaSuccess) return;
+        if (cudaEventCreate(&t.b) != cudaSuccess) {
+            cudaEventDestroy(t.a);
+            return;
+        }
+    }
+    t.kind = kind;
+    cudaEventRecord(t.a, ctx->stream);
+    ctx->timers.push_back(t);
+    *out_end = t.b;
+}
+
+void timer_end(sph_ctx *ctx, cudaEvent_t end)
+{
+    if (end) cudaEventRecord(end, ctx->stream);
+}
+
+static void free_particles(sph_ctx *c)
+{
+    void *ptrs[] = {c->pos4, c->vel4, c->thermo4, c->upred, c->active, c->ids, c->ids_tmp, c->ngb_hash,
+                    c->keys, c->keys_alt, c->vals, c->vals_alt, c->hist, c->s64, c->s32, c->tiles};
+    for (void *p : ptrs) cudaFree(p);
+    c->pos4 = c->vel4 = c->thermo4 = nullptr;
+    c->upred = nullptr;
+    c->active = nullptr;
+    c->ids = c->ids_tmp = nullptr;
+    c->ngb_hash = nullptr;
+    c->keys = c->keys_alt = c->vals = c->vals_alt = c->hist = nullptr;
+    c->s64 = nullptr;
+    c->s32 = nullptr;
+    c->tiles = nullptr;
+    c->cap = 0;
+}
+
+static int alloc_particles(sph_ctx *c, int64_t cap)
+{
+    free_particles(c);
+    cap = std::max<int64_t>(cap, 1);
+    int64_t sort_tiles = (cap + 4095) / 4096;
+    c->tile_cap = cap + cap / kTile + 64;
+    SPH_CUDA(c, cudaMalloc(&c->pos4, sizeof(float4) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->vel4, sizeof(float4) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->thermo4, sizeof(float4) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->upred, sizeof(float) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->active, cap));
+    SPH_CUDA(c, cudaMalloc(&c->ids, sizeof(int64_t) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->ids_tmp, sizeof(int64_t) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->ngb_hash, sizeof(uint64_t) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->keys, sizeof(uint32_t) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->keys_alt, sizeof(uint32_t) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->vals, sizeof(uint32_t) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->vals_alt, sizeof(uint32_t) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->hist, sizeof(uint32_t) * 256 * sort_tiles));
+    SPH_CUDA(c, cudaMalloc(&c->s64, sizeof(double) * 6 * cap));
+    SPH_CUDA(c, cudaMalloc(&c->s32, sizeof(float) * 8 * cap));
+    SPH_CUDA(c, cudaMalloc(&c->tiles, sizeof(int4) * c->tile_cap));
+    SPH_CUDA(c, cudaMemsetAsync(c->ngb_hash, 0, sizeof(uint64_t) * cap, c->stream));
+    c->cap = cap;
+    return SPH_OK;
+}
+
+static bool parts_ok(const sph_particles *p)
+{
+    const void *a[] = {p->x,   p->y, p->z, p->vx,   p->vy,    p->vz, p->m,  p->u,  p->h,  p->rho, p->P,
+                       p->c,   p->f, p->divv, p->curl, p->n_ngb, p->ax, p->ay, p->az, p->dudt, p->vsig};
+    for (const void *q : a)
+        if (!q) return false;
+    return true;
+}
+
+static int check_params(const sph_params *p, std::string &why)
+{
+    if (p->n < 0 || p->n >= (1ll << 31)) why = "n must be in [0, 2^31)";
+    else if (!(p->box_size > 0) || !isfinite(p->box_size)) why = "box_size must be finite and > 0";
+    else if (!(p->gamma > 1.f)) why = "gamma must be > 1";
+    else if (!(p->n_ngb > 32.f / 3.f)) why = "n_ngb must exceed the self contribution 32/3";
+    else if (!(p->h_tol > 0.f)) why = "h_tol must be > 0";
+    else if (!(p->alpha_visc >= 0.f)) why = "alpha_visc must be >= 0";
+    else if (!(p->cfl > 0.f)) why = "cfl must be > 0";
+    else if (!(p->cell_factor >= 1.f) || !isfinite(p->cell_factor)) why = "cell_factor must be >= 1";
+    else if (p->max_h_iter < 1) why = "max_h_iter must be >= 1";
+    else if (p->kernel != 0) why = "kernel must be 0 (cubic spline)";
+    else return SPH_OK;
+    return SPH_ERR_INVALID_ARG;
+}
+
+static int read_counters(sph_ctx *ctx)
+{
+    SPH_CUDA(ctx, cudaMemcpyAsync(ctx->h_counters, ctx->counters, C_NCOUNTERS * sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return SPH_OK;
+}
+
+static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
+{
+    if (!ctx->built) return fail(ctx, SPH_ERR_STATE, "sph_density needs sph_build_cells on the current positions");
+    int n = (int)ctx->n;
+    int iters = 0;
+    unsigned long long unconv = 0;
+    if (n > 0) {
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, n, ctx->stream));
+        for (;;) {
+            const bool last = iters == ctx->p.max_h_iter - 1;
+            SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_UNCONV, 0, 2 * sizeof(unsigned long long),
+                                          ctx->stream));
+            int rc = run_density_pass(ctx, parts, last);
+            if (rc) return rc;
+            ++iters;
+            rc = read_counters(ctx);
+            if (rc) return rc;
+            unconv = ctx->h_counters[C_UNCONV];
+            if (unconv == 0 || last) break;
+            if (ctx->h_counters[C_HFLAG]) {
+                // some h outgrew its cell: re-bin with the new h (permutes the arrays)
+                cudaEvent_t end = nullptr;
+                timer_begin(ctx, 2, &end);
+                rc = build_cells(ctx, parts);
+                timer_end(ctx, end);
+                if (rc) return rc;
+                ctx->st.rebuilds++;
+                SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, n, ctx->stream));
+            }
+        }
+        int rc = sync_h(ctx, parts);
+        if (rc) return rc;
+    }
+    if (iters_out) *iters_out = iters;
+    ctx->density_valid = true;
+    ctx->hydro_valid = false;
+    if (unconv) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "%llu smoothing lengths not converged after %d passes", unconv, iters);
+        return fail(ctx, SPH_ERR_NOT_CONVERGED, buf);
+    }
+    return SPH_OK;
+}
+
+static int do_force(sph_ctx *ctx, sph_particles *parts)
+{
+    if (!ctx->density_valid) return fail(ctx, SPH_ERR_STATE, "sph_force needs sph_density on the current state");
+    if (ctx->n > 0) {
+        int rc = device_max_h(ctx, parts->h);
+        if (rc) return rc;
+        rc = run_force_pass(ctx, parts);
+        if (rc) return rc;
+    }
+    ctx->hydro_valid = true;
+    return SPH_OK;
+}
+
+static int do_build(sph_ctx *ctx, sph_particles *parts)
+{
+    cudaEvent_t end = nullptr;
+    timer_begin(ctx, 2, &end);
+    int rc = build_cells(ctx, parts);
+    timer_end(ctx, end);
+    ctx->hydro_valid = false;
+    return rc;
+}
+
+static int hydro(sph_ctx *ctx, sph_particles *parts)
+{
+    int rc = do_build(ctx, parts);
+    if (rc) return rc;
+    rc = do_density(ctx, parts, nullptr);
+    if (rc) return rc;
+    return do_force(ctx, parts);
+}
+
+static int do_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_used, sph_conserved *out)
+{
+    int rc;
+    ctx->pred_half = 0.0;
+    if (!ctx->hydro_valid) {
+        rc = hydro(ctx, parts);
+        if (rc) return rc;
+    }
+    if (!(dt > 0)) {
+        rc = cfl_dt(ctx, parts, &dt);
+        if (rc) return rc;
+        if (!isfinite(dt)) return fail(ctx, SPH_ERR_INVALID_ARG, "no signal velocity: pass an explicit dt");
+    }
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_FLOORS, 0, sizeof(unsigned long long), ctx->stream));
+    const double half = 0.5 * dt;
+    rc = kick(ctx, parts, half);
+    if (rc) return rc;
+    rc = drift(ctx, parts, dt);
+    if (rc) return rc;
+    // the hydro pass sees v and u predicted to the end of the step (vel4 / upred)
+    ctx->pred_half = half;
+    rc = hydro(ctx, parts);
+    ctx->pred_half = 0.0;
+    if (rc) return rc;
+    rc = kick(ctx, parts, half);
+    if (rc) return rc;
+    if (dt_used) *dt_used = dt;
+    if (out) {
+        rc = conserved(ctx, parts, out);
+        if (rc) return rc;
+        rc = cfl_dt(ctx, parts, &out->dt_next);
+        if (rc) return rc;
+    }
+    return SPH_OK;
+}
+
+}  // namespace sph
+
+using namespace sph;
+
+extern "C" {
+
+int sph_default_params(sph_params *p)
+{
+    if (!p) return SPH_ERR_INVALID_ARG;
+    memset(p, 0, sizeof *p);
+    p->n = 0;
+    p->box_size = 1.0;
+    p->gamma = 5.f / 3.f;
+    p->n_ngb = 48.f;
+    p->h_tol = 1e-4f;
+    p->alpha_visc = 0.8f;
+    p->cfl = 0.1f;
+    p->cell_factor = 1.1f;
+    p->max_h_iter = 30;
+    p->use_balsara = 1;
+    p->kernel = 0;
+    p->flags = 0;
+    return SPH_OK;
+}
+
+int sph_init(sph_ctx **out, const sph_params *p, int device, void *cuda_stream)
+{
+    if (!out) return SPH_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!p) return SPH_ERR_INVALID_ARG;
+    std::string why;
+    if (check_params(p, why)) return SPH_ERR_INVALID_ARG;
+    sph_ctx *c = new sph_ctx();
+    c->p = *p;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->n = p->n;
+    int rc = SPH_OK;
+    auto bail = [&](int code) {
+        sph_destroy(c);
+        return code;
+    };
+    if (cudaSetDevice(device) != cudaSuccess) return bail(SPH_ERR_CUDA);
+    if (cudaMalloc(&c->counters, C_NCOUNTERS * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMallocHost(&c->h_counters, C_NCOUNTERS * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_scalars, 8 * sizeof(float)) != cudaSuccess ||
+        cudaMallocHost(&c->h_scalars, 8 * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&c->d_red, red_scratch_doubles() * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->h_red, 8 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->scan_aux, kScanAuxCap * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&c->n_tiles, sizeof(int)) != cudaSuccess)
+        return bail(SPH_ERR_CUDA);
+    if (cudaMemsetAsync(c->counters, 0, C_NCOUNTERS * sizeof(unsigned long long), c->stream) != cudaSuccess)
+        return bail(SPH_ERR_CUDA);
+    rc = alloc_particles(c, c->n);
+    if (rc) return bail(rc);
+    *out = c;
+    return SPH_OK;
+}
+
+int sph_set_n(sph_ctx *ctx, int64_t n)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (n < 0 || n >= (1ll << 31)) return fail(ctx, SPH_ERR_INVALID_ARG, "n must be in [0, 2^31)");
+    if (n > ctx->cap) {
+        int rc = alloc_particles(ctx, n);
+        if (rc) return rc;
+    }
+    ctx->n = n;
+    ctx->p.n = n;
+    ctx->built = ctx->density_valid = ctx->hydro_valid = false;
+    ctx->ids_valid = false;
+    return SPH_OK;
+}
+
+int sph_build_cells(sph_ctx *ctx, sph_particles *parts)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!parts || (ctx->n > 0 && !parts_ok(parts))) return fail(ctx, SPH_ERR_INVALID_ARG, "null particle array");
+    ctx->pred_half = 0.0;
+    return do_build(ctx, parts);
+}
+
+int sph_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!parts || (ctx->n > 0 && !parts_ok(parts))) return fail(ctx, SPH_ERR_INVALID_ARG, "null particle array");
+    return do_density(ctx, parts, iters_out);
+}
+
+int sph_force(sph_ctx *ctx, sph_particles *parts)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!parts || (ctx->n > 0 && !parts_ok(parts))) return fail(ctx, SPH_ERR_INVALID_ARG, "null particle array");
+    return do_force(ctx, parts);
+}
+
+int sph_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_used, sph_conserved *out)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!parts || (ctx->n > 0 && !parts_ok(parts))) return fail(ctx, SPH_ERR_INVALID_ARG, "null particle array");
+    if (!isfinite(dt)) return fail(ctx, SPH_ERR_INVALID_ARG, "dt must be finite");
+    return do_step(ctx, parts, dt, dt_used, out);
+}
+
+int sph_step_host(sph_ctx *ctx, sph_particles *hp, double dt, double *dt_used, sph_conserved *out)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!hp || (ctx->n > 0 && !parts_ok(hp))) return fail(ctx, SPH_ERR_INVALID_ARG, "null particle array");
+    if (!isfinite(dt)) return fail(ctx, SPH_ERR_INVALID_ARG, "dt must be finite");
+    const int64_t n = ctx->n;
+    if (ctx->mirror_cap < n || !ctx->mirror_block) {
+        cudaFree(ctx->mirror_block);
+        ctx->mirror_block = nullptr;
+        int64_t cap = std::max<int64_t>(n, 1);
+        size_t bytes = (size_t)cap * (6 * 8 + 15 * 4) + 32 * 256;
+        SPH_CUDA(ctx, cudaMalloc(&ctx->mirror_block, bytes));
+        char *b = (char *)ctx->mirror_block;
+        auto take = [&](size_t sz) {
+            char *r = b;
+            b += (sz + 255) & ~(size_t)255;
+            return r;
+        };
+        sph_particles &m = ctx->dev_mirror;
+        m.x = (double *)take(8 * cap);
+        m.y = (double *)take(8 * cap);
+        m.z = (double *)take(8 * cap);
+        m.vx = (double *)take(8 * cap);
+        m.vy = (double *)take(8 * cap);
+        m.vz = (double *)take(8 * cap);
+        float **f32[] = {&m.m, &m.u, &m.h, &m.rho, &m.P, &m.c, &m.f, &m.divv, &m.curl,
+                         &m.ax, &m.ay, &m.az, &m.dudt, &m.vsig};
+        for (float **q : f32) *q = (float *)take(4 * cap);
+        m.n_ngb = (int32_t *)take(4 * cap);
+        ctx->mirror_cap = cap;
+    }
+    sph_particles &d = ctx->dev_mirror;
+    cudaStream_t s = ctx->stream;
+    const size_t b8 = 8 * (size_t)n, b4 = 4 * (size_t)n;
+    // inputs of a step: the state and the rates from the previous hydro pass
+    double *in64[][2] = {{d.x, hp->x}, {d.y, hp->y}, {d.z, hp->z}, {d.vx, hp->vx}, {d.vy, hp->vy}, {d.vz, hp->vz}};
+    float *in32[][2] = {{d.m, hp->m},   {d.u, hp->u},   {d.h, hp->h},       {d.ax, hp->ax},
+                        {d.ay, hp->ay}, {d.az, hp->az}, {d.dudt, hp->dudt}, {d.vsig, hp->vsig}};
+    for (auto &q : in64) SPH_CUDA(ctx, cudaMemcpyAsync(q[0], q[1], b8, cudaMemcpyHostToDevice, s));
+    for (auto &q : in32) SPH_CUDA(ctx, cudaMemcpyAsync(q[0], q[1], b4, cudaMemcpyHostToDevice, s));
+    // the device copies replace whatever the context held: cells must be rebuilt
+    ctx->built = ctx->density_valid = false;
+    int rc = do_step(ctx, &d, dt, dt_used, out);
+    if (rc) return rc;
+    for (auto &q : in64) SPH_CUDA(ctx, cudaMemcpyAsync(q[1], q[0], b8, cudaMemcpyDeviceToHost, s));
+    for (auto &q : in32) SPH_CUDA(ctx, cudaMemcpyAsync(q[1], q[0], b4, cudaMemcpyDeviceToHost, s));
+    float *out32[][2] = {{d.rho, hp->rho}, {d.P, hp->P}, {d.c, hp->c}, {d.f, hp->f}, {d.divv, hp->divv},
+                         {d.curl, hp->curl}};
+    for (auto &q : out32) SPH_CUDA(ctx, cudaMemcpyAsync(q[1], q[0], b4, cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(ctx, cudaMemcpyAsync(hp->n_ngb, d.n_ngb, b4, cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(ctx, cudaStreamSynchronize(s));
+    return SPH_OK;
+}
+
+int sph_get_permutation(sph_ctx *ctx, int64_t *dev_perm)
+{
+    if (!ctx || !dev_perm) return SPH_ERR_INVALID_ARG;
+    if (!ctx->ids_valid) return fail(ctx, SPH_ERR_STATE, "no cell build yet");
+    SPH_CUDA(ctx, cudaMemcpyAsync(dev_perm, ctx->ids, sizeof(int64_t) * ctx->n, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+    return SPH_OK;
+}
+
+int sph_reset_ids(sph_ctx *ctx)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    ctx->ids_valid = false;
+    return SPH_OK;
+}
+
+int sph_get_cell_keys(sph_ctx *ctx, int32_t *dev_keys)
+{
+    if (!ctx || !dev_keys) return SPH_ERR_INVALID_ARG;
+    if (!ctx->built) return fail(ctx, SPH_ERR_STATE, "no cell build on the current positions");
+    SPH_CUDA(ctx, cudaMemcpyAsync(dev_keys, ctx->keys, sizeof(int32_t) * ctx->n, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+    return SPH_OK;
+}
+
+int sph_get_ngb_hash(sph_ctx *ctx, uint64_t *dev_hash)
+{
+    if (!ctx || !dev_hash) return SPH_ERR_INVALID_ARG;
+    if (!(ctx->p.flags & SPH_FLAG_NGB_HASH)) return fail(ctx, SPH_ERR_STATE, "SPH_FLAG_NGB_HASH not set");
+    SPH_CUDA(ctx, cudaMemcpyAsync(dev_hash, ctx->ngb_hash, sizeof(uint64_t) * ctx->n, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+    return SPH_OK;
+}
+
+int sph_get_stats(sph_ctx *ctx, sph_stats *s)
+{
+    if (!ctx || !s) return SPH_ERR_INVALID_ARG;
+    int rc = read_counters(ctx);
+    if (rc) return rc;
+    double t[3] = {0, 0, 0};
+    for (Timer &tm : ctx->timers) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, tm.a, tm.b) == cudaSuccess) t[tm.kind] += ms;
+    }
+    sph_stats &st = ctx->st;
+    st.density_pairs = (int64_t)ctx->h_counters[C_DPAIRS];
+    st.force_pairs = (int64_t)ctx->h_counters[C_FPAIRS];
+    st.density_candidates = (int64_t)ctx->h_counters[C_DCAND];
+    st.force_candidates = (int64_t)ctx->h_counters[C_FCAND];
+    st.density_targets = (int64_t)ctx->h_counters[C_DTARGETS];
+    st.t_density_ms = t[0];
+    st.t_force_ms = t[1];
+    st.t_build_ms = t[2];
+    *s = st;
+    return SPH_OK;
+}
+
+int sph_reset_stats(sph_ctx *ctx)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (Timer &t : ctx->timers) ctx->free_timers.push_back(t);
+    ctx->timers.clear();
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_DPAIRS, 0, 6 * sizeof(unsigned long long), ctx->stream));
+    int nc = ctx->st.nc;
+    int64_t ncell = ctx->st.n_cells;
+    double cs = ctx->st.cell_size;
+    memset(&ctx->st, 0, sizeof ctx->st);
+    ctx->st.nc = nc;
+    ctx->st.n_cells = ncell;
+    ctx->st.cell_size = cs;
+    return SPH_OK;
+}
+
+const char *sph_last_error(const sph_ctx *ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+void sph_destroy(sph_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    free_particles(ctx);
+    cudaFree(ctx->cell_start);
+    cudaFree(ctx->cell_tiles);
+    cudaFree(ctx->counters);
+    cudaFreeHost(ctx->h_counters);
+    cudaFree(ctx->d_scalars);
+    cudaFreeHost(ctx->h_scalars);
+    cudaFree(ctx->d_red);
+    cudaFreeHost(ctx->h_red);
+    cudaFree(ctx->scan_aux);
+    cudaFree(ctx->n_tiles);
+    cudaFree(ctx->mirror_block);
+    for (Timer &t : ctx->timers) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (Timer &t : ctx->free_timers) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,468 @@
+// sph_cells.cu -- cubic cells no smaller than the smoothing length (Theuns et al.
+// 2015, Sec. 3.1): periodic wrap, cell keys, a stable LSD radix sort of the
+// particles by cell, the in-place permutation of the caller's arrays into cell
+// order (particles of a cell contiguous in memory, Sec. 3.1), cell ranges and the
+// warp work items (tiles of up to 32 targets of one cell).
+#include <math.h>
+
+#include <algorithm>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+// ----------------------------------------------------------------- exclusive scan
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
+{
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive scan of one value per thread over the block; returns the block total.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *sh_warp, uint32_t &total)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t inc = warp_incl_scan(v);
+    if (lane == 31) sh_warp[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = lane < nw ? sh_warp[lane] : 0u;
+        uint32_t ti = warp_incl_scan(t);
+        if (lane < nw) sh_warp[lane] = ti - t;
+        if (lane == 31) sh_warp[32] = ti;
+    }
+    __syncthreads();
+    uint32_t r = sh_warp[w] + inc - v;
+    total = sh_warp[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__restrict__ in, int64_t n,
+                                                              uint32_t *__restrict__ bsum)
+{
+    __shared__ uint32_t sh[33];
+    int64_t base = (int64_t)blockIdx.x * kScanChunk;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    uint32_t tot;
+    block_excl_scan(s, sh, tot);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// single block: in-place exclusive scan of nb block sums, in chunks with a carry
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(uint32_t *bsum, int64_t nb)
+{
+    __shared__ uint32_t sh[33];
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < nb; base += kScanThreads) {
+        int64_t i = base + threadIdx.x;
+        uint32_t v = i < nb ? bsum[i] : 0u;
+        uint32_t tot;
+        uint32_t e = block_excl_scan(v, sh, tot);
+        if (i < nb) bsum[i] = carry + e;
+        carry += tot;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t *in, uint32_t *out, int64_t n,
+                                                            const uint32_t *__restrict__ bsum)
+{
+    __shared__ uint32_t sh[33];
+    int64_t base = (int64_t)blockIdx.x * kScanChunk + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k;
+        v[k] = i < n ? in[i] : 0u;
+        s += v[k];
+    }
+    uint32_t tot;
+    uint32_t e = block_excl_scan(s, sh, tot) + bsum[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k;
+        if (i < n) out[i] = e;
+        e += v[k];
+    }
+}
+
+int exclusive_scan_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n)
+{
+    if (n <= 0) return SPH_OK;
+    int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(in, n, ctx->scan_aux);
+    SPH_LAUNCH(ctx, "scan reduce");
+    k_scan_top<<<1, kScanThreads, 0, ctx->stream>>>(ctx->scan_aux, nb);
+    SPH_LAUNCH(ctx, "scan top");
+    k_scan_down<<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(in, out, n, ctx->scan_aux);
+    SPH_LAUNCH(ctx, "scan down");
+    return SPH_OK;
+}
+
+// ------------------------------------------------------------ LSD radix sort
+// Keys are cell indices; 8-bit digits; one tile = 256 threads x 16 keys.  Ranks
+// inside a tile are stable: warp w owns the contiguous sub-tile [w*512, w*512+512)
+// and visits it in rounds of 32 consecutive keys; equal digits in a round are
+// ranked by lane (match_any), rounds in order, warps in order.
+
+constexpr int kRsThreads = 256;
+constexpr int kRsItems = 16;
+constexpr int kRsTile = kRsThreads * kRsItems;  // 4096
+constexpr int kRsWarps = kRsThreads / 32;
+
+__global__ void __launch_bounds__(kRsThreads) k_radix_hist(const uint32_t *__restrict__ keys, int n, int shift,
+                                                           uint32_t *__restrict__ hist, int ntiles)
+{
+    __shared__ uint32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kRsTile;
+#pragma unroll 4
+    for (int k = 0; k < kRsItems; ++k) {
+        int64_t i = base + k * kRsThreads + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const uint32_t *__restrict__ kin,
+                                                              const uint32_t *__restrict__ vin,
+                                                              uint32_t *__restrict__ kout,
+                                                              uint32_t *__restrict__ vout, int n, int shift,
+                                                              const uint32_t *__restrict__ offs, int ntiles)
+{
+    __shared__ uint32_t wcnt[kRsWarps][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
+    __syncwarp();
+    const int64_t base = (int64_t)blockIdx.x * kRsTile + (int64_t)w * (kRsItems * 32);
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t key[kRsItems], val[kRsItems];
+    uint16_t rank[kRsItems];
+#pragma unroll
+    for (int it = 0; it < kRsItems; ++it) {
+        int64_t i = base + it * 32 + lane;
+        bool ok = i < n;
+        uint32_t k = ok ? kin[i] : 0u;
+        key[it] = k;
+        val[it] = ok ? (vin ? vin[i] : (uint32_t)i) : 0u;
+        uint32_t d = ok ? ((k >> shift) & 255u) : 256u;
+        unsigned peers = __match_any_sync(kFull, d);
+        uint32_t before = ok ? wcnt[w][d] : 0u;
+        rank[it] = (uint16_t)(before + __popc(peers & lt));
+        __syncwarp();
+        int leader = 31 - __clz(peers);
+        if (ok && lane == leader) wcnt[w][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // exclusive prefix of the per-warp counts, per digit, in warp order
+    __shared__ uint32_t woff[kRsWarps][256];
+    {
+        int d = threadIdx.x;  // 256 threads = 256 digits
+        uint32_t s = 0;
+#pragma unroll
+        for (int ww = 0; ww < kRsWarps; ++ww) {
+            woff[ww][d] = s;
+            s += wcnt[ww][d];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kRsItems; ++it) {
+        int64_t i = base + it * 32 + lane;
+        if (i < n) {
+            uint32_t d = (key[it] >> shift) & 255u;
+            uint32_t dst = offs[(int64_t)d * ntiles + blockIdx.x] + woff[w][d] + rank[it];
+            kout[dst] = key[it];
+            vout[dst] = val[it];
+        }
+    }
+}
+
+// Sorts ctx->keys (n entries, key_bits significant) stably; values start as the
+// identity.  On return ctx->keys / ctx->vals hold the sorted keys / source slots.
+static int radix_sort(sph_ctx *ctx, int n, int key_bits)
+{
+    int ntiles = (n + kRsTile - 1) / kRsTile;
+    uint32_t *kin = ctx->keys, *kout = ctx->keys_alt;
+    uint32_t *vin = nullptr, *vout = ctx->vals_alt;
+    int passes = std::max(1, (key_bits + 7) / 8);
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        k_radix_hist<<<ntiles, kRsThreads, 0, ctx->stream>>>(kin, n, shift, ctx->hist, ntiles);
+        SPH_LAUNCH(ctx, "radix histogram");
+        int rc = exclusive_scan_u32(ctx, ctx->hist, ctx->hist, (int64_t)256 * ntiles);
+        if (rc) return rc;
+        k_radix_scatter<<<ntiles, kRsThreads, 0, ctx->stream>>>(kin, vin, kout, vout, n, shift, ctx->hist,
+                                                               ntiles);
+        SPH_LAUNCH(ctx, "radix scatter");
+        std::swap(kin, kout);
+        vin = vout;
+        vout = (vin == ctx->vals_alt) ? ctx->vals : ctx->vals_alt;
+    }
+    if (kin != ctx->keys) std::swap(ctx->keys, ctx->keys_alt);
+    if (vin != ctx->vals) std::swap(ctx->vals, ctx->vals_alt);
+    return SPH_OK;
+}
+
+// -------------------------------------------------------- wrap, key, gather
+
+struct GridDev {
+    int nc;
+    double box, s, L64;
+};
+
+__device__ __forceinline__ double wrap64(double v, double box)
+{
+    double w = __dsub_rn(v, __dmul_rn(box, floor(__ddiv_rn(v, box))));
+    if (w >= box) w = __dsub_rn(w, box);
+    return w;
+}
+
+__device__ __forceinline__ int cell_of(double v, double s, int nc)
+{
+    int c = (int)floor(__dmul_rn(v, s));
+    return c < 0 ? 0 : (c > nc - 1 ? nc - 1 : c);
+}
+
+__global__ void k_wrap_key(double *x, double *y, double *z, int n, GridDev g, uint32_t *__restrict__ keys)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double a = wrap64(x[i], g.box), b = wrap64(y[i], g.box), c = wrap64(z[i], g.box);
+    x[i] = a;
+    y[i] = b;
+    z[i] = c;
+    int ix = cell_of(a, g.s, g.nc), iy = cell_of(b, g.s, g.nc), iz = cell_of(c, g.s, g.nc);
+    keys[i] = (uint32_t)((iz * g.nc + iy) * g.nc + ix);
+}
+
+struct GatherArgs {
+    sph_particles P;
+    const uint32_t *perm, *skeys;
+    double *s64;
+    float *s32;
+    int64_t cap;
+    const int64_t *ids_in;
+    int64_t *ids_out;
+    int ids_valid;
+    float4 *pos4, *vel4;
+    float *upred;
+    double pred_half;
+    int n;
+    GridDev g;
+};
+
+__global__ void k_gather(GatherArgs a)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.n) return;
+    int src = (int)a.perm[p];
+    const sph_particles &P = a.P;
+    double x = P.x[src], y = P.y[src], z = P.z[src];
+    double vx = P.vx[src], vy = P.vy[src], vz = P.vz[src];
+    float m = P.m[src], u = P.u[src], h = P.h[src];
+    float ax = P.ax[src], ay = P.ay[src], az = P.az[src], du = P.dudt[src], vs = P.vsig[src];
+    uint32_t key = a.skeys[p];
+    int nc = a.g.nc;
+    int ix = key % nc, iy = (key / nc) % nc, iz = key / (nc * nc);
+    double cx = ((double)ix + 0.5) * a.g.L64, cy = ((double)iy + 0.5) * a.g.L64,
+           cz = ((double)iz + 0.5) * a.g.L64;
+    a.pos4[p] = make_float4((float)(x - cx), (float)(y - cy), (float)(z - cz), h);
+    double ph = a.pred_half;
+    a.vel4[p] = make_float4((float)(vx + (double)ax * ph), (float)(vy + (double)ay * ph),
+                            (float)(vz + (double)az * ph), m);
+    double up = (double)u + (double)du * ph;
+    a.upred[p] = (float)(up > 0.0 ? up : 0.0);
+    int64_t c = a.cap;
+    a.s64[p] = x;
+    a.s64[c + p] = y;
+    a.s64[2 * c + p] = z;
+    a.s64[3 * c + p] = vx;
+    a.s64[4 * c + p] = vy;
+    a.s64[5 * c + p] = vz;
+    a.s32[p] = m;
+    a.s32[c + p] = u;
+    a.s32[2 * c + p] = h;
+    a.s32[3 * c + p] = ax;
+    a.s32[4 * c + p] = ay;
+    a.s32[5 * c + p] = az;
+    a.s32[6 * c + p] = du;
+    a.s32[7 * c + p] = vs;
+    a.ids_out[p] = a.ids_valid ? a.ids_in[src] : (int64_t)src;
+}
+
+__global__ void k_copy_back(sph_particles P, const double *__restrict__ s64, const float *__restrict__ s32,
+                            int64_t cap, int n)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int64_t c = cap;
+    P.x[p] = s64[p];
+    P.y[p] = s64[c + p];
+    P.z[p] = s64[2 * c + p];
+    P.vx[p] = s64[3 * c + p];
+    P.vy[p] = s64[4 * c + p];
+    P.vz[p] = s64[5 * c + p];
+    P.m[p] = s32[p];
+    P.u[p] = s32[c + p];
+    P.h[p] = s32[2 * c + p];
+    P.ax[p] = s32[3 * c + p];
+    P.ay[p] = s32[4 * c + p];
+    P.az[p] = s32[5 * c + p];
+    P.dudt[p] = s32[6 * c + p];
+    P.vsig[p] = s32[7 * c + p];
+}
+
+// cell_start[c] = first slot with key >= c (lower bound), c in [0, n_cells]
+__global__ void k_cell_start(const uint32_t *__restrict__ skeys, int n, int64_t ncells, int *__restrict__ cs)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > ncells) return;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((int64_t)skeys[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    cs[c] = lo;
+}
+
+__global__ void k_cell_tiles(const int *__restrict__ cs, int64_t ncells, uint32_t *__restrict__ nt)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    int cnt = cs[c + 1] - cs[c];
+    nt[c] = (uint32_t)((cnt + kTile - 1) / kTile);
+}
+
+__global__ void k_tiles_write(const int *__restrict__ cs, int64_t ncells, const uint32_t *__restrict__ toff,
+                              int4 *__restrict__ tiles, int *__restrict__ n_tiles)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    int s = cs[c], cnt = cs[c + 1] - s;
+    uint32_t off = toff[c];
+    int k = 0;
+    for (int b = 0; b < cnt; b += kTile, ++k)
+        tiles[off + k] = make_int4((int)c, s + b, min(kTile, cnt - b), 0);
+    if (c == ncells - 1) *n_tiles = (int)(off + k);
+}
+
+static int ensure_cells(sph_ctx *ctx, int64_t ncells)
+{
+    if (ncells + 1 > ctx->cell_cap) {
+        cudaFree(ctx->cell_start);
+        cudaFree(ctx->cell_tiles);
+        ctx->cell_start = nullptr;
+        ctx->cell_tiles = nullptr;
+        int64_t cap = ncells + 1 + 1024;
+        SPH_CUDA(ctx, cudaMalloc(&ctx->cell_start, sizeof(int) * cap));
+        SPH_CUDA(ctx, cudaMalloc(&ctx->cell_tiles, sizeof(uint32_t) * cap));
+        ctx->cell_cap = cap;
+    }
+    // the scan of per-cell tile counts needs ceil(ncells / chunk) block sums
+    int64_t nb = (ncells + kScanChunk - 1) / kScanChunk + 1;
+    if (nb > kScanAuxCap) return fail(ctx, SPH_ERR_INVALID_ARG, "cell grid too large for scan scratch");
+    return SPH_OK;
+}
+
+static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+int build_cells(sph_ctx *ctx, sph_particles *parts)
+{
+    const int n = (int)ctx->n;
+    const double box = ctx->p.box_size;
+    float hmax = (float)(box / 3.0);  // an empty set gets the coarsest grid
+    int rc = SPH_OK;
+    if (n > 0) rc = reduce_max_h(ctx, parts->h, &hmax);
+    if (rc) return rc;
+    if (!(hmax > 0.f) || !isfinite(hmax))
+        return fail(ctx, SPH_ERR_NAN, "smoothing lengths must be finite and > 0");
+    if ((double)hmax > box / 3.0)
+        return fail(ctx, SPH_ERR_H_EXCEEDS_CELL, "max h exceeds box/3: no periodic grid with >= 3 cells");
+    double hc = (double)hmax * (double)ctx->p.cell_factor;
+    int nc = (int)floor(box / hc);
+    int cap_n = (int)floor(cbrt(8.0 * (double)std::max(n, 1)));
+    nc = std::min(nc, std::min(kMaxNc, std::max(3, cap_n)));
+    if (nc < 3) nc = 3;  // hmax <= box/3 guarantees cells of side box/3 hold the support
+    Grid &g = ctx->grid;
+    g.nc = nc;
+    g.n_cells = (int64_t)nc * nc * nc;
+    g.L64 = box / nc;
+    g.L32 = (float)g.L64;
+    g.inv_s = (double)nc / box;
+    int bits = 1;
+    while ((1ll << bits) < g.n_cells) ++bits;
+    g.key_bits = bits;
+    rc = ensure_cells(ctx, g.n_cells);
+    if (rc) return rc;
+
+    GridDev gd{nc, box, g.inv_s, g.L64};
+    if (n > 0) {
+        k_wrap_key<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(parts->x, parts->y, parts->z, n, gd, ctx->keys);
+        SPH_LAUNCH(ctx, "wrap/key");
+        rc = radix_sort(ctx, n, bits);
+        if (rc) return rc;
+        GatherArgs ga;
+        ga.P = *parts;
+        ga.perm = ctx->vals;
+        ga.skeys = ctx->keys;
+        ga.s64 = ctx->s64;
+        ga.s32 = ctx->s32;
+        ga.cap = ctx->cap;
+        ga.ids_in = ctx->ids;
+        ga.ids_out = ctx->ids_tmp;
+        ga.ids_valid = ctx->ids_valid ? 1 : 0;
+        ga.pos4 = ctx->pos4;
+        ga.vel4 = ctx->vel4;
+        ga.upred = ctx->upred;
+        ga.pred_half = ctx->pred_half;
+        ga.n = n;
+        ga.g = gd;
+        k_gather<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(ga);
+        SPH_LAUNCH(ctx, "gather");
+        k_copy_back<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(*parts, ctx->s64, ctx->s32, ctx->cap, n);
+        SPH_LAUNCH(ctx, "copy back");
+        std::swap(ctx->ids, ctx->ids_tmp);
+        ctx->ids_valid = true;
+    }
+    k_cell_start<<<blocks_for(g.n_cells + 1, 256), 256, 0, ctx->stream>>>(ctx->keys, n, g.n_cells,
+                                                                         ctx->cell_start);
+    SPH_LAUNCH(ctx, "cell start");
+    k_cell_tiles<<<blocks_for(g.n_cells, 256), 256, 0, ctx->stream>>>(ctx->cell_start, g.n_cells,
+                                                                     ctx->cell_tiles);
+    SPH_LAUNCH(ctx, "cell tiles");
+    rc = exclusive_scan_u32(ctx, ctx->cell_tiles, ctx->cell_tiles, g.n_cells);
+    if (rc) return rc;
+    k_tiles_write<<<blocks_for(g.n_cells, 256), 256, 0, ctx->stream>>>(ctx->cell_start, g.n_cells,
+                                                                      ctx->cell_tiles, ctx->tiles,
+                                                                      ctx->n_tiles);
+    SPH_LAUNCH(ctx, "tiles");
+    ctx->built = true;
+    ctx->density_valid = false;
+    ctx->st.nc = nc;
+    ctx->st.n_cells = g.n_cells;
+    ctx->st.cell_size = g.L64;
+    return SPH_OK;
+}
+
+}  // namespace sph

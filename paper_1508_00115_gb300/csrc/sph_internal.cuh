@@ -1,0 +1,215 @@
+// sph_internal.cuh -- library-private declarations shared by the libsph sources.
+//
+// Layout in HBM (all library-owned unless noted, n = particle count, cell order):
+//   caller SoA (FP64 x,y,z,vx,vy,vz; FP32 m,u,h and outputs)  -- caller-owned
+//   pos4[n]     float4 {x - c_cell, y - c_cell, z - c_cell, h}  cell-relative FP32
+//   vel4[n]     float4 {vx, vy, vz, m} (FP32; predicted velocities inside a step)
+//   thermo4[n]  float4 {rho, A = f P / rho^2, c, B}  written by the density pass
+//   upred[n]    FP32 internal energy seen by the pressure (predicted inside a step)
+//   ids[n]      int64 composite permutation (original index of each slot)
+//   cell_start[n_cells + 1], tiles[n_tiles]  cell ranges and warp work items
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sph.h"
+
+namespace sph {
+
+constexpr float kSigma = 2.54647908947032550f;  // 8/pi, 3-D cubic-spline normalisation
+constexpr float kFourPi3 = 4.18879020478639098f; // 4 pi / 3
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kTile = 32;             // targets per warp work item
+constexpr int kMaxNc = 512;           // cells per side cap
+constexpr int64_t kScanAuxCap = 65536; // block sums of one exclusive scan (4096 items/block)
+// FP32 distance tests within kBandK * h * (h + L) of the cutoff are re-decided in
+// FP64 from the absolute positions (2^-19; the FP32 error bound is ~2^-21 h(3.5L+h)).
+constexpr float kBandK = 1.9073486328125e-06f;
+// Box pruning keeps sources up to (1 + kPruneMargin) H^2 so that no pair the FP32 or
+// FP64 test accepts is pruned.
+constexpr float kPruneMargin = 2.44140625e-04f;  // 2^-12
+
+// device counters (unsigned long long slots)
+enum Counter {
+    C_UNCONV = 0,     // unconverged particles after the last density pass
+    C_HFLAG = 1,      // some h outgrew the cell side
+    C_DPAIRS = 2,     // density interactions
+    C_FPAIRS = 3,     // force interactions
+    C_DCAND = 4,      // density candidate tests
+    C_FCAND = 5,      // force candidate tests
+    C_FLOORS = 6,     // u floors
+    C_DTARGETS = 7,   // active density targets
+    C_NCOUNTERS = 16
+};
+
+struct Grid {
+    int nc = 0;
+    int64_t n_cells = 0;
+    double L64 = 0;   // cell side (box / nc)
+    float L32 = 0;    // cell side, FP32
+    double inv_s = 0; // nc / box
+    int key_bits = 0;
+};
+
+struct Timer {
+    cudaEvent_t a, b;
+    int kind;  // 0 density, 1 force, 2 build
+};
+
+}  // namespace sph
+
+struct sph_ctx {
+    sph_params p{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t n = 0, cap = 0;
+
+    // packed particle data
+    float4 *pos4 = nullptr, *vel4 = nullptr, *thermo4 = nullptr;
+    float *upred = nullptr;
+    uint8_t *active = nullptr;
+    int64_t *ids = nullptr, *ids_tmp = nullptr;
+    uint64_t *ngb_hash = nullptr;
+    // sort
+    uint32_t *keys = nullptr, *keys_alt = nullptr, *vals = nullptr, *vals_alt = nullptr;
+    uint32_t *hist = nullptr;  // 256 * n_sort_tiles
+    uint32_t *scan_aux = nullptr;
+    int64_t hist_cap = 0;
+    // permutation scratch (gather targets before the copy back)
+    double *s64 = nullptr;  // 6 * cap
+    float *s32 = nullptr;   // 8 * cap
+    // cells
+    sph::Grid grid;
+    int *cell_start = nullptr;
+    int64_t cell_cap = 0;
+    int4 *tiles = nullptr;
+    int64_t tile_cap = 0;
+    int *n_tiles = nullptr;      // device scalar
+    uint32_t *cell_tiles = nullptr;  // per-cell tile counts -> offsets
+    // scalars
+    unsigned long long *counters = nullptr;  // device
+    unsigned long long *h_counters = nullptr; // pinned host mirror
+    float *d_scalars = nullptr;   // [0] max h, [1] min h/vsig
+    float *h_scalars = nullptr;   // pinned
+    double *d_red = nullptr;      // FP64 reduction partials
+    double *h_red = nullptr;      // pinned
+    int64_t red_blocks = 0;
+    // host-buffer stepping
+    sph_particles dev_mirror{};
+    int64_t mirror_cap = 0;
+    void *mirror_block = nullptr;
+
+    bool ids_valid = false;   // ids hold a permutation
+    bool built = false;       // cells match the current positions
+    bool density_valid = false;
+    bool hydro_valid = false; // a, dudt, vsig match the current state
+    double pred_half = 0.0;   // prediction interval used when gathering vel4/upred
+
+    // statistics
+    sph_stats st{};
+    std::vector<sph::Timer> timers;
+    std::vector<sph::Timer> free_timers;
+    std::string err;
+};
+
+namespace sph {
+
+// error plumbing -------------------------------------------------------------
+int fail(sph_ctx *ctx, int code, const std::string &msg);
+int cuda_fail(sph_ctx *ctx, cudaError_t e, const char *what);
+#define SPH_CUDA(ctx, call)                                          \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return sph::cuda_fail(ctx, e_, #call); \
+    } while (0)
+// after every kernel launch: count it and surface launch errors
+#define SPH_LAUNCH(ctx, what)                                         \
+    do {                                                              \
+        (ctx)->st.kernel_launches++;                                  \
+        cudaError_t e_ = cudaGetLastError();                          \
+        if (e_ != cudaSuccess) return sph::cuda_fail(ctx, e_, what);  \
+    } while (0)
+
+// timing
+void timer_begin(sph_ctx *ctx, int kind, cudaEvent_t *out_end);
+void timer_end(sph_ctx *ctx, cudaEvent_t end);
+
+// launch wrappers (defined in the .cu files) ---------------------------------
+int build_cells(sph_ctx *ctx, sph_particles *parts);            // sph_cells.cu
+int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass);  // sph_pairs.cu
+int run_force_pass(sph_ctx *ctx, sph_particles *parts);                    // sph_pairs.cu
+int sync_h(sph_ctx *ctx, sph_particles *parts);                            // sph_pairs.cu
+int reduce_max_h(sph_ctx *ctx, const float *h, float *h_out_host);         // sph_integrate.cu
+int kick(sph_ctx *ctx, sph_particles *parts, double half_dt);              // sph_integrate.cu
+int drift(sph_ctx *ctx, sph_particles *parts, double dt);                  // sph_integrate.cu
+int device_max_h(sph_ctx *ctx, const float *h);                             // sph_integrate.cu
+int cfl_dt(sph_ctx *ctx, sph_particles *parts, double *dt_out);            // sph_integrate.cu
+int conserved(sph_ctx *ctx, sph_particles *parts, sph_conserved *out);     // sph_integrate.cu
+int exclusive_scan_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n);  // sph_cells.cu
+
+// FP32 pair math ---------------------------------------------------------------
+
+// Cubic spline of support 1 (Monaghan & Lattanzio 1985): w(q) and dw/dq, zero for q >= 1.
+__device__ __forceinline__ void spline(float q, float &w, float &dw)
+{
+    float t = fmaxf(1.f - q, 0.f);
+    float t2 = t * t;
+    float q2 = q * q;
+    bool inner = q <= 0.5f;
+    float w_in = fmaf(6.f * q2, q - 1.f, 1.f);  // 1 - 6q^2 + 6q^3
+    float dw_in = q * fmaf(18.f, q, -12.f);     // -12q + 18q^2
+    w = kSigma * (inner ? w_in : 2.f * t2 * t);
+    dw = kSigma * (inner ? dw_in : -6.f * t2);
+}
+
+__device__ __forceinline__ float spline_dw(float q)
+{
+    float t = fmaxf(1.f - q, 0.f);
+    float dw_in = q * fmaf(18.f, q, -12.f);
+    return kSigma * (q <= 0.5f ? dw_in : -6.f * t * t);
+}
+
+// Compensated (Kahan) accumulation; __fadd_rn/__fsub_rn keep the compiler from
+// contracting or reassociating the error term away.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
+{
+    float y = __fsub_rn(x, c);
+    float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+// splitmix64 finaliser (neighbour-set fingerprint term)
+__device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// FP64 re-decision of r_ij^2 < h^2 from absolute positions, minimal image, with the
+// operation order of the plain definition (no contraction).
+__device__ __forceinline__ double sep2_64(const double *__restrict__ x, const double *__restrict__ y,
+                                          const double *__restrict__ z, int i, int j, double box)
+{
+    double dx = __dsub_rn(x[i], x[j]);
+    dx = __dsub_rn(dx, __dmul_rn(box, rint(__ddiv_rn(dx, box))));
+    double dy = __dsub_rn(y[i], y[j]);
+    dy = __dsub_rn(dy, __dmul_rn(box, rint(__ddiv_rn(dy, box))));
+    double dz = __dsub_rn(z[i], z[j]);
+    dz = __dsub_rn(dz, __dmul_rn(box, rint(__ddiv_rn(dz, box))));
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+__device__ __forceinline__ bool within64(double r2, float h)
+{
+    double hh = (double)h;
+    return r2 < __dmul_rn(hh, hh);
+}
+
+}  // namespace sph
