@@ -391,7 +391,7 @@ int build_cells(sph_ctx *ctx, sph_particles *parts)
 {
     const int n = (int)ctx->n;
     const double box = ctx->p.box_size;
-    float hmax = (float)(box / 3.0);  // an empty set gets the coarsest grid
+    float hmax = (float)(box / 4.0);  // an empty set gets the coarsest grid
     int rc = SPH_OK;
     if (n > 0) rc = reduce_max_h(ctx, parts->h, &hmax);
     if (rc) return rc;
