@@ -68,6 +68,9 @@ typedef struct {
     int32_t use_balsara; /* 1: viscosity scaled by the Balsara switch                */
     int32_t kernel;      /* 0: cubic spline (the only kernel)                        */
     uint32_t flags;      /* SPH_FLAG_*                                               */
+    int32_t tile_width;  /* targets per warp work item: 16 (two cells per warp) or   */
+                         /* 32 (one cell per warp); 0 = default (16)                 */
+    int32_t reserved;    /* must be 0                                                */
 } sph_params;
 
 /*
@@ -126,7 +129,8 @@ typedef struct {
 } sph_stats;
 
 /* Fill *p with the defaults: gamma 5/3, n_ngb 48, h_tol 1e-4, alpha 0.8, cfl 0.1,
- * cell_factor 1.1, max_h_iter 30, use_balsara 1, kernel 0, flags 0, box 1. */
+ * cell_factor 1.1, max_h_iter 30, use_balsara 1, kernel 0, flags 0, box 1,
+ * tile_width 0 (default schedule). */
 int sph_default_params(sph_params *p);
 
 /* Create a context for up to p->n particles on CUDA device `device`, enqueuing on

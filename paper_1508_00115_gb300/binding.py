@@ -47,7 +47,8 @@ class sph_params(ctypes.Structure):
                 ("n_ngb", ctypes.c_float), ("h_tol", ctypes.c_float), ("alpha_visc", ctypes.c_float),
                 ("cfl", ctypes.c_float), ("cell_factor", ctypes.c_float),
                 ("max_h_iter", ctypes.c_int32), ("use_balsara", ctypes.c_int32),
-                ("kernel", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+                ("kernel", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("tile_width", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _PFIELDS = ["x", "y", "z", "vx", "vy", "vz", "m", "u", "h", "rho", "P", "c", "f", "divv", "curl",

@@ -77,7 +77,7 @@ static int alloc_particles(sph_ctx *c, int64_t cap)
     free_particles(c);
     cap = std::max<int64_t>(cap, 1);
     int64_t sort_tiles = (cap + 4095) / 4096;
-    c->tile_cap = cap + cap / kTile + 64;
+    c->tile_cap = cap + cap / kMinTile + 64;
     SPH_CUDA(c, cudaMalloc(&c->pos4, sizeof(float4) * cap));
     SPH_CUDA(c, cudaMalloc(&c->vel4, sizeof(float4) * cap));
     SPH_CUDA(c, cudaMalloc(&c->thermo4, sizeof(float4) * cap));
@@ -120,6 +120,7 @@ static int check_params(const sph_params *p, std::string &why)
     else if (!(p->cell_factor >= 1.f) || !isfinite(p->cell_factor)) why = "cell_factor must be >= 1";
     else if (p->max_h_iter < 1) why = "max_h_iter must be >= 1";
     else if (p->kernel != 0) why = "kernel must be 0 (cubic spline)";
+    else if (p->tile_width != 0 && p->tile_width != 16 && p->tile_width != 32) why = "tile_width must be 0, 16 or 32";
     else return SPH_OK;
     return SPH_ERR_INVALID_ARG;
 }
@@ -281,6 +282,7 @@ int sph_init(sph_ctx **out, const sph_params *p, int device, void *cuda_stream)
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
     c->n = p->n;
+    c->tile_w = p->tile_width == 32 ? 32 : 16;
     int rc = SPH_OK;
     auto bail = [&](int code) {
         sph_destroy(c);

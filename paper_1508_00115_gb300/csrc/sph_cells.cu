@@ -2,7 +2,7 @@
 // 2015, Sec. 3.1): periodic wrap, cell keys, a stable LSD radix sort of the
 // particles by cell, the in-place permutation of the caller's arrays into cell
 // order (particles of a cell contiguous in memory, Sec. 3.1), cell ranges and the
-// warp work items (tiles of up to 32 targets of one cell).
+// warp work items (tiles of up to 16 or 32 targets of one cell).
 #include <math.h>
 
 #include <algorithm>
@@ -346,15 +346,15 @@ __global__ void k_cell_start(const uint32_t *__restrict__ skeys, int n, int64_t 
     cs[c] = lo;
 }
 
-__global__ void k_cell_tiles(const int *__restrict__ cs, int64_t ncells, uint32_t *__restrict__ nt)
+__global__ void k_cell_tiles(const int *__restrict__ cs, int64_t ncells, int tw, uint32_t *__restrict__ nt)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
     int cnt = cs[c + 1] - cs[c];
-    nt[c] = (uint32_t)((cnt + kTile - 1) / kTile);
+    nt[c] = (uint32_t)((cnt + tw - 1) / tw);
 }
 
-__global__ void k_tiles_write(const int *__restrict__ cs, int64_t ncells, const uint32_t *__restrict__ toff,
+__global__ void k_tiles_write(const int *__restrict__ cs, int64_t ncells, int tw, const uint32_t *__restrict__ toff,
                               int4 *__restrict__ tiles, int *__restrict__ n_tiles)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -362,8 +362,8 @@ __global__ void k_tiles_write(const int *__restrict__ cs, int64_t ncells, const 
     int s = cs[c], cnt = cs[c + 1] - s;
     uint32_t off = toff[c];
     int k = 0;
-    for (int b = 0; b < cnt; b += kTile, ++k)
-        tiles[off + k] = make_int4((int)c, s + b, min(kTile, cnt - b), 0);
+    for (int b = 0; b < cnt; b += tw, ++k)
+        tiles[off + k] = make_int4((int)c, s + b, min(tw, cnt - b), 0);
     if (c == ncells - 1) *n_tiles = (int)(off + k);
 }
 
@@ -449,13 +449,13 @@ int build_cells(sph_ctx *ctx, sph_particles *parts)
                                                                          ctx->cell_start);
     SPH_LAUNCH(ctx, "cell start");
     k_cell_tiles<<<blocks_for(g.n_cells, 256), 256, 0, ctx->stream>>>(ctx->cell_start, g.n_cells,
-                                                                     ctx->cell_tiles);
+                                                                     ctx->tile_w, ctx->cell_tiles);
     SPH_LAUNCH(ctx, "cell tiles");
     rc = exclusive_scan_u32(ctx, ctx->cell_tiles, ctx->cell_tiles, g.n_cells);
     if (rc) return rc;
     k_tiles_write<<<blocks_for(g.n_cells, 256), 256, 0, ctx->stream>>>(ctx->cell_start, g.n_cells,
-                                                                      ctx->cell_tiles, ctx->tiles,
-                                                                      ctx->n_tiles);
+                                                                      ctx->tile_w, ctx->cell_tiles,
+                                                                      ctx->tiles, ctx->n_tiles);
     SPH_LAUNCH(ctx, "tiles");
     ctx->built = true;
     ctx->density_valid = false;

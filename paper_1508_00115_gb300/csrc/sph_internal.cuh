@@ -23,7 +23,7 @@ namespace sph {
 constexpr float kSigma = 2.54647908947032550f;  // 8/pi, 3-D cubic-spline normalisation
 constexpr float kFourPi3 = 4.18879020478639098f; // 4 pi / 3
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kTile = 32;             // targets per warp work item
+constexpr int kMinTile = 16;          // smallest tile (targets per warp work item)
 constexpr int kMaxNc = 512;           // cells per side cap
 constexpr int64_t kScanAuxCap = 65536; // block sums of one exclusive scan (4096 items/block)
 // FP32 distance tests within kBandK * h * (h + L) of the cutoff are re-decided in
@@ -84,6 +84,7 @@ struct sph_ctx {
     float *s32 = nullptr;   // 8 * cap
     // cells
     sph::Grid grid;
+    int tile_w = 16;             // targets per tile: 16 (two tiles per warp) or 32
     int *cell_start = nullptr;
     int64_t cell_cap = 0;
     int4 *tiles = nullptr;
@@ -210,6 +211,16 @@ __device__ __forceinline__ bool within64(double r2, float h)
 {
     double hh = (double)h;
     return r2 < __dmul_rn(hh, hh);
+}
+
+// FP64 decision for a pair whose FP32 distance test fell inside the
+// rounding band: bit 0 = (r_ij < h_a), bit 1 = (r_ij < h_b).  Rarely taken.
+__device__ __forceinline__ unsigned band_decide(const double *__restrict__ x, const double *__restrict__ y,
+                                             const double *__restrict__ z, int i, int j, double box, float ha,
+                                             float hb)
+{
+    const double r2 = sep2_64(x, y, z, i, j, box);
+    return (within64(r2, ha) ? 1u : 0u) | (within64(r2, hb) ? 2u : 0u);
 }
 
 }  // namespace sph

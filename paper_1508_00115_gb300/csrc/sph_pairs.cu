@@ -5,23 +5,33 @@
 //   force:   Eq. 2 in the Gadget-2 form with signal-velocity viscosity.
 //
 // Work decomposition (replaces the paper's self/pair tasks and task scheduler):
-// one warp owns a tile of up to 32 target particles of one cell (one lane per
-// target) and gathers from its own cell and the 26 adjacent cells (cells are no
-// smaller than any h, Sec. 3.1).  Sources of each adjacent cell are read 32 at a
-// time with one coalesced float4 load; a warp-parallel box test against the
-// tile's bounding box (grown by the largest cutoff) stands in for the paper's
-// sort-and-sweep pruning (Sec. 3.1, "sorting"): only sources that can reach some
-// target survive the ballot, and each survivor is broadcast to all lanes by
-// register shuffles.  Each target is written by exactly one lane, so the passes
-// need no locks or atomics on particle data (the paper resolves the same write
-// conflicts between tasks with locks).  Pair arithmetic is FP32 on cell-relative
-// positions with compensated sums; distance tests within a few ulps of the
-// cutoff are re-decided in FP64 so that neighbour sets are exact.
+// a tile is up to TW (16 or 32) target particles of one cell, one lane per
+// target; a warp holds 32/TW tiles.  Each tile gathers from its own cell and the
+// 26 adjacent cells (cells are no smaller than any h, Sec. 3.1), so every target
+// is written by exactly one lane: no locks or atomics on particle data (the paper
+// resolves the same write conflicts between tasks with locks).
+//
+// Per tile, sources arrive TW at a time by one coalesced float4 load and are
+// tested against the tile's bounding box grown by the cutoff -- the warp-parallel
+// stand-in for the paper's sort-and-sweep pruning (Sec. 3.1, "sorting").  The
+// survivors are compacted into a per-tile batch in shared memory.  A full batch
+// is processed in two phases:
+//   1. distance tests: every lane tests its target against each staged source
+//      (broadcast shared-memory reads) and records its hits in a 64-bit mask;
+//   2. interactions: every lane walks only its own hits.
+// so the interaction body never runs for a lane that does not need it.
+// Pair arithmetic is FP32 on cell-relative positions with compensated sums;
+// distance tests within a few ulps of the cutoff are re-decided in FP64 so that
+// neighbour sets are exact.
 #include <algorithm>
 
 #include "sph_internal.cuh"
 
 namespace sph {
+
+constexpr int kBatchD = 64;  // staged survivors per tile, density
+constexpr int kBatchF = 48;  // staged survivors per tile, force
+constexpr int kPairThreads = 256;
 
 struct DensityArgs {
     const float4 *__restrict__ pos4;
@@ -49,16 +59,19 @@ struct DensityArgs {
     int last_pass;
 };
 
-__device__ __forceinline__ float warp_min(float v)
+// reductions over the TW lanes of a tile (xor offsets < TW stay inside the tile)
+template <int TW>
+__device__ __forceinline__ float tile_min(float v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
+    for (int o = TW / 2; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(kFull, v, o));
     return v;
 }
-__device__ __forceinline__ float warp_max(float v)
+template <int TW>
+__device__ __forceinline__ float tile_max(float v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+    for (int o = TW / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
     return v;
 }
 __device__ __forceinline__ unsigned long long warp_sum_ull(unsigned long long v)
@@ -70,30 +83,48 @@ __device__ __forceinline__ unsigned long long warp_sum_ull(unsigned long long v)
 
 __device__ __forceinline__ int wrapc(int j, int nc) { return j < 0 ? j + nc : (j >= nc ? j - nc : j); }
 
-template <bool HASH>
-__global__ void __launch_bounds__(256) k_density(DensityArgs a)
+template <int TW, bool HASH>
+__global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
 {
-    const int lane = threadIdx.x & 31;
+    constexpr int TPW = 32 / TW;
+    constexpr int B = kBatchD;
+    constexpr int SLOT = B + 1;  // one float4 of padding: the tiles of a warp hit different banks
+    extern __shared__ float4 smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int sub = lane / TW, tl = lane % TW;
+    float4 *sA = smem + (size_t)wib * (2 * TPW * SLOT) + sub * SLOT;  // {x, y, z, j} in target frame
+    float4 *sB = sA + TPW * SLOT;                                      // {vx, vy, vz, m}
+    const unsigned gmask = TW == 32 ? kFull : (((1u << TW) - 1u) << (sub * TW));
+    const unsigned lt = (1u << lane) - 1u;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int ntiles = *a.n_tiles;
+    const int ngroups = (ntiles + TPW - 1) / TPW;
     const int nc = a.nc;
     const float L = a.L32;
-    for (int t = gw; t < ntiles; t += nw) {
-        const int4 tile = a.tiles[t];
-        const int ca = tile.x, i = tile.y + lane;
-        const bool valid = lane < tile.z;
+    const float inf = __int_as_float(0x7f800000);
+
+    for (int grp = gw; grp < ngroups; grp += nw) {
+        const int t = grp * TPW + sub;
+        const int4 tile = t < ntiles ? a.tiles[t] : make_int4(0, 0, 0, 0);
+        const int ca = tile.x, i = tile.y + tl;
+        const bool valid = tl < tile.z;
         const bool act = valid && a.active[i];
         const unsigned amask = __ballot_sync(kFull, act);
         if (!amask) continue;
-        float4 pi = valid ? a.pos4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float hi = act ? a.h[i] : 0.f;
-        const float4 vi = act ? a.vel4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float inf = __int_as_float(0x7f800000);
-        const float lox = warp_min(act ? pi.x : inf), hix = warp_max(act ? pi.x : -inf);
-        const float loy = warp_min(act ? pi.y : inf), hiy = warp_max(act ? pi.y : -inf);
-        const float loz = warp_min(act ? pi.z : inf), hiz = warp_max(act ? pi.z : -inf);
-        const float hmax = warp_max(hi);
+        const bool live = (amask & gmask) != 0;  // uniform within the tile
+
+        float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), vi = pi;
+        float hi = 0.f;
+        if (act) {
+            pi = a.pos4[i];
+            vi = a.vel4[i];
+            hi = a.h[i];
+        }
+        const float lox = tile_min<TW>(act ? pi.x : inf), hix = tile_max<TW>(act ? pi.x : -inf);
+        const float loy = tile_min<TW>(act ? pi.y : inf), hiy = tile_max<TW>(act ? pi.y : -inf);
+        const float loz = tile_min<TW>(act ? pi.z : inf), hiz = tile_max<TW>(act ? pi.z : -inf);
+        const float hmax = tile_max<TW>(hi);
         // grown so that pairs the FP64 band re-decision may accept are never pruned
         const float reach2 = hmax * hmax * (1.f + kPruneMargin) + 2.f * kBandK * hmax * (hmax + L);
         const float hi2 = hi * hi;
@@ -110,7 +141,57 @@ __global__ void __launch_bounds__(256) k_density(DensityArgs a)
         float dv = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
         int cnt = 0;
         uint64_t hh = 0;
-        unsigned long long cand = 0;
+        unsigned cand = 0;
+        int nst = 0;  // staged survivors of this tile (uniform within the tile)
+
+        auto flush = [&]() {
+            __syncwarp();
+            const int nmax = __reduce_max_sync(kFull, (unsigned)nst);
+            cand += (unsigned)nst;
+            // phase 1: distance tests, broadcast reads of the staged sources
+            uint64_t hm = 0;
+#pragma unroll 4
+            for (int k = 0; k < nmax; ++k) {
+                const float4 s = sA[k];
+                const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const int j = __float_as_int(s.w);
+                bool in = r2 < hi2;
+                const bool ok = act && k < nst && j != i;
+                if (ok && fabsf(r2 - hi2) <= band) in = band_decide(a.x, a.y, a.z, i, j, a.box, hi, hi) & 1u;
+                if (ok && in) hm |= 1ull << k;
+            }
+            // phase 2: each lane walks its own hits
+            while (__any_sync(kFull, hm != 0)) {
+                if (hm) {
+                    const int k = __ffsll((long long)hm) - 1;
+                    hm &= hm - 1;
+                    const float4 s = sA[k];
+                    const float4 vj = sB[k];
+                    const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                    const float q = r2 * rinv * hinv;
+                    float w, dw;
+                    spline(q, w, dw);
+                    const float mj = vj.w;
+                    kahan_add(rho_s, rho_c, mj * w);
+                    kahan_add(sw_s, sw_c, w);
+                    sqdw = fmaf(q, dw, sqdw);
+                    drho = fmaf(mj, fmaf(q, dw, 3.f * w), drho);
+                    const float fr = mj * dw * rinv;
+                    const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+                    dv = fmaf(fr, fmaf(vx, dx, fmaf(vy, dy, vz * dz)), dv);
+                    cx = fmaf(fr, fmaf(vy, dz, -vz * dy), cx);
+                    cy = fmaf(fr, fmaf(vz, dx, -vx * dz), cy);
+                    cz = fmaf(fr, fmaf(vx, dy, -vy * dx), cz);
+                    ++cnt;
+                    if (HASH) hh += mix64((uint64_t)a.ids[__float_as_int(s.w)]);
+                }
+            }
+            nst = 0;
+            __syncwarp();
+        };
 
         for (int oz = -1; oz <= 1; ++oz) {
             const int jz = wrapc(iz + oz, nc);
@@ -118,71 +199,49 @@ __global__ void __launch_bounds__(256) k_density(DensityArgs a)
                 const int jy = wrapc(iy + oy, nc);
                 for (int ox = -1; ox <= 1; ++ox) {
                     const int jx = wrapc(ix + ox, nc);
-                    const int cb = (jz * nc + jy) * nc + jx;
+                    int bs = 0, be = 0;
+                    if (live) {
+                        const int cb = (jz * nc + jy) * nc + jx;
+                        bs = a.cell_start[cb];
+                        be = a.cell_start[cb + 1];
+                    }
                     const float shx = (float)ox * L, shy = (float)oy * L, shz = (float)oz * L;
-                    const int bs = a.cell_start[cb], be = a.cell_start[cb + 1];
-                    for (int base = bs; base < be; base += 32) {
-                        const int j = base + lane;
-                        const bool has = j < be;
-                        float sx = 0.f, sy = 0.f, sz = 0.f;
+                    const int nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
+                    for (int ch = 0; ch < nchunk; ++ch) {
+                        const int j = bs + ch * TW + tl;
                         bool keep = false;
-                        if (has) {
-                            const float4 pj = __ldg(a.pos4 + j);
-                            sx = pj.x + shx;
-                            sy = pj.y + shy;
-                            sz = pj.z + shz;
-                            const float ex = fmaxf(fmaxf(lox - sx, sx - hix), 0.f);
-                            const float ey = fmaxf(fmaxf(loy - sy, sy - hiy), 0.f);
-                            const float ez = fmaxf(fmaxf(loz - sz, sz - hiz), 0.f);
-                            keep = ex * ex + ey * ey + ez * ez < reach2;
+                        float4 pj;
+                        if (j < be) {
+                            pj = __ldg(a.pos4 + j);
+                            pj.x += shx;
+                            pj.y += shy;
+                            pj.z += shz;
+                            const float ex = fmaxf(fmaxf(lox - pj.x, pj.x - hix), 0.f);
+                            const float ey = fmaxf(fmaxf(loy - pj.y, pj.y - hiy), 0.f);
+                            const float ez = fmaxf(fmaxf(loz - pj.z, pj.z - hiz), 0.f);
+                            keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < reach2;
                         }
-                        unsigned mask = __ballot_sync(kFull, keep);
-                        cand += (unsigned long long)__popc(mask);
-                        while (mask) {
-                            const int k = __ffs(mask) - 1;
-                            mask &= mask - 1;
-                            const float qx = __shfl_sync(kFull, sx, k);
-                            const float qy = __shfl_sync(kFull, sy, k);
-                            const float qz = __shfl_sync(kFull, sz, k);
-                            const int jj = base + k;
-                            if (act && jj != i) {
-                                const float dx = pi.x - qx, dy = pi.y - qy, dz = pi.z - qz;
-                                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                                bool in = r2 < hi2;
-                                if (fabsf(r2 - hi2) <= band)
-                                    in = within64(sep2_64(a.x, a.y, a.z, i, jj, a.box), hi);
-                                if (in) {
-                                    const float4 vj = __ldg(a.vel4 + jj);
-                                    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                                    const float q = r2 * rinv * hinv;
-                                    float w, dw;
-                                    spline(q, w, dw);
-                                    const float mj = vj.w;
-                                    kahan_add(rho_s, rho_c, mj * w);
-                                    kahan_add(sw_s, sw_c, w);
-                                    sqdw = fmaf(q, dw, sqdw);
-                                    drho = fmaf(mj, fmaf(q, dw, 3.f * w), drho);
-                                    const float fr = mj * dw * rinv;
-                                    const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
-                                    dv = fmaf(fr, fmaf(vx, dx, fmaf(vy, dy, vz * dz)), dv);
-                                    cx = fmaf(fr, fmaf(vy, dz, -vz * dy), cx);
-                                    cy = fmaf(fr, fmaf(vz, dx, -vx * dz), cy);
-                                    cz = fmaf(fr, fmaf(vx, dy, -vy * dx), cz);
-                                    ++cnt;
-                                    if (HASH) hh += mix64((uint64_t)a.ids[jj]);
-                                }
-                            }
+                        const unsigned mine = __ballot_sync(kFull, keep) & gmask;
+                        if (keep) {
+                            const int pos = nst + __popc(mine & lt);
+                            sA[pos] = make_float4(pj.x, pj.y, pj.z, __int_as_float(j));
+                            sB[pos] = __ldg(a.vel4 + j);
                         }
+                        nst += __popc(mine);
+                        if ((int)__reduce_max_sync(kFull, (unsigned)nst) > B - TW) flush();
                     }
                 }
             }
         }
+        if (__reduce_max_sync(kFull, (unsigned)nst) > 0) flush();
 
         // counters (one atomic per warp)
-        unsigned long long pairs = warp_sum_ull((unsigned long long)cnt);
+        const unsigned long long pairs = warp_sum_ull((unsigned long long)cnt);
+        const unsigned long long cands =
+            warp_sum_ull(tl == 0 ? (unsigned long long)cand * __popc(amask & gmask) : 0ull);
         if (lane == 0) {
             atomicAdd(a.counters + C_DPAIRS, pairs);
-            atomicAdd(a.counters + C_DCAND, cand * (unsigned long long)__popc(amask));
+            atomicAdd(a.counters + C_DCAND, cands);
             atomicAdd(a.counters + C_DTARGETS, (unsigned long long)__popc(amask));
         }
         if (!act) continue;
@@ -212,13 +271,13 @@ __global__ void __launch_bounds__(256) k_density(DensityArgs a)
         const float P = (gam - 1.f) * rho * u;
         const float cs = sqrtf(gam * (gam - 1.f) * u);
         const float fgh = 1.f / (1.f + hi / (3.f * rho) * drho_dh);
-        float B = 1.f;
+        float Bq = 1.f;
         if (a.use_balsara) {
             const float ad = fabsf(divv);
             const float den = ad + curl + 1e-4f * cs * hinv;
-            B = den > 0.f ? ad / den : 0.f;
+            Bq = den > 0.f ? ad / den : 0.f;
         }
-        a.thermo4[i] = make_float4(rho, fgh * P / (rho * rho), cs, B);
+        a.thermo4[i] = make_float4(rho, fgh * P / (rho * rho), cs, Bq);
         a.rho[i] = rho;
         a.P[i] = P;
         a.c[i] = cs;
@@ -249,123 +308,184 @@ struct ForceArgs {
     float alpha;
 };
 
-__global__ void __launch_bounds__(256) k_force(ForceArgs a)
+template <int TW>
+__global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
 {
-    const int lane = threadIdx.x & 31;
+    constexpr int TPW = 32 / TW;
+    constexpr int B = kBatchF;
+    constexpr int SLOT = B + 1;
+    extern __shared__ float4 smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int sub = lane / TW, tl = lane % TW;
+    float4 *sA = smem + (size_t)wib * (3 * TPW * SLOT) + sub * SLOT;  // {x, y, z, h_j} in target frame
+    float4 *sB = sA + TPW * SLOT;                                      // {vx, vy, vz, m}
+    float4 *sC = sB + TPW * SLOT;                                      // {rho, A, c, B}
+    int *sI = (int *)(smem + (size_t)(blockDim.x >> 5) * (3 * TPW * SLOT)) + (size_t)wib * TPW * SLOT +
+              sub * SLOT;
+    const unsigned gmask = TW == 32 ? kFull : (((1u << TW) - 1u) << (sub * TW));
+    const unsigned lt = (1u << lane) - 1u;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int ntiles = *a.n_tiles;
+    const int ngroups = (ntiles + TPW - 1) / TPW;
     const int nc = a.nc;
     const float L = a.L32;
     const float hglob = *a.hmax_global;
-    for (int t = gw; t < ntiles; t += nw) {
-        const int4 tile = a.tiles[t];
-        const int ca = tile.x, i = tile.y + lane;
-        const bool act = lane < tile.z;
+    const float inf = __int_as_float(0x7f800000);
+
+    for (int grp = gw; grp < ngroups; grp += nw) {
+        const int t = grp * TPW + sub;
+        const int4 tile = t < ntiles ? a.tiles[t] : make_int4(0, 0, 0, 0);
+        const int ca = tile.x, i = tile.y + tl;
+        const bool act = tl < tile.z;
         const unsigned amask = __ballot_sync(kFull, act);
-        const float4 pi = act ? a.pos4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 vi = act ? a.vel4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 ti = act ? a.thermo4[i] : make_float4(1.f, 0.f, 0.f, 0.f);
-        const float inf = __int_as_float(0x7f800000);
-        const float lox = warp_min(act ? pi.x : inf), hix = warp_max(act ? pi.x : -inf);
-        const float loy = warp_min(act ? pi.y : inf), hiy = warp_max(act ? pi.y : -inf);
-        const float loz = warp_min(act ? pi.z : inf), hiz = warp_max(act ? pi.z : -inf);
+        const bool live = (amask & gmask) != 0;
+        float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), vi = pi, ti = make_float4(1.f, 0.f, 0.f, 0.f);
+        if (act) {
+            pi = a.pos4[i];
+            vi = a.vel4[i];
+            ti = a.thermo4[i];
+        }
+        const float lox = tile_min<TW>(act ? pi.x : inf), hix = tile_max<TW>(act ? pi.x : -inf);
+        const float loy = tile_min<TW>(act ? pi.y : inf), hiy = tile_max<TW>(act ? pi.y : -inf);
+        const float loz = tile_min<TW>(act ? pi.z : inf), hiz = tile_max<TW>(act ? pi.z : -inf);
         const float hi = pi.w;
-        const float H = fmaxf(warp_max(hi), hglob);
+        const float H = fmaxf(tile_max<TW>(hi), hglob);
         const float reach2 = H * H * (1.f + kPruneMargin) + 2.f * kBandK * H * (H + L);
         const float hi2 = hi * hi;
         const float hinv = act ? 1.f / hi : 0.f;
         const float hinv4 = hinv * hinv * hinv * hinv;
         const float band_i = kBandK * hi * (hi + L);
         const int ix = ca % nc, iy = (ca / nc) % nc, iz = ca / (nc * nc);
-        const float rhoi = ti.x, Ai = ti.y, ci = ti.z, Bi = ti.w;
         float sx_ = 0.f, sxc = 0.f, sy_ = 0.f, syc = 0.f, sz_ = 0.f, szc = 0.f, su = 0.f, suc = 0.f;
         float vs = 0.f;
         int cnt = 0;
-        unsigned long long cand = 0;
+        unsigned cand = 0;
+        int nst = 0;
+
+        // exact neighbour decision for the pair (i, j): r < h_i and r < h_j
+        auto decide = [&](float r2, float hj, int j, bool &in_i, bool &in_j) {
+            const float hj2 = hj * hj;
+            in_i = r2 < hi2;
+            in_j = r2 < hj2;
+            const float band_j = kBandK * hj * (hj + L);
+            if (fabsf(r2 - hi2) <= band_i || fabsf(r2 - hj2) <= band_j) {
+                const unsigned d = band_decide(a.x, a.y, a.z, i, j, a.box, hi, hj);
+                in_i = d & 1u;
+                in_j = d & 2u;
+            }
+        };
+
+        auto flush = [&]() {
+            __syncwarp();
+            const int nmax = __reduce_max_sync(kFull, (unsigned)nst);
+            cand += (unsigned)nst;
+            uint64_t hm = 0;
+#pragma unroll 4
+            for (int k = 0; k < nmax; ++k) {
+                const float4 s = sA[k];
+                const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (act && k < nst) {
+                    const int j = sI[k];
+                    const float r2max = fmaxf(hi2, s.w * s.w);
+                    // cheap test first; the exact decision only near a cutoff
+                    if (j != i && r2 < r2max * (1.f + kPruneMargin) + 2.f * kBandK * H * (H + L)) {
+                        bool in_i, in_j;
+                        decide(r2, s.w, j, in_i, in_j);
+                        if (in_i || in_j) hm |= 1ull << k;
+                    }
+                }
+            }
+            while (__any_sync(kFull, hm != 0)) {
+                if (hm) {
+                    const int k = __ffsll((long long)hm) - 1;
+                    hm &= hm - 1;
+                    const float4 s = sA[k];
+                    const float4 vj = sB[k];
+                    const float4 tj = sC[k];
+                    const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    bool in_i, in_j;
+                    decide(r2, s.w, sI[k], in_i, in_j);
+                    ++cnt;
+                    if (r2 > 0.f) {
+                        const float rinv = rsqrtf(r2);
+                        const float r = r2 * rinv;
+                        const float hjinv = __fdividef(1.f, s.w);
+                        const float hj2inv = hjinv * hjinv;
+                        const float dWi = in_i ? spline_dw(r * hinv) * hinv4 : 0.f;
+                        const float dWj = in_j ? spline_dw(r * hjinv) * (hj2inv * hj2inv) : 0.f;
+                        const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+                        const float mu = fmaf(vx, dx, fmaf(vy, dy, vz * dz)) * rinv;
+                        float Pi = 0.f;
+                        if (mu < 0.f)
+                            Pi = -a.alpha * (ti.z + tj.z - 3.f * mu) * mu * (0.5f * (ti.w + tj.w)) / (ti.x + tj.x);
+                        const float dWbar = 0.5f * (dWi + dWj);
+                        const float mj = vj.w;
+                        const float sc = mj * fmaf(ti.y, dWi, fmaf(tj.y, dWj, Pi * dWbar)) * rinv;
+                        kahan_add(sx_, sxc, -sc * dx);
+                        kahan_add(sy_, syc, -sc * dy);
+                        kahan_add(sz_, szc, -sc * dz);
+                        kahan_add(su, suc, mj * mu * fmaf(ti.y, dWi, 0.5f * Pi * dWbar));
+                        vs = fmaxf(vs, ti.z + tj.z - 3.f * fminf(mu, 0.f));
+                    }
+                }
+            }
+            nst = 0;
+            __syncwarp();
+        };
+
         for (int oz = -1; oz <= 1; ++oz) {
             const int jz = wrapc(iz + oz, nc);
             for (int oy = -1; oy <= 1; ++oy) {
                 const int jy = wrapc(iy + oy, nc);
                 for (int ox = -1; ox <= 1; ++ox) {
                     const int jx = wrapc(ix + ox, nc);
-                    const int cb = (jz * nc + jy) * nc + jx;
+                    int bs = 0, be = 0;
+                    if (live) {
+                        const int cb = (jz * nc + jy) * nc + jx;
+                        bs = a.cell_start[cb];
+                        be = a.cell_start[cb + 1];
+                    }
                     const float shx = (float)ox * L, shy = (float)oy * L, shz = (float)oz * L;
-                    const int bs = a.cell_start[cb], be = a.cell_start[cb + 1];
-                    for (int base = bs; base < be; base += 32) {
-                        const int j = base + lane;
-                        const bool has = j < be;
-                        float sx = 0.f, sy = 0.f, sz = 0.f, sh = 0.f;
+                    const int nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
+                    for (int ch = 0; ch < nchunk; ++ch) {
+                        const int j = bs + ch * TW + tl;
                         bool keep = false;
-                        if (has) {
-                            const float4 pj = __ldg(a.pos4 + j);
-                            sx = pj.x + shx;
-                            sy = pj.y + shy;
-                            sz = pj.z + shz;
-                            sh = pj.w;
-                            const float ex = fmaxf(fmaxf(lox - sx, sx - hix), 0.f);
-                            const float ey = fmaxf(fmaxf(loy - sy, sy - hiy), 0.f);
-                            const float ez = fmaxf(fmaxf(loz - sz, sz - hiz), 0.f);
-                            keep = ex * ex + ey * ey + ez * ez < reach2;
+                        float4 pj;
+                        if (j < be) {
+                            pj = __ldg(a.pos4 + j);
+                            pj.x += shx;
+                            pj.y += shy;
+                            pj.z += shz;
+                            const float ex = fmaxf(fmaxf(lox - pj.x, pj.x - hix), 0.f);
+                            const float ey = fmaxf(fmaxf(loy - pj.y, pj.y - hiy), 0.f);
+                            const float ez = fmaxf(fmaxf(loz - pj.z, pj.z - hiz), 0.f);
+                            keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < reach2;
                         }
-                        unsigned mask = __ballot_sync(kFull, keep);
-                        cand += (unsigned long long)__popc(mask);
-                        while (mask) {
-                            const int k = __ffs(mask) - 1;
-                            mask &= mask - 1;
-                            const float qx = __shfl_sync(kFull, sx, k);
-                            const float qy = __shfl_sync(kFull, sy, k);
-                            const float qz = __shfl_sync(kFull, sz, k);
-                            const float hj = __shfl_sync(kFull, sh, k);
-                            const int jj = base + k;
-                            if (act && jj != i) {
-                                const float dx = pi.x - qx, dy = pi.y - qy, dz = pi.z - qz;
-                                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                                const float hj2 = hj * hj;
-                                bool in_i = r2 < hi2, in_j = r2 < hj2;
-                                const float band_j = kBandK * hj * (hj + L);
-                                if (fabsf(r2 - hi2) <= band_i || fabsf(r2 - hj2) <= band_j) {
-                                    const double r64 = sep2_64(a.x, a.y, a.z, i, jj, a.box);
-                                    in_i = within64(r64, hi);
-                                    in_j = within64(r64, hj);
-                                }
-                                if ((in_i || in_j) && r2 > 0.f) {
-                                    const float4 vj = __ldg(a.vel4 + jj);
-                                    const float4 tj = __ldg(a.thermo4 + jj);
-                                    const float rinv = rsqrtf(r2);
-                                    const float r = r2 * rinv;
-                                    const float hjinv = __fdividef(1.f, hj);
-                                    const float hj2inv = hjinv * hjinv;
-                                    const float dWi = in_i ? spline_dw(r * hinv) * hinv4 : 0.f;
-                                    const float dWj = in_j ? spline_dw(r * hjinv) * (hj2inv * hj2inv) : 0.f;
-                                    const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
-                                    const float mu = fmaf(vx, dx, fmaf(vy, dy, vz * dz)) * rinv;
-                                    float Pi = 0.f;
-                                    if (mu < 0.f)
-                                        Pi = -a.alpha * (ci + tj.z - 3.f * mu) * mu * (0.5f * (Bi + tj.w)) /
-                                             (rhoi + tj.x);
-                                    const float dWbar = 0.5f * (dWi + dWj);
-                                    const float mj = vj.w;
-                                    const float s = mj * fmaf(Ai, dWi, fmaf(tj.y, dWj, Pi * dWbar)) * rinv;
-                                    kahan_add(sx_, sxc, -s * dx);
-                                    kahan_add(sy_, syc, -s * dy);
-                                    kahan_add(sz_, szc, -s * dz);
-                                    kahan_add(su, suc, mj * mu * fmaf(Ai, dWi, 0.5f * Pi * dWbar));
-                                    vs = fmaxf(vs, ci + tj.z - 3.f * fminf(mu, 0.f));
-                                    ++cnt;
-                                } else if (in_i || in_j) {
-                                    ++cnt;  // coincident pair: counted, no direction (w'(0) = 0)
-                                }
-                            }
+                        const unsigned mine = __ballot_sync(kFull, keep) & gmask;
+                        if (keep) {
+                            const int pos = nst + __popc(mine & lt);
+                            sA[pos] = pj;
+                            sB[pos] = __ldg(a.vel4 + j);
+                            sC[pos] = __ldg(a.thermo4 + j);
+                            sI[pos] = j;
                         }
+                        nst += __popc(mine);
+                        if ((int)__reduce_max_sync(kFull, (unsigned)nst) > B - TW) flush();
                     }
                 }
             }
         }
-        unsigned long long pairs = warp_sum_ull((unsigned long long)cnt);
+        if (__reduce_max_sync(kFull, (unsigned)nst) > 0) flush();
+
+        const unsigned long long pairs = warp_sum_ull((unsigned long long)cnt);
+        const unsigned long long cands =
+            warp_sum_ull(tl == 0 ? (unsigned long long)cand * __popc(amask & gmask) : 0ull);
         if (lane == 0) {
             atomicAdd(a.counters + C_FPAIRS, pairs);
-            atomicAdd(a.counters + C_FCAND, cand * (unsigned long long)__popc(amask));
+            atomicAdd(a.counters + C_FCAND, cands);
         }
         if (!act) continue;
         a.ax[i] = sx_ - sxc;
@@ -382,14 +502,26 @@ __global__ void k_sync_h(const float *__restrict__ h, float4 *__restrict__ pos4,
     if (i < n) pos4[i].w = h[i];
 }
 
-static int pair_grid(sph_ctx *ctx)
+template <int TW>
+static size_t density_smem()
+{
+    return (size_t)(kPairThreads / 32) * 2 * (32 / TW) * (kBatchD + 1) * sizeof(float4);
+}
+template <int TW>
+static size_t force_smem()
+{
+    const size_t slots = (size_t)(kPairThreads / 32) * (32 / TW) * (kBatchF + 1);
+    return slots * (3 * sizeof(float4) + sizeof(int));
+}
+
+static int pair_grid(sph_ctx *ctx, int blocks_per_sm)
 {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (sms <= 0) sms = 148;
-    // persistent grid: 8 blocks of 8 warps per SM, warps stride over the tiles
-    int64_t want = ((int64_t)ctx->n / kTile + ctx->grid.n_cells) / 8 + 1;
-    int64_t g = std::min<int64_t>((int64_t)sms * 8, want);
+    // persistent grid: warps stride over the tile groups
+    int64_t want = ((int64_t)ctx->n / ctx->tile_w + ctx->grid.n_cells) / (kPairThreads / 32) + 1;
+    int64_t g = std::min<int64_t>((int64_t)sms * blocks_per_sm, want);
     return (int)std::max<int64_t>(g, 1);
 }
 
@@ -428,13 +560,19 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass)
     a.h_cell_limit = (float)(ctx->grid.L64 * (1.0 - 1e-6));
     a.use_balsara = ctx->p.use_balsara;
     a.last_pass = last_pass ? 1 : 0;
-    int g = pair_grid(ctx);
+    const int g = pair_grid(ctx, 3);
+    const bool hash = (ctx->p.flags & SPH_FLAG_NGB_HASH) != 0;
     cudaEvent_t end = nullptr;
     timer_begin(ctx, 0, &end);
-    if (ctx->p.flags & SPH_FLAG_NGB_HASH)
-        k_density<true><<<g, 256, 0, ctx->stream>>>(a);
-    else
-        k_density<false><<<g, 256, 0, ctx->stream>>>(a);
+    if (ctx->tile_w == 32) {
+        const size_t sm = density_smem<32>();
+        if (hash) k_density<32, true><<<g, kPairThreads, sm, ctx->stream>>>(a);
+        else k_density<32, false><<<g, kPairThreads, sm, ctx->stream>>>(a);
+    } else {
+        const size_t sm = density_smem<16>();
+        if (hash) k_density<16, true><<<g, kPairThreads, sm, ctx->stream>>>(a);
+        else k_density<16, false><<<g, kPairThreads, sm, ctx->stream>>>(a);
+    }
     timer_end(ctx, end);
     SPH_LAUNCH(ctx, "density kernel");
     ctx->st.density_passes++;
@@ -464,10 +602,11 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts)
     a.L32 = ctx->grid.L32;
     a.box = ctx->p.box_size;
     a.alpha = ctx->p.alpha_visc;
-    int g = pair_grid(ctx);
+    const int g = pair_grid(ctx, 2);
     cudaEvent_t end = nullptr;
     timer_begin(ctx, 1, &end);
-    k_force<<<g, 256, 0, ctx->stream>>>(a);
+    if (ctx->tile_w == 32) k_force<32><<<g, kPairThreads, force_smem<32>(), ctx->stream>>>(a);
+    else k_force<16><<<g, kPairThreads, force_smem<16>(), ctx->stream>>>(a);
     timer_end(ctx, end);
     SPH_LAUNCH(ctx, "force kernel");
     ctx->st.force_passes++;

@@ -62,7 +62,8 @@ def test_default_params(L):
 
 def test_init_rejects_bad_params_without_touching_the_device(L):
     for k, v in (("n", -1), ("box_size", 0.0), ("gamma", 1.0), ("n_ngb", 5.0), ("h_tol", 0.0),
-                 ("cell_factor", 0.5), ("max_h_iter", 0), ("kernel", 3), ("cfl", 0.0)):
+                 ("cell_factor", 0.5), ("max_h_iter", 0), ("kernel", 3), ("cfl", 0.0),
+                 ("tile_width", 24)):
         p = binding.sph_default_params()
         setattr(p, k, v)
         h = ctypes.c_void_p(123)
