@@ -29,9 +29,19 @@
 
 namespace sph {
 
-constexpr int kBatchD = 64;  // staged survivors per tile, density
-constexpr int kBatchF = 48;  // staged survivors per tile, force
+constexpr int kBatchD = 128;  // staged survivors per tile, density (4 hit-mask words)
+constexpr int kBatchF = 128;  // staged survivors per tile, force
 constexpr int kPairThreads = 256;
+constexpr float kFar = 1e30f;  // padding source position: its squared distance overflows to +inf
+
+// Neighbour cells in visiting order: the own cell, then each of the 13 directions
+// of a half stencil followed by its opposite, so that every staged batch mixes
+// cells on both sides of the tile and the lanes' hit counts stay balanced.
+__constant__ signed char kOrder[27][3] = {
+    {0, 0, 0},   {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},   {0, 0, 1},  {0, 0, -1},
+    {1, 1, 0},   {-1, -1, 0}, {1, -1, 0},  {-1, 1, 0},  {1, 0, 1},    {-1, 0, -1}, {1, 0, -1},
+    {-1, 0, 1},  {0, 1, 1},   {0, -1, -1}, {0, 1, -1},  {0, -1, 1},   {1, 1, 1},  {-1, -1, -1},
+    {1, 1, -1},  {-1, -1, 1}, {1, -1, 1},  {-1, 1, -1}, {-1, 1, 1},   {1, -1, -1}};
 
 struct DensityArgs {
     const float4 *__restrict__ pos4;
@@ -83,6 +93,36 @@ __device__ __forceinline__ unsigned long long warp_sum_ull(unsigned long long v)
 
 __device__ __forceinline__ int wrapc(int j, int nc) { return j < 0 ? j + nc : (j >= nc ? j - nc : j); }
 
+// Pop the lowest set bit of a 128-bit mask held in four words; returns its index.
+__device__ __forceinline__ int pop_bit(unsigned &m0, unsigned &m1, unsigned &m2, unsigned &m3)
+{
+    const bool a = m0 != 0, b = m1 != 0, c = m2 != 0;
+    const unsigned m = a ? m0 : (b ? m1 : (c ? m2 : m3));
+    const int base = a ? 0 : (b ? 32 : (c ? 64 : 96));
+    const unsigned r = m & (m - 1u);
+    if (a) m0 = r;
+    else if (b) m1 = r;
+    else if (c) m2 = r;
+    else m3 = r;
+    return base + __ffs(m) - 1;
+}
+
+// Cubic spline of support 1 without its normalisation sigma, in truncated-power form:
+// w/sigma = 2(1-q)^3_+ - 8(1/2-q)^3_+,  (dw/dq)/sigma = -6(1-q)^2_+ + 24(1/2-q)^2_+
+// (identical to the piecewise polynomial; branch-free).
+__device__ __forceinline__ void spline_u(float q, float &w, float &dw)
+{
+    const float a = fmaxf(1.f - q, 0.f), b = fmaxf(0.5f - q, 0.f);
+    const float a2 = a * a, b2 = b * b;
+    w = fmaf(-8.f * b2, b, 2.f * a2 * a);
+    dw = fmaf(24.f, b2, -6.f * a2);
+}
+__device__ __forceinline__ float spline_dw_u(float q)
+{
+    const float a = fmaxf(1.f - q, 0.f), b = fmaxf(0.5f - q, 0.f);
+    return fmaf(24.f * b, b, -6.f * a * a);
+}
+
 template <int TW, bool HASH>
 __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
 {
@@ -127,17 +167,20 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
         const float hmax = tile_max<TW>(hi);
         // grown so that pairs the FP64 band re-decision may accept are never pruned
         const float reach2 = hmax * hmax * (1.f + kPruneMargin) + 2.f * kBandK * hmax * (hmax + L);
-        const float hi2 = hi * hi;
+        // r^2 below lob: neighbour; above hib: not; in between: decided in FP64.
+        // Lanes without an active target get thresholds no distance can pass.
         const float band = kBandK * hi * (hi + L);
+        const float hi2 = act ? hi * hi : -1.f;
+        const float lob = hi2 - band, hib = hi2 + band;
         const float hinv = act ? 1.f / hi : 0.f;
         const int ix = ca % nc, iy = (ca / nc) % nc, iz = ca / (nc * nc);
 
-        // sums; the self term (q = 0: w = sigma, w' = 0) starts them
-        const float mi = vi.w;
-        float rho_s = mi * kSigma, rho_c = 0.f;  // sum m_j w_j
-        float sw_s = kSigma, sw_c = 0.f;          // sum w_j
-        float sqdw = 0.f;                         // sum q_j w'_j
-        float drho = 3.f * mi * kSigma;           // sum m_j (3 w_j + q_j w'_j)
+        // sums without the kernel normalisation (applied at the end); the pair
+        // (i, i) is met in the own cell and supplies the self term of Eq. 1
+        float rho_s = 0.f, rho_c = 0.f;  // sum m_j w_j
+        float sw_s = 0.f, sw_c = 0.f;    // sum w_j
+        float sqdw = 0.f;                // sum q_j w'_j
+        float drho = 0.f;                // sum m_j (3 w_j + q_j w'_j)
         float dv = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
         int cnt = 0;
         uint64_t hh = 0;
@@ -145,27 +188,31 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
         int nst = 0;  // staged survivors of this tile (uniform within the tile)
 
         auto flush = [&]() {
-            __syncwarp();
             const int nmax = __reduce_max_sync(kFull, (unsigned)nst);
+            for (int k = nst + tl; k < nmax; k += TW) sA[k] = make_float4(kFar, kFar, kFar, 0.f);
+            __syncwarp();
             cand += (unsigned)nst;
             // phase 1: distance tests, broadcast reads of the staged sources
-            uint64_t hm = 0;
+            unsigned m[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int wd = 0; wd < 4; ++wd) {
+                const int kend = min(32, nmax - 32 * wd);
 #pragma unroll 4
-            for (int k = 0; k < nmax; ++k) {
-                const float4 s = sA[k];
-                const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const int j = __float_as_int(s.w);
-                bool in = r2 < hi2;
-                const bool ok = act && k < nst && j != i;
-                if (ok && fabsf(r2 - hi2) <= band) in = band_decide(a.x, a.y, a.z, i, j, a.box, hi, hi) & 1u;
-                if (ok && in) hm |= 1ull << k;
+                for (int kk = 0; kk < kend; ++kk) {
+                    const float4 s = sA[32 * wd + kk];
+                    const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    bool in = r2 < lob;
+                    if (!in && r2 < hib)
+                        in = band_decide(a.x, a.y, a.z, i, __float_as_int(s.w), a.box, hi, hi) & 1u;
+                    m[wd] |= (unsigned)in << kk;
+                }
             }
             // phase 2: each lane walks its own hits
-            while (__any_sync(kFull, hm != 0)) {
-                if (hm) {
-                    const int k = __ffsll((long long)hm) - 1;
-                    hm &= hm - 1;
+            unsigned m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
+            while (__any_sync(kFull, (m0 | m1 | m2 | m3) != 0u)) {
+                if (m0 | m1 | m2 | m3) {
+                    const int k = pop_bit(m0, m1, m2, m3);
                     const float4 s = sA[k];
                     const float4 vj = sB[k];
                     const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
@@ -173,7 +220,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
                     const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
                     const float q = r2 * rinv * hinv;
                     float w, dw;
-                    spline(q, w, dw);
+                    spline_u(q, w, dw);
                     const float mj = vj.w;
                     kahan_add(rho_s, rho_c, mj * w);
                     kahan_add(sw_s, sw_c, w);
@@ -193,50 +240,45 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
             __syncwarp();
         };
 
-        for (int oz = -1; oz <= 1; ++oz) {
-            const int jz = wrapc(iz + oz, nc);
-            for (int oy = -1; oy <= 1; ++oy) {
-                const int jy = wrapc(iy + oy, nc);
-                for (int ox = -1; ox <= 1; ++ox) {
-                    const int jx = wrapc(ix + ox, nc);
-                    int bs = 0, be = 0;
-                    if (live) {
-                        const int cb = (jz * nc + jy) * nc + jx;
-                        bs = a.cell_start[cb];
-                        be = a.cell_start[cb + 1];
-                    }
-                    const float shx = (float)ox * L, shy = (float)oy * L, shz = (float)oz * L;
-                    const int nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
-                    for (int ch = 0; ch < nchunk; ++ch) {
-                        const int j = bs + ch * TW + tl;
-                        bool keep = false;
-                        float4 pj;
-                        if (j < be) {
-                            pj = __ldg(a.pos4 + j);
-                            pj.x += shx;
-                            pj.y += shy;
-                            pj.z += shz;
-                            const float ex = fmaxf(fmaxf(lox - pj.x, pj.x - hix), 0.f);
-                            const float ey = fmaxf(fmaxf(loy - pj.y, pj.y - hiy), 0.f);
-                            const float ez = fmaxf(fmaxf(loz - pj.z, pj.z - hiz), 0.f);
-                            keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < reach2;
-                        }
-                        const unsigned mine = __ballot_sync(kFull, keep) & gmask;
-                        if (keep) {
-                            const int pos = nst + __popc(mine & lt);
-                            sA[pos] = make_float4(pj.x, pj.y, pj.z, __int_as_float(j));
-                            sB[pos] = __ldg(a.vel4 + j);
-                        }
-                        nst += __popc(mine);
-                        if ((int)__reduce_max_sync(kFull, (unsigned)nst) > B - TW) flush();
-                    }
+        for (int o = 0; o < 27; ++o) {
+            const int ox = kOrder[o][0], oy = kOrder[o][1], oz = kOrder[o][2];
+            int bs = 0, be = 0;
+            if (live) {
+                const int cb = (wrapc(iz + oz, nc) * nc + wrapc(iy + oy, nc)) * nc + wrapc(ix + ox, nc);
+                bs = a.cell_start[cb];
+                be = a.cell_start[cb + 1];
+            }
+            const float shx = (float)ox * L, shy = (float)oy * L, shz = (float)oz * L;
+            const int nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
+            for (int ch = 0; ch < nchunk; ++ch) {
+                const int j = bs + ch * TW + tl;
+                bool keep = false;
+                float4 pj;
+                if (j < be) {
+                    pj = __ldg(a.pos4 + j);
+                    pj.x += shx;
+                    pj.y += shy;
+                    pj.z += shz;
+                    const float ex = fmaxf(fmaxf(lox - pj.x, pj.x - hix), 0.f);
+                    const float ey = fmaxf(fmaxf(loy - pj.y, pj.y - hiy), 0.f);
+                    const float ez = fmaxf(fmaxf(loz - pj.z, pj.z - hiz), 0.f);
+                    keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < reach2;
                 }
+                const unsigned mine = __ballot_sync(kFull, keep) & gmask;
+                if (keep) {
+                    const int pos = nst + __popc(mine & lt);
+                    sA[pos] = make_float4(pj.x, pj.y, pj.z, __int_as_float(j));
+                    sB[pos] = __ldg(a.vel4 + j);
+                }
+                nst += __popc(mine);
+                if ((int)__reduce_max_sync(kFull, (unsigned)nst) > B - TW) flush();
             }
         }
         if (__reduce_max_sync(kFull, (unsigned)nst) > 0) flush();
 
         // counters (one atomic per warp)
-        const unsigned long long pairs = warp_sum_ull((unsigned long long)cnt);
+        const int nself = act ? 1 : 0;  // the (i, i) pair is not a neighbour
+        const unsigned long long pairs = warp_sum_ull((unsigned long long)(cnt - nself));
         const unsigned long long cands =
             warp_sum_ull(tl == 0 ? (unsigned long long)cand * __popc(amask & gmask) : 0ull);
         if (lane == 0) {
@@ -247,12 +289,12 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
         if (!act) continue;
 
         const float hinv3 = hinv * hinv * hinv, hinv4 = hinv3 * hinv;
-        const float rho = hinv3 * (rho_s - rho_c);
-        const float nw_ = kFourPi3 * (sw_s - sw_c);
-        const float dnw_dh = -kFourPi3 * sqdw * hinv;
-        const float drho_dh = -hinv4 * drho;
-        const float divv = -hinv4 * dv / rho;
-        const float curl = hinv4 * sqrtf(cx * cx + cy * cy + cz * cz) / rho;
+        const float rho = kSigma * hinv3 * (rho_s - rho_c);
+        const float nw_ = kSigma * kFourPi3 * (sw_s - sw_c);
+        const float dnw_dh = -kSigma * kFourPi3 * sqdw * hinv;
+        const float drho_dh = -kSigma * hinv4 * drho;
+        const float divv = -kSigma * hinv4 * dv / rho;
+        const float curl = kSigma * hinv4 * sqrtf(cx * cx + cy * cy + cz * cz) / rho;
         const float g = nw_ - a.n_ngb_target;
         const bool conv = fabsf(g) <= a.h_tol * a.n_ngb_target;
         if (!conv && !a.last_pass) {
@@ -284,8 +326,8 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
         a.f[i] = fgh;
         a.divv[i] = divv;
         a.curl[i] = curl;
-        a.n_ngb[i] = cnt;
-        if (HASH) a.ngb_hash[i] = hh;
+        a.n_ngb[i] = cnt - 1;
+        if (HASH) a.ngb_hash[i] = hh - mix64((uint64_t)a.ids[i]);
     }
 }
 
@@ -340,7 +382,9 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
         const bool act = tl < tile.z;
         const unsigned amask = __ballot_sync(kFull, act);
         const bool live = (amask & gmask) != 0;
-        float4 pi = make_float4(0.f, 0.f, 0.f, 0.f), vi = pi, ti = make_float4(1.f, 0.f, 0.f, 0.f);
+        // lanes without a target sit far away so that no distance test passes
+        float4 pi = make_float4(kFar, kFar, kFar, 0.f), vi = make_float4(0.f, 0.f, 0.f, 0.f),
+               ti = make_float4(1.f, 0.f, 0.f, 0.f);
         if (act) {
             pi = a.pos4[i];
             vi = a.vel4[i];
@@ -351,7 +395,8 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
         const float loz = tile_min<TW>(act ? pi.z : inf), hiz = tile_max<TW>(act ? pi.z : -inf);
         const float hi = pi.w;
         const float H = fmaxf(tile_max<TW>(hi), hglob);
-        const float reach2 = H * H * (1.f + kPruneMargin) + 2.f * kBandK * H * (H + L);
+        const float bandmax = 2.f * kBandK * H * (H + L);
+        const float reach2 = H * H * (1.f + kPruneMargin) + bandmax;
         const float hi2 = hi * hi;
         const float hinv = act ? 1.f / hi : 0.f;
         const float hinv4 = hinv * hinv * hinv * hinv;
@@ -377,45 +422,48 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
         };
 
         auto flush = [&]() {
-            __syncwarp();
             const int nmax = __reduce_max_sync(kFull, (unsigned)nst);
+            for (int k = nst + tl; k < nmax; k += TW) sA[k] = make_float4(kFar, kFar, kFar, 0.f);
+            __syncwarp();
             cand += (unsigned)nst;
-            uint64_t hm = 0;
+            unsigned m[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int wd = 0; wd < 4; ++wd) {
+                const int kend = min(32, nmax - 32 * wd);
 #pragma unroll 4
-            for (int k = 0; k < nmax; ++k) {
-                const float4 s = sA[k];
-                const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
-                const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (act && k < nst) {
-                    const int j = sI[k];
-                    const float r2max = fmaxf(hi2, s.w * s.w);
-                    // cheap test first; the exact decision only near a cutoff
-                    if (j != i && r2 < r2max * (1.f + kPruneMargin) + 2.f * kBandK * H * (H + L)) {
+                for (int kk = 0; kk < kend; ++kk) {
+                    const float4 s = sA[32 * wd + kk];
+                    const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float m2 = fmaxf(hi2, s.w * s.w);
+                    bool in = r2 < m2 - bandmax;
+                    if (!in && r2 < m2 + bandmax) {
                         bool in_i, in_j;
-                        decide(r2, s.w, j, in_i, in_j);
-                        if (in_i || in_j) hm |= 1ull << k;
+                        decide(r2, s.w, sI[32 * wd + kk], in_i, in_j);
+                        in = in_i || in_j;
                     }
+                    m[wd] |= (unsigned)in << kk;
                 }
             }
-            while (__any_sync(kFull, hm != 0)) {
-                if (hm) {
-                    const int k = __ffsll((long long)hm) - 1;
-                    hm &= hm - 1;
+            unsigned m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
+            while (__any_sync(kFull, (m0 | m1 | m2 | m3) != 0u)) {
+                if (m0 | m1 | m2 | m3) {
+                    const int k = pop_bit(m0, m1, m2, m3);
                     const float4 s = sA[k];
                     const float4 vj = sB[k];
                     const float4 tj = sC[k];
                     const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    bool in_i, in_j;
-                    decide(r2, s.w, sI[k], in_i, in_j);
                     ++cnt;
-                    if (r2 > 0.f) {
+                    if (r2 > 0.f) {  // the pair (i, i), and coincident pairs, have no direction
+                        bool in_i, in_j;
+                        decide(r2, s.w, sI[k], in_i, in_j);
                         const float rinv = rsqrtf(r2);
                         const float r = r2 * rinv;
                         const float hjinv = __fdividef(1.f, s.w);
                         const float hj2inv = hjinv * hjinv;
-                        const float dWi = in_i ? spline_dw(r * hinv) * hinv4 : 0.f;
-                        const float dWj = in_j ? spline_dw(r * hjinv) * (hj2inv * hj2inv) : 0.f;
+                        const float dWi = in_i ? kSigma * spline_dw_u(r * hinv) * hinv4 : 0.f;
+                        const float dWj = in_j ? kSigma * spline_dw_u(r * hjinv) * (hj2inv * hj2inv) : 0.f;
                         const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
                         const float mu = fmaf(vx, dx, fmaf(vy, dy, vz * dz)) * rinv;
                         float Pi = 0.f;
@@ -436,51 +484,46 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
             __syncwarp();
         };
 
-        for (int oz = -1; oz <= 1; ++oz) {
-            const int jz = wrapc(iz + oz, nc);
-            for (int oy = -1; oy <= 1; ++oy) {
-                const int jy = wrapc(iy + oy, nc);
-                for (int ox = -1; ox <= 1; ++ox) {
-                    const int jx = wrapc(ix + ox, nc);
-                    int bs = 0, be = 0;
-                    if (live) {
-                        const int cb = (jz * nc + jy) * nc + jx;
-                        bs = a.cell_start[cb];
-                        be = a.cell_start[cb + 1];
-                    }
-                    const float shx = (float)ox * L, shy = (float)oy * L, shz = (float)oz * L;
-                    const int nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
-                    for (int ch = 0; ch < nchunk; ++ch) {
-                        const int j = bs + ch * TW + tl;
-                        bool keep = false;
-                        float4 pj;
-                        if (j < be) {
-                            pj = __ldg(a.pos4 + j);
-                            pj.x += shx;
-                            pj.y += shy;
-                            pj.z += shz;
-                            const float ex = fmaxf(fmaxf(lox - pj.x, pj.x - hix), 0.f);
-                            const float ey = fmaxf(fmaxf(loy - pj.y, pj.y - hiy), 0.f);
-                            const float ez = fmaxf(fmaxf(loz - pj.z, pj.z - hiz), 0.f);
-                            keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < reach2;
-                        }
-                        const unsigned mine = __ballot_sync(kFull, keep) & gmask;
-                        if (keep) {
-                            const int pos = nst + __popc(mine & lt);
-                            sA[pos] = pj;
-                            sB[pos] = __ldg(a.vel4 + j);
-                            sC[pos] = __ldg(a.thermo4 + j);
-                            sI[pos] = j;
-                        }
-                        nst += __popc(mine);
-                        if ((int)__reduce_max_sync(kFull, (unsigned)nst) > B - TW) flush();
-                    }
+        for (int o = 0; o < 27; ++o) {
+            const int ox = kOrder[o][0], oy = kOrder[o][1], oz = kOrder[o][2];
+            int bs = 0, be = 0;
+            if (live) {
+                const int cb = (wrapc(iz + oz, nc) * nc + wrapc(iy + oy, nc)) * nc + wrapc(ix + ox, nc);
+                bs = a.cell_start[cb];
+                be = a.cell_start[cb + 1];
+            }
+            const float shx = (float)ox * L, shy = (float)oy * L, shz = (float)oz * L;
+            const int nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
+            for (int ch = 0; ch < nchunk; ++ch) {
+                const int j = bs + ch * TW + tl;
+                bool keep = false;
+                float4 pj;
+                if (j < be) {
+                    pj = __ldg(a.pos4 + j);
+                    pj.x += shx;
+                    pj.y += shy;
+                    pj.z += shz;
+                    const float ex = fmaxf(fmaxf(lox - pj.x, pj.x - hix), 0.f);
+                    const float ey = fmaxf(fmaxf(loy - pj.y, pj.y - hiy), 0.f);
+                    const float ez = fmaxf(fmaxf(loz - pj.z, pj.z - hiz), 0.f);
+                    keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < reach2;
                 }
+                const unsigned mine = __ballot_sync(kFull, keep) & gmask;
+                if (keep) {
+                    const int pos = nst + __popc(mine & lt);
+                    sA[pos] = pj;
+                    sB[pos] = __ldg(a.vel4 + j);
+                    sC[pos] = __ldg(a.thermo4 + j);
+                    sI[pos] = j;
+                }
+                nst += __popc(mine);
+                if ((int)__reduce_max_sync(kFull, (unsigned)nst) > B - TW) flush();
             }
         }
         if (__reduce_max_sync(kFull, (unsigned)nst) > 0) flush();
 
-        const unsigned long long pairs = warp_sum_ull((unsigned long long)cnt);
+        const int nself = act ? 1 : 0;  // the (i, i) pair is not a neighbour
+        const unsigned long long pairs = warp_sum_ull((unsigned long long)(cnt - nself));
         const unsigned long long cands =
             warp_sum_ull(tl == 0 ? (unsigned long long)cand * __popc(amask & gmask) : 0ull);
         if (lane == 0) {
@@ -512,6 +555,28 @@ static size_t force_smem()
 {
     const size_t slots = (size_t)(kPairThreads / 32) * (32 / TW) * (kBatchF + 1);
     return slots * (3 * sizeof(float4) + sizeof(int));
+}
+
+// Opt the pair kernels into more than 48 KB of dynamic shared memory (once per process;
+// the attribute is per function, not per device).
+static int smem_optin(sph_ctx *ctx)
+{
+    static bool done = false;
+    if (done) return SPH_OK;
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)density_smem<16>()));
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)density_smem<16>()));
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)density_smem<32>()));
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)density_smem<32>()));
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_force<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)force_smem<16>()));
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_force<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)force_smem<32>()));
+    done = true;
+    return SPH_OK;
 }
 
 static int pair_grid(sph_ctx *ctx, int blocks_per_sm)
@@ -560,6 +625,8 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass)
     a.h_cell_limit = (float)(ctx->grid.L64 * (1.0 - 1e-6));
     a.use_balsara = ctx->p.use_balsara;
     a.last_pass = last_pass ? 1 : 0;
+    int rc = smem_optin(ctx);
+    if (rc) return rc;
     const int g = pair_grid(ctx, 3);
     const bool hash = (ctx->p.flags & SPH_FLAG_NGB_HASH) != 0;
     cudaEvent_t end = nullptr;
@@ -602,6 +669,8 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts)
     a.L32 = ctx->grid.L32;
     a.box = ctx->p.box_size;
     a.alpha = ctx->p.alpha_visc;
+    int rc = smem_optin(ctx);
+    if (rc) return rc;
     const int g = pair_grid(ctx, 2);
     cudaEvent_t end = nullptr;
     timer_begin(ctx, 1, &end);
