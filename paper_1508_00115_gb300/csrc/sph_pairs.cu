@@ -32,7 +32,9 @@ namespace sph {
 constexpr int kBatchD = 128;  // staged survivors per tile, density (4 hit-mask words)
 constexpr int kBatchF = 128;  // staged survivors per tile, force
 constexpr int kPairThreads = 256;
-constexpr float kFar = 1e30f;  // padding source position: its squared distance overflows to +inf
+// Padding sources sit at -kFar and target-less lanes at +kFar: the squared distance
+// between either and anything else overflows to +inf, so no test can pass.
+constexpr float kFar = 1e30f;
 
 // Neighbour cells in visiting order: the own cell, then each of the 13 directions
 // of a half stencil followed by its opposite, so that every staged batch mixes
@@ -189,7 +191,8 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
 
         auto flush = [&]() {
             const int nmax = __reduce_max_sync(kFull, (unsigned)nst);
-            for (int k = nst + tl; k < nmax; k += TW) sA[k] = make_float4(kFar, kFar, kFar, 0.f);
+            // pad this tile's batch up to the warp's longest one (index 0 is a valid particle)
+            for (int k = nst + tl; k < nmax; k += TW) sA[k] = make_float4(-kFar, -kFar, -kFar, __int_as_float(0));
             __syncwarp();
             cand += (unsigned)nst;
             // phase 1: distance tests, broadcast reads of the staged sources
@@ -423,7 +426,11 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
 
         auto flush = [&]() {
             const int nmax = __reduce_max_sync(kFull, (unsigned)nst);
-            for (int k = nst + tl; k < nmax; k += TW) sA[k] = make_float4(kFar, kFar, kFar, 0.f);
+            // pad this tile's batch up to the warp's longest one (index 0 is a valid particle)
+            for (int k = nst + tl; k < nmax; k += TW) {
+                sA[k] = make_float4(-kFar, -kFar, -kFar, 0.f);
+                sI[k] = 0;
+            }
             __syncwarp();
             cand += (unsigned)nst;
             unsigned m[4] = {0u, 0u, 0u, 0u};
