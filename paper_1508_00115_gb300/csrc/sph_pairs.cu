@@ -196,23 +196,29 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
             __syncwarp();
             cand += (unsigned)nst;
             // phase 1: distance tests, broadcast reads of the staged sources
-            unsigned m[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-            for (int wd = 0; wd < 4; ++wd) {
+            unsigned m0 = 0u, m1 = 0u, m2 = 0u, m3 = 0u;
+            const int nwords = (nmax + 31) >> 5;
+#pragma unroll 1
+            for (int wd = 0; wd < nwords; ++wd) {
                 const int kend = min(32, nmax - 32 * wd);
+                const float4 *sw = sA + 32 * wd;
+                unsigned mw = 0u;
 #pragma unroll 4
                 for (int kk = 0; kk < kend; ++kk) {
-                    const float4 s = sA[32 * wd + kk];
+                    const float4 s = sw[kk];
                     const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                     bool in = r2 < lob;
                     if (!in && r2 < hib)
                         in = band_decide(a.x, a.y, a.z, i, __float_as_int(s.w), a.box, hi, hi) & 1u;
-                    m[wd] |= (unsigned)in << kk;
+                    mw |= (unsigned)in << kk;
                 }
+                m0 = wd == 0 ? mw : m0;
+                m1 = wd == 1 ? mw : m1;
+                m2 = wd == 2 ? mw : m2;
+                m3 = wd == 3 ? mw : m3;
             }
             // phase 2: each lane walks its own hits
-            unsigned m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
             while (__any_sync(kFull, (m0 | m1 | m2 | m3) != 0u)) {
                 if (m0 | m1 | m2 | m3) {
                     const int k = pop_bit(m0, m1, m2, m3);
@@ -243,22 +249,46 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
             __syncwarp();
         };
 
-        for (int o = 0; o < 27; ++o) {
-            const int ox = kOrder[o][0], oy = kOrder[o][1], oz = kOrder[o][2];
-            int bs = 0, be = 0;
-            if (live) {
-                const int cb = (wrapc(iz + oz, nc) * nc + wrapc(iy + oy, nc)) * nc + wrapc(ix + ox, nc);
-                bs = a.cell_start[cb];
-                be = a.cell_start[cb + 1];
+        // the 27 cell ranges of the tile, fetched at once: lane tl holds cells tl, tl + TW
+        int cs0 = 0, ce0 = 0, cs1 = 0, ce1 = 0;
+        if (live) {
+            if (tl < 27) {
+                const int cb = (wrapc(iz + kOrder[tl][2], nc) * nc + wrapc(iy + kOrder[tl][1], nc)) * nc +
+                               wrapc(ix + kOrder[tl][0], nc);
+                cs0 = a.cell_start[cb];
+                ce0 = a.cell_start[cb + 1];
             }
-            const float shx = (float)ox * L, shy = (float)oy * L, shz = (float)oz * L;
-            const int nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
-            for (int ch = 0; ch < nchunk; ++ch) {
+            if (tl + TW < 27) {
+                const int o2 = tl + TW;
+                const int cb = (wrapc(iz + kOrder[o2][2], nc) * nc + wrapc(iy + kOrder[o2][1], nc)) * nc +
+                               wrapc(ix + kOrder[o2][0], nc);
+                cs1 = a.cell_start[cb];
+                ce1 = a.cell_start[cb + 1];
+            }
+        }
+        // stage chunk after chunk; one flush site (keeps the kernel small)
+        int o = -1, ch = 0, nchunk = 0, bs = 0, be = 0;
+        float shx = 0.f, shy = 0.f, shz = 0.f;
+        for (;;) {
+            while (ch >= nchunk && o < 26) {
+                ++o;
+                ch = 0;
+                const int src = o < TW ? o : o - TW;
+                bs = __shfl_sync(kFull, o < TW ? cs0 : cs1, src, TW);
+                be = __shfl_sync(kFull, o < TW ? ce0 : ce1, src, TW);
+                nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
+                shx = (float)kOrder[o][0] * L;
+                shy = (float)kOrder[o][1] * L;
+                shz = (float)kOrder[o][2] * L;
+            }
+            const bool more = ch < nchunk;  // warp-uniform
+            if (more) {
                 const int j = bs + ch * TW + tl;
                 bool keep = false;
-                float4 pj;
+                float4 pj, vj;
                 if (j < be) {
                     pj = __ldg(a.pos4 + j);
+                    vj = __ldg(a.vel4 + j);
                     pj.x += shx;
                     pj.y += shy;
                     pj.z += shz;
@@ -271,13 +301,15 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
                 if (keep) {
                     const int pos = nst + __popc(mine & lt);
                     sA[pos] = make_float4(pj.x, pj.y, pj.z, __int_as_float(j));
-                    sB[pos] = __ldg(a.vel4 + j);
+                    sB[pos] = vj;
                 }
                 nst += __popc(mine);
-                if ((int)__reduce_max_sync(kFull, (unsigned)nst) > B - TW) flush();
+                ++ch;
             }
+            const int mx = (int)__reduce_max_sync(kFull, (unsigned)nst);
+            if (mx > B - TW || (!more && mx > 0)) flush();
+            if (!more) break;
         }
-        if (__reduce_max_sync(kFull, (unsigned)nst) > 0) flush();
 
         // counters (one atomic per warp)
         const int nself = act ? 1 : 0;  // the (i, i) pair is not a neighbour
@@ -433,26 +465,31 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
             }
             __syncwarp();
             cand += (unsigned)nst;
-            unsigned m[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-            for (int wd = 0; wd < 4; ++wd) {
+            unsigned m0 = 0u, m1 = 0u, m2 = 0u, m3 = 0u;
+            const int nwords = (nmax + 31) >> 5;
+#pragma unroll 1
+            for (int wd = 0; wd < nwords; ++wd) {
                 const int kend = min(32, nmax - 32 * wd);
+                const float4 *sw = sA + 32 * wd;
+                unsigned mw = 0u;
 #pragma unroll 4
                 for (int kk = 0; kk < kend; ++kk) {
-                    const float4 s = sA[32 * wd + kk];
+                    const float4 s = sw[kk];
                     const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float m2 = fmaxf(hi2, s.w * s.w);
-                    bool in = r2 < m2 - bandmax;
-                    if (!in && r2 < m2 + bandmax) {
-                        bool in_i, in_j;
-                        decide(r2, s.w, sI[32 * wd + kk], in_i, in_j);
-                        in = in_i || in_j;
+                    const float m2x = fmaxf(hi2, s.w * s.w);
+                    bool in = r2 < m2x - bandmax;
+                    if (!in && r2 < m2x + bandmax) {
+                        const unsigned d = band_decide(a.x, a.y, a.z, i, sI[32 * wd + kk], a.box, hi, s.w);
+                        in = d != 0u;
                     }
-                    m[wd] |= (unsigned)in << kk;
+                    mw |= (unsigned)in << kk;
                 }
+                m0 = wd == 0 ? mw : m0;
+                m1 = wd == 1 ? mw : m1;
+                m2 = wd == 2 ? mw : m2;
+                m3 = wd == 3 ? mw : m3;
             }
-            unsigned m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
             while (__any_sync(kFull, (m0 | m1 | m2 | m3) != 0u)) {
                 if (m0 | m1 | m2 | m3) {
                     const int k = pop_bit(m0, m1, m2, m3);
@@ -491,22 +528,49 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
             __syncwarp();
         };
 
-        for (int o = 0; o < 27; ++o) {
-            const int ox = kOrder[o][0], oy = kOrder[o][1], oz = kOrder[o][2];
-            int bs = 0, be = 0;
-            if (live) {
-                const int cb = (wrapc(iz + oz, nc) * nc + wrapc(iy + oy, nc)) * nc + wrapc(ix + ox, nc);
-                bs = a.cell_start[cb];
-                be = a.cell_start[cb + 1];
+        // the 27 cell ranges of the tile, fetched at once: lane tl holds cells tl, tl + TW
+        int cs0 = 0, ce0 = 0, cs1 = 0, ce1 = 0;
+        if (live) {
+            if (tl < 27) {
+                const int cb = (wrapc(iz + kOrder[tl][2], nc) * nc + wrapc(iy + kOrder[tl][1], nc)) * nc +
+                               wrapc(ix + kOrder[tl][0], nc);
+                cs0 = a.cell_start[cb];
+                ce0 = a.cell_start[cb + 1];
             }
-            const float shx = (float)ox * L, shy = (float)oy * L, shz = (float)oz * L;
-            const int nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
-            for (int ch = 0; ch < nchunk; ++ch) {
+            if (tl + TW < 27) {
+                const int o2 = tl + TW;
+                const int cb = (wrapc(iz + kOrder[o2][2], nc) * nc + wrapc(iy + kOrder[o2][1], nc)) * nc +
+                               wrapc(ix + kOrder[o2][0], nc);
+                cs1 = a.cell_start[cb];
+                ce1 = a.cell_start[cb + 1];
+            }
+        }
+        // stage chunk after chunk; one flush site (keeps the kernel small)
+        int o = -1, ch = 0, nchunk = 0, bs = 0, be = 0;
+        float shx = 0.f, shy = 0.f, shz = 0.f;
+        for (;;) {
+            while (ch >= nchunk && o < 26) {
+                ++o;
+                ch = 0;
+                const int src = o < TW ? o : o - TW;
+                bs = __shfl_sync(kFull, o < TW ? cs0 : cs1, src, TW);
+                be = __shfl_sync(kFull, o < TW ? ce0 : ce1, src, TW);
+                nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
+                shx = (float)kOrder[o][0] * L;
+                shy = (float)kOrder[o][1] * L;
+                shz = (float)kOrder[o][2] * L;
+            }
+            const bool more = ch < nchunk;  // warp-uniform
+            if (more) {
                 const int j = bs + ch * TW + tl;
                 bool keep = false;
-                float4 pj;
+                float4 pj, vj, tj;
+                int jj = 0;
                 if (j < be) {
                     pj = __ldg(a.pos4 + j);
+                    vj = __ldg(a.vel4 + j);
+                    tj = __ldg(a.thermo4 + j);
+                    jj = j;
                     pj.x += shx;
                     pj.y += shy;
                     pj.z += shz;
@@ -519,15 +583,17 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
                 if (keep) {
                     const int pos = nst + __popc(mine & lt);
                     sA[pos] = pj;
-                    sB[pos] = __ldg(a.vel4 + j);
-                    sC[pos] = __ldg(a.thermo4 + j);
-                    sI[pos] = j;
+                    sB[pos] = vj;
+                    sC[pos] = tj;
+                    sI[pos] = jj;
                 }
                 nst += __popc(mine);
-                if ((int)__reduce_max_sync(kFull, (unsigned)nst) > B - TW) flush();
+                ++ch;
             }
+            const int mx = (int)__reduce_max_sync(kFull, (unsigned)nst);
+            if (mx > B - TW || (!more && mx > 0)) flush();
+            if (!more) break;
         }
-        if (__reduce_max_sync(kFull, (unsigned)nst) > 0) flush();
 
         const int nself = act ? 1 : 0;  // the (i, i) pair is not a neighbour
         const unsigned long long pairs = warp_sum_ull((unsigned long long)(cnt - nself));
