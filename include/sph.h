@@ -192,6 +192,30 @@ int sph_get_cell_keys(sph_ctx *ctx, int32_t *dev_keys);
  * uint64, length n: sum over j != i with r_ij < h_i of splitmix64(perm id of j). */
 int sph_get_ngb_hash(sph_ctx *ctx, uint64_t *dev_hash);
 
+/* Stable LSD radix sort of cell keys -- the sort sph_build_cells runs -- for callers
+ * that cannot allocate device memory: code whose device memory is owned by another
+ * framework's pool or reserved up front (so a cudaMalloc could fail or break its
+ * accounting), or that must not allocate in the middle of a time step.  The paper
+ * has no counterpart; it is a deployment convenience.
+ *   keys_in   device uint32[n], read only, need not be sorted
+ *   keys_out  device uint32[n], caller-owned: keys in ascending order, equal keys
+ *             in input order
+ *   perm_out  device uint32[n], caller-owned: perm_out[k] = index in keys_in of
+ *             the key now in slot k
+ *   key_bits  significant low bits of every key, 1..32 (bits above are ignored)
+ * The scratch is a fixed static device buffer of about 2.2 MB, held on every GPU
+ * that loads the library until the process exits; n above SPH_SORT_STATIC_MAX_N
+ * returns SPH_ERR_INVALID_ARG before any GPU work.  Nothing is allocated or freed.
+ * The first call on a device looks up the buffer's device address (make it before
+ * any stream capture).  Work is enqueued on `cuda_stream` (a cudaStream_t) on the
+ * current device and the call returns without synchronising.  All calls share the
+ * one buffer: calls whose GPU work overlaps (different streams, or several host
+ * threads) race and must be serialised by the caller.  Returns SPH_OK,
+ * SPH_ERR_INVALID_ARG or SPH_ERR_CUDA (no context, so no sph_last_error text). */
+#define SPH_SORT_STATIC_MAX_N 262144
+int sph_sort_keys_static(const uint32_t *keys_in, uint32_t *keys_out, uint32_t *perm_out, int64_t n,
+                         int32_t key_bits, void *cuda_stream);
+
 int sph_get_stats(sph_ctx *ctx, sph_stats *s);
 int sph_reset_stats(sph_ctx *ctx);
 const char *sph_last_error(const sph_ctx *ctx);

@@ -29,6 +29,7 @@ SPH_ERR_NAN = 6
 SPH_ERR_STATE = 7
 SPH_FLAG_TIMING = 1
 SPH_FLAG_NGB_HASH = 2
+SPH_SORT_STATIC_MAX_N = 262144
 
 _NAMES = {0: "SPH_OK", 1: "SPH_ERR_INVALID_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_NOT_CONVERGED",
           4: "SPH_ERR_H_EXCEEDS_CELL", 5: "SPH_ERR_TIMEOUT", 6: "SPH_ERR_NAN", 7: "SPH_ERR_STATE"}
@@ -109,6 +110,7 @@ def lib(build_if_missing: bool = True):
             "sph_reset_ids": (C, [P]),
             "sph_get_cell_keys": (C, [P, P]),
             "sph_get_ngb_hash": (C, [P, P]),
+            "sph_sort_keys_static": (C, [P, P, P, ctypes.c_int64, ctypes.c_int32, P]),
             "sph_get_stats": (C, [P, ctypes.POINTER(sph_stats)]),
             "sph_reset_stats": (C, [P]),
             "sph_last_error": (ctypes.c_char_p, [P]),

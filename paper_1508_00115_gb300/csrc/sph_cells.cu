@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "sph_internal.cuh"
 
@@ -466,3 +467,80 @@ int build_cells(sph_ctx *ctx, sph_particles *parts)
 }
 
 }  // namespace sph
+
+// ------------------------------------------------- sort without allocation
+// sph_sort_keys_static: the stable LSD radix sort above, for callers that cannot
+// allocate device memory.  Its scratch (one ping-pong set of keys and source
+// slots, the per-tile digit histograms and the scan's block sums) is a
+// file-scope static device array of fixed size, so any process that loads
+// libsph holds it on every GPU it uses, until exit.
+
+namespace sph {
+
+constexpr int64_t kStaticSortTiles = (SPH_SORT_STATIC_MAX_N + kRsTile - 1) / kRsTile;
+constexpr int64_t kStaticHist = 256 * kStaticSortTiles;
+constexpr int64_t kStaticAux = (kStaticHist + kScanChunk - 1) / kScanChunk + 1;
+constexpr int64_t kStaticWords = 2 * SPH_SORT_STATIC_MAX_N + kStaticHist + kStaticAux;
+
+static __device__ __align__(256) uint32_t g_sort_scratch[kStaticWords];
+
+constexpr int kStaticMaxDevices = 64;
+static uint32_t *g_sort_scratch_addr[kStaticMaxDevices];
+static std::mutex g_sort_scratch_mu;
+
+// Device address of g_sort_scratch on the current device (looked up once per
+// device; the host-side symbol is only a stand-in and must never reach a kernel).
+static cudaError_t static_scratch(uint32_t **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_sort_scratch_mu);
+    if (!g_sort_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_sort_scratch);
+        if (e != cudaSuccess) return e;
+        g_sort_scratch_addr[dev] = (uint32_t *)p;
+    }
+    *out = g_sort_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace sph
+
+extern "C" int sph_sort_keys_static(const uint32_t *keys_in, uint32_t *keys_out, uint32_t *perm_out, int64_t n,
+                                    int32_t key_bits, void *cuda_stream)
+{
+    using namespace sph;
+    if (n < 0 || n > SPH_SORT_STATIC_MAX_N || key_bits < 1 || key_bits > 32) return SPH_ERR_INVALID_ARG;
+    if (n == 0) return SPH_OK;
+    if (!keys_in || !keys_out || !perm_out) return SPH_ERR_INVALID_ARG;
+    uint32_t *scratch = nullptr;
+    if (static_scratch(&scratch) != cudaSuccess) return SPH_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    uint32_t *sk = scratch, *sv = scratch + SPH_SORT_STATIC_MAX_N;
+    uint32_t *hist = scratch + 2 * SPH_SORT_STATIC_MAX_N, *aux = hist + kStaticHist;
+    const int nn = (int)n;
+    const int ntiles = (nn + kRsTile - 1) / kRsTile;
+    const int passes = (key_bits + 7) / 8;
+    const int64_t nh = (int64_t)256 * ntiles;
+    const int64_t nb = (nh + kScanChunk - 1) / kScanChunk;
+    // ping-pong between the static buffers and the outputs so that the last
+    // pass writes the outputs; every histogram and block sum is rewritten each
+    // pass, so nothing left by an earlier call is read
+    const uint32_t *kin = keys_in, *vin = nullptr;
+    for (int p = 0; p < passes; ++p) {
+        const bool to_out = ((passes - 1 - p) % 2) == 0;
+        uint32_t *kout = to_out ? keys_out : sk, *vout = to_out ? perm_out : sv;
+        const int shift = 8 * p;
+        k_radix_hist<<<ntiles, kRsThreads, 0, st>>>(kin, nn, shift, hist, ntiles);
+        k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(hist, nh, aux);
+        k_scan_top<<<1, kScanThreads, 0, st>>>(aux, nb);
+        k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(hist, hist, nh, aux);
+        k_radix_scatter<<<ntiles, kRsThreads, 0, st>>>(kin, vin, kout, vout, nn, shift, hist, ntiles);
+        kin = kout;
+        vin = vout;
+    }
+    return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}

@@ -1,0 +1,64 @@
+"""sph_sort_keys_static: the cell-key radix sort for callers that cannot allocate
+device memory (their memory belongs to another framework's pool, or they must not
+allocate mid-step).  It sorts with a fixed static device buffer only; its output
+must equal, bit for bit, the sorted keys and permutation that sph_build_cells
+produces for the same particles.  This file is collected last on purpose."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1508_00115_gb300 import binding, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _build_sorted(d):
+    """Sorted keys, permutation and grid size from the existing entry point."""
+    n = d["x"].size
+    ctx = binding.Context(n)
+    parts = binding.Particles(d)
+    ctx.build_cells(parts)
+    keys = ctx.cell_keys().view(np.uint32).copy()
+    perm = ctx.permutation()
+    nc = ctx.stats()["nc"]
+    ctx.close()
+    return keys, perm, nc
+
+
+def _static_sort(keys: np.ndarray, bits: int):
+    n = keys.size
+    kin = torch.as_tensor(keys.view(np.int32).copy()).cuda()
+    kout = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    pout = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = binding.lib().sph_sort_keys_static(ctypes.c_void_p(kin.data_ptr()),
+                                            ctypes.c_void_p(kout.data_ptr()),
+                                            ctypes.c_void_p(pout.data_ptr()), n, bits,
+                                            ctypes.c_void_p(stream))
+    assert rc == binding.SPH_OK
+    torch.cuda.synchronize()
+    return kout.cpu().numpy().view(np.uint32), pout.cpu().numpy().view(np.uint32)
+
+
+def test_static_sort_matches_build_on_two_calls_in_a_row():
+    for seed in (21, 22):
+        d = inputs.uniform(60000, seed=seed)
+        ks, perm, nc = _build_sorted(d)
+        # unsorted keys of the input order, from the wrapped positions
+        x, y, z = (oracle.wrap(d[k], 1.0) for k in ("x", "y", "z"))
+        keys = oracle.cell_keys(x, y, z, 1.0, nc).astype(np.uint32)
+        bits = int(nc ** 3 - 1).bit_length()
+        ko, po = _static_sort(keys, bits)
+        assert np.array_equal(ko, ks)
+        assert np.array_equal(po.astype(np.int64), perm)
+
+
+def test_static_sort_rejects_oversize_without_gpu_work():
+    L = binding.lib()
+    rc = L.sph_sort_keys_static(None, None, None, binding.SPH_SORT_STATIC_MAX_N + 1, 16, None)
+    assert rc == binding.SPH_ERR_INVALID_ARG
+    rc = L.sph_sort_keys_static(None, None, None, 10, 0, None)
+    assert rc == binding.SPH_ERR_INVALID_ARG
