@@ -69,13 +69,22 @@ double orc_dw(double q)
 
 /* ---- periodic box (Sec. 2: "the simulated volume is periodically replicated") ---- */
 
+/* Wrap into [0, box): positions already inside are returned unchanged; others are
+ * shifted by box*floor(x/box), then corrected by one box if rounding left them
+ * just outside (and set to 0 if still outside). */
+double orc_wrap1(double v, double box)
+{
+    if (v >= 0.0 && v < box) return v;
+    double w = v - box * floor(v / box);
+    if (w < 0.0) w += box;
+    if (w >= box) w -= box;
+    if (w < 0.0 || w >= box) w = 0.0;
+    return w;
+}
+
 void orc_wrap(int64_t n, double box, double *x)
 {
-    for (int64_t i = 0; i < n; ++i) {
-        double v = x[i] - box * floor(x[i] / box);
-        if (v >= box) v -= box;
-        x[i] = v;
-    }
+    for (int64_t i = 0; i < n; ++i) x[i] = orc_wrap1(x[i], box);
 }
 
 static inline double min_image(double d, double box)

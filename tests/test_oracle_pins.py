@@ -341,6 +341,15 @@ def test_cell_keys_and_wrap():
     assert k == (4 * nc + 2) * nc
     w = oracle.wrap(np.array([-0.25, 1.25, 1.0, -1e-20, 0.5]), 1.0)
     assert list(w) == [0.75, 0.25, 0.0, 0.0, 0.5]
+    # always inside [0, L), also for boxes whose quotients round up to an integer
+    rng = np.random.default_rng(3)
+    for box in (0.37, 1.0, 3.3):
+        v = np.concatenate([rng.uniform(-5, 5, 2000) * box, box * (1 - 2.0 ** -np.arange(40, 54)),
+                            -box * 2.0 ** -np.arange(40, 60)])
+        w = oracle.wrap(v, box)
+        assert np.all((w >= 0) & (w < box))
+        inside = (v >= 0) & (v < box)
+        assert np.array_equal(w[inside], v[inside])
 
 
 def test_hash_is_order_independent_fingerprint():
