@@ -151,6 +151,13 @@ def _traffic(kernel: str):
     return val
 
 
+def _schedule(args, binding) -> dict:
+    """Tile width / cell factor: fixed when given, else chosen by the autotuner."""
+    if args.tile_width == 0 and args.cell_factor == 0:
+        return {"flags": binding.SPH_FLAG_AUTOTUNE}
+    return {"flags": 0, "tile_width": args.tile_width or 16, "cell_factor": args.cell_factor or 1.1}
+
+
 def workload(seed: int = 2):
     from paper_1508_00115_gb300 import inputs
     return inputs.sedov(128, seed=seed)
@@ -238,8 +245,9 @@ def run_ours(args):
     d = workload()
     n = int(d["x"].size)
     stream = torch.cuda.Stream()
-    ctx = binding.Context(n, device=local, stream=stream.cuda_stream, flags=binding.SPH_FLAG_TIMING,
-                          tile_width=args.tile_width, cell_factor=args.cell_factor)
+    sched = _schedule(args, binding)
+    ctx = binding.Context(n, device=local, stream=stream.cuda_stream,
+                          flags=binding.SPH_FLAG_TIMING | sched.pop("flags"), **sched)
     parts = binding.Particles(d)
     torch.cuda.synchronize()
     for _ in range(args.warmup):
@@ -300,8 +308,9 @@ def run_ours(args):
     # end to end through the public C-ABI with host buffers (pinned)
     e2e = None
     if not args.no_e2e:
+        sched_h = _schedule(args, binding)
         ctx_h = binding.Context(n, device=local, stream=stream.cuda_stream,
-                                tile_width=args.tile_width, cell_factor=args.cell_factor)
+                                flags=sched_h.pop("flags"), **sched_h)
         hp = binding.Particles(d, device="cpu", pin=True)
         for _ in range(max(1, args.warmup)):
             ctx_h.step_host(hp)
@@ -335,8 +344,10 @@ def run_ours(args):
            "config": {"workload": "sedov-taylor 128^3 jittered lattice, KDK step: cells + "
                                   "density/h-iteration + force + kicks (plain path)",
                       "n_particles": n, "n_ngb": 48, "h_tol": float(ctx.params.h_tol),
-                      "tile_width": int(ctx.params.tile_width) or 16,
-                      "cell_factor": float(ctx.params.cell_factor),
+                      "tile_width": int(st["tile_width"]),
+                      "cell_factor": round(float(st["cell_factor"]), 3),
+                      "schedule": "autotuned" if args.tile_width == 0 and args.cell_factor == 0
+                                  else "fixed",
                       "l2": f"inputs larger than L2 (~{work_mb:.0f} MB resident per step > 129 MB)",
                       "parallelism": f"replicas x{world}"},
            "pair_interactions_per_s": world * pairs / sec,
@@ -369,8 +380,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-force-targets", type=int, default=48)
-    ap.add_argument("--tile-width", type=int, default=0, help="0 (default), 16 or 32")
-    ap.add_argument("--cell-factor", type=float, default=1.1)
+    ap.add_argument("--tile-width", type=int, default=0, help="16 or 32 (0: autotuned)")
+    ap.add_argument("--cell-factor", type=float, default=0.0, help=">= 1 (0: autotuned)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")

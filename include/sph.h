@@ -54,6 +54,10 @@ typedef struct sph_ctx sph_ctx; /* opaque, library-owned */
 /* Flags for sph_params.flags */
 #define SPH_FLAG_TIMING 1u /* record CUDA events around the pair kernels */
 #define SPH_FLAG_NGB_HASH 2u /* density pass also writes a neighbour-set hash */
+#define SPH_FLAG_AUTOTUNE 4u /* before the first density pass, time one pass for each
+                                candidate schedule (tile width 16/32 x cell factor
+                                1.05/1.25/1.5) on the current particles and keep the
+                                fastest; overrides tile_width and cell_factor */
 
 typedef struct {
     int64_t n;           /* particles; 0 <= n < 2^31                                  */
@@ -126,6 +130,8 @@ typedef struct {
     double t_force_ms;         /* summed device time of force launches (TIMING)     */
     double t_build_ms;         /* summed device time of cell builds (TIMING)        */
     int64_t kernel_launches;   /* libsph kernels launched                           */
+    int32_t tile_width;        /* schedule in use: targets per tile (16 or 32)       */
+    float cell_factor;         /* schedule in use: cell side / max h                 */
 } sph_stats;
 
 /* Fill *p with the defaults: gamma 5/3, n_ngb 48, h_tol 1e-4, alpha 0.8, cfl 0.1,
@@ -143,9 +149,12 @@ int sph_set_n(sph_ctx *ctx, int64_t n);
 
 /* Sec. 3.1 cells: wrap positions into [0, L), choose nc = floor(L / (cell_factor *
  * max h)) (>= 3), key each particle by its cell ((iz*nc+iy)*nc+ix with
- * ix = floor(x * nc/L)), stable LSD radix sort by key, and permute x..h, vx..vz,
- * m, u IN PLACE into cell order.  The composite permutation since the first build
- * (or since sph_reset_ids) is kept: sph_get_permutation.  Host read: max h.
+ * ix = floor(x * nc/L)) and its octant inside the cell (x, y, z at or above the
+ * cell centre), stable LSD radix sort by that key, and permute x, y, z, vx, vy,
+ * vz, m, u, h and the force outputs ax, ay, az, dudt, vsig IN PLACE into cell
+ * order (density outputs are left as they are and are stale until sph_density).
+ * The composite permutation since the first build (or since sph_reset_ids) is
+ * kept: sph_get_permutation.  Host read: max h.
  * Errors: SPH_ERR_H_EXCEEDS_CELL if max h > L/3. */
 int sph_build_cells(sph_ctx *ctx, sph_particles *parts);
 

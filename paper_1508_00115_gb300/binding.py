@@ -29,6 +29,7 @@ SPH_ERR_NAN = 6
 SPH_ERR_STATE = 7
 SPH_FLAG_TIMING = 1
 SPH_FLAG_NGB_HASH = 2
+SPH_FLAG_AUTOTUNE = 4
 SPH_SORT_STATIC_MAX_N = 262144
 
 _NAMES = {0: "SPH_OK", 1: "SPH_ERR_INVALID_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_NOT_CONVERGED",
@@ -73,7 +74,8 @@ class sph_stats(ctypes.Structure):
                 ("density_targets", ctypes.c_int64), ("force_pairs", ctypes.c_int64),
                 ("density_candidates", ctypes.c_int64), ("force_candidates", ctypes.c_int64),
                 ("t_density_ms", ctypes.c_double), ("t_force_ms", ctypes.c_double),
-                ("t_build_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+                ("t_build_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("tile_width", ctypes.c_int32), ("cell_factor", ctypes.c_float)]
 
 
 _lock = threading.Lock()

@@ -58,7 +58,8 @@ void timer_end(sph_ctx *ctx, cudaEvent_t end)
 static void free_particles(sph_ctx *c)
 {
     void *ptrs[] = {c->pos4, c->vel4, c->thermo4, c->upred, c->active, c->ids, c->ids_tmp, c->ngb_hash,
-                    c->keys, c->keys_alt, c->vals, c->vals_alt, c->hist, c->s64, c->s32, c->tiles};
+                    c->keys, c->keys_alt, c->vals, c->vals_alt, c->hist, c->s64, c->s32, c->tiles,
+                    c->act_tiles};
     for (void *p : ptrs) cudaFree(p);
     c->pos4 = c->vel4 = c->thermo4 = nullptr;
     c->upred = nullptr;
@@ -69,6 +70,7 @@ static void free_particles(sph_ctx *c)
     c->s64 = nullptr;
     c->s32 = nullptr;
     c->tiles = nullptr;
+    c->act_tiles = nullptr;
     c->cap = 0;
 }
 
@@ -94,6 +96,7 @@ static int alloc_particles(sph_ctx *c, int64_t cap)
     SPH_CUDA(c, cudaMalloc(&c->s64, sizeof(double) * 6 * cap));
     SPH_CUDA(c, cudaMalloc(&c->s32, sizeof(float) * 8 * cap));
     SPH_CUDA(c, cudaMalloc(&c->tiles, sizeof(int4) * c->tile_cap));
+    SPH_CUDA(c, cudaMalloc(&c->act_tiles, sizeof(int4) * c->tile_cap));
     SPH_CUDA(c, cudaMemsetAsync(c->ngb_hash, 0, sizeof(uint64_t) * cap, c->stream));
     c->cap = cap;
     return SPH_OK;
@@ -133,19 +136,72 @@ static int read_counters(sph_ctx *ctx)
     return SPH_OK;
 }
 
+// Autotuner: one timed density pass (no h update) per candidate schedule on the
+// current particles; keeps the fastest and leaves the cells built for it.
+static int autotune(sph_ctx *ctx, sph_particles *parts)
+{
+    const int tws[2] = {16, 32};
+    const float cfs[3] = {1.05f, 1.25f, 1.5f};
+    cudaEvent_t e0, e1;
+    SPH_CUDA(ctx, cudaEventCreate(&e0));
+    SPH_CUDA(ctx, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_tw = ctx->tile_w;
+    float best_cf = ctx->p.cell_factor;
+    const uint32_t flags = ctx->p.flags;
+    ctx->p.flags &= ~SPH_FLAG_TIMING;  // probes are not part of the statistics
+    int rc = SPH_OK;
+    for (int a = 0; a < 2 && rc == SPH_OK; ++a)
+        for (int b = 0; b < 3 && rc == SPH_OK; ++b) {
+            ctx->tile_w = tws[a];
+            ctx->p.cell_factor = cfs[b];
+            rc = build_cells(ctx, parts);
+            if (rc == SPH_ERR_H_EXCEEDS_CELL) {  // this cell factor cannot hold the largest h
+                rc = SPH_OK;
+                continue;
+            }
+            if (rc) break;
+            SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, ctx->n, ctx->stream));
+            SPH_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+            rc = run_density_pass(ctx, parts, true, false);
+            SPH_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+            SPH_CUDA(ctx, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            SPH_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_tw = tws[a];
+                best_cf = cfs[b];
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->p.flags = flags;
+    if (rc) return rc;
+    ctx->tile_w = best_tw;
+    ctx->p.cell_factor = best_cf;
+    ctx->tuned = true;
+    return build_cells(ctx, parts);
+}
+
 static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
 {
     if (!ctx->built) return fail(ctx, SPH_ERR_STATE, "sph_density needs sph_build_cells on the current positions");
     int n = (int)ctx->n;
     int iters = 0;
     unsigned long long unconv = 0;
+    if (n > 0 && (ctx->p.flags & SPH_FLAG_AUTOTUNE) && !ctx->tuned) {
+        int rc = autotune(ctx, parts);
+        if (rc) return rc;
+    }
     if (n > 0) {
         SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, n, ctx->stream));
+        bool all_tiles = true;  // first pass (and after a rebuild): every tile
         for (;;) {
             const bool last = iters == ctx->p.max_h_iter - 1;
             SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_UNCONV, 0, 2 * sizeof(unsigned long long),
                                           ctx->stream));
-            int rc = run_density_pass(ctx, parts, last);
+            int rc = run_density_pass(ctx, parts, last, !all_tiles);
             if (rc) return rc;
             ++iters;
             rc = read_counters(ctx);
@@ -161,6 +217,11 @@ static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
                 if (rc) return rc;
                 ctx->st.rebuilds++;
                 SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, n, ctx->stream));
+                all_tiles = true;
+            } else {
+                rc = compact_active_tiles(ctx);
+                if (rc) return rc;
+                all_tiles = false;
             }
         }
         int rc = sync_h(ctx, parts);
@@ -296,7 +357,8 @@ int sph_init(sph_ctx **out, const sph_params *p, int device, void *cuda_stream)
         cudaMalloc(&c->d_red, red_scratch_doubles() * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&c->h_red, 8 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->scan_aux, kScanAuxCap * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMalloc(&c->n_tiles, sizeof(int)) != cudaSuccess)
+        cudaMalloc(&c->n_tiles, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->n_act_tiles, sizeof(int)) != cudaSuccess)
         return bail(SPH_ERR_CUDA);
     if (cudaMemsetAsync(c->counters, 0, C_NCOUNTERS * sizeof(unsigned long long), c->stream) != cudaSuccess)
         return bail(SPH_ERR_CUDA);
@@ -425,9 +487,7 @@ int sph_get_cell_keys(sph_ctx *ctx, int32_t *dev_keys)
 {
     if (!ctx || !dev_keys) return SPH_ERR_INVALID_ARG;
     if (!ctx->built) return fail(ctx, SPH_ERR_STATE, "no cell build on the current positions");
-    SPH_CUDA(ctx, cudaMemcpyAsync(dev_keys, ctx->keys, sizeof(int32_t) * ctx->n, cudaMemcpyDeviceToDevice,
-                                  ctx->stream));
-    return SPH_OK;
+    return cell_keys_out(ctx, dev_keys);
 }
 
 int sph_get_ngb_hash(sph_ctx *ctx, uint64_t *dev_hash)
@@ -458,6 +518,8 @@ int sph_get_stats(sph_ctx *ctx, sph_stats *s)
     st.t_density_ms = t[0];
     st.t_force_ms = t[1];
     st.t_build_ms = t[2];
+    st.tile_width = ctx->tile_w;
+    st.cell_factor = ctx->p.cell_factor;
     *s = st;
     return SPH_OK;
 }
@@ -500,6 +562,7 @@ void sph_destroy(sph_ctx *ctx)
     cudaFreeHost(ctx->h_red);
     cudaFree(ctx->scan_aux);
     cudaFree(ctx->n_tiles);
+    cudaFree(ctx->n_act_tiles);
     cudaFree(ctx->mirror_block);
     for (Timer &t : ctx->timers) {
         cudaEventDestroy(t.a);

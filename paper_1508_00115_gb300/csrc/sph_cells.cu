@@ -231,12 +231,21 @@ struct GridDev {
     double box, s, L64;
 };
 
+// Wrap into [0, box): positions already inside (the common case) are returned
+// unchanged without the FP64 division; others are shifted by box*floor(v/box) and
+// corrected by one box if rounding left them just outside.
 __device__ __forceinline__ double wrap64(double v, double box)
 {
+    if (v >= 0.0 && v < box) return v;
     double w = __dsub_rn(v, __dmul_rn(box, floor(__ddiv_rn(v, box))));
+    if (w < 0.0) w = __dadd_rn(w, box);
     if (w >= box) w = __dsub_rn(w, box);
+    if (w < 0.0 || w >= box) w = 0.0;
     return w;
 }
+
+// centre of cell index c along one axis, (c + 1/2) * L
+__device__ __forceinline__ double centre64(int c, double L64) { return __dmul_rn(__dadd_rn((double)c, 0.5), L64); }
 
 __device__ __forceinline__ int cell_of(double v, double s, int nc)
 {
@@ -253,7 +262,11 @@ __global__ void k_wrap_key(double *x, double *y, double *z, int n, GridDev g, ui
     y[i] = b;
     z[i] = c;
     int ix = cell_of(a, g.s, g.nc), iy = cell_of(b, g.s, g.nc), iz = cell_of(c, g.s, g.nc);
-    keys[i] = (uint32_t)((iz * g.nc + iy) * g.nc + ix);
+    // key = cell * 8 + octant: inside a cell particles are grouped by octant (z
+    // slowest), so the tiles of a cell split in two are each about half a cell
+    const unsigned oct = (a >= centre64(ix, g.L64) ? 1u : 0u) | (b >= centre64(iy, g.L64) ? 2u : 0u) |
+                         (c >= centre64(iz, g.L64) ? 4u : 0u);
+    keys[i] = ((uint32_t)((iz * g.nc + iy) * g.nc + ix) << 3) | oct;
 }
 
 struct GatherArgs {
@@ -282,11 +295,10 @@ __global__ void k_gather(GatherArgs a)
     double vx = P.vx[src], vy = P.vy[src], vz = P.vz[src];
     float m = P.m[src], u = P.u[src], h = P.h[src];
     float ax = P.ax[src], ay = P.ay[src], az = P.az[src], du = P.dudt[src], vs = P.vsig[src];
-    uint32_t key = a.skeys[p];
+    uint32_t key = a.skeys[p] >> 3;
     int nc = a.g.nc;
     int ix = key % nc, iy = (key / nc) % nc, iz = key / (nc * nc);
-    double cx = ((double)ix + 0.5) * a.g.L64, cy = ((double)iy + 0.5) * a.g.L64,
-           cz = ((double)iz + 0.5) * a.g.L64;
+    double cx = centre64(ix, a.g.L64), cy = centre64(iy, a.g.L64), cz = centre64(iz, a.g.L64);
     a.pos4[p] = make_float4((float)(x - cx), (float)(y - cy), (float)(z - cz), h);
     double ph = a.pred_half;
     a.vel4[p] = make_float4((float)(vx + (double)ax * ph), (float)(vy + (double)ay * ph),
@@ -341,7 +353,7 @@ __global__ void k_cell_start(const uint32_t *__restrict__ skeys, int n, int64_t 
     int lo = 0, hi = n;
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
-        if ((int64_t)skeys[mid] < c) lo = mid + 1;
+        if ((int64_t)(skeys[mid] >> 3) < c) lo = mid + 1;
         else hi = mid;
     }
     cs[c] = lo;
@@ -366,6 +378,21 @@ __global__ void k_tiles_write(const int *__restrict__ cs, int64_t ncells, int tw
     for (int b = 0; b < cnt; b += tw, ++k)
         tiles[off + k] = make_int4((int)c, s + b, min(tw, cnt - b), 0);
     if (c == ncells - 1) *n_tiles = (int)(off + k);
+}
+
+__global__ void k_cell_of_key(const uint32_t *__restrict__ skeys, int n, int32_t *__restrict__ out)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) out[p] = (int32_t)(skeys[p] >> 3);
+}
+
+int cell_keys_out(sph_ctx *ctx, int32_t *dev_keys)
+{
+    const int n = (int)ctx->n;
+    if (n <= 0) return SPH_OK;
+    k_cell_of_key<<<(n + 255) / 256, 256, 0, ctx->stream>>>(ctx->keys, n, dev_keys);
+    SPH_LAUNCH(ctx, "cell keys");
+    return SPH_OK;
 }
 
 static int ensure_cells(sph_ctx *ctx, int64_t ncells)
@@ -413,6 +440,7 @@ int build_cells(sph_ctx *ctx, sph_particles *parts)
     g.inv_s = (double)nc / box;
     int bits = 1;
     while ((1ll << bits) < g.n_cells) ++bits;
+    bits += 3;  // octant within the cell
     g.key_bits = bits;
     rc = ensure_cells(ctx, g.n_cells);
     if (rc) return rc;

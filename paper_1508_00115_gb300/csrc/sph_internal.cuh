@@ -90,6 +90,9 @@ struct sph_ctx {
     int4 *tiles = nullptr;
     int64_t tile_cap = 0;
     int *n_tiles = nullptr;      // device scalar
+    int4 *act_tiles = nullptr;   // tiles with an unconverged target (later density passes)
+    int *n_act_tiles = nullptr;  // device scalar
+    bool tuned = false;          // autotuner ran
     uint32_t *cell_tiles = nullptr;  // per-cell tile counts -> offsets
     // scalars
     unsigned long long *counters = nullptr;  // device
@@ -141,7 +144,9 @@ void timer_end(sph_ctx *ctx, cudaEvent_t end);
 
 // launch wrappers (defined in the .cu files) ---------------------------------
 int build_cells(sph_ctx *ctx, sph_particles *parts);            // sph_cells.cu
-int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass);  // sph_pairs.cu
+int cell_keys_out(sph_ctx *ctx, int32_t *dev_keys);             // sph_cells.cu
+int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool active_list);  // sph_pairs.cu
+int compact_active_tiles(sph_ctx *ctx);                                    // sph_pairs.cu
 int run_force_pass(sph_ctx *ctx, sph_particles *parts);                    // sph_pairs.cu
 int sync_h(sph_ctx *ctx, sph_particles *parts);                            // sph_pairs.cu
 int reduce_max_h(sph_ctx *ctx, const float *h, float *h_out_host);         // sph_integrate.cu

@@ -663,14 +663,44 @@ static int pair_grid(sph_ctx *ctx, int blocks_per_sm)
     return (int)std::max<int64_t>(g, 1);
 }
 
-int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass)
+// Tiles that still hold an unconverged target, for the later density passes
+// (order of the list is irrelevant: every target is summed by one lane).
+__global__ void k_compact_tiles(const int4 *__restrict__ tiles, const int *__restrict__ n_tiles,
+                                const uint8_t *__restrict__ active, int4 *__restrict__ out, int *__restrict__ n_out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    bool keep = false;
+    int4 tile = make_int4(0, 0, 0, 0);
+    if (t < *n_tiles) {
+        tile = tiles[t];
+        for (int k = 0; k < tile.z && !keep; ++k) keep = active[tile.y + k] != 0;
+    }
+    const unsigned b = __ballot_sync(kFull, keep);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && b) base = atomicAdd(n_out, __popc(b));
+    base = __shfl_sync(kFull, base, 0);
+    if (keep) out[base + __popc(b & ((1u << lane) - 1u))] = tile;
+}
+
+int compact_active_tiles(sph_ctx *ctx)
+{
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->n_act_tiles, 0, sizeof(int), ctx->stream));
+    const int64_t cap = ctx->tile_cap;
+    k_compact_tiles<<<(unsigned)((cap + 255) / 256), 256, 0, ctx->stream>>>(ctx->tiles, ctx->n_tiles, ctx->active,
+                                                                           ctx->act_tiles, ctx->n_act_tiles);
+    SPH_LAUNCH(ctx, "compact tiles");
+    return SPH_OK;
+}
+
+int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool active_list)
 {
     DensityArgs a;
     a.pos4 = ctx->pos4;
     a.vel4 = ctx->vel4;
     a.cell_start = ctx->cell_start;
-    a.tiles = ctx->tiles;
-    a.n_tiles = ctx->n_tiles;
+    a.tiles = active_list ? ctx->act_tiles : ctx->tiles;
+    a.n_tiles = active_list ? ctx->n_act_tiles : ctx->n_tiles;
     a.x = parts->x;
     a.y = parts->y;
     a.z = parts->z;

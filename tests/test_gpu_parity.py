@@ -186,6 +186,28 @@ def test_edge_cases():
     assert e.value.code == binding.SPH_ERR_NAN
 
 
+def test_autotuned_schedule_parity():
+    """The autotuner rebuilds cells with other tile widths / cell factors; results
+    must still match the oracle."""
+    from paper_1508_00115_gb300 import binding
+    d = _uniform_moving(9000, 14)
+    ctx, parts, g = gpu_hydro(d, flags=binding.SPH_FLAG_NGB_HASH | binding.SPH_FLAG_AUTOTUNE)
+    assert g["stats"]["tile_width"] in (16, 32)
+    s = oracle_state(g)
+    dd = check_density(g, s)
+    check_ghost(g, s, dd, np.arange(s.n))
+    check_force(g, s)
+
+
+@pytest.mark.parametrize("tw", [16, 32])
+def test_tile_widths_parity(tw):
+    d = _uniform_moving(7000, 15)
+    ctx, parts, g = gpu_hydro(d, tile_width=tw, cell_factor=1.3)
+    s = oracle_state(g)
+    check_density(g, s)
+    check_force(g, s)
+
+
 def test_h_growth_forces_rebuild():
     """A guess far below the converged h forces cells to be rebuilt mid-iteration;
     the result still matches the oracle."""

@@ -47,12 +47,18 @@ def test_static_sort_matches_build_on_two_calls_in_a_row():
     for seed in (21, 22):
         d = inputs.uniform(60000, seed=seed)
         ks, perm, nc = _build_sorted(d)
-        # unsorted keys of the input order, from the wrapped positions
-        x, y, z = (oracle.wrap(d[k], 1.0) for k in ("x", "y", "z"))
-        keys = oracle.cell_keys(x, y, z, 1.0, nc).astype(np.uint32)
-        bits = int(nc ** 3 - 1).bit_length()
+        # unsorted build keys of the input order: cell * 8 + octant of the wrapped
+        # position inside its cell (bits x, y, z at or above the cell centre)
+        pos = [oracle.wrap(d[k], 1.0) for k in ("x", "y", "z")]
+        cell = oracle.cell_keys(*pos, 1.0, nc).astype(np.uint32)
+        L = 1.0 / nc
+        idx = (cell % nc, (cell // nc) % nc, cell // (nc * nc))
+        octant = sum(((p >= (i + 0.5) * L).astype(np.uint32) << b)
+                     for b, (p, i) in enumerate(zip(pos, idx)))
+        keys = (cell << 3) | octant
+        bits = int(nc ** 3 - 1).bit_length() + 3
         ko, po = _static_sort(keys, bits)
-        assert np.array_equal(ko, ks)
+        assert np.array_equal(ko >> 3, ks)
         assert np.array_equal(po.astype(np.int64), perm)
 
 
