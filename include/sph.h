@@ -74,7 +74,12 @@ typedef struct {
     uint32_t flags;      /* SPH_FLAG_*                                               */
     int32_t tile_width;  /* targets per warp work item: 16 (two cells per warp) or   */
                          /* 32 (one cell per warp); 0 = default (16)                 */
-    int32_t reserved;    /* must be 0                                                */
+    int32_t n_boxes;     /* independent periodic boxes batched in one set (0 or 1:   */
+                         /* a single box); every box has side box_size               */
+    const int64_t *box_offsets; /* HOST, n_boxes + 1 entries, 0 = first <= ... <= */
+                         /* last = n: box b owns particles [off[b], off[b+1]); each  */
+                         /* box gets its own cell grid; NULL when n_boxes <= 1;      */
+                         /* copied by sph_init                                       */
 } sph_params;
 
 /*
@@ -114,10 +119,10 @@ typedef struct {
 
 /* Counters since the last sph_reset_stats (sph_get_stats synchronises the stream). */
 typedef struct {
-    int32_t nc;                /* cells per side of the current grid                 */
+    int32_t nc;                /* cells per side of the grid of box 0                */
     int32_t rebuilds;          /* cell rebuilds forced by h growing past the cell    */
-    int64_t n_cells;           /* nc^3                                               */
-    double cell_size;          /* L / nc                                             */
+    int64_t n_cells;           /* cells of all boxes                                 */
+    double cell_size;          /* cell side of box 0                                 */
     int64_t density_passes;    /* density-kernel launches                            */
     int64_t force_passes;      /* force-kernel launches                              */
     int64_t density_pairs;     /* directed pairs (i, j != i) with r_ij < h_i, summed */
@@ -132,6 +137,7 @@ typedef struct {
     int64_t kernel_launches;   /* libsph kernels launched                           */
     int32_t tile_width;        /* schedule in use: targets per tile (16 or 32)       */
     float cell_factor;         /* schedule in use: cell side / max h                 */
+    int64_t graph_steps;       /* steps replayed from a captured graph (sph_steps)   */
 } sph_stats;
 
 /* Fill *p with the defaults: gamma 5/3, n_ngb 48, h_tol 1e-4, alpha 0.8, cfl 0.1,
@@ -179,6 +185,20 @@ int sph_force(sph_ctx *ctx, sph_particles *parts);
  * (either may be NULL) receive the step taken and the conserved quantities.
  * Host read: dt and the reductions. */
 int sph_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_used, sph_conserved *out);
+
+/* n_steps KDK steps (as sph_step) with no host synchronisation between them: the
+ * step is captured once into a CUDA graph and replayed.  Differences from calling
+ * sph_step n_steps times: dt lives on the device (dt <= 0: the CFL step of each
+ * step's start, else the fixed dt); the cell grid of every box is planned once at
+ * entry and kept (cells stay correct while every h stays within twice the planned
+ * cell side; beyond that the call returns SPH_ERR_H_EXCEEDS_CELL); each density
+ * evaluation runs a fixed number of passes, min(max_h_iter, 6) -- passes after
+ * convergence find no work -- and SPH_ERR_NOT_CONVERGED is returned if any
+ * particle was still unconverged after them.  *out (may be NULL) receives the
+ * conserved quantities after the last step; *dt_last (may be NULL) its dt.
+ * Synchronises the stream once, at the end. */
+int sph_steps(sph_ctx *ctx, sph_particles *parts, int32_t n_steps, double dt, double *dt_last,
+              sph_conserved *out);
 
 /* sph_step on HOST arrays (pinned memory recommended): copies x..h, vx..vz, m, u,
  * ax, ay, az, dudt, vsig to library-owned device buffers, steps, and copies every

@@ -50,7 +50,8 @@ class sph_params(ctypes.Structure):
                 ("cfl", ctypes.c_float), ("cell_factor", ctypes.c_float),
                 ("max_h_iter", ctypes.c_int32), ("use_balsara", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("flags", ctypes.c_uint32),
-                ("tile_width", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tile_width", ctypes.c_int32), ("n_boxes", ctypes.c_int32),
+                ("box_offsets", ctypes.c_void_p)]
 
 
 _PFIELDS = ["x", "y", "z", "vx", "vy", "vz", "m", "u", "h", "rho", "P", "c", "f", "divv", "curl",
@@ -75,7 +76,8 @@ class sph_stats(ctypes.Structure):
                 ("density_candidates", ctypes.c_int64), ("force_candidates", ctypes.c_int64),
                 ("t_density_ms", ctypes.c_double), ("t_force_ms", ctypes.c_double),
                 ("t_build_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
-                ("tile_width", ctypes.c_int32), ("cell_factor", ctypes.c_float)]
+                ("tile_width", ctypes.c_int32), ("cell_factor", ctypes.c_float),
+                ("graph_steps", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
@@ -108,6 +110,8 @@ def lib(build_if_missing: bool = True):
                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(sph_conserved)]),
             "sph_step_host": (C, [P, ctypes.POINTER(sph_particles), ctypes.c_double,
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(sph_conserved)]),
+            "sph_steps": (C, [P, ctypes.POINTER(sph_particles), ctypes.c_int32, ctypes.c_double,
+                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(sph_conserved)]),
             "sph_get_permutation": (C, [P, P]),
             "sph_reset_ids": (C, [P]),
             "sph_get_cell_keys": (C, [P, P]),
@@ -180,6 +184,14 @@ def sph_step(ctx, parts: sph_particles, dt: float = 0.0):
     _check(lib().sph_step(ctx, ctypes.byref(parts), float(dt), ctypes.byref(used),
                           ctypes.byref(cons)), ctx)
     return float(used.value), _cons_dict(cons)
+
+
+def sph_steps(ctx, parts: sph_particles, n_steps: int, dt: float = 0.0, allow=()):
+    last = ctypes.c_double(0)
+    cons = sph_conserved()
+    _check(lib().sph_steps(ctx, ctypes.byref(parts), int(n_steps), float(dt), ctypes.byref(last),
+                           ctypes.byref(cons)), ctx, allow)
+    return float(last.value), _cons_dict(cons)
 
 
 def sph_step_host(ctx, parts: sph_particles, dt: float = 0.0):
@@ -255,12 +267,17 @@ class Particles:
 class Context:
     """Owns an sph_ctx; methods mirror the C entry points."""
 
-    def __init__(self, n: int, device: int = 0, stream=None, **overrides):
+    def __init__(self, n: int, device: int = 0, stream=None, box_offsets=None, **overrides):
         import torch
         self.params = sph_default_params()
         self.params.n = int(n)
         for k, v in overrides.items():
             setattr(self.params, k, v)
+        self._offs = None
+        if box_offsets is not None and len(box_offsets) > 2:
+            self._offs = (ctypes.c_int64 * len(box_offsets))(*[int(v) for v in box_offsets])
+            self.params.n_boxes = len(box_offsets) - 1
+            self.params.box_offsets = ctypes.cast(self._offs, ctypes.c_void_p)
         if stream is None:
             stream = torch.cuda.current_stream(device).cuda_stream
         self.stream = stream
@@ -278,6 +295,9 @@ class Context:
 
     def step(self, parts: Particles, dt: float = 0.0):
         return sph_step(self.h, parts.struct(), dt)
+
+    def steps(self, parts: Particles, n_steps: int, dt: float = 0.0, allow=()):
+        return sph_steps(self.h, parts.struct(), n_steps, dt, allow)
 
     def step_host(self, parts: Particles, dt: float = 0.0):
         return sph_step_host(self.h, parts.struct(), dt)

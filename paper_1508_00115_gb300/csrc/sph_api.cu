@@ -124,6 +124,10 @@ static int check_params(const sph_params *p, std::string &why)
     else if (p->max_h_iter < 1) why = "max_h_iter must be >= 1";
     else if (p->kernel != 0) why = "kernel must be 0 (cubic spline)";
     else if (p->tile_width != 0 && p->tile_width != 16 && p->tile_width != 32) why = "tile_width must be 0, 16 or 32";
+    else if (p->n_boxes < 0) why = "n_boxes must be >= 0";
+    else if (p->n_boxes > 1 && !p->box_offsets) why = "box_offsets required for n_boxes > 1";
+    else if (p->n_boxes > 1 && (p->box_offsets[0] != 0 || p->box_offsets[p->n_boxes] != p->n)) why = "box_offsets must run from 0 to n";
+    else if (p->n_boxes > 1 && !std::is_sorted(p->box_offsets, p->box_offsets + p->n_boxes + 1)) why = "box_offsets must be non-decreasing";
     else return SPH_OK;
     return SPH_ERR_INVALID_ARG;
 }
@@ -242,7 +246,7 @@ static int do_force(sph_ctx *ctx, sph_particles *parts)
 {
     if (!ctx->density_valid) return fail(ctx, SPH_ERR_STATE, "sph_force needs sph_density on the current state");
     if (ctx->n > 0) {
-        int rc = device_max_h(ctx, parts->h);
+        int rc = box_max_h(ctx, parts->h);  // reach of every box for r < max(h_i, h_j)
         if (rc) return rc;
         rc = run_force_pass(ctx, parts);
         if (rc) return rc;
@@ -273,36 +277,159 @@ static int hydro(sph_ctx *ctx, sph_particles *parts)
 static int do_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_used, sph_conserved *out)
 {
     int rc;
-    ctx->pred_half = 0.0;
+    ctx->predict = false;
     if (!ctx->hydro_valid) {
         rc = hydro(ctx, parts);
         if (rc) return rc;
     }
-    if (!(dt > 0)) {
-        rc = cfl_dt(ctx, parts, &dt);
+    if (dt > 0) {
+        rc = set_dt(ctx, dt);
+        if (rc) return rc;
+    } else {
+        rc = cfl_dt(ctx, parts, &dt);  // also leaves dt in *d_dt
         if (rc) return rc;
         if (!isfinite(dt)) return fail(ctx, SPH_ERR_INVALID_ARG, "no signal velocity: pass an explicit dt");
     }
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_FLOORS, 0, sizeof(unsigned long long), ctx->stream));
-    const double half = 0.5 * dt;
-    rc = kick(ctx, parts, half);
+    rc = kick(ctx, parts);
     if (rc) return rc;
-    rc = drift(ctx, parts, dt);
+    rc = drift(ctx, parts);
     if (rc) return rc;
     // the hydro pass sees v and u predicted to the end of the step (vel4 / upred)
-    ctx->pred_half = half;
+    ctx->predict = true;
     rc = hydro(ctx, parts);
-    ctx->pred_half = 0.0;
+    ctx->predict = false;
     if (rc) return rc;
-    rc = kick(ctx, parts, half);
+    rc = kick(ctx, parts);
     if (rc) return rc;
     if (dt_used) *dt_used = dt;
     if (out) {
-        rc = conserved(ctx, parts, out);
+        rc = conserved_device(ctx, parts);
+        if (rc) return rc;
+        rc = conserved_read(ctx, out);
         if (rc) return rc;
         rc = cfl_dt(ctx, parts, &out->dt_next);
         if (rc) return rc;
     }
+    return SPH_OK;
+}
+
+// --------------------------------------------------------- graph-captured steps
+
+// flags of one step, ORed into C_GFLAGS: 1 = unconverged h, 2 = h beyond the cells
+__global__ void k_step_flags(unsigned long long *c)
+{
+    unsigned long long f = 0;
+    if (c[C_UNCONV]) f |= 1ull;
+    if (c[C_HFLAG]) f |= 2ull;
+    c[C_GFLAGS] |= f;
+}
+
+// One KDK step with no host synchronisation (the plan of the cell grids is fixed).
+static int graph_step(sph_ctx *ctx, sph_particles *parts, double dt, int passes)
+{
+    int rc = dt > 0 ? set_dt(ctx, dt) : cfl_dt_device(ctx, parts);
+    if (rc) return rc;
+    rc = kick(ctx, parts);
+    if (rc) return rc;
+    rc = drift(ctx, parts);
+    if (rc) return rc;
+    ctx->predict = true;
+    rc = build_planned(ctx, parts);
+    if (rc) return rc;
+    const int n = (int)ctx->n;
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, n, ctx->stream));
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_UNCONV, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    for (int p = 0; p < passes; ++p) {
+        if (p > 0) {
+            rc = compact_active_tiles(ctx);
+            if (rc) return rc;
+            SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_UNCONV, 0, sizeof(unsigned long long), ctx->stream));
+        }
+        rc = run_density_pass(ctx, parts, p == passes - 1, p > 0);
+        if (rc) return rc;
+    }
+    k_step_flags<<<1, 1, 0, ctx->stream>>>(ctx->counters);
+    SPH_LAUNCH(ctx, "step flags");
+    rc = sync_h(ctx, parts);
+    if (rc) return rc;
+    rc = box_max_h(ctx, parts->h);
+    if (rc) return rc;
+    rc = run_force_pass(ctx, parts);
+    if (rc) return rc;
+    ctx->predict = false;
+    rc = kick(ctx, parts);
+    if (rc) return rc;
+    return conserved_device(ctx, parts);
+}
+
+static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, double *dt_last,
+                    sph_conserved *out)
+{
+    int rc;
+    ctx->predict = false;
+    if (n_steps <= 0) return SPH_OK;
+    if (!ctx->hydro_valid) {
+        rc = hydro(ctx, parts);
+        if (rc) return rc;
+    }
+    if (!(dt > 0)) {  // a CFL step must exist before the run starts
+        double d0 = 0;
+        rc = cfl_dt(ctx, parts, &d0);
+        if (rc) return rc;
+        if (!isfinite(d0)) return fail(ctx, SPH_ERR_INVALID_ARG, "no signal velocity: pass an explicit dt");
+    }
+    rc = plan_cells(ctx, parts);  // fixed for the whole run
+    if (rc) return rc;
+    const int passes = std::max(1, std::min(ctx->p.max_h_iter, 6));
+    // capture one step; the timing flag is suspended (events are not capturable here)
+    const uint32_t flags = ctx->p.flags;
+    ctx->p.flags &= ~SPH_FLAG_TIMING;
+    SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    SPH_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t launches0 = ctx->st.kernel_launches;
+    rc = graph_step(ctx, parts, dt, passes);
+    const int64_t per_step = ctx->st.kernel_launches - launches0;
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    ctx->p.flags = flags;
+    ctx->predict = false;
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph capture");
+    if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+    ctx->step_exec = nullptr;
+    ce = cudaGraphInstantiate(&ctx->step_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph instantiate");
+    ctx->st.kernel_launches = launches0;  // capture launched nothing
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_FLOORS, 0, sizeof(unsigned long long), ctx->stream));
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_GFLAGS, 0, sizeof(unsigned long long), ctx->stream));
+    for (int k = 0; k < n_steps; ++k) SPH_CUDA(ctx, cudaGraphLaunch(ctx->step_exec, ctx->stream));
+    ctx->st.kernel_launches += per_step * n_steps;
+    ctx->st.density_passes += (int64_t)passes * n_steps;
+    ctx->st.force_passes += n_steps;
+    ctx->st.graph_steps += n_steps;
+    ctx->hydro_valid = true;
+    ctx->density_valid = true;
+    ctx->built = true;
+    sph_conserved tmp;
+    rc = conserved_read(ctx, out ? out : &tmp);
+    if (rc) return rc;
+    SPH_CUDA(ctx, cudaMemcpyAsync(ctx->h_dt, ctx->d_dt, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (dt_last) *dt_last = *ctx->h_dt;
+    if (out) {
+        double nd = 0;
+        rc = cfl_dt(ctx, parts, &nd);
+        if (rc) return rc;
+        out->dt_next = nd;
+    }
+    const unsigned long long gf = ctx->h_counters[C_GFLAGS];
+    if (gf & 2ull) return fail(ctx, SPH_ERR_H_EXCEEDS_CELL, "some h grew beyond twice the planned cell side");
+    if (gf & 1ull) return fail(ctx, SPH_ERR_NOT_CONVERGED, "smoothing lengths not converged in a captured step");
     return SPH_OK;
 }
 
@@ -344,6 +471,10 @@ int sph_init(sph_ctx **out, const sph_params *p, int device, void *cuda_stream)
     c->stream = (cudaStream_t)cuda_stream;
     c->n = p->n;
     c->tile_w = p->tile_width == 32 ? 32 : 16;
+    c->n_boxes = p->n_boxes > 1 ? p->n_boxes : 1;
+    if (p->n_boxes > 1) c->box_off.assign(p->box_offsets, p->box_offsets + p->n_boxes + 1);
+    else c->box_off = {0, p->n};
+    c->p.box_offsets = nullptr;  // the caller's array need not outlive sph_init
     int rc = SPH_OK;
     auto bail = [&](int code) {
         sph_destroy(c);
@@ -358,7 +489,17 @@ int sph_init(sph_ctx **out, const sph_params *p, int device, void *cuda_stream)
         cudaMallocHost(&c->h_red, 8 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->scan_aux, kScanAuxCap * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&c->n_tiles, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&c->n_act_tiles, sizeof(int)) != cudaSuccess)
+        cudaMalloc(&c->n_act_tiles, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->d_dt, sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->h_dt, sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_boxes, sizeof(BoxDev) * c->n_boxes) != cudaSuccess ||
+        cudaMallocHost(&c->h_boxes, sizeof(BoxDev) * c->n_boxes) != cudaSuccess ||
+        cudaMalloc(&c->d_box_hmax, sizeof(float) * c->n_boxes) != cudaSuccess ||
+        cudaMallocHost(&c->h_box_hmax, sizeof(float) * c->n_boxes) != cudaSuccess ||
+        cudaMalloc(&c->d_box_off, sizeof(int64_t) * (c->n_boxes + 1)) != cudaSuccess)
+        return bail(SPH_ERR_CUDA);
+    if (cudaMemcpy(c->d_box_off, c->box_off.data(), sizeof(int64_t) * (c->n_boxes + 1), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
         return bail(SPH_ERR_CUDA);
     if (cudaMemsetAsync(c->counters, 0, C_NCOUNTERS * sizeof(unsigned long long), c->stream) != cudaSuccess)
         return bail(SPH_ERR_CUDA);
@@ -372,6 +513,9 @@ int sph_set_n(sph_ctx *ctx, int64_t n)
 {
     if (!ctx) return SPH_ERR_INVALID_ARG;
     if (n < 0 || n >= (1ll << 31)) return fail(ctx, SPH_ERR_INVALID_ARG, "n must be in [0, 2^31)");
+    if (ctx->n_boxes > 1) return fail(ctx, SPH_ERR_STATE, "sph_set_n applies to single-box contexts");
+    ctx->box_off = {0, n};
+    SPH_CUDA(ctx, cudaMemcpy(ctx->d_box_off, ctx->box_off.data(), sizeof(int64_t) * 2, cudaMemcpyHostToDevice));
     if (n > ctx->cap) {
         int rc = alloc_particles(ctx, n);
         if (rc) return rc;
@@ -387,7 +531,7 @@ int sph_build_cells(sph_ctx *ctx, sph_particles *parts)
 {
     if (!ctx) return SPH_ERR_INVALID_ARG;
     if (!parts || (ctx->n > 0 && !parts_ok(parts))) return fail(ctx, SPH_ERR_INVALID_ARG, "null particle array");
-    ctx->pred_half = 0.0;
+    ctx->predict = false;
     return do_build(ctx, parts);
 }
 
@@ -411,6 +555,15 @@ int sph_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_used, sph
     if (!parts || (ctx->n > 0 && !parts_ok(parts))) return fail(ctx, SPH_ERR_INVALID_ARG, "null particle array");
     if (!isfinite(dt)) return fail(ctx, SPH_ERR_INVALID_ARG, "dt must be finite");
     return do_step(ctx, parts, dt, dt_used, out);
+}
+
+int sph_steps(sph_ctx *ctx, sph_particles *parts, int32_t n_steps, double dt, double *dt_last, sph_conserved *out)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!parts || (ctx->n > 0 && !parts_ok(parts))) return fail(ctx, SPH_ERR_INVALID_ARG, "null particle array");
+    if (!isfinite(dt)) return fail(ctx, SPH_ERR_INVALID_ARG, "dt must be finite");
+    if (n_steps < 0) return fail(ctx, SPH_ERR_INVALID_ARG, "n_steps must be >= 0");
+    return do_steps(ctx, parts, n_steps, dt, dt_last, out);
 }
 
 int sph_step_host(sph_ctx *ctx, sph_particles *hp, double dt, double *dt_used, sph_conserved *out)
@@ -563,6 +716,14 @@ void sph_destroy(sph_ctx *ctx)
     cudaFree(ctx->scan_aux);
     cudaFree(ctx->n_tiles);
     cudaFree(ctx->n_act_tiles);
+    cudaFree(ctx->d_dt);
+    cudaFreeHost(ctx->h_dt);
+    cudaFree(ctx->d_boxes);
+    cudaFreeHost(ctx->h_boxes);
+    cudaFree(ctx->d_box_hmax);
+    cudaFreeHost(ctx->h_box_hmax);
+    cudaFree(ctx->d_box_off);
+    if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
     cudaFree(ctx->mirror_block);
     for (Timer &t : ctx->timers) {
         cudaEventDestroy(t.a);

@@ -226,11 +226,6 @@ static int radix_sort(sph_ctx *ctx, int n, int key_bits)
 
 // -------------------------------------------------------- wrap, key, gather
 
-struct GridDev {
-    int nc;
-    double box, s, L64;
-};
-
 // Wrap into [0, box): positions already inside (the common case) are returned
 // unchanged without the FP64 division; others are shifted by box*floor(v/box) and
 // corrected by one box if rounding left them just outside.
@@ -253,20 +248,83 @@ __device__ __forceinline__ int cell_of(double v, double s, int nc)
     return c < 0 ? 0 : (c > nc - 1 ? nc - 1 : c);
 }
 
-__global__ void k_wrap_key(double *x, double *y, double *z, int n, GridDev g, uint32_t *__restrict__ keys)
+// box owning particle slot p / global cell c (boxes are contiguous in both)
+__device__ __forceinline__ int box_of_slot(int p, const BoxDev *__restrict__ bx, int nb)
+{
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bx[mid].p_begin <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int box_of_cell(int c, const BoxDev *__restrict__ bx, int nb)
+{
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bx[mid].cell_off <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// max h of every box (one block per box); h must be finite and > 0 (NaN and
+// negative values surface as NaN bits, which order above +inf)
+__global__ void k_box_max_h(const float *__restrict__ h, const int64_t *__restrict__ off, unsigned *__restrict__ out)
+{
+    const int b = blockIdx.x;
+    const int64_t lo = off[b], hi = off[b + 1];
+    unsigned m = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        unsigned v = __float_as_uint(h[i]);
+        if ((int)v < 0) v = 0x7fc00000u;
+        m = max(m, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+    __shared__ unsigned sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned r = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = max(r, sh[w]);
+        out[b] = r;
+    }
+}
+
+int box_max_h(sph_ctx *ctx, const float *h)
+{
+    if (ctx->n <= 0) return SPH_OK;
+    k_box_max_h<<<ctx->n_boxes, 256, 0, ctx->stream>>>(h, ctx->d_box_off, (unsigned *)ctx->d_box_hmax);
+    SPH_LAUNCH(ctx, "box max h");
+    return SPH_OK;
+}
+
+struct WrapArgs {
+    double *x, *y, *z;
+    int n, nb;
+    double box;
+    const BoxDev *bx;
+    uint32_t *keys;
+};
+
+__global__ void k_wrap_key(WrapArgs a)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double a = wrap64(x[i], g.box), b = wrap64(y[i], g.box), c = wrap64(z[i], g.box);
-    x[i] = a;
-    y[i] = b;
-    z[i] = c;
-    int ix = cell_of(a, g.s, g.nc), iy = cell_of(b, g.s, g.nc), iz = cell_of(c, g.s, g.nc);
+    if (i >= a.n) return;
+    const BoxDev g = a.bx[a.nb == 1 ? 0 : box_of_slot(i, a.bx, a.nb)];
+    double x = wrap64(a.x[i], a.box), y = wrap64(a.y[i], a.box), z = wrap64(a.z[i], a.box);
+    a.x[i] = x;
+    a.y[i] = y;
+    a.z[i] = z;
+    int ix = cell_of(x, g.s, g.nc), iy = cell_of(y, g.s, g.nc), iz = cell_of(z, g.s, g.nc);
     // key = cell * 8 + octant: inside a cell particles are grouped by octant (z
     // slowest), so the tiles of a cell split in two are each about half a cell
-    const unsigned oct = (a >= centre64(ix, g.L64) ? 1u : 0u) | (b >= centre64(iy, g.L64) ? 2u : 0u) |
-                         (c >= centre64(iz, g.L64) ? 4u : 0u);
-    keys[i] = ((uint32_t)((iz * g.nc + iy) * g.nc + ix) << 3) | oct;
+    const unsigned oct = (x >= centre64(ix, g.L64) ? 1u : 0u) | (y >= centre64(iy, g.L64) ? 2u : 0u) |
+                         (z >= centre64(iz, g.L64) ? 4u : 0u);
+    a.keys[i] = ((uint32_t)(g.cell_off + (iz * g.nc + iy) * g.nc + ix) << 3) | oct;
 }
 
 struct GatherArgs {
@@ -280,9 +338,9 @@ struct GatherArgs {
     int ids_valid;
     float4 *pos4, *vel4;
     float *upred;
-    double pred_half;
-    int n;
-    GridDev g;
+    const double *d_dt;  // non-null inside a step: predict v, u by d_dt/2
+    int n, nb;
+    const BoxDev *bx;
 };
 
 __global__ void k_gather(GatherArgs a)
@@ -295,16 +353,22 @@ __global__ void k_gather(GatherArgs a)
     double vx = P.vx[src], vy = P.vy[src], vz = P.vz[src];
     float m = P.m[src], u = P.u[src], h = P.h[src];
     float ax = P.ax[src], ay = P.ay[src], az = P.az[src], du = P.dudt[src], vs = P.vsig[src];
-    uint32_t key = a.skeys[p] >> 3;
-    int nc = a.g.nc;
-    int ix = key % nc, iy = (key / nc) % nc, iz = key / (nc * nc);
-    double cx = centre64(ix, a.g.L64), cy = centre64(iy, a.g.L64), cz = centre64(iz, a.g.L64);
+    const BoxDev g = a.bx[a.nb == 1 ? 0 : box_of_slot(p, a.bx, a.nb)];
+    const int cell = (int)(a.skeys[p] >> 3) - g.cell_off;
+    const int nc = g.nc;
+    const int ix = cell % nc, iy = (cell / nc) % nc, iz = cell / (nc * nc);
+    const double cx = centre64(ix, g.L64), cy = centre64(iy, g.L64), cz = centre64(iz, g.L64);
     a.pos4[p] = make_float4((float)(x - cx), (float)(y - cy), (float)(z - cz), h);
-    double ph = a.pred_half;
-    a.vel4[p] = make_float4((float)(vx + (double)ax * ph), (float)(vy + (double)ay * ph),
-                            (float)(vz + (double)az * ph), m);
-    double up = (double)u + (double)du * ph;
-    a.upred[p] = (float)(up > 0.0 ? up : 0.0);
+    if (a.d_dt) {
+        const double ph = 0.5 * *a.d_dt;
+        a.vel4[p] = make_float4((float)(vx + (double)ax * ph), (float)(vy + (double)ay * ph),
+                                (float)(vz + (double)az * ph), m);
+        const double up = (double)u + (double)du * ph;
+        a.upred[p] = (float)(up > 0.0 ? up : 0.0);
+    } else {
+        a.vel4[p] = make_float4((float)vx, (float)vy, (float)vz, m);
+        a.upred[p] = u;
+    }
     int64_t c = a.cap;
     a.s64[p] = x;
     a.s64[c + p] = y;
@@ -345,7 +409,7 @@ __global__ void k_copy_back(sph_particles P, const double *__restrict__ s64, con
     P.vsig[p] = s32[7 * c + p];
 }
 
-// cell_start[c] = first slot with key >= c (lower bound), c in [0, n_cells]
+// cell_start[c] = first slot with cell >= c (lower bound), c in [0, n_cells]
 __global__ void k_cell_start(const uint32_t *__restrict__ skeys, int n, int64_t ncells, int *__restrict__ cs)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -367,16 +431,18 @@ __global__ void k_cell_tiles(const int *__restrict__ cs, int64_t ncells, int tw,
     nt[c] = (uint32_t)((cnt + tw - 1) / tw);
 }
 
+// tile = {global cell, first slot, count, box}
 __global__ void k_tiles_write(const int *__restrict__ cs, int64_t ncells, int tw, const uint32_t *__restrict__ toff,
-                              int4 *__restrict__ tiles, int *__restrict__ n_tiles)
+                              const BoxDev *__restrict__ bx, int nb, int4 *__restrict__ tiles,
+                              int *__restrict__ n_tiles)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncells) return;
     int s = cs[c], cnt = cs[c + 1] - s;
     uint32_t off = toff[c];
+    const int box = nb == 1 ? 0 : box_of_cell((int)c, bx, nb);
     int k = 0;
-    for (int b = 0; b < cnt; b += tw, ++k)
-        tiles[off + k] = make_int4((int)c, s + b, min(tw, cnt - b), 0);
+    for (int b = 0; b < cnt; b += tw, ++k) tiles[off + k] = make_int4((int)c, s + b, min(tw, cnt - b), box);
     if (c == ncells - 1) *n_tiles = (int)(off + k);
 }
 
@@ -415,41 +481,72 @@ static int ensure_cells(sph_ctx *ctx, int64_t ncells)
 
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-int build_cells(sph_ctx *ctx, sph_particles *parts)
+// Plan the cell grid of every box from its largest h (one host read): the cell
+// side is the smallest L = box / nc with L >= cell_factor * max h and nc >= 3 (cells
+// no smaller than the smoothing length, Sec. 3.1), nc capped near (8 n_box)^(1/3).
+int plan_cells(sph_ctx *ctx, sph_particles *parts)
 {
-    const int n = (int)ctx->n;
     const double box = ctx->p.box_size;
-    float hmax = (float)(box / 4.0);  // an empty set gets the coarsest grid
-    int rc = SPH_OK;
-    if (n > 0) rc = reduce_max_h(ctx, parts->h, &hmax);
-    if (rc) return rc;
-    if (!(hmax > 0.f) || !isfinite(hmax))
-        return fail(ctx, SPH_ERR_NAN, "smoothing lengths must be finite and > 0");
-    if ((double)hmax > box / 3.0)
-        return fail(ctx, SPH_ERR_H_EXCEEDS_CELL, "max h exceeds box/3: no periodic grid with >= 3 cells");
-    double hc = (double)hmax * (double)ctx->p.cell_factor;
-    int nc = (int)floor(box / hc);
-    int cap_n = (int)floor(cbrt(8.0 * (double)std::max(n, 1)));
-    nc = std::min(nc, std::min(kMaxNc, std::max(3, cap_n)));
-    if (nc < 3) nc = 3;  // hmax <= box/3 guarantees cells of side box/3 hold the support
+    const int nb = ctx->n_boxes;
+    BoxDev *hb = ctx->h_boxes;
+    if (ctx->n > 0) {
+        int rc = box_max_h(ctx, parts->h);
+        if (rc) return rc;
+        SPH_CUDA(ctx, cudaMemcpyAsync(ctx->h_box_hmax, ctx->d_box_hmax, sizeof(float) * nb, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    int64_t cells = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int64_t np = ctx->box_off[b + 1] - ctx->box_off[b];
+        float hmax = np > 0 ? ctx->h_box_hmax[b] : (float)(box / 4.0);  // empty box: coarsest grid
+        if (!(hmax > 0.f) || !isfinite(hmax)) return fail(ctx, SPH_ERR_NAN, "smoothing lengths must be finite and > 0");
+        if ((double)hmax > box / 3.0)
+            return fail(ctx, SPH_ERR_H_EXCEEDS_CELL, "max h exceeds box/3: no periodic grid with >= 3 cells");
+        int nc = (int)floor(box / ((double)hmax * (double)ctx->p.cell_factor));
+        const int cap_n = (int)floor(cbrt(8.0 * (double)std::max<int64_t>(np, 1)));
+        nc = std::min(nc, std::min(kMaxNc, std::max(3, cap_n)));
+        if (nc < 3) nc = 3;  // hmax <= box/3 guarantees cells of side box/3 hold the support
+        hb[b].p_begin = (int)ctx->box_off[b];
+        hb[b].p_end = (int)ctx->box_off[b + 1];
+        hb[b].cell_off = (int)cells;
+        hb[b].nc = nc;
+        hb[b].L64 = box / nc;
+        hb[b].s = (double)nc / box;
+        hb[b].L32 = (float)hb[b].L64;
+        hb[b].hplan = hmax;
+        cells += (int64_t)nc * nc * nc;
+        if (cells * 8 >= (1ll << 32)) return fail(ctx, SPH_ERR_INVALID_ARG, "too many cells for 32-bit keys");
+    }
+    SPH_CUDA(ctx, cudaMemcpyAsync(ctx->d_boxes, hb, sizeof(BoxDev) * nb, cudaMemcpyHostToDevice, ctx->stream));
     Grid &g = ctx->grid;
-    g.nc = nc;
-    g.n_cells = (int64_t)nc * nc * nc;
-    g.L64 = box / nc;
-    g.L32 = (float)g.L64;
-    g.inv_s = (double)nc / box;
+    g.nc = hb[0].nc;
+    g.n_cells = cells;
+    g.L64 = hb[0].L64;
     int bits = 1;
     while ((1ll << bits) < g.n_cells) ++bits;
-    bits += 3;  // octant within the cell
-    g.key_bits = bits;
-    rc = ensure_cells(ctx, g.n_cells);
+    g.key_bits = bits + 3;  // octant within the cell
+    int rc = ensure_cells(ctx, g.n_cells);
     if (rc) return rc;
+    ctx->planned = true;
+    ctx->st.nc = g.nc;
+    ctx->st.n_cells = g.n_cells;
+    ctx->st.cell_size = g.L64;
+    return SPH_OK;
+}
 
-    GridDev gd{nc, box, g.inv_s, g.L64};
+// Bin, sort and permute with the current plan: no host synchronisation.
+int build_planned(sph_ctx *ctx, sph_particles *parts)
+{
+    if (!ctx->planned) return fail(ctx, SPH_ERR_STATE, "no cell plan");
+    const int n = (int)ctx->n;
+    const Grid &g = ctx->grid;
+    int rc;
     if (n > 0) {
-        k_wrap_key<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(parts->x, parts->y, parts->z, n, gd, ctx->keys);
+        WrapArgs wa{parts->x, parts->y, parts->z, n, ctx->n_boxes, ctx->p.box_size, ctx->d_boxes, ctx->keys};
+        k_wrap_key<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(wa);
         SPH_LAUNCH(ctx, "wrap/key");
-        rc = radix_sort(ctx, n, bits);
+        rc = radix_sort(ctx, n, g.key_bits);
         if (rc) return rc;
         GatherArgs ga;
         ga.P = *parts;
@@ -464,9 +561,10 @@ int build_cells(sph_ctx *ctx, sph_particles *parts)
         ga.pos4 = ctx->pos4;
         ga.vel4 = ctx->vel4;
         ga.upred = ctx->upred;
-        ga.pred_half = ctx->pred_half;
+        ga.d_dt = ctx->predict ? ctx->d_dt : nullptr;
         ga.n = n;
-        ga.g = gd;
+        ga.nb = ctx->n_boxes;
+        ga.bx = ctx->d_boxes;
         k_gather<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(ga);
         SPH_LAUNCH(ctx, "gather");
         k_copy_back<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(*parts, ctx->s64, ctx->s32, ctx->cap, n);
@@ -474,24 +572,27 @@ int build_cells(sph_ctx *ctx, sph_particles *parts)
         std::swap(ctx->ids, ctx->ids_tmp);
         ctx->ids_valid = true;
     }
-    k_cell_start<<<blocks_for(g.n_cells + 1, 256), 256, 0, ctx->stream>>>(ctx->keys, n, g.n_cells,
-                                                                         ctx->cell_start);
+    k_cell_start<<<blocks_for(g.n_cells + 1, 256), 256, 0, ctx->stream>>>(ctx->keys, n, g.n_cells, ctx->cell_start);
     SPH_LAUNCH(ctx, "cell start");
-    k_cell_tiles<<<blocks_for(g.n_cells, 256), 256, 0, ctx->stream>>>(ctx->cell_start, g.n_cells,
-                                                                     ctx->tile_w, ctx->cell_tiles);
+    k_cell_tiles<<<blocks_for(g.n_cells, 256), 256, 0, ctx->stream>>>(ctx->cell_start, g.n_cells, ctx->tile_w,
+                                                                     ctx->cell_tiles);
     SPH_LAUNCH(ctx, "cell tiles");
     rc = exclusive_scan_u32(ctx, ctx->cell_tiles, ctx->cell_tiles, g.n_cells);
     if (rc) return rc;
-    k_tiles_write<<<blocks_for(g.n_cells, 256), 256, 0, ctx->stream>>>(ctx->cell_start, g.n_cells,
-                                                                      ctx->tile_w, ctx->cell_tiles,
-                                                                      ctx->tiles, ctx->n_tiles);
+    k_tiles_write<<<blocks_for(g.n_cells, 256), 256, 0, ctx->stream>>>(
+        ctx->cell_start, g.n_cells, ctx->tile_w, ctx->cell_tiles, ctx->d_boxes, ctx->n_boxes, ctx->tiles,
+        ctx->n_tiles);
     SPH_LAUNCH(ctx, "tiles");
     ctx->built = true;
     ctx->density_valid = false;
-    ctx->st.nc = nc;
-    ctx->st.n_cells = g.n_cells;
-    ctx->st.cell_size = g.L64;
     return SPH_OK;
+}
+
+int build_cells(sph_ctx *ctx, sph_particles *parts)
+{
+    int rc = plan_cells(ctx, parts);
+    if (rc) return rc;
+    return build_planned(ctx, parts);
 }
 
 }  // namespace sph

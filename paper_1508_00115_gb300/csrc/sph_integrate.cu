@@ -1,8 +1,9 @@
 // sph_integrate.cu -- marching particles forward in time (Theuns et al. 2015,
 // Sec. 2: "positions by velocities, velocities by accelerations") and the O(N)
-// reductions around the pair passes: max h (cell size), CFL time step, and the
-// conserved quantities.  Positions, velocities, kicks, drifts and the global sums
-// are FP64; the sums use a fixed grid and tree order, so they are deterministic.
+// reductions around the pair passes: CFL time step and the conserved quantities.
+// Positions, velocities, kicks, drifts and the global sums are FP64; the sums use a
+// fixed grid and tree order, so they are deterministic.  The step's dt lives on the
+// device (ctx->d_dt), so a whole step can be replayed from a CUDA graph.
 #include <math.h>
 
 #include "sph_internal.cuh"
@@ -12,45 +13,20 @@ namespace sph {
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocks = 304;  // fixed grid (2 x 152 SMs) for deterministic sums
 
-__global__ void k_max_h(const float *__restrict__ h, int n, unsigned *__restrict__ out)
-{
-    unsigned m = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        // positive floats order like their bit patterns; NaN sorts above +inf
-        unsigned b = __float_as_uint(h[i]);
-        if ((int)b < 0) b = 0x7fc00000u;  // negative values are invalid: report as NaN
-        m = max(m, b);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
-}
+__global__ void k_set_dt(double *d_dt, double dt) { *d_dt = dt; }
 
-int device_max_h(sph_ctx *ctx, const float *h)
+int set_dt(sph_ctx *ctx, double dt)
 {
-    SPH_CUDA(ctx, cudaMemsetAsync(ctx->d_scalars, 0, sizeof(float), ctx->stream));
-    if (ctx->n > 0) {
-        k_max_h<<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(h, (int)ctx->n, (unsigned *)ctx->d_scalars);
-        SPH_LAUNCH(ctx, "max h");
-    }
+    k_set_dt<<<1, 1, 0, ctx->stream>>>(ctx->d_dt, dt);
+    SPH_LAUNCH(ctx, "set dt");
     return SPH_OK;
 }
 
-int reduce_max_h(sph_ctx *ctx, const float *h, float *h_out_host)
-{
-    int rc = device_max_h(ctx, h);
-    if (rc) return rc;
-    SPH_CUDA(ctx, cudaMemcpyAsync(ctx->h_scalars, ctx->d_scalars, sizeof(float), cudaMemcpyDeviceToHost,
-                                  ctx->stream));
-    SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    *h_out_host = ctx->h_scalars[0];
-    return SPH_OK;
-}
-
-// v += a * half_dt (FP64); u <- max(u + dudt * half_dt, 0), counting floors
-__global__ void k_kick(sph_particles P, int n, double half_dt, unsigned long long *floors)
+// v += a * dt/2 (FP64); u <- max(u + dudt * dt/2, 0), counting floors
+__global__ void k_kick(sph_particles P, int n, const double *__restrict__ d_dt, unsigned long long *floors)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double half_dt = 0.5 * *d_dt;
     bool fl = false;
     if (i < n) {
         P.vx[i] += (double)P.ax[i] * half_dt;
@@ -64,35 +40,36 @@ __global__ void k_kick(sph_particles P, int n, double half_dt, unsigned long lon
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(floors, (unsigned long long)__popc(b));
 }
 
-int kick(sph_ctx *ctx, sph_particles *parts, double half_dt)
+int kick(sph_ctx *ctx, sph_particles *parts)
 {
     int n = (int)ctx->n;
     if (n <= 0) return SPH_OK;
-    k_kick<<<(n + 255) / 256, 256, 0, ctx->stream>>>(*parts, n, half_dt, ctx->counters + C_FLOORS);
+    k_kick<<<(n + 255) / 256, 256, 0, ctx->stream>>>(*parts, n, ctx->d_dt, ctx->counters + C_FLOORS);
     SPH_LAUNCH(ctx, "kick");
     return SPH_OK;
 }
 
 // x += v dt (FP64); the periodic wrap follows in the cell build
-__global__ void k_drift(sph_particles P, int n, double dt)
+__global__ void k_drift(sph_particles P, int n, const double *__restrict__ d_dt)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const double dt = *d_dt;
     P.x[i] += P.vx[i] * dt;
     P.y[i] += P.vy[i] * dt;
     P.z[i] += P.vz[i] * dt;
 }
 
-int drift(sph_ctx *ctx, sph_particles *parts, double dt)
+int drift(sph_ctx *ctx, sph_particles *parts)
 {
     int n = (int)ctx->n;
     if (n <= 0) return SPH_OK;
-    k_drift<<<(n + 255) / 256, 256, 0, ctx->stream>>>(*parts, n, dt);
+    k_drift<<<(n + 255) / 256, 256, 0, ctx->stream>>>(*parts, n, ctx->d_dt);
     SPH_LAUNCH(ctx, "drift");
     return SPH_OK;
 }
 
-// min_i h_i / vsig_i over vsig_i > 0 (positive floats: order of bit patterns)
+// min_i h_i / vsig_i over vsig_i > 0 (positive floats order like their bit patterns)
 __global__ void k_cfl(const float *__restrict__ h, const float *__restrict__ vsig, int n,
                       unsigned *__restrict__ out)
 {
@@ -106,21 +83,36 @@ __global__ void k_cfl(const float *__restrict__ h, const float *__restrict__ vsi
     if ((threadIdx.x & 31) == 0) atomicMin(out, m);
 }
 
-int cfl_dt(sph_ctx *ctx, sph_particles *parts, double *dt_out)
+__global__ void k_cfl_init(unsigned *out) { *out = 0x7f800000u; }
+
+// dt = cfl * min h/vsig (+inf without signal velocities)
+__global__ void k_cfl_final(const unsigned *__restrict__ m, double cfl, double *__restrict__ d_dt)
 {
-    unsigned init = 0x7f800000u;
-    SPH_CUDA(ctx, cudaMemcpyAsync(ctx->d_scalars + 1, &init, sizeof(unsigned), cudaMemcpyHostToDevice,
-                                  ctx->stream));
+    const float r = __uint_as_float(*m);
+    *d_dt = isfinite(r) ? cfl * (double)r : INFINITY;
+}
+
+int cfl_dt_device(sph_ctx *ctx, sph_particles *parts)
+{
+    unsigned *slot = (unsigned *)(ctx->d_scalars + 1);
+    k_cfl_init<<<1, 1, 0, ctx->stream>>>(slot);
+    SPH_LAUNCH(ctx, "cfl init");
     if (ctx->n > 0) {
-        k_cfl<<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(parts->h, parts->vsig, (int)ctx->n,
-                                                           (unsigned *)(ctx->d_scalars + 1));
+        k_cfl<<<kRedBlocks * 4, kRedThreads, 0, ctx->stream>>>(parts->h, parts->vsig, (int)ctx->n, slot);
         SPH_LAUNCH(ctx, "cfl");
     }
-    SPH_CUDA(ctx, cudaMemcpyAsync(ctx->h_scalars + 1, ctx->d_scalars + 1, sizeof(float),
-                                  cudaMemcpyDeviceToHost, ctx->stream));
+    k_cfl_final<<<1, 1, 0, ctx->stream>>>(slot, (double)ctx->p.cfl, ctx->d_dt);
+    SPH_LAUNCH(ctx, "cfl final");
+    return SPH_OK;
+}
+
+int cfl_dt(sph_ctx *ctx, sph_particles *parts, double *dt_out)
+{
+    int rc = cfl_dt_device(ctx, parts);
+    if (rc) return rc;
+    SPH_CUDA(ctx, cudaMemcpyAsync(ctx->h_dt, ctx->d_dt, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    float r = ctx->h_scalars[1];
-    *dt_out = isfinite(r) ? (double)ctx->p.cfl * (double)r : INFINITY;
+    *dt_out = *ctx->h_dt;
     return SPH_OK;
 }
 
@@ -160,13 +152,18 @@ __global__ void k_conserved_final(const double *part, double *out)
     if (lane == 0) out[k] = s;
 }
 
-int conserved(sph_ctx *ctx, sph_particles *parts, sph_conserved *out)
+int conserved_device(sph_ctx *ctx, sph_particles *parts)
 {
     int n = (int)ctx->n;
     k_conserved_part<<<kRedBlocks, kRedThreads, 0, ctx->stream>>>(*parts, n, ctx->d_red);
     SPH_LAUNCH(ctx, "conserved partials");
     k_conserved_final<<<1, 160, 0, ctx->stream>>>(ctx->d_red, ctx->d_red + 5 * kRedBlocks);
     SPH_LAUNCH(ctx, "conserved final");
+    return SPH_OK;
+}
+
+int conserved_read(sph_ctx *ctx, sph_conserved *out)
+{
     SPH_CUDA(ctx, cudaMemcpyAsync(ctx->h_red, ctx->d_red + 5 * kRedBlocks, 5 * sizeof(double),
                                   cudaMemcpyDeviceToHost, ctx->stream));
     SPH_CUDA(ctx, cudaMemcpyAsync(ctx->h_counters, ctx->counters, C_NCOUNTERS * sizeof(unsigned long long),

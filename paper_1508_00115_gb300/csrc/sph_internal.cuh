@@ -36,22 +36,33 @@ constexpr float kPruneMargin = 2.44140625e-04f;  // 2^-12
 // device counters (unsigned long long slots)
 enum Counter {
     C_UNCONV = 0,     // unconverged particles after the last density pass
-    C_HFLAG = 1,      // some h outgrew the cell side
+    C_HFLAG = 1,      // some h outgrew twice the planned cell side
     C_DPAIRS = 2,     // density interactions
     C_FPAIRS = 3,     // force interactions
     C_DCAND = 4,      // density candidate tests
     C_FCAND = 5,      // force candidate tests
     C_FLOORS = 6,     // u floors
     C_DTARGETS = 7,   // active density targets
+    C_GFLAGS = 8,     // multi-step run: OR of per-step flags (1: unconverged, 2: h beyond cells)
     C_NCOUNTERS = 16
 };
 
+// Cell grid of one periodic box (every box has side box_size; boxes are batched
+// by concatenating their particle ranges and their cell numberings).
+struct BoxDev {
+    int p_begin, p_end;  // particle slots of the box (cell order keeps boxes contiguous)
+    int cell_off;        // global id of the box's first cell
+    int nc;              // cells per side
+    double L64;          // cell side, box / nc
+    double s;            // nc / box
+    float L32;           // cell side, FP32
+    float hplan;         // max h the grid was planned for
+};
+
 struct Grid {
-    int nc = 0;
-    int64_t n_cells = 0;
-    double L64 = 0;   // cell side (box / nc)
-    float L32 = 0;    // cell side, FP32
-    double inv_s = 0; // nc / box
+    int nc = 0;          // box 0 (statistics)
+    int64_t n_cells = 0; // all boxes
+    double L64 = 0;      // box 0
     int key_bits = 0;
 };
 
@@ -82,6 +93,15 @@ struct sph_ctx {
     // permutation scratch (gather targets before the copy back)
     double *s64 = nullptr;  // 6 * cap
     float *s32 = nullptr;   // 8 * cap
+    // boxes and their cell grids
+    int n_boxes = 1;
+    std::vector<int64_t> box_off;     // host, n_boxes + 1
+    int64_t *d_box_off = nullptr;     // device copy
+    sph::BoxDev *d_boxes = nullptr;   // device, n_boxes
+    sph::BoxDev *h_boxes = nullptr;   // pinned host mirror
+    float *d_box_hmax = nullptr;      // device, n_boxes
+    float *h_box_hmax = nullptr;      // pinned
+    bool planned = false;             // d_boxes holds a grid plan
     // cells
     sph::Grid grid;
     int tile_w = 16;             // targets per tile: 16 (two tiles per warp) or 32
@@ -111,7 +131,13 @@ struct sph_ctx {
     bool built = false;       // cells match the current positions
     bool density_valid = false;
     bool hydro_valid = false; // a, dudt, vsig match the current state
-    double pred_half = 0.0;   // prediction interval used when gathering vel4/upred
+    bool predict = false;     // gather predicts v, u by half of *d_dt (inside a step)
+    double *d_dt = nullptr;   // device: the step's dt
+    double *h_dt = nullptr;   // pinned
+    // captured multi-step graph
+    cudaGraphExec_t step_exec = nullptr;
+    double graph_dt = 0.0;    // dt mode the graph was captured with (<= 0: CFL)
+    int graph_passes = 0;
 
     // statistics
     sph_stats st{};
@@ -143,18 +169,22 @@ void timer_begin(sph_ctx *ctx, int kind, cudaEvent_t *out_end);
 void timer_end(sph_ctx *ctx, cudaEvent_t end);
 
 // launch wrappers (defined in the .cu files) ---------------------------------
-int build_cells(sph_ctx *ctx, sph_particles *parts);            // sph_cells.cu
+int plan_cells(sph_ctx *ctx, sph_particles *parts);             // sph_cells.cu (host read)
+int build_cells(sph_ctx *ctx, sph_particles *parts);            // sph_cells.cu (plan + build)
+int build_planned(sph_ctx *ctx, sph_particles *parts);          // sph_cells.cu (no host read)
+int box_max_h(sph_ctx *ctx, const float *h);                    // sph_cells.cu
 int cell_keys_out(sph_ctx *ctx, int32_t *dev_keys);             // sph_cells.cu
 int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool active_list);  // sph_pairs.cu
 int compact_active_tiles(sph_ctx *ctx);                                    // sph_pairs.cu
 int run_force_pass(sph_ctx *ctx, sph_particles *parts);                    // sph_pairs.cu
 int sync_h(sph_ctx *ctx, sph_particles *parts);                            // sph_pairs.cu
-int reduce_max_h(sph_ctx *ctx, const float *h, float *h_out_host);         // sph_integrate.cu
-int kick(sph_ctx *ctx, sph_particles *parts, double half_dt);              // sph_integrate.cu
-int drift(sph_ctx *ctx, sph_particles *parts, double dt);                  // sph_integrate.cu
-int device_max_h(sph_ctx *ctx, const float *h);                             // sph_integrate.cu
+int kick(sph_ctx *ctx, sph_particles *parts);    // by *d_dt / 2           // sph_integrate.cu
+int drift(sph_ctx *ctx, sph_particles *parts);   // by *d_dt               // sph_integrate.cu
+int set_dt(sph_ctx *ctx, double dt);             // *d_dt = dt (kernel)    // sph_integrate.cu
+int cfl_dt_device(sph_ctx *ctx, sph_particles *parts);  // *d_dt = CFL    // sph_integrate.cu
+int conserved_device(sph_ctx *ctx, sph_particles *parts);                  // sph_integrate.cu
+int conserved_read(sph_ctx *ctx, sph_conserved *out);                      // sph_integrate.cu
 int cfl_dt(sph_ctx *ctx, sph_particles *parts, double *dt_out);            // sph_integrate.cu
-int conserved(sph_ctx *ctx, sph_particles *parts, sph_conserved *out);     // sph_integrate.cu
 int exclusive_scan_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n);  // sph_cells.cu
 
 // FP32 pair math ---------------------------------------------------------------

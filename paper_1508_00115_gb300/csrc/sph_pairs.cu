@@ -63,10 +63,9 @@ struct DensityArgs {
     float4 *thermo4;
     uint64_t *ngb_hash;
     unsigned long long *counters;
-    int nc;
-    float L32;
+    const BoxDev *__restrict__ boxes;
     double box;
-    float n_ngb_target, h_tol, gamma, h_cell_limit;
+    float n_ngb_target, h_tol, gamma;
     int use_balsara;
     int last_pass;
 };
@@ -142,14 +141,12 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int ntiles = *a.n_tiles;
     const int ngroups = (ntiles + TPW - 1) / TPW;
-    const int nc = a.nc;
-    const float L = a.L32;
     const float inf = __int_as_float(0x7f800000);
 
     for (int grp = gw; grp < ngroups; grp += nw) {
         const int t = grp * TPW + sub;
         const int4 tile = t < ntiles ? a.tiles[t] : make_int4(0, 0, 0, 0);
-        const int ca = tile.x, i = tile.y + tl;
+        const int i = tile.y + tl;
         const bool valid = tl < tile.z;
         const bool act = valid && a.active[i];
         const unsigned amask = __ballot_sync(kFull, act);
@@ -167,6 +164,11 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
         const float loy = tile_min<TW>(act ? pi.y : inf), hiy = tile_max<TW>(act ? pi.y : -inf);
         const float loz = tile_min<TW>(act ? pi.z : inf), hiz = tile_max<TW>(act ? pi.z : -inf);
         const float hmax = tile_max<TW>(hi);
+        const BoxDev bx = a.boxes[tile.w];
+        const int nc = bx.nc;
+        const float L = bx.L32;
+        // stencil radius (cells) that holds the tile's cutoff; warp-uniform
+        const int R = (int)__reduce_max_sync(kFull, hmax * (1.f + kPruneMargin) > L ? 2u : 1u);
         // grown so that pairs the FP64 band re-decision may accept are never pruned
         const float reach2 = hmax * hmax * (1.f + kPruneMargin) + 2.f * kBandK * hmax * (hmax + L);
         // r^2 below lob: neighbour; above hib: not; in between: decided in FP64.
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
         const float hi2 = act ? hi * hi : -1.f;
         const float lob = hi2 - band, hib = hi2 + band;
         const float hinv = act ? 1.f / hi : 0.f;
+        const int ca = tile.x - bx.cell_off;
         const int ix = ca % nc, iy = (ca / nc) % nc, iz = ca / (nc * nc);
 
         // sums without the kernel normalisation (applied at the end); the pair
@@ -250,17 +253,20 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
         };
 
         // the 27 cell ranges of the tile, fetched at once: lane tl holds cells tl, tl + TW
+        // (radius-2 stencils, for h beyond the planned cell, load ranges one by one)
         int cs0 = 0, ce0 = 0, cs1 = 0, ce1 = 0;
-        if (live) {
+        if (live && R == 1) {
             if (tl < 27) {
-                const int cb = (wrapc(iz + kOrder[tl][2], nc) * nc + wrapc(iy + kOrder[tl][1], nc)) * nc +
+                const int cb = bx.cell_off +
+                               (wrapc(iz + kOrder[tl][2], nc) * nc + wrapc(iy + kOrder[tl][1], nc)) * nc +
                                wrapc(ix + kOrder[tl][0], nc);
                 cs0 = a.cell_start[cb];
                 ce0 = a.cell_start[cb + 1];
             }
             if (tl + TW < 27) {
                 const int o2 = tl + TW;
-                const int cb = (wrapc(iz + kOrder[o2][2], nc) * nc + wrapc(iy + kOrder[o2][1], nc)) * nc +
+                const int cb = bx.cell_off +
+                               (wrapc(iz + kOrder[o2][2], nc) * nc + wrapc(iy + kOrder[o2][1], nc)) * nc +
                                wrapc(ix + kOrder[o2][0], nc);
                 cs1 = a.cell_start[cb];
                 ce1 = a.cell_start[cb + 1];
@@ -268,18 +274,36 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
         }
         // stage chunk after chunk; one flush site (keeps the kernel small)
         int o = -1, ch = 0, nchunk = 0, bs = 0, be = 0;
+        const int ncell = R == 1 ? 27 : 125;
         float shx = 0.f, shy = 0.f, shz = 0.f;
         for (;;) {
-            while (ch >= nchunk && o < 26) {
+            while (ch >= nchunk && o < ncell - 1) {
                 ++o;
                 ch = 0;
-                const int src = o < TW ? o : o - TW;
-                bs = __shfl_sync(kFull, o < TW ? cs0 : cs1, src, TW);
-                be = __shfl_sync(kFull, o < TW ? ce0 : ce1, src, TW);
+                int ox, oy, oz;
+                if (R == 1) {
+                    const int src = o < TW ? o : o - TW;
+                    bs = __shfl_sync(kFull, o < TW ? cs0 : cs1, src, TW);
+                    be = __shfl_sync(kFull, o < TW ? ce0 : ce1, src, TW);
+                    ox = kOrder[o][0];
+                    oy = kOrder[o][1];
+                    oz = kOrder[o][2];
+                } else {
+                    ox = o % 5 - 2;
+                    oy = (o / 5) % 5 - 2;
+                    oz = o / 25 - 2;
+                    bs = be = 0;
+                    if (live) {
+                        const int cb = bx.cell_off + (wrapc(iz + oz, nc) * nc + wrapc(iy + oy, nc)) * nc +
+                                       wrapc(ix + ox, nc);
+                        bs = a.cell_start[cb];
+                        be = a.cell_start[cb + 1];
+                    }
+                }
                 nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
-                shx = (float)kOrder[o][0] * L;
-                shy = (float)kOrder[o][1] * L;
-                shz = (float)kOrder[o][2] * L;
+                shx = (float)ox * L;
+                shy = (float)oy * L;
+                shz = (float)oz * L;
             }
             const bool more = ch < nchunk;  // warp-uniform
             if (more) {
@@ -337,7 +361,8 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
             hn = fminf(fmaxf(hn, 0.5f * hi), 2.f * hi);
             a.h[i] = hn;
             atomicAdd(a.counters + C_UNCONV, 1ull);
-            if (hn > a.h_cell_limit) atomicOr(a.counters + C_HFLAG, 1ull);
+            // beyond the radius-2 stencil of its cell: the grid must be planned again
+            if ((double)hn > 2.0 * bx.L64 * (1.0 - 1e-6)) atomicOr(a.counters + C_HFLAG, 1ull);
             continue;
         }
         if (!conv) atomicAdd(a.counters + C_UNCONV, 1ull);
@@ -376,11 +401,10 @@ struct ForceArgs {
     const double *__restrict__ x;
     const double *__restrict__ y;
     const double *__restrict__ z;
-    const float *__restrict__ hmax_global;
+    const float *__restrict__ box_hmax;
     float *ax, *ay, *az, *dudt, *vsig;
     unsigned long long *counters;
-    int nc;
-    float L32;
+    const BoxDev *__restrict__ boxes;
     double box;
     float alpha;
 };
@@ -405,15 +429,12 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int ntiles = *a.n_tiles;
     const int ngroups = (ntiles + TPW - 1) / TPW;
-    const int nc = a.nc;
-    const float L = a.L32;
-    const float hglob = *a.hmax_global;
     const float inf = __int_as_float(0x7f800000);
 
     for (int grp = gw; grp < ngroups; grp += nw) {
         const int t = grp * TPW + sub;
         const int4 tile = t < ntiles ? a.tiles[t] : make_int4(0, 0, 0, 0);
-        const int ca = tile.x, i = tile.y + tl;
+        const int i = tile.y + tl;
         const bool act = tl < tile.z;
         const unsigned amask = __ballot_sync(kFull, act);
         const bool live = (amask & gmask) != 0;
@@ -429,13 +450,18 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
         const float loy = tile_min<TW>(act ? pi.y : inf), hiy = tile_max<TW>(act ? pi.y : -inf);
         const float loz = tile_min<TW>(act ? pi.z : inf), hiz = tile_max<TW>(act ? pi.z : -inf);
         const float hi = pi.w;
-        const float H = fmaxf(tile_max<TW>(hi), hglob);
+        const BoxDev bx = a.boxes[tile.w];
+        const int nc = bx.nc;
+        const float L = bx.L32;
+        const float H = fmaxf(tile_max<TW>(hi), a.box_hmax[tile.w]);
+        const int R = (int)__reduce_max_sync(kFull, H * (1.f + kPruneMargin) > L ? 2u : 1u);
         const float bandmax = 2.f * kBandK * H * (H + L);
         const float reach2 = H * H * (1.f + kPruneMargin) + bandmax;
         const float hi2 = hi * hi;
         const float hinv = act ? 1.f / hi : 0.f;
         const float hinv4 = hinv * hinv * hinv * hinv;
         const float band_i = kBandK * hi * (hi + L);
+        const int ca = tile.x - bx.cell_off;
         const int ix = ca % nc, iy = (ca / nc) % nc, iz = ca / (nc * nc);
         float sx_ = 0.f, sxc = 0.f, sy_ = 0.f, syc = 0.f, sz_ = 0.f, szc = 0.f, su = 0.f, suc = 0.f;
         float vs = 0.f;
@@ -529,17 +555,20 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
         };
 
         // the 27 cell ranges of the tile, fetched at once: lane tl holds cells tl, tl + TW
+        // (radius-2 stencils, for h beyond the planned cell, load ranges one by one)
         int cs0 = 0, ce0 = 0, cs1 = 0, ce1 = 0;
-        if (live) {
+        if (live && R == 1) {
             if (tl < 27) {
-                const int cb = (wrapc(iz + kOrder[tl][2], nc) * nc + wrapc(iy + kOrder[tl][1], nc)) * nc +
+                const int cb = bx.cell_off +
+                               (wrapc(iz + kOrder[tl][2], nc) * nc + wrapc(iy + kOrder[tl][1], nc)) * nc +
                                wrapc(ix + kOrder[tl][0], nc);
                 cs0 = a.cell_start[cb];
                 ce0 = a.cell_start[cb + 1];
             }
             if (tl + TW < 27) {
                 const int o2 = tl + TW;
-                const int cb = (wrapc(iz + kOrder[o2][2], nc) * nc + wrapc(iy + kOrder[o2][1], nc)) * nc +
+                const int cb = bx.cell_off +
+                               (wrapc(iz + kOrder[o2][2], nc) * nc + wrapc(iy + kOrder[o2][1], nc)) * nc +
                                wrapc(ix + kOrder[o2][0], nc);
                 cs1 = a.cell_start[cb];
                 ce1 = a.cell_start[cb + 1];
@@ -547,18 +576,36 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
         }
         // stage chunk after chunk; one flush site (keeps the kernel small)
         int o = -1, ch = 0, nchunk = 0, bs = 0, be = 0;
+        const int ncell = R == 1 ? 27 : 125;
         float shx = 0.f, shy = 0.f, shz = 0.f;
         for (;;) {
-            while (ch >= nchunk && o < 26) {
+            while (ch >= nchunk && o < ncell - 1) {
                 ++o;
                 ch = 0;
-                const int src = o < TW ? o : o - TW;
-                bs = __shfl_sync(kFull, o < TW ? cs0 : cs1, src, TW);
-                be = __shfl_sync(kFull, o < TW ? ce0 : ce1, src, TW);
+                int ox, oy, oz;
+                if (R == 1) {
+                    const int src = o < TW ? o : o - TW;
+                    bs = __shfl_sync(kFull, o < TW ? cs0 : cs1, src, TW);
+                    be = __shfl_sync(kFull, o < TW ? ce0 : ce1, src, TW);
+                    ox = kOrder[o][0];
+                    oy = kOrder[o][1];
+                    oz = kOrder[o][2];
+                } else {
+                    ox = o % 5 - 2;
+                    oy = (o / 5) % 5 - 2;
+                    oz = o / 25 - 2;
+                    bs = be = 0;
+                    if (live) {
+                        const int cb = bx.cell_off + (wrapc(iz + oz, nc) * nc + wrapc(iy + oy, nc)) * nc +
+                                       wrapc(ix + ox, nc);
+                        bs = a.cell_start[cb];
+                        be = a.cell_start[cb + 1];
+                    }
+                }
                 nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
-                shx = (float)kOrder[o][0] * L;
-                shy = (float)kOrder[o][1] * L;
-                shz = (float)kOrder[o][2] * L;
+                shx = (float)ox * L;
+                shy = (float)oy * L;
+                shz = (float)oz * L;
             }
             const bool more = ch < nchunk;  // warp-uniform
             if (more) {
@@ -718,14 +765,11 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool ac
     a.thermo4 = ctx->thermo4;
     a.ngb_hash = ctx->ngb_hash;
     a.counters = ctx->counters;
-    a.nc = ctx->grid.nc;
-    a.L32 = ctx->grid.L32;
+    a.boxes = ctx->d_boxes;
     a.box = ctx->p.box_size;
     a.n_ngb_target = ctx->p.n_ngb;
     a.h_tol = ctx->p.h_tol;
     a.gamma = ctx->p.gamma;
-    // largest h the current cells can hold (cells are no smaller than any h)
-    a.h_cell_limit = (float)(ctx->grid.L64 * (1.0 - 1e-6));
     a.use_balsara = ctx->p.use_balsara;
     a.last_pass = last_pass ? 1 : 0;
     int rc = smem_optin(ctx);
@@ -761,15 +805,14 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts)
     a.x = parts->x;
     a.y = parts->y;
     a.z = parts->z;
-    a.hmax_global = ctx->d_scalars;
+    a.box_hmax = ctx->d_box_hmax;
     a.ax = parts->ax;
     a.ay = parts->ay;
     a.az = parts->az;
     a.dudt = parts->dudt;
     a.vsig = parts->vsig;
     a.counters = ctx->counters;
-    a.nc = ctx->grid.nc;
-    a.L32 = ctx->grid.L32;
+    a.boxes = ctx->d_boxes;
     a.box = ctx->p.box_size;
     a.alpha = ctx->p.alpha_visc;
     int rc = smem_optin(ctx);

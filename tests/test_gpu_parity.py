@@ -217,3 +217,119 @@ def test_h_growth_forces_rebuild():
     s = oracle_state(g)
     check_density(g, s)
     check_force(g, s)
+
+
+def test_radius_two_stencil():
+    """Cells planned for a guess at 0.6x the converged h: converged h reach past
+    one cell, so the passes use the radius-2 stencil instead of re-binning."""
+    d = inputs.uniform(8000, seed=16)
+    d["h"] *= 0.6
+    ctx, parts, g = gpu_hydro(d, cell_factor=1.0)
+    assert g["stats"]["rebuilds"] == 0
+    assert g["h"].max() > g["stats"]["cell_size"]
+    s = oracle_state(g)
+    check_density(g, s)
+    check_force(g, s)
+
+
+def _boxes(sizes, seed):
+    """Independent periodic unit boxes of uneven occupancy, concatenated; equal
+    masses 1/N_box; random velocities."""
+    parts, offs = [], [0]
+    for k, nb in enumerate(sizes):
+        b = inputs.random_velocities(inputs.uniform(nb, seed=seed + k), 0.2, seed + 50 + k)
+        parts.append(b)
+        offs.append(offs[-1] + nb)
+    d = {k: np.concatenate([b[k] for b in parts]) for k in inputs.FIELDS}
+    return d, offs
+
+
+def test_batched_boxes_match_each_box_alone():
+    """Several uneven periodic boxes in one context (one launch per pass): every
+    box must match the oracle run on that box alone."""
+    sizes = [1200, 5000, 300 + 17, 9000]
+    d, offs = _boxes(sizes, 60)
+    ctx, parts, g = gpu_hydro(d, box_offsets=offs)
+    perm = g["perm"]
+    for b in range(len(sizes)):
+        sl = np.arange(offs[b], offs[b + 1])
+        assert np.all((perm[sl] >= offs[b]) & (perm[sl] < offs[b + 1]))  # boxes stay contiguous
+        sub = {k: g[k][sl] for k in ("x", "y", "z", "vx", "vy", "vz", "m", "u", "h", "rho", "P", "c", "f",
+                                     "divv", "curl", "n_ngb", "ax", "ay", "az", "dudt", "vsig")}
+        sub["perm"] = perm[sl]
+        sub["ngb_hash"] = g["ngb_hash"][sl]
+        s = oracle_state(sub)
+        dd = check_density(sub, s)
+        check_force(sub, s)
+
+
+def _state_equal(g1, g2, perm1, perm2, rtol):
+    i1 = np.argsort(perm1)
+    i2 = np.argsort(perm2)
+    for k in ("x", "y", "z"):
+        dx = g1[k][i1] - g2[k][i2]
+        dx -= np.rint(dx)
+        assert np.abs(dx).max() < 1e-9, k
+    for k in ("vx", "vy", "vz"):
+        scale = np.abs(g1[k]).max() + 1e-30
+        assert np.abs(g1[k][i1] - g2[k][i2]).max() <= rtol * scale, k
+    assert rel(g1["u"][i1], g2["u"][i2]).max() <= rtol
+    assert rel(g1["h"][i1], g2["h"][i2]).max() <= rtol
+
+
+@pytest.mark.parametrize("dt", [0.0, 4e-4])
+def test_graph_steps_match_host_steps(dt):
+    """sph_steps (one captured step replayed) against sph_step called in a loop."""
+    from paper_1508_00115_gb300 import binding
+    d = _uniform_moving(6000, 17)
+    out = []
+    for mode in ("host", "graph"):
+        ctx = binding.Context(d["x"].size, h_tol=1e-6)
+        parts = binding.Particles(d)
+        if mode == "host":
+            for _ in range(3):
+                ctx.step(parts, dt)
+        else:
+            ctx.steps(parts, 3, dt)
+            assert ctx.stats()["graph_steps"] == 3
+        out.append((parts.numpy(), ctx.permutation()))
+    (g1, p1), (g2, p2) = out
+    _state_equal(g1, g2, p1, p2, 1e-5)
+
+
+def test_graph_steps_batched_boxes_match_oracle():
+    """Batched boxes stepped by the captured graph, each box against the oracle's
+    integrator (common dt)."""
+    from paper_1508_00115_gb300 import binding
+    sizes = [3000, 1500, 4500]
+    d, offs = _boxes(sizes, 80)
+    ctx = binding.Context(d["x"].size, box_offsets=offs, h_tol=1e-6)
+    parts = binding.Particles(d)
+    ctx.build_cells(parts)
+    ctx.density(parts)
+    ctx.force(parts)
+    g0 = parts.numpy()
+    perm0 = ctx.permutation()
+    dt = 0.5 * min(float(np.min(g0["h"][g0["vsig"] > 0] / g0["vsig"][g0["vsig"] > 0])) * 0.1, 1e9)
+    ctx.steps(parts, 2, dt)
+    g = parts.numpy()
+    perm = ctx.permutation()
+    for b in range(len(sizes)):
+        sl0 = np.arange(offs[b], offs[b + 1])
+        s = oracle.State(**{k: g0[k][sl0].astype(np.float64) for k in inputs.FIELDS})
+        acc = oracle.hydro(s)
+        for _ in range(2):
+            s, acc, _ = oracle.step(s, acc, dt)
+        # GPU slots of box b, mapped to the first build's order inside the box
+        sl = np.arange(offs[b], offs[b + 1])
+        inv = np.empty(d["x"].size, np.int64)
+        inv[perm0] = np.arange(d["x"].size)
+        idx = inv[perm[sl]] - offs[b]
+        for k in ("x", "y", "z"):
+            dx = g[k][sl] - getattr(s, k)[idx]
+            dx -= np.rint(dx)
+            assert np.abs(dx).max() < 1e-8
+        vscale = np.sqrt(np.mean(s.vx ** 2 + s.vy ** 2 + s.vz ** 2))
+        for k in ("vx", "vy", "vz"):
+            assert np.abs(g[k][sl] - getattr(s, k)[idx]).max() < 1e-5 * vscale
+        assert rel(g["u"][sl], s.u[idx]).max() < 1e-5
