@@ -45,6 +45,25 @@ __constant__ signed char kOrder[27][3] = {
     {-1, 0, 1},  {0, 1, 1},   {0, -1, -1}, {0, 1, -1},  {0, -1, 1},   {1, 1, 1},  {-1, -1, -1},
     {1, 1, -1},  {-1, -1, 1}, {1, -1, 1},  {-1, 1, -1}, {-1, 1, 1},   {1, -1, -1}};
 
+// Radius-2 stencils visit the 27 cells above, in that order, then the 98 cells at
+// distance two (z, y, x lexicographic), so a tile's summation order never depends
+// on which stencil its warp runs.
+__constant__ signed char kOuter[98][3] = {
+    {-2, -2, -2}, {-1, -2, -2}, {0, -2, -2}, {1, -2, -2}, {2, -2, -2}, {-2, -1, -2}, {-1, -1, -2},
+    {0, -1, -2}, {1, -1, -2}, {2, -1, -2}, {-2, 0, -2}, {-1, 0, -2}, {0, 0, -2}, {1, 0, -2},
+    {2, 0, -2}, {-2, 1, -2}, {-1, 1, -2}, {0, 1, -2}, {1, 1, -2}, {2, 1, -2}, {-2, 2, -2},
+    {-1, 2, -2}, {0, 2, -2}, {1, 2, -2}, {2, 2, -2}, {-2, -2, -1}, {-1, -2, -1}, {0, -2, -1},
+    {1, -2, -1}, {2, -2, -1}, {-2, -1, -1}, {2, -1, -1}, {-2, 0, -1}, {2, 0, -1}, {-2, 1, -1},
+    {2, 1, -1}, {-2, 2, -1}, {-1, 2, -1}, {0, 2, -1}, {1, 2, -1}, {2, 2, -1}, {-2, -2, 0},
+    {-1, -2, 0}, {0, -2, 0}, {1, -2, 0}, {2, -2, 0}, {-2, -1, 0}, {2, -1, 0}, {-2, 0, 0},
+    {2, 0, 0}, {-2, 1, 0}, {2, 1, 0}, {-2, 2, 0}, {-1, 2, 0}, {0, 2, 0}, {1, 2, 0},
+    {2, 2, 0}, {-2, -2, 1}, {-1, -2, 1}, {0, -2, 1}, {1, -2, 1}, {2, -2, 1}, {-2, -1, 1},
+    {2, -1, 1}, {-2, 0, 1}, {2, 0, 1}, {-2, 1, 1}, {2, 1, 1}, {-2, 2, 1}, {-1, 2, 1},
+    {0, 2, 1}, {1, 2, 1}, {2, 2, 1}, {-2, -2, 2}, {-1, -2, 2}, {0, -2, 2}, {1, -2, 2},
+    {2, -2, 2}, {-2, -1, 2}, {-1, -1, 2}, {0, -1, 2}, {1, -1, 2}, {2, -1, 2}, {-2, 0, 2},
+    {-1, 0, 2}, {0, 0, 2}, {1, 0, 2}, {2, 0, 2}, {-2, 1, 2}, {-1, 1, 2}, {0, 1, 2},
+    {1, 1, 2}, {2, 1, 2}, {-2, 2, 2}, {-1, 2, 2}, {0, 2, 2}, {1, 2, 2}, {2, 2, 2},};
+
 struct DensityArgs {
     const float4 *__restrict__ pos4;
     const float4 *__restrict__ vel4;
@@ -289,9 +308,9 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
                     oy = kOrder[o][1];
                     oz = kOrder[o][2];
                 } else {
-                    ox = o % 5 - 2;
-                    oy = (o / 5) % 5 - 2;
-                    oz = o / 25 - 2;
+                    ox = o < 27 ? kOrder[o][0] : kOuter[o - 27][0];
+                    oy = o < 27 ? kOrder[o][1] : kOuter[o - 27][1];
+                    oz = o < 27 ? kOrder[o][2] : kOuter[o - 27][2];
                     bs = be = 0;
                     if (live) {
                         const int cb = bx.cell_off + (wrapc(iz + oz, nc) * nc + wrapc(iy + oy, nc)) * nc +
@@ -591,9 +610,9 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
                     oy = kOrder[o][1];
                     oz = kOrder[o][2];
                 } else {
-                    ox = o % 5 - 2;
-                    oy = (o / 5) % 5 - 2;
-                    oz = o / 25 - 2;
+                    ox = o < 27 ? kOrder[o][0] : kOuter[o - 27][0];
+                    oy = o < 27 ? kOrder[o][1] : kOuter[o - 27][1];
+                    oz = o < 27 ? kOrder[o][2] : kOuter[o - 27][2];
                     bs = be = 0;
                     if (live) {
                         const int cb = bx.cell_off + (wrapc(iz + oz, nc) * nc + wrapc(iy + oy, nc)) * nc +
