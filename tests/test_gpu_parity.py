@@ -220,10 +220,11 @@ def test_h_growth_forces_rebuild():
 
 
 def test_radius_two_stencil():
-    """Cells planned for a guess at 0.6x the converged h: converged h reach past
-    one cell, so the passes use the radius-2 stencil instead of re-binning."""
-    d = inputs.uniform(8000, seed=16)
-    d["h"] *= 0.6
+    """Cells planned for a guess at 0.7x the converged h (jittered lattice, nearly
+    uniform h): the converged h reach past one cell but stay within two, so the
+    passes use the radius-2 stencil instead of re-binning."""
+    d = inputs.lattice(20, jitter=0.3, seed=16)
+    d["h"] *= 0.7
     ctx, parts, g = gpu_hydro(d, cell_factor=1.0)
     assert g["stats"]["rebuilds"] == 0
     assert g["h"].max() > g["stats"]["cell_size"]
