@@ -382,16 +382,27 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
     rc = plan_cells(ctx, parts);  // fixed for the whole run
     if (rc) return rc;
     const int passes = std::max(1, std::min(ctx->p.max_h_iter, 6));
-    // capture one step; the timing flag is suspended (events are not capturable here)
+    // capture one step on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); the graph is then launched on the caller's
+    // stream.  The timing flag is suspended while capturing.
+    if (!ctx->cap_stream) SPH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     const uint32_t flags = ctx->p.flags;
     ctx->p.flags &= ~SPH_FLAG_TIMING;
     SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    SPH_CUDA(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    cudaStream_t user = ctx->stream;
+    ctx->stream = ctx->cap_stream;
+    cudaError_t ce = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) {
+        ctx->stream = user;
+        ctx->p.flags = flags;
+        return cuda_fail(ctx, ce, "begin capture");
+    }
     const int64_t launches0 = ctx->st.kernel_launches;
     rc = graph_step(ctx, parts, dt, passes);
     const int64_t per_step = ctx->st.kernel_launches - launches0;
     cudaGraph_t graph = nullptr;
-    cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    ce = cudaStreamEndCapture(ctx->stream, &graph);
+    ctx->stream = user;
     ctx->p.flags = flags;
     ctx->predict = false;
     if (rc) {
@@ -400,6 +411,7 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
     }
     if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph capture");
     if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     ctx->step_exec = nullptr;
     ce = cudaGraphInstantiate(&ctx->step_exec, graph, 0);
     cudaGraphDestroy(graph);

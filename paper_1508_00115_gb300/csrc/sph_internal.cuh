@@ -136,6 +136,7 @@ struct sph_ctx {
     double *h_dt = nullptr;   // pinned
     // captured multi-step graph
     cudaGraphExec_t step_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream the step is captured on
     double graph_dt = 0.0;    // dt mode the graph was captured with (<= 0: CFL)
     int graph_passes = 0;
 
