@@ -387,12 +387,15 @@ __global__ void k_gather(GatherArgs a)
     a.ids_out[p] = a.ids_valid ? a.ids_in[src] : (int64_t)src;
 }
 
+// Copy the gathered arrays back into place (no pointer swaps: a captured step must
+// read and write the same buffers on every replay).
 __global__ void k_copy_back(sph_particles P, const double *__restrict__ s64, const float *__restrict__ s32,
-                            int64_t cap, int n)
+                            const int64_t *__restrict__ ids_tmp, int64_t *__restrict__ ids, int64_t cap, int n)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     int64_t c = cap;
+    ids[p] = ids_tmp[p];
     P.x[p] = s64[p];
     P.y[p] = s64[c + p];
     P.z[p] = s64[2 * c + p];
@@ -567,9 +570,9 @@ int build_planned(sph_ctx *ctx, sph_particles *parts)
         ga.bx = ctx->d_boxes;
         k_gather<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(ga);
         SPH_LAUNCH(ctx, "gather");
-        k_copy_back<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(*parts, ctx->s64, ctx->s32, ctx->cap, n);
+        k_copy_back<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(*parts, ctx->s64, ctx->s32, ctx->ids_tmp,
+                                                                 ctx->ids, ctx->cap, n);
         SPH_LAUNCH(ctx, "copy back");
-        std::swap(ctx->ids, ctx->ids_tmp);
         ctx->ids_valid = true;
     }
     k_cell_start<<<blocks_for(g.n_cells + 1, 256), 256, 0, ctx->stream>>>(ctx->keys, n, g.n_cells, ctx->cell_start);
