@@ -384,39 +384,47 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
     const int passes = std::max(1, std::min(ctx->p.max_h_iter, 6));
     // capture one step on a private stream (the caller's may be the legacy default
     // stream, which cannot be captured); the graph is then launched on the caller's
-    // stream.  The timing flag is suspended while capturing.
-    if (!ctx->cap_stream) SPH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
-    const uint32_t flags = ctx->p.flags;
-    ctx->p.flags &= ~SPH_FLAG_TIMING;
-    SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    cudaStream_t user = ctx->stream;
-    ctx->stream = ctx->cap_stream;
-    cudaError_t ce = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
-    if (ce != cudaSuccess) {
+    // stream.  The timing flag is suspended while capturing.  A graph captured for
+    // the same arrays, dt mode and launch shapes is reused.
+    sph_ctx::GraphKey key{*parts, dt > 0 ? dt : 0.0, ctx->n, ctx->grid.n_cells, ctx->grid.key_bits, passes, ctx->tile_w};
+    if (!ctx->step_exec || !(key == ctx->graph_key)) {
+        if (!ctx->cap_stream) SPH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        const uint32_t flags = ctx->p.flags;
+        ctx->p.flags &= ~SPH_FLAG_TIMING;
+        SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        cudaStream_t user = ctx->stream;
+        ctx->stream = ctx->cap_stream;
+        cudaError_t ce = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) {
+            ctx->stream = user;
+            ctx->p.flags = flags;
+            return cuda_fail(ctx, ce, "begin capture");
+        }
+        const int64_t launches0 = ctx->st.kernel_launches;
+        const int64_t passes0 = ctx->st.density_passes, fpasses0 = ctx->st.force_passes;
+        rc = graph_step(ctx, parts, dt, passes);
+        ctx->graph_launches = ctx->st.kernel_launches - launches0;
+        ctx->st.kernel_launches = launches0;  // capture launched nothing
+        ctx->st.density_passes = passes0;
+        ctx->st.force_passes = fpasses0;
+        cudaGraph_t graph = nullptr;
+        ce = cudaStreamEndCapture(ctx->stream, &graph);
         ctx->stream = user;
         ctx->p.flags = flags;
-        return cuda_fail(ctx, ce, "begin capture");
+        ctx->predict = false;
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph capture");
+        if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+        ctx->step_exec = nullptr;
+        ce = cudaGraphInstantiate(&ctx->step_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph instantiate");
+        ctx->graph_key = key;
     }
-    const int64_t launches0 = ctx->st.kernel_launches;
-    rc = graph_step(ctx, parts, dt, passes);
-    const int64_t per_step = ctx->st.kernel_launches - launches0;
-    cudaGraph_t graph = nullptr;
-    ce = cudaStreamEndCapture(ctx->stream, &graph);
-    ctx->stream = user;
-    ctx->p.flags = flags;
-    ctx->predict = false;
-    if (rc) {
-        if (graph) cudaGraphDestroy(graph);
-        return rc;
-    }
-    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph capture");
-    if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
-    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
-    ctx->step_exec = nullptr;
-    ce = cudaGraphInstantiate(&ctx->step_exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph instantiate");
-    ctx->st.kernel_launches = launches0;  // capture launched nothing
+    const int64_t per_step = ctx->graph_launches;
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_FLOORS, 0, sizeof(unsigned long long), ctx->stream));
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_GFLAGS, 0, sizeof(unsigned long long), ctx->stream));
     for (int k = 0; k < n_steps; ++k) SPH_CUDA(ctx, cudaGraphLaunch(ctx->step_exec, ctx->stream));

@@ -270,34 +270,32 @@ __device__ __forceinline__ int box_of_cell(int c, const BoxDev *__restrict__ bx,
     return lo;
 }
 
-// max h of every box (one block per box); h must be finite and > 0 (NaN and
-// negative values surface as NaN bits, which order above +inf)
+// max h of every box (blockIdx.y = box, blockIdx.x strides its particles; the
+// result is an atomic max of bit patterns into a zeroed slot).  h must be finite
+// and > 0: NaN and negative values surface as NaN bits, which order above +inf.
 __global__ void k_box_max_h(const float *__restrict__ h, const int64_t *__restrict__ off, unsigned *__restrict__ out)
 {
-    const int b = blockIdx.x;
+    const int b = blockIdx.y;
     const int64_t lo = off[b], hi = off[b + 1];
     unsigned m = 0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += (int64_t)gridDim.x * blockDim.x) {
         unsigned v = __float_as_uint(h[i]);
         if ((int)v < 0) v = 0x7fc00000u;
         m = max(m, v);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
-    __shared__ unsigned sh[32];
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned r = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = max(r, sh[w]);
-        out[b] = r;
-    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out + b, m);
 }
 
 int box_max_h(sph_ctx *ctx, const float *h)
 {
     if (ctx->n <= 0) return SPH_OK;
-    k_box_max_h<<<ctx->n_boxes, 256, 0, ctx->stream>>>(h, ctx->d_box_off, (unsigned *)ctx->d_box_hmax);
+    int64_t most = 0;
+    for (int b = 0; b < ctx->n_boxes; ++b) most = std::max(most, ctx->box_off[b + 1] - ctx->box_off[b]);
+    const unsigned bpb = (unsigned)std::min<int64_t>(512, std::max<int64_t>(1, most / 8192));
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->d_box_hmax, 0, sizeof(float) * ctx->n_boxes, ctx->stream));
+    k_box_max_h<<<dim3(bpb, ctx->n_boxes), 256, 0, ctx->stream>>>(h, ctx->d_box_off, (unsigned *)ctx->d_box_hmax);
     SPH_LAUNCH(ctx, "box max h");
     return SPH_OK;
 }

@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string.h>
+
 #include <string>
 #include <vector>
 
@@ -137,8 +139,19 @@ struct sph_ctx {
     // captured multi-step graph
     cudaGraphExec_t step_exec = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream the step is captured on
-    double graph_dt = 0.0;    // dt mode the graph was captured with (<= 0: CFL)
-    int graph_passes = 0;
+    // what the captured step depends on besides device memory: reuse it while equal
+    struct GraphKey {
+        sph_particles parts;
+        double dt;
+        int64_t n, n_cells;
+        int key_bits, passes, tile_w;
+        bool operator==(const GraphKey &o) const
+        {
+            return memcmp(&parts, &o.parts, sizeof parts) == 0 && dt == o.dt && n == o.n && n_cells == o.n_cells &&
+                   key_bits == o.key_bits && passes == o.passes && tile_w == o.tile_w;
+        }
+    } graph_key{};
+    int64_t graph_launches = 0;  // kernels in one captured step
 
     // statistics
     sph_stats st{};
