@@ -246,7 +246,7 @@ static int do_force(sph_ctx *ctx, sph_particles *parts)
 {
     if (!ctx->density_valid) return fail(ctx, SPH_ERR_STATE, "sph_force needs sph_density on the current state");
     if (ctx->n > 0) {
-        int rc = box_max_h(ctx, parts->h);  // reach of every box for r < max(h_i, h_j)
+        int rc = cell_reach(ctx);  // reach of every cell for r < max(h_i, h_j)
         if (rc) return rc;
         rc = run_force_pass(ctx, parts);
         if (rc) return rc;
@@ -353,7 +353,7 @@ static int graph_step(sph_ctx *ctx, sph_particles *parts, double dt, int passes)
     SPH_LAUNCH(ctx, "step flags");
     rc = sync_h(ctx, parts);
     if (rc) return rc;
-    rc = box_max_h(ctx, parts->h);
+    rc = cell_reach(ctx);
     if (rc) return rc;
     rc = run_force_pass(ctx, parts);
     if (rc) return rc;

@@ -462,16 +462,72 @@ int cell_keys_out(sph_ctx *ctx, int32_t *dev_keys)
     return SPH_OK;
 }
 
+// Largest h that can reach each cell: the max h of its particles, then the max of
+// that over the 5 x 5 x 5 block of cells around it (periodic, within its box), done
+// as three one-axis passes.  Any particle whose support reaches a cell lies in that
+// block as long as every h is within two cell sides (beyond that the density pass
+// flags the grid for re-planning).
+__global__ void k_cell_hmax(const int *__restrict__ cs, const float4 *__restrict__ pos4, int64_t ncells,
+                            float *__restrict__ out)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    float m = 0.f;
+    for (int p = cs[c]; p < cs[c + 1]; ++p) m = fmaxf(m, pos4[p].w);
+    out[c] = m;
+}
+
+__global__ void k_cell_max_axis(const float *__restrict__ in, float *__restrict__ out, int64_t ncells,
+                                const BoxDev *__restrict__ bx, int nb, int axis)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    const BoxDev g = bx[nb == 1 ? 0 : box_of_cell((int)c, bx, nb)];
+    const int nc = g.nc, loc = (int)c - g.cell_off;
+    int i3[3] = {loc % nc, (loc / nc) % nc, loc / (nc * nc)};
+    float m = 0.f;
+    for (int d = -2; d <= 2; ++d) {
+        int j3[3] = {i3[0], i3[1], i3[2]};
+        int v = i3[axis] + d;
+        v = v < 0 ? v + nc : (v >= nc ? v - nc : v);
+        v = v < 0 ? v + nc : (v >= nc ? v - nc : v);  // nc >= 3: two corrections suffice
+        j3[axis] = v;
+        m = fmaxf(m, in[g.cell_off + (j3[2] * nc + j3[1]) * nc + j3[0]]);
+    }
+    out[c] = m;
+}
+
+int cell_reach(sph_ctx *ctx)
+{
+    const int64_t nc = ctx->grid.n_cells;
+    const unsigned blocks = (unsigned)((nc + 255) / 256);
+    k_cell_hmax<<<blocks, 256, 0, ctx->stream>>>(ctx->cell_start, ctx->pos4, nc, ctx->cell_hmax);
+    SPH_LAUNCH(ctx, "cell max h");
+    k_cell_max_axis<<<blocks, 256, 0, ctx->stream>>>(ctx->cell_hmax, ctx->cell_tmp, nc, ctx->d_boxes, ctx->n_boxes, 0);
+    SPH_LAUNCH(ctx, "cell reach x");
+    k_cell_max_axis<<<blocks, 256, 0, ctx->stream>>>(ctx->cell_tmp, ctx->cell_hmax, nc, ctx->d_boxes, ctx->n_boxes, 1);
+    SPH_LAUNCH(ctx, "cell reach y");
+    k_cell_max_axis<<<blocks, 256, 0, ctx->stream>>>(ctx->cell_hmax, ctx->cell_tmp, nc, ctx->d_boxes, ctx->n_boxes, 2);
+    SPH_LAUNCH(ctx, "cell reach z");  // result in cell_tmp
+    return SPH_OK;
+}
+
 static int ensure_cells(sph_ctx *ctx, int64_t ncells)
 {
     if (ncells + 1 > ctx->cell_cap) {
         cudaFree(ctx->cell_start);
         cudaFree(ctx->cell_tiles);
+        cudaFree(ctx->cell_hmax);
+        cudaFree(ctx->cell_tmp);
         ctx->cell_start = nullptr;
         ctx->cell_tiles = nullptr;
+        ctx->cell_hmax = nullptr;
+        ctx->cell_tmp = nullptr;
         int64_t cap = ncells + 1 + 1024;
         SPH_CUDA(ctx, cudaMalloc(&ctx->cell_start, sizeof(int) * cap));
         SPH_CUDA(ctx, cudaMalloc(&ctx->cell_tiles, sizeof(uint32_t) * cap));
+        SPH_CUDA(ctx, cudaMalloc(&ctx->cell_hmax, sizeof(float) * cap));
+        SPH_CUDA(ctx, cudaMalloc(&ctx->cell_tmp, sizeof(float) * cap));
         ctx->cell_cap = cap;
     }
     // the scan of per-cell tile counts needs ceil(ncells / chunk) block sums

@@ -109,6 +109,8 @@ struct sph_ctx {
     int tile_w = 16;             // targets per tile: 16 (two tiles per warp) or 32
     int *cell_start = nullptr;
     int64_t cell_cap = 0;
+    float *cell_hmax = nullptr;   // max h per cell (scratch of the reach passes)
+    float *cell_tmp = nullptr;    // after cell_reach: max h over the 5x5x5 cell block
     int4 *tiles = nullptr;
     int64_t tile_cap = 0;
     int *n_tiles = nullptr;      // device scalar
@@ -187,6 +189,7 @@ int plan_cells(sph_ctx *ctx, sph_particles *parts);             // sph_cells.cu 
 int build_cells(sph_ctx *ctx, sph_particles *parts);            // sph_cells.cu (plan + build)
 int build_planned(sph_ctx *ctx, sph_particles *parts);          // sph_cells.cu (no host read)
 int box_max_h(sph_ctx *ctx, const float *h);                    // sph_cells.cu
+int cell_reach(sph_ctx *ctx);  // cell_tmp = max h within two cells   // sph_cells.cu
 int cell_keys_out(sph_ctx *ctx, int32_t *dev_keys);             // sph_cells.cu
 int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool active_list);  // sph_pairs.cu
 int compact_active_tiles(sph_ctx *ctx);                                    // sph_pairs.cu

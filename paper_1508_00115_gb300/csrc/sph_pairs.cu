@@ -420,7 +420,7 @@ struct ForceArgs {
     const double *__restrict__ x;
     const double *__restrict__ y;
     const double *__restrict__ z;
-    const float *__restrict__ box_hmax;
+    const float *__restrict__ cell_reach;  // per global cell: max h within two cells
     float *ax, *ay, *az, *dudt, *vsig;
     unsigned long long *counters;
     const BoxDev *__restrict__ boxes;
@@ -472,7 +472,9 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
         const BoxDev bx = a.boxes[tile.w];
         const int nc = bx.nc;
         const float L = bx.L32;
-        const float H = fmaxf(tile_max<TW>(hi), a.box_hmax[tile.w]);
+        // cutoff reach of the tile: r < max(h_i, h_j) with h_j of any particle that can
+        // reach its cell (a tile beyond the last has tile.x = 0, a valid cell)
+        const float H = fmaxf(tile_max<TW>(hi), a.cell_reach[tile.x]);
         const int R = (int)__reduce_max_sync(kFull, H * (1.f + kPruneMargin) > L ? 2u : 1u);
         const float bandmax = 2.f * kBandK * H * (H + L);
         const float reach2 = H * H * (1.f + kPruneMargin) + bandmax;
@@ -824,7 +826,7 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts)
     a.x = parts->x;
     a.y = parts->y;
     a.z = parts->z;
-    a.box_hmax = ctx->d_box_hmax;
+    a.cell_reach = ctx->cell_tmp;
     a.ax = parts->ax;
     a.ay = parts->ay;
     a.az = parts->az;
