@@ -189,9 +189,11 @@ int sph_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_used, sph
 /* n_steps KDK steps (as sph_step) with no host synchronisation between them: the
  * step is captured once into a CUDA graph and replayed.  Differences from calling
  * sph_step n_steps times: dt lives on the device (dt <= 0: the CFL step of each
- * step's start, else the fixed dt); the cell grid of every box is planned once at
- * entry and kept (cells stay correct while every h stays within twice the planned
- * cell side; beyond that the call returns SPH_ERR_H_EXCEEDS_CELL); each density
+ * step's start, else the fixed dt); the cell grid of every box is fixed for the
+ * run -- the grid of the previous run is kept while every box's max h is within
+ * 1.8 of its cell side (and not far below), else it is planned again at entry
+ * (cells stay correct while every h stays within twice the planned cell side;
+ * beyond that the call returns SPH_ERR_H_EXCEEDS_CELL); each density
  * evaluation runs a fixed number of passes, min(max_h_iter, 6) -- passes after
  * convergence find no work -- and SPH_ERR_NOT_CONVERGED is returned if any
  * particle was still unconverged after them.  *out (may be NULL) receives the

@@ -379,8 +379,14 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
         if (rc) return rc;
         if (!isfinite(d0)) return fail(ctx, SPH_ERR_INVALID_ARG, "no signal velocity: pass an explicit dt");
     }
-    rc = plan_cells(ctx, parts);  // fixed for the whole run
+    // the cell plan is fixed for the whole run; an existing plan (and the graph
+    // captured for it) is kept while it still suits the particles
+    rc = read_box_max_h(ctx, parts);
     if (rc) return rc;
+    if (!plan_still_good(ctx)) {
+        rc = plan_from_hmax(ctx);
+        if (rc) return rc;
+    }
     const int passes = std::max(1, std::min(ctx->p.max_h_iter, 6));
     // capture one step on a private stream (the caller's may be the legacy default
     // stream, which cannot be captured); the graph is then launched on the caller's

@@ -541,18 +541,44 @@ static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t -
 // Plan the cell grid of every box from its largest h (one host read): the cell
 // side is the smallest L = box / nc with L >= cell_factor * max h and nc >= 3 (cells
 // no smaller than the smoothing length, Sec. 3.1), nc capped near (8 n_box)^(1/3).
+// max h of every box into ctx->h_box_hmax (one host read)
+int read_box_max_h(sph_ctx *ctx, sph_particles *parts)
+{
+    if (ctx->n <= 0) return SPH_OK;
+    int rc = box_max_h(ctx, parts->h);
+    if (rc) return rc;
+    SPH_CUDA(ctx, cudaMemcpyAsync(ctx->h_box_hmax, ctx->d_box_hmax, sizeof(float) * ctx->n_boxes,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return SPH_OK;
+}
+
+// True while the current plan still suits the particles: every box's max h within
+// 1.8 cell sides (the radius-2 stencil reaches two) and not far below the side the
+// cell factor asks for (cells much larger than needed cost candidates).
+bool plan_still_good(sph_ctx *ctx)
+{
+    if (!ctx->planned) return false;
+    for (int b = 0; b < ctx->n_boxes; ++b) {
+        if (ctx->box_off[b + 1] == ctx->box_off[b]) continue;
+        const double h = ctx->h_box_hmax[b], L = ctx->h_boxes[b].L64;
+        if (!(h > 0) || h > 1.8 * L || h * ctx->p.cell_factor < 0.6 * L) return false;
+    }
+    return true;
+}
+
 int plan_cells(sph_ctx *ctx, sph_particles *parts)
+{
+    int rc = read_box_max_h(ctx, parts);
+    if (rc) return rc;
+    return plan_from_hmax(ctx);
+}
+
+int plan_from_hmax(sph_ctx *ctx)
 {
     const double box = ctx->p.box_size;
     const int nb = ctx->n_boxes;
     BoxDev *hb = ctx->h_boxes;
-    if (ctx->n > 0) {
-        int rc = box_max_h(ctx, parts->h);
-        if (rc) return rc;
-        SPH_CUDA(ctx, cudaMemcpyAsync(ctx->h_box_hmax, ctx->d_box_hmax, sizeof(float) * nb, cudaMemcpyDeviceToHost,
-                                      ctx->stream));
-        SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    }
     int64_t cells = 0;
     for (int b = 0; b < nb; ++b) {
         const int64_t np = ctx->box_off[b + 1] - ctx->box_off[b];

@@ -186,6 +186,9 @@ void timer_end(sph_ctx *ctx, cudaEvent_t end);
 
 // launch wrappers (defined in the .cu files) ---------------------------------
 int plan_cells(sph_ctx *ctx, sph_particles *parts);             // sph_cells.cu (host read)
+int read_box_max_h(sph_ctx *ctx, sph_particles *parts);         // sph_cells.cu (host read)
+int plan_from_hmax(sph_ctx *ctx);                               // sph_cells.cu
+bool plan_still_good(sph_ctx *ctx);                             // sph_cells.cu
 int build_cells(sph_ctx *ctx, sph_particles *parts);            // sph_cells.cu (plan + build)
 int build_planned(sph_ctx *ctx, sph_particles *parts);          // sph_cells.cu (no host read)
 int box_max_h(sph_ctx *ctx, const float *h);                    // sph_cells.cu
