@@ -252,8 +252,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     for _ in range(args.warmup):
         ctx.step(parts)
-    # the captured multi-step path: capture once (kept for the timed call)
-    ctx.steps(parts, 1)
+    # both timed paths start from this state
+    snap = {k: v.clone() for k, v in parts.t.items()}
+    torch.cuda.synchronize()
 
     def timed(fn):
         torch.cuda.synchronize()
@@ -286,14 +287,20 @@ def run_ours(args):
     ms_plain, floors = timed(plain)
     st = ctx.stats()
 
-    # production path: all K steps from one captured CUDA graph, no host sync between
-    # (one untimed call first, so the timed call replays a graph already captured)
-    ctx.steps(parts, 1)
-    ctx.reset_stats()
+    # production path: all K steps from one captured CUDA graph, no host sync between.
+    # Same starting state and schedule; a fresh context is prepared (hydro pass, cell
+    # plan, graph capture) outside the timed region.
+    tuned = {"tile_width": int(st["tile_width"]), "cell_factor": float(st["cell_factor"])}
+    for k, v in snap.items():
+        parts.t[k].copy_(v)
+    ctx.close()
+    ctx = binding.Context(n, device=local, stream=stream.cuda_stream, **tuned)
+    ctx.steps(parts, 0)
     sampler = ClockSampler(_gpu_id(local)) if rank == 0 else None
     if sampler:
         sampler.start()
         time.sleep(0.3)
+    ctx.reset_stats()
     ms, (dt_last, cons_g) = timed(lambda: ctx.steps(parts, args.steps))
     clocks = sampler.stop() if sampler else None
     st_g = ctx.stats()

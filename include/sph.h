@@ -198,7 +198,8 @@ int sph_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_used, sph
  * convergence find no work -- and SPH_ERR_NOT_CONVERGED is returned if any
  * particle was still unconverged after them.  *out (may be NULL) receives the
  * conserved quantities after the last step; *dt_last (may be NULL) its dt.
- * Synchronises the stream once, at the end. */
+ * n_steps = 0 only prepares (hydro pass if needed, plan, capture).  Synchronises
+ * the stream at entry (max h, first dt) and at the end. */
 int sph_steps(sph_ctx *ctx, sph_particles *parts, int32_t n_steps, double dt, double *dt_last,
               sph_conserved *out);
 

@@ -368,7 +368,6 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
 {
     int rc;
     ctx->predict = false;
-    if (n_steps <= 0) return SPH_OK;
     if (!ctx->hydro_valid) {
         rc = hydro(ctx, parts);
         if (rc) return rc;
@@ -430,6 +429,7 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
         if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph instantiate");
         ctx->graph_key = key;
     }
+    if (n_steps == 0) return SPH_OK;  // prepared: hydro, plan and graph are ready
     const int64_t per_step = ctx->graph_launches;
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_FLOORS, 0, sizeof(unsigned long long), ctx->stream));
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_GFLAGS, 0, sizeof(unsigned long long), ctx->stream));
