@@ -58,6 +58,14 @@ typedef struct sph_ctx sph_ctx; /* opaque, library-owned */
                                 candidate schedule (tile width 16/32 x cell factor
                                 1.05/1.25/1.5) on the current particles and keep the
                                 fastest; overrides tile_width and cell_factor */
+#define SPH_FLAG_ADAPTIVE 8u /* adaptive cells (Sec. 3.1): the uniform grid becomes the
+                                top level of an octree refined while a node holds more
+                                than 32 particles and its children stay no smaller than
+                                cell_factor x their largest h; leaves are the work
+                                items, each with a list of the leaves within reach.
+                                For h spanning decades (clustered matter).  Builds read
+                                tree sizes on the host, so sph_steps runs its steps
+                                one by one instead of replaying a CUDA graph. */
 
 typedef struct {
     int64_t n;           /* particles; 0 <= n < 2^31                                  */
@@ -217,7 +225,8 @@ int sph_get_permutation(sph_ctx *ctx, int64_t *dev_perm);
 /* Forget the permutation: the next build numbers particles 0..n-1 afresh. */
 int sph_reset_ids(sph_ctx *ctx);
 
-/* Cell key of every slot (device, int32, length n) for the current grid. */
+/* Cell key of every slot (device, int32, length n) for the current grid (with
+ * SPH_FLAG_ADAPTIVE: the top-level cell holding the slot). */
 int sph_get_cell_keys(sph_ctx *ctx, int32_t *dev_keys);
 
 /* Neighbour-set hash of the last density pass (needs SPH_FLAG_NGB_HASH): device,

@@ -30,6 +30,7 @@ SPH_ERR_STATE = 7
 SPH_FLAG_TIMING = 1
 SPH_FLAG_NGB_HASH = 2
 SPH_FLAG_AUTOTUNE = 4
+SPH_FLAG_ADAPTIVE = 8
 SPH_SORT_STATIC_MAX_N = 262144
 
 _NAMES = {0: "SPH_OK", 1: "SPH_ERR_INVALID_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_NOT_CONVERGED",

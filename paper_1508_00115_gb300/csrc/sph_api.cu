@@ -246,7 +246,8 @@ static int do_force(sph_ctx *ctx, sph_particles *parts)
 {
     if (!ctx->density_valid) return fail(ctx, SPH_ERR_STATE, "sph_force needs sph_density on the current state");
     if (ctx->n > 0) {
-        int rc = cell_reach(ctx);  // reach of every cell for r < max(h_i, h_j)
+        // reach of every cell (leaf) for r < max(h_i, h_j)
+        int rc = ctx->adaptive ? tree_reach(ctx) : cell_reach(ctx);
         if (rc) return rc;
         rc = run_force_pass(ctx, parts);
         if (rc) return rc;
@@ -368,6 +369,18 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
 {
     int rc;
     ctx->predict = false;
+    if (ctx->adaptive) {
+        // tree builds read their sizes on the host: the steps run one by one
+        sph_conserved tmp;
+        double used = 0;
+        if (n_steps == 0) return ctx->hydro_valid ? SPH_OK : hydro(ctx, parts);
+        for (int k = 0; k < n_steps; ++k) {
+            rc = do_step(ctx, parts, dt, &used, k == n_steps - 1 ? (out ? out : &tmp) : nullptr);
+            if (rc) return rc;
+        }
+        if (dt_last) *dt_last = used;
+        return SPH_OK;
+    }
     if (!ctx->hydro_valid) {
         rc = hydro(ctx, parts);
         if (rc) return rc;
@@ -497,6 +510,7 @@ int sph_init(sph_ctx **out, const sph_params *p, int device, void *cuda_stream)
     c->stream = (cudaStream_t)cuda_stream;
     c->n = p->n;
     c->tile_w = p->tile_width == 32 ? 32 : 16;
+    c->adaptive = (p->flags & SPH_FLAG_ADAPTIVE) != 0;
     c->n_boxes = p->n_boxes > 1 ? p->n_boxes : 1;
     if (p->n_boxes > 1) c->box_off.assign(p->box_offsets, p->box_offsets + p->n_boxes + 1);
     else c->box_off = {0, p->n};
@@ -666,7 +680,7 @@ int sph_get_cell_keys(sph_ctx *ctx, int32_t *dev_keys)
 {
     if (!ctx || !dev_keys) return SPH_ERR_INVALID_ARG;
     if (!ctx->built) return fail(ctx, SPH_ERR_STATE, "no cell build on the current positions");
-    return cell_keys_out(ctx, dev_keys);
+    return ctx->adaptive ? tree_cell_keys_out(ctx, dev_keys) : cell_keys_out(ctx, dev_keys);
 }
 
 int sph_get_ngb_hash(sph_ctx *ctx, uint64_t *dev_hash)
@@ -731,6 +745,7 @@ void sph_destroy(sph_ctx *ctx)
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
     free_particles(ctx);
+    free_tree(ctx);
     cudaFree(ctx->cell_start);
     cudaFree(ctx->cell_tiles);
     cudaFree(ctx->counters);

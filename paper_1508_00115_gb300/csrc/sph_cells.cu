@@ -127,7 +127,8 @@ constexpr int kRsItems = 16;
 constexpr int kRsTile = kRsThreads * kRsItems;  // 4096
 constexpr int kRsWarps = kRsThreads / 32;
 
-__global__ void __launch_bounds__(kRsThreads) k_radix_hist(const uint32_t *__restrict__ keys, int n, int shift,
+template <typename K>
+__global__ void __launch_bounds__(kRsThreads) k_radix_hist(const K *__restrict__ keys, int n, int shift,
                                                            uint32_t *__restrict__ hist, int ntiles)
 {
     __shared__ uint32_t cnt[256];
@@ -137,15 +138,16 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const uint32_t *__res
 #pragma unroll 4
     for (int k = 0; k < kRsItems; ++k) {
         int64_t i = base + k * kRsThreads + threadIdx.x;
-        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
+        if (i < n) atomicAdd(&cnt[(uint32_t)(keys[i] >> shift) & 255u], 1u);
     }
     __syncthreads();
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const uint32_t *__restrict__ kin,
+template <typename K>
+__global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const K *__restrict__ kin,
                                                               const uint32_t *__restrict__ vin,
-                                                              uint32_t *__restrict__ kout,
+                                                              K *__restrict__ kout,
                                                               uint32_t *__restrict__ vout, int n, int shift,
                                                               const uint32_t *__restrict__ offs, int ntiles)
 {
@@ -155,16 +157,17 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const uint32_t *__
     __syncwarp();
     const int64_t base = (int64_t)blockIdx.x * kRsTile + (int64_t)w * (kRsItems * 32);
     const unsigned lt = (1u << lane) - 1u;
-    uint32_t key[kRsItems], val[kRsItems];
+    K key[kRsItems];
+    uint32_t val[kRsItems];
     uint16_t rank[kRsItems];
 #pragma unroll
     for (int it = 0; it < kRsItems; ++it) {
         int64_t i = base + it * 32 + lane;
         bool ok = i < n;
-        uint32_t k = ok ? kin[i] : 0u;
+        K k = ok ? kin[i] : (K)0;
         key[it] = k;
         val[it] = ok ? (vin ? vin[i] : (uint32_t)i) : 0u;
-        uint32_t d = ok ? ((k >> shift) & 255u) : 256u;
+        uint32_t d = ok ? ((uint32_t)(k >> shift) & 255u) : 256u;
         unsigned peers = __match_any_sync(kFull, d);
         uint32_t before = ok ? wcnt[w][d] : 0u;
         rank[it] = (uint16_t)(before + __popc(peers & lt));
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const uint32_t *__
     for (int it = 0; it < kRsItems; ++it) {
         int64_t i = base + it * 32 + lane;
         if (i < n) {
-            uint32_t d = (key[it] >> shift) & 255u;
+            uint32_t d = (uint32_t)(key[it] >> shift) & 255u;
             uint32_t dst = offs[(int64_t)d * ntiles + blockIdx.x] + woff[w][d] + rank[it];
             kout[dst] = key[it];
             vout[dst] = val[it];
@@ -198,30 +201,39 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const uint32_t *__
     }
 }
 
-// Sorts ctx->keys (n entries, key_bits significant) stably; values start as the
-// identity.  On return ctx->keys / ctx->vals hold the sorted keys / source slots.
-static int radix_sort(sph_ctx *ctx, int n, int key_bits)
+// Stable LSD sort of keys[] (n entries, key_bits significant) with source slots as
+// values (identity at the start); the sorted keys and slots end in keys[] / vals[]
+// (the buffers are swapped on the host when the pass count is odd).
+template <typename K>
+static int radix_sort_any(sph_ctx *ctx, int n, int key_bits, K *&keys, K *&keys_alt)
 {
     int ntiles = (n + kRsTile - 1) / kRsTile;
-    uint32_t *kin = ctx->keys, *kout = ctx->keys_alt;
+    K *kin = keys, *kout = keys_alt;
     uint32_t *vin = nullptr, *vout = ctx->vals_alt;
     int passes = std::max(1, (key_bits + 7) / 8);
     for (int p = 0; p < passes; ++p) {
         int shift = 8 * p;
-        k_radix_hist<<<ntiles, kRsThreads, 0, ctx->stream>>>(kin, n, shift, ctx->hist, ntiles);
+        k_radix_hist<K><<<ntiles, kRsThreads, 0, ctx->stream>>>(kin, n, shift, ctx->hist, ntiles);
         SPH_LAUNCH(ctx, "radix histogram");
         int rc = exclusive_scan_u32(ctx, ctx->hist, ctx->hist, (int64_t)256 * ntiles);
         if (rc) return rc;
-        k_radix_scatter<<<ntiles, kRsThreads, 0, ctx->stream>>>(kin, vin, kout, vout, n, shift, ctx->hist,
-                                                               ntiles);
+        k_radix_scatter<K><<<ntiles, kRsThreads, 0, ctx->stream>>>(kin, vin, kout, vout, n, shift, ctx->hist,
+                                                                  ntiles);
         SPH_LAUNCH(ctx, "radix scatter");
         std::swap(kin, kout);
         vin = vout;
         vout = (vin == ctx->vals_alt) ? ctx->vals : ctx->vals_alt;
     }
-    if (kin != ctx->keys) std::swap(ctx->keys, ctx->keys_alt);
+    if (kin != keys) std::swap(keys, keys_alt);
     if (vin != ctx->vals) std::swap(ctx->vals, ctx->vals_alt);
     return SPH_OK;
+}
+
+static int radix_sort(sph_ctx *ctx, int n, int key_bits) { return radix_sort_any(ctx, n, key_bits, ctx->keys, ctx->keys_alt); }
+
+int radix_sort64(sph_ctx *ctx, int n, int key_bits)
+{
+    return radix_sort_any(ctx, n, key_bits, ctx->keys64, ctx->keys64_alt);
 }
 
 // -------------------------------------------------------- wrap, key, gather
@@ -351,12 +363,14 @@ __global__ void k_gather(GatherArgs a)
     double vx = P.vx[src], vy = P.vy[src], vz = P.vz[src];
     float m = P.m[src], u = P.u[src], h = P.h[src];
     float ax = P.ax[src], ay = P.ay[src], az = P.az[src], du = P.dudt[src], vs = P.vsig[src];
-    const BoxDev g = a.bx[a.nb == 1 ? 0 : box_of_slot(p, a.bx, a.nb)];
-    const int cell = (int)(a.skeys[p] >> 3) - g.cell_off;
-    const int nc = g.nc;
-    const int ix = cell % nc, iy = (cell / nc) % nc, iz = cell / (nc * nc);
-    const double cx = centre64(ix, g.L64), cy = centre64(iy, g.L64), cz = centre64(iz, g.L64);
-    a.pos4[p] = make_float4((float)(x - cx), (float)(y - cy), (float)(z - cz), h);
+    if (a.skeys) {
+        const BoxDev g = a.bx[a.nb == 1 ? 0 : box_of_slot(p, a.bx, a.nb)];
+        const int cell = (int)(a.skeys[p] >> 3) - g.cell_off;
+        const int nc = g.nc;
+        const int ix = cell % nc, iy = (cell / nc) % nc, iz = cell / (nc * nc);
+        const double cx = centre64(ix, g.L64), cy = centre64(iy, g.L64), cz = centre64(iz, g.L64);
+        a.pos4[p] = make_float4((float)(x - cx), (float)(y - cy), (float)(z - cz), h);
+    }
     if (a.d_dt) {
         const double ph = 0.5 * *a.d_dt;
         a.vel4[p] = make_float4((float)(vx + (double)ax * ph), (float)(vy + (double)ay * ph),
@@ -584,12 +598,21 @@ int plan_from_hmax(sph_ctx *ctx)
         const int64_t np = ctx->box_off[b + 1] - ctx->box_off[b];
         float hmax = np > 0 ? ctx->h_box_hmax[b] : (float)(box / 4.0);  // empty box: coarsest grid
         if (!(hmax > 0.f) || !isfinite(hmax)) return fail(ctx, SPH_ERR_NAN, "smoothing lengths must be finite and > 0");
-        if ((double)hmax > box / 3.0)
-            return fail(ctx, SPH_ERR_H_EXCEEDS_CELL, "max h exceeds box/3: no periodic grid with >= 3 cells");
         int nc = (int)floor(box / ((double)hmax * (double)ctx->p.cell_factor));
         const int cap_n = (int)floor(cbrt(8.0 * (double)std::max<int64_t>(np, 1)));
-        nc = std::min(nc, std::min(kMaxNc, std::max(3, cap_n)));
-        if (nc < 3) nc = 3;  // hmax <= box/3 guarantees cells of side box/3 hold the support
+        if (ctx->adaptive) {
+            // the leaf lists take every periodic image of the 27 top cells around a
+            // leaf, so one or two top cells per side are fine; the minimum-image
+            // convention still needs h below half the box
+            if ((double)hmax >= 0.5 * box * (1.0 - 1e-6))
+                return fail(ctx, SPH_ERR_H_EXCEEDS_CELL, "max h reaches box/2: no unique periodic image");
+            nc = std::max(1, std::min(nc, std::min(kMaxNc, std::max(1, cap_n))));
+        } else {
+            if ((double)hmax > box / 3.0)
+                return fail(ctx, SPH_ERR_H_EXCEEDS_CELL, "max h exceeds box/3: no periodic grid with >= 3 cells");
+            nc = std::min(nc, std::min(kMaxNc, std::max(3, cap_n)));
+            if (nc < 3) nc = 3;  // hmax <= box/3 guarantees cells of side box/3 hold the support
+        }
         hb[b].p_begin = (int)ctx->box_off[b];
         hb[b].p_end = (int)ctx->box_off[b + 1];
         hb[b].cell_off = (int)cells;
@@ -618,10 +641,44 @@ int plan_from_hmax(sph_ctx *ctx)
     return SPH_OK;
 }
 
+// Gather every particle array into the sorted order held in ctx->vals and copy it
+// back in place; cell_pos: also write pos4 relative to the uniform cell centres
+// (keys in ctx->keys), else pos4 is written by the caller.
+int permute_particles(sph_ctx *ctx, sph_particles *parts, bool cell_pos)
+{
+    const int n = (int)ctx->n;
+    if (n <= 0) return SPH_OK;
+    GatherArgs ga;
+    ga.P = *parts;
+    ga.perm = ctx->vals;
+    ga.skeys = cell_pos ? ctx->keys : nullptr;
+    ga.s64 = ctx->s64;
+    ga.s32 = ctx->s32;
+    ga.cap = ctx->cap;
+    ga.ids_in = ctx->ids;
+    ga.ids_out = ctx->ids_tmp;
+    ga.ids_valid = ctx->ids_valid ? 1 : 0;
+    ga.pos4 = ctx->pos4;
+    ga.vel4 = ctx->vel4;
+    ga.upred = ctx->upred;
+    ga.d_dt = ctx->predict ? ctx->d_dt : nullptr;
+    ga.n = n;
+    ga.nb = ctx->n_boxes;
+    ga.bx = ctx->d_boxes;
+    k_gather<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(ga);
+    SPH_LAUNCH(ctx, "gather");
+    k_copy_back<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(*parts, ctx->s64, ctx->s32, ctx->ids_tmp, ctx->ids,
+                                                             ctx->cap, n);
+    SPH_LAUNCH(ctx, "copy back");
+    ctx->ids_valid = true;
+    return SPH_OK;
+}
+
 // Bin, sort and permute with the current plan: no host synchronisation.
 int build_planned(sph_ctx *ctx, sph_particles *parts)
 {
     if (!ctx->planned) return fail(ctx, SPH_ERR_STATE, "no cell plan");
+    if (ctx->adaptive) return build_tree(ctx, parts);
     const int n = (int)ctx->n;
     const Grid &g = ctx->grid;
     int rc;
@@ -631,29 +688,8 @@ int build_planned(sph_ctx *ctx, sph_particles *parts)
         SPH_LAUNCH(ctx, "wrap/key");
         rc = radix_sort(ctx, n, g.key_bits);
         if (rc) return rc;
-        GatherArgs ga;
-        ga.P = *parts;
-        ga.perm = ctx->vals;
-        ga.skeys = ctx->keys;
-        ga.s64 = ctx->s64;
-        ga.s32 = ctx->s32;
-        ga.cap = ctx->cap;
-        ga.ids_in = ctx->ids;
-        ga.ids_out = ctx->ids_tmp;
-        ga.ids_valid = ctx->ids_valid ? 1 : 0;
-        ga.pos4 = ctx->pos4;
-        ga.vel4 = ctx->vel4;
-        ga.upred = ctx->upred;
-        ga.d_dt = ctx->predict ? ctx->d_dt : nullptr;
-        ga.n = n;
-        ga.nb = ctx->n_boxes;
-        ga.bx = ctx->d_boxes;
-        k_gather<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(ga);
-        SPH_LAUNCH(ctx, "gather");
-        k_copy_back<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(*parts, ctx->s64, ctx->s32, ctx->ids_tmp,
-                                                                 ctx->ids, ctx->cap, n);
-        SPH_LAUNCH(ctx, "copy back");
-        ctx->ids_valid = true;
+        rc = permute_particles(ctx, parts, true);
+        if (rc) return rc;
     }
     k_cell_start<<<blocks_for(g.n_cells + 1, 256), 256, 0, ctx->stream>>>(ctx->keys, n, g.n_cells, ctx->cell_start);
     SPH_LAUNCH(ctx, "cell start");
@@ -746,11 +782,11 @@ extern "C" int sph_sort_keys_static(const uint32_t *keys_in, uint32_t *keys_out,
         const bool to_out = ((passes - 1 - p) % 2) == 0;
         uint32_t *kout = to_out ? keys_out : sk, *vout = to_out ? perm_out : sv;
         const int shift = 8 * p;
-        k_radix_hist<<<ntiles, kRsThreads, 0, st>>>(kin, nn, shift, hist, ntiles);
+        k_radix_hist<uint32_t><<<ntiles, kRsThreads, 0, st>>>(kin, nn, shift, hist, ntiles);
         k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(hist, nh, aux);
         k_scan_top<<<1, kScanThreads, 0, st>>>(aux, nb);
         k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(hist, hist, nh, aux);
-        k_radix_scatter<<<ntiles, kRsThreads, 0, st>>>(kin, vin, kout, vout, nn, shift, hist, ntiles);
+        k_radix_scatter<uint32_t><<<ntiles, kRsThreads, 0, st>>>(kin, vin, kout, vout, nn, shift, hist, ntiles);
         kin = kout;
         vin = vout;
     }

@@ -38,7 +38,7 @@ constexpr float kPruneMargin = 2.44140625e-04f;  // 2^-12
 // device counters (unsigned long long slots)
 enum Counter {
     C_UNCONV = 0,     // unconverged particles after the last density pass
-    C_HFLAG = 1,      // some h outgrew twice the planned cell side
+    C_HFLAG = 1,      // 1: some h outgrew what the cells hold; 2 (adaptive): some h shrank far below its leaf's
     C_DPAIRS = 2,     // density interactions
     C_FPAIRS = 3,     // force interactions
     C_DCAND = 4,      // density candidate tests
@@ -59,6 +59,52 @@ struct BoxDev {
     double s;            // nc / box
     float L32;           // cell side, FP32
     float hplan;         // max h the grid was planned for
+};
+
+// Adaptive cells: a leaf's neighbour list holds every leaf whose bounding box comes
+// within kTreeReach x (the larger of the two leaves' largest h at build time), so
+// the lists stay exact while no h grows beyond kTreeReach x its leaf's build value.
+constexpr float kTreeReach = 1.25f;
+// ... and a leaf whose particles' h fell below kTreeShrink x its build value is
+// worth refining: the density pass asks for a rebuild
+constexpr float kTreeShrink = 0.45f;
+
+// octree node inside a top cell: a contiguous range of the sorted particles
+struct TreeNode {
+    int lo, hi;        // particle slots [lo, hi)
+    int child;         // first child node (children are consecutive), -1 for a leaf
+    int nchild;
+    int top;           // global top-cell id
+    int level;         // 0 = the top cell itself
+    unsigned long long prefix;  // Morton prefix inside the top cell (3 bits per level)
+    float hmax;        // largest h of its particles
+    float bx0, by0, bz0, bx1, by1, bz1;  // bounding box, relative to the top-cell centre
+};
+
+// adaptive cells (sph_tree.cu): arrays and their capacities
+struct AdaptiveTree {
+    TreeNode *nodes = nullptr;
+    int *front = nullptr, *front2 = nullptr, *bounds = nullptr, *node_leaf = nullptr, *node_at = nullptr;
+    uint32_t *nkids = nullptr;
+    int *top_node = nullptr;   // root node of every top cell (-1: empty)
+    int *leaf_of = nullptr;    // leaf of every particle slot
+    int *leaf_node = nullptr;
+    int2 *leaf_rng = nullptr;  // particle slots of every leaf
+    double *leaf_cen = nullptr; // absolute centre of every leaf (3 per leaf)
+    float *leaf_h = nullptr;     // largest h per leaf when the tree was built
+    float *leaf_hc = nullptr;    // largest current h per leaf (tree_reach)
+    float *leaf_reach = nullptr; // force reach per leaf: max current h over the leaf and its list
+    float *leaf_scale = nullptr; // coordinate scale of the leaf's pair arithmetic (FP32 band width)
+    uint32_t *list_off = nullptr; // neighbour-list offsets, n_leaves + 1
+    float4 *list = nullptr;     // {offset between leaf centres, neighbour leaf}
+    uint32_t *h_u32 = nullptr;  // pinned scratch for host reads
+    int *h_i32 = nullptr;
+    int64_t cap_keys = 0, cap_keys2 = 0, cap_leaf_of = 0, cap_node_at = 0, cap_top = 0, cap_nodes = 0,
+            cap_front = 0, cap_front2 = 0, cap_bounds = 0, cap_nkids = 0, cap_node_leaf = 0, cap_leaf_node = 0,
+            cap_leaf_rng = 0, cap_leaf_cen = 0, cap_leaf_h = 0, cap_leaf_hc = 0, cap_leaf_reach = 0,
+            cap_leaf_scale = 0, cap_list_off = 0, cap_list = 0;
+    int n_nodes = 0, n_leaves = 0;
+    int64_t n_entries = 0;
 };
 
 struct Grid {
@@ -89,12 +135,16 @@ struct sph_ctx {
     uint64_t *ngb_hash = nullptr;
     // sort
     uint32_t *keys = nullptr, *keys_alt = nullptr, *vals = nullptr, *vals_alt = nullptr;
+    uint64_t *keys64 = nullptr, *keys64_alt = nullptr;  // adaptive cells (allocated on first use)
     uint32_t *hist = nullptr;  // 256 * n_sort_tiles
     uint32_t *scan_aux = nullptr;
     int64_t hist_cap = 0;
     // permutation scratch (gather targets before the copy back)
     double *s64 = nullptr;  // 6 * cap
     float *s32 = nullptr;   // 8 * cap
+    // adaptive cells (SPH_FLAG_ADAPTIVE)
+    bool adaptive = false;
+    sph::AdaptiveTree tree;
     // boxes and their cell grids
     int n_boxes = 1;
     std::vector<int64_t> box_off;     // host, n_boxes + 1
@@ -193,6 +243,11 @@ int build_cells(sph_ctx *ctx, sph_particles *parts);            // sph_cells.cu 
 int build_planned(sph_ctx *ctx, sph_particles *parts);          // sph_cells.cu (no host read)
 int box_max_h(sph_ctx *ctx, const float *h);                    // sph_cells.cu
 int cell_reach(sph_ctx *ctx);  // cell_tmp = max h within two cells   // sph_cells.cu
+int permute_particles(sph_ctx *ctx, sph_particles *parts, bool cell_pos);  // sph_cells.cu
+int build_tree(sph_ctx *ctx, sph_particles *parts);             // sph_tree.cu
+int tree_reach(sph_ctx *ctx);                                   // sph_tree.cu
+int tree_cell_keys_out(sph_ctx *ctx, int32_t *dev_keys);        // sph_tree.cu
+void free_tree(sph_ctx *ctx);                                   // sph_tree.cu
 int cell_keys_out(sph_ctx *ctx, int32_t *dev_keys);             // sph_cells.cu
 int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool active_list);  // sph_pairs.cu
 int compact_active_tiles(sph_ctx *ctx);                                    // sph_pairs.cu
@@ -206,6 +261,7 @@ int conserved_device(sph_ctx *ctx, sph_particles *parts);                  // sp
 int conserved_read(sph_ctx *ctx, sph_conserved *out);                      // sph_integrate.cu
 int cfl_dt(sph_ctx *ctx, sph_particles *parts, double *dt_out);            // sph_integrate.cu
 int exclusive_scan_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n);  // sph_cells.cu
+int radix_sort64(sph_ctx *ctx, int n, int key_bits);                                   // sph_cells.cu
 
 // FP32 pair math ---------------------------------------------------------------
 

@@ -83,6 +83,12 @@ struct DensityArgs {
     uint64_t *ngb_hash;
     unsigned long long *counters;
     const BoxDev *__restrict__ boxes;
+    // adaptive cells: tile.x is a leaf, sources come from its neighbour list
+    const uint32_t *__restrict__ list_off;
+    const float4 *__restrict__ list;
+    const int2 *__restrict__ leaf_rng;
+    const float *__restrict__ leaf_scale;
+    const float *__restrict__ leaf_hb;
     double box;
     float n_ngb_target, h_tol, gamma;
     int use_balsara;
@@ -143,7 +149,7 @@ __device__ __forceinline__ float spline_dw_u(float q)
     return fmaf(24.f * b, b, -6.f * a * a);
 }
 
-template <int TW, bool HASH>
+template <int TW, bool HASH, bool LIST>
 __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
 {
     constexpr int TPW = 32 / TW;
@@ -185,9 +191,10 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
         const float hmax = tile_max<TW>(hi);
         const BoxDev bx = a.boxes[tile.w];
         const int nc = bx.nc;
-        const float L = bx.L32;
+        // coordinate scale of the FP32 arithmetic: the cell side, or the leaf's scale
+        const float L = LIST ? a.leaf_scale[tile.x] : bx.L32;
         // stencil radius (cells) that holds the tile's cutoff; warp-uniform
-        const int R = (int)__reduce_max_sync(kFull, hmax * (1.f + kPruneMargin) > L ? 2u : 1u);
+        const int R = LIST ? 1 : (int)__reduce_max_sync(kFull, hmax * (1.f + kPruneMargin) > L ? 2u : 1u);
         // grown so that pairs the FP64 band re-decision may accept are never pruned
         const float reach2 = hmax * hmax * (1.f + kPruneMargin) + 2.f * kBandK * hmax * (hmax + L);
         // r^2 below lob: neighbour; above hib: not; in between: decided in FP64.
@@ -274,7 +281,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
         // the 27 cell ranges of the tile, fetched at once: lane tl holds cells tl, tl + TW
         // (radius-2 stencils, for h beyond the planned cell, load ranges one by one)
         int cs0 = 0, ce0 = 0, cs1 = 0, ce1 = 0;
-        if (live && R == 1) {
+        if (!LIST && live && R == 1) {
             if (tl < 27) {
                 const int cb = bx.cell_off +
                                (wrapc(iz + kOrder[tl][2], nc) * nc + wrapc(iy + kOrder[tl][1], nc)) * nc +
@@ -292,13 +299,33 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
             }
         }
         // stage chunk after chunk; one flush site (keeps the kernel small)
+        // (adaptive cells: the tile's list entries, each a leaf and its offset)
+        int e0 = 0, ne = 0;
+        if (LIST && live) {
+            e0 = (int)a.list_off[tile.x];
+            ne = (int)a.list_off[tile.x + 1] - e0;
+        }
         int o = -1, ch = 0, nchunk = 0, bs = 0, be = 0;
-        const int ncell = R == 1 ? 27 : 125;
+        const int ncell = LIST ? (int)__reduce_max_sync(kFull, (unsigned)ne) : (R == 1 ? 27 : 125);
         float shx = 0.f, shy = 0.f, shz = 0.f;
         for (;;) {
             while (ch >= nchunk && o < ncell - 1) {
                 ++o;
                 ch = 0;
+                if (LIST) {
+                    bs = be = 0;
+                    if (o < ne) {
+                        const float4 en = a.list[e0 + o];
+                        const int2 r = a.leaf_rng[__float_as_int(en.w)];
+                        bs = r.x;
+                        be = r.y;
+                        shx = en.x;
+                        shy = en.y;
+                        shz = en.z;
+                    }
+                    nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
+                    continue;
+                }
                 int ox, oy, oz;
                 if (R == 1) {
                     const int src = o < TW ? o : o - TW;
@@ -364,49 +391,70 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
             atomicAdd(a.counters + C_DCAND, cands);
             atomicAdd(a.counters + C_DTARGETS, (unsigned long long)__popc(amask));
         }
-        if (!act) continue;
 
-        const float hinv3 = hinv * hinv * hinv, hinv4 = hinv3 * hinv;
-        const float rho = kSigma * hinv3 * (rho_s - rho_c);
-        const float nw_ = kSigma * kFourPi3 * (sw_s - sw_c);
-        const float dnw_dh = -kSigma * kFourPi3 * sqdw * hinv;
-        const float drho_dh = -kSigma * hinv4 * drho;
-        const float divv = -kSigma * hinv4 * dv / rho;
-        const float curl = kSigma * hinv4 * sqrtf(cx * cx + cy * cy + cz * cz) / rho;
-        const float g = nw_ - a.n_ngb_target;
-        const bool conv = fabsf(g) <= a.h_tol * a.n_ngb_target;
-        if (!conv && !a.last_pass) {
-            float hn = dnw_dh > 0.f ? hi - g / dnw_dh : (g < 0.f ? 2.f * hi : 0.5f * hi);
-            hn = fminf(fmaxf(hn, 0.5f * hi), 2.f * hi);
-            a.h[i] = hn;
-            atomicAdd(a.counters + C_UNCONV, 1ull);
-            // beyond the radius-2 stencil of its cell: the grid must be planned again
-            if ((double)hn > 2.0 * bx.L64 * (1.0 - 1e-6)) atomicOr(a.counters + C_HFLAG, 1ull);
-            continue;
+        // bit 0: not converged; bit 1: h beyond what the cells hold (rebuild needed);
+        // bit 2 (adaptive): h far below its leaf's build value (rebuild worthwhile)
+        unsigned flag = 0u;
+        if (act) {
+            const float hinv3 = hinv * hinv * hinv, hinv4 = hinv3 * hinv;
+            const float rho = kSigma * hinv3 * (rho_s - rho_c);
+            const float nw_ = kSigma * kFourPi3 * (sw_s - sw_c);
+            const float dnw_dh = -kSigma * kFourPi3 * sqdw * hinv;
+            const float drho_dh = -kSigma * hinv4 * drho;
+            const float divv = -kSigma * hinv4 * dv / rho;
+            const float curl = kSigma * hinv4 * sqrtf(cx * cx + cy * cy + cz * cz) / rho;
+            const float g = nw_ - a.n_ngb_target;
+            const bool conv = fabsf(g) <= a.h_tol * a.n_ngb_target;
+            if (!conv && !a.last_pass) {
+                float hn = dnw_dh > 0.f ? hi - g / dnw_dh : (g < 0.f ? 2.f * hi : 0.5f * hi);
+                hn = fminf(fmaxf(hn, 0.5f * hi), 2.f * hi);
+                // adaptive cells take h up to just below half the box (the minimum
+                // image); a step past it is cut back there instead of failing
+                if (LIST) hn = fminf(hn, (float)(0.5 * a.box) * (1.f - 1e-5f));
+                a.h[i] = hn;
+                flag = 1u;
+                if (LIST) {
+                    // beyond what its leaf's list or the adjacent top cells hold
+                    const float hb = a.leaf_hb[tile.x];
+                    const float lim = fminf(fminf(kTreeReach * hb, bx.L32), (float)(0.5 * a.box));
+                    if (hn > lim * (1.f - 1e-6f)) flag |= 2u;
+                    else if (hn < kTreeShrink * hb) flag |= 4u;
+                } else if ((double)hn > 2.0 * bx.L64 * (1.0 - 1e-6)) {
+                    flag |= 2u;  // beyond the radius-2 stencil of its cell
+                }
+            } else {
+                if (!conv) flag = 1u;
+                a.active[i] = 0;
+                // quantities needed before the pressure gradient (EOS, grad-h, Balsara)
+                const float u = a.upred[i];
+                const float gam = a.gamma;
+                const float P = (gam - 1.f) * rho * u;
+                const float cs = sqrtf(gam * (gam - 1.f) * u);
+                const float fgh = 1.f / (1.f + hi / (3.f * rho) * drho_dh);
+                float Bq = 1.f;
+                if (a.use_balsara) {
+                    const float ad = fabsf(divv);
+                    const float den = ad + curl + 1e-4f * cs * hinv;
+                    Bq = den > 0.f ? ad / den : 0.f;
+                }
+                a.thermo4[i] = make_float4(rho, fgh * P / (rho * rho), cs, Bq);
+                a.rho[i] = rho;
+                a.P[i] = P;
+                a.c[i] = cs;
+                a.f[i] = fgh;
+                a.divv[i] = divv;
+                a.curl[i] = curl;
+                a.n_ngb[i] = cnt - 1;
+                if (HASH) a.ngb_hash[i] = hh - mix64((uint64_t)a.ids[i]);
+            }
         }
-        if (!conv) atomicAdd(a.counters + C_UNCONV, 1ull);
-        a.active[i] = 0;
-        // quantities needed before the pressure gradient (EOS, grad-h, Balsara)
-        const float u = a.upred[i];
-        const float gam = a.gamma;
-        const float P = (gam - 1.f) * rho * u;
-        const float cs = sqrtf(gam * (gam - 1.f) * u);
-        const float fgh = 1.f / (1.f + hi / (3.f * rho) * drho_dh);
-        float Bq = 1.f;
-        if (a.use_balsara) {
-            const float ad = fabsf(divv);
-            const float den = ad + curl + 1e-4f * cs * hinv;
-            Bq = den > 0.f ? ad / den : 0.f;
+        // one atomic per warp and counter
+        const unsigned unc = __ballot_sync(kFull, flag & 1u);
+        const unsigned fl = __reduce_or_sync(kFull, flag & 6u);
+        if (lane == 0) {
+            if (unc) atomicAdd(a.counters + C_UNCONV, (unsigned long long)__popc(unc));
+            if (fl) atomicOr(a.counters + C_HFLAG, (unsigned long long)(fl >> 1));
         }
-        a.thermo4[i] = make_float4(rho, fgh * P / (rho * rho), cs, Bq);
-        a.rho[i] = rho;
-        a.P[i] = P;
-        a.c[i] = cs;
-        a.f[i] = fgh;
-        a.divv[i] = divv;
-        a.curl[i] = curl;
-        a.n_ngb[i] = cnt - 1;
-        if (HASH) a.ngb_hash[i] = hh - mix64((uint64_t)a.ids[i]);
     }
 }
 
@@ -420,15 +468,19 @@ struct ForceArgs {
     const double *__restrict__ x;
     const double *__restrict__ y;
     const double *__restrict__ z;
-    const float *__restrict__ cell_reach;  // per global cell: max h within two cells
+    const float *__restrict__ cell_reach;  // per cell (leaf): max h of anything that can reach it
     float *ax, *ay, *az, *dudt, *vsig;
     unsigned long long *counters;
     const BoxDev *__restrict__ boxes;
+    const uint32_t *__restrict__ list_off;
+    const float4 *__restrict__ list;
+    const int2 *__restrict__ leaf_rng;
+    const float *__restrict__ leaf_scale;
     double box;
     float alpha;
 };
 
-template <int TW>
+template <int TW, bool LIST>
 __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
 {
     constexpr int TPW = 32 / TW;
@@ -471,11 +523,11 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
         const float hi = pi.w;
         const BoxDev bx = a.boxes[tile.w];
         const int nc = bx.nc;
-        const float L = bx.L32;
+        const float L = LIST ? a.leaf_scale[tile.x] : bx.L32;
         // cutoff reach of the tile: r < max(h_i, h_j) with h_j of any particle that can
         // reach its cell (a tile beyond the last has tile.x = 0, a valid cell)
         const float H = fmaxf(tile_max<TW>(hi), a.cell_reach[tile.x]);
-        const int R = (int)__reduce_max_sync(kFull, H * (1.f + kPruneMargin) > L ? 2u : 1u);
+        const int R = LIST ? 1 : (int)__reduce_max_sync(kFull, H * (1.f + kPruneMargin) > L ? 2u : 1u);
         const float bandmax = 2.f * kBandK * H * (H + L);
         const float reach2 = H * H * (1.f + kPruneMargin) + bandmax;
         const float hi2 = hi * hi;
@@ -578,7 +630,7 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
         // the 27 cell ranges of the tile, fetched at once: lane tl holds cells tl, tl + TW
         // (radius-2 stencils, for h beyond the planned cell, load ranges one by one)
         int cs0 = 0, ce0 = 0, cs1 = 0, ce1 = 0;
-        if (live && R == 1) {
+        if (!LIST && live && R == 1) {
             if (tl < 27) {
                 const int cb = bx.cell_off +
                                (wrapc(iz + kOrder[tl][2], nc) * nc + wrapc(iy + kOrder[tl][1], nc)) * nc +
@@ -596,13 +648,33 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
             }
         }
         // stage chunk after chunk; one flush site (keeps the kernel small)
+        // (adaptive cells: the tile's list entries, each a leaf and its offset)
+        int e0 = 0, ne = 0;
+        if (LIST && live) {
+            e0 = (int)a.list_off[tile.x];
+            ne = (int)a.list_off[tile.x + 1] - e0;
+        }
         int o = -1, ch = 0, nchunk = 0, bs = 0, be = 0;
-        const int ncell = R == 1 ? 27 : 125;
+        const int ncell = LIST ? (int)__reduce_max_sync(kFull, (unsigned)ne) : (R == 1 ? 27 : 125);
         float shx = 0.f, shy = 0.f, shz = 0.f;
         for (;;) {
             while (ch >= nchunk && o < ncell - 1) {
                 ++o;
                 ch = 0;
+                if (LIST) {
+                    bs = be = 0;
+                    if (o < ne) {
+                        const float4 en = a.list[e0 + o];
+                        const int2 r = a.leaf_rng[__float_as_int(en.w)];
+                        bs = r.x;
+                        be = r.y;
+                        shx = en.x;
+                        shy = en.y;
+                        shz = en.z;
+                    }
+                    nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
+                    continue;
+                }
                 int ox, oy, oz;
                 if (R == 1) {
                     const int src = o < TW ? o : o - TW;
@@ -704,18 +776,21 @@ static int smem_optin(sph_ctx *ctx)
 {
     static bool done = false;
     if (done) return SPH_OK;
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)density_smem<16>()));
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)density_smem<16>()));
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)density_smem<32>()));
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)density_smem<32>()));
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_force<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)force_smem<16>()));
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_force<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)force_smem<32>()));
+    const int d16 = (int)density_smem<16>(), d32 = (int)density_smem<32>();
+    const int f16 = (int)force_smem<16>(), f32 = (int)force_smem<32>();
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<16, false, false>, at, d16));
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<16, true, false>, at, d16));
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<32, false, false>, at, d32));
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<32, true, false>, at, d32));
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<16, false, true>, at, d16));
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<16, true, true>, at, d16));
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<32, false, true>, at, d32));
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<32, true, true>, at, d32));
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_force<16, false>, at, f16));
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_force<32, false>, at, f32));
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_force<16, true>, at, f16));
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_force<32, true>, at, f32));
     done = true;
     return SPH_OK;
 }
@@ -726,7 +801,8 @@ static int pair_grid(sph_ctx *ctx, int blocks_per_sm)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (sms <= 0) sms = 148;
     // persistent grid: warps stride over the tile groups
-    int64_t want = ((int64_t)ctx->n / ctx->tile_w + ctx->grid.n_cells) / (kPairThreads / 32) + 1;
+    const int64_t cells = ctx->adaptive ? ctx->tree.n_leaves : ctx->grid.n_cells;
+    int64_t want = ((int64_t)ctx->n / ctx->tile_w + cells) / (kPairThreads / 32) + 1;
     int64_t g = std::min<int64_t>((int64_t)sms * blocks_per_sm, want);
     return (int)std::max<int64_t>(g, 1);
 }
@@ -787,6 +863,11 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool ac
     a.ngb_hash = ctx->ngb_hash;
     a.counters = ctx->counters;
     a.boxes = ctx->d_boxes;
+    a.list_off = ctx->tree.list_off;
+    a.list = ctx->tree.list;
+    a.leaf_rng = ctx->tree.leaf_rng;
+    a.leaf_scale = ctx->tree.leaf_scale;
+    a.leaf_hb = ctx->tree.leaf_h;
     a.box = ctx->p.box_size;
     a.n_ngb_target = ctx->p.n_ngb;
     a.h_tol = ctx->p.h_tol;
@@ -799,14 +880,25 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool ac
     const bool hash = (ctx->p.flags & SPH_FLAG_NGB_HASH) != 0;
     cudaEvent_t end = nullptr;
     timer_begin(ctx, 0, &end);
+    const bool list = ctx->adaptive;
     if (ctx->tile_w == 32) {
         const size_t sm = density_smem<32>();
-        if (hash) k_density<32, true><<<g, kPairThreads, sm, ctx->stream>>>(a);
-        else k_density<32, false><<<g, kPairThreads, sm, ctx->stream>>>(a);
+        if (list) {
+            if (hash) k_density<32, true, true><<<g, kPairThreads, sm, ctx->stream>>>(a);
+            else k_density<32, false, true><<<g, kPairThreads, sm, ctx->stream>>>(a);
+        } else {
+            if (hash) k_density<32, true, false><<<g, kPairThreads, sm, ctx->stream>>>(a);
+            else k_density<32, false, false><<<g, kPairThreads, sm, ctx->stream>>>(a);
+        }
     } else {
         const size_t sm = density_smem<16>();
-        if (hash) k_density<16, true><<<g, kPairThreads, sm, ctx->stream>>>(a);
-        else k_density<16, false><<<g, kPairThreads, sm, ctx->stream>>>(a);
+        if (list) {
+            if (hash) k_density<16, true, true><<<g, kPairThreads, sm, ctx->stream>>>(a);
+            else k_density<16, false, true><<<g, kPairThreads, sm, ctx->stream>>>(a);
+        } else {
+            if (hash) k_density<16, true, false><<<g, kPairThreads, sm, ctx->stream>>>(a);
+            else k_density<16, false, false><<<g, kPairThreads, sm, ctx->stream>>>(a);
+        }
     }
     timer_end(ctx, end);
     SPH_LAUNCH(ctx, "density kernel");
@@ -826,7 +918,11 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts)
     a.x = parts->x;
     a.y = parts->y;
     a.z = parts->z;
-    a.cell_reach = ctx->cell_tmp;
+    a.cell_reach = ctx->adaptive ? ctx->tree.leaf_reach : ctx->cell_tmp;
+    a.list_off = ctx->tree.list_off;
+    a.list = ctx->tree.list;
+    a.leaf_rng = ctx->tree.leaf_rng;
+    a.leaf_scale = ctx->tree.leaf_scale;
     a.ax = parts->ax;
     a.ay = parts->ay;
     a.az = parts->az;
@@ -841,8 +937,13 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts)
     const int g = pair_grid(ctx, 2);
     cudaEvent_t end = nullptr;
     timer_begin(ctx, 1, &end);
-    if (ctx->tile_w == 32) k_force<32><<<g, kPairThreads, force_smem<32>(), ctx->stream>>>(a);
-    else k_force<16><<<g, kPairThreads, force_smem<16>(), ctx->stream>>>(a);
+    if (ctx->adaptive) {
+        if (ctx->tile_w == 32) k_force<32, true><<<g, kPairThreads, force_smem<32>(), ctx->stream>>>(a);
+        else k_force<16, true><<<g, kPairThreads, force_smem<16>(), ctx->stream>>>(a);
+    } else {
+        if (ctx->tile_w == 32) k_force<32, false><<<g, kPairThreads, force_smem<32>(), ctx->stream>>>(a);
+        else k_force<16, false><<<g, kPairThreads, force_smem<16>(), ctx->stream>>>(a);
+    }
     timer_end(ctx, end);
     SPH_LAUNCH(ctx, "force kernel");
     ctx->st.force_passes++;

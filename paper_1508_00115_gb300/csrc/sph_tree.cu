@@ -1,0 +1,653 @@
+// sph_tree.cu -- adaptive cells (Theuns et al. 2015, Sec. 3.1: the dynamic range of
+// h calls for an adaptive mesh of cells; the tree is cut off at cells of ~100
+// particles, and neighbouring cells are themselves found with a tree).
+//
+// Top-level cells are the uniform per-box grid (side >= cell_factor * max h), so a
+// particle's neighbours always lie in the 27 top cells around it.  Inside each top
+// cell particles are ordered by a 3 x 14-bit Morton code; every octree node is then
+// a contiguous range of the sorted particles.  Nodes are refined top-down, one level
+// per step, while they hold more than kLeafMax particles (32: one or two tiles).
+// Unlike the paper's cells, a leaf may be smaller than the h of its particles: its
+// neighbours need not lie in the adjacent leaves, because every leaf carries an
+// explicit list of the leaves within reach.  For every leaf the list
+// holds every leaf met in the 27 surrounding top-cell subtrees whose bounding box
+// comes within reach -- max of the two leaves' largest h, grown by kTreeReach so
+// that h may grow during the density iteration -- and every entry carries the FP32
+// offset between the two leaf centres (computed in FP64, periodic image included).
+// Particle positions are stored relative to their leaf's centre, so FP32 keeps
+// ~2^-24 of a leaf side even where h is 10^-3 of the top cell.
+#include <math.h>
+
+#include <algorithm>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+constexpr int kMortonBits = 14;       // per axis, inside a top cell
+constexpr int kMortonShift = 3 * kMortonBits;
+constexpr int kLeafMax = 32;          // refine nodes holding more particles than this
+
+__device__ __forceinline__ uint64_t spread3(uint32_t v)  // 14 bits -> every third bit
+{
+    uint64_t x = v & 0x3fffu;
+    x = (x | (x << 16)) & 0x0000ff0000ffull;
+    x = (x | (x << 8)) & 0x00f00f00f00f00full;
+    x = (x | (x << 4)) & 0x0c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x249249249249249ull;
+    return x;
+}
+__device__ __forceinline__ uint32_t compact3(uint64_t x)  // inverse of spread3
+{
+    x &= 0x249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x0c30c30c30c30c3ull;
+    x = (x ^ (x >> 4)) & 0x00f00f00f00f00full;
+    x = (x ^ (x >> 8)) & 0x0000ff0000ffull;
+    x = (x ^ (x >> 16)) & 0x3fffull;
+    return (uint32_t)x;
+}
+
+__device__ __forceinline__ double twrap(double v, double box)
+{
+    if (v >= 0.0 && v < box) return v;
+    double w = __dsub_rn(v, __dmul_rn(box, floor(__ddiv_rn(v, box))));
+    if (w < 0.0) w = __dadd_rn(w, box);
+    if (w >= box) w = __dsub_rn(w, box);
+    if (w < 0.0 || w >= box) w = 0.0;
+    return w;
+}
+
+__device__ __forceinline__ int tbox_of_slot(int p, const BoxDev *__restrict__ bx, int nb)
+{
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bx[mid].p_begin <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int tbox_of_cell(int c, const BoxDev *__restrict__ bx, int nb)
+{
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bx[mid].cell_off <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+__device__ __forceinline__ int tcell_of(double v, double s, int nc)
+{
+    int c = (int)floor(__dmul_rn(v, s));
+    return c < 0 ? 0 : (c > nc - 1 ? nc - 1 : c);
+}
+
+// key = top cell << 42 | Morton code of the position inside the top cell
+__global__ void k_tree_keys(double *x, double *y, double *z, int n, int nb, double box,
+                            const BoxDev *__restrict__ bxs, uint64_t *__restrict__ keys)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const BoxDev g = bxs[nb == 1 ? 0 : tbox_of_slot(i, bxs, nb)];
+    const double px = twrap(x[i], box), py = twrap(y[i], box), pz = twrap(z[i], box);
+    x[i] = px;
+    y[i] = py;
+    z[i] = pz;
+    const int ix = tcell_of(px, g.s, g.nc), iy = tcell_of(py, g.s, g.nc), iz = tcell_of(pz, g.s, g.nc);
+    const double sub = (double)(1 << kMortonBits) * g.s;  // sub-cells per unit length
+    auto subi = [&](double p, int c) {
+        int v = (int)floor((p - (double)c * g.L64) * sub);
+        return (uint32_t)(v < 0 ? 0 : (v > (1 << kMortonBits) - 1 ? (1 << kMortonBits) - 1 : v));
+    };
+    const uint64_t m = spread3(subi(px, ix)) | (spread3(subi(py, iy)) << 1) | (spread3(subi(pz, iz)) << 2);
+    const uint64_t top = (uint64_t)(g.cell_off + (iz * g.nc + iy) * g.nc + ix);
+    keys[i] = (top << kMortonShift) | m;
+}
+
+__global__ void k_top_start(const uint64_t *__restrict__ k, int n, int64_t ntop, int *__restrict__ cs)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > ntop) return;
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int64_t)(k[mid] >> kMortonShift) < c) lo = mid + 1;
+        else hi = mid;
+    }
+    cs[c] = lo;
+}
+
+__global__ void k_nonempty(const int *__restrict__ cs, int64_t ntop, uint32_t *__restrict__ f)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < ntop) f[c] = cs[c + 1] > cs[c] ? 1u : 0u;
+}
+
+// roots: one node per non-empty top cell, numbered in cell order
+__global__ void k_roots(const int *__restrict__ cs, int64_t ntop, const uint32_t *__restrict__ off,
+                        TreeNode *__restrict__ nodes, int *__restrict__ top_node, int *__restrict__ front)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ntop) return;
+    if (cs[c + 1] == cs[c]) {
+        top_node[c] = -1;
+        return;
+    }
+    const int id = (int)off[c];
+    TreeNode t;
+    t.lo = cs[c];
+    t.hi = cs[c + 1];
+    t.child = -1;
+    t.nchild = 0;
+    t.top = (int)c;
+    t.level = 0;
+    t.prefix = 0;
+    nodes[id] = t;
+    top_node[c] = id;
+    front[id] = id;
+}
+
+// per frontier node: largest h and bounding box (relative to the top-cell centre) of
+// its particles, and its non-empty children if it is to be refined.  One warp/node.
+__global__ void k_node_stats(const int *__restrict__ front, int nfront, TreeNode *__restrict__ nodes,
+                             const uint64_t *__restrict__ keys, const double *__restrict__ x,
+                             const double *__restrict__ y, const double *__restrict__ z, const float *__restrict__ h,
+                             const BoxDev *__restrict__ bxs, int nb, int *__restrict__ bounds,
+                             uint32_t *__restrict__ nkids)
+{
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= nfront) return;
+    const int id = front[w];
+    TreeNode t = nodes[id];
+    const BoxDev g = bxs[nb == 1 ? 0 : tbox_of_cell(t.top, bxs, nb)];
+    const int loc = t.top - g.cell_off;
+    const double cx = ((double)(loc % g.nc) + 0.5) * g.L64, cy = ((double)((loc / g.nc) % g.nc) + 0.5) * g.L64,
+                 cz = ((double)(loc / (g.nc * g.nc)) + 0.5) * g.L64;
+    float hm = 0.f, x0 = 1e30f, y0 = 1e30f, z0 = 1e30f, x1 = -1e30f, y1 = -1e30f, z1 = -1e30f;
+    for (int p = t.lo + lane; p < t.hi; p += 32) {
+        hm = fmaxf(hm, h[p]);
+        const float px = (float)(x[p] - cx), py = (float)(y[p] - cy), pz = (float)(z[p] - cz);
+        x0 = fminf(x0, px);
+        x1 = fmaxf(x1, px);
+        y0 = fminf(y0, py);
+        y1 = fmaxf(y1, py);
+        z0 = fminf(z0, pz);
+        z1 = fmaxf(z1, pz);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        hm = fmaxf(hm, __shfl_xor_sync(kFull, hm, o));
+        x0 = fminf(x0, __shfl_xor_sync(kFull, x0, o));
+        x1 = fmaxf(x1, __shfl_xor_sync(kFull, x1, o));
+        y0 = fminf(y0, __shfl_xor_sync(kFull, y0, o));
+        y1 = fmaxf(y1, __shfl_xor_sync(kFull, y1, o));
+        z0 = fminf(z0, __shfl_xor_sync(kFull, z0, o));
+        z1 = fmaxf(z1, __shfl_xor_sync(kFull, z1, o));
+    }
+    // the bounding box is widened by one FP32 ulp of the top cell so that rounding of
+    // the positions above never shrinks it
+    const float pad = g.L32 * 1.2e-7f;
+    // refine while there are too many particles (down to the Morton resolution)
+    const bool split = (t.hi - t.lo) > kLeafMax && t.level < kMortonBits;
+    int cnt = 0;
+    if (split) {
+        // child boundaries: first slot whose next Morton digit is >= k (k = 1..7)
+        const int sh = 3 * (kMortonBits - 1 - t.level);
+        int b[9];
+        b[0] = t.lo;
+        b[8] = t.hi;
+        for (int k = 1; k < 8; ++k) {
+            int lo = t.lo, hi = t.hi;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((int)((keys[mid] >> sh) & 7u) < k) lo = mid + 1;
+                else hi = mid;
+            }
+            b[k] = lo;
+        }
+        if (lane == 0)
+            for (int k = 0; k < 9; ++k) bounds[9 * w + k] = b[k];
+        for (int k = 0; k < 8; ++k) cnt += b[k + 1] > b[k] ? 1 : 0;
+    }
+    if (lane == 0) {
+        t.hmax = hm;
+        t.bx0 = x0 - pad;
+        t.by0 = y0 - pad;
+        t.bz0 = z0 - pad;
+        t.bx1 = x1 + pad;
+        t.by1 = y1 + pad;
+        t.bz1 = z1 + pad;
+        nodes[id] = t;
+        nkids[w] = (uint32_t)cnt;
+    }
+}
+
+// children of the refined frontier nodes, numbered in frontier order (deterministic)
+__global__ void k_make_children(const int *__restrict__ front, int nfront, TreeNode *__restrict__ nodes,
+                                const int *__restrict__ bounds, const uint32_t *__restrict__ off, uint32_t total,
+                                int base, int *__restrict__ next)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfront) return;
+    const uint32_t first = off[f], end = f + 1 < nfront ? off[f + 1] : total;
+    if (end == first) return;  // not refined: a leaf
+    const int id = front[f];
+    const int *b = bounds + 9 * f;
+    TreeNode &t = nodes[id];
+    int c = 0;
+    for (int k = 0; k < 8; ++k) {
+        if (b[k + 1] <= b[k]) continue;
+        TreeNode ch;
+        ch.lo = b[k];
+        ch.hi = b[k + 1];
+        ch.child = -1;
+        ch.nchild = 0;
+        ch.top = t.top;
+        ch.level = t.level + 1;
+        ch.prefix = (t.prefix << 3) | (uint64_t)k;
+        const int cid = base + (int)first + c;
+        nodes[cid] = ch;
+        next[first + c] = cid;
+        ++c;
+    }
+    t.child = base + (int)first;
+    t.nchild = c;
+}
+
+// flags the first slot of every leaf (leaves partition the particles)
+__global__ void k_leaf_marks(const TreeNode *__restrict__ nodes, int n_nodes, uint32_t *__restrict__ flag,
+                             int *__restrict__ node_at)
+{
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n_nodes) return;
+    const TreeNode t = nodes[id];
+    if (t.child >= 0) return;
+    flag[t.lo] = 1u;
+    node_at[t.lo] = id;
+}
+
+// leaves in particle (Morton) order: leaf id of slot p = (number of leaf starts <= p) - 1
+__global__ void k_leaves(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ excl, int n,
+                         const int *__restrict__ node_at, const TreeNode *__restrict__ nodes,
+                         const BoxDev *__restrict__ bxs, int nb, int *__restrict__ leaf_of, int *__restrict__ leaf_node,
+                         int *__restrict__ node_leaf, int2 *__restrict__ leaf_rng, double *__restrict__ leaf_cen,
+                         float *__restrict__ leaf_h)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int lid = (int)excl[p] + (int)flag[p] - 1;
+    leaf_of[p] = lid;
+    if (!flag[p]) return;
+    const int id = node_at[p];
+    const TreeNode t = nodes[id];
+    leaf_node[lid] = id;
+    node_leaf[id] = lid;
+    leaf_rng[lid] = make_int2(t.lo, t.hi);
+    leaf_h[lid] = t.hmax;
+    const BoxDev g = bxs[nb == 1 ? 0 : tbox_of_cell(t.top, bxs, nb)];
+    const int loc = t.top - g.cell_off;
+    const int ix = loc % g.nc, iy = (loc / g.nc) % g.nc, iz = loc / (g.nc * g.nc);
+    // the leaf's cube: Morton prefix at its level gives its sub-cell coordinates
+    const uint64_t pre = t.prefix << (3 * (kMortonBits - t.level));
+    const double side = g.L64 / (double)(1 << t.level);
+    const double fine = g.L64 / (double)(1 << kMortonBits);
+    const double sx = (double)compact3(pre) * fine, sy = (double)compact3(pre >> 1) * fine,
+                 sz = (double)compact3(pre >> 2) * fine;
+    leaf_cen[3 * lid + 0] = (double)ix * g.L64 + sx + 0.5 * side;
+    leaf_cen[3 * lid + 1] = (double)iy * g.L64 + sy + 0.5 * side;
+    leaf_cen[3 * lid + 2] = (double)iz * g.L64 + sz + 0.5 * side;
+}
+
+// positions relative to the leaf centre
+__global__ void k_leaf_pos(const int *__restrict__ leaf_of, const double *__restrict__ leaf_cen,
+                           const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+                           const float *__restrict__ h, int n, float4 *__restrict__ pos4)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int l = leaf_of[p];
+    pos4[p] = make_float4((float)(x[p] - leaf_cen[3 * l]), (float)(y[p] - leaf_cen[3 * l + 1]),
+                          (float)(z[p] - leaf_cen[3 * l + 2]), h[p]);
+}
+
+__global__ void k_leaf_tiles_n(const int2 *__restrict__ rng, int nl, int tw, uint32_t *__restrict__ nt)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < nl) nt[l] = (uint32_t)((rng[l].y - rng[l].x + tw - 1) / tw);
+}
+
+// tile = {leaf, first slot, count, box}
+__global__ void k_leaf_tiles(const int2 *__restrict__ rng, const int *__restrict__ leaf_node,
+                             const TreeNode *__restrict__ nodes, int nl, int tw, const uint32_t *__restrict__ off,
+                             const BoxDev *__restrict__ bxs, int nb, int4 *__restrict__ tiles, int *__restrict__ ntiles)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nl) return;
+    const int s = rng[l].x, cnt = rng[l].y - s;
+    const int box = nb == 1 ? 0 : tbox_of_cell(nodes[leaf_node[l]].top, bxs, nb);
+    int k = 0;
+    for (int b = 0; b < cnt; b += tw, ++k) tiles[off[l] + k] = make_int4(l, s + b, min(tw, cnt - b), box);
+    if (l == nl - 1) *ntiles = (int)(off[l] + k);
+}
+
+// Neighbour leaves of leaf `l`: walk the subtrees of the 27 top cells around its own,
+// keeping nodes whose bounding box is within reach.  COUNT: only count; else write
+// {offset between the leaf centres (FP32), neighbour leaf} from out[0].
+template <bool COUNT>
+__device__ int leaf_pairs(int l, const int *__restrict__ leaf_node, const TreeNode *__restrict__ nodes,
+                          const int *__restrict__ top_node, const int *__restrict__ node_leaf,
+                          const double *__restrict__ leaf_cen, const BoxDev *__restrict__ bxs, int nb, double box,
+                          float4 *__restrict__ out, float *__restrict__ scale_out)
+{
+    const TreeNode A = nodes[leaf_node[l]];
+    const BoxDev g = bxs[nb == 1 ? 0 : tbox_of_cell(A.top, bxs, nb)];
+    const int nc = g.nc, loc = A.top - g.cell_off;
+    const int ix = loc % nc, iy = (loc / nc) % nc, iz = loc / (nc * nc);
+    const float hA = A.hmax * kTreeReach;
+    // FP32 rounding of the boxes and offsets (a few ulps of the top cell) is covered
+    // by a slack added to every reach
+    const float slack = 4.8e-7f * g.L32;
+    const double cAx = leaf_cen[3 * l], cAy = leaf_cen[3 * l + 1], cAz = leaf_cen[3 * l + 2];
+    const double sideA = g.L64 / (double)(1 << A.level);
+    double scale = sideA;
+    int stack[8 * (kMortonBits + 1)];
+    int cnt = 0;
+    for (int o = 0; o < 27; ++o) {
+        const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+        int jx = ix + ox, jy = iy + oy, jz = iz + oz;
+        // periodic image: k_ * box added to the neighbour's absolute positions
+        const int kx = jx < 0 ? -1 : (jx >= nc ? 1 : 0), ky = jy < 0 ? -1 : (jy >= nc ? 1 : 0),
+                  kz = jz < 0 ? -1 : (jz >= nc ? 1 : 0);
+        jx -= kx * nc;
+        jy -= ky * nc;
+        jz -= kz * nc;
+        const int root = top_node[g.cell_off + (jz * nc + jy) * nc + jx];
+        if (root < 0) continue;
+        // offset of the neighbour top cell's centre relative to A's (FP32, multiples of L)
+        const float dx = (float)ox * g.L32, dy = (float)oy * g.L32, dz = (float)oz * g.L32;
+        int sp = 0;
+        stack[sp++] = root;
+        while (sp > 0) {
+            const int id = stack[--sp];
+            const TreeNode N = nodes[id];
+            const float gx = fmaxf(fmaxf(N.bx0 + dx - A.bx1, A.bx0 - (N.bx1 + dx)), 0.f);
+            const float gy = fmaxf(fmaxf(N.by0 + dy - A.by1, A.by0 - (N.by1 + dy)), 0.f);
+            const float gz = fmaxf(fmaxf(N.bz0 + dz - A.bz1, A.bz0 - (N.bz1 + dz)), 0.f);
+            const float reach = fmaxf(hA, N.hmax * kTreeReach) * (1.f + 1e-5f) + slack;
+            if (gx * gx + gy * gy + gz * gz >= reach * reach) continue;
+            if (N.child < 0) {
+                if (!COUNT) {
+                    const int b = node_leaf[id];
+                    const double sx = leaf_cen[3 * b] + kx * box - cAx, sy = leaf_cen[3 * b + 1] + ky * box - cAy,
+                                 sz = leaf_cen[3 * b + 2] + kz * box - cAz;
+                    out[cnt] = make_float4((float)sx, (float)sy, (float)sz, __int_as_float(b));
+                    // coordinates met in this pair's FP32 arithmetic are below
+                    // |p_i| + |p_j| + |shift| <= (sides of both leaves + shift)
+                    const double m = fmax(fabs(sx), fmax(fabs(sy), fabs(sz)));
+                    scale = fmax(scale, 0.5 * (sideA + g.L64 / (double)(1 << N.level) + m));
+                }
+                ++cnt;
+            } else {
+                for (int c = N.nchild - 1; c >= 0; --c) stack[sp++] = N.child + c;
+            }
+        }
+    }
+    if (!COUNT) *scale_out = (float)scale;
+    return cnt;
+}
+
+__global__ void k_pairs_count(int nl, const int *__restrict__ leaf_node, const TreeNode *__restrict__ nodes,
+                              const int *__restrict__ top_node, const int *__restrict__ node_leaf,
+                              const double *__restrict__ leaf_cen, const BoxDev *__restrict__ bxs, int nb, double box,
+                              uint32_t *__restrict__ cnt)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < nl) cnt[l] = (uint32_t)leaf_pairs<true>(l, leaf_node, nodes, top_node, node_leaf, leaf_cen, bxs, nb, box,
+                                                   nullptr, nullptr);
+}
+
+__global__ void k_pairs_fill(int nl, const int *__restrict__ leaf_node, const TreeNode *__restrict__ nodes,
+                             const int *__restrict__ top_node, const int *__restrict__ node_leaf,
+                             const double *__restrict__ leaf_cen, const BoxDev *__restrict__ bxs, int nb, double box,
+                             const uint32_t *__restrict__ off, float4 *__restrict__ list, float *__restrict__ scale)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < nl)
+        leaf_pairs<false>(l, leaf_node, nodes, top_node, node_leaf, leaf_cen, bxs, nb, box, list + off[l], scale + l);
+}
+
+// reach of every leaf for the force pass: its own largest h and that of every leaf in
+// its list (current h, after the density iteration)
+__global__ void k_leaf_hmax(const int2 *__restrict__ rng, int nl, const float4 *__restrict__ pos4,
+                            float *__restrict__ leaf_h)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nl) return;
+    float m = 0.f;
+    for (int p = rng[l].x; p < rng[l].y; ++p) m = fmaxf(m, pos4[p].w);
+    leaf_h[l] = m;
+}
+
+__global__ void k_leaf_reach(int nl, const uint32_t *__restrict__ off, const float4 *__restrict__ list,
+                             const float *__restrict__ leaf_h, float *__restrict__ reach)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nl) return;
+    float m = leaf_h[l];
+    for (uint32_t e = off[l]; e < off[l + 1]; ++e) m = fmaxf(m, leaf_h[__float_as_int(list[e].w)]);
+    reach[l] = m;
+}
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
+
+template <typename T>
+static int grow(sph_ctx *ctx, T *&p, int64_t &cap, int64_t need)
+{
+    if (need <= cap) return SPH_OK;
+    cudaFree(p);
+    p = nullptr;
+    const int64_t c = need + need / 4 + 1024;
+    SPH_CUDA(ctx, cudaMalloc(&p, sizeof(T) * c));
+    cap = c;
+    return SPH_OK;
+}
+
+// Build the adaptive cells for the current plan (top grids): keys, sort, permutation,
+// tree, leaves, leaf-relative positions, tiles and neighbour lists.
+int build_tree(sph_ctx *ctx, sph_particles *parts)
+{
+    AdaptiveTree &T = ctx->tree;
+    const int n = (int)ctx->n;
+    const int64_t ntop = ctx->grid.n_cells;
+    int rc;
+    int64_t np = std::max<int64_t>(ctx->cap, 1);
+    if ((rc = grow(ctx, ctx->keys64, T.cap_keys, np)) || (rc = grow(ctx, ctx->keys64_alt, T.cap_keys2, np)) ||
+        (rc = grow(ctx, T.leaf_of, T.cap_leaf_of, np)) || (rc = grow(ctx, T.node_at, T.cap_node_at, np)) ||
+        (rc = grow(ctx, T.top_node, T.cap_top, ntop + 1)))
+        return rc;
+    if (!T.h_u32) SPH_CUDA(ctx, cudaMallocHost(&T.h_u32, 16 * sizeof(uint32_t)));
+    if (!T.h_i32) SPH_CUDA(ctx, cudaMallocHost(&T.h_i32, 16 * sizeof(int)));
+    int top_bits = 1;
+    while ((1ll << top_bits) < ntop) ++top_bits;
+    if (top_bits + kMortonShift > 64) return fail(ctx, SPH_ERR_INVALID_ARG, "too many top cells for 64-bit keys");
+    if (n <= 0) {  // nothing to refine: no leaves, no tiles
+        T.n_nodes = T.n_leaves = 0;
+        T.n_entries = 0;
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->n_tiles, 0, sizeof(int), ctx->stream));
+        ctx->built = true;
+        ctx->density_valid = false;
+        ctx->st.n_cells = 0;
+        return SPH_OK;
+    }
+    {
+        k_tree_keys<<<nblk(n, 256), 256, 0, ctx->stream>>>(parts->x, parts->y, parts->z, n, ctx->n_boxes,
+                                                           ctx->p.box_size, ctx->d_boxes, ctx->keys64);
+        SPH_LAUNCH(ctx, "tree keys");
+        rc = radix_sort64(ctx, n, top_bits + kMortonShift);
+        if (rc) return rc;
+        rc = permute_particles(ctx, parts, false);  // caller arrays into sorted order
+        if (rc) return rc;
+    }
+    // top-cell ranges and roots
+    k_top_start<<<nblk(ntop + 1, 256), 256, 0, ctx->stream>>>(ctx->keys64, n, ntop, ctx->cell_start);
+    SPH_LAUNCH(ctx, "top starts");
+    k_nonempty<<<nblk(ntop, 256), 256, 0, ctx->stream>>>(ctx->cell_start, ntop, ctx->cell_tiles);
+    SPH_LAUNCH(ctx, "top nonempty");
+    rc = exclusive_scan_u32(ctx, ctx->cell_tiles, ctx->cell_tiles, ntop);
+    if (rc) return rc;
+    // roots = exclusive count before the last top cell + whether the last is non-empty
+    SPH_CUDA(ctx, cudaMemcpyAsync(&T.h_u32[0], ctx->cell_tiles + (ntop - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    SPH_CUDA(ctx, cudaMemcpyAsync(&T.h_i32[0], ctx->cell_start + (ntop - 1), sizeof(int), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const uint32_t nroot = T.h_u32[0] + (T.h_i32[0] < n ? 1u : 0u);
+    const int64_t node_cap_need = (int64_t)nroot + 4 * (int64_t)n + 64;
+    if ((rc = grow(ctx, T.nodes, T.cap_nodes, node_cap_need)) || (rc = grow(ctx, T.front, T.cap_front, node_cap_need)) ||
+        (rc = grow(ctx, T.front2, T.cap_front2, node_cap_need)) ||
+        (rc = grow(ctx, T.bounds, T.cap_bounds, 9 * node_cap_need)) ||
+        (rc = grow(ctx, T.nkids, T.cap_nkids, node_cap_need)) || (rc = grow(ctx, T.node_leaf, T.cap_node_leaf, node_cap_need)))
+        return rc;
+    k_roots<<<nblk(ntop, 256), 256, 0, ctx->stream>>>(ctx->cell_start, ntop, ctx->cell_tiles, T.nodes, T.top_node,
+                                                      T.front);
+    SPH_LAUNCH(ctx, "tree roots");
+    // refine level by level (host reads the next frontier size)
+    int n_nodes = (int)nroot, nfront = (int)nroot;
+    int *cur = T.front, *nxt = T.front2;
+    for (int level = 0; level <= kMortonBits && nfront > 0; ++level) {
+        k_node_stats<<<nblk((int64_t)nfront * 32, 256), 256, 0, ctx->stream>>>(
+            cur, nfront, T.nodes, ctx->keys64, parts->x, parts->y, parts->z, parts->h, ctx->d_boxes, ctx->n_boxes,
+            T.bounds, T.nkids);
+        SPH_LAUNCH(ctx, "node stats");
+        SPH_CUDA(ctx, cudaMemcpyAsync(&T.h_u32[1], T.nkids + (nfront - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        rc = exclusive_scan_u32(ctx, T.nkids, T.nkids, nfront);
+        if (rc) return rc;
+        SPH_CUDA(ctx, cudaMemcpyAsync(&T.h_u32[2], T.nkids + (nfront - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        const int nnext = (int)(T.h_u32[1] + T.h_u32[2]);
+        if (nnext == 0) break;
+        if ((int64_t)n_nodes + nnext > T.cap_nodes) return fail(ctx, SPH_ERR_INVALID_ARG, "tree node capacity exceeded");
+        k_make_children<<<nblk(nfront, 256), 256, 0, ctx->stream>>>(cur, nfront, T.nodes, T.bounds, T.nkids,
+                                                                    (uint32_t)nnext, n_nodes, nxt);
+        SPH_LAUNCH(ctx, "make children");
+        n_nodes += nnext;
+        nfront = nnext;
+        std::swap(cur, nxt);
+    }
+    T.n_nodes = n_nodes;
+    // leaves in particle order
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->keys, 0, sizeof(uint32_t) * std::max(n, 1), ctx->stream));
+    k_leaf_marks<<<nblk(n_nodes, 256), 256, 0, ctx->stream>>>(T.nodes, n_nodes, ctx->keys, T.node_at);
+    SPH_LAUNCH(ctx, "leaf marks");
+    rc = exclusive_scan_u32(ctx, ctx->keys, ctx->keys_alt, n);
+    if (rc) return rc;
+    SPH_CUDA(ctx, cudaMemcpyAsync(&T.h_u32[3], ctx->keys_alt + (n - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    SPH_CUDA(ctx, cudaMemcpyAsync(&T.h_u32[4], ctx->keys + (n - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const int nl = (int)(T.h_u32[3] + T.h_u32[4]);
+    T.n_leaves = nl;
+    if ((rc = grow(ctx, T.leaf_node, T.cap_leaf_node, nl + 1)) || (rc = grow(ctx, T.leaf_rng, T.cap_leaf_rng, nl + 1)) ||
+        (rc = grow(ctx, T.leaf_cen, T.cap_leaf_cen, 3 * (int64_t)nl + 3)) ||
+        (rc = grow(ctx, T.leaf_h, T.cap_leaf_h, nl + 1)) || (rc = grow(ctx, T.leaf_hc, T.cap_leaf_hc, nl + 1)) ||
+        (rc = grow(ctx, T.leaf_reach, T.cap_leaf_reach, nl + 1)) ||
+        (rc = grow(ctx, T.leaf_scale, T.cap_leaf_scale, nl + 1)) ||
+        (rc = grow(ctx, T.list_off, T.cap_list_off, nl + 2)))
+        return rc;
+    {
+        k_leaves<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->keys, ctx->keys_alt, n, T.node_at, T.nodes, ctx->d_boxes,
+                                                        ctx->n_boxes, T.leaf_of, T.leaf_node, T.node_leaf, T.leaf_rng,
+                                                        T.leaf_cen, T.leaf_h);
+        SPH_LAUNCH(ctx, "leaves");
+        k_leaf_pos<<<nblk(n, 256), 256, 0, ctx->stream>>>(T.leaf_of, T.leaf_cen, parts->x, parts->y, parts->z,
+                                                          parts->h, n, ctx->pos4);
+        SPH_LAUNCH(ctx, "leaf positions");
+    }
+    // tiles
+    if (nl > 0) {
+        k_leaf_tiles_n<<<nblk(nl, 256), 256, 0, ctx->stream>>>(T.leaf_rng, nl, ctx->tile_w, T.list_off);
+        SPH_LAUNCH(ctx, "leaf tile counts");
+        rc = exclusive_scan_u32(ctx, T.list_off, T.list_off, nl);
+        if (rc) return rc;
+        k_leaf_tiles<<<nblk(nl, 256), 256, 0, ctx->stream>>>(T.leaf_rng, T.leaf_node, T.nodes, nl, ctx->tile_w,
+                                                            T.list_off, ctx->d_boxes, ctx->n_boxes, ctx->tiles,
+                                                            ctx->n_tiles);
+        SPH_LAUNCH(ctx, "leaf tiles");
+        // neighbour lists: count, scan, fill
+        k_pairs_count<<<nblk(nl, 128), 128, 0, ctx->stream>>>(nl, T.leaf_node, T.nodes, T.top_node, T.node_leaf,
+                                                             T.leaf_cen, ctx->d_boxes, ctx->n_boxes, ctx->p.box_size,
+                                                             T.list_off);
+        SPH_LAUNCH(ctx, "pair count");
+        SPH_CUDA(ctx, cudaMemcpyAsync(&T.h_u32[5], T.list_off + (nl - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        rc = exclusive_scan_u32(ctx, T.list_off, T.list_off, nl);
+        if (rc) return rc;
+        SPH_CUDA(ctx, cudaMemcpyAsync(&T.h_u32[6], T.list_off + (nl - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        const int64_t ne = (int64_t)T.h_u32[5] + T.h_u32[6];
+        T.n_entries = ne;
+        T.h_u32[7] = (uint32_t)ne;  // list_off[nl] = total (pinned source, copied in order)
+        SPH_CUDA(ctx, cudaMemcpyAsync(T.list_off + nl, &T.h_u32[7], sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                      ctx->stream));
+        if ((rc = grow(ctx, T.list, T.cap_list, ne + 1))) return rc;
+        k_pairs_fill<<<nblk(nl, 128), 128, 0, ctx->stream>>>(nl, T.leaf_node, T.nodes, T.top_node, T.node_leaf,
+                                                            T.leaf_cen, ctx->d_boxes, ctx->n_boxes, ctx->p.box_size,
+                                                            T.list_off, T.list, T.leaf_scale);
+        SPH_LAUNCH(ctx, "pair fill");
+    } else {
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->n_tiles, 0, sizeof(int), ctx->stream));
+    }
+    ctx->built = true;
+    ctx->density_valid = false;
+    ctx->st.n_cells = nl;
+    return SPH_OK;
+}
+
+// after the density iteration: current largest h per leaf, then per leaf the
+// largest h over itself and its list (the force pass's reach)
+int tree_reach(sph_ctx *ctx)
+{
+    AdaptiveTree &T = ctx->tree;
+    const int nl = T.n_leaves;
+    if (nl <= 0) return SPH_OK;
+    k_leaf_hmax<<<nblk(nl, 256), 256, 0, ctx->stream>>>(T.leaf_rng, nl, ctx->pos4, T.leaf_hc);
+    SPH_LAUNCH(ctx, "leaf max h");
+    k_leaf_reach<<<nblk(nl, 256), 256, 0, ctx->stream>>>(nl, T.list_off, T.list, T.leaf_hc, T.leaf_reach);
+    SPH_LAUNCH(ctx, "leaf reach");
+    return SPH_OK;
+}
+
+__global__ void k_top_of_key(const uint64_t *__restrict__ keys, int n, int32_t *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (int32_t)(keys[i] >> kMortonShift);
+}
+
+int tree_cell_keys_out(sph_ctx *ctx, int32_t *dev_keys)
+{
+    const int n = (int)ctx->n;
+    if (n <= 0) return SPH_OK;
+    k_top_of_key<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->keys64, n, dev_keys);
+    SPH_LAUNCH(ctx, "top cell keys");
+    return SPH_OK;
+}
+
+void free_tree(sph_ctx *ctx)
+{
+    AdaptiveTree &T = ctx->tree;
+    void *ptrs[] = {ctx->keys64, ctx->keys64_alt, T.leaf_of, T.node_at, T.top_node, T.nodes, T.front, T.front2,
+                    T.bounds, T.nkids, T.node_leaf, T.leaf_node, T.leaf_rng, T.leaf_cen, T.leaf_h, T.leaf_hc,
+                    T.leaf_reach, T.leaf_scale, T.list_off, T.list};
+    for (void *p : ptrs) cudaFree(p);
+    cudaFreeHost(T.h_u32);
+    cudaFreeHost(T.h_i32);
+    ctx->keys64 = ctx->keys64_alt = nullptr;
+    T = AdaptiveTree();
+}
+
+}  // namespace sph
