@@ -45,8 +45,10 @@ typedef enum {
                                 /* least 3 cells per side can hold the support   */
     SPH_ERR_TIMEOUT = 5,        /* a bounded device-side wait ran out            */
     SPH_ERR_NAN = 6,            /* a non-finite input or result was detected     */
-    SPH_ERR_STATE = 7           /* call order violated (e.g. force before        */
+    SPH_ERR_STATE = 7,          /* call order violated (e.g. force before        */
                                 /* density on the current positions)             */
+    SPH_ERR_CAPACITY = 8        /* a size limit was exceeded (adaptive cells:    */
+                                /* more than 2^32 - 2 neighbour-list entries)    */
 } sph_status;
 
 typedef struct sph_ctx sph_ctx; /* opaque, library-owned */
@@ -56,16 +58,25 @@ typedef struct sph_ctx sph_ctx; /* opaque, library-owned */
 #define SPH_FLAG_NGB_HASH 2u /* density pass also writes a neighbour-set hash */
 #define SPH_FLAG_AUTOTUNE 4u /* before the first density pass, time one pass for each
                                 candidate schedule (tile width 16/32 x cell factor
-                                1.05/1.25/1.5) on the current particles and keep the
-                                fastest; overrides tile_width and cell_factor */
+                                1.05/1.25/1.5; with SPH_FLAG_ADAPTIVE: tile width x
+                                leaf size 32/64/128) on the current particles and keep
+                                the fastest; overrides tile_width and cell_factor
+                                (leaf_max) */
 #define SPH_FLAG_ADAPTIVE 8u /* adaptive cells (Sec. 3.1): the uniform grid becomes the
                                 top level of an octree refined while a node holds more
-                                than 32 particles and its children stay no smaller than
-                                cell_factor x their largest h; leaves are the work
-                                items, each with a list of the leaves within reach.
+                                than leaf_max particles; leaves are the work items,
+                                each with a list of the leaves within reach.  Top
+                                cells may number 1 or 2 per side (h < box/2).
                                 For h spanning decades (clustered matter).  Builds read
                                 tree sizes on the host, so sph_steps runs its steps
                                 one by one instead of replaying a CUDA graph. */
+#define SPH_FLAG_TREE_H_GUESS 16u /* with SPH_FLAG_ADAPTIVE: the first cell build
+                                replaces every input h by an estimate from the number
+                                density n of the smallest tree node around it that
+                                holds at least 2 N_ngb particles, h = (3 N_ngb /
+                                (4 pi n))^(1/3), so that the density iteration starts
+                                near its root even where the input guess is off by
+                                decades (it converges to the same h) */
 
 typedef struct {
     int64_t n;           /* particles; 0 <= n < 2^31                                  */
@@ -88,6 +99,8 @@ typedef struct {
                          /* last = n: box b owns particles [off[b], off[b+1]); each  */
                          /* box gets its own cell grid; NULL when n_boxes <= 1;      */
                          /* copied by sph_init                                       */
+    int32_t leaf_max;    /* SPH_FLAG_ADAPTIVE: refine nodes holding more particles   */
+                         /* than this (1..4096; 0 = default 64)                     */
 } sph_params;
 
 /*
@@ -146,6 +159,7 @@ typedef struct {
     int32_t tile_width;        /* schedule in use: targets per tile (16 or 32)       */
     float cell_factor;         /* schedule in use: cell side / max h                 */
     int64_t graph_steps;       /* steps replayed from a captured graph (sph_steps)   */
+    int32_t leaf_max;          /* adaptive cells: leaf size in use (0: uniform grid) */
 } sph_stats;
 
 /* Fill *p with the defaults: gamma 5/3, n_ngb 48, h_tol 1e-4, alpha 0.8, cfl 0.1,

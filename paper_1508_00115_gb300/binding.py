@@ -27,14 +27,17 @@ SPH_ERR_H_EXCEEDS_CELL = 4
 SPH_ERR_TIMEOUT = 5
 SPH_ERR_NAN = 6
 SPH_ERR_STATE = 7
+SPH_ERR_CAPACITY = 8
 SPH_FLAG_TIMING = 1
 SPH_FLAG_NGB_HASH = 2
 SPH_FLAG_AUTOTUNE = 4
 SPH_FLAG_ADAPTIVE = 8
+SPH_FLAG_TREE_H_GUESS = 16
 SPH_SORT_STATIC_MAX_N = 262144
 
 _NAMES = {0: "SPH_OK", 1: "SPH_ERR_INVALID_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_NOT_CONVERGED",
-          4: "SPH_ERR_H_EXCEEDS_CELL", 5: "SPH_ERR_TIMEOUT", 6: "SPH_ERR_NAN", 7: "SPH_ERR_STATE"}
+          4: "SPH_ERR_H_EXCEEDS_CELL", 5: "SPH_ERR_TIMEOUT", 6: "SPH_ERR_NAN", 7: "SPH_ERR_STATE",
+          8: "SPH_ERR_CAPACITY"}
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "sph.h")
 
@@ -52,7 +55,7 @@ class sph_params(ctypes.Structure):
                 ("max_h_iter", ctypes.c_int32), ("use_balsara", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("tile_width", ctypes.c_int32), ("n_boxes", ctypes.c_int32),
-                ("box_offsets", ctypes.c_void_p)]
+                ("box_offsets", ctypes.c_void_p), ("leaf_max", ctypes.c_int32)]
 
 
 _PFIELDS = ["x", "y", "z", "vx", "vy", "vz", "m", "u", "h", "rho", "P", "c", "f", "divv", "curl",
@@ -78,7 +81,7 @@ class sph_stats(ctypes.Structure):
                 ("t_density_ms", ctypes.c_double), ("t_force_ms", ctypes.c_double),
                 ("t_build_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("tile_width", ctypes.c_int32), ("cell_factor", ctypes.c_float),
-                ("graph_steps", ctypes.c_int64)]
+                ("graph_steps", ctypes.c_int64), ("leaf_max", ctypes.c_int32)]
 
 
 _lock = threading.Lock()

@@ -57,12 +57,13 @@ void timer_end(sph_ctx *ctx, cudaEvent_t end)
 
 static void free_particles(sph_ctx *c)
 {
-    void *ptrs[] = {c->pos4, c->vel4, c->thermo4, c->upred, c->active, c->ids, c->ids_tmp, c->ngb_hash,
+    void *ptrs[] = {c->pos4, c->vel4, c->thermo4, c->upred, c->h_lo, c->h_hi, c->active, c->ids, c->ids_tmp, c->ngb_hash,
                     c->keys, c->keys_alt, c->vals, c->vals_alt, c->hist, c->s64, c->s32, c->tiles,
                     c->act_tiles};
     for (void *p : ptrs) cudaFree(p);
     c->pos4 = c->vel4 = c->thermo4 = nullptr;
     c->upred = nullptr;
+    c->h_lo = c->h_hi = nullptr;
     c->active = nullptr;
     c->ids = c->ids_tmp = nullptr;
     c->ngb_hash = nullptr;
@@ -84,6 +85,8 @@ static int alloc_particles(sph_ctx *c, int64_t cap)
     SPH_CUDA(c, cudaMalloc(&c->vel4, sizeof(float4) * cap));
     SPH_CUDA(c, cudaMalloc(&c->thermo4, sizeof(float4) * cap));
     SPH_CUDA(c, cudaMalloc(&c->upred, sizeof(float) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->h_lo, sizeof(float) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->h_hi, sizeof(float) * cap));
     SPH_CUDA(c, cudaMalloc(&c->active, cap));
     SPH_CUDA(c, cudaMalloc(&c->ids, sizeof(int64_t) * cap));
     SPH_CUDA(c, cudaMalloc(&c->ids_tmp, sizeof(int64_t) * cap));
@@ -124,6 +127,7 @@ static int check_params(const sph_params *p, std::string &why)
     else if (p->max_h_iter < 1) why = "max_h_iter must be >= 1";
     else if (p->kernel != 0) why = "kernel must be 0 (cubic spline)";
     else if (p->tile_width != 0 && p->tile_width != 16 && p->tile_width != 32) why = "tile_width must be 0, 16 or 32";
+    else if (p->leaf_max < 0 || p->leaf_max > 4096) why = "leaf_max must be in [0, 4096]";
     else if (p->n_boxes < 0) why = "n_boxes must be >= 0";
     else if (p->n_boxes > 1 && !p->box_offsets) why = "box_offsets required for n_boxes > 1";
     else if (p->n_boxes > 1 && (p->box_offsets[0] != 0 || p->box_offsets[p->n_boxes] != p->n)) why = "box_offsets must run from 0 to n";
@@ -146,19 +150,22 @@ static int autotune(sph_ctx *ctx, sph_particles *parts)
 {
     const int tws[2] = {16, 32};
     const float cfs[3] = {1.05f, 1.25f, 1.5f};
+    const int leaves[3] = {32, 64, 128};  // adaptive cells: leaf sizes instead of cell factors
     cudaEvent_t e0, e1;
     SPH_CUDA(ctx, cudaEventCreate(&e0));
     SPH_CUDA(ctx, cudaEventCreate(&e1));
     float best = 1e30f;
     int best_tw = ctx->tile_w;
     float best_cf = ctx->p.cell_factor;
+    int best_leaf = ctx->leaf_max;
     const uint32_t flags = ctx->p.flags;
     ctx->p.flags &= ~SPH_FLAG_TIMING;  // probes are not part of the statistics
     int rc = SPH_OK;
     for (int a = 0; a < 2 && rc == SPH_OK; ++a)
         for (int b = 0; b < 3 && rc == SPH_OK; ++b) {
             ctx->tile_w = tws[a];
-            ctx->p.cell_factor = cfs[b];
+            if (ctx->adaptive) ctx->leaf_max = leaves[b];
+            else ctx->p.cell_factor = cfs[b];
             rc = build_cells(ctx, parts);
             if (rc == SPH_ERR_H_EXCEEDS_CELL) {  // this cell factor cannot hold the largest h
                 rc = SPH_OK;
@@ -175,7 +182,8 @@ static int autotune(sph_ctx *ctx, sph_particles *parts)
             if (ms < best) {
                 best = ms;
                 best_tw = tws[a];
-                best_cf = cfs[b];
+                best_cf = ctx->p.cell_factor;
+                best_leaf = ctx->leaf_max;
             }
         }
     cudaEventDestroy(e0);
@@ -184,6 +192,7 @@ static int autotune(sph_ctx *ctx, sph_particles *parts)
     if (rc) return rc;
     ctx->tile_w = best_tw;
     ctx->p.cell_factor = best_cf;
+    ctx->leaf_max = best_leaf;
     ctx->tuned = true;
     return build_cells(ctx, parts);
 }
@@ -200,19 +209,27 @@ static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
     }
     if (n > 0) {
         SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, n, ctx->stream));
+        int rc = reset_h_brackets(ctx);
+        if (rc) return rc;
         bool all_tiles = true;  // first pass (and after a rebuild): every tile
         for (;;) {
             const bool last = iters == ctx->p.max_h_iter - 1;
             SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_UNCONV, 0, 2 * sizeof(unsigned long long),
                                           ctx->stream));
-            int rc = run_density_pass(ctx, parts, last, !all_tiles);
+            rc = run_density_pass(ctx, parts, last, !all_tiles);
             if (rc) return rc;
             ++iters;
+            if (ctx->adaptive && !last) {
+                rc = tree_shrink_count(ctx, parts);
+                if (rc) return rc;
+            }
             rc = read_counters(ctx);
             if (rc) return rc;
             unconv = ctx->h_counters[C_UNCONV];
             if (unconv == 0 || last) break;
-            if (ctx->h_counters[C_HFLAG]) {
+            // adaptive: lists much longer than the current h need (1 leaf in 16)
+            const bool shrunk = ctx->adaptive && ctx->h_counters[C_SHRINK] * 16 > (unsigned long long)ctx->tree.n_leaves;
+            if (ctx->h_counters[C_HFLAG] || shrunk) {
                 // some h outgrew its cell: re-bin with the new h (permutes the arrays)
                 cudaEvent_t end = nullptr;
                 timer_begin(ctx, 2, &end);
@@ -221,6 +238,8 @@ static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
                 if (rc) return rc;
                 ctx->st.rebuilds++;
                 SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, n, ctx->stream));
+                rc = reset_h_brackets(ctx);  // slots were permuted
+                if (rc) return rc;
                 all_tiles = true;
             } else {
                 rc = compact_active_tiles(ctx);
@@ -228,7 +247,7 @@ static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
                 all_tiles = false;
             }
         }
-        int rc = sync_h(ctx, parts);
+        rc = sync_h(ctx, parts);
         if (rc) return rc;
     }
     if (iters_out) *iters_out = iters;
@@ -246,8 +265,9 @@ static int do_force(sph_ctx *ctx, sph_particles *parts)
 {
     if (!ctx->density_valid) return fail(ctx, SPH_ERR_STATE, "sph_force needs sph_density on the current state");
     if (ctx->n > 0) {
-        // reach of every cell (leaf) for r < max(h_i, h_j)
-        int rc = ctx->adaptive ? tree_reach(ctx) : cell_reach(ctx);
+        // uniform grid: reach of every cell for r < max(h_i, h_j) (adaptive cells
+        // prune every source with its own h)
+        int rc = ctx->adaptive ? SPH_OK : cell_reach(ctx);
         if (rc) return rc;
         rc = run_force_pass(ctx, parts);
         if (rc) return rc;
@@ -340,6 +360,8 @@ static int graph_step(sph_ctx *ctx, sph_particles *parts, double dt, int passes)
     if (rc) return rc;
     const int n = (int)ctx->n;
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, n, ctx->stream));
+    rc = reset_h_brackets(ctx);
+    if (rc) return rc;
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_UNCONV, 0, 2 * sizeof(unsigned long long), ctx->stream));
     for (int p = 0; p < passes; ++p) {
         if (p > 0) {
@@ -511,6 +533,8 @@ int sph_init(sph_ctx **out, const sph_params *p, int device, void *cuda_stream)
     c->n = p->n;
     c->tile_w = p->tile_width == 32 ? 32 : 16;
     c->adaptive = (p->flags & SPH_FLAG_ADAPTIVE) != 0;
+    c->leaf_max = p->leaf_max > 0 ? p->leaf_max : 64;
+    c->h_guess_pending = c->adaptive && (p->flags & SPH_FLAG_TREE_H_GUESS);
     c->n_boxes = p->n_boxes > 1 ? p->n_boxes : 1;
     if (p->n_boxes > 1) c->box_off.assign(p->box_offsets, p->box_offsets + p->n_boxes + 1);
     else c->box_off = {0, p->n};
@@ -713,6 +737,7 @@ int sph_get_stats(sph_ctx *ctx, sph_stats *s)
     st.t_build_ms = t[2];
     st.tile_width = ctx->tile_w;
     st.cell_factor = ctx->p.cell_factor;
+    st.leaf_max = ctx->adaptive ? ctx->leaf_max : 0;
     *s = st;
     return SPH_OK;
 }

@@ -38,7 +38,7 @@ constexpr float kPruneMargin = 2.44140625e-04f;  // 2^-12
 // device counters (unsigned long long slots)
 enum Counter {
     C_UNCONV = 0,     // unconverged particles after the last density pass
-    C_HFLAG = 1,      // 1: some h outgrew what the cells hold; 2 (adaptive): some h shrank far below its leaf's
+    C_HFLAG = 1,      // some h outgrew what the cells (leaf lists) hold
     C_DPAIRS = 2,     // density interactions
     C_FPAIRS = 3,     // force interactions
     C_DCAND = 4,      // density candidate tests
@@ -46,6 +46,9 @@ enum Counter {
     C_FLOORS = 6,     // u floors
     C_DTARGETS = 7,   // active density targets
     C_GFLAGS = 8,     // multi-step run: OR of per-step flags (1: unconverged, 2: h beyond cells)
+    C_SHRINK = 9,     // adaptive: leaves whose largest h fell below kTreeShrink x its build value
+    C_WALKOVF = 10,   // adaptive: leaf walks whose stack overflowed
+    C_LISTTOT = 11,   // adaptive: neighbour-list entries (64-bit total)
     C_NCOUNTERS = 16
 };
 
@@ -65,8 +68,8 @@ struct BoxDev {
 // within kTreeReach x (the larger of the two leaves' largest h at build time), so
 // the lists stay exact while no h grows beyond kTreeReach x its leaf's build value.
 constexpr float kTreeReach = 1.25f;
-// ... and a leaf whose particles' h fell below kTreeShrink x its build value is
-// worth refining: the density pass asks for a rebuild
+// ... and once many leaves' largest h fell below kTreeShrink x its build value the
+// lists are worth rebuilding (they are valid, only longer than needed)
 constexpr float kTreeShrink = 0.45f;
 
 // octree node inside a top cell: a contiguous range of the sorted particles
@@ -78,6 +81,7 @@ struct TreeNode {
     int level;         // 0 = the top cell itself
     unsigned long long prefix;  // Morton prefix inside the top cell (3 bits per level)
     float hmax;        // largest h of its particles
+    int parent;        // -1 for a top cell
     float bx0, by0, bz0, bx1, by1, bz1;  // bounding box, relative to the top-cell centre
 };
 
@@ -92,8 +96,6 @@ struct AdaptiveTree {
     int2 *leaf_rng = nullptr;  // particle slots of every leaf
     double *leaf_cen = nullptr; // absolute centre of every leaf (3 per leaf)
     float *leaf_h = nullptr;     // largest h per leaf when the tree was built
-    float *leaf_hc = nullptr;    // largest current h per leaf (tree_reach)
-    float *leaf_reach = nullptr; // force reach per leaf: max current h over the leaf and its list
     float *leaf_scale = nullptr; // coordinate scale of the leaf's pair arithmetic (FP32 band width)
     uint32_t *list_off = nullptr; // neighbour-list offsets, n_leaves + 1
     float4 *list = nullptr;     // {offset between leaf centres, neighbour leaf}
@@ -101,8 +103,7 @@ struct AdaptiveTree {
     int *h_i32 = nullptr;
     int64_t cap_keys = 0, cap_keys2 = 0, cap_leaf_of = 0, cap_node_at = 0, cap_top = 0, cap_nodes = 0,
             cap_front = 0, cap_front2 = 0, cap_bounds = 0, cap_nkids = 0, cap_node_leaf = 0, cap_leaf_node = 0,
-            cap_leaf_rng = 0, cap_leaf_cen = 0, cap_leaf_h = 0, cap_leaf_hc = 0, cap_leaf_reach = 0,
-            cap_leaf_scale = 0, cap_list_off = 0, cap_list = 0;
+            cap_leaf_rng = 0, cap_leaf_cen = 0, cap_leaf_h = 0, cap_leaf_scale = 0, cap_list_off = 0, cap_list = 0;
     int n_nodes = 0, n_leaves = 0;
     int64_t n_entries = 0;
 };
@@ -130,6 +131,7 @@ struct sph_ctx {
     // packed particle data
     float4 *pos4 = nullptr, *vel4 = nullptr, *thermo4 = nullptr;
     float *upred = nullptr;
+    float *h_lo = nullptr, *h_hi = nullptr;  // bracket of each particle's h root (density iteration)
     uint8_t *active = nullptr;
     int64_t *ids = nullptr, *ids_tmp = nullptr;
     uint64_t *ngb_hash = nullptr;
@@ -144,6 +146,8 @@ struct sph_ctx {
     float *s32 = nullptr;   // 8 * cap
     // adaptive cells (SPH_FLAG_ADAPTIVE)
     bool adaptive = false;
+    int leaf_max = 64;
+    bool h_guess_pending = false;  // SPH_FLAG_TREE_H_GUESS before the first build
     sph::AdaptiveTree tree;
     // boxes and their cell grids
     int n_boxes = 1;
@@ -245,8 +249,9 @@ int box_max_h(sph_ctx *ctx, const float *h);                    // sph_cells.cu
 int cell_reach(sph_ctx *ctx);  // cell_tmp = max h within two cells   // sph_cells.cu
 int permute_particles(sph_ctx *ctx, sph_particles *parts, bool cell_pos);  // sph_cells.cu
 int build_tree(sph_ctx *ctx, sph_particles *parts);             // sph_tree.cu
-int tree_reach(sph_ctx *ctx);                                   // sph_tree.cu
 int tree_cell_keys_out(sph_ctx *ctx, int32_t *dev_keys);        // sph_tree.cu
+int tree_shrink_count(sph_ctx *ctx, sph_particles *parts);      // sph_tree.cu
+int reset_h_brackets(sph_ctx *ctx);                             // sph_pairs.cu
 void free_tree(sph_ctx *ctx);                                   // sph_tree.cu
 int cell_keys_out(sph_ctx *ctx, int32_t *dev_keys);             // sph_cells.cu
 int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool active_list);  // sph_pairs.cu

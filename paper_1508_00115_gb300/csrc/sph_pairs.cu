@@ -35,6 +35,8 @@ constexpr int kPairThreads = 256;
 // Padding sources sit at -kFar and target-less lanes at +kFar: the squared distance
 // between either and anything else overflows to +inf, so no test can pass.
 constexpr float kFar = 1e30f;
+// an h bracket end at or above this is open (the bytes 0x7f7f7f7f read 3.39e38)
+constexpr float kHUnbounded = 3e38f;
 
 // Neighbour cells in visiting order: the own cell, then each of the 13 directions
 // of a half stencil followed by its opposite, so that every staged batch mixes
@@ -77,6 +79,7 @@ struct DensityArgs {
     const float *__restrict__ upred;
     uint8_t *active;
     float *h;
+    float *h_lo, *h_hi;  // bracket of the root of N_w(h) = N_ngb
     float *rho, *P, *c, *f, *divv, *curl;
     int32_t *n_ngb;
     float4 *thermo4;
@@ -300,29 +303,40 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
         }
         // stage chunk after chunk; one flush site (keeps the kernel small)
         // (adaptive cells: the tile's list entries, each a leaf and its offset)
-        int e0 = 0, ne = 0;
+        uint32_t e0 = 0;
+        int ne = 0;
         if (LIST && live) {
-            e0 = (int)a.list_off[tile.x];
-            ne = (int)a.list_off[tile.x + 1] - e0;
+            e0 = a.list_off[tile.x];
+            ne = (int)(a.list_off[tile.x + 1] - e0);
         }
         int o = -1, ch = 0, nchunk = 0, bs = 0, be = 0;
         const int ncell = LIST ? (int)__reduce_max_sync(kFull, (unsigned)ne) : (R == 1 ? 27 : 125);
         float shx = 0.f, shy = 0.f, shz = 0.f;
+        int pb = 0, pe = 0;  // list entries fetched TW at a time: lane tl holds entry o + tl
+        float px = 0.f, py = 0.f, pz = 0.f;
         for (;;) {
             while (ch >= nchunk && o < ncell - 1) {
                 ++o;
                 ch = 0;
                 if (LIST) {
-                    bs = be = 0;
-                    if (o < ne) {
-                        const float4 en = a.list[e0 + o];
-                        const int2 r = a.leaf_rng[__float_as_int(en.w)];
-                        bs = r.x;
-                        be = r.y;
-                        shx = en.x;
-                        shy = en.y;
-                        shz = en.z;
+                    const int src = o & (TW - 1);  // o is warp-uniform
+                    if (src == 0) {
+                        pb = pe = 0;
+                        if (o + tl < ne) {
+                            const float4 en = a.list[e0 + (uint32_t)(o + tl)];
+                            const int2 r = a.leaf_rng[__float_as_int(en.w)];
+                            pb = r.x;
+                            pe = r.y;
+                            px = en.x;
+                            py = en.y;
+                            pz = en.z;
+                        }
                     }
+                    bs = __shfl_sync(kFull, pb, src, TW);
+                    be = __shfl_sync(kFull, pe, src, TW);
+                    shx = __shfl_sync(kFull, px, src, TW);
+                    shy = __shfl_sync(kFull, py, src, TW);
+                    shz = __shfl_sync(kFull, pz, src, TW);
                     nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
                     continue;
                 }
@@ -392,8 +406,7 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
             atomicAdd(a.counters + C_DTARGETS, (unsigned long long)__popc(amask));
         }
 
-        // bit 0: not converged; bit 1: h beyond what the cells hold (rebuild needed);
-        // bit 2 (adaptive): h far below its leaf's build value (rebuild worthwhile)
+        // bit 0: not converged; bit 1: h beyond what the cells hold (rebuild needed)
         unsigned flag = 0u;
         if (act) {
             const float hinv3 = hinv * hinv * hinv, hinv4 = hinv3 * hinv;
@@ -406,19 +419,27 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
             const float g = nw_ - a.n_ngb_target;
             const bool conv = fabsf(g) <= a.h_tol * a.n_ngb_target;
             if (!conv && !a.last_pass) {
+                // Newton step, at most a factor 2 either way; N_w is non-decreasing in
+                // h, so every evaluation also narrows a bracket of the root, and a step
+                // that leaves a two-sided bracket is replaced by its geometric middle
+                float lo = a.h_lo[i], up = a.h_hi[i];
+                if (g < 0.f) lo = fmaxf(lo, hi);
+                else up = fminf(up, hi);
                 float hn = dnw_dh > 0.f ? hi - g / dnw_dh : (g < 0.f ? 2.f * hi : 0.5f * hi);
                 hn = fminf(fmaxf(hn, 0.5f * hi), 2.f * hi);
+                if (lo > 0.f && up < kHUnbounded && !(hn > lo && hn < up)) hn = sqrtf(lo) * sqrtf(up);
                 // adaptive cells take h up to just below half the box (the minimum
                 // image); a step past it is cut back there instead of failing
                 if (LIST) hn = fminf(hn, (float)(0.5 * a.box) * (1.f - 1e-5f));
                 a.h[i] = hn;
+                a.h_lo[i] = lo;
+                a.h_hi[i] = up;
                 flag = 1u;
                 if (LIST) {
                     // beyond what its leaf's list or the adjacent top cells hold
                     const float hb = a.leaf_hb[tile.x];
                     const float lim = fminf(fminf(kTreeReach * hb, bx.L32), (float)(0.5 * a.box));
                     if (hn > lim * (1.f - 1e-6f)) flag |= 2u;
-                    else if (hn < kTreeShrink * hb) flag |= 4u;
                 } else if ((double)hn > 2.0 * bx.L64 * (1.0 - 1e-6)) {
                     flag |= 2u;  // beyond the radius-2 stencil of its cell
                 }
@@ -450,10 +471,10 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
         }
         // one atomic per warp and counter
         const unsigned unc = __ballot_sync(kFull, flag & 1u);
-        const unsigned fl = __reduce_or_sync(kFull, flag & 6u);
+        const unsigned fl = __reduce_or_sync(kFull, flag & 2u);
         if (lane == 0) {
             if (unc) atomicAdd(a.counters + C_UNCONV, (unsigned long long)__popc(unc));
-            if (fl) atomicOr(a.counters + C_HFLAG, (unsigned long long)(fl >> 1));
+            if (fl) atomicOr(a.counters + C_HFLAG, 1ull);
         }
     }
 }
@@ -468,7 +489,7 @@ struct ForceArgs {
     const double *__restrict__ x;
     const double *__restrict__ y;
     const double *__restrict__ z;
-    const float *__restrict__ cell_reach;  // per cell (leaf): max h of anything that can reach it
+    const float *__restrict__ cell_reach;  // per cell: max h of anything that can reach it
     float *ax, *ay, *az, *dudt, *vsig;
     unsigned long long *counters;
     const BoxDev *__restrict__ boxes;
@@ -526,7 +547,9 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
         const float L = LIST ? a.leaf_scale[tile.x] : bx.L32;
         // cutoff reach of the tile: r < max(h_i, h_j) with h_j of any particle that can
         // reach its cell (a tile beyond the last has tile.x = 0, a valid cell)
-        const float H = fmaxf(tile_max<TW>(hi), a.cell_reach[tile.x]);
+        // (adaptive cells: the leaf's list holds every source in reach, and each source
+        // is pruned with its own h below)
+        const float H = LIST ? tile_max<TW>(hi) : fmaxf(tile_max<TW>(hi), a.cell_reach[tile.x]);
         const int R = LIST ? 1 : (int)__reduce_max_sync(kFull, H * (1.f + kPruneMargin) > L ? 2u : 1u);
         const float bandmax = 2.f * kBandK * H * (H + L);
         const float reach2 = H * H * (1.f + kPruneMargin) + bandmax;
@@ -576,9 +599,17 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
                     const float4 s = sw[kk];
                     const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float m2x = fmaxf(hi2, s.w * s.w);
-                    bool in = r2 < m2x - bandmax;
-                    if (!in && r2 < m2x + bandmax) {
+                    float m2x, bm;
+                    if (LIST) {  // band of this pair: h spans decades within a list
+                        const float mm = fmaxf(hi, s.w);
+                        m2x = mm * mm;
+                        bm = kBandK * mm * (mm + L);
+                    } else {
+                        m2x = fmaxf(hi2, s.w * s.w);
+                        bm = bandmax;
+                    }
+                    bool in = r2 < m2x - bm;
+                    if (!in && r2 < m2x + bm) {
                         const unsigned d = band_decide(a.x, a.y, a.z, i, sI[32 * wd + kk], a.box, hi, s.w);
                         in = d != 0u;
                     }
@@ -649,29 +680,40 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
         }
         // stage chunk after chunk; one flush site (keeps the kernel small)
         // (adaptive cells: the tile's list entries, each a leaf and its offset)
-        int e0 = 0, ne = 0;
+        uint32_t e0 = 0;
+        int ne = 0;
         if (LIST && live) {
-            e0 = (int)a.list_off[tile.x];
-            ne = (int)a.list_off[tile.x + 1] - e0;
+            e0 = a.list_off[tile.x];
+            ne = (int)(a.list_off[tile.x + 1] - e0);
         }
         int o = -1, ch = 0, nchunk = 0, bs = 0, be = 0;
         const int ncell = LIST ? (int)__reduce_max_sync(kFull, (unsigned)ne) : (R == 1 ? 27 : 125);
         float shx = 0.f, shy = 0.f, shz = 0.f;
+        int pb = 0, pe = 0;  // list entries fetched TW at a time: lane tl holds entry o + tl
+        float px = 0.f, py = 0.f, pz = 0.f;
         for (;;) {
             while (ch >= nchunk && o < ncell - 1) {
                 ++o;
                 ch = 0;
                 if (LIST) {
-                    bs = be = 0;
-                    if (o < ne) {
-                        const float4 en = a.list[e0 + o];
-                        const int2 r = a.leaf_rng[__float_as_int(en.w)];
-                        bs = r.x;
-                        be = r.y;
-                        shx = en.x;
-                        shy = en.y;
-                        shz = en.z;
+                    const int src = o & (TW - 1);  // o is warp-uniform
+                    if (src == 0) {
+                        pb = pe = 0;
+                        if (o + tl < ne) {
+                            const float4 en = a.list[e0 + (uint32_t)(o + tl)];
+                            const int2 r = a.leaf_rng[__float_as_int(en.w)];
+                            pb = r.x;
+                            pe = r.y;
+                            px = en.x;
+                            py = en.y;
+                            pz = en.z;
+                        }
                     }
+                    bs = __shfl_sync(kFull, pb, src, TW);
+                    be = __shfl_sync(kFull, pe, src, TW);
+                    shx = __shfl_sync(kFull, px, src, TW);
+                    shy = __shfl_sync(kFull, py, src, TW);
+                    shz = __shfl_sync(kFull, pz, src, TW);
                     nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
                     continue;
                 }
@@ -717,7 +759,12 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
                     const float ex = fmaxf(fmaxf(lox - pj.x, pj.x - hix), 0.f);
                     const float ey = fmaxf(fmaxf(loy - pj.y, pj.y - hiy), 0.f);
                     const float ez = fmaxf(fmaxf(loz - pj.z, pj.z - hiz), 0.f);
-                    keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < reach2;
+                    float r2max = reach2;
+                    if (LIST) {
+                        const float m = fmaxf(H, pj.w);
+                        r2max = m * m * (1.f + kPruneMargin) + 2.f * kBandK * m * (m + L);
+                    }
+                    keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < r2max;
                 }
                 const unsigned mine = __ballot_sync(kFull, keep) & gmask;
                 if (keep) {
@@ -852,6 +899,8 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool ac
     a.upred = ctx->upred;
     a.active = ctx->active;
     a.h = parts->h;
+    a.h_lo = ctx->h_lo;
+    a.h_hi = ctx->h_hi;
     a.rho = parts->rho;
     a.P = parts->P;
     a.c = parts->c;
@@ -918,7 +967,7 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts)
     a.x = parts->x;
     a.y = parts->y;
     a.z = parts->z;
-    a.cell_reach = ctx->adaptive ? ctx->tree.leaf_reach : ctx->cell_tmp;
+    a.cell_reach = ctx->cell_tmp;  // uniform grid only
     a.list_off = ctx->tree.list_off;
     a.list = ctx->tree.list;
     a.leaf_rng = ctx->tree.leaf_rng;
@@ -947,6 +996,16 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts)
     timer_end(ctx, end);
     SPH_LAUNCH(ctx, "force kernel");
     ctx->st.force_passes++;
+    return SPH_OK;
+}
+
+// Open brackets: lower end 0, upper end kHUnbounded (bytes 0x7f: 3.39e38).
+int reset_h_brackets(sph_ctx *ctx)
+{
+    const int64_t n = ctx->n;
+    if (n <= 0) return SPH_OK;
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->h_lo, 0, sizeof(float) * n, ctx->stream));
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->h_hi, 0x7f, sizeof(float) * n, ctx->stream));
     return SPH_OK;
 }
 

@@ -6,7 +6,7 @@
 // particle's neighbours always lie in the 27 top cells around it.  Inside each top
 // cell particles are ordered by a 3 x 14-bit Morton code; every octree node is then
 // a contiguous range of the sorted particles.  Nodes are refined top-down, one level
-// per step, while they hold more than kLeafMax particles (32: one or two tiles).
+// per step, while they hold more than leaf_max particles (a parameter, 64 by default).
 // Unlike the paper's cells, a leaf may be smaller than the h of its particles: its
 // neighbours need not lie in the adjacent leaves, because every leaf carries an
 // explicit list of the leaves within reach.  For every leaf the list
@@ -18,6 +18,8 @@
 // ~2^-24 of a leaf side even where h is 10^-3 of the top cell.
 #include <math.h>
 
+#include <string.h>
+
 #include <algorithm>
 
 #include "sph_internal.cuh"
@@ -26,7 +28,6 @@ namespace sph {
 
 constexpr int kMortonBits = 14;       // per axis, inside a top cell
 constexpr int kMortonShift = 3 * kMortonBits;
-constexpr int kLeafMax = 32;          // refine nodes holding more particles than this
 
 __device__ __forceinline__ uint64_t spread3(uint32_t v)  // 14 bits -> every third bit
 {
@@ -143,6 +144,7 @@ __global__ void k_roots(const int *__restrict__ cs, int64_t ntop, const uint32_t
     t.top = (int)c;
     t.level = 0;
     t.prefix = 0;
+    t.parent = -1;
     nodes[id] = t;
     top_node[c] = id;
     front[id] = id;
@@ -153,7 +155,7 @@ __global__ void k_roots(const int *__restrict__ cs, int64_t ntop, const uint32_t
 __global__ void k_node_stats(const int *__restrict__ front, int nfront, TreeNode *__restrict__ nodes,
                              const uint64_t *__restrict__ keys, const double *__restrict__ x,
                              const double *__restrict__ y, const double *__restrict__ z, const float *__restrict__ h,
-                             const BoxDev *__restrict__ bxs, int nb, int *__restrict__ bounds,
+                             const BoxDev *__restrict__ bxs, int nb, int leaf_max, int *__restrict__ bounds,
                              uint32_t *__restrict__ nkids)
 {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -189,7 +191,7 @@ __global__ void k_node_stats(const int *__restrict__ front, int nfront, TreeNode
     // the positions above never shrinks it
     const float pad = g.L32 * 1.2e-7f;
     // refine while there are too many particles (down to the Morton resolution)
-    const bool split = (t.hi - t.lo) > kLeafMax && t.level < kMortonBits;
+    const bool split = (t.hi - t.lo) > leaf_max && t.level < kMortonBits;
     int cnt = 0;
     if (split) {
         // child boundaries: first slot whose next Morton digit is >= k (k = 1..7)
@@ -246,6 +248,7 @@ __global__ void k_make_children(const int *__restrict__ front, int nfront, TreeN
         ch.top = t.top;
         ch.level = t.level + 1;
         ch.prefix = (t.prefix << 3) | (uint64_t)k;
+        ch.parent = id;
         const int cid = base + (int)first + c;
         nodes[cid] = ch;
         next[first + c] = cid;
@@ -253,6 +256,49 @@ __global__ void k_make_children(const int *__restrict__ front, int nfront, TreeN
     }
     t.child = base + (int)first;
     t.nchild = c;
+}
+
+// Initial h from the tree: for every leaf, the smallest node around it (itself or an
+// ancestor) that holds at least min_count particles gives a number density n =
+// count / side^3, and h = (3 N_ngb / (4 pi n))^(1/3) -- the h at which a uniform
+// medium of that density meets the criterion -- is written to the leaf's particles.
+__global__ void k_h_guess(const TreeNode *__restrict__ nodes, int n_nodes, const BoxDev *__restrict__ bxs, int nb,
+                          int min_count, float n_ngb, double box, float *__restrict__ h)
+{
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n_nodes) return;
+    const TreeNode t = nodes[id];
+    if (t.child >= 0) return;
+    TreeNode A = t;
+    while (A.hi - A.lo < min_count && A.parent >= 0) A = nodes[A.parent];
+    const BoxDev g = bxs[nb == 1 ? 0 : tbox_of_cell(A.top, bxs, nb)];
+    const double side = ldexp(g.L64, -A.level);
+    const double dens = (double)(A.hi - A.lo) / (side * side * side);
+    double h0 = cbrt(3.0 * (double)n_ngb / (4.0 * 3.14159265358979323846 * dens));
+    h0 = fmin(h0, 0.45 * box);
+    for (int p = t.lo; p < t.hi; ++p) h[p] = (float)h0;
+}
+
+// largest h of every node (one warp per node)
+__global__ void k_node_hmax(TreeNode *__restrict__ nodes, int n_nodes, const float *__restrict__ h)
+{
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= n_nodes) return;
+    const int lo = nodes[w].lo, hi = nodes[w].hi;
+    float m = 0.f;
+    for (int p = lo + lane; p < hi; p += 32) m = fmaxf(m, h[p]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+    if (lane == 0) nodes[w].hmax = m;
+}
+
+__global__ void k_sum_u32(const uint32_t *__restrict__ v, int n, unsigned long long *__restrict__ out)
+{
+    unsigned long long s = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) s += v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
 }
 
 // flags the first slot of every leaf (leaves partition the particles)
@@ -349,7 +395,7 @@ __device__ int leaf_pairs(int l, const int *__restrict__ leaf_node, const TreeNo
     // by a slack added to every reach
     const float slack = 4.8e-7f * g.L32;
     const double cAx = leaf_cen[3 * l], cAy = leaf_cen[3 * l + 1], cAz = leaf_cen[3 * l + 2];
-    const double sideA = g.L64 / (double)(1 << A.level);
+    const double sideA = ldexp(g.L64, -A.level);
     double scale = sideA;
     int stack[8 * (kMortonBits + 1)];
     int cnt = 0;
@@ -385,7 +431,7 @@ __device__ int leaf_pairs(int l, const int *__restrict__ leaf_node, const TreeNo
                     // coordinates met in this pair's FP32 arithmetic are below
                     // |p_i| + |p_j| + |shift| <= (sides of both leaves + shift)
                     const double m = fmax(fabs(sx), fmax(fabs(sy), fabs(sz)));
-                    scale = fmax(scale, 0.5 * (sideA + g.L64 / (double)(1 << N.level) + m));
+                    scale = fmax(scale, 0.5 * (sideA + ldexp(g.L64, -N.level) + m));
                 }
                 ++cnt;
             } else {
@@ -417,26 +463,144 @@ __global__ void k_pairs_fill(int nl, const int *__restrict__ leaf_node, const Tr
         leaf_pairs<false>(l, leaf_node, nodes, top_node, node_leaf, leaf_cen, bxs, nb, box, list + off[l], scale + l);
 }
 
-// reach of every leaf for the force pass: its own largest h and that of every leaf in
-// its list (current h, after the density iteration)
-__global__ void k_leaf_hmax(const int2 *__restrict__ rng, int nl, const float4 *__restrict__ pos4,
-                            float *__restrict__ leaf_h)
-{
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= nl) return;
-    float m = 0.f;
-    for (int p = rng[l].x; p < rng[l].y; ++p) m = fmaxf(m, pos4[p].w);
-    leaf_h[l] = m;
-}
+// The same lists built by one warp per leaf: the warp pops up to 32 (node, image)
+// items of a shared-memory stack per round, tests them in parallel, appends the
+// leaves within reach (lane order) and pushes the children of the other nodes within
+// reach.  Entry order is fixed by the algorithm, so the counting and the writing
+// pass agree.  A walk whose stack would overflow sets *overflow and the caller
+// falls back to the one-thread walk above.
+constexpr int kWalkWarps = 2;
+constexpr int kWalkCap = 2048;  // stack items per warp (16 KB)
 
-__global__ void k_leaf_reach(int nl, const uint32_t *__restrict__ off, const float4 *__restrict__ list,
-                             const float *__restrict__ leaf_h, float *__restrict__ reach)
+struct WalkArgs {
+    int nl;
+    const int *__restrict__ leaf_node;
+    const TreeNode *__restrict__ nodes;
+    const int *__restrict__ top_node;
+    const int *__restrict__ node_leaf;
+    const double *__restrict__ leaf_cen;
+    const BoxDev *__restrict__ bxs;
+    int nb;
+    double box;
+    const uint32_t *__restrict__ off;  // fill: first entry of every leaf
+    float4 *__restrict__ list;         // fill: entries
+    float *__restrict__ scale;         // fill: coordinate scale per leaf
+    uint32_t *__restrict__ cnt;        // count: entries per leaf
+    unsigned long long *overflow;
+};
+
+template <bool COUNT>
+__global__ void __launch_bounds__(32 * kWalkWarps) k_leaf_walk(WalkArgs a)
 {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= nl) return;
-    float m = leaf_h[l];
-    for (uint32_t e = off[l]; e < off[l + 1]; ++e) m = fmaxf(m, leaf_h[__float_as_int(list[e].w)]);
-    reach[l] = m;
+    __shared__ int2 stk[kWalkWarps][kWalkCap];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int l = blockIdx.x * kWalkWarps + wib;
+    if (l >= a.nl) return;  // warp-uniform
+    int2 *st = stk[wib];
+    const TreeNode A = a.nodes[a.leaf_node[l]];
+    const BoxDev g = a.bxs[a.nb == 1 ? 0 : tbox_of_cell(A.top, a.bxs, a.nb)];
+    const int nc = g.nc, loc = A.top - g.cell_off;
+    const int ix = loc % nc, iy = (loc / nc) % nc, iz = loc / (nc * nc);
+    const float hA = A.hmax * kTreeReach;
+    const float slack = 4.8e-7f * g.L32;
+    const float sideA = ldexpf(g.L32, -A.level);
+    // roots: the non-empty top cells around A's, item = {root node, image index}
+    int sp;
+    {
+        int root = -1;
+        if (lane < 27) {
+            int jx = ix + lane % 3 - 1, jy = iy + (lane / 3) % 3 - 1, jz = iz + lane / 9 - 1;
+            jx = jx < 0 ? jx + nc : (jx >= nc ? jx - nc : jx);
+            jy = jy < 0 ? jy + nc : (jy >= nc ? jy - nc : jy);
+            jz = jz < 0 ? jz + nc : (jz >= nc ? jz - nc : jz);
+            root = a.top_node[g.cell_off + (jz * nc + jy) * nc + jx];
+        }
+        const unsigned b = __ballot_sync(kFull, root >= 0);
+        if (root >= 0) st[__popc(b & lt)] = make_int2(root, lane);
+        sp = __popc(b);
+    }
+    __syncwarp();
+    uint32_t cnt = 0;
+    const uint32_t base = COUNT ? 0u : a.off[l];
+    float sc = sideA;
+    double cAx = 0.0, cAy = 0.0, cAz = 0.0;
+    if (!COUNT) {
+        cAx = a.leaf_cen[3 * l];
+        cAy = a.leaf_cen[3 * l + 1];
+        cAz = a.leaf_cen[3 * l + 2];
+    }
+    bool ovf = false;
+    while (sp > 0) {
+        const int take = min(sp, 32);
+        int2 it = make_int2(-1, 0);
+        if (lane < take) it = st[sp - 1 - lane];
+        sp -= take;
+        __syncwarp();
+        bool emit = false;
+        int nch = 0, child = 0, level = 0;
+        const int o = it.y;
+        const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+        if (it.x >= 0) {
+            const TreeNode N = a.nodes[it.x];
+            const float dx = (float)ox * g.L32, dy = (float)oy * g.L32, dz = (float)oz * g.L32;
+            const float gx = fmaxf(fmaxf(N.bx0 + dx - A.bx1, A.bx0 - (N.bx1 + dx)), 0.f);
+            const float gy = fmaxf(fmaxf(N.by0 + dy - A.by1, A.by0 - (N.by1 + dy)), 0.f);
+            const float gz = fmaxf(fmaxf(N.bz0 + dz - A.bz1, A.bz0 - (N.bz1 + dz)), 0.f);
+            const float reach = fmaxf(hA, N.hmax * kTreeReach) * (1.f + 1e-5f) + slack;
+            if (gx * gx + gy * gy + gz * gz < reach * reach) {
+                if (N.child < 0) {
+                    emit = true;
+                    level = N.level;
+                } else {
+                    nch = N.nchild;
+                    child = N.child;
+                }
+            }
+        }
+        const unsigned eb = __ballot_sync(kFull, emit);
+        if (!COUNT && emit) {
+            const int b = a.node_leaf[it.x];
+            const int jx = ix + ox, jy = iy + oy, jz = iz + oz;
+            const double kx = jx < 0 ? -1.0 : (jx >= nc ? 1.0 : 0.0), ky = jy < 0 ? -1.0 : (jy >= nc ? 1.0 : 0.0),
+                         kz = jz < 0 ? -1.0 : (jz >= nc ? 1.0 : 0.0);
+            const double sx = a.leaf_cen[3 * b] + kx * a.box - cAx, sy = a.leaf_cen[3 * b + 1] + ky * a.box - cAy,
+                         sz = a.leaf_cen[3 * b + 2] + kz * a.box - cAz;
+            const float fx = (float)sx, fy = (float)sy, fz = (float)sz;
+            a.list[base + cnt + __popc(eb & lt)] = make_float4(fx, fy, fz, __int_as_float(b));
+            // coordinates met in this pair's FP32 arithmetic stay below the two leaf
+            // sides plus the offset
+            const float m = fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz)));
+            sc = fmaxf(sc, 0.5f * (sideA + ldexpf(g.L32, -level) + m) * (1.f + 1e-6f));
+        }
+        cnt += (uint32_t)__popc(eb);
+        // push the children of the nodes within reach (lane order)
+        int incl = nch;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        if (sp + total > kWalkCap) {
+            ovf = true;
+            break;
+        }
+        const int start = sp + incl - nch;
+        for (int c = 0; c < nch; ++c) st[start + c] = make_int2(child + nch - 1 - c, o);
+        sp += total;
+        __syncwarp();
+    }
+    if (ovf) {
+        if (lane == 0) atomicAdd(a.overflow, 1ull);
+        return;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) sc = fmaxf(sc, __shfl_xor_sync(kFull, sc, d));
+    if (lane == 0) {
+        if (COUNT) a.cnt[l] = cnt;
+        else a.scale[l] = sc;
+    }
 }
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
@@ -518,7 +682,7 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
     for (int level = 0; level <= kMortonBits && nfront > 0; ++level) {
         k_node_stats<<<nblk((int64_t)nfront * 32, 256), 256, 0, ctx->stream>>>(
             cur, nfront, T.nodes, ctx->keys64, parts->x, parts->y, parts->z, parts->h, ctx->d_boxes, ctx->n_boxes,
-            T.bounds, T.nkids);
+            ctx->leaf_max, T.bounds, T.nkids);
         SPH_LAUNCH(ctx, "node stats");
         SPH_CUDA(ctx, cudaMemcpyAsync(&T.h_u32[1], T.nkids + (nfront - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost,
                                       ctx->stream));
@@ -538,6 +702,27 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
         std::swap(cur, nxt);
     }
     T.n_nodes = n_nodes;
+    if (ctx->h_guess_pending) {
+        // first build with SPH_FLAG_TREE_H_GUESS: h from the tree, node maxima again;
+        // if the largest h no longer fits the top grid, plan and build once more
+        ctx->h_guess_pending = false;
+        k_h_guess<<<nblk(n_nodes, 128), 128, 0, ctx->stream>>>(T.nodes, n_nodes, ctx->d_boxes, ctx->n_boxes,
+                                                              (int)(2.f * ctx->p.n_ngb), ctx->p.n_ngb,
+                                                              ctx->p.box_size, parts->h);
+        SPH_LAUNCH(ctx, "tree h guess");
+        k_node_hmax<<<nblk((int64_t)n_nodes * 32, 256), 256, 0, ctx->stream>>>(T.nodes, n_nodes, parts->h);
+        SPH_LAUNCH(ctx, "node max h");
+        rc = read_box_max_h(ctx, parts);
+        if (rc) return rc;
+        bool fits = true;
+        for (int b = 0; b < ctx->n_boxes; ++b)
+            if ((double)ctx->h_box_hmax[b] * ctx->p.cell_factor > ctx->h_boxes[b].L64) fits = false;
+        if (!fits) {
+            rc = plan_from_hmax(ctx);
+            if (rc) return rc;
+            return build_tree(ctx, parts);
+        }
+    }
     // leaves in particle order
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->keys, 0, sizeof(uint32_t) * std::max(n, 1), ctx->stream));
     k_leaf_marks<<<nblk(n_nodes, 256), 256, 0, ctx->stream>>>(T.nodes, n_nodes, ctx->keys, T.node_at);
@@ -553,9 +738,7 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
     T.n_leaves = nl;
     if ((rc = grow(ctx, T.leaf_node, T.cap_leaf_node, nl + 1)) || (rc = grow(ctx, T.leaf_rng, T.cap_leaf_rng, nl + 1)) ||
         (rc = grow(ctx, T.leaf_cen, T.cap_leaf_cen, 3 * (int64_t)nl + 3)) ||
-        (rc = grow(ctx, T.leaf_h, T.cap_leaf_h, nl + 1)) || (rc = grow(ctx, T.leaf_hc, T.cap_leaf_hc, nl + 1)) ||
-        (rc = grow(ctx, T.leaf_reach, T.cap_leaf_reach, nl + 1)) ||
-        (rc = grow(ctx, T.leaf_scale, T.cap_leaf_scale, nl + 1)) ||
+        (rc = grow(ctx, T.leaf_h, T.cap_leaf_h, nl + 1)) || (rc = grow(ctx, T.leaf_scale, T.cap_leaf_scale, nl + 1)) ||
         (rc = grow(ctx, T.list_off, T.cap_list_off, nl + 2)))
         return rc;
     {
@@ -577,11 +760,35 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
                                                             T.list_off, ctx->d_boxes, ctx->n_boxes, ctx->tiles,
                                                             ctx->n_tiles);
         SPH_LAUNCH(ctx, "leaf tiles");
-        // neighbour lists: count, scan, fill
-        k_pairs_count<<<nblk(nl, 128), 128, 0, ctx->stream>>>(nl, T.leaf_node, T.nodes, T.top_node, T.node_leaf,
-                                                             T.leaf_cen, ctx->d_boxes, ctx->n_boxes, ctx->p.box_size,
-                                                             T.list_off);
-        SPH_LAUNCH(ctx, "pair count");
+        // neighbour lists: count, scan, fill (warp walks; one-thread walks if a warp's
+        // stack overflowed)
+        WalkArgs wa{nl, T.leaf_node, T.nodes, T.top_node, T.node_leaf, T.leaf_cen, ctx->d_boxes, ctx->n_boxes,
+                    ctx->p.box_size, T.list_off, T.list, T.leaf_scale, T.list_off, ctx->counters + C_WALKOVF};
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_WALKOVF, 0, sizeof(unsigned long long), ctx->stream));
+        k_leaf_walk<true><<<nblk(nl, kWalkWarps), 32 * kWalkWarps, 0, ctx->stream>>>(wa);
+        SPH_LAUNCH(ctx, "leaf walk count");
+        SPH_CUDA(ctx, cudaMemcpyAsync(&T.h_u32[8], ctx->counters + C_WALKOVF, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        const bool warp_walk = T.h_u32[8] == 0u;
+        if (!warp_walk) {
+            k_pairs_count<<<nblk(nl, 128), 128, 0, ctx->stream>>>(nl, T.leaf_node, T.nodes, T.top_node, T.node_leaf,
+                                                                 T.leaf_cen, ctx->d_boxes, ctx->n_boxes,
+                                                                 ctx->p.box_size, T.list_off);
+            SPH_LAUNCH(ctx, "pair count");
+        }
+        // the 32-bit offsets must hold the total
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_LISTTOT, 0, sizeof(unsigned long long), ctx->stream));
+        k_sum_u32<<<nblk(std::min(nl, 1 << 20), 256), 256, 0, ctx->stream>>>(T.list_off, nl, ctx->counters + C_LISTTOT);
+        SPH_LAUNCH(ctx, "list total");
+        SPH_CUDA(ctx, cudaMemcpyAsync(&T.h_u32[10], ctx->counters + C_LISTTOT, sizeof(unsigned long long),
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+        SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        unsigned long long total = 0;
+        memcpy(&total, &T.h_u32[10], sizeof total);
+        if (total > 0xfffffffeull)
+            return fail(ctx, SPH_ERR_CAPACITY, "neighbour lists exceed 2^32 - 2 entries (h far above the particle "
+                                               "spacing in dense regions: see SPH_FLAG_TREE_H_GUESS)");
         SPH_CUDA(ctx, cudaMemcpyAsync(&T.h_u32[5], T.list_off + (nl - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost,
                                       ctx->stream));
         rc = exclusive_scan_u32(ctx, T.list_off, T.list_off, nl);
@@ -595,10 +802,16 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
         SPH_CUDA(ctx, cudaMemcpyAsync(T.list_off + nl, &T.h_u32[7], sizeof(uint32_t), cudaMemcpyHostToDevice,
                                       ctx->stream));
         if ((rc = grow(ctx, T.list, T.cap_list, ne + 1))) return rc;
-        k_pairs_fill<<<nblk(nl, 128), 128, 0, ctx->stream>>>(nl, T.leaf_node, T.nodes, T.top_node, T.node_leaf,
-                                                            T.leaf_cen, ctx->d_boxes, ctx->n_boxes, ctx->p.box_size,
-                                                            T.list_off, T.list, T.leaf_scale);
-        SPH_LAUNCH(ctx, "pair fill");
+        if (warp_walk) {
+            wa.list = T.list;
+            k_leaf_walk<false><<<nblk(nl, kWalkWarps), 32 * kWalkWarps, 0, ctx->stream>>>(wa);
+            SPH_LAUNCH(ctx, "leaf walk fill");
+        } else {
+            k_pairs_fill<<<nblk(nl, 128), 128, 0, ctx->stream>>>(nl, T.leaf_node, T.nodes, T.top_node, T.node_leaf,
+                                                                T.leaf_cen, ctx->d_boxes, ctx->n_boxes,
+                                                                ctx->p.box_size, T.list_off, T.list, T.leaf_scale);
+            SPH_LAUNCH(ctx, "pair fill");
+        }
     } else {
         SPH_CUDA(ctx, cudaMemsetAsync(ctx->n_tiles, 0, sizeof(int), ctx->stream));
     }
@@ -608,17 +821,29 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
     return SPH_OK;
 }
 
-// after the density iteration: current largest h per leaf, then per leaf the
-// largest h over itself and its list (the force pass's reach)
-int tree_reach(sph_ctx *ctx)
+// leaves whose largest current h fell below kTreeShrink x their build value
+__global__ void k_leaf_shrink(const int2 *__restrict__ rng, int nl, const float *__restrict__ h,
+                              const float *__restrict__ hb, unsigned long long *__restrict__ count)
 {
-    AdaptiveTree &T = ctx->tree;
-    const int nl = T.n_leaves;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    bool s = false;
+    if (l < nl) {
+        float m = 0.f;
+        for (int p = rng[l].x; p < rng[l].y; ++p) m = fmaxf(m, h[p]);
+        s = m < kTreeShrink * hb[l];
+    }
+    const unsigned b = __ballot_sync(kFull, s);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(count, (unsigned long long)__popc(b));
+}
+
+int tree_shrink_count(sph_ctx *ctx, sph_particles *parts)
+{
+    const int nl = ctx->tree.n_leaves;
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_SHRINK, 0, sizeof(unsigned long long), ctx->stream));
     if (nl <= 0) return SPH_OK;
-    k_leaf_hmax<<<nblk(nl, 256), 256, 0, ctx->stream>>>(T.leaf_rng, nl, ctx->pos4, T.leaf_hc);
-    SPH_LAUNCH(ctx, "leaf max h");
-    k_leaf_reach<<<nblk(nl, 256), 256, 0, ctx->stream>>>(nl, T.list_off, T.list, T.leaf_hc, T.leaf_reach);
-    SPH_LAUNCH(ctx, "leaf reach");
+    k_leaf_shrink<<<nblk(nl, 256), 256, 0, ctx->stream>>>(ctx->tree.leaf_rng, nl, parts->h, ctx->tree.leaf_h,
+                                                         ctx->counters + C_SHRINK);
+    SPH_LAUNCH(ctx, "leaf shrink");
     return SPH_OK;
 }
 
@@ -641,8 +866,8 @@ void free_tree(sph_ctx *ctx)
 {
     AdaptiveTree &T = ctx->tree;
     void *ptrs[] = {ctx->keys64, ctx->keys64_alt, T.leaf_of, T.node_at, T.top_node, T.nodes, T.front, T.front2,
-                    T.bounds, T.nkids, T.node_leaf, T.leaf_node, T.leaf_rng, T.leaf_cen, T.leaf_h, T.leaf_hc,
-                    T.leaf_reach, T.leaf_scale, T.list_off, T.list};
+                    T.bounds, T.nkids, T.node_leaf, T.leaf_node, T.leaf_rng, T.leaf_cen, T.leaf_h,
+                    T.leaf_scale, T.list_off, T.list};
     for (void *p : ptrs) cudaFree(p);
     cudaFreeHost(T.h_u32);
     cudaFreeHost(T.h_i32);

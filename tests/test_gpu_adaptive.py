@@ -52,6 +52,25 @@ def test_adaptive_clustered_matches_oracle():
     assert np.array_equal(np.sort(g["perm"]), np.arange(s.n))
 
 
+def test_adaptive_tree_h_guess():
+    """SPH_FLAG_TREE_H_GUESS: the first build replaces the uniform guess by the tree's
+    local-density estimate; the iteration reaches the same root in fewer passes."""
+    from paper_1508_00115_gb300 import binding
+    d = _clustered(40000, 21, 20)
+    _, _, g0 = gpu_hydro(d, flags=_flags())
+    ctx, parts, g = gpu_hydro(d, flags=_flags() | binding.SPH_FLAG_TREE_H_GUESS)
+    assert g["iters"] < g0["iters"]
+    s = oracle_state(g)
+    t = _targets(g, 400, 2)
+    dd = check_density(g, s, targets=t)
+    check_ghost(g, s, dd, t)
+    check_force(g, s, targets=t)
+    # same root as without the guess, particle by particle: each h meets the
+    # criterion to h_tol = 1e-4 in N_w, and N_w grows like h^k with k >= ~1
+    i0, i1 = np.argsort(g0["perm"]), np.argsort(g["perm"])
+    assert rel(g["h"][i1], g0["h"][i0]).max() <= 3e-4
+
+
 @pytest.mark.parametrize("n,seed,tw", [(1000, 3, 16), (12345, 5, 16), (7000, 6, 32)])
 def test_adaptive_uniform_ragged(n, seed, tw):
     d = inputs.random_velocities(inputs.uniform(n, seed=seed), 0.3, seed + 1)
