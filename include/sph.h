@@ -77,6 +77,10 @@ typedef struct sph_ctx sph_ctx; /* opaque, library-owned */
                                 (4 pi n))^(1/3), so that the density iteration starts
                                 near its root even where the input guess is off by
                                 decades (it converges to the same h) */
+#define SPH_FLAG_HPREDICT 32u /* sph_step / sph_steps start every step's density
+                                iteration at the learned h guess (weights from
+                                sph_hpredict_init / _load / _train) instead of at
+                                the previous h; same root, same h_tol */
 
 typedef struct {
     int64_t n;           /* particles; 0 <= n < 2^31                                  */
@@ -160,6 +164,7 @@ typedef struct {
     float cell_factor;         /* schedule in use: cell side / max h                 */
     int64_t graph_steps;       /* steps replayed from a captured graph (sph_steps)   */
     int32_t leaf_max;          /* adaptive cells: leaf size in use (0: uniform grid) */
+    int64_t hp_samples;        /* learned h: (features, target) pairs collected so far */
 } sph_stats;
 
 /* Fill *p with the defaults: gamma 5/3, n_ngb 48, h_tol 1e-4, alpha 0.8, cfl 0.1,
@@ -179,11 +184,16 @@ int sph_set_n(sph_ctx *ctx, int64_t n);
  * max h)) (>= 3), key each particle by its cell ((iz*nc+iy)*nc+ix with
  * ix = floor(x * nc/L)) and its octant inside the cell (x, y, z at or above the
  * cell centre), stable LSD radix sort by that key, and permute x, y, z, vx, vy,
- * vz, m, u, h and the force outputs ax, ay, az, dudt, vsig IN PLACE into cell
- * order (density outputs are left as they are and are stale until sph_density).
+ * vz, m, u, h, the force outputs ax, ay, az, dudt, vsig and the density outputs
+ * divv and n_ngb IN PLACE into cell order (rho, P, c, f and curl are left as they
+ * are and are stale until sph_density).
  * The composite permutation since the first build (or since sph_reset_ids) is
  * kept: sph_get_permutation.  Host read: max h.
- * Errors: SPH_ERR_H_EXCEEDS_CELL if max h > L/3. */
+ * With SPH_FLAG_ADAPTIVE the grid is the top level (nc >= 1) of an octree keyed
+ * by (top cell, Morton code inside it); the build also forms the leaves and their
+ * neighbour lists (host reads: tree sizes, list total).
+ * Errors: SPH_ERR_H_EXCEEDS_CELL if max h > L/3 (adaptive: max h >= L/2);
+ * SPH_ERR_CAPACITY if the lists would exceed 2^32 - 2 entries. */
 int sph_build_cells(sph_ctx *ctx, sph_particles *parts);
 
 /* Eq. 1 with the smoothing-length iteration: starting from parts->h, Newton steps
@@ -246,6 +256,56 @@ int sph_get_cell_keys(sph_ctx *ctx, int32_t *dev_keys);
 /* Neighbour-set hash of the last density pass (needs SPH_FLAG_NGB_HASH): device,
  * uint64, length n: sum over j != i with r_ij < h_i of splitmix64(perm id of j). */
 int sph_get_ngb_hash(sph_ctx *ctx, uint64_t *dev_hash);
+
+/* ---------------------------------------------------------------------------
+ * Learned initial smoothing lengths (not in the paper).  The h iteration above
+ * (Sec. 2) may start from an MLP's guess instead of the previous h: 6 features per
+ * particle (dt*divv_prev, log(n_ngb_prev/N_ngb), log(h_cell/h_prev),
+ * log(count/N_ngb), log(h_prev/side), dt*vsig_prev/h_prev; "cell" = the
+ * particle's cell, with SPH_FLAG_ADAPTIVE its leaf, h_cell the h of a uniform
+ * medium of the cell's number density) -> 6-64-64-1 MLP with SiLU -> log(h/h_prev),
+ * clamped to [log 1/2, log 1.2].  Weights BF16, activations BF16, accumulation
+ * FP32; features and the target are normalised by means and standard deviations
+ * stored with the weights.
+ *   weights  w_bf16[SPH_HP_NBF16] = W1[64][6], W2[64][64] (row = output unit),
+ *            W3[64]  (raw bfloat16 bits)
+ *   floats   f32[SPH_HP_NF32] = b1[64], b2[64], b3, feature means[6], feature
+ *            standard deviations[6], target mean, target standard deviation
+ * All device arrays are caller-owned; features are row-major n x 6. */
+#define SPH_HP_NBF16 4544
+#define SPH_HP_NF32 143
+
+/* Random (Glorot-uniform) weights from a seed; unit normalisation. */
+int sph_hpredict_init(sph_ctx *ctx, uint64_t seed);
+/* Weights and floats from HOST arrays (layout above). */
+int sph_hpredict_load(sph_ctx *ctx, const uint16_t *w_bf16, const float *f32);
+/* Current weights (BF16, as used for inference) and floats to HOST arrays. */
+int sph_hpredict_save(sph_ctx *ctx, uint16_t *w_bf16, float *f32);
+/* FP32 training state to a HOST array of SPH_HP_NPARAM floats: W1[64][6], b1[64],
+ * W2[64][64], b2[64], W3[64], b3 (the BF16 weights are its rounding). */
+#define SPH_HP_NPARAM 4673
+int sph_hpredict_params(sph_ctx *ctx, float *params);
+/* Features of the current state (after sph_build_cells, before sph_density; the
+ * density/force outputs from the previous hydro pass are the "prev" inputs) with
+ * time step dt, into dev_feats (n x 6); also remembers the current h as h_prev. */
+int sph_hpredict_features(sph_ctx *ctx, sph_particles *parts, double dt, float *dev_feats);
+/* Targets log(h / h_prev) of the remembered h_prev (after sph_density). */
+int sph_hpredict_targets(sph_ctx *ctx, sph_particles *parts, float *dev_target);
+/* Predictions log(h0 / h_prev) for n feature rows (BF16 tensor-core inference,
+ * clamped to [log 1/2, log 1.2]) into dev_out. */
+int sph_hpredict_eval(sph_ctx *ctx, const float *dev_feats, int64_t n, float *dev_out);
+/* Train on n (features, target) pairs: `epochs` passes of ceil(n / 16384) Adam
+ * steps (batch 16384, mean squared error of the normalised target, beta 0.9 /
+ * 0.999).  Sample k of step s is row (s*16384 + k) mod n when seed = 0, else a
+ * hash of (seed, s*16384 + k) mod n.  Initialises the weights (from seed, or 1)
+ * if none were set; the normalisation comes from these samples unless it was
+ * loaded.  *loss_out (host, may be NULL): loss of the last step.  Synchronises. */
+int sph_hpredict_train(sph_ctx *ctx, const float *dev_feats, const float *dev_target, int64_t n,
+                       int32_t epochs, float lr, uint64_t seed, float *loss_out);
+/* Let sph_step append every step's (features, target) pairs to dev_feats (n x 6
+ * per step) and dev_target until `capacity` rows are filled (a step that would
+ * not fit is skipped); capacity 0 stops collecting.  Count: sph_stats.hp_samples. */
+int sph_hpredict_collect(sph_ctx *ctx, float *dev_feats, float *dev_target, int64_t capacity);
 
 /* Stable LSD radix sort of cell keys -- the sort sph_build_cells runs -- for callers
  * that cannot allocate device memory: code whose device memory is owned by another

@@ -33,6 +33,10 @@ SPH_FLAG_NGB_HASH = 2
 SPH_FLAG_AUTOTUNE = 4
 SPH_FLAG_ADAPTIVE = 8
 SPH_FLAG_TREE_H_GUESS = 16
+SPH_FLAG_HPREDICT = 32
+SPH_HP_NBF16 = 4544
+SPH_HP_NF32 = 143
+SPH_HP_NPARAM = 4673
 SPH_SORT_STATIC_MAX_N = 262144
 
 _NAMES = {0: "SPH_OK", 1: "SPH_ERR_INVALID_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_NOT_CONVERGED",
@@ -81,7 +85,8 @@ class sph_stats(ctypes.Structure):
                 ("t_density_ms", ctypes.c_double), ("t_force_ms", ctypes.c_double),
                 ("t_build_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("tile_width", ctypes.c_int32), ("cell_factor", ctypes.c_float),
-                ("graph_steps", ctypes.c_int64), ("leaf_max", ctypes.c_int32)]
+                ("graph_steps", ctypes.c_int64), ("leaf_max", ctypes.c_int32),
+                ("hp_samples", ctypes.c_int64)]
 
 
 _lock = threading.Lock()
@@ -121,6 +126,16 @@ def lib(build_if_missing: bool = True):
             "sph_get_cell_keys": (C, [P, P]),
             "sph_get_ngb_hash": (C, [P, P]),
             "sph_sort_keys_static": (C, [P, P, P, ctypes.c_int64, ctypes.c_int32, P]),
+            "sph_hpredict_init": (C, [P, ctypes.c_uint64]),
+            "sph_hpredict_load": (C, [P, P, P]),
+            "sph_hpredict_save": (C, [P, P, P]),
+            "sph_hpredict_params": (C, [P, P]),
+            "sph_hpredict_features": (C, [P, ctypes.POINTER(sph_particles), ctypes.c_double, P]),
+            "sph_hpredict_targets": (C, [P, ctypes.POINTER(sph_particles), P]),
+            "sph_hpredict_eval": (C, [P, P, ctypes.c_int64, P]),
+            "sph_hpredict_train": (C, [P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64,
+                                       ctypes.POINTER(ctypes.c_float)]),
+            "sph_hpredict_collect": (C, [P, P, P, ctypes.c_int64]),
             "sph_get_stats": (C, [P, ctypes.POINTER(sph_stats)]),
             "sph_reset_stats": (C, [P]),
             "sph_last_error": (ctypes.c_char_p, [P]),
@@ -209,6 +224,60 @@ def sph_step_host(ctx, parts: sph_particles, dt: float = 0.0):
 def _cons_dict(c: sph_conserved) -> dict:
     return dict(momentum=np.array(list(c.momentum)), e_kin=c.e_kin, e_th=c.e_th,
                 e_tot=c.e_kin + c.e_th, dt_next=c.dt_next, u_floors=int(c.u_floors))
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def sph_hpredict_init(ctx, seed: int = 1) -> int:
+    return _check(lib().sph_hpredict_init(ctx, int(seed)), ctx)
+
+
+def sph_hpredict_load(ctx, w_bf16: np.ndarray, f32: np.ndarray) -> int:
+    w = np.ascontiguousarray(w_bf16, dtype=np.uint16)
+    f = np.ascontiguousarray(f32, dtype=np.float32)
+    assert w.size == SPH_HP_NBF16 and f.size == SPH_HP_NF32
+    return _check(lib().sph_hpredict_load(ctx, w.ctypes.data_as(ctypes.c_void_p),
+                                          f.ctypes.data_as(ctypes.c_void_p)), ctx)
+
+
+def sph_hpredict_save(ctx):
+    w = np.zeros(SPH_HP_NBF16, np.uint16)
+    f = np.zeros(SPH_HP_NF32, np.float32)
+    _check(lib().sph_hpredict_save(ctx, w.ctypes.data_as(ctypes.c_void_p), f.ctypes.data_as(ctypes.c_void_p)), ctx)
+    return w, f
+
+
+def sph_hpredict_params(ctx) -> np.ndarray:
+    p = np.zeros(SPH_HP_NPARAM, np.float32)
+    _check(lib().sph_hpredict_params(ctx, p.ctypes.data_as(ctypes.c_void_p)), ctx)
+    return p
+
+
+def sph_hpredict_features(ctx, parts: sph_particles, dt: float, feats) -> int:
+    return _check(lib().sph_hpredict_features(ctx, ctypes.byref(parts), float(dt),
+                                              _ptr(feats) if feats is not None else None), ctx)
+
+
+def sph_hpredict_targets(ctx, parts: sph_particles, target) -> int:
+    return _check(lib().sph_hpredict_targets(ctx, ctypes.byref(parts), _ptr(target)), ctx)
+
+
+def sph_hpredict_eval(ctx, feats, n: int, out) -> int:
+    return _check(lib().sph_hpredict_eval(ctx, _ptr(feats), int(n), _ptr(out)), ctx)
+
+
+def sph_hpredict_train(ctx, feats, target, n: int, epochs: int, lr: float, seed: int = 0) -> float:
+    loss = ctypes.c_float(0)
+    _check(lib().sph_hpredict_train(ctx, _ptr(feats), _ptr(target), int(n), int(epochs), float(lr), int(seed),
+                                    ctypes.byref(loss)), ctx)
+    return float(loss.value)
+
+
+def sph_hpredict_collect(ctx, feats, target, capacity: int) -> int:
+    return _check(lib().sph_hpredict_collect(ctx, _ptr(feats) if feats is not None else None,
+                                             _ptr(target) if target is not None else None, int(capacity)), ctx)
 
 
 def sph_get_stats(ctx) -> dict:
@@ -329,6 +398,46 @@ class Context:
         _check(lib().sph_get_ngb_hash(self.h, ctypes.c_void_p(t.data_ptr())), self.h)
         torch.cuda.synchronize()
         return t[:n].cpu().numpy().view(np.uint64)
+
+    # learned initial h (device tensors in, device tensors out)
+    def hp_init(self, seed: int = 1):
+        return sph_hpredict_init(self.h, seed)
+
+    def hp_load(self, w_bf16, f32):
+        return sph_hpredict_load(self.h, w_bf16, f32)
+
+    def hp_save(self):
+        return sph_hpredict_save(self.h)
+
+    def hp_params(self) -> np.ndarray:
+        return sph_hpredict_params(self.h)
+
+    def hp_features(self, parts: Particles, dt: float):
+        import torch
+        f = torch.empty((max(parts.n, 1), 6), dtype=torch.float32, device="cuda")
+        sph_hpredict_features(self.h, parts.struct(), dt, f)
+        return f[: parts.n]
+
+    def hp_targets(self, parts: Particles):
+        import torch
+        t = torch.empty(max(parts.n, 1), dtype=torch.float32, device="cuda")
+        sph_hpredict_targets(self.h, parts.struct(), t)
+        return t[: parts.n]
+
+    def hp_eval(self, feats):
+        import torch
+        n = int(feats.shape[0])
+        out = torch.empty(max(n, 1), dtype=torch.float32, device="cuda")
+        sph_hpredict_eval(self.h, feats.contiguous(), n, out)
+        return out[:n]
+
+    def hp_train(self, feats, target, epochs: int = 1, lr: float = 1e-3, seed: int = 0) -> float:
+        return sph_hpredict_train(self.h, feats.contiguous(), target.contiguous(), int(target.shape[0]), epochs,
+                                  lr, seed)
+
+    def hp_collect(self, feats, target, capacity: int):
+        self._hp_bufs = (feats, target)  # keep the buffers alive while collecting
+        return sph_hpredict_collect(self.h, feats, target, capacity)
 
     def stats(self) -> dict:
         return sph_get_stats(self.h)

@@ -97,7 +97,7 @@ static int alloc_particles(sph_ctx *c, int64_t cap)
     SPH_CUDA(c, cudaMalloc(&c->vals_alt, sizeof(uint32_t) * cap));
     SPH_CUDA(c, cudaMalloc(&c->hist, sizeof(uint32_t) * 256 * sort_tiles));
     SPH_CUDA(c, cudaMalloc(&c->s64, sizeof(double) * 6 * cap));
-    SPH_CUDA(c, cudaMalloc(&c->s32, sizeof(float) * 8 * cap));
+    SPH_CUDA(c, cudaMalloc(&c->s32, sizeof(float) * 10 * cap));
     SPH_CUDA(c, cudaMalloc(&c->tiles, sizeof(int4) * c->tile_cap));
     SPH_CUDA(c, cudaMalloc(&c->act_tiles, sizeof(int4) * c->tile_cap));
     SPH_CUDA(c, cudaMemsetAsync(c->ngb_hash, 0, sizeof(uint64_t) * cap, c->stream));
@@ -286,12 +286,27 @@ static int do_build(sph_ctx *ctx, sph_particles *parts)
     return rc;
 }
 
-static int hydro(sph_ctx *ctx, sph_particles *parts)
+// build -> density -> force.  in_step: the hydro pass inside a step, where the
+// previous pass's outputs feed the learned h guess and the sample collection.
+static int hydro(sph_ctx *ctx, sph_particles *parts, bool in_step = false)
 {
     int rc = do_build(ctx, parts);
     if (rc) return rc;
+    const bool predict = in_step && (ctx->p.flags & SPH_FLAG_HPREDICT);
+    const bool collect = in_step && ctx->hp.col_feats;
+    if (predict) {
+        rc = hp_apply_step(ctx, parts);
+        if (rc) return rc;
+    } else if (collect) {
+        rc = hp_features(ctx, parts);
+        if (rc) return rc;
+    }
     rc = do_density(ctx, parts, nullptr);
     if (rc) return rc;
+    if (collect) {
+        rc = hp_collect(ctx, parts);
+        if (rc) return rc;
+    }
     return do_force(ctx, parts);
 }
 
@@ -318,7 +333,7 @@ static int do_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_use
     if (rc) return rc;
     // the hydro pass sees v and u predicted to the end of the step (vel4 / upred)
     ctx->predict = true;
-    rc = hydro(ctx, parts);
+    rc = hydro(ctx, parts, true);
     ctx->predict = false;
     if (rc) return rc;
     rc = kick(ctx, parts);
@@ -358,6 +373,10 @@ static int graph_step(sph_ctx *ctx, sph_particles *parts, double dt, int passes)
     ctx->predict = true;
     rc = build_planned(ctx, parts);
     if (rc) return rc;
+    if (ctx->p.flags & SPH_FLAG_HPREDICT) {
+        rc = hp_apply_step(ctx, parts);
+        if (rc) return rc;
+    }
     const int n = (int)ctx->n;
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, n, ctx->stream));
     rc = reset_h_brackets(ctx);
@@ -422,6 +441,10 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
         if (rc) return rc;
     }
     const int passes = std::max(1, std::min(ctx->p.max_h_iter, 6));
+    if (ctx->p.flags & SPH_FLAG_HPREDICT) {  // allocate before any capture
+        rc = hp_ensure(ctx, std::max<int64_t>(ctx->n, 1));
+        if (rc) return rc;
+    }
     // capture one step on a private stream (the caller's may be the legacy default
     // stream, which cannot be captured); the graph is then launched on the caller's
     // stream.  The timing flag is suspended while capturing.  A graph captured for
@@ -618,6 +641,8 @@ int sph_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_used, sph
     if (!ctx) return SPH_ERR_INVALID_ARG;
     if (!parts || (ctx->n > 0 && !parts_ok(parts))) return fail(ctx, SPH_ERR_INVALID_ARG, "null particle array");
     if (!isfinite(dt)) return fail(ctx, SPH_ERR_INVALID_ARG, "dt must be finite");
+    if ((ctx->p.flags & SPH_FLAG_HPREDICT) && !ctx->hp.ready)
+        return fail(ctx, SPH_ERR_STATE, "SPH_FLAG_HPREDICT without predictor weights");
     return do_step(ctx, parts, dt, dt_used, out);
 }
 
@@ -627,6 +652,8 @@ int sph_steps(sph_ctx *ctx, sph_particles *parts, int32_t n_steps, double dt, do
     if (!parts || (ctx->n > 0 && !parts_ok(parts))) return fail(ctx, SPH_ERR_INVALID_ARG, "null particle array");
     if (!isfinite(dt)) return fail(ctx, SPH_ERR_INVALID_ARG, "dt must be finite");
     if (n_steps < 0) return fail(ctx, SPH_ERR_INVALID_ARG, "n_steps must be >= 0");
+    if ((ctx->p.flags & SPH_FLAG_HPREDICT) && !ctx->hp.ready)
+        return fail(ctx, SPH_ERR_STATE, "SPH_FLAG_HPREDICT without predictor weights");
     return do_steps(ctx, parts, n_steps, dt, dt_last, out);
 }
 
@@ -738,6 +765,7 @@ int sph_get_stats(sph_ctx *ctx, sph_stats *s)
     st.tile_width = ctx->tile_w;
     st.cell_factor = ctx->p.cell_factor;
     st.leaf_max = ctx->adaptive ? ctx->leaf_max : 0;
+    st.hp_samples = ctx->hp.col_n;
     *s = st;
     return SPH_OK;
 }
@@ -759,6 +787,85 @@ int sph_reset_stats(sph_ctx *ctx)
     return SPH_OK;
 }
 
+int sph_hpredict_init(sph_ctx *ctx, uint64_t seed)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    return hp_init(ctx, seed);
+}
+
+int sph_hpredict_load(sph_ctx *ctx, const uint16_t *w_bf16, const float *f32)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!w_bf16 || !f32) return fail(ctx, SPH_ERR_INVALID_ARG, "null weight array");
+    return hp_load(ctx, w_bf16, f32);
+}
+
+int sph_hpredict_save(sph_ctx *ctx, uint16_t *w_bf16, float *f32)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!w_bf16 || !f32) return fail(ctx, SPH_ERR_INVALID_ARG, "null weight array");
+    return hp_save(ctx, w_bf16, f32);
+}
+
+int sph_hpredict_params(sph_ctx *ctx, float *params)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!params) return fail(ctx, SPH_ERR_INVALID_ARG, "null array");
+    return hp_params(ctx, params);
+}
+
+int sph_hpredict_features(sph_ctx *ctx, sph_particles *parts, double dt, float *dev_feats)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!parts || (ctx->n > 0 && !parts_ok(parts))) return fail(ctx, SPH_ERR_INVALID_ARG, "null particle array");
+    if (!isfinite(dt) || dt < 0) return fail(ctx, SPH_ERR_INVALID_ARG, "dt must be finite and >= 0");
+    int rc = set_dt(ctx, dt);
+    if (rc) return rc;
+    rc = hp_features(ctx, parts);
+    if (rc) return rc;
+    if (dev_feats && ctx->n > 0)
+        SPH_CUDA(ctx, cudaMemcpyAsync(dev_feats, ctx->hp.feats, sizeof(float) * 6 * ctx->n,
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+    return SPH_OK;
+}
+
+int sph_hpredict_targets(sph_ctx *ctx, sph_particles *parts, float *dev_target)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!parts || !dev_target) return fail(ctx, SPH_ERR_INVALID_ARG, "null array");
+    return hp_targets(ctx, parts, dev_target);
+}
+
+int sph_hpredict_eval(sph_ctx *ctx, const float *dev_feats, int64_t n, float *dev_out)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (n < 0 || n >= (1ll << 31)) return fail(ctx, SPH_ERR_INVALID_ARG, "n must be in [0, 2^31)");
+    if (n > 0 && (!dev_feats || !dev_out)) return fail(ctx, SPH_ERR_INVALID_ARG, "null array");
+    return hp_run(ctx, dev_feats, nullptr, dev_out, n, logf(0.5f), logf(1.2f));
+}
+
+int sph_hpredict_train(sph_ctx *ctx, const float *dev_feats, const float *dev_target, int64_t n, int32_t epochs,
+                       float lr, uint64_t seed, float *loss_out)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (n <= 0 || !dev_feats || !dev_target) return fail(ctx, SPH_ERR_INVALID_ARG, "need n > 0 training pairs");
+    if (epochs < 0 || !(lr > 0.f) || !isfinite(lr)) return fail(ctx, SPH_ERR_INVALID_ARG, "bad epochs or lr");
+    return hp_train(ctx, dev_feats, dev_target, n, epochs, lr, seed, loss_out);
+}
+
+int sph_hpredict_collect(sph_ctx *ctx, float *dev_feats, float *dev_target, int64_t capacity)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (capacity < 0) return fail(ctx, SPH_ERR_INVALID_ARG, "capacity must be >= 0");
+    if (capacity > 0 && (!dev_feats || !dev_target)) return fail(ctx, SPH_ERR_INVALID_ARG, "null buffer");
+    HPredictor &H = ctx->hp;
+    H.col_feats = capacity > 0 ? dev_feats : nullptr;
+    H.col_target = capacity > 0 ? dev_target : nullptr;
+    H.col_cap = capacity;
+    H.col_n = 0;
+    return SPH_OK;
+}
+
 const char *sph_last_error(const sph_ctx *ctx)
 {
     if (!ctx) return "null context";
@@ -771,6 +878,7 @@ void sph_destroy(sph_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     free_particles(ctx);
     free_tree(ctx);
+    hp_free(ctx);
     cudaFree(ctx->cell_start);
     cudaFree(ctx->cell_tiles);
     cudaFree(ctx->counters);

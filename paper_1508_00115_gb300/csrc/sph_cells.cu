@@ -396,6 +396,10 @@ __global__ void k_gather(GatherArgs a)
     a.s32[5 * c + p] = az;
     a.s32[6 * c + p] = du;
     a.s32[7 * c + p] = vs;
+    // the previous hydro pass's divergence and neighbour count travel along (inputs
+    // of the learned h guess)
+    a.s32[8 * c + p] = P.divv[src];
+    a.s32[9 * c + p] = __int_as_float(P.n_ngb[src]);
     a.ids_out[p] = a.ids_valid ? a.ids_in[src] : (int64_t)src;
 }
 
@@ -422,6 +426,8 @@ __global__ void k_copy_back(sph_particles P, const double *__restrict__ s64, con
     P.az[p] = s32[5 * c + p];
     P.dudt[p] = s32[6 * c + p];
     P.vsig[p] = s32[7 * c + p];
+    P.divv[p] = s32[8 * c + p];
+    P.n_ngb[p] = __float_as_int(s32[9 * c + p]);
 }
 
 // cell_start[c] = first slot with cell >= c (lower bound), c in [0, n_cells]

@@ -108,6 +108,25 @@ struct AdaptiveTree {
     int64_t n_entries = 0;
 };
 
+// learned initial h (sph_hpredict.cu)
+struct HPredictor {
+    float *params = nullptr, *adam_m = nullptr, *adam_v = nullptr;  // FP32 parameters, Adam moments
+    float *norm = nullptr;        // feature / target normalisation
+    uint16_t *wbf = nullptr;      // BF16 inference copy
+    float *gpart = nullptr;       // per-block partial gradients
+    double *stat_part = nullptr;  // normalisation sums
+    float *d_loss = nullptr, *h_loss = nullptr;
+    float *feats = nullptr, *h_prev = nullptr;  // features of the current state, h before the iteration
+    int64_t cap = 0;
+    std::vector<float> h_params = std::vector<float>(4673), h_norm = std::vector<float>(14);
+    std::vector<uint16_t> h_wbf = std::vector<uint16_t>(5184);
+    int64_t adam_t = 0;
+    bool ready = false, norm_set = false;
+    // sample collection during sph_step (caller's device buffers)
+    float *col_feats = nullptr, *col_target = nullptr;
+    int64_t col_cap = 0, col_n = 0;
+};
+
 struct Grid {
     int nc = 0;          // box 0 (statistics)
     int64_t n_cells = 0; // all boxes
@@ -143,11 +162,12 @@ struct sph_ctx {
     int64_t hist_cap = 0;
     // permutation scratch (gather targets before the copy back)
     double *s64 = nullptr;  // 6 * cap
-    float *s32 = nullptr;   // 8 * cap
+    float *s32 = nullptr;   // 10 * cap
     // adaptive cells (SPH_FLAG_ADAPTIVE)
     bool adaptive = false;
     int leaf_max = 64;
     bool h_guess_pending = false;  // SPH_FLAG_TREE_H_GUESS before the first build
+    sph::HPredictor hp;            // learned initial h (SPH_FLAG_HPREDICT)
     sph::AdaptiveTree tree;
     // boxes and their cell grids
     int n_boxes = 1;
@@ -252,6 +272,20 @@ int build_tree(sph_ctx *ctx, sph_particles *parts);             // sph_tree.cu
 int tree_cell_keys_out(sph_ctx *ctx, int32_t *dev_keys);        // sph_tree.cu
 int tree_shrink_count(sph_ctx *ctx, sph_particles *parts);      // sph_tree.cu
 int reset_h_brackets(sph_ctx *ctx);                             // sph_pairs.cu
+// sph_hpredict.cu
+int hp_init(sph_ctx *ctx, uint64_t seed);
+int hp_load(sph_ctx *ctx, const uint16_t *w_bf16, const float *f32);
+int hp_save(sph_ctx *ctx, uint16_t *w_bf16, float *f32);
+int hp_params(sph_ctx *ctx, float *out);
+int hp_ensure(sph_ctx *ctx, int64_t n);  // feature buffers for n particles (outside graph capture)
+int hp_features(sph_ctx *ctx, sph_particles *parts);
+int hp_run(sph_ctx *ctx, const float *feats, const float *h_prev, float *out, int64_t n, float log_lo, float log_hi);
+int hp_apply_step(sph_ctx *ctx, sph_particles *parts);
+int hp_targets(sph_ctx *ctx, sph_particles *parts, float *dev_target);
+int hp_collect(sph_ctx *ctx, sph_particles *parts);
+int hp_train(sph_ctx *ctx, const float *X, const float *Y, int64_t n, int epochs, float lr, uint64_t seed,
+             float *loss_out);
+void hp_free(sph_ctx *ctx);
 void free_tree(sph_ctx *ctx);                                   // sph_tree.cu
 int cell_keys_out(sph_ctx *ctx, int32_t *dev_keys);             // sph_cells.cu
 int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool active_list);  // sph_pairs.cu
