@@ -1,6 +1,7 @@
 """Benchmark of the SPH hot path on GB300: KDK steps of the Sedov-Taylor workload.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload sedov|clustered|boxes] [--hpredict]
 
 One step = one pass of the whole hot path over the particle set: kick, drift,
 cell binning (wrap, key, radix sort, permute), density with the smoothing-length
@@ -16,6 +17,11 @@ rank steps its own replica (the path does not shard across GPUs here).
 --impl reference times the FP64 brute-force oracle on this host's cores on a
 bounded sample of the same workload (the oracle is the only other
 implementation of this path), extrapolated to particles/s.
+
+--workload clustered / boxes measure the adaptive-cell path on the clustered halo
+field (256^3) and on 512 batched boxes of uneven occupancy; --hpredict adds the
+learned initial h (trained on another seed before the timed region).  These are
+secondary lines: the default run is the Sedov headline.
 """
 from __future__ import annotations
 
@@ -163,22 +169,52 @@ def workload(seed: int = 2):
     return inputs.sedov(128, seed=seed)
 
 
+def clustered_workload(n_side: int = 256, seed: int = 77):
+    """Clustered halo field: n_side^3 particles, 70% in 200 Plummer spheres (scale
+    radii log-uniform 1e-3..1e-2, halo masses dN/dM ~ M^-1.9), 30% uniform;
+    velocities Gaussian with sigma 0.05, u uniform in [0.5, 2]."""
+    from paper_1508_00115_gb300 import inputs
+    n = n_side ** 3
+    d = inputs.random_velocities(inputs.plummer_mix(n, seed=seed), 0.05, seed + 1)
+    d["u"] = np.random.default_rng(seed + 2).uniform(0.5, 2.0, n)
+    return d
+
+
+def boxes_workload(n_boxes: int = 512, seed: int = 91):
+    """Independent periodic unit boxes, N log-uniform in [1e3, 2e5]; each a
+    uniform-plus-Plummer mix (70% in max(1, N/1000) halos), masses 1/N per box."""
+    from paper_1508_00115_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(1e3), np.log(2e5), n_boxes)).astype(np.int64)
+    parts, offs = [], [0]
+    for b, nb in enumerate(sizes):
+        d = inputs.plummer_mix(int(nb), seed=seed + 10 + b, n_halos=max(1, int(nb) // 1000))
+        d = inputs.random_velocities(d, 0.05, seed + 5000 + b)
+        parts.append(d)
+        offs.append(offs[-1] + int(nb))
+    d = {k: np.concatenate([p[k] for p in parts]) for k in inputs.FIELDS}
+    return d, offs
+
+
 # ------------------------------------------------------------------ CPU oracle
 
 
-def oracle_sample(d: dict, n_force: int, seed: int = 5) -> dict:
+def oracle_sample(d: dict, n_force: int, seed: int = 5, label: str = "Sedov 128^3",
+                  local_radius: bool = False) -> dict:
     """Time the FP64 oracle on a bounded sample of the workload: n_force random
     targets get the full path (h solve + density for them and for every particle
     within 1.5 h of them, then the force sum), each brute-forced against all N.
-    particles/s = 1 / (T_density/S_density + T_force/S_force)."""
+    particles/s = 1 / (T_density/S_density + T_force/S_force).  local_radius: the
+    neighbourhood of a target is 2 x its own h (h spans decades), else 1.5 x max h."""
     import oracle
     n = d["x"].size
     s = oracle.State(**{k: d[k] for k in ("x", "y", "z", "vx", "vy", "vz", "m", "u", "h")})
     rng = np.random.default_rng(seed)
     tf = rng.choice(n, n_force, replace=False)
-    R = 1.5 * float(np.max(d["h"]))
+    R_all = 1.5 * float(np.max(d["h"]))
     near = []
     for i in tf:  # sample selection (not timed): everything that can be a neighbour
+        R = 2.0 * float(d["h"][i]) if local_radius else R_all
         dx = s.x - s.x[i]; dx -= np.rint(dx)
         dy = s.y - s.y[i]; dy -= np.rint(dy)
         dz = s.z - s.z[i]; dz -= np.rint(dz)
@@ -199,7 +235,7 @@ def oracle_sample(d: dict, n_force: int, seed: int = 5) -> dict:
     per = td_s / td.size + tf_s / tf.size
     return {"value": 1.0 / per, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": (f"{td.size} density/h-solve targets + {tf.size} force targets of the "
-                       f"{n}-particle Sedov 128^3 state, each brute-forced against all N "
+                       f"{n}-particle {label} state, each brute-forced against all N "
                        f"(FP64, OpenMP); {td_s:.1f} s + {tf_s:.1f} s"),
             "seconds": td_s + tf_s}
 
@@ -403,6 +439,200 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------- adaptive-cell workloads
+
+
+def _train_predictor(binding, n_side, local, stream):
+    """Learned h guess trained on another seed of the clustered field: two steps at
+    h_tol 1e-6 collected, six epochs.  Returns (weights, floats)."""
+    import torch
+    d = clustered_workload(n_side, seed=5)
+    n = d["x"].size
+    ctx = binding.Context(n, device=local, stream=stream.cuda_stream, h_tol=1e-6, leaf_max=128, tile_width=32,
+                          flags=binding.SPH_FLAG_ADAPTIVE | binding.SPH_FLAG_TREE_H_GUESS)
+    parts = binding.Particles(d)
+    ctx.step(parts)
+    F = torch.zeros((2 * n, 6), dtype=torch.float32, device="cuda")
+    T = torch.zeros(2 * n, dtype=torch.float32, device="cuda")
+    ctx.hp_collect(F, T, 2 * n)
+    ctx.step(parts)
+    ctx.step(parts)
+    ctx.hp_init(1)
+    for ep in range(6):
+        ctx.hp_train(F, T, epochs=1, lr=1e-3 if ep < 4 else 3e-4, seed=ep + 1)
+    wf = ctx.hp_save()
+    ctx.close()
+    return wf
+
+
+def run_adaptive(args):
+    """Clustered halo field (--workload clustered) or batched uneven boxes
+    (--workload boxes) on adaptive cells; one sph_step call per step (tree builds
+    read their sizes on the host, so these steps are not graph-replayed)."""
+    import torch
+    from paper_1508_00115_gb300 import binding
+
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    binding.lib()
+    offs = None
+    if args.workload == "clustered":
+        d = clustered_workload(args.side)
+        label = f"clustered halo field {args.side}^3 (200 Plummer spheres + 30% uniform)"
+    else:
+        d, offs = boxes_workload(args.n_boxes)
+        label = (f"{args.n_boxes} periodic boxes, N log-uniform in [1e3, 2e5], uniform + Plummer "
+                 f"mix, batched in one context")
+    n = int(d["x"].size)
+    stream = torch.cuda.Stream()
+    base = binding.SPH_FLAG_ADAPTIVE | binding.SPH_FLAG_TREE_H_GUESS
+    sched = {}
+    if args.tile_width == 0 and args.leaf_max == 0:
+        base |= binding.SPH_FLAG_AUTOTUNE
+    else:
+        sched = {"tile_width": args.tile_width or 32, "leaf_max": args.leaf_max or 128}
+    wf = _train_predictor(binding, max(64, args.side // 2), local, stream) if args.hpredict else None
+
+    ctx = binding.Context(n, device=local, stream=stream.cuda_stream, box_offsets=offs,
+                          flags=base | binding.SPH_FLAG_TIMING, **sched)
+    parts = binding.Particles(d)
+    for _ in range(args.warmup):
+        ctx.step(parts)
+    st0 = ctx.stats()
+    tuned = {"tile_width": int(st0["tile_width"]), "leaf_max": int(st0["leaf_max"])}
+    snap = {k: v.clone() for k, v in parts.t.items()}
+    ctx.close()
+    torch.cuda.synchronize()
+
+    def timed(flags):
+        for k, v in snap.items():
+            parts.t[k].copy_(v)
+        c = binding.Context(n, device=local, stream=stream.cuda_stream, box_offsets=offs,
+                            flags=flags | binding.SPH_FLAG_TIMING, **tuned)
+        if wf is not None and flags & binding.SPH_FLAG_HPREDICT:
+            c.hp_load(*wf)
+        c.step(parts)  # first hydro on the snapshot, outside the timed region
+        c.reset_stats()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(_gpu_id(local)) if rank == 0 else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        e0.record(stream)
+        fl = 0
+        for _ in range(args.steps):
+            _, cons = c.step(parts)
+            fl += cons["u_floors"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        ms_ = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms_], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_ = float(t.item())
+        st = c.stats()
+        c.close()
+        return ms_, st, clocks, fl
+
+    base_t = binding.SPH_FLAG_ADAPTIVE
+    ms_plain, st_plain, clocks_plain, floors = timed(base_t)
+    if args.hpredict:
+        ms, st, clocks, floors = timed(base_t | binding.SPH_FLAG_HPREDICT)
+    else:
+        ms, st, clocks = ms_plain, st_plain, clocks_plain
+    sec = ms / 1e3
+    value = world * n * args.steps / sec
+    pairs = st["density_pairs"] + st["force_pairs"]
+
+    props = torch.cuda.get_device_properties(local)
+    peak, peak_how = fp32_peak_tflops(props.multi_processor_count, _peaks())
+    kernels = {"density": (st["t_density_ms"], st["density_pairs"] * FLOP_DENSITY_PAIR, st["density_passes"]),
+               "force": (st["t_force_ms"], st["force_pairs"] * FLOP_FORCE_PAIR, st["force_passes"])}
+    dom = max(kernels, key=lambda k: kernels[k][0])
+    t_ms, flops, launches = kernels[dom]
+    achieved = flops / (t_ms / 1e3) / 1e12 if t_ms > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": f"k_{dom} (list mode)", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"derived: {peak_how} (FP32 non-tensor)",
+                "launches": launches, "avg_launch_ms": t_ms / max(launches, 1)}
+
+    e2e = None
+    if not args.no_e2e:
+        ctx_h = binding.Context(n, device=local, stream=stream.cuda_stream, box_offsets=offs,
+                                flags=base | (binding.SPH_FLAG_HPREDICT if args.hpredict else 0), **tuned)
+        if args.hpredict:
+            ctx_h.hp_load(*wf)
+        hp = binding.Particles({k: snap[k].cpu().numpy() for k in snap}, device="cpu", pin=True)
+        ctx_h.step_host(hp)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx_h.step_host(hp)
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": world * n * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": n * (6 * 8 + 8 * 4), "d2h_bytes_per_step": n * (6 * 8 + 14 * 4 + 4)}
+        ctx_h.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        g = {k: snap[k].cpu().numpy().astype(np.float64) for k in ("x", "y", "z", "vx", "vy", "vz", "m", "u",
+                                                                    "h")}
+        if offs is not None:  # the largest box, on its own
+            b = int(np.argmax(np.diff(offs)))
+            g = {k: v[offs[b]:offs[b + 1]] for k, v in g.items()}
+            lab = f"largest box (N={offs[b + 1] - offs[b]}) of the batched set"
+        else:
+            lab = label
+        cpu = oracle_sample(g, n_force=args.cpu_force_targets // 3, label=lab, local_radius=True)
+        cpu.pop("seconds", None)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "path": ("sph_step per step on adaptive cells" + (" with the learned h guess" if args.hpredict else "")),
+           "plain": {"value": world * n * args.steps / (ms_plain / 1e3), "unit": UNIT,
+                     "ms_per_step": ms_plain / args.steps,
+                     "density_passes_per_step": st_plain["density_passes"] / args.steps,
+                     "path": "sph_step per step on adaptive cells, h iteration from the previous h"},
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "dtype_detail": "FP32 pair arithmetic on leaf-relative positions with compensated sums; "
+                           "FP64 positions, kicks/drifts, wrap and global reductions; BF16/FP32 MLP",
+           "data": "synthetic",
+           "config": {"workload": label, "n_particles": n, "n_boxes": len(offs) - 1 if offs else 1,
+                      "n_ngb": 48, "h_tol": 1e-4, "tile_width": tuned["tile_width"],
+                      "leaf_max": tuned["leaf_max"],
+                      "schedule": "autotuned" if not sched else "fixed",
+                      "h_guess": "tree density estimate on the first build; learned MLP guess per step"
+                                 if args.hpredict else "tree density estimate on the first build",
+                      "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
+           "pair_interactions_per_s": world * pairs / sec,
+           "per_step": {"density_pairs": st["density_pairs"] / args.steps,
+                        "force_pairs": st["force_pairs"] / args.steps,
+                        "density_passes": st["density_passes"] / args.steps,
+                        "density_targets": st["density_targets"] / args.steps,
+                        "density_candidates": st["density_candidates"] / args.steps,
+                        "force_candidates": st["force_candidates"] / args.steps,
+                        "rebuilds": st["rebuilds"] / args.steps, "leaves": st["n_cells"],
+                        "t_density_ms": st["t_density_ms"] / args.steps,
+                        "t_force_ms": st["t_force_ms"] / args.steps,
+                        "t_build_ms": st["t_build_ms"] / args.steps, "u_floors": floors / args.steps},
+           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": int(st["kernel_launches"]), "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -414,11 +644,21 @@ def main():
     ap.add_argument("--cpu-force-targets", type=int, default=48)
     ap.add_argument("--tile-width", type=int, default=0, help="16 or 32 (0: autotuned)")
     ap.add_argument("--cell-factor", type=float, default=0.0, help=">= 1 (0: autotuned)")
+    ap.add_argument("--workload", choices=["sedov", "clustered", "boxes"], default="sedov",
+                    help="sedov: Sedov-Taylor 128^3 (the headline); clustered: clustered halo field on "
+                         "adaptive cells; boxes: batched uneven boxes on adaptive cells")
+    ap.add_argument("--side", type=int, default=256, help="clustered: particles per side")
+    ap.add_argument("--n-boxes", type=int, default=512, help="boxes: number of boxes")
+    ap.add_argument("--leaf-max", type=int, default=0, help="adaptive: leaf size (0: autotuned)")
+    ap.add_argument("--hpredict", action="store_true",
+                    help="adaptive workloads: train the learned h guess on another seed and use it")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "sedov":
+        run_adaptive(args)
     else:
         run_ours(args)
 

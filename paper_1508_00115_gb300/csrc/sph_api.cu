@@ -59,7 +59,7 @@ static void free_particles(sph_ctx *c)
 {
     void *ptrs[] = {c->pos4, c->vel4, c->thermo4, c->upred, c->h_lo, c->h_hi, c->active, c->ids, c->ids_tmp, c->ngb_hash,
                     c->keys, c->keys_alt, c->vals, c->vals_alt, c->hist, c->s64, c->s32, c->tiles,
-                    c->act_tiles};
+                    c->act_tiles, c->tile_flag, c->tile_pos};
     for (void *p : ptrs) cudaFree(p);
     c->pos4 = c->vel4 = c->thermo4 = nullptr;
     c->upred = nullptr;
@@ -72,6 +72,7 @@ static void free_particles(sph_ctx *c)
     c->s32 = nullptr;
     c->tiles = nullptr;
     c->act_tiles = nullptr;
+    c->tile_flag = c->tile_pos = nullptr;
     c->cap = 0;
 }
 
@@ -100,6 +101,8 @@ static int alloc_particles(sph_ctx *c, int64_t cap)
     SPH_CUDA(c, cudaMalloc(&c->s32, sizeof(float) * 10 * cap));
     SPH_CUDA(c, cudaMalloc(&c->tiles, sizeof(int4) * c->tile_cap));
     SPH_CUDA(c, cudaMalloc(&c->act_tiles, sizeof(int4) * c->tile_cap));
+    SPH_CUDA(c, cudaMalloc(&c->tile_flag, sizeof(uint32_t) * c->tile_cap));
+    SPH_CUDA(c, cudaMalloc(&c->tile_pos, sizeof(uint32_t) * c->tile_cap));
     SPH_CUDA(c, cudaMemsetAsync(c->ngb_hash, 0, sizeof(uint64_t) * cap, c->stream));
     c->cap = cap;
     return SPH_OK;

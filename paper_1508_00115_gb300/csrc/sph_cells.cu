@@ -107,6 +107,7 @@ int exclusive_scan_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t 
 {
     if (n <= 0) return SPH_OK;
     int64_t nb = (n + kScanChunk - 1) / kScanChunk;
+    if (nb > kScanAuxCap) return fail(ctx, SPH_ERR_CAPACITY, "prefix sum longer than its block-sum scratch");
     k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(in, n, ctx->scan_aux);
     SPH_LAUNCH(ctx, "scan reduce");
     k_scan_top<<<1, kScanThreads, 0, ctx->stream>>>(ctx->scan_aux, nb);

@@ -189,6 +189,7 @@ struct sph_ctx {
     int64_t tile_cap = 0;
     int *n_tiles = nullptr;      // device scalar
     int4 *act_tiles = nullptr;   // tiles with an unconverged target (later density passes)
+    uint32_t *tile_flag = nullptr, *tile_pos = nullptr;  // compaction by prefix sum (tile_cap each)
     int *n_act_tiles = nullptr;  // device scalar
     bool tuned = false;          // autotuner ran
     uint32_t *cell_tiles = nullptr;  // per-cell tile counts -> offsets

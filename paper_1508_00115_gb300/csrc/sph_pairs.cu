@@ -20,7 +20,8 @@
 //      (broadcast shared-memory reads) and records its hits in a 64-bit mask;
 //   2. interactions: every lane walks only its own hits.
 // so the interaction body never runs for a lane that does not need it.
-// Pair arithmetic is FP32 on cell-relative positions with compensated sums;
+// Pair arithmetic is FP32 on cell-relative positions; the terms of one staged batch
+// are summed plainly and the batch sums are accumulated with Kahan compensation;
 // distance tests within a few ulps of the cutoff are re-decided in FP64 so that
 // neighbour sets are exact.
 #include <algorithm>
@@ -250,7 +251,9 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
                 m2 = wd == 2 ? mw : m2;
                 m3 = wd == 3 ? mw : m3;
             }
-            // phase 2: each lane walks its own hits
+            // phase 2: each lane walks its own hits; the batch's terms are summed plainly
+            // (at most kBatchD of them) and the batch sums are added with compensation
+            float rb = 0.f, wb = 0.f;
             while (__any_sync(kFull, (m0 | m1 | m2 | m3) != 0u)) {
                 if (m0 | m1 | m2 | m3) {
                     const int k = pop_bit(m0, m1, m2, m3);
@@ -263,8 +266,8 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
                     float w, dw;
                     spline_u(q, w, dw);
                     const float mj = vj.w;
-                    kahan_add(rho_s, rho_c, mj * w);
-                    kahan_add(sw_s, sw_c, w);
+                    rb = fmaf(mj, w, rb);
+                    wb += w;
                     sqdw = fmaf(q, dw, sqdw);
                     drho = fmaf(mj, fmaf(q, dw, 3.f * w), drho);
                     const float fr = mj * dw * rinv;
@@ -277,6 +280,8 @@ __global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
                     if (HASH) hh += mix64((uint64_t)a.ids[__float_as_int(s.w)]);
                 }
             }
+            kahan_add(rho_s, rho_c, rb);
+            kahan_add(sw_s, sw_c, wb);
             nst = 0;
             __syncwarp();
         };
@@ -620,6 +625,8 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
                 m2 = wd == 2 ? mw : m2;
                 m3 = wd == 3 ? mw : m3;
             }
+            // batch sums plain, compensated across batches
+            float bx = 0.f, by = 0.f, bz = 0.f, bu = 0.f;
             while (__any_sync(kFull, (m0 | m1 | m2 | m3) != 0u)) {
                 if (m0 | m1 | m2 | m3) {
                     const int k = pop_bit(m0, m1, m2, m3);
@@ -646,14 +653,18 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
                         const float dWbar = 0.5f * (dWi + dWj);
                         const float mj = vj.w;
                         const float sc = mj * fmaf(ti.y, dWi, fmaf(tj.y, dWj, Pi * dWbar)) * rinv;
-                        kahan_add(sx_, sxc, -sc * dx);
-                        kahan_add(sy_, syc, -sc * dy);
-                        kahan_add(sz_, szc, -sc * dz);
-                        kahan_add(su, suc, mj * mu * fmaf(ti.y, dWi, 0.5f * Pi * dWbar));
+                        bx = fmaf(-sc, dx, bx);
+                        by = fmaf(-sc, dy, by);
+                        bz = fmaf(-sc, dz, bz);
+                        bu = fmaf(mj * mu, fmaf(ti.y, dWi, 0.5f * Pi * dWbar), bu);
                         vs = fmaxf(vs, ti.z + tj.z - 3.f * fminf(mu, 0.f));
                     }
                 }
             }
+            kahan_add(sx_, sxc, bx);
+            kahan_add(sy_, syc, by);
+            kahan_add(sz_, szc, bz);
+            kahan_add(su, suc, bu);
             nst = 0;
             __syncwarp();
         };
@@ -854,32 +865,43 @@ static int pair_grid(sph_ctx *ctx, int blocks_per_sm)
     return (int)std::max<int64_t>(g, 1);
 }
 
-// Tiles that still hold an unconverged target, for the later density passes
-// (order of the list is irrelevant: every target is summed by one lane).
-__global__ void k_compact_tiles(const int4 *__restrict__ tiles, const int *__restrict__ n_tiles,
-                                const uint8_t *__restrict__ active, int4 *__restrict__ out, int *__restrict__ n_out)
+// Tiles that still hold an unconverged target, for the later density passes, kept
+// in their original order (flags, exclusive prefix sum, scatter): which tiles share
+// a warp, and so where a tile's staged batches end, is then the same on every run,
+// and with it every rounding.
+__global__ void k_tile_flags(const int4 *__restrict__ tiles, const int *__restrict__ n_tiles,
+                             const uint8_t *__restrict__ active, int64_t cap, uint32_t *__restrict__ flag)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cap) return;
     bool keep = false;
-    int4 tile = make_int4(0, 0, 0, 0);
     if (t < *n_tiles) {
-        tile = tiles[t];
+        const int4 tile = tiles[t];
         for (int k = 0; k < tile.z && !keep; ++k) keep = active[tile.y + k] != 0;
     }
-    const unsigned b = __ballot_sync(kFull, keep);
-    const int lane = threadIdx.x & 31;
-    int base = 0;
-    if (lane == 0 && b) base = atomicAdd(n_out, __popc(b));
-    base = __shfl_sync(kFull, base, 0);
-    if (keep) out[base + __popc(b & ((1u << lane) - 1u))] = tile;
+    flag[t] = keep ? 1u : 0u;
+}
+
+__global__ void k_tile_scatter(const int4 *__restrict__ tiles, const uint32_t *__restrict__ flag,
+                               const uint32_t *__restrict__ pos, int64_t cap, int4 *__restrict__ out,
+                               int *__restrict__ n_out)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cap) return;
+    if (flag[t]) out[pos[t]] = tiles[t];
+    if (t == cap - 1) *n_out = (int)(pos[t] + flag[t]);
 }
 
 int compact_active_tiles(sph_ctx *ctx)
 {
-    SPH_CUDA(ctx, cudaMemsetAsync(ctx->n_act_tiles, 0, sizeof(int), ctx->stream));
     const int64_t cap = ctx->tile_cap;
-    k_compact_tiles<<<(unsigned)((cap + 255) / 256), 256, 0, ctx->stream>>>(ctx->tiles, ctx->n_tiles, ctx->active,
-                                                                           ctx->act_tiles, ctx->n_act_tiles);
+    const unsigned blocks = (unsigned)((cap + 255) / 256);
+    k_tile_flags<<<blocks, 256, 0, ctx->stream>>>(ctx->tiles, ctx->n_tiles, ctx->active, cap, ctx->tile_flag);
+    SPH_LAUNCH(ctx, "tile flags");
+    int rc = exclusive_scan_u32(ctx, ctx->tile_flag, ctx->tile_pos, cap);
+    if (rc) return rc;
+    k_tile_scatter<<<blocks, 256, 0, ctx->stream>>>(ctx->tiles, ctx->tile_flag, ctx->tile_pos, cap, ctx->act_tiles,
+                                                   ctx->n_act_tiles);
     SPH_LAUNCH(ctx, "compact tiles");
     return SPH_OK;
 }
