@@ -33,6 +33,8 @@ namespace sph {
 constexpr int kBatchD = 128;  // staged survivors per tile, density (4 hit-mask words)
 constexpr int kBatchF = 128;  // staged survivors per tile, force
 constexpr int kPairThreads = 256;
+constexpr int kDensityBlocks = 2;  // resident blocks per SM the density kernel is compiled for
+constexpr int kForceBlocks = 2;
 // Padding sources sit at -kFar and target-less lanes at +kFar: the squared distance
 // between either and anything else overflows to +inf, so no test can pass.
 constexpr float kFar = 1e30f;
@@ -154,7 +156,7 @@ __device__ __forceinline__ float spline_dw_u(float q)
 }
 
 template <int TW, bool HASH, bool LIST>
-__global__ void __launch_bounds__(kPairThreads, 3) k_density(DensityArgs a)
+__global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(DensityArgs a)
 {
     constexpr int TPW = 32 / TW;
     constexpr int B = kBatchD;
@@ -507,7 +509,7 @@ struct ForceArgs {
 };
 
 template <int TW, bool LIST>
-__global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
+__global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs a)
 {
     constexpr int TPW = 32 / TW;
     constexpr int B = kBatchF;
@@ -571,13 +573,13 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
         int nst = 0;
 
         // exact neighbour decision for the pair (i, j): r < h_i and r < h_j
-        auto decide = [&](float r2, float hj, int j, bool &in_i, bool &in_j) {
+        auto decide = [&](float r2, float hj, const int *jp, bool &in_i, bool &in_j) {
             const float hj2 = hj * hj;
             in_i = r2 < hi2;
             in_j = r2 < hj2;
             const float band_j = kBandK * hj * (hj + L);
             if (fabsf(r2 - hi2) <= band_i || fabsf(r2 - hj2) <= band_j) {
-                const unsigned d = band_decide(a.x, a.y, a.z, i, j, a.box, hi, hj);
+                const unsigned d = band_decide(a.x, a.y, a.z, i, *jp, a.box, hi, hj);
                 in_i = d & 1u;
                 in_j = d & 2u;
             }
@@ -638,7 +640,7 @@ __global__ void __launch_bounds__(kPairThreads, 2) k_force(ForceArgs a)
                     ++cnt;
                     if (r2 > 0.f) {  // the pair (i, i), and coincident pairs, have no direction
                         bool in_i, in_j;
-                        decide(r2, s.w, sI[k], in_i, in_j);
+                        decide(r2, s.w, sI + k, in_i, in_j);
                         const float rinv = rsqrtf(r2);
                         const float r = r2 * rinv;
                         const float hjinv = __fdividef(1.f, s.w);
@@ -947,7 +949,7 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool ac
     a.last_pass = last_pass ? 1 : 0;
     int rc = smem_optin(ctx);
     if (rc) return rc;
-    const int g = pair_grid(ctx, 3);
+    const int g = pair_grid(ctx, kDensityBlocks);
     const bool hash = (ctx->p.flags & SPH_FLAG_NGB_HASH) != 0;
     cudaEvent_t end = nullptr;
     timer_begin(ctx, 0, &end);
@@ -1005,7 +1007,7 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts)
     a.alpha = ctx->p.alpha_visc;
     int rc = smem_optin(ctx);
     if (rc) return rc;
-    const int g = pair_grid(ctx, 2);
+    const int g = pair_grid(ctx, kForceBlocks);
     cudaEvent_t end = nullptr;
     timer_begin(ctx, 1, &end);
     if (ctx->adaptive) {

@@ -219,3 +219,51 @@ def test_adaptive_edge_cases():
     with pytest.raises(binding.SphError) as e:  # a point mass has no h root for its members
         ctx.density(parts)
     assert e.value.code == binding.SPH_ERR_NOT_CONVERGED
+
+
+@pytest.mark.slow
+def test_clustered_256_sampled():
+    """Clustered halo field at full size (256^3 = 16.8M particles) in the bench's
+    schedule (adaptive cells, tree h guess, tile 32, leaf 128); sampled targets --
+    smallest h, largest h, random -- against the brute force over all N."""
+    from paper_1508_00115_gb300 import binding
+    n = 256 ** 3
+    d = inputs.random_velocities(inputs.plummer_mix(n, seed=77), 0.05, 78)
+    d["u"] = np.random.default_rng(79).uniform(0.5, 2.0, n)
+    ctx, parts, g = gpu_hydro(d, flags=_flags() | binding.SPH_FLAG_TREE_H_GUESS, tile_width=32, leaf_max=128)
+    assert g["h"].max() / g["h"].min() > 100.0
+    s = oracle_state(g)
+    t = _targets(g, 100, 4)
+    dd = check_density(g, s, targets=t)
+    check_ghost(g, s, dd, t)
+    check_force(g, s, targets=t[::2])
+
+
+@pytest.mark.slow
+def test_boxes_512_sampled():
+    """512 uneven clustered boxes (17.5M particles, N per box log-uniform in
+    [1e3, 2e5]) batched in one adaptive context; the smallest, the median and the
+    largest box checked against the oracle run on that box alone."""
+    from paper_1508_00115_gb300 import binding
+    rng = np.random.default_rng(91)
+    sizes = np.exp(rng.uniform(np.log(1e3), np.log(2e5), 512)).astype(np.int64)
+    boxes, offs = [], [0]
+    for b, nb in enumerate(sizes):
+        dd = inputs.plummer_mix(int(nb), seed=101 + b, n_halos=max(1, int(nb) // 1000))
+        boxes.append(inputs.random_velocities(dd, 0.05, 5091 + b))
+        offs.append(offs[-1] + int(nb))
+    d = {k: np.concatenate([bx[k] for bx in boxes]) for k in inputs.FIELDS}
+    ctx, parts, g = gpu_hydro(d, flags=_flags() | binding.SPH_FLAG_TREE_H_GUESS, box_offsets=offs,
+                              tile_width=32, leaf_max=128)
+    order = np.argsort(sizes)
+    for b in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        sl = np.arange(offs[b], offs[b + 1])
+        sub = {k: g[k][sl] for k in ("x", "y", "z", "vx", "vy", "vz", "m", "u", "h", "rho", "P", "c", "f",
+                                     "divv", "curl", "n_ngb", "ax", "ay", "az", "dudt", "vsig")}
+        sub["perm"] = g["perm"][sl]  # global ids: the hash terms are those of the batched run
+        sub["ngb_hash"] = g["ngb_hash"][sl]
+        assert np.all((g["perm"][sl] >= offs[b]) & (g["perm"][sl] < offs[b + 1]))
+        s = oracle_state(sub)
+        t = _targets(sub, 100, b)
+        check_density(sub, s, targets=t)
+        check_force(sub, s, targets=t)
