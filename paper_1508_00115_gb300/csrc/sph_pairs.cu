@@ -256,30 +256,48 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
             // phase 2: each lane walks its own hits; the batch's terms are summed plainly
             // (at most kBatchD of them) and the batch sums are added with compensation
             float rb = 0.f, wb = 0.f;
+            // one pair term, evaluated for staged source k
+            auto term = [&](int k, float &w, float &dw, float &q, float &fr, float &mj, float3 &d, float3 &v) {
+                const float4 sk = sA[k];
+                const float4 vj = sB[k];
+                d = make_float3(pi.x - sk.x, pi.y - sk.y, pi.z - sk.z);
+                const float r2 = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+                const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                q = r2 * rinv * hinv;
+                spline_u(q, w, dw);
+                mj = vj.w;
+                fr = mj * dw * rinv;
+                v = make_float3(vi.x - vj.x, vi.y - vj.y, vi.z - vj.z);
+            };
+            auto accumulate = [&](float w, float dw, float q, float fr, float mj, float3 d, float3 v) {
+                rb = fmaf(mj, w, rb);
+                wb += w;
+                sqdw = fmaf(q, dw, sqdw);
+                drho = fmaf(mj, fmaf(q, dw, 3.f * w), drho);
+                dv = fmaf(fr, fmaf(v.x, d.x, fmaf(v.y, d.y, v.z * d.z)), dv);
+                cx = fmaf(fr, fmaf(v.y, d.z, -v.z * d.y), cx);
+                cy = fmaf(fr, fmaf(v.z, d.x, -v.x * d.z), cy);
+                cz = fmaf(fr, fmaf(v.x, d.y, -v.y * d.x), cz);
+            };
+            // two hits per round (independent instruction streams; the terms are still
+            // added in ascending staged order, so the sums are those of one at a time)
             while (__any_sync(kFull, (m0 | m1 | m2 | m3) != 0u)) {
                 if (m0 | m1 | m2 | m3) {
-                    const int k = pop_bit(m0, m1, m2, m3);
-                    const float4 s = sA[k];
-                    const float4 vj = sB[k];
-                    const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                    const float q = r2 * rinv * hinv;
-                    float w, dw;
-                    spline_u(q, w, dw);
-                    const float mj = vj.w;
-                    rb = fmaf(mj, w, rb);
-                    wb += w;
-                    sqdw = fmaf(q, dw, sqdw);
-                    drho = fmaf(mj, fmaf(q, dw, 3.f * w), drho);
-                    const float fr = mj * dw * rinv;
-                    const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
-                    dv = fmaf(fr, fmaf(vx, dx, fmaf(vy, dy, vz * dz)), dv);
-                    cx = fmaf(fr, fmaf(vy, dz, -vz * dy), cx);
-                    cy = fmaf(fr, fmaf(vz, dx, -vx * dz), cy);
-                    cz = fmaf(fr, fmaf(vx, dy, -vy * dx), cz);
-                    ++cnt;
-                    if (HASH) hh += mix64((uint64_t)a.ids[__float_as_int(s.w)]);
+                    const int k1 = pop_bit(m0, m1, m2, m3);
+                    const bool two = (m0 | m1 | m2 | m3) != 0u;
+                    int k2 = k1;
+                    if (two) k2 = pop_bit(m0, m1, m2, m3);
+                    float w1, dw1, q1, fr1, mj1, w2, dw2, q2, fr2, mj2;
+                    float3 d1, v1, d2, v2;
+                    term(k1, w1, dw1, q1, fr1, mj1, d1, v1);
+                    term(k2, w2, dw2, q2, fr2, mj2, d2, v2);
+                    accumulate(w1, dw1, q1, fr1, mj1, d1, v1);
+                    if (two) accumulate(w2, dw2, q2, fr2, mj2, d2, v2);
+                    cnt += two ? 2 : 1;
+                    if (HASH) {
+                        hh += mix64((uint64_t)a.ids[__float_as_int(sA[k1].w)]);
+                        if (two) hh += mix64((uint64_t)a.ids[__float_as_int(sA[k2].w)]);
+                    }
                 }
             }
             kahan_add(rho_s, rho_c, rb);
