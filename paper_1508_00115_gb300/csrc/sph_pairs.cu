@@ -174,6 +174,9 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
     const int ngroups = (ntiles + TPW - 1) / TPW;
     const float inf = __int_as_float(0x7f800000);
 
+    // statistics and flags, kept per lane over all tile groups of this warp and added
+    // to the global counters once at the end (one atomic per warp and counter)
+    unsigned acc_pairs = 0u, acc_cand = 0u, acc_targets = 0u, acc_unc = 0u, acc_hf = 0u;
     for (int grp = gw; grp < ngroups; grp += nw) {
         const int t = grp * TPW + sub;
         const int4 tile = t < ntiles ? a.tiles[t] : make_int4(0, 0, 0, 0);
@@ -334,13 +337,17 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
             e0 = a.list_off[tile.x];
             ne = (int)(a.list_off[tile.x + 1] - e0);
         }
-        int o = -1, ch = 0, nchunk = 0, bs = 0, be = 0;
+        int o = -1, ch = -1, nchunk = 0, bs = 0, be = 0;
         const int ncell = LIST ? (int)__reduce_max_sync(kFull, (unsigned)ne) : (R == 1 ? 27 : 125);
         float shx = 0.f, shy = 0.f, shz = 0.f;
         int pb = 0, pe = 0;  // list entries fetched TW at a time: lane tl holds entry o + tl
         float px = 0.f, py = 0.f, pz = 0.f;
-        for (;;) {
-            while (ch >= nchunk && o < ncell - 1) {
+        // cursor over (cell or list entry o, chunk ch): moves to the next chunk, false at
+        // the end (warp-uniform)
+        auto next_chunk = [&]() -> bool {
+            ++ch;
+            while (ch >= nchunk) {
+                if (o >= ncell - 1) return false;
                 ++o;
                 ch = 0;
                 if (LIST) {
@@ -362,74 +369,82 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
                     shx = __shfl_sync(kFull, px, src, TW);
                     shy = __shfl_sync(kFull, py, src, TW);
                     shz = __shfl_sync(kFull, pz, src, TW);
-                    nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
-                    continue;
-                }
-                int ox, oy, oz;
-                if (R == 1) {
-                    const int src = o < TW ? o : o - TW;
-                    bs = __shfl_sync(kFull, o < TW ? cs0 : cs1, src, TW);
-                    be = __shfl_sync(kFull, o < TW ? ce0 : ce1, src, TW);
-                    ox = kOrder[o][0];
-                    oy = kOrder[o][1];
-                    oz = kOrder[o][2];
                 } else {
-                    ox = o < 27 ? kOrder[o][0] : kOuter[o - 27][0];
-                    oy = o < 27 ? kOrder[o][1] : kOuter[o - 27][1];
-                    oz = o < 27 ? kOrder[o][2] : kOuter[o - 27][2];
-                    bs = be = 0;
-                    if (live) {
-                        const int cb = bx.cell_off + (wrapc(iz + oz, nc) * nc + wrapc(iy + oy, nc)) * nc +
-                                       wrapc(ix + ox, nc);
-                        bs = a.cell_start[cb];
-                        be = a.cell_start[cb + 1];
+                    int ox, oy, oz;
+                    if (R == 1) {
+                        const int src = o < TW ? o : o - TW;
+                        bs = __shfl_sync(kFull, o < TW ? cs0 : cs1, src, TW);
+                        be = __shfl_sync(kFull, o < TW ? ce0 : ce1, src, TW);
+                        ox = kOrder[o][0];
+                        oy = kOrder[o][1];
+                        oz = kOrder[o][2];
+                    } else {
+                        ox = o < 27 ? kOrder[o][0] : kOuter[o - 27][0];
+                        oy = o < 27 ? kOrder[o][1] : kOuter[o - 27][1];
+                        oz = o < 27 ? kOrder[o][2] : kOuter[o - 27][2];
+                        bs = be = 0;
+                        if (live) {
+                            const int cb = bx.cell_off + (wrapc(iz + oz, nc) * nc + wrapc(iy + oy, nc)) * nc +
+                                           wrapc(ix + ox, nc);
+                            bs = a.cell_start[cb];
+                            be = a.cell_start[cb + 1];
+                        }
                     }
+                    shx = (float)ox * L;
+                    shy = (float)oy * L;
+                    shz = (float)oz * L;
                 }
                 nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
-                shx = (float)ox * L;
-                shy = (float)oy * L;
-                shz = (float)oz * L;
             }
-            const bool more = ch < nchunk;  // warp-uniform
-            if (more) {
-                const int j = bs + ch * TW + tl;
-                bool keep = false;
-                float4 pj, vj;
-                if (j < be) {
-                    pj = __ldg(a.pos4 + j);
-                    vj = __ldg(a.vel4 + j);
-                    pj.x += shx;
-                    pj.y += shy;
-                    pj.z += shz;
-                    const float ex = fmaxf(fmaxf(lox - pj.x, pj.x - hix), 0.f);
-                    const float ey = fmaxf(fmaxf(loy - pj.y, pj.y - hiy), 0.f);
-                    const float ez = fmaxf(fmaxf(loz - pj.z, pj.z - hiz), 0.f);
-                    keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < reach2;
-                }
-                const unsigned mine = __ballot_sync(kFull, keep) & gmask;
-                if (keep) {
-                    const int pos = nst + __popc(mine & lt);
-                    sA[pos] = make_float4(pj.x, pj.y, pj.z, __int_as_float(j));
-                    sB[pos] = vj;
-                }
-                nst += __popc(mine);
-                ++ch;
+            return true;
+        };
+        // software pipeline: the positions of the next chunk are loaded before the
+        // current chunk is tested, so their latency overlaps the test, the staging
+        // and a flush
+        bool have = next_chunk();
+        int jc = bs + ch * TW + tl;
+        bool vc = have && jc < be;
+        float4 pc = vc ? __ldg(a.pos4 + jc) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float scx = shx, scy = shy, scz = shz;
+        while (have) {
+            const bool have_n = next_chunk();
+            const int jn = bs + ch * TW + tl;
+            const bool vn = have_n && jn < be;
+            const float4 pn = vn ? __ldg(a.pos4 + jn) : make_float4(0.f, 0.f, 0.f, 0.f);
+            bool keep = false;
+            float4 vj;
+            if (vc) {
+                vj = __ldg(a.vel4 + jc);
+                pc.x += scx;
+                pc.y += scy;
+                pc.z += scz;
+                const float ex = fmaxf(fmaxf(lox - pc.x, pc.x - hix), 0.f);
+                const float ey = fmaxf(fmaxf(loy - pc.y, pc.y - hiy), 0.f);
+                const float ez = fmaxf(fmaxf(loz - pc.z, pc.z - hiz), 0.f);
+                keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < reach2;
             }
+            const unsigned mine = __ballot_sync(kFull, keep) & gmask;
+            if (keep) {
+                const int pos = nst + __popc(mine & lt);
+                sA[pos] = make_float4(pc.x, pc.y, pc.z, __int_as_float(jc));
+                sB[pos] = vj;
+            }
+            nst += __popc(mine);
             const int mx = (int)__reduce_max_sync(kFull, (unsigned)nst);
-            if (mx > B - TW || (!more && mx > 0)) flush();
-            if (!more) break;
+            if (mx > B - TW || (!have_n && mx > 0)) flush();
+            have = have_n;
+            jc = jn;
+            vc = vn;
+            pc = pn;
+            scx = shx;
+            scy = shy;
+            scz = shz;
         }
 
-        // counters (one atomic per warp)
         const int nself = act ? 1 : 0;  // the (i, i) pair is not a neighbour
-        const unsigned long long pairs = warp_sum_ull((unsigned long long)(cnt - nself));
-        const unsigned long long cands =
-            warp_sum_ull(tl == 0 ? (unsigned long long)cand * __popc(amask & gmask) : 0ull);
-        if (lane == 0) {
-            atomicAdd(a.counters + C_DPAIRS, pairs);
-            atomicAdd(a.counters + C_DCAND, cands);
-            atomicAdd(a.counters + C_DTARGETS, (unsigned long long)__popc(amask));
-        }
+        acc_pairs += (unsigned)(cnt - nself);
+        if (tl == 0) acc_cand += cand * (unsigned)__popc(amask & gmask);
+        if (lane == 0) acc_targets += (unsigned)__popc(amask);
 
         // bit 0: not converged; bit 1: h beyond what the cells hold (rebuild needed)
         unsigned flag = 0u;
@@ -494,13 +509,17 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
                 if (HASH) a.ngb_hash[i] = hh - mix64((uint64_t)a.ids[i]);
             }
         }
-        // one atomic per warp and counter
-        const unsigned unc = __ballot_sync(kFull, flag & 1u);
-        const unsigned fl = __reduce_or_sync(kFull, flag & 2u);
-        if (lane == 0) {
-            if (unc) atomicAdd(a.counters + C_UNCONV, (unsigned long long)__popc(unc));
-            if (fl) atomicOr(a.counters + C_HFLAG, 1ull);
-        }
+        acc_unc += flag & 1u;
+        acc_hf |= flag & 2u;
+    }
+    const unsigned long long tp = warp_sum_ull(acc_pairs), tc = warp_sum_ull(acc_cand);  // 64-bit sums
+    const unsigned tu = __reduce_add_sync(kFull, acc_unc), th = __reduce_or_sync(kFull, acc_hf);
+    if (lane == 0) {
+        if (tp) atomicAdd(a.counters + C_DPAIRS, tp);
+        if (tc) atomicAdd(a.counters + C_DCAND, tc);
+        if (acc_targets) atomicAdd(a.counters + C_DTARGETS, (unsigned long long)acc_targets);
+        if (tu) atomicAdd(a.counters + C_UNCONV, (unsigned long long)tu);
+        if (th) atomicOr(a.counters + C_HFLAG, 1ull);
     }
 }
 
@@ -548,6 +567,7 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
     const int ngroups = (ntiles + TPW - 1) / TPW;
     const float inf = __int_as_float(0x7f800000);
 
+    unsigned acc_pairs = 0u, acc_cand = 0u;  // per lane; added to the counters at the end
     for (int grp = gw; grp < ngroups; grp += nw) {
         const int t = grp * TPW + sub;
         const int4 tile = t < ntiles ? a.tiles[t] : make_int4(0, 0, 0, 0);
@@ -814,19 +834,19 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
         }
 
         const int nself = act ? 1 : 0;  // the (i, i) pair is not a neighbour
-        const unsigned long long pairs = warp_sum_ull((unsigned long long)(cnt - nself));
-        const unsigned long long cands =
-            warp_sum_ull(tl == 0 ? (unsigned long long)cand * __popc(amask & gmask) : 0ull);
-        if (lane == 0) {
-            atomicAdd(a.counters + C_FPAIRS, pairs);
-            atomicAdd(a.counters + C_FCAND, cands);
-        }
+        acc_pairs += (unsigned)(cnt - nself);
+        if (tl == 0) acc_cand += cand * (unsigned)__popc(amask & gmask);
         if (!act) continue;
         a.ax[i] = sx_ - sxc;
         a.ay[i] = sy_ - syc;
         a.az[i] = sz_ - szc;
         a.dudt[i] = su - suc;
         a.vsig[i] = vs;
+    }
+    const unsigned long long tp = warp_sum_ull(acc_pairs), tc = warp_sum_ull(acc_cand);  // 64-bit sums
+    if (lane == 0) {
+        if (tp) atomicAdd(a.counters + C_FPAIRS, tp);
+        if (tc) atomicAdd(a.counters + C_FCAND, tc);
     }
 }
 
