@@ -687,9 +687,11 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
                         const float dWj = in_j ? kSigma * spline_dw_u(r * hjinv) * (hj2inv * hj2inv) : 0.f;
                         const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
                         const float mu = fmaf(vx, dx, fmaf(vy, dy, vz * dz)) * rinv;
-                        float Pi = 0.f;
-                        if (mu < 0.f)
-                            Pi = -a.alpha * (ti.z + tj.z - 3.f * mu) * mu * (0.5f * (ti.w + tj.w)) / (ti.x + tj.x);
+                        // viscosity only on approach (mu < 0): branch-free, Pi = 0 otherwise
+                        const float muc = fminf(mu, 0.f);
+                        const float vsig_ij = ti.z + tj.z - 3.f * muc;
+                        const float Pi = -a.alpha * vsig_ij * muc * (0.5f * (ti.w + tj.w)) *
+                                         __fdividef(1.f, ti.x + tj.x);
                         const float dWbar = 0.5f * (dWi + dWj);
                         const float mj = vj.w;
                         const float sc = mj * fmaf(ti.y, dWi, fmaf(tj.y, dWj, Pi * dWbar)) * rinv;
@@ -697,7 +699,7 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
                         by = fmaf(-sc, dy, by);
                         bz = fmaf(-sc, dz, bz);
                         bu = fmaf(mj * mu, fmaf(ti.y, dWi, 0.5f * Pi * dWbar), bu);
-                        vs = fmaxf(vs, ti.z + tj.z - 3.f * fminf(mu, 0.f));
+                        vs = fmaxf(vs, vsig_ij);
                     }
                 }
             }
