@@ -95,6 +95,7 @@ struct DensityArgs {
     const int2 *__restrict__ leaf_rng;
     const float *__restrict__ leaf_scale;
     const float *__restrict__ leaf_hb;
+    const int *__restrict__ tord;  // adaptive: targets of a leaf in ascending h (tiles index this)
     double box;
     float n_ngb_target, h_tol, gamma;
     int use_balsara;
@@ -180,8 +181,8 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
     for (int grp = gw; grp < ngroups; grp += nw) {
         const int t = grp * TPW + sub;
         const int4 tile = t < ntiles ? a.tiles[t] : make_int4(0, 0, 0, 0);
-        const int i = tile.y + tl;
         const bool valid = tl < tile.z;
+        const int i = LIST ? (valid ? a.tord[tile.y + tl] : 0) : tile.y + tl;
         const bool act = valid && a.active[i];
         const unsigned amask = __ballot_sync(kFull, act);
         if (!amask) continue;
@@ -541,6 +542,7 @@ struct ForceArgs {
     const float4 *__restrict__ list;
     const int2 *__restrict__ leaf_rng;
     const float *__restrict__ leaf_scale;
+    const int *__restrict__ tord;
     double box;
     float alpha;
 };
@@ -571,8 +573,8 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
     for (int grp = gw; grp < ngroups; grp += nw) {
         const int t = grp * TPW + sub;
         const int4 tile = t < ntiles ? a.tiles[t] : make_int4(0, 0, 0, 0);
-        const int i = tile.y + tl;
         const bool act = tl < tile.z;
+        const int i = LIST ? (act ? a.tord[tile.y + tl] : 0) : tile.y + tl;
         const unsigned amask = __ballot_sync(kFull, act);
         const bool live = (amask & gmask) != 0;
         // lanes without a target sit far away so that no distance test passes
@@ -912,14 +914,15 @@ static int pair_grid(sph_ctx *ctx, int blocks_per_sm)
 // a warp, and so where a tile's staged batches end, is then the same on every run,
 // and with it every rounding.
 __global__ void k_tile_flags(const int4 *__restrict__ tiles, const int *__restrict__ n_tiles,
-                             const uint8_t *__restrict__ active, int64_t cap, uint32_t *__restrict__ flag)
+                             const uint8_t *__restrict__ active, const int *__restrict__ tord, int64_t cap,
+                             uint32_t *__restrict__ flag)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cap) return;
     bool keep = false;
     if (t < *n_tiles) {
         const int4 tile = tiles[t];
-        for (int k = 0; k < tile.z && !keep; ++k) keep = active[tile.y + k] != 0;
+        for (int k = 0; k < tile.z && !keep; ++k) keep = active[tord ? tord[tile.y + k] : tile.y + k] != 0;
     }
     flag[t] = keep ? 1u : 0u;
 }
@@ -938,7 +941,8 @@ int compact_active_tiles(sph_ctx *ctx)
 {
     const int64_t cap = ctx->tile_cap;
     const unsigned blocks = (unsigned)((cap + 255) / 256);
-    k_tile_flags<<<blocks, 256, 0, ctx->stream>>>(ctx->tiles, ctx->n_tiles, ctx->active, cap, ctx->tile_flag);
+    k_tile_flags<<<blocks, 256, 0, ctx->stream>>>(ctx->tiles, ctx->n_tiles, ctx->active,
+                                                 ctx->adaptive ? ctx->tree.tord : nullptr, cap, ctx->tile_flag);
     SPH_LAUNCH(ctx, "tile flags");
     int rc = exclusive_scan_u32(ctx, ctx->tile_flag, ctx->tile_pos, cap);
     if (rc) return rc;
@@ -981,6 +985,7 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool ac
     a.leaf_rng = ctx->tree.leaf_rng;
     a.leaf_scale = ctx->tree.leaf_scale;
     a.leaf_hb = ctx->tree.leaf_h;
+    a.tord = ctx->tree.tord;
     a.box = ctx->p.box_size;
     a.n_ngb_target = ctx->p.n_ngb;
     a.h_tol = ctx->p.h_tol;
@@ -1036,6 +1041,7 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts)
     a.list = ctx->tree.list;
     a.leaf_rng = ctx->tree.leaf_rng;
     a.leaf_scale = ctx->tree.leaf_scale;
+    a.tord = ctx->tree.tord;
     a.ax = parts->ax;
     a.ay = parts->ay;
     a.az = parts->az;

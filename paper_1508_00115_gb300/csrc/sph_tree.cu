@@ -357,6 +357,37 @@ __global__ void k_leaf_pos(const int *__restrict__ leaf_of, const double *__rest
                           (float)(z[p] - leaf_cen[3 * l + 2]), h[p]);
 }
 
+// Targets of every leaf in ascending h (ties by slot), so that a tile holds targets of
+// similar h: its reach -- and with it the candidates of every target -- is not set by
+// one large-h particle among small ones.  One warp per leaf; leaves above kSortMax
+// particles keep their order.
+constexpr int kSortMax = 256;
+constexpr int kSortWarps = 4;
+__global__ void __launch_bounds__(32 * kSortWarps) k_leaf_hsort(const int2 *__restrict__ rng, int nl,
+                                                                const float *__restrict__ h, int *__restrict__ tord)
+{
+    __shared__ float sh[kSortWarps][kSortMax];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int l = blockIdx.x * kSortWarps + wib;
+    if (l >= nl) return;  // warp-uniform
+    const int lo = rng[l].x, c = rng[l].y - lo;
+    if (c > kSortMax) {
+        for (int k = lane; k < c; k += 32) tord[lo + k] = lo + k;
+        return;
+    }
+    for (int k = lane; k < c; k += 32) sh[wib][k] = h[lo + k];
+    __syncwarp();
+    for (int k = lane; k < c; k += 32) {
+        const float hk = sh[wib][k];
+        int rank = 0;
+        for (int m = 0; m < c; ++m) {
+            const float hm = sh[wib][m];
+            rank += (hm < hk || (hm == hk && m < k)) ? 1 : 0;
+        }
+        tord[lo + rank] = lo + k;
+    }
+}
+
 __global__ void k_leaf_tiles_n(const int2 *__restrict__ rng, int nl, int tw, uint32_t *__restrict__ nt)
 {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
@@ -628,6 +659,7 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
     int64_t np = std::max<int64_t>(ctx->cap, 1);
     if ((rc = grow(ctx, ctx->keys64, T.cap_keys, np)) || (rc = grow(ctx, ctx->keys64_alt, T.cap_keys2, np)) ||
         (rc = grow(ctx, T.leaf_of, T.cap_leaf_of, np)) || (rc = grow(ctx, T.node_at, T.cap_node_at, np)) ||
+        (rc = grow(ctx, T.tord, T.cap_tord, np)) ||
         (rc = grow(ctx, T.top_node, T.cap_top, ntop + 1)))
         return rc;
     if (!T.h_u32) SPH_CUDA(ctx, cudaMallocHost(&T.h_u32, 16 * sizeof(uint32_t)));
@@ -752,6 +784,8 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
     }
     // tiles
     if (nl > 0) {
+        k_leaf_hsort<<<nblk(nl, kSortWarps), 32 * kSortWarps, 0, ctx->stream>>>(T.leaf_rng, nl, parts->h, T.tord);
+        SPH_LAUNCH(ctx, "leaf h order");
         k_leaf_tiles_n<<<nblk(nl, 256), 256, 0, ctx->stream>>>(T.leaf_rng, nl, ctx->tile_w, T.list_off);
         SPH_LAUNCH(ctx, "leaf tile counts");
         rc = exclusive_scan_u32(ctx, T.list_off, T.list_off, nl);
@@ -865,7 +899,7 @@ int tree_cell_keys_out(sph_ctx *ctx, int32_t *dev_keys)
 void free_tree(sph_ctx *ctx)
 {
     AdaptiveTree &T = ctx->tree;
-    void *ptrs[] = {ctx->keys64, ctx->keys64_alt, T.leaf_of, T.node_at, T.top_node, T.nodes, T.front, T.front2,
+    void *ptrs[] = {ctx->keys64, ctx->keys64_alt, T.leaf_of, T.tord, T.node_at, T.top_node, T.nodes, T.front, T.front2,
                     T.bounds, T.nkids, T.node_leaf, T.leaf_node, T.leaf_rng, T.leaf_cen, T.leaf_h,
                     T.leaf_scale, T.list_off, T.list};
     for (void *p : ptrs) cudaFree(p);
