@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "sph_internal.cuh"
 
@@ -150,18 +151,51 @@ __global__ void k_roots(const int *__restrict__ cs, int64_t ntop, const uint32_t
     front[id] = id;
 }
 
-// per frontier node: largest h and bounding box (relative to the top-cell centre) of
-// its particles, and its non-empty children if it is to be refined.  One warp/node.
-__global__ void k_node_stats(const int *__restrict__ front, int nfront, TreeNode *__restrict__ nodes,
-                             const uint64_t *__restrict__ keys, const double *__restrict__ x,
-                             const double *__restrict__ y, const double *__restrict__ z, const float *__restrict__ h,
-                             const BoxDev *__restrict__ bxs, int nb, int leaf_max, int *__restrict__ bounds,
+// Refinement decision of every frontier node (one thread per node): a node is split
+// while it holds more than leaf_max particles (down to the Morton resolution); its
+// non-empty children's particle ranges come from binary searches on the next Morton
+// digit.
+__global__ void k_node_split(const int *__restrict__ front, int nfront, const TreeNode *__restrict__ nodes,
+                             const uint64_t *__restrict__ keys, int leaf_max, int *__restrict__ bounds,
                              uint32_t *__restrict__ nkids)
 {
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= nfront) return;
-    const int id = front[w];
-    TreeNode t = nodes[id];
+    const TreeNode t = nodes[front[w]];
+    const bool split = (t.hi - t.lo) > leaf_max && t.level < kMortonBits;
+    int cnt = 0;
+    if (split) {
+        // child boundaries: first slot whose next Morton digit is >= k (k = 1..7)
+        const int sh = 3 * (kMortonBits - 1 - t.level);
+        int b[9];
+        b[0] = t.lo;
+        b[8] = t.hi;
+        for (int k = 1; k < 8; ++k) {
+            int lo = b[k - 1], hi = t.hi;  // digits are sorted: search from the previous bound
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((int)((keys[mid] >> sh) & 7u) < k) lo = mid + 1;
+                else hi = mid;
+            }
+            b[k] = lo;
+        }
+        for (int k = 0; k < 9; ++k) bounds[9 * w + k] = b[k];
+        for (int k = 0; k < 8; ++k) cnt += b[k + 1] > b[k] ? 1 : 0;
+    }
+    nkids[w] = (uint32_t)cnt;
+}
+
+// Largest h and bounding box (relative to the top-cell centre) of every leaf, one warp
+// per leaf node; the box is widened by one FP32 ulp of the top cell so that rounding of
+// the positions never shrinks it.
+__global__ void k_leaf_box(TreeNode *__restrict__ nodes, int n_nodes, const double *__restrict__ x,
+                           const double *__restrict__ y, const double *__restrict__ z, const float *__restrict__ h,
+                           const BoxDev *__restrict__ bxs, int nb)
+{
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= n_nodes) return;
+    TreeNode t = nodes[w];
+    if (t.child >= 0) return;  // warp-uniform
     const BoxDev g = bxs[nb == 1 ? 0 : tbox_of_cell(t.top, bxs, nb)];
     const int loc = t.top - g.cell_off;
     const double cx = ((double)(loc % g.nc) + 0.5) * g.L64, cy = ((double)((loc / g.nc) % g.nc) + 0.5) * g.L64,
@@ -187,32 +221,8 @@ __global__ void k_node_stats(const int *__restrict__ front, int nfront, TreeNode
         z0 = fminf(z0, __shfl_xor_sync(kFull, z0, o));
         z1 = fmaxf(z1, __shfl_xor_sync(kFull, z1, o));
     }
-    // the bounding box is widened by one FP32 ulp of the top cell so that rounding of
-    // the positions above never shrinks it
-    const float pad = g.L32 * 1.2e-7f;
-    // refine while there are too many particles (down to the Morton resolution)
-    const bool split = (t.hi - t.lo) > leaf_max && t.level < kMortonBits;
-    int cnt = 0;
-    if (split) {
-        // child boundaries: first slot whose next Morton digit is >= k (k = 1..7)
-        const int sh = 3 * (kMortonBits - 1 - t.level);
-        int b[9];
-        b[0] = t.lo;
-        b[8] = t.hi;
-        for (int k = 1; k < 8; ++k) {
-            int lo = t.lo, hi = t.hi;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if ((int)((keys[mid] >> sh) & 7u) < k) lo = mid + 1;
-                else hi = mid;
-            }
-            b[k] = lo;
-        }
-        if (lane == 0)
-            for (int k = 0; k < 9; ++k) bounds[9 * w + k] = b[k];
-        for (int k = 0; k < 8; ++k) cnt += b[k + 1] > b[k] ? 1 : 0;
-    }
     if (lane == 0) {
+        const float pad = g.L32 * 1.2e-7f;
         t.hmax = hm;
         t.bx0 = x0 - pad;
         t.by0 = y0 - pad;
@@ -220,9 +230,36 @@ __global__ void k_node_stats(const int *__restrict__ front, int nfront, TreeNode
         t.bx1 = x1 + pad;
         t.by1 = y1 + pad;
         t.bz1 = z1 + pad;
-        nodes[id] = t;
-        nkids[w] = (uint32_t)cnt;
+        nodes[w] = t;
     }
+}
+
+// internal nodes of one level [first, last): union of their children's boxes and max h
+__global__ void k_merge_children(TreeNode *__restrict__ nodes, int first, int last)
+{
+    const int id = first + blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= last) return;
+    TreeNode t = nodes[id];
+    if (t.child < 0) return;
+    float hm = 0.f, x0 = 1e30f, y0 = 1e30f, z0 = 1e30f, x1 = -1e30f, y1 = -1e30f, z1 = -1e30f;
+    for (int c = t.child; c < t.child + t.nchild; ++c) {
+        const TreeNode k = nodes[c];
+        hm = fmaxf(hm, k.hmax);
+        x0 = fminf(x0, k.bx0);
+        y0 = fminf(y0, k.by0);
+        z0 = fminf(z0, k.bz0);
+        x1 = fmaxf(x1, k.bx1);
+        y1 = fmaxf(y1, k.by1);
+        z1 = fmaxf(z1, k.bz1);
+    }
+    t.hmax = hm;
+    t.bx0 = x0;
+    t.by0 = y0;
+    t.bz0 = z0;
+    t.bx1 = x1;
+    t.by1 = y1;
+    t.bz1 = z1;
+    nodes[id] = t;
 }
 
 // children of the refined frontier nodes, numbered in frontier order (deterministic)
@@ -277,19 +314,6 @@ __global__ void k_h_guess(const TreeNode *__restrict__ nodes, int n_nodes, const
     double h0 = cbrt(3.0 * (double)n_ngb / (4.0 * 3.14159265358979323846 * dens));
     h0 = fmin(h0, 0.45 * box);
     for (int p = t.lo; p < t.hi; ++p) h[p] = (float)h0;
-}
-
-// largest h of every node (one warp per node)
-__global__ void k_node_hmax(TreeNode *__restrict__ nodes, int n_nodes, const float *__restrict__ h)
-{
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (w >= n_nodes) return;
-    const int lo = nodes[w].lo, hi = nodes[w].hi;
-    float m = 0.f;
-    for (int p = lo + lane; p < hi; p += 32) m = fmaxf(m, h[p]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
-    if (lane == 0) nodes[w].hmax = m;
 }
 
 __global__ void k_sum_u32(const uint32_t *__restrict__ v, int n, unsigned long long *__restrict__ out)
@@ -711,11 +735,11 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
     // refine level by level (host reads the next frontier size)
     int n_nodes = (int)nroot, nfront = (int)nroot;
     int *cur = T.front, *nxt = T.front2;
+    std::vector<int> level_begin(1, 0);  // nodes of level L: [level_begin[L], level_begin[L + 1])
     for (int level = 0; level <= kMortonBits && nfront > 0; ++level) {
-        k_node_stats<<<nblk((int64_t)nfront * 32, 256), 256, 0, ctx->stream>>>(
-            cur, nfront, T.nodes, ctx->keys64, parts->x, parts->y, parts->z, parts->h, ctx->d_boxes, ctx->n_boxes,
-            ctx->leaf_max, T.bounds, T.nkids);
-        SPH_LAUNCH(ctx, "node stats");
+        k_node_split<<<nblk(nfront, 256), 256, 0, ctx->stream>>>(cur, nfront, T.nodes, ctx->keys64, ctx->leaf_max,
+                                                                 T.bounds, T.nkids);
+        SPH_LAUNCH(ctx, "node split");
         SPH_CUDA(ctx, cudaMemcpyAsync(&T.h_u32[1], T.nkids + (nfront - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost,
                                       ctx->stream));
         rc = exclusive_scan_u32(ctx, T.nkids, T.nkids, nfront);
@@ -724,6 +748,7 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
                                       ctx->stream));
         SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         const int nnext = (int)(T.h_u32[1] + T.h_u32[2]);
+        level_begin.push_back(n_nodes);
         if (nnext == 0) break;
         if ((int64_t)n_nodes + nnext > T.cap_nodes) return fail(ctx, SPH_ERR_INVALID_ARG, "tree node capacity exceeded");
         k_make_children<<<nblk(nfront, 256), 256, 0, ctx->stream>>>(cur, nfront, T.nodes, T.bounds, T.nkids,
@@ -734,6 +759,25 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
         std::swap(cur, nxt);
     }
     T.n_nodes = n_nodes;
+    if (level_begin.back() != n_nodes) level_begin.push_back(n_nodes);
+    // largest h and bounding box of every node: leaves from their particles, then the
+    // levels upwards from their children
+    auto node_boxes = [&]() -> int {
+        k_leaf_box<<<nblk((int64_t)n_nodes * 32, 256), 256, 0, ctx->stream>>>(
+            T.nodes, n_nodes, parts->x, parts->y, parts->z, parts->h, ctx->d_boxes, ctx->n_boxes);
+        SPH_LAUNCH(ctx, "leaf boxes");
+        for (int L = (int)level_begin.size() - 2; L >= 0; --L) {
+            const int first = level_begin[L], last = level_begin[L + 1];
+            if (last <= first) continue;
+            k_merge_children<<<nblk(last - first, 256), 256, 0, ctx->stream>>>(T.nodes, first, last);
+            SPH_LAUNCH(ctx, "merge children");
+        }
+        return SPH_OK;
+    };
+    if (n > 0) {
+        rc = node_boxes();
+        if (rc) return rc;
+    }
     if (ctx->h_guess_pending) {
         // first build with SPH_FLAG_TREE_H_GUESS: h from the tree, node maxima again;
         // if the largest h no longer fits the top grid, plan and build once more
@@ -742,8 +786,8 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
                                                               (int)(2.f * ctx->p.n_ngb), ctx->p.n_ngb,
                                                               ctx->p.box_size, parts->h);
         SPH_LAUNCH(ctx, "tree h guess");
-        k_node_hmax<<<nblk((int64_t)n_nodes * 32, 256), 256, 0, ctx->stream>>>(T.nodes, n_nodes, parts->h);
-        SPH_LAUNCH(ctx, "node max h");
+        rc = node_boxes();
+        if (rc) return rc;
         rc = read_box_max_h(ctx, parts);
         if (rc) return rc;
         bool fits = true;
