@@ -159,9 +159,10 @@ def _traffic(kernel: str):
 
 def _schedule(args, binding) -> dict:
     """Tile width / cell factor: fixed when given, else chosen by the autotuner."""
+    sweep = binding.SPH_FLAG_AXIS_SWEEP if getattr(args, "axis_sweep", False) else 0
     if args.tile_width == 0 and args.cell_factor == 0:
-        return {"flags": binding.SPH_FLAG_AUTOTUNE}
-    return {"flags": 0, "tile_width": args.tile_width or 16, "cell_factor": args.cell_factor or 1.1}
+        return {"flags": binding.SPH_FLAG_AUTOTUNE | sweep}
+    return {"flags": sweep, "tile_width": args.tile_width or 16, "cell_factor": args.cell_factor or 1.1}
 
 
 def workload(seed: int = 2):
@@ -330,7 +331,8 @@ def run_ours(args):
     for k, v in snap.items():
         parts.t[k].copy_(v)
     ctx.close()
-    ctx = binding.Context(n, device=local, stream=stream.cuda_stream, **tuned)
+    ctx = binding.Context(n, device=local, stream=stream.cuda_stream,
+                          flags=binding.SPH_FLAG_AXIS_SWEEP if args.axis_sweep else 0, **tuned)
     ctx.steps(parts, 0)
     sampler = ClockSampler(_gpu_id(local)) if rank == 0 else None
     if sampler:
@@ -414,6 +416,7 @@ def run_ours(args):
                       "cell_factor": round(float(st["cell_factor"]), 3),
                       "schedule": "autotuned" if args.tile_width == 0 and args.cell_factor == 0
                                   else "fixed",
+                      "pruning": "axis sweep + tile box" if args.axis_sweep else "tile box",
                       "l2": f"inputs larger than L2 (~{work_mb:.0f} MB resident per step > 129 MB)",
                       "parallelism": f"replicas x{world}"},
            "pair_interactions_per_s": world * pairs / sec,
@@ -650,6 +653,8 @@ def main():
     ap.add_argument("--side", type=int, default=256, help="clustered: particles per side")
     ap.add_argument("--n-boxes", type=int, default=512, help="boxes: number of boxes")
     ap.add_argument("--leaf-max", type=int, default=0, help="adaptive: leaf size (0: autotuned)")
+    ap.add_argument("--axis-sweep", action="store_true",
+                    help="sedov: sort cells along the 13 half-stencil axes and sweep (SPH_FLAG_AXIS_SWEEP)")
     ap.add_argument("--hpredict", action="store_true",
                     help="adaptive workloads: train the learned h guess on another seed and use it")
     args = ap.parse_args()

@@ -81,6 +81,14 @@ typedef struct sph_ctx sph_ctx; /* opaque, library-owned */
                                 iteration at the learned h guess (weights from
                                 sph_hpredict_init / _load / _train) instead of at
                                 the previous h; same root, same h_tol */
+#define SPH_FLAG_AXIS_SWEEP 64u /* uniform grid: after each build, sort every cell's
+                                particles along the 13 half-stencil directions (Sec. 3.1,
+                                "sorting"); the pair passes then read a neighbour
+                                cell in the order of the direction joining the two
+                                cells and skip the particles whose projected distance
+                                already exceeds the cutoff (exact: projected distance
+                                <= distance).  Default off: the tile bounding-box test
+                                alone prunes the same pairs */
 
 typedef struct {
     int64_t n;           /* particles; 0 <= n < 2^31                                  */

@@ -34,6 +34,7 @@ SPH_FLAG_AUTOTUNE = 4
 SPH_FLAG_ADAPTIVE = 8
 SPH_FLAG_TREE_H_GUESS = 16
 SPH_FLAG_HPREDICT = 32
+SPH_FLAG_AXIS_SWEEP = 64
 SPH_HP_NBF16 = 4544
 SPH_HP_NF32 = 143
 SPH_HP_NPARAM = 4673

@@ -881,6 +881,7 @@ void sph_destroy(sph_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     free_particles(ctx);
     free_tree(ctx);
+    cudaFree(ctx->axis);
     hp_free(ctx);
     cudaFree(ctx->cell_start);
     cudaFree(ctx->cell_tiles);

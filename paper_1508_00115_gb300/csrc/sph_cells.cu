@@ -655,7 +655,7 @@ int permute_particles(sph_ctx *ctx, sph_particles *parts, bool cell_pos)
 {
     const int n = (int)ctx->n;
     if (n <= 0) return SPH_OK;
-    GatherArgs ga;
+    GatherArgs ga{};
     ga.P = *parts;
     ga.perm = ctx->vals;
     ga.skeys = cell_pos ? ctx->keys : nullptr;
@@ -709,8 +709,79 @@ int build_planned(sph_ctx *ctx, sph_particles *parts)
         ctx->cell_start, g.n_cells, ctx->tile_w, ctx->cell_tiles, ctx->d_boxes, ctx->n_boxes, ctx->tiles,
         ctx->n_tiles);
     SPH_LAUNCH(ctx, "tiles");
+    if ((ctx->p.flags & SPH_FLAG_AXIS_SWEEP) && n > 0) {
+        rc = axis_sort(ctx);
+        if (rc) return rc;
+    }
     ctx->built = true;
     ctx->density_valid = false;
+    return SPH_OK;
+}
+
+// ------------------------------------------------------ per-axis cell orders
+// Sec. 3.1 ("sorting"): the particles of a cell, sorted by their projection on the
+// axis joining it to a neighbour, let a pair sweep stop once the projected distance
+// exceeds the cutoff.  The 13 directions of a half stencil cover all 26 neighbours
+// (a neighbour in direction -d reads the order of d backwards).
+
+__constant__ signed char kAxisDir[13][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0},  {1, -1, 0},
+                                            {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
+                                            {1, 1, -1}, {1, -1, 1}, {1, -1, -1}};
+constexpr int kAxisMax = 256;  // cells above this keep slot order (their sweep never stops early)
+constexpr int kAxisWarps = 4;
+
+// one warp per cell: projections (cell-relative FP32 positions, unit directions) and
+// their ranks (ties by slot); a cell too large for the shared buffer is written in
+// slot order with projections -inf, so that no sweep stops inside it
+__global__ void __launch_bounds__(32 * kAxisWarps) k_axis_sort(const int *__restrict__ cs, int64_t ncells,
+                                                                const float4 *__restrict__ pos4, int64_t cap,
+                                                                float2 *__restrict__ axis)
+{
+    __shared__ float sp[kAxisWarps][kAxisMax];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * kAxisWarps + wib;
+    if (c >= ncells) return;  // warp-uniform
+    const int b = cs[c], cnt = cs[c + 1] - b;
+    for (int d = 0; d < 13; ++d) {
+        const float dx = kAxisDir[d][0], dy = kAxisDir[d][1], dz = kAxisDir[d][2];
+        const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+        float2 *out = axis + (size_t)d * cap + b;
+        if (cnt > kAxisMax) {
+            for (int k = lane; k < cnt; k += 32) out[k] = make_float2(-INFINITY, __int_as_float(b + k));
+            continue;
+        }
+        for (int k = lane; k < cnt; k += 32) {
+            const float4 p = pos4[b + k];
+            sp[wib][k] = (p.x * dx + p.y * dy + p.z * dz) * inv;
+        }
+        __syncwarp();
+        for (int k = lane; k < cnt; k += 32) {
+            const float sk = sp[wib][k];
+            int rank = 0;
+            for (int m = 0; m < cnt; ++m) {
+                const float sm = sp[wib][m];
+                rank += (sm < sk || (sm == sk && m < k)) ? 1 : 0;
+            }
+            out[rank] = make_float2(sk, __int_as_float(b + k));
+        }
+        __syncwarp();
+    }
+}
+
+int axis_sort(sph_ctx *ctx)
+{
+    const int64_t need = 13 * std::max<int64_t>(ctx->cap, 1);
+    if (ctx->axis_cap < need) {
+        cudaFree(ctx->axis);
+        ctx->axis = nullptr;
+        ctx->axis_cap = 0;
+        SPH_CUDA(ctx, cudaMalloc(&ctx->axis, sizeof(float2) * need));
+        ctx->axis_cap = need;
+    }
+    const int64_t nc = ctx->grid.n_cells;
+    k_axis_sort<<<(unsigned)((nc + kAxisWarps - 1) / kAxisWarps), 32 * kAxisWarps, 0, ctx->stream>>>(
+        ctx->cell_start, nc, ctx->pos4, std::max<int64_t>(ctx->cap, 1), ctx->axis);
+    SPH_LAUNCH(ctx, "axis sort");
     return SPH_OK;
 }
 

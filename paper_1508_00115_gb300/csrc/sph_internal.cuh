@@ -150,6 +150,10 @@ struct sph_ctx {
 
     // packed particle data
     float4 *pos4 = nullptr, *vel4 = nullptr, *thermo4 = nullptr;
+    // SPH_FLAG_AXIS_SWEEP: for each of the 13 half-stencil directions, every cell's
+    // particles sorted by their projection on it: {projection, slot}, 13 x cap
+    float2 *axis = nullptr;
+    int64_t axis_cap = 0;
     float *upred = nullptr;
     float *h_lo = nullptr, *h_hi = nullptr;  // bracket of each particle's h root (density iteration)
     uint8_t *active = nullptr;
@@ -270,6 +274,7 @@ int build_planned(sph_ctx *ctx, sph_particles *parts);          // sph_cells.cu 
 int box_max_h(sph_ctx *ctx, const float *h);                    // sph_cells.cu
 int cell_reach(sph_ctx *ctx);  // cell_tmp = max h within two cells   // sph_cells.cu
 int permute_particles(sph_ctx *ctx, sph_particles *parts, bool cell_pos);  // sph_cells.cu
+int axis_sort(sph_ctx *ctx);  // SPH_FLAG_AXIS_SWEEP: per-cell orders along the 13 directions  // sph_cells.cu
 int build_tree(sph_ctx *ctx, sph_particles *parts);             // sph_tree.cu
 int tree_cell_keys_out(sph_ctx *ctx, int32_t *dev_keys);        // sph_tree.cu
 int tree_shrink_count(sph_ctx *ctx, sph_particles *parts);      // sph_tree.cu

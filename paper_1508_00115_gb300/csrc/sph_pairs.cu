@@ -69,6 +69,30 @@ __constant__ signed char kOuter[98][3] = {
     {-1, 0, 2}, {0, 0, 2}, {1, 0, 2}, {2, 0, 2}, {-2, 1, 2}, {-1, 1, 2}, {0, 1, 2},
     {1, 1, 2}, {2, 1, 2}, {-2, 2, 2}, {-1, 2, 2}, {0, 2, 2}, {1, 2, 2}, {2, 2, 2},};
 
+// SPH_FLAG_AXIS_SWEEP: for stencil cell o (kOrder index) the direction d of the 13
+// half-stencil axes with kOrder[o] = sign * axis d, and |axis d| (1, sqrt 2, sqrt 3)
+__constant__ signed char kOrderAxis[27][2] = {
+    {-1, 0}, {0, 1},  {0, -1}, {1, 1},  {1, -1}, {2, 1},   {2, -1},  {3, 1},  {3, -1},
+    {4, 1},  {4, -1}, {5, 1},  {5, -1}, {6, 1},  {6, -1},  {7, 1},   {7, -1}, {8, 1},
+    {8, -1}, {9, 1},  {9, -1}, {10, 1}, {10, -1}, {11, 1}, {11, -1}, {12, -1}, {12, 1}};
+__constant__ float kAxisLen[13] = {1.f, 1.f, 1.f, 1.41421356f, 1.41421356f, 1.41421356f, 1.41421356f,
+                                   1.41421356f, 1.41421356f, 1.73205081f, 1.73205081f, 1.73205081f, 1.73205081f};
+
+// Sweep bound of a neighbour cell: a source whose projection on the unit vector u from
+// the tile's cell towards it (relative to the neighbour's centre; = sign x its stored
+// projection on axis d) reaches lim or more is farther than rlim from every target of
+// the tile, whose box is [lo, hi] -- projected distance never exceeds distance.  The
+// bound is loosened by 1e-5 L against FP32 rounding.
+__device__ __forceinline__ float sweep_limit(int o, float L, float rlim, float lox, float hix, float loy, float hiy,
+                                             float loz, float hiz)
+{
+    const float len = kAxisLen[kOrderAxis[o][0]];
+    // u points from the tile's cell to the neighbour (kOrder[o] = sign * axis d)
+    const float ux = kOrder[o][0] / len, uy = kOrder[o][1] / len, uz = kOrder[o][2] / len;
+    const float tmax = fmaxf(lox * ux, hix * ux) + fmaxf(loy * uy, hiy * uy) + fmaxf(loz * uz, hiz * uz);
+    return rlim + tmax - len * L + 1e-5f * L;
+}
+
 struct DensityArgs {
     const float4 *__restrict__ pos4;
     const float4 *__restrict__ vel4;
@@ -96,6 +120,8 @@ struct DensityArgs {
     const float *__restrict__ leaf_scale;
     const float *__restrict__ leaf_hb;
     const int *__restrict__ tord;  // adaptive: targets of a leaf in ascending h (tiles index this)
+    const float2 *__restrict__ axis;  // SPH_FLAG_AXIS_SWEEP orders (uniform grid), or null
+    int64_t axis_stride;
     double box;
     float n_ngb_target, h_tol, gamma;
     int use_balsara;
@@ -156,9 +182,12 @@ __device__ __forceinline__ float spline_dw_u(float q)
     return fmaf(24.f * b, b, -6.f * a * a);
 }
 
-template <int TW, bool HASH, bool LIST>
+// MODE: 0 = uniform grid, 1 = adaptive cells (leaf lists), 2 = uniform grid with the
+// per-axis sweep (SPH_FLAG_AXIS_SWEEP)
+template <int TW, bool HASH, int MODE>
 __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(DensityArgs a)
 {
+    constexpr bool LIST = MODE == 1, SWEEP = MODE == 2;
     constexpr int TPW = 32 / TW;
     constexpr int B = kBatchD;
     constexpr int SLOT = B + 1;  // one float4 of padding: the tiles of a warp hit different banks
@@ -343,6 +372,10 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
         float shx = 0.f, shy = 0.f, shz = 0.f;
         int pb = 0, pe = 0;  // list entries fetched TW at a time: lane tl holds entry o + tl
         float px = 0.f, py = 0.f, pz = 0.f;
+        // axis sweep of the cell at the cursor (SPH_FLAG_AXIS_SWEEP, radius-1 stencils)
+        int sw_d = -1;
+        float sw_sg = 0.f, sw_lim = 0.f;
+        const float rlim = SWEEP ? sqrtf(reach2) : 0.f;
         // cursor over (cell or list entry o, chunk ch): moves to the next chunk, false at
         // the end (warp-uniform)
         auto next_chunk = [&]() -> bool {
@@ -394,10 +427,29 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
                     shx = (float)ox * L;
                     shy = (float)oy * L;
                     shz = (float)oz * L;
+                    sw_d = -1;
+                    if (SWEEP && R == 1 && o > 0) {
+                        sw_d = kOrderAxis[o][0];
+                        sw_sg = (float)kOrderAxis[o][1];
+                        sw_lim = sweep_limit(o, L, rlim, lox, hix, loy, hiy, loz, hiz);
+                    }
                 }
                 nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
             }
             return true;
+        };
+        // slot of this lane's source in the chunk at the cursor: slot order, or the
+        // cell's order along the axis (backwards for the negative direction), dropping
+        // sources at or beyond the sweep bound
+        auto slot_at = [&](int &j, bool &v) {
+            const int q = ch * TW + tl;
+            v = q < be - bs;
+            j = bs + q;
+            if (SWEEP && sw_d >= 0 && v) {
+                const float2 e = a.axis[(size_t)sw_d * a.axis_stride + bs + (sw_sg > 0.f ? q : be - bs - 1 - q)];
+                j = __float_as_int(e.y);
+                v = sw_sg * e.x < sw_lim;
+            }
         };
         // software pipeline: the positions of the next chunk are loaded before the
         // current chunk is tested, so their latency overlaps the test, the staging
@@ -405,12 +457,14 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
         bool have = next_chunk();
         int jc = bs + ch * TW + tl;
         bool vc = have && jc < be;
+        if (SWEEP && have) slot_at(jc, vc);
         float4 pc = vc ? __ldg(a.pos4 + jc) : make_float4(0.f, 0.f, 0.f, 0.f);
         float scx = shx, scy = shy, scz = shz;
         while (have) {
             const bool have_n = next_chunk();
-            const int jn = bs + ch * TW + tl;
-            const bool vn = have_n && jn < be;
+            int jn = bs + ch * TW + tl;
+            bool vn = have_n && jn < be;
+            if (SWEEP && have_n) slot_at(jn, vn);
             const float4 pn = vn ? __ldg(a.pos4 + jn) : make_float4(0.f, 0.f, 0.f, 0.f);
             bool keep = false;
             float4 vj;
@@ -543,13 +597,16 @@ struct ForceArgs {
     const int2 *__restrict__ leaf_rng;
     const float *__restrict__ leaf_scale;
     const int *__restrict__ tord;
+    const float2 *__restrict__ axis;
+    int64_t axis_stride;
     double box;
     float alpha;
 };
 
-template <int TW, bool LIST>
+template <int TW, int MODE>
 __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs a)
 {
+    constexpr bool LIST = MODE == 1, SWEEP = MODE == 2;
     constexpr int TPW = 32 / TW;
     constexpr int B = kBatchF;
     constexpr int SLOT = B + 1;
@@ -746,6 +803,9 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
         float shx = 0.f, shy = 0.f, shz = 0.f;
         int pb = 0, pe = 0;  // list entries fetched TW at a time: lane tl holds entry o + tl
         float px = 0.f, py = 0.f, pz = 0.f;
+        int sw_d = -1;  // axis sweep of the current cell (SPH_FLAG_AXIS_SWEEP, radius 1)
+        float sw_sg = 0.f, sw_lim = 0.f;
+        const float rlim = SWEEP ? sqrtf(reach2) : 0.f;
         for (;;) {
             while (ch >= nchunk && o < ncell - 1) {
                 ++o;
@@ -796,14 +856,27 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
                 shx = (float)ox * L;
                 shy = (float)oy * L;
                 shz = (float)oz * L;
+                sw_d = -1;
+                if (SWEEP && R == 1 && o > 0) {
+                    sw_d = kOrderAxis[o][0];
+                    sw_sg = (float)kOrderAxis[o][1];
+                    sw_lim = sweep_limit(o, L, rlim, lox, hix, loy, hiy, loz, hiz);
+                }
             }
             const bool more = ch < nchunk;  // warp-uniform
             if (more) {
-                const int j = bs + ch * TW + tl;
+                const int q = ch * TW + tl;
+                int j = bs + q;
+                bool vq = q < be - bs;
+                if (SWEEP && sw_d >= 0 && vq) {  // the cell's order along the axis, up to the sweep bound
+                    const float2 e = a.axis[(size_t)sw_d * a.axis_stride + bs + (sw_sg > 0.f ? q : be - bs - 1 - q)];
+                    j = __float_as_int(e.y);
+                    vq = sw_sg * e.x < sw_lim;
+                }
                 bool keep = false;
                 float4 pj, vj, tj;
                 int jj = 0;
-                if (j < be) {
+                if (vq) {
                     pj = __ldg(a.pos4 + j);
                     vj = __ldg(a.vel4 + j);
                     tj = __ldg(a.thermo4 + j);
@@ -881,18 +954,17 @@ static int smem_optin(sph_ctx *ctx)
     const int d16 = (int)density_smem<16>(), d32 = (int)density_smem<32>();
     const int f16 = (int)force_smem<16>(), f32 = (int)force_smem<32>();
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<16, false, false>, at, d16));
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<16, true, false>, at, d16));
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<32, false, false>, at, d32));
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<32, true, false>, at, d32));
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<16, false, true>, at, d16));
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<16, true, true>, at, d16));
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<32, false, true>, at, d32));
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<32, true, true>, at, d32));
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_force<16, false>, at, f16));
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_force<32, false>, at, f32));
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_force<16, true>, at, f16));
-    SPH_CUDA(ctx, cudaFuncSetAttribute(k_force<32, true>, at, f32));
+#define SPH_OPT_D(M)                                                              \
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<16, false, M>, at, d16));        \
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<16, true, M>, at, d16));         \
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<32, false, M>, at, d32));        \
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<32, true, M>, at, d32));         \
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_force<16, M>, at, f16));                 \
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_force<32, M>, at, f32));
+    SPH_OPT_D(0)
+    SPH_OPT_D(1)
+    SPH_OPT_D(2)
+#undef SPH_OPT_D
     done = true;
     return SPH_OK;
 }
@@ -954,7 +1026,7 @@ int compact_active_tiles(sph_ctx *ctx)
 
 int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool active_list)
 {
-    DensityArgs a;
+    DensityArgs a{};  // every field not set below is null / zero
     a.pos4 = ctx->pos4;
     a.vel4 = ctx->vel4;
     a.cell_start = ctx->cell_start;
@@ -986,6 +1058,8 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool ac
     a.leaf_scale = ctx->tree.leaf_scale;
     a.leaf_hb = ctx->tree.leaf_h;
     a.tord = ctx->tree.tord;
+    a.axis = (ctx->p.flags & SPH_FLAG_AXIS_SWEEP) && !ctx->adaptive ? ctx->axis : nullptr;
+    a.axis_stride = std::max<int64_t>(ctx->cap, 1);
     a.box = ctx->p.box_size;
     a.n_ngb_target = ctx->p.n_ngb;
     a.h_tol = ctx->p.h_tol;
@@ -998,26 +1072,19 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool ac
     const bool hash = (ctx->p.flags & SPH_FLAG_NGB_HASH) != 0;
     cudaEvent_t end = nullptr;
     timer_begin(ctx, 0, &end);
-    const bool list = ctx->adaptive;
+    const int mode = ctx->adaptive ? 1 : (a.axis ? 2 : 0);
+    const size_t sm = ctx->tile_w == 32 ? density_smem<32>() : density_smem<16>();
+#define SPH_LAUNCH_D(TWv, Hv, Mv) k_density<TWv, Hv, Mv><<<g, kPairThreads, sm, ctx->stream>>>(a)
     if (ctx->tile_w == 32) {
-        const size_t sm = density_smem<32>();
-        if (list) {
-            if (hash) k_density<32, true, true><<<g, kPairThreads, sm, ctx->stream>>>(a);
-            else k_density<32, false, true><<<g, kPairThreads, sm, ctx->stream>>>(a);
-        } else {
-            if (hash) k_density<32, true, false><<<g, kPairThreads, sm, ctx->stream>>>(a);
-            else k_density<32, false, false><<<g, kPairThreads, sm, ctx->stream>>>(a);
-        }
+        if (mode == 1) { if (hash) SPH_LAUNCH_D(32, true, 1); else SPH_LAUNCH_D(32, false, 1); }
+        else if (mode == 2) { if (hash) SPH_LAUNCH_D(32, true, 2); else SPH_LAUNCH_D(32, false, 2); }
+        else { if (hash) SPH_LAUNCH_D(32, true, 0); else SPH_LAUNCH_D(32, false, 0); }
     } else {
-        const size_t sm = density_smem<16>();
-        if (list) {
-            if (hash) k_density<16, true, true><<<g, kPairThreads, sm, ctx->stream>>>(a);
-            else k_density<16, false, true><<<g, kPairThreads, sm, ctx->stream>>>(a);
-        } else {
-            if (hash) k_density<16, true, false><<<g, kPairThreads, sm, ctx->stream>>>(a);
-            else k_density<16, false, false><<<g, kPairThreads, sm, ctx->stream>>>(a);
-        }
+        if (mode == 1) { if (hash) SPH_LAUNCH_D(16, true, 1); else SPH_LAUNCH_D(16, false, 1); }
+        else if (mode == 2) { if (hash) SPH_LAUNCH_D(16, true, 2); else SPH_LAUNCH_D(16, false, 2); }
+        else { if (hash) SPH_LAUNCH_D(16, true, 0); else SPH_LAUNCH_D(16, false, 0); }
     }
+#undef SPH_LAUNCH_D
     timer_end(ctx, end);
     SPH_LAUNCH(ctx, "density kernel");
     ctx->st.density_passes++;
@@ -1026,7 +1093,7 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool ac
 
 int run_force_pass(sph_ctx *ctx, sph_particles *parts)
 {
-    ForceArgs a;
+    ForceArgs a{};
     a.pos4 = ctx->pos4;
     a.vel4 = ctx->vel4;
     a.thermo4 = ctx->thermo4;
@@ -1042,6 +1109,8 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts)
     a.leaf_rng = ctx->tree.leaf_rng;
     a.leaf_scale = ctx->tree.leaf_scale;
     a.tord = ctx->tree.tord;
+    a.axis = (ctx->p.flags & SPH_FLAG_AXIS_SWEEP) && !ctx->adaptive ? ctx->axis : nullptr;
+    a.axis_stride = std::max<int64_t>(ctx->cap, 1);
     a.ax = parts->ax;
     a.ay = parts->ay;
     a.az = parts->az;
@@ -1056,13 +1125,15 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts)
     const int g = pair_grid(ctx, kForceBlocks);
     cudaEvent_t end = nullptr;
     timer_begin(ctx, 1, &end);
-    if (ctx->adaptive) {
-        if (ctx->tile_w == 32) k_force<32, true><<<g, kPairThreads, force_smem<32>(), ctx->stream>>>(a);
-        else k_force<16, true><<<g, kPairThreads, force_smem<16>(), ctx->stream>>>(a);
+    const int mode = ctx->adaptive ? 1 : (a.axis ? 2 : 0);
+    const size_t smf = ctx->tile_w == 32 ? force_smem<32>() : force_smem<16>();
+#define SPH_LAUNCH_F(TWv, Mv) k_force<TWv, Mv><<<g, kPairThreads, smf, ctx->stream>>>(a)
+    if (ctx->tile_w == 32) {
+        if (mode == 1) SPH_LAUNCH_F(32, 1); else if (mode == 2) SPH_LAUNCH_F(32, 2); else SPH_LAUNCH_F(32, 0);
     } else {
-        if (ctx->tile_w == 32) k_force<32, false><<<g, kPairThreads, force_smem<32>(), ctx->stream>>>(a);
-        else k_force<16, false><<<g, kPairThreads, force_smem<16>(), ctx->stream>>>(a);
+        if (mode == 1) SPH_LAUNCH_F(16, 1); else if (mode == 2) SPH_LAUNCH_F(16, 2); else SPH_LAUNCH_F(16, 0);
     }
+#undef SPH_LAUNCH_F
     timer_end(ctx, end);
     SPH_LAUNCH(ctx, "force kernel");
     ctx->st.force_passes++;
