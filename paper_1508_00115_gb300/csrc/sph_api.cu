@@ -245,7 +245,7 @@ static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
                 if (rc) return rc;
                 all_tiles = true;
             } else {
-                rc = compact_active_tiles(ctx);
+                rc = ctx->adaptive ? compact_active_leaf_tiles(ctx) : compact_active_tiles(ctx);
                 if (rc) return rc;
                 all_tiles = false;
             }

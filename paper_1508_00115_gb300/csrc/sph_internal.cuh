@@ -93,6 +93,8 @@ struct AdaptiveTree {
     int *top_node = nullptr;   // root node of every top cell (-1: empty)
     int *leaf_of = nullptr;    // leaf of every particle slot
     int *tord = nullptr;       // slots of every leaf in ascending h (the targets of its tiles)
+    int *act_ord = nullptr;    // later density passes: active slots packed per leaf (tord order)
+    int *nact_leaf = nullptr;  // active targets per leaf
     int *leaf_node = nullptr;
     int2 *leaf_rng = nullptr;  // particle slots of every leaf
     double *leaf_cen = nullptr; // absolute centre of every leaf (3 per leaf)
@@ -102,7 +104,7 @@ struct AdaptiveTree {
     float4 *list = nullptr;     // {offset between leaf centres, neighbour leaf}
     uint32_t *h_u32 = nullptr;  // pinned scratch for host reads
     int *h_i32 = nullptr;
-    int64_t cap_keys = 0, cap_keys2 = 0, cap_leaf_of = 0, cap_tord = 0, cap_node_at = 0, cap_top = 0, cap_nodes = 0,
+    int64_t cap_keys = 0, cap_keys2 = 0, cap_leaf_of = 0, cap_tord = 0, cap_act_ord = 0, cap_nact_leaf = 0, cap_node_at = 0, cap_top = 0, cap_nodes = 0,
             cap_front = 0, cap_front2 = 0, cap_bounds = 0, cap_nkids = 0, cap_node_leaf = 0, cap_leaf_node = 0,
             cap_leaf_rng = 0, cap_leaf_cen = 0, cap_leaf_h = 0, cap_leaf_scale = 0, cap_list_off = 0, cap_list = 0;
     int n_nodes = 0, n_leaves = 0;
@@ -297,6 +299,7 @@ void free_tree(sph_ctx *ctx);                                   // sph_tree.cu
 int cell_keys_out(sph_ctx *ctx, int32_t *dev_keys);             // sph_cells.cu
 int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool active_list);  // sph_pairs.cu
 int compact_active_tiles(sph_ctx *ctx);                                    // sph_pairs.cu
+int compact_active_leaf_tiles(sph_ctx *ctx);  // adaptive cells: tiles of active targets only  // sph_tree.cu
 int run_force_pass(sph_ctx *ctx, sph_particles *parts);                    // sph_pairs.cu
 int sync_h(sph_ctx *ctx, sph_particles *parts);                            // sph_pairs.cu
 int kick(sph_ctx *ctx, sph_particles *parts);    // by *d_dt / 2           // sph_integrate.cu

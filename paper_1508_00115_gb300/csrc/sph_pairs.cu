@@ -1057,7 +1057,8 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool ac
     a.leaf_rng = ctx->tree.leaf_rng;
     a.leaf_scale = ctx->tree.leaf_scale;
     a.leaf_hb = ctx->tree.leaf_h;
-    a.tord = ctx->tree.tord;
+    // adaptive cells: later passes run tiles of the active targets only (act_ord)
+    a.tord = ctx->adaptive && active_list ? ctx->tree.act_ord : ctx->tree.tord;
     a.axis = (ctx->p.flags & SPH_FLAG_AXIS_SWEEP) && !ctx->adaptive ? ctx->axis : nullptr;
     a.axis_stride = std::max<int64_t>(ctx->cap, 1);
     a.box = ctx->p.box_size;

@@ -432,6 +432,47 @@ __global__ void k_leaf_tiles(const int2 *__restrict__ rng, const int *__restrict
     if (l == nl - 1) *ntiles = (int)(off[l] + k);
 }
 
+// Later density passes of adaptive cells: the still-active targets of every leaf,
+// packed to the front of its range in act_ord (in tord order, one warp per leaf),
+// and their tile counts; a tile then holds only targets that need the pass.
+__global__ void k_leaf_active(const int2 *__restrict__ rng, int nl, const int *__restrict__ tord,
+                              const uint8_t *__restrict__ active, int tw, int *__restrict__ act_ord,
+                              uint32_t *__restrict__ ntiles_leaf, int *__restrict__ nact_leaf)
+{
+    const int lane = threadIdx.x & 31;
+    const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (l >= nl) return;  // warp-uniform
+    const int lo = rng[l].x, hi = rng[l].y;
+    int c = 0;
+    for (int q0 = lo; q0 < hi; q0 += 32) {
+        const int q = q0 + lane;
+        const int slot = q < hi ? tord[q] : 0;
+        const bool a = q < hi && active[slot] != 0;
+        const unsigned b = __ballot_sync(kFull, a);
+        if (a) act_ord[lo + c + __popc(b & ((1u << lane) - 1u))] = slot;
+        c += __popc(b);
+    }
+    if (lane == 0) {
+        ntiles_leaf[l] = (uint32_t)((c + tw - 1) / tw);
+        nact_leaf[l] = c;
+    }
+}
+
+__global__ void k_leaf_active_tiles(const int2 *__restrict__ rng, const int *__restrict__ leaf_node,
+                                    const TreeNode *__restrict__ nodes, int nl, int tw,
+                                    const uint32_t *__restrict__ off, const int *__restrict__ nact_leaf,
+                                    const BoxDev *__restrict__ bxs, int nb, int4 *__restrict__ tiles,
+                                    int *__restrict__ ntiles)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nl) return;
+    const int s = rng[l].x, cnt = nact_leaf[l];
+    const int box = nb == 1 ? 0 : tbox_of_cell(nodes[leaf_node[l]].top, bxs, nb);
+    int k = 0;
+    for (int b = 0; b < cnt; b += tw, ++k) tiles[off[l] + k] = make_int4(l, s + b, min(tw, cnt - b), box);
+    if (l == nl - 1) *ntiles = (int)(off[l] + k);
+}
+
 // Neighbour leaves of leaf `l`: walk the subtrees of the 27 top cells around its own,
 // keeping nodes whose bounding box is within reach.  COUNT: only count; else write
 // {offset between the leaf centres (FP32), neighbour leaf} from out[0].
@@ -940,10 +981,36 @@ int tree_cell_keys_out(sph_ctx *ctx, int32_t *dev_keys)
     return SPH_OK;
 }
 
+int compact_active_leaf_tiles(sph_ctx *ctx)
+{
+    AdaptiveTree &T = ctx->tree;
+    const int nl = T.n_leaves;
+    if (nl <= 0) {
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->n_act_tiles, 0, sizeof(int), ctx->stream));
+        return SPH_OK;
+    }
+    int rc;
+    if ((rc = grow(ctx, T.act_ord, T.cap_act_ord, std::max<int64_t>(ctx->cap, 1))) ||
+        (rc = grow(ctx, T.nact_leaf, T.cap_nact_leaf, nl + 1)))
+        return rc;
+    // per-leaf tile counts in nkids (free outside the build; it holds >= n_leaves entries)
+    k_leaf_active<<<nblk((int64_t)nl * 32, 256), 256, 0, ctx->stream>>>(T.leaf_rng, nl, T.tord, ctx->active,
+                                                                        ctx->tile_w, T.act_ord, T.nkids,
+                                                                        T.nact_leaf);
+    SPH_LAUNCH(ctx, "leaf active targets");
+    rc = exclusive_scan_u32(ctx, T.nkids, T.nkids, nl);
+    if (rc) return rc;
+    k_leaf_active_tiles<<<nblk(nl, 256), 256, 0, ctx->stream>>>(T.leaf_rng, T.leaf_node, T.nodes, nl, ctx->tile_w,
+                                                               T.nkids, T.nact_leaf, ctx->d_boxes, ctx->n_boxes,
+                                                               ctx->act_tiles, ctx->n_act_tiles);
+    SPH_LAUNCH(ctx, "leaf active tiles");
+    return SPH_OK;
+}
+
 void free_tree(sph_ctx *ctx)
 {
     AdaptiveTree &T = ctx->tree;
-    void *ptrs[] = {ctx->keys64, ctx->keys64_alt, T.leaf_of, T.tord, T.node_at, T.top_node, T.nodes, T.front, T.front2,
+    void *ptrs[] = {ctx->keys64, ctx->keys64_alt, T.leaf_of, T.tord, T.act_ord, T.nact_leaf, T.node_at, T.top_node, T.nodes, T.front, T.front2,
                     T.bounds, T.nkids, T.node_leaf, T.leaf_node, T.leaf_rng, T.leaf_cen, T.leaf_h,
                     T.leaf_scale, T.list_off, T.list};
     for (void *p : ptrs) cudaFree(p);
