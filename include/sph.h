@@ -99,7 +99,7 @@ typedef struct {
     float alpha_visc;    /* artificial-viscosity strength alpha                      */
     float cfl;           /* dt = cfl * min_i h_i / vsig_i                            */
     float cell_factor;   /* cell side >= cell_factor * max h  (>= 1)                  */
-    int32_t max_h_iter;  /* cap on density passes per sph_density call               */
+    int32_t max_h_iter;  /* cap on density passes after the last re-binning          */
     int32_t use_balsara; /* 1: viscosity scaled by the Balsara switch                */
     int32_t kernel;      /* 0: cubic spline (the only kernel)                        */
     uint32_t flags;      /* SPH_FLAG_*                                               */
@@ -199,15 +199,21 @@ int sph_set_n(sph_ctx *ctx, int64_t n);
  * kept: sph_get_permutation.  Host read: max h.
  * With SPH_FLAG_ADAPTIVE the grid is the top level (nc >= 1) of an octree keyed
  * by (top cell, Morton code inside it); the build also forms the leaves and their
- * neighbour lists (host reads: tree sizes, list total).
+ * neighbour lists (host reads: tree sizes, list total; the build inside sph_steps
+ * has none).
  * Errors: SPH_ERR_H_EXCEEDS_CELL if max h > L/3 (adaptive: max h >= L/2);
  * SPH_ERR_CAPACITY if the lists would exceed 2^32 - 2 entries. */
 int sph_build_cells(sph_ctx *ctx, sph_particles *parts);
 
 /* Eq. 1 with the smoothing-length iteration: starting from parts->h, Newton steps
- * on N_w(h) = n_ngb (step clamped to [h/2, 2h]) re-running only unconverged
- * particles, until all satisfy |N_w/N_ngb - 1| <= h_tol or max_h_iter passes ran.
- * Rebuilds the cells (permuting the arrays again) if some h outgrows its cell.
+ * on N_w(h) = n_ngb (step clamped to [h/2, 2h]; a step leaving the bracket of the
+ * root that the evaluations so far give is replaced by the bracket's geometric
+ * middle) re-running only unconverged particles, until all satisfy
+ * |N_w/N_ngb - 1| <= h_tol -- or their bracket is narrower than 2^-21 h, the
+ * resolution of the FP32 sums -- or max_h_iter passes ran since the last
+ * re-binning.  Rebuilds the cells (permuting the arrays again, restarting the
+ * iteration) if some h outgrows its cell, at most 8 times per call
+ * (SPH_ERR_NOT_CONVERGED beyond that).
  * Writes h, rho, P, c, f, divv, curl, n_ngb.  *iters_out (may be NULL) = passes
  * run.  Requires sph_build_cells on the current positions.  Host read: the
  * unconverged count after each pass. */
@@ -227,7 +233,11 @@ int sph_force(sph_ctx *ctx, sph_particles *parts);
 int sph_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_used, sph_conserved *out);
 
 /* n_steps KDK steps (as sph_step) with no host synchronisation between them: the
- * step is captured once into a CUDA graph and replayed.  Differences from calling
+ * step is captured once into a CUDA graph and replayed (SPH_FLAG_ADAPTIVE included:
+ * the captured tree build keeps its sizes on the device, in arrays whose capacity
+ * is fixed at entry -- the lists get twice the entries of the last host build, at
+ * least 2^20; lists that outgrow that return SPH_ERR_CAPACITY, the step that met
+ * it having done no pair work).  Differences from calling
  * sph_step n_steps times: dt lives on the device (dt <= 0: the CFL step of each
  * step's start, else the fixed dt); the cell grid of every box is fixed for the
  * run -- the grid of the previous run is kept while every box's max h is within

@@ -200,11 +200,17 @@ static int autotune(sph_ctx *ctx, sph_particles *parts)
     return build_cells(ctx, parts);
 }
 
+// re-binnings of one density call (h outgrew the cells, or adaptive lists far too
+// long); each restarts the h iteration with a fresh pass budget
+constexpr int kMaxRebins = 32;
+
 static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
 {
     if (!ctx->built) return fail(ctx, SPH_ERR_STATE, "sph_density needs sph_build_cells on the current positions");
     int n = (int)ctx->n;
     int iters = 0;
+    int since = 0;     // passes since the last re-binning (each restarts the iteration)
+    int rebinned = 0;  // re-binnings in this call
     unsigned long long unconv = 0;
     if (n > 0 && (ctx->p.flags & SPH_FLAG_AUTOTUNE) && !ctx->tuned) {
         int rc = autotune(ctx, parts);
@@ -216,12 +222,13 @@ static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
         if (rc) return rc;
         bool all_tiles = true;  // first pass (and after a rebuild): every tile
         for (;;) {
-            const bool last = iters == ctx->p.max_h_iter - 1;
+            const bool last = since == ctx->p.max_h_iter - 1;
             SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_UNCONV, 0, 2 * sizeof(unsigned long long),
                                           ctx->stream));
             rc = run_density_pass(ctx, parts, last, !all_tiles);
             if (rc) return rc;
             ++iters;
+            ++since;
             if (ctx->adaptive && !last) {
                 rc = tree_shrink_count(ctx, parts);
                 if (rc) return rc;
@@ -232,7 +239,13 @@ static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
             if (unconv == 0 || last) break;
             // adaptive: lists much longer than the current h need (1 leaf in 16)
             const bool shrunk = ctx->adaptive && ctx->h_counters[C_SHRINK] * 16 > (unsigned long long)ctx->tree.n_leaves;
-            if (ctx->h_counters[C_HFLAG] || shrunk) {
+            const bool outgrown = ctx->h_counters[C_HFLAG] != 0;
+            if (outgrown && rebinned >= kMaxRebins) {
+                char buf[160];
+                snprintf(buf, sizeof buf, "smoothing lengths still outgrow the cells after %d re-binnings", rebinned);
+                return fail(ctx, SPH_ERR_NOT_CONVERGED, buf);
+            }
+            if (outgrown || (shrunk && rebinned < kMaxRebins)) {
                 // some h outgrew its cell: re-bin with the new h (permutes the arrays)
                 cudaEvent_t end = nullptr;
                 timer_begin(ctx, 2, &end);
@@ -240,6 +253,8 @@ static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
                 timer_end(ctx, end);
                 if (rc) return rc;
                 ctx->st.rebuilds++;
+                ++rebinned;
+                since = 0;
                 SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, n, ctx->stream));
                 rc = reset_h_brackets(ctx);  // slots were permuted
                 if (rc) return rc;
@@ -387,7 +402,7 @@ static int graph_step(sph_ctx *ctx, sph_particles *parts, double dt, int passes)
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_UNCONV, 0, 2 * sizeof(unsigned long long), ctx->stream));
     for (int p = 0; p < passes; ++p) {
         if (p > 0) {
-            rc = compact_active_tiles(ctx);
+            rc = ctx->adaptive ? compact_active_leaf_tiles(ctx) : compact_active_tiles(ctx);
             if (rc) return rc;
             SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_UNCONV, 0, sizeof(unsigned long long), ctx->stream));
         }
@@ -398,7 +413,7 @@ static int graph_step(sph_ctx *ctx, sph_particles *parts, double dt, int passes)
     SPH_LAUNCH(ctx, "step flags");
     rc = sync_h(ctx, parts);
     if (rc) return rc;
-    rc = cell_reach(ctx);
+    rc = ctx->adaptive ? SPH_OK : cell_reach(ctx);  // adaptive cells prune with each source's h
     if (rc) return rc;
     rc = run_force_pass(ctx, parts);
     if (rc) return rc;
@@ -413,18 +428,6 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
 {
     int rc;
     ctx->predict = false;
-    if (ctx->adaptive) {
-        // tree builds read their sizes on the host: the steps run one by one
-        sph_conserved tmp;
-        double used = 0;
-        if (n_steps == 0) return ctx->hydro_valid ? SPH_OK : hydro(ctx, parts);
-        for (int k = 0; k < n_steps; ++k) {
-            rc = do_step(ctx, parts, dt, &used, k == n_steps - 1 ? (out ? out : &tmp) : nullptr);
-            if (rc) return rc;
-        }
-        if (dt_last) *dt_last = used;
-        return SPH_OK;
-    }
     if (!ctx->hydro_valid) {
         rc = hydro(ctx, parts);
         if (rc) return rc;
@@ -439,7 +442,21 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
     // captured for it) is kept while it still suits the particles
     rc = read_box_max_h(ctx, parts);
     if (rc) return rc;
-    if (!plan_still_good(ctx)) {
+    if (ctx->adaptive) {
+        // adaptive cells: a particle's neighbours lie in the 27 top cells around it,
+        // so the fixed top grid keeps a margin: sides >= 1.3 max h, planned at 1.6
+        bool good = ctx->planned;
+        for (int b = 0; b < ctx->n_boxes && good; ++b)
+            if (ctx->box_off[b + 1] > ctx->box_off[b] && 1.3 * (double)ctx->h_box_hmax[b] > ctx->h_boxes[b].L64)
+                good = false;
+        if (!good) {
+            const float cf = ctx->p.cell_factor;
+            ctx->p.cell_factor = std::max(cf, 1.6f);
+            rc = plan_from_hmax(ctx);
+            ctx->p.cell_factor = cf;
+            if (rc) return rc;
+        }
+    } else if (!plan_still_good(ctx)) {
         rc = plan_from_hmax(ctx);
         if (rc) return rc;
     }
@@ -448,11 +465,19 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
         rc = hp_ensure(ctx, std::max<int64_t>(ctx->n, 1));
         if (rc) return rc;
     }
+    // adaptive cells: the captured build keeps its sizes on the device, in arrays of
+    // fixed capacity allocated here
+    uint64_t tree_sig = 0;
+    if (ctx->adaptive && ctx->n > 0) {
+        rc = tree_prepare_device(ctx, &tree_sig);
+        if (rc) return rc;
+    }
     // capture one step on a private stream (the caller's may be the legacy default
     // stream, which cannot be captured); the graph is then launched on the caller's
     // stream.  The timing flag is suspended while capturing.  A graph captured for
     // the same arrays, dt mode and launch shapes is reused.
-    sph_ctx::GraphKey key{*parts, dt > 0 ? dt : 0.0, ctx->n, ctx->grid.n_cells, ctx->grid.key_bits, passes, ctx->tile_w};
+    sph_ctx::GraphKey key{*parts, dt > 0 ? dt : 0.0, ctx->n, ctx->grid.n_cells, ctx->grid.key_bits, passes, ctx->tile_w,
+                          tree_sig};
     if (!ctx->step_exec || !(key == ctx->graph_key)) {
         if (!ctx->cap_stream) SPH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
         const uint32_t flags = ctx->p.flags;
@@ -468,7 +493,9 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
         }
         const int64_t launches0 = ctx->st.kernel_launches;
         const int64_t passes0 = ctx->st.density_passes, fpasses0 = ctx->st.force_passes;
+        ctx->tree.device_sized = ctx->adaptive;
         rc = graph_step(ctx, parts, dt, passes);
+        ctx->tree.device_sized = false;
         ctx->graph_launches = ctx->st.kernel_launches - launches0;
         ctx->st.kernel_launches = launches0;  // capture launched nothing
         ctx->st.density_passes = passes0;
@@ -489,12 +516,25 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
         cudaGraphDestroy(graph);
         if (ce != cudaSuccess) return cuda_fail(ctx, ce, "graph instantiate");
         ctx->graph_key = key;
+        ctx->g_keys = ctx->keys;
+        ctx->g_keys_alt = ctx->keys_alt;
+        ctx->g_vals = ctx->vals;
+        ctx->g_vals_alt = ctx->vals_alt;
+        ctx->g_keys64 = ctx->keys64;
+        ctx->g_keys64_alt = ctx->keys64_alt;
     }
     if (n_steps == 0) return SPH_OK;  // prepared: hydro, plan and graph are ready
     const int64_t per_step = ctx->graph_launches;
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_FLOORS, 0, sizeof(unsigned long long), ctx->stream));
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_GFLAGS, 0, sizeof(unsigned long long), ctx->stream));
     for (int k = 0; k < n_steps; ++k) SPH_CUDA(ctx, cudaGraphLaunch(ctx->step_exec, ctx->stream));
+    // host builds since the capture may have swapped the sort buffers back
+    ctx->keys = ctx->g_keys;
+    ctx->keys_alt = ctx->g_keys_alt;
+    ctx->vals = ctx->g_vals;
+    ctx->vals_alt = ctx->g_vals_alt;
+    ctx->keys64 = ctx->g_keys64;
+    ctx->keys64_alt = ctx->g_keys64_alt;
     ctx->st.kernel_launches += per_step * n_steps;
     ctx->st.density_passes += (int64_t)passes * n_steps;
     ctx->st.force_passes += n_steps;
@@ -513,6 +553,10 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
         rc = cfl_dt(ctx, parts, &nd);
         if (rc) return rc;
         out->dt_next = nd;
+    }
+    if (ctx->adaptive) {
+        rc = tree_read_device(ctx);
+        if (rc) return rc;
     }
     const unsigned long long gf = ctx->h_counters[C_GFLAGS];
     if (gf & 2ull) return fail(ctx, SPH_ERR_H_EXCEEDS_CELL, "some h grew beyond twice the planned cell side");

@@ -85,6 +85,18 @@ struct TreeNode {
     float bx0, by0, bz0, bx1, by1, bz1;  // bounding box, relative to the top-cell centre
 };
 
+// device-side sizes of an adaptive build that runs without host reads (the build
+// inside a graph-captured step)
+struct TreeCounts {
+    int nl, err;
+    int level_begin[18];           // nodes of level L: [level_begin[L], level_begin[L + 1])
+    unsigned long long list_total;
+    unsigned long long walk_ovf;   // a warp's list walk overflowed its stack
+};
+// TreeCounts.err bits: the nodes did not fit (some leaves stay above leaf_max, the
+// lists remain exact), the neighbour lists did not fit (the step did no pair work)
+constexpr int kTreeErrNodes = 1, kTreeErrList = 2;
+
 // adaptive cells (sph_tree.cu): arrays and their capacities
 struct AdaptiveTree {
     TreeNode *nodes = nullptr;
@@ -109,6 +121,11 @@ struct AdaptiveTree {
             cap_leaf_rng = 0, cap_leaf_cen = 0, cap_leaf_h = 0, cap_leaf_scale = 0, cap_list_off = 0, cap_list = 0;
     int n_nodes = 0, n_leaves = 0;
     int64_t n_entries = 0;
+    // graph-captured steps: counts on the device (dc) and their pinned host copy (hc),
+    // fixed capacities of a frontier and of the node array, and the build mode
+    TreeCounts *dc = nullptr, *hc = nullptr;
+    int64_t dev_capf = 0, dev_cap_nodes = 0;
+    bool device_sized = false;   // build without host reads (set while a step is captured)
 };
 
 // learned initial h (sph_hpredict.cu)
@@ -229,13 +246,18 @@ struct sph_ctx {
         double dt;
         int64_t n, n_cells;
         int key_bits, passes, tile_w;
+        uint64_t tree_sig;  // adaptive cells: arrays and capacities the captured build uses
         bool operator==(const GraphKey &o) const
         {
             return memcmp(&parts, &o.parts, sizeof parts) == 0 && dt == o.dt && n == o.n && n_cells == o.n_cells &&
-                   key_bits == o.key_bits && passes == o.passes && tile_w == o.tile_w;
+                   key_bits == o.key_bits && passes == o.passes && tile_w == o.tile_w && tree_sig == o.tree_sig;
         }
     } graph_key{};
     int64_t graph_launches = 0;  // kernels in one captured step
+    // sort buffers as a replay leaves them (an odd number of radix passes swaps the
+    // ping-pong pair on the host while capturing; replays always end in these)
+    uint32_t *g_keys = nullptr, *g_keys_alt = nullptr, *g_vals = nullptr, *g_vals_alt = nullptr;
+    uint64_t *g_keys64 = nullptr, *g_keys64_alt = nullptr;
 
     // statistics
     sph_stats st{};
@@ -278,6 +300,8 @@ int cell_reach(sph_ctx *ctx);  // cell_tmp = max h within two cells   // sph_cel
 int permute_particles(sph_ctx *ctx, sph_particles *parts, bool cell_pos);  // sph_cells.cu
 int axis_sort(sph_ctx *ctx);  // SPH_FLAG_AXIS_SWEEP: per-cell orders along the 13 directions  // sph_cells.cu
 int build_tree(sph_ctx *ctx, sph_particles *parts);             // sph_tree.cu
+int tree_prepare_device(sph_ctx *ctx, uint64_t *sig);           // sph_tree.cu (before a capture)
+int tree_read_device(sph_ctx *ctx);                             // sph_tree.cu (after replays)
 int tree_cell_keys_out(sph_ctx *ctx, int32_t *dev_keys);        // sph_tree.cu
 int tree_shrink_count(sph_ctx *ctx, sph_particles *parts);      // sph_tree.cu
 int reset_h_brackets(sph_ctx *ctx);                             // sph_pairs.cu

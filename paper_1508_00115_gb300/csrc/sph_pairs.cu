@@ -40,6 +40,11 @@ constexpr int kForceBlocks = 2;
 constexpr float kFar = 1e30f;
 // an h bracket end at or above this is open (the bytes 0x7f7f7f7f read 3.39e38)
 constexpr float kHUnbounded = 3e38f;
+// relative width of an h bracket at which the iteration stops refining (2^-21: 4 to 8
+// FP32 ulps of h); near the root the FP32 neighbour sums are noisy at about this level
+// of h, so that for particles whose N_w is very sensitive to h a tolerance far below
+// 1e-5 may have no FP32 h that meets it
+constexpr float kHResolution = 4.76837158e-7f;
 
 // Neighbour cells in visiting order: the own cell, then each of the 13 directions
 // of a half stencil followed by its opposite, so that every staged batch mixes
@@ -119,6 +124,7 @@ struct DensityArgs {
     const int2 *__restrict__ leaf_rng;
     const float *__restrict__ leaf_scale;
     const float *__restrict__ leaf_hb;
+    int hold_cells;  // list mode: the cells cannot be rebuilt during this iteration
     const int *__restrict__ tord;  // adaptive: targets of a leaf in ascending h (tiles index this)
     const float2 *__restrict__ axis;  // SPH_FLAG_AXIS_SWEEP orders (uniform grid), or null
     int64_t axis_stride;
@@ -512,32 +518,49 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
             const float divv = -kSigma * hinv4 * dv / rho;
             const float curl = kSigma * hinv4 * sqrtf(cx * cx + cy * cy + cz * cz) / rho;
             const float g = nw_ - a.n_ngb_target;
-            const bool conv = fabsf(g) <= a.h_tol * a.n_ngb_target;
-            if (!conv && !a.last_pass) {
-                // Newton step, at most a factor 2 either way; N_w is non-decreasing in
-                // h, so every evaluation also narrows a bracket of the root, and a step
-                // that leaves a two-sided bracket is replaced by its geometric middle
-                float lo = a.h_lo[i], up = a.h_hi[i];
+            bool conv = fabsf(g) <= a.h_tol * a.n_ngb_target;
+            float lo = 0.f, up = kHUnbounded;
+            if (!conv) {
+                // N_w is non-decreasing in h, so every evaluation narrows a bracket of
+                // the root; once the bracket is a few FP32 ulps wide the FP32 sums
+                // cannot place the root more finely and h is accepted
+                lo = a.h_lo[i];
+                up = a.h_hi[i];
                 if (g < 0.f) lo = fmaxf(lo, hi);
                 else up = fminf(up, hi);
+                conv = lo > 0.f && up < kHUnbounded && up - lo <= kHResolution * lo;
+            }
+            if (!conv && !a.last_pass) {
+                // Newton step, at most a factor 2 either way; a step that leaves a
+                // two-sided bracket is replaced by its geometric middle
                 float hn = dnw_dh > 0.f ? hi - g / dnw_dh : (g < 0.f ? 2.f * hi : 0.5f * hi);
                 hn = fminf(fmaxf(hn, 0.5f * hi), 2.f * hi);
                 if (lo > 0.f && up < kHUnbounded && !(hn > lo && hn < up)) hn = sqrtf(lo) * sqrtf(up);
-                // adaptive cells take h up to just below half the box (the minimum
-                // image); a step past it is cut back there instead of failing
-                if (LIST) hn = fminf(hn, (float)(0.5 * a.box) * (1.f - 1e-5f));
-                a.h[i] = hn;
-                a.h_lo[i] = lo;
-                a.h_hi[i] = up;
                 flag = 1u;
                 if (LIST) {
-                    // beyond what its leaf's list or the adjacent top cells hold
+                    // adaptive cells: h up to just below half the box (the minimum
+                    // image); beyond what its leaf's list or the adjacent top cells hold
+                    // the cells are built again -- or, where they cannot be (captured
+                    // steps), the step is cut back to that limit and new cells are
+                    // reported only once the iterate sits there with N_w still short
                     const float hb = a.leaf_hb[tile.x];
                     const float lim = fminf(fminf(kTreeReach * hb, bx.L32), (float)(0.5 * a.box));
-                    if (hn > lim * (1.f - 1e-6f)) flag |= 2u;
+                    hn = fminf(hn, (float)(0.5 * a.box) * (1.f - 1e-5f));
+                    if (a.hold_cells) {
+                        const float cap = lim * (1.f - 2e-6f);
+                        if (hn > cap) {
+                            if (g < 0.f && hi >= cap * (1.f - 1e-6f)) flag |= 2u;
+                            hn = cap;
+                        }
+                    } else if (hn > lim * (1.f - 1e-6f)) {
+                        flag |= 2u;
+                    }
                 } else if ((double)hn > 2.0 * bx.L64 * (1.0 - 1e-6)) {
                     flag |= 2u;  // beyond the radius-2 stencil of its cell
                 }
+                a.h[i] = hn;
+                a.h_lo[i] = lo;
+                a.h_hi[i] = up;
             } else {
                 if (!conv) flag = 1u;
                 a.active[i] = 0;
@@ -1057,6 +1080,7 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool ac
     a.leaf_rng = ctx->tree.leaf_rng;
     a.leaf_scale = ctx->tree.leaf_scale;
     a.leaf_hb = ctx->tree.leaf_h;
+    a.hold_cells = ctx->tree.device_sized ? 1 : 0;  // captured steps
     // adaptive cells: later passes run tiles of the active targets only (act_ord)
     a.tord = ctx->adaptive && active_list ? ctx->tree.act_ord : ctx->tree.tord;
     a.axis = (ctx->p.flags & SPH_FLAG_AXIS_SWEEP) && !ctx->adaptive ? ctx->axis : nullptr;

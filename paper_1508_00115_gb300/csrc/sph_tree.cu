@@ -155,12 +155,20 @@ __global__ void k_roots(const int *__restrict__ cs, int64_t ntop, const uint32_t
 // while it holds more than leaf_max particles (down to the Morton resolution); its
 // non-empty children's particle ranges come from binary searches on the next Morton
 // digit.
-__global__ void k_node_split(const int *__restrict__ front, int nfront, const TreeNode *__restrict__ nodes,
-                             const uint64_t *__restrict__ keys, int leaf_max, int *__restrict__ bounds,
-                             uint32_t *__restrict__ nkids)
+// (Sizes: the host count, or -- builds inside captured steps -- the level's node range
+// lvl[0] .. lvl[1] on the device, the kernel then covering cap entries and writing
+// zero counts past the frontier.)
+__global__ void k_node_split(const int *__restrict__ front, int nfront_h, const int *__restrict__ lvl, int cap,
+                             const TreeNode *__restrict__ nodes, const uint64_t *__restrict__ keys, int leaf_max,
+                             int *__restrict__ bounds, uint32_t *__restrict__ nkids)
 {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= nfront) return;
+    const int nfront = lvl ? lvl[1] - lvl[0] : nfront_h;
+    const int end = lvl ? cap : nfront;
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < end; w += gridDim.x * blockDim.x) {
+    if (w >= nfront) {
+        nkids[w] = 0u;
+        continue;
+    }
     const TreeNode t = nodes[front[w]];
     const bool split = (t.hi - t.lo) > leaf_max && t.level < kMortonBits;
     int cnt = 0;
@@ -183,19 +191,21 @@ __global__ void k_node_split(const int *__restrict__ front, int nfront, const Tr
         for (int k = 0; k < 8; ++k) cnt += b[k + 1] > b[k] ? 1 : 0;
     }
     nkids[w] = (uint32_t)cnt;
+    }
 }
 
 // Largest h and bounding box (relative to the top-cell centre) of every leaf, one warp
 // per leaf node; the box is widened by one FP32 ulp of the top cell so that rounding of
 // the positions never shrinks it.
-__global__ void k_leaf_box(TreeNode *__restrict__ nodes, int n_nodes, const double *__restrict__ x,
-                           const double *__restrict__ y, const double *__restrict__ z, const float *__restrict__ h,
-                           const BoxDev *__restrict__ bxs, int nb)
+__global__ void k_leaf_box(TreeNode *__restrict__ nodes, int n_nodes_h, const int *__restrict__ np,
+                           const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+                           const float *__restrict__ h, const BoxDev *__restrict__ bxs, int nb)
 {
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (w >= n_nodes) return;
+    const int n_nodes = np ? *np : n_nodes_h;
+    const int lane = threadIdx.x & 31;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_nodes; w += (gridDim.x * blockDim.x) >> 5) {
     TreeNode t = nodes[w];
-    if (t.child >= 0) return;  // warp-uniform
+    if (t.child >= 0) continue;  // warp-uniform
     const BoxDev g = bxs[nb == 1 ? 0 : tbox_of_cell(t.top, bxs, nb)];
     const int loc = t.top - g.cell_off;
     const double cx = ((double)(loc % g.nc) + 0.5) * g.L64, cy = ((double)((loc / g.nc) % g.nc) + 0.5) * g.L64,
@@ -232,15 +242,17 @@ __global__ void k_leaf_box(TreeNode *__restrict__ nodes, int n_nodes, const doub
         t.bz1 = z1 + pad;
         nodes[w] = t;
     }
+    }
 }
 
 // internal nodes of one level [first, last): union of their children's boxes and max h
-__global__ void k_merge_children(TreeNode *__restrict__ nodes, int first, int last)
+__global__ void k_merge_children(TreeNode *__restrict__ nodes, int first_h, int last_h, const int *__restrict__ lb,
+                                 int level)
 {
-    const int id = first + blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= last) return;
+    const int first = lb ? lb[level] : first_h, last = lb ? lb[level + 1] : last_h;
+    for (int id = first + blockIdx.x * blockDim.x + threadIdx.x; id < last; id += gridDim.x * blockDim.x) {
     TreeNode t = nodes[id];
-    if (t.child < 0) return;
+    if (t.child < 0) continue;
     float hm = 0.f, x0 = 1e30f, y0 = 1e30f, z0 = 1e30f, x1 = -1e30f, y1 = -1e30f, z1 = -1e30f;
     for (int c = t.child; c < t.child + t.nchild; ++c) {
         const TreeNode k = nodes[c];
@@ -260,17 +272,23 @@ __global__ void k_merge_children(TreeNode *__restrict__ nodes, int first, int la
     t.by1 = y1;
     t.bz1 = z1;
     nodes[id] = t;
+    }
 }
 
 // children of the refined frontier nodes, numbered in frontier order (deterministic)
-__global__ void k_make_children(const int *__restrict__ front, int nfront, TreeNode *__restrict__ nodes,
-                                const int *__restrict__ bounds, const uint32_t *__restrict__ off, uint32_t total,
-                                int base, int *__restrict__ next)
+// (device sizes: the frontier is level lvl[0] .. lvl[1], its children lvl[1] .. lvl[2];
+// an empty child range -- nothing refined, or no room for the children -- makes none)
+__global__ void k_make_children(const int *__restrict__ front, int nfront_h, TreeNode *__restrict__ nodes,
+                                const int *__restrict__ bounds, const uint32_t *__restrict__ off, uint32_t total_h,
+                                int base_h, const int *__restrict__ lvl, int *__restrict__ next)
 {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nfront) return;
+    const int nfront = lvl ? lvl[1] - lvl[0] : nfront_h;
+    const uint32_t total = lvl ? (uint32_t)(lvl[2] - lvl[1]) : total_h;
+    const int base = lvl ? lvl[1] : base_h;
+    if (total == 0u) return;
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nfront; f += gridDim.x * blockDim.x) {
     const uint32_t first = off[f], end = f + 1 < nfront ? off[f + 1] : total;
-    if (end == first) return;  // not refined: a leaf
+    if (end == first) continue;  // not refined: a leaf
     const int id = front[f];
     const int *b = bounds + 9 * f;
     TreeNode &t = nodes[id];
@@ -293,6 +311,7 @@ __global__ void k_make_children(const int *__restrict__ front, int nfront, TreeN
     }
     t.child = base + (int)first;
     t.nchild = c;
+    }
 }
 
 // Initial h from the tree: for every leaf, the smallest node around it (itself or an
@@ -326,15 +345,16 @@ __global__ void k_sum_u32(const uint32_t *__restrict__ v, int n, unsigned long l
 }
 
 // flags the first slot of every leaf (leaves partition the particles)
-__global__ void k_leaf_marks(const TreeNode *__restrict__ nodes, int n_nodes, uint32_t *__restrict__ flag,
-                             int *__restrict__ node_at)
+__global__ void k_leaf_marks(const TreeNode *__restrict__ nodes, int n_nodes_h, const int *__restrict__ np,
+                             uint32_t *__restrict__ flag, int *__restrict__ node_at)
 {
-    const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= n_nodes) return;
-    const TreeNode t = nodes[id];
-    if (t.child >= 0) return;
-    flag[t.lo] = 1u;
-    node_at[t.lo] = id;
+    const int n_nodes = np ? *np : n_nodes_h;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n_nodes; id += gridDim.x * blockDim.x) {
+        const TreeNode t = nodes[id];
+        if (t.child >= 0) continue;
+        flag[t.lo] = 1u;
+        node_at[t.lo] = id;
+    }
 }
 
 // leaves in particle (Morton) order: leaf id of slot p = (number of leaf starts <= p) - 1
@@ -387,90 +407,112 @@ __global__ void k_leaf_pos(const int *__restrict__ leaf_of, const double *__rest
 // particles keep their order.
 constexpr int kSortMax = 256;
 constexpr int kSortWarps = 4;
-__global__ void __launch_bounds__(32 * kSortWarps) k_leaf_hsort(const int2 *__restrict__ rng, int nl,
+__global__ void __launch_bounds__(32 * kSortWarps) k_leaf_hsort(const int2 *__restrict__ rng, int nl_h,
+                                                                const int *__restrict__ nlp,
                                                                 const float *__restrict__ h, int *__restrict__ tord)
 {
     __shared__ float sh[kSortWarps][kSortMax];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int l = blockIdx.x * kSortWarps + wib;
-    if (l >= nl) return;  // warp-uniform
-    const int lo = rng[l].x, c = rng[l].y - lo;
-    if (c > kSortMax) {
-        for (int k = lane; k < c; k += 32) tord[lo + k] = lo + k;
-        return;
-    }
-    for (int k = lane; k < c; k += 32) sh[wib][k] = h[lo + k];
-    __syncwarp();
-    for (int k = lane; k < c; k += 32) {
-        const float hk = sh[wib][k];
-        int rank = 0;
-        for (int m = 0; m < c; ++m) {
-            const float hm = sh[wib][m];
-            rank += (hm < hk || (hm == hk && m < k)) ? 1 : 0;
+    const int nl = nlp ? *nlp : nl_h;
+    for (int l = blockIdx.x * kSortWarps + wib; l < nl; l += gridDim.x * kSortWarps) {  // warp-uniform
+        const int lo = rng[l].x, c = rng[l].y - lo;
+        if (c > kSortMax) {
+            for (int k = lane; k < c; k += 32) tord[lo + k] = lo + k;
+            continue;
         }
-        tord[lo + rank] = lo + k;
+        __syncwarp();
+        for (int k = lane; k < c; k += 32) sh[wib][k] = h[lo + k];
+        __syncwarp();
+        for (int k = lane; k < c; k += 32) {
+            const float hk = sh[wib][k];
+            int rank = 0;
+            for (int m = 0; m < c; ++m) {
+                const float hm = sh[wib][m];
+                rank += (hm < hk || (hm == hk && m < k)) ? 1 : 0;
+            }
+            tord[lo + rank] = lo + k;
+        }
     }
 }
 
-__global__ void k_leaf_tiles_n(const int2 *__restrict__ rng, int nl, int tw, uint32_t *__restrict__ nt)
+// (device count: entries from nl up to cap are set to zero for the prefix sum)
+__global__ void k_leaf_tiles_n(const int2 *__restrict__ rng, int nl_h, const int *__restrict__ nlp, int cap, int tw,
+                               uint32_t *__restrict__ nt)
 {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l < nl) nt[l] = (uint32_t)((rng[l].y - rng[l].x + tw - 1) / tw);
+    const int nl = nlp ? *nlp : nl_h;
+    const int end = nlp ? cap : nl;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < end; l += gridDim.x * blockDim.x)
+        nt[l] = l < nl ? (uint32_t)((rng[l].y - rng[l].x + tw - 1) / tw) : 0u;
 }
 
 // tile = {leaf, first slot, count, box}
 __global__ void k_leaf_tiles(const int2 *__restrict__ rng, const int *__restrict__ leaf_node,
-                             const TreeNode *__restrict__ nodes, int nl, int tw, const uint32_t *__restrict__ off,
-                             const BoxDev *__restrict__ bxs, int nb, int4 *__restrict__ tiles, int *__restrict__ ntiles)
+                             const TreeNode *__restrict__ nodes, int nl_h, const int *__restrict__ nlp, int tw,
+                             const uint32_t *__restrict__ off, const BoxDev *__restrict__ bxs, int nb,
+                             int4 *__restrict__ tiles, int *__restrict__ ntiles)
 {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= nl) return;
-    const int s = rng[l].x, cnt = rng[l].y - s;
-    const int box = nb == 1 ? 0 : tbox_of_cell(nodes[leaf_node[l]].top, bxs, nb);
-    int k = 0;
-    for (int b = 0; b < cnt; b += tw, ++k) tiles[off[l] + k] = make_int4(l, s + b, min(tw, cnt - b), box);
-    if (l == nl - 1) *ntiles = (int)(off[l] + k);
+    const int nl = nlp ? *nlp : nl_h;
+    if (nl == 0 && blockIdx.x == 0 && threadIdx.x == 0) *ntiles = 0;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += gridDim.x * blockDim.x) {
+        const int s = rng[l].x, cnt = rng[l].y - s;
+        const int box = nb == 1 ? 0 : tbox_of_cell(nodes[leaf_node[l]].top, bxs, nb);
+        int k = 0;
+        for (int b = 0; b < cnt; b += tw, ++k) tiles[off[l] + k] = make_int4(l, s + b, min(tw, cnt - b), box);
+        if (l == nl - 1) *ntiles = (int)(off[l] + k);
+    }
 }
 
 // Later density passes of adaptive cells: the still-active targets of every leaf,
 // packed to the front of its range in act_ord (in tord order, one warp per leaf),
 // and their tile counts; a tile then holds only targets that need the pass.
-__global__ void k_leaf_active(const int2 *__restrict__ rng, int nl, const int *__restrict__ tord,
-                              const uint8_t *__restrict__ active, int tw, int *__restrict__ act_ord,
-                              uint32_t *__restrict__ ntiles_leaf, int *__restrict__ nact_leaf)
+__global__ void k_leaf_active(const int2 *__restrict__ rng, int nl_h, const int *__restrict__ nlp, int cap,
+                              const int *__restrict__ tord, const uint8_t *__restrict__ active, int tw,
+                              int *__restrict__ act_ord, uint32_t *__restrict__ ntiles_leaf,
+                              int *__restrict__ nact_leaf)
 {
     const int lane = threadIdx.x & 31;
-    const int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (l >= nl) return;  // warp-uniform
-    const int lo = rng[l].x, hi = rng[l].y;
-    int c = 0;
-    for (int q0 = lo; q0 < hi; q0 += 32) {
-        const int q = q0 + lane;
-        const int slot = q < hi ? tord[q] : 0;
-        const bool a = q < hi && active[slot] != 0;
-        const unsigned b = __ballot_sync(kFull, a);
-        if (a) act_ord[lo + c + __popc(b & ((1u << lane) - 1u))] = slot;
-        c += __popc(b);
+    const int nl = nlp ? *nlp : nl_h;
+    for (int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; l < nl; l += (gridDim.x * blockDim.x) >> 5) {
+        const int lo = rng[l].x, hi = rng[l].y;  // warp-uniform
+        int c = 0;
+        for (int q0 = lo; q0 < hi; q0 += 32) {
+            const int q = q0 + lane;
+            const int slot = q < hi ? tord[q] : 0;
+            const bool a = q < hi && active[slot] != 0;
+            const unsigned b = __ballot_sync(kFull, a);
+            if (a) act_ord[lo + c + __popc(b & ((1u << lane) - 1u))] = slot;
+            c += __popc(b);
+        }
+        if (lane == 0) {
+            ntiles_leaf[l] = (uint32_t)((c + tw - 1) / tw);
+            nact_leaf[l] = c;
+        }
     }
-    if (lane == 0) {
-        ntiles_leaf[l] = (uint32_t)((c + tw - 1) / tw);
-        nact_leaf[l] = c;
-    }
+    // device count: zero counts past the last leaf, up to cap, for the prefix sum
+    if (nlp)
+        for (int l = nl + blockIdx.x * blockDim.x + threadIdx.x; l < cap; l += gridDim.x * blockDim.x)
+            ntiles_leaf[l] = 0u;
 }
 
 __global__ void k_leaf_active_tiles(const int2 *__restrict__ rng, const int *__restrict__ leaf_node,
-                                    const TreeNode *__restrict__ nodes, int nl, int tw,
+                                    const TreeNode *__restrict__ nodes, int nl_h, const int *__restrict__ nlp, int tw,
                                     const uint32_t *__restrict__ off, const int *__restrict__ nact_leaf,
-                                    const BoxDev *__restrict__ bxs, int nb, int4 *__restrict__ tiles,
-                                    int *__restrict__ ntiles)
+                                    const BoxDev *__restrict__ bxs, int nb, const int *__restrict__ err,
+                                    int4 *__restrict__ tiles, int *__restrict__ ntiles)
 {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= nl) return;
-    const int s = rng[l].x, cnt = nact_leaf[l];
-    const int box = nb == 1 ? 0 : tbox_of_cell(nodes[leaf_node[l]].top, bxs, nb);
-    int k = 0;
-    for (int b = 0; b < cnt; b += tw, ++k) tiles[off[l] + k] = make_int4(l, s + b, min(tw, cnt - b), box);
-    if (l == nl - 1) *ntiles = (int)(off[l] + k);
+    if (err && *err) {  // the lists did not fit: no tile runs
+        if (blockIdx.x == 0 && threadIdx.x == 0) *ntiles = 0;
+        return;
+    }
+    const int nl = nlp ? *nlp : nl_h;
+    if (nl == 0 && blockIdx.x == 0 && threadIdx.x == 0) *ntiles = 0;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += gridDim.x * blockDim.x) {
+        const int s = rng[l].x, cnt = nact_leaf[l];
+        const int box = nb == 1 ? 0 : tbox_of_cell(nodes[leaf_node[l]].top, bxs, nb);
+        int k = 0;
+        for (int b = 0; b < cnt; b += tw, ++k) tiles[off[l] + k] = make_int4(l, s + b, min(tw, cnt - b), box);
+        if (l == nl - 1) *ntiles = (int)(off[l] + k);
+    }
 }
 
 // Neighbour leaves of leaf `l`: walk the subtrees of the 27 top cells around its own,
@@ -539,23 +581,33 @@ __device__ int leaf_pairs(int l, const int *__restrict__ leaf_node, const TreeNo
     return cnt;
 }
 
-__global__ void k_pairs_count(int nl, const int *__restrict__ leaf_node, const TreeNode *__restrict__ nodes,
+// (device count: runs only when *ovf reports an overflowed warp walk)
+__global__ void k_pairs_count(int nl_h, const int *__restrict__ nlp, const unsigned long long *__restrict__ ovf,
+                              const int *__restrict__ leaf_node, const TreeNode *__restrict__ nodes,
                               const int *__restrict__ top_node, const int *__restrict__ node_leaf,
                               const double *__restrict__ leaf_cen, const BoxDev *__restrict__ bxs, int nb, double box,
                               uint32_t *__restrict__ cnt)
 {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l < nl) cnt[l] = (uint32_t)leaf_pairs<true>(l, leaf_node, nodes, top_node, node_leaf, leaf_cen, bxs, nb, box,
-                                                   nullptr, nullptr);
+    if (ovf && *ovf == 0ull) return;
+    const int nl = nlp ? *nlp : nl_h;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += gridDim.x * blockDim.x)
+        cnt[l] = (uint32_t)leaf_pairs<true>(l, leaf_node, nodes, top_node, node_leaf, leaf_cen, bxs, nb, box, nullptr,
+                                            nullptr);
 }
 
-__global__ void k_pairs_fill(int nl, const int *__restrict__ leaf_node, const TreeNode *__restrict__ nodes,
-                             const int *__restrict__ top_node, const int *__restrict__ node_leaf,
-                             const double *__restrict__ leaf_cen, const BoxDev *__restrict__ bxs, int nb, double box,
-                             const uint32_t *__restrict__ off, float4 *__restrict__ list, float *__restrict__ scale)
+// (device count: runs only when *ovf reports an overflowed warp walk and *err holds
+// no list-capacity error)
+__global__ void k_pairs_fill(int nl_h, const int *__restrict__ nlp, const unsigned long long *__restrict__ ovf,
+                             const int *__restrict__ err, const int *__restrict__ leaf_node,
+                             const TreeNode *__restrict__ nodes, const int *__restrict__ top_node,
+                             const int *__restrict__ node_leaf, const double *__restrict__ leaf_cen,
+                             const BoxDev *__restrict__ bxs, int nb, double box, const uint32_t *__restrict__ off,
+                             float4 *__restrict__ list, float *__restrict__ scale)
 {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l < nl)
+    if (ovf && *ovf == 0ull) return;
+    if (err && *err) return;
+    const int nl = nlp ? *nlp : nl_h;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nl; l += gridDim.x * blockDim.x)
         leaf_pairs<false>(l, leaf_node, nodes, top_node, node_leaf, leaf_cen, bxs, nb, box, list + off[l], scale + l);
 }
 
@@ -570,6 +622,9 @@ constexpr int kWalkCap = 2048;  // stack items per warp (16 KB)
 
 struct WalkArgs {
     int nl;
+    const int *__restrict__ nlp;                     // device leaf count (replaces nl when set)
+    const unsigned long long *__restrict__ skip_ovf;  // fill: skip when a counting walk overflowed
+    const int *__restrict__ err;                      // fill: skip when the lists did not fit
     const int *__restrict__ leaf_node;
     const TreeNode *__restrict__ nodes;
     const int *__restrict__ top_node;
@@ -586,14 +641,10 @@ struct WalkArgs {
 };
 
 template <bool COUNT>
-__global__ void __launch_bounds__(32 * kWalkWarps) k_leaf_walk(WalkArgs a)
+__device__ void walk_leaf(const WalkArgs &a, int l, int2 *st)
 {
-    __shared__ int2 stk[kWalkWarps][kWalkCap];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int l = blockIdx.x * kWalkWarps + wib;
-    if (l >= a.nl) return;  // warp-uniform
-    int2 *st = stk[wib];
     const TreeNode A = a.nodes[a.leaf_node[l]];
     const BoxDev g = a.bxs[a.nb == 1 ? 0 : tbox_of_cell(A.top, a.bxs, a.nb)];
     const int nc = g.nc, loc = A.top - g.cell_off;
@@ -699,6 +750,20 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_leaf_walk(WalkArgs a)
     }
 }
 
+template <bool COUNT>
+__global__ void __launch_bounds__(32 * kWalkWarps) k_leaf_walk(WalkArgs a)
+{
+    __shared__ int2 stk[kWalkWarps][kWalkCap];
+    if (!COUNT && a.skip_ovf && *a.skip_ovf) return;
+    if (!COUNT && a.err && *a.err) return;
+    const int wib = threadIdx.x >> 5;
+    const int nl = a.nlp ? *a.nlp : a.nl;
+    for (int l = blockIdx.x * kWalkWarps + wib; l < nl; l += gridDim.x * kWalkWarps) {  // warp-uniform
+        walk_leaf<COUNT>(a, l, stk[wib]);
+        __syncwarp();
+    }
+}
+
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 template <typename T>
@@ -713,11 +778,254 @@ static int grow(sph_ctx *ctx, T *&p, int64_t &cap, int64_t need)
     return SPH_OK;
 }
 
+// ------------------------------------------------ builds without host reads
+// Inside a graph-captured step the sizes of the tree (frontiers, nodes, leaves, list
+// entries) stay on the device (TreeCounts): every kernel reads its count there and
+// strides over a fixed capacity, so the launch shapes do not depend on the data.
+// The capacities are set before the capture: a frontier holds at most
+// min(n, 8 floor(n / (leaf_max + 1))) children (only nodes of > leaf_max particles
+// split, and they are disjoint on a level), so the nodes of the 14 refined levels
+// always fit; the lists get a reserve over the last host build, and lists that
+// outgrow it leave the step without pair work and an error for the host.
+
+__global__ void k_tree_begin(const int *__restrict__ cs, int64_t ntop, const uint32_t *__restrict__ off, int n,
+                             TreeCounts *__restrict__ tc)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int nroot = (int)off[ntop - 1] + (cs[ntop - 1] < n ? 1 : 0);
+    tc->nl = 0;
+    tc->err = 0;
+    for (int k = 0; k < 18; ++k) tc->level_begin[k] = nroot;
+    tc->level_begin[0] = 0;
+    tc->list_total = 0ull;
+    tc->walk_ovf = 0ull;
+}
+
+// children of level L: lb[L + 2] = lb[L + 1] + their count (none if they do not fit)
+__global__ void k_level_adv(TreeCounts *__restrict__ tc, int level, const uint32_t *__restrict__ nk, int64_t capf,
+                            int64_t cap_nodes)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    int64_t nnext = nk[capf];  // exclusive prefix past the last frontier entry: the total
+    const int64_t b = tc->level_begin[level + 1];
+    if (nnext > capf || b + nnext > cap_nodes) {
+        tc->err |= kTreeErrNodes;
+        nnext = 0;
+    }
+    tc->level_begin[level + 2] = (int)(b + nnext);
+}
+
+__global__ void k_set_nl(const uint32_t *__restrict__ flag, const uint32_t *__restrict__ excl, int n,
+                         TreeCounts *__restrict__ tc)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0) tc->nl = (int)(excl[n - 1] + flag[n - 1]);
+}
+
+// entries [*nlp, cap) of v set to zero
+__global__ void k_zero_tail(uint32_t *__restrict__ v, const int *__restrict__ nlp, int64_t cap)
+{
+    for (int64_t i = *nlp + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = 0u;
+}
+
+// the lists must fit their reserve and the 32-bit offsets; if not, no tile is run
+__global__ void k_list_check(TreeCounts *__restrict__ tc, int64_t cap_list, int *__restrict__ n_tiles)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const unsigned long long t = tc->list_total;
+    if (t > 0xfffffffeull || (int64_t)t > cap_list) {
+        tc->err |= kTreeErrList;
+        *n_tiles = 0;
+    }
+}
+
+static int sm_count(sph_ctx *ctx)
+{
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    return sms > 0 ? sms : 148;
+}
+
+static int build_tree_device(sph_ctx *ctx, sph_particles *parts)
+{
+    AdaptiveTree &T = ctx->tree;
+    const int n = (int)ctx->n;
+    const int64_t ntop = ctx->grid.n_cells;
+    const int64_t capf = T.dev_capf;
+    TreeCounts *dc = T.dc;
+    int rc;
+    int top_bits = 1;
+    while ((1ll << top_bits) < ntop) ++top_bits;
+    if (n <= 0 || !dc) return fail(ctx, SPH_ERR_STATE, "device-sized tree build without prepared capacities");
+    const int sms = sm_count(ctx);
+    const unsigned gp = (unsigned)(8 * sms);  // grid-stride launches
+    k_tree_keys<<<nblk(n, 256), 256, 0, ctx->stream>>>(parts->x, parts->y, parts->z, n, ctx->n_boxes, ctx->p.box_size,
+                                                       ctx->d_boxes, ctx->keys64);
+    SPH_LAUNCH(ctx, "tree keys");
+    if ((rc = radix_sort64(ctx, n, top_bits + kMortonShift))) return rc;
+    if ((rc = permute_particles(ctx, parts, false))) return rc;
+    k_top_start<<<nblk(ntop + 1, 256), 256, 0, ctx->stream>>>(ctx->keys64, n, ntop, ctx->cell_start);
+    SPH_LAUNCH(ctx, "top starts");
+    k_nonempty<<<nblk(ntop, 256), 256, 0, ctx->stream>>>(ctx->cell_start, ntop, ctx->cell_tiles);
+    SPH_LAUNCH(ctx, "top nonempty");
+    if ((rc = exclusive_scan_u32(ctx, ctx->cell_tiles, ctx->cell_tiles, ntop))) return rc;
+    k_tree_begin<<<1, 32, 0, ctx->stream>>>(ctx->cell_start, ntop, ctx->cell_tiles, n, dc);
+    SPH_LAUNCH(ctx, "tree begin");
+    k_roots<<<nblk(ntop, 256), 256, 0, ctx->stream>>>(ctx->cell_start, ntop, ctx->cell_tiles, T.nodes, T.top_node,
+                                                      T.front);
+    SPH_LAUNCH(ctx, "tree roots");
+    int *cur = T.front, *nxt = T.front2;
+    int *lb = dc->level_begin;
+    for (int level = 0; level < kMortonBits; ++level) {
+        k_node_split<<<gp, 256, 0, ctx->stream>>>(cur, 0, lb + level, (int)capf + 1, T.nodes, ctx->keys64,
+                                                  ctx->leaf_max, T.bounds, T.nkids);
+        SPH_LAUNCH(ctx, "node split");
+        if ((rc = exclusive_scan_u32(ctx, T.nkids, T.nkids, capf + 1))) return rc;
+        k_level_adv<<<1, 32, 0, ctx->stream>>>(dc, level, T.nkids, capf, T.dev_cap_nodes);
+        SPH_LAUNCH(ctx, "level advance");
+        k_make_children<<<gp, 256, 0, ctx->stream>>>(cur, 0, T.nodes, T.bounds, T.nkids, 0u, 0, lb + level, nxt);
+        SPH_LAUNCH(ctx, "make children");
+        std::swap(cur, nxt);
+    }
+    const int *n_nodes = lb + kMortonBits + 1;
+    k_leaf_box<<<gp, 256, 0, ctx->stream>>>(T.nodes, 0, n_nodes, parts->x, parts->y, parts->z, parts->h,
+                                            ctx->d_boxes, ctx->n_boxes);
+    SPH_LAUNCH(ctx, "leaf boxes");
+    for (int L = kMortonBits - 1; L >= 0; --L) {  // level kMortonBits holds leaves only
+        k_merge_children<<<gp, 256, 0, ctx->stream>>>(T.nodes, 0, 0, lb, L);
+        SPH_LAUNCH(ctx, "merge children");
+    }
+    // leaves in particle order
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->keys, 0, sizeof(uint32_t) * n, ctx->stream));
+    k_leaf_marks<<<gp, 256, 0, ctx->stream>>>(T.nodes, 0, n_nodes, ctx->keys, T.node_at);
+    SPH_LAUNCH(ctx, "leaf marks");
+    if ((rc = exclusive_scan_u32(ctx, ctx->keys, ctx->keys_alt, n))) return rc;
+    k_set_nl<<<1, 32, 0, ctx->stream>>>(ctx->keys, ctx->keys_alt, n, dc);
+    SPH_LAUNCH(ctx, "leaf count");
+    k_leaves<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->keys, ctx->keys_alt, n, T.node_at, T.nodes, ctx->d_boxes,
+                                                    ctx->n_boxes, T.leaf_of, T.leaf_node, T.node_leaf, T.leaf_rng,
+                                                    T.leaf_cen, T.leaf_h);
+    SPH_LAUNCH(ctx, "leaves");
+    k_leaf_pos<<<nblk(n, 256), 256, 0, ctx->stream>>>(T.leaf_of, T.leaf_cen, parts->x, parts->y, parts->z, parts->h,
+                                                      n, ctx->pos4);
+    SPH_LAUNCH(ctx, "leaf positions");
+    // tiles (the leaf arrays hold n + 1 entries: nl <= n)
+    const int *nlp = &dc->nl;
+    const int64_t capl = (int64_t)n + 1;
+    k_leaf_hsort<<<gp, 32 * kSortWarps, 0, ctx->stream>>>(T.leaf_rng, 0, nlp, parts->h, T.tord);
+    SPH_LAUNCH(ctx, "leaf h order");
+    k_leaf_tiles_n<<<gp, 256, 0, ctx->stream>>>(T.leaf_rng, 0, nlp, (int)capl, ctx->tile_w, T.list_off);
+    SPH_LAUNCH(ctx, "leaf tile counts");
+    if ((rc = exclusive_scan_u32(ctx, T.list_off, T.list_off, capl))) return rc;
+    k_leaf_tiles<<<gp, 256, 0, ctx->stream>>>(T.leaf_rng, T.leaf_node, T.nodes, 0, nlp, ctx->tile_w, T.list_off,
+                                              ctx->d_boxes, ctx->n_boxes, ctx->tiles, ctx->n_tiles);
+    SPH_LAUNCH(ctx, "leaf tiles");
+    // neighbour lists: warp walks, or one-thread walks where a warp's stack overflowed
+    const unsigned gw = (unsigned)(7 * sms);  // 7 blocks of 2 walking warps (32 KB stacks) per SM
+    WalkArgs wa{0, nlp, nullptr, nullptr, T.leaf_node, T.nodes, T.top_node, T.node_leaf, T.leaf_cen, ctx->d_boxes,
+                ctx->n_boxes, ctx->p.box_size, T.list_off, T.list, T.leaf_scale, T.list_off, &dc->walk_ovf};
+    k_leaf_walk<true><<<gw, 32 * kWalkWarps, 0, ctx->stream>>>(wa);
+    SPH_LAUNCH(ctx, "leaf walk count");
+    k_pairs_count<<<gp, 128, 0, ctx->stream>>>(0, nlp, &dc->walk_ovf, T.leaf_node, T.nodes, T.top_node, T.node_leaf,
+                                               T.leaf_cen, ctx->d_boxes, ctx->n_boxes, ctx->p.box_size, T.list_off);
+    SPH_LAUNCH(ctx, "pair count");
+    k_zero_tail<<<gp, 256, 0, ctx->stream>>>(T.list_off, nlp, capl);
+    SPH_LAUNCH(ctx, "list tail");
+    k_sum_u32<<<gp, 256, 0, ctx->stream>>>(T.list_off, (int)capl, &dc->list_total);
+    SPH_LAUNCH(ctx, "list total");
+    if ((rc = exclusive_scan_u32(ctx, T.list_off, T.list_off, capl))) return rc;  // list_off[nl] = total
+    k_list_check<<<1, 32, 0, ctx->stream>>>(dc, T.cap_list, ctx->n_tiles);
+    SPH_LAUNCH(ctx, "list check");
+    wa.skip_ovf = &dc->walk_ovf;
+    wa.err = &dc->err;
+    k_leaf_walk<false><<<gw, 32 * kWalkWarps, 0, ctx->stream>>>(wa);
+    SPH_LAUNCH(ctx, "leaf walk fill");
+    k_pairs_fill<<<gp, 128, 0, ctx->stream>>>(0, nlp, &dc->walk_ovf, &dc->err, T.leaf_node, T.nodes, T.top_node,
+                                              T.node_leaf, T.leaf_cen, ctx->d_boxes, ctx->n_boxes, ctx->p.box_size,
+                                              T.list_off, T.list, T.leaf_scale);
+    SPH_LAUNCH(ctx, "pair fill");
+    ctx->built = true;
+    ctx->density_valid = false;
+    return SPH_OK;
+}
+
+// Capacities for device-sized builds of the current plan (allocations happen here,
+// never inside a capture); *sig identifies the arrays a captured build uses.
+int tree_prepare_device(sph_ctx *ctx, uint64_t *sig)
+{
+    AdaptiveTree &T = ctx->tree;
+    const int64_t n = std::max<int64_t>(ctx->n, 1);
+    const int64_t ntop = ctx->grid.n_cells;
+    const int64_t lm = std::max(ctx->leaf_max, 1);
+    const int64_t kids = std::min<int64_t>(n, 8 * (n / (lm + 1)) + 8);
+    const int64_t capf = std::max<int64_t>(ntop, kids);
+    const int64_t cap_nodes = ntop + kMortonBits * kids + 64;
+    if (cap_nodes >= (1ll << 31)) return fail(ctx, SPH_ERR_CAPACITY, "tree node capacity beyond 32-bit indices");
+    // arrays sized for the host build's needs as well (ntop + 4n + 64 nodes), so that
+    // host builds between captured runs do not move them
+    const int64_t host_nodes = ntop + 4 * n + 64;
+    const int64_t an = std::max(cap_nodes, host_nodes), af = std::max(capf + 1, host_nodes);
+    // list reserve: twice the last build's entries, at least 2^20
+    const int64_t list_need = std::max<int64_t>(2 * T.n_entries, 1 << 20) + 1;
+    int rc;
+    if ((rc = grow(ctx, ctx->keys64, T.cap_keys, n)) || (rc = grow(ctx, ctx->keys64_alt, T.cap_keys2, n)) ||
+        (rc = grow(ctx, T.leaf_of, T.cap_leaf_of, n)) || (rc = grow(ctx, T.node_at, T.cap_node_at, n)) ||
+        (rc = grow(ctx, T.tord, T.cap_tord, n)) || (rc = grow(ctx, T.act_ord, T.cap_act_ord, n)) ||
+        (rc = grow(ctx, T.top_node, T.cap_top, ntop + 1)) || (rc = grow(ctx, T.nodes, T.cap_nodes, an)) ||
+        (rc = grow(ctx, T.node_leaf, T.cap_node_leaf, an)) || (rc = grow(ctx, T.front, T.cap_front, af)) ||
+        (rc = grow(ctx, T.front2, T.cap_front2, af)) || (rc = grow(ctx, T.bounds, T.cap_bounds, 9 * af)) ||
+        (rc = grow(ctx, T.nkids, T.cap_nkids, std::max(af, n + 2))) ||
+        (rc = grow(ctx, T.leaf_node, T.cap_leaf_node, n + 1)) || (rc = grow(ctx, T.leaf_rng, T.cap_leaf_rng, n + 1)) ||
+        (rc = grow(ctx, T.leaf_cen, T.cap_leaf_cen, 3 * n + 3)) || (rc = grow(ctx, T.leaf_h, T.cap_leaf_h, n + 1)) ||
+        (rc = grow(ctx, T.leaf_scale, T.cap_leaf_scale, n + 1)) ||
+        (rc = grow(ctx, T.nact_leaf, T.cap_nact_leaf, n + 1)) || (rc = grow(ctx, T.list_off, T.cap_list_off, n + 2)) ||
+        (rc = grow(ctx, T.list, T.cap_list, list_need)))
+        return rc;
+    if (!T.dc) SPH_CUDA(ctx, cudaMalloc(&T.dc, sizeof(TreeCounts)));
+    if (!T.hc) SPH_CUDA(ctx, cudaMallocHost(&T.hc, sizeof(TreeCounts)));
+    T.dev_capf = capf;
+    T.dev_cap_nodes = cap_nodes;
+    // FNV-1a over every array address and capacity the captured kernels see
+    // (the sort's ping-pong pair in either order: captures may swap it)
+    const void *ptrs[] = {std::min(ctx->keys64, ctx->keys64_alt), std::max(ctx->keys64, ctx->keys64_alt), T.leaf_of, T.node_at, T.tord, T.act_ord, T.top_node,
+                          T.nodes, T.node_leaf, T.front, T.front2, T.bounds, T.nkids, T.leaf_node, T.leaf_rng,
+                          T.leaf_cen, T.leaf_h, T.leaf_scale, T.nact_leaf, T.list_off, T.list, T.dc};
+    const int64_t caps[] = {capf, T.dev_cap_nodes, T.cap_list, ctx->leaf_max};
+    uint64_t hsh = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) {
+        for (int b = 0; b < 8; ++b) hsh = (hsh ^ ((v >> (8 * b)) & 0xffu)) * 1099511628211ull;
+    };
+    for (const void *q : ptrs) mix((uint64_t)(uintptr_t)q);
+    for (int64_t c : caps) mix((uint64_t)c);
+    *sig = hsh;
+    return SPH_OK;
+}
+
+// Host copies of the device sizes after captured steps; the list error is fatal
+// (the step that met it ran no pair work), an overfull node array is not (its
+// leaves stayed larger, the lists exact).
+int tree_read_device(sph_ctx *ctx)
+{
+    AdaptiveTree &T = ctx->tree;
+    if (!T.dc) return SPH_OK;
+    SPH_CUDA(ctx, cudaMemcpyAsync(T.hc, T.dc, sizeof(TreeCounts), cudaMemcpyDeviceToHost, ctx->stream));
+    SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    T.n_nodes = T.hc->level_begin[kMortonBits + 1];
+    T.n_leaves = T.hc->nl;
+    T.n_entries = (int64_t)T.hc->list_total;
+    ctx->st.n_cells = T.hc->nl;
+    if (T.hc->err & kTreeErrList)
+        return fail(ctx, SPH_ERR_CAPACITY, "neighbour lists outgrew the reserve of the captured steps (the step "
+                                           "that met it did no pair work)");
+    return SPH_OK;
+}
+
 // Build the adaptive cells for the current plan (top grids): keys, sort, permutation,
 // tree, leaves, leaf-relative positions, tiles and neighbour lists.
 int build_tree(sph_ctx *ctx, sph_particles *parts)
 {
     AdaptiveTree &T = ctx->tree;
+    if (T.device_sized) return build_tree_device(ctx, parts);
     const int n = (int)ctx->n;
     const int64_t ntop = ctx->grid.n_cells;
     int rc;
@@ -778,8 +1086,8 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
     int *cur = T.front, *nxt = T.front2;
     std::vector<int> level_begin(1, 0);  // nodes of level L: [level_begin[L], level_begin[L + 1])
     for (int level = 0; level <= kMortonBits && nfront > 0; ++level) {
-        k_node_split<<<nblk(nfront, 256), 256, 0, ctx->stream>>>(cur, nfront, T.nodes, ctx->keys64, ctx->leaf_max,
-                                                                 T.bounds, T.nkids);
+        k_node_split<<<nblk(nfront, 256), 256, 0, ctx->stream>>>(cur, nfront, nullptr, 0, T.nodes, ctx->keys64,
+                                                                 ctx->leaf_max, T.bounds, T.nkids);
         SPH_LAUNCH(ctx, "node split");
         SPH_CUDA(ctx, cudaMemcpyAsync(&T.h_u32[1], T.nkids + (nfront - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost,
                                       ctx->stream));
@@ -793,7 +1101,7 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
         if (nnext == 0) break;
         if ((int64_t)n_nodes + nnext > T.cap_nodes) return fail(ctx, SPH_ERR_INVALID_ARG, "tree node capacity exceeded");
         k_make_children<<<nblk(nfront, 256), 256, 0, ctx->stream>>>(cur, nfront, T.nodes, T.bounds, T.nkids,
-                                                                    (uint32_t)nnext, n_nodes, nxt);
+                                                                    (uint32_t)nnext, n_nodes, nullptr, nxt);
         SPH_LAUNCH(ctx, "make children");
         n_nodes += nnext;
         nfront = nnext;
@@ -805,12 +1113,12 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
     // levels upwards from their children
     auto node_boxes = [&]() -> int {
         k_leaf_box<<<nblk((int64_t)n_nodes * 32, 256), 256, 0, ctx->stream>>>(
-            T.nodes, n_nodes, parts->x, parts->y, parts->z, parts->h, ctx->d_boxes, ctx->n_boxes);
+            T.nodes, n_nodes, nullptr, parts->x, parts->y, parts->z, parts->h, ctx->d_boxes, ctx->n_boxes);
         SPH_LAUNCH(ctx, "leaf boxes");
         for (int L = (int)level_begin.size() - 2; L >= 0; --L) {
             const int first = level_begin[L], last = level_begin[L + 1];
             if (last <= first) continue;
-            k_merge_children<<<nblk(last - first, 256), 256, 0, ctx->stream>>>(T.nodes, first, last);
+            k_merge_children<<<nblk(last - first, 256), 256, 0, ctx->stream>>>(T.nodes, first, last, nullptr, 0);
             SPH_LAUNCH(ctx, "merge children");
         }
         return SPH_OK;
@@ -842,7 +1150,7 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
     }
     // leaves in particle order
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->keys, 0, sizeof(uint32_t) * std::max(n, 1), ctx->stream));
-    k_leaf_marks<<<nblk(n_nodes, 256), 256, 0, ctx->stream>>>(T.nodes, n_nodes, ctx->keys, T.node_at);
+    k_leaf_marks<<<nblk(n_nodes, 256), 256, 0, ctx->stream>>>(T.nodes, n_nodes, nullptr, ctx->keys, T.node_at);
     SPH_LAUNCH(ctx, "leaf marks");
     rc = exclusive_scan_u32(ctx, ctx->keys, ctx->keys_alt, n);
     if (rc) return rc;
@@ -869,19 +1177,20 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
     }
     // tiles
     if (nl > 0) {
-        k_leaf_hsort<<<nblk(nl, kSortWarps), 32 * kSortWarps, 0, ctx->stream>>>(T.leaf_rng, nl, parts->h, T.tord);
+        k_leaf_hsort<<<nblk(nl, kSortWarps), 32 * kSortWarps, 0, ctx->stream>>>(T.leaf_rng, nl, nullptr, parts->h,
+                                                                                 T.tord);
         SPH_LAUNCH(ctx, "leaf h order");
-        k_leaf_tiles_n<<<nblk(nl, 256), 256, 0, ctx->stream>>>(T.leaf_rng, nl, ctx->tile_w, T.list_off);
+        k_leaf_tiles_n<<<nblk(nl, 256), 256, 0, ctx->stream>>>(T.leaf_rng, nl, nullptr, 0, ctx->tile_w, T.list_off);
         SPH_LAUNCH(ctx, "leaf tile counts");
         rc = exclusive_scan_u32(ctx, T.list_off, T.list_off, nl);
         if (rc) return rc;
-        k_leaf_tiles<<<nblk(nl, 256), 256, 0, ctx->stream>>>(T.leaf_rng, T.leaf_node, T.nodes, nl, ctx->tile_w,
-                                                            T.list_off, ctx->d_boxes, ctx->n_boxes, ctx->tiles,
+        k_leaf_tiles<<<nblk(nl, 256), 256, 0, ctx->stream>>>(T.leaf_rng, T.leaf_node, T.nodes, nl, nullptr,
+                                                            ctx->tile_w, T.list_off, ctx->d_boxes, ctx->n_boxes, ctx->tiles,
                                                             ctx->n_tiles);
         SPH_LAUNCH(ctx, "leaf tiles");
         // neighbour lists: count, scan, fill (warp walks; one-thread walks if a warp's
         // stack overflowed)
-        WalkArgs wa{nl, T.leaf_node, T.nodes, T.top_node, T.node_leaf, T.leaf_cen, ctx->d_boxes, ctx->n_boxes,
+        WalkArgs wa{nl, nullptr, nullptr, nullptr, T.leaf_node, T.nodes, T.top_node, T.node_leaf, T.leaf_cen, ctx->d_boxes, ctx->n_boxes,
                     ctx->p.box_size, T.list_off, T.list, T.leaf_scale, T.list_off, ctx->counters + C_WALKOVF};
         SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_WALKOVF, 0, sizeof(unsigned long long), ctx->stream));
         k_leaf_walk<true><<<nblk(nl, kWalkWarps), 32 * kWalkWarps, 0, ctx->stream>>>(wa);
@@ -891,7 +1200,7 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
         SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         const bool warp_walk = T.h_u32[8] == 0u;
         if (!warp_walk) {
-            k_pairs_count<<<nblk(nl, 128), 128, 0, ctx->stream>>>(nl, T.leaf_node, T.nodes, T.top_node, T.node_leaf,
+            k_pairs_count<<<nblk(nl, 128), 128, 0, ctx->stream>>>(nl, nullptr, nullptr, T.leaf_node, T.nodes, T.top_node, T.node_leaf,
                                                                  T.leaf_cen, ctx->d_boxes, ctx->n_boxes,
                                                                  ctx->p.box_size, T.list_off);
             SPH_LAUNCH(ctx, "pair count");
@@ -926,7 +1235,7 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
             k_leaf_walk<false><<<nblk(nl, kWalkWarps), 32 * kWalkWarps, 0, ctx->stream>>>(wa);
             SPH_LAUNCH(ctx, "leaf walk fill");
         } else {
-            k_pairs_fill<<<nblk(nl, 128), 128, 0, ctx->stream>>>(nl, T.leaf_node, T.nodes, T.top_node, T.node_leaf,
+            k_pairs_fill<<<nblk(nl, 128), 128, 0, ctx->stream>>>(nl, nullptr, nullptr, nullptr, T.leaf_node, T.nodes, T.top_node, T.node_leaf,
                                                                 T.leaf_cen, ctx->d_boxes, ctx->n_boxes,
                                                                 ctx->p.box_size, T.list_off, T.list, T.leaf_scale);
             SPH_LAUNCH(ctx, "pair fill");
@@ -984,6 +1293,20 @@ int tree_cell_keys_out(sph_ctx *ctx, int32_t *dev_keys)
 int compact_active_leaf_tiles(sph_ctx *ctx)
 {
     AdaptiveTree &T = ctx->tree;
+    if (T.device_sized) {  // counts on the device, capacities set by tree_prepare_device
+        const int64_t capl = std::max<int64_t>(ctx->n, 1) + 1;
+        const unsigned gp = (unsigned)(8 * sm_count(ctx));
+        k_leaf_active<<<gp, 256, 0, ctx->stream>>>(T.leaf_rng, 0, &T.dc->nl, (int)capl, T.tord, ctx->active,
+                                                   ctx->tile_w, T.act_ord, T.nkids, T.nact_leaf);
+        SPH_LAUNCH(ctx, "leaf active targets");
+        int rc = exclusive_scan_u32(ctx, T.nkids, T.nkids, capl);
+        if (rc) return rc;
+        k_leaf_active_tiles<<<gp, 256, 0, ctx->stream>>>(T.leaf_rng, T.leaf_node, T.nodes, 0, &T.dc->nl, ctx->tile_w,
+                                                         T.nkids, T.nact_leaf, ctx->d_boxes, ctx->n_boxes, &T.dc->err,
+                                                         ctx->act_tiles, ctx->n_act_tiles);
+        SPH_LAUNCH(ctx, "leaf active tiles");
+        return SPH_OK;
+    }
     const int nl = T.n_leaves;
     if (nl <= 0) {
         SPH_CUDA(ctx, cudaMemsetAsync(ctx->n_act_tiles, 0, sizeof(int), ctx->stream));
@@ -994,15 +1317,17 @@ int compact_active_leaf_tiles(sph_ctx *ctx)
         (rc = grow(ctx, T.nact_leaf, T.cap_nact_leaf, nl + 1)))
         return rc;
     // per-leaf tile counts in nkids (free outside the build; it holds >= n_leaves entries)
-    k_leaf_active<<<nblk((int64_t)nl * 32, 256), 256, 0, ctx->stream>>>(T.leaf_rng, nl, T.tord, ctx->active,
+    k_leaf_active<<<nblk((int64_t)nl * 32, 256), 256, 0, ctx->stream>>>(T.leaf_rng, nl, nullptr, 0, T.tord,
+                                                                        ctx->active,
                                                                         ctx->tile_w, T.act_ord, T.nkids,
                                                                         T.nact_leaf);
     SPH_LAUNCH(ctx, "leaf active targets");
     rc = exclusive_scan_u32(ctx, T.nkids, T.nkids, nl);
     if (rc) return rc;
-    k_leaf_active_tiles<<<nblk(nl, 256), 256, 0, ctx->stream>>>(T.leaf_rng, T.leaf_node, T.nodes, nl, ctx->tile_w,
+    k_leaf_active_tiles<<<nblk(nl, 256), 256, 0, ctx->stream>>>(T.leaf_rng, T.leaf_node, T.nodes, nl, nullptr,
+                                                               ctx->tile_w,
                                                                T.nkids, T.nact_leaf, ctx->d_boxes, ctx->n_boxes,
-                                                               ctx->act_tiles, ctx->n_act_tiles);
+                                                               nullptr, ctx->act_tiles, ctx->n_act_tiles);
     SPH_LAUNCH(ctx, "leaf active tiles");
     return SPH_OK;
 }
@@ -1014,6 +1339,8 @@ void free_tree(sph_ctx *ctx)
                     T.bounds, T.nkids, T.node_leaf, T.leaf_node, T.leaf_rng, T.leaf_cen, T.leaf_h,
                     T.leaf_scale, T.list_off, T.list};
     for (void *p : ptrs) cudaFree(p);
+    cudaFree(T.dc);
+    cudaFreeHost(T.hc);
     cudaFreeHost(T.h_u32);
     cudaFreeHost(T.h_i32);
     ctx->keys64 = ctx->keys64_alt = nullptr;

@@ -143,7 +143,7 @@ def test_adaptive_step_matches_oracle():
     for _ in range(2):
         s, acc, _ = oracle.step(s, acc, dt)
     ctx.steps(parts, 2, dt)
-    assert ctx.stats()["graph_steps"] == 0  # adaptive builds run step by step
+    assert ctx.stats()["graph_steps"] == 2  # captured steps, tree sizes on the device
     g = parts.numpy()
     inv = np.empty(n, np.int64)
     inv[perm0] = np.arange(n)
@@ -157,6 +157,95 @@ def test_adaptive_step_matches_oracle():
         assert np.abs(g[k] - getattr(s, k)[idx]).max() < 1e-5 * vscale
     assert rel(g["u"], s.u[idx]).max() < 1e-5
     assert rel(g["h"], s.h[idx]).max() < 1e-5
+
+
+def _same_state(g1, g2, p1, p2, rtol, rtol_rho=None):
+    """Two runs of the same particles (slots mapped through the permutations)."""
+    i1, i2 = np.argsort(p1), np.argsort(p2)
+    for k in ("x", "y", "z"):
+        dx = g1[k][i1] - g2[k][i2]
+        dx -= np.rint(dx)
+        assert np.abs(dx).max() < 1e-9, k
+    for k in ("vx", "vy", "vz"):
+        assert np.abs(g1[k][i1] - g2[k][i2]).max() <= rtol * (np.abs(g1[k]).max() + 1e-30), k
+    assert rel(g1["u"][i1], g2["u"][i2]).max() <= rtol
+    assert rel(g1["h"][i1], g2["h"][i2]).max() <= rtol
+    assert rel(g1["rho"][i1], g2["rho"][i2]).max() <= (rtol if rtol_rho is None else rtol_rho)
+
+
+def _half_cfl(d, **params):
+    """Half the CFL step (factor 0.1) of the state's first hydro pass."""
+    ctx, _, g = gpu_hydro(d, flags=_flags(False), **params)
+    ctx.close()
+    ok = g["vsig"] > 0
+    return 0.05 * float(np.min(g["h"][ok] / g["vsig"][ok]))
+
+
+# Tolerances of the comparisons between captured and host steps: both iterations stop
+# within h_tol = 1e-6 of N_w (h within ~h_tol / 3) or at a bracket of 2^-21 h, so the
+# two h differ by up to ~1.6e-6 relative; densities (rho ~ N_w / h^3) by 3x that plus
+# twice h_tol, ~7e-6.
+_RT_STEPS, _RT_RHO = 3e-6, 1e-5
+
+
+@pytest.mark.parametrize("fixed_dt,tw,leaf", [(False, 16, 64), (True, 32, 32)])
+def test_adaptive_graph_steps_match_host_steps(fixed_dt, tw, leaf):
+    """Captured steps (the tree built with its sizes on the device, fixed-capacity
+    arrays, a fixed number of density passes) against host steps: same state."""
+    from paper_1508_00115_gb300 import binding
+    d = _clustered(20000, 40, 8, sigma=0.2)
+    n = d["x"].size
+    dt = _half_cfl(d, h_tol=1e-6) if fixed_dt else 0.0
+    out = []
+    for mode in ("host", "graph"):
+        ctx = binding.Context(n, flags=_flags(False), h_tol=1e-6, tile_width=tw, leaf_max=leaf)
+        parts = binding.Particles(d)
+        if mode == "host":
+            for _ in range(3):
+                ctx.step(parts, dt)
+        else:
+            ctx.steps(parts, 3, dt)
+            assert ctx.stats()["graph_steps"] == 3
+        out.append((parts.numpy(), ctx.permutation(), ctx.stats()))
+    (g1, p1, s1), (g2, p2, s2) = out
+    assert s2["n_cells"] > 0
+    # (the trees may differ: host steps re-bin when h outgrows a leaf's reach, and
+    # captured steps plan their top grid with a margin; the neighbour sets do not)
+    _same_state(g1, g2, p1, p2, _RT_STEPS, _RT_RHO)
+
+
+def test_adaptive_graph_steps_batched_boxes():
+    """Uneven boxes batched in one adaptive context, stepped by the captured graph,
+    against host steps; then host and captured steps mixed on one context."""
+    from paper_1508_00115_gb300 import binding
+    boxes = [_clustered(5000, 41, 4), inputs.random_velocities(inputs.uniform(700, seed=42), 0.2, 43),
+             _clustered(2500 + 3, 44, 2)]
+    offs = [0]
+    for b in boxes:
+        offs.append(offs[-1] + b["x"].size)
+    d = {k: np.concatenate([b[k] for b in boxes]) for k in inputs.FIELDS}
+    n = d["x"].size
+    dt = _half_cfl(d, h_tol=1e-6, box_offsets=offs)
+    out = []
+    for mode in ("host", "graph", "mixed"):
+        ctx = binding.Context(n, flags=_flags(False), h_tol=1e-6, box_offsets=offs)
+        parts = binding.Particles(d)
+        if mode == "host":
+            for _ in range(4):
+                ctx.step(parts, dt)
+        elif mode == "graph":
+            ctx.steps(parts, 4, dt)
+        else:
+            ctx.steps(parts, 2, dt)
+            ctx.step(parts, dt)
+            ctx.steps(parts, 1, dt)  # the captured graph is reused
+            assert ctx.stats()["graph_steps"] == 3
+        out.append((parts.numpy(), ctx.permutation()))
+    g1, p1 = out[0]
+    for g2, p2 in out[1:]:
+        for b in range(len(boxes)):  # particles stay in their box
+            assert np.all((p2[offs[b]:offs[b + 1]] >= offs[b]) & (p2[offs[b]:offs[b + 1]] < offs[b + 1]))
+        _same_state(g1, g2, p1, p2, _RT_STEPS, _RT_RHO)
 
 
 def test_adaptive_batched_boxes():
