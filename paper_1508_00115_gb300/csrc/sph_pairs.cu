@@ -98,6 +98,74 @@ __device__ __forceinline__ float sweep_limit(int o, float L, float rlim, float l
     return rlim + tmax - len * L + 1e-5f * L;
 }
 
+// The sources of a tile's leaf list as one stream (adaptive cells).  The TW entries
+// of a window are fetched at once (lane tl: entry wb + tl), their particle counts are
+// prefix-summed across the TW lanes, and chunk ch of the window covers stream
+// positions [ch TW, ch TW + TW): leaves much smaller than TW share a chunk instead of
+// each leaving lanes idle.  The stream order -- entries in list order, particles in
+// slot order -- is that of the entries taken one by one.
+template <int TW>
+struct ListStream {
+    int wb = -TW;  // first entry of the window (warp-uniform)
+    int incl = 0;  // prefix count of the window's entries up to this lane's, inclusive
+    int st = 0;    // stream position of this lane's entry (its first particle)
+    int sb = 0;    // first slot of this lane's entry minus its stream position
+    int tot = 0;   // particles in this tile's window
+    float px = 0.f, py = 0.f, pz = 0.f;  // offset of this lane's entry
+
+    // next window (warp-uniform); false once the longest list of the warp is done;
+    // *nchunk = the warp's largest chunk count of the window
+    __device__ __forceinline__ bool next(const float4 *__restrict__ list, const int2 *__restrict__ rng, uint32_t e0,
+                                         int ne, int ncell, int tl, int &nchunk)
+    {
+        wb += TW;
+        if (wb >= ncell) return false;
+        int c = 0, b = 0;
+        px = py = pz = 0.f;
+        if (wb + tl < ne) {
+            const float4 en = list[e0 + (uint32_t)(wb + tl)];
+            const int2 r = rng[__float_as_int(en.w)];
+            b = r.x;
+            c = r.y - r.x;
+            px = en.x;
+            py = en.y;
+            pz = en.z;
+        }
+        incl = c;
+#pragma unroll
+        for (int d = 1; d < TW; d <<= 1) {
+            const int v = __shfl_up_sync(kFull, incl, d, TW);
+            if (tl >= d) incl += v;
+        }
+        st = incl - c;
+        sb = b - st;
+        tot = __shfl_sync(kFull, incl, TW - 1, TW);
+        nchunk = (int)__reduce_max_sync(kFull, (unsigned)((tot + TW - 1) / TW));
+        return true;
+    }
+
+    // slot j, validity and entry offset of the stream position base + tl of chunk
+    // base (every lane calls it): the entry holding position base is the number of
+    // entries that end at or before it; each entry that starts inside the chunk, at
+    // or before the lane's position, adds one
+    __device__ __forceinline__ void slot(int base, int tl, int &j, bool &v, float &sx, float &sy,
+                                         float &sz) const
+    {
+        const int g = TW == 32 ? 0 : (int)(threadIdx.x & 31) / TW;  // tile of the lane within the warp
+        const unsigned gm = TW == 32 ? kFull : (((1u << TW) - 1u) << (TW * g));
+        const bool inside = st > base && st < base + TW && st < incl;
+        const unsigned starts = __reduce_or_sync(kFull, inside ? 1u << (TW * g + st - base) : 0u) >> (TW * g);
+        const int eb = __popc(__ballot_sync(kFull, incl <= base) & gm);
+        const int e = min(eb + __popc(starts & ((2u << tl) - 2u)), TW - 1);
+        const int q = base + tl;
+        j = __shfl_sync(kFull, sb, e, TW) + q;
+        sx = __shfl_sync(kFull, px, e, TW);
+        sy = __shfl_sync(kFull, py, e, TW);
+        sz = __shfl_sync(kFull, pz, e, TW);
+        v = q < tot;
+    }
+};
+
 struct DensityArgs {
     const float4 *__restrict__ pos4;
     const float4 *__restrict__ vel4;
@@ -375,41 +443,28 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
         }
         int o = -1, ch = -1, nchunk = 0, bs = 0, be = 0;
         const int ncell = LIST ? (int)__reduce_max_sync(kFull, (unsigned)ne) : (R == 1 ? 27 : 125);
-        float shx = 0.f, shy = 0.f, shz = 0.f;
-        int pb = 0, pe = 0;  // list entries fetched TW at a time: lane tl holds entry o + tl
-        float px = 0.f, py = 0.f, pz = 0.f;
+        float shx = 0.f, shy = 0.f, shz = 0.f;  // offset of the chunk's sources (list mode: per lane)
         // axis sweep of the cell at the cursor (SPH_FLAG_AXIS_SWEEP, radius-1 stencils)
         int sw_d = -1;
         float sw_sg = 0.f, sw_lim = 0.f;
         const float rlim = SWEEP ? sqrtf(reach2) : 0.f;
         // cursor over (cell or list entry o, chunk ch): moves to the next chunk, false at
         // the end (warp-uniform)
+        ListStream<TW> ls;
         auto next_chunk = [&]() -> bool {
             ++ch;
+            if (LIST) {
+                while (ch >= nchunk) {
+                    if (!ls.next(a.list, a.leaf_rng, e0, ne, ncell, tl, nchunk)) return false;
+                    ch = 0;
+                }
+                return true;
+            }
             while (ch >= nchunk) {
                 if (o >= ncell - 1) return false;
                 ++o;
                 ch = 0;
-                if (LIST) {
-                    const int src = o & (TW - 1);  // o is warp-uniform
-                    if (src == 0) {
-                        pb = pe = 0;
-                        if (o + tl < ne) {
-                            const float4 en = a.list[e0 + (uint32_t)(o + tl)];
-                            const int2 r = a.leaf_rng[__float_as_int(en.w)];
-                            pb = r.x;
-                            pe = r.y;
-                            px = en.x;
-                            py = en.y;
-                            pz = en.z;
-                        }
-                    }
-                    bs = __shfl_sync(kFull, pb, src, TW);
-                    be = __shfl_sync(kFull, pe, src, TW);
-                    shx = __shfl_sync(kFull, px, src, TW);
-                    shy = __shfl_sync(kFull, py, src, TW);
-                    shz = __shfl_sync(kFull, pz, src, TW);
-                } else {
+                {
                     int ox, oy, oz;
                     if (R == 1) {
                         const int src = o < TW ? o : o - TW;
@@ -463,6 +518,7 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
         bool have = next_chunk();
         int jc = bs + ch * TW + tl;
         bool vc = have && jc < be;
+        if (LIST && have) ls.slot(ch * TW, tl, jc, vc, shx, shy, shz);
         if (SWEEP && have) slot_at(jc, vc);
         float4 pc = vc ? __ldg(a.pos4 + jc) : make_float4(0.f, 0.f, 0.f, 0.f);
         float scx = shx, scy = shy, scz = shz;
@@ -470,6 +526,7 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
             const bool have_n = next_chunk();
             int jn = bs + ch * TW + tl;
             bool vn = have_n && jn < be;
+            if (LIST && have_n) ls.slot(ch * TW, tl, jn, vn, shx, shy, shz);
             if (SWEEP && have_n) slot_at(jn, vn);
             const float4 pn = vn ? __ldg(a.pos4 + jn) : make_float4(0.f, 0.f, 0.f, 0.f);
             bool keep = false;
@@ -823,38 +880,18 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
         }
         int o = -1, ch = 0, nchunk = 0, bs = 0, be = 0;
         const int ncell = LIST ? (int)__reduce_max_sync(kFull, (unsigned)ne) : (R == 1 ? 27 : 125);
-        float shx = 0.f, shy = 0.f, shz = 0.f;
-        int pb = 0, pe = 0;  // list entries fetched TW at a time: lane tl holds entry o + tl
-        float px = 0.f, py = 0.f, pz = 0.f;
+        float shx = 0.f, shy = 0.f, shz = 0.f;  // offset of the chunk's sources (list mode: per lane)
+        ListStream<TW> ls;
         int sw_d = -1;  // axis sweep of the current cell (SPH_FLAG_AXIS_SWEEP, radius 1)
         float sw_sg = 0.f, sw_lim = 0.f;
         const float rlim = SWEEP ? sqrtf(reach2) : 0.f;
         for (;;) {
-            while (ch >= nchunk && o < ncell - 1) {
+            if (LIST) {
+                while (ch >= nchunk && ls.next(a.list, a.leaf_rng, e0, ne, ncell, tl, nchunk)) ch = 0;
+            }
+            while (!LIST && ch >= nchunk && o < ncell - 1) {
                 ++o;
                 ch = 0;
-                if (LIST) {
-                    const int src = o & (TW - 1);  // o is warp-uniform
-                    if (src == 0) {
-                        pb = pe = 0;
-                        if (o + tl < ne) {
-                            const float4 en = a.list[e0 + (uint32_t)(o + tl)];
-                            const int2 r = a.leaf_rng[__float_as_int(en.w)];
-                            pb = r.x;
-                            pe = r.y;
-                            px = en.x;
-                            py = en.y;
-                            pz = en.z;
-                        }
-                    }
-                    bs = __shfl_sync(kFull, pb, src, TW);
-                    be = __shfl_sync(kFull, pe, src, TW);
-                    shx = __shfl_sync(kFull, px, src, TW);
-                    shy = __shfl_sync(kFull, py, src, TW);
-                    shz = __shfl_sync(kFull, pz, src, TW);
-                    nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
-                    continue;
-                }
                 int ox, oy, oz;
                 if (R == 1) {
                     const int src = o < TW ? o : o - TW;
@@ -891,6 +928,7 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
                 const int q = ch * TW + tl;
                 int j = bs + q;
                 bool vq = q < be - bs;
+                if (LIST) ls.slot(ch * TW, tl, j, vq, shx, shy, shz);
                 if (SWEEP && sw_d >= 0 && vq) {  // the cell's order along the axis, up to the sweep bound
                     const float2 e = a.axis[(size_t)sw_d * a.axis_stride + bs + (sw_sg > 0.f ? q : be - bs - 1 - q)];
                     j = __float_as_int(e.y);
