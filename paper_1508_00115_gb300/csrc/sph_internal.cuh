@@ -49,6 +49,7 @@ enum Counter {
     C_SHRINK = 9,     // adaptive: leaves whose largest h fell below kTreeShrink x its build value
     C_WALKOVF = 10,   // adaptive: leaf walks whose stack overflowed
     C_LISTTOT = 11,   // adaptive: neighbour-list entries (64-bit total)
+    C_TICKET = 12,    // pair kernels: next tile group to hand out (reset before each launch)
     C_NCOUNTERS = 16
 };
 

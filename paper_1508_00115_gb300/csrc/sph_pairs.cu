@@ -281,7 +281,15 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
     // statistics and flags, kept per lane over all tile groups of this warp and added
     // to the global counters once at the end (one atomic per warp and counter)
     unsigned acc_pairs = 0u, acc_cand = 0u, acc_targets = 0u, acc_unc = 0u, acc_hf = 0u;
-    for (int grp = gw; grp < ngroups; grp += nw) {
+    // tile groups: the warp's first one by its index, the others handed out by a ticket
+    // counter (taken one group ahead, so that its latency hides behind a tile), so
+    // that warps that met costly tiles take fewer
+    unsigned *ticket = reinterpret_cast<unsigned *>(a.counters + C_TICKET);  // its low word
+    unsigned tk = 0u;
+    if (lane == 0) tk = atomicAdd(ticket, 1u);
+    for (int grp = gw, g_after = 0; grp < ngroups; grp = g_after) {
+        g_after = nw + (int)__shfl_sync(kFull, tk, 0);
+        if (lane == 0 && g_after < ngroups) tk = atomicAdd(ticket, 1u);
         const int t = grp * TPW + sub;
         const int4 tile = t < ntiles ? a.tiles[t] : make_int4(0, 0, 0, 0);
         const bool valid = tl < tile.z;
@@ -707,7 +715,15 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
     const float inf = __int_as_float(0x7f800000);
 
     unsigned acc_pairs = 0u, acc_cand = 0u;  // per lane; added to the counters at the end
-    for (int grp = gw; grp < ngroups; grp += nw) {
+    // tile groups: the warp's first one by its index, the others handed out by a ticket
+    // counter (taken one group ahead, so that its latency hides behind a tile), so
+    // that warps that met costly tiles take fewer
+    unsigned *ticket = reinterpret_cast<unsigned *>(a.counters + C_TICKET);  // its low word
+    unsigned tk = 0u;
+    if (lane == 0) tk = atomicAdd(ticket, 1u);
+    for (int grp = gw, g_after = 0; grp < ngroups; grp = g_after) {
+        g_after = nw + (int)__shfl_sync(kFull, tk, 0);
+        if (lane == 0 && g_after < ngroups) tk = atomicAdd(ticket, 1u);
         const int t = grp * TPW + sub;
         const int4 tile = t < ntiles ? a.tiles[t] : make_int4(0, 0, 0, 0);
         const bool act = tl < tile.z;
@@ -1132,6 +1148,7 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool ac
     int rc = smem_optin(ctx);
     if (rc) return rc;
     const int g = pair_grid(ctx, kDensityBlocks);
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_TICKET, 0, sizeof(unsigned long long), ctx->stream));
     const bool hash = (ctx->p.flags & SPH_FLAG_NGB_HASH) != 0;
     cudaEvent_t end = nullptr;
     timer_begin(ctx, 0, &end);
@@ -1186,6 +1203,7 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts)
     int rc = smem_optin(ctx);
     if (rc) return rc;
     const int g = pair_grid(ctx, kForceBlocks);
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_TICKET, 0, sizeof(unsigned long long), ctx->stream));
     cudaEvent_t end = nullptr;
     timer_begin(ctx, 1, &end);
     const int mode = ctx->adaptive ? 1 : (a.axis ? 2 : 0);
