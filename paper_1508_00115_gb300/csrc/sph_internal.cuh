@@ -93,6 +93,7 @@ struct TreeCounts {
     int level_begin[18];           // nodes of level L: [level_begin[L], level_begin[L + 1])
     unsigned long long list_total;
     unsigned long long walk_ovf;   // a warp's list walk overflowed its stack
+    unsigned walk_ticket[2];       // leaf tickets of the counting and the filling walk
 };
 // TreeCounts.err bits: the nodes did not fit (some leaves stay above leaf_max, the
 // lists remain exact), the neighbour lists did not fit (the step did no pair work)

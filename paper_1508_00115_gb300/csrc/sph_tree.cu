@@ -28,6 +28,7 @@
 namespace sph {
 
 constexpr int kMortonBits = 14;       // per axis, inside a top cell
+constexpr int kBoundsW = 10;          // words per frontier node: 9 octant bounds + child starts
 constexpr int kMortonShift = 3 * kMortonBits;
 
 __device__ __forceinline__ uint64_t spread3(uint32_t v)  // 14 bits -> every third bit
@@ -153,8 +154,12 @@ __global__ void k_roots(const int *__restrict__ cs, int64_t ntop, const uint32_t
 
 // Refinement decision of every frontier node (one thread per node): a node is split
 // while it holds more than leaf_max particles (down to the Morton resolution); its
-// non-empty children's particle ranges come from binary searches on the next Morton
-// digit.
+// non-empty octants' particle ranges come from binary searches on the next Morton
+// digit.  Octants are joined along the Morton order into halves (4 octants, a slab)
+// or quarters (2 octants, a bar) of the node while the part holds at most leaf_max
+// particles (a leaf spanning several octants keeps its parent's cube), so that a node
+// just above leaf_max gives two to four full leaves instead of up to eight sparse
+// ones.  Word 9 of a node's bounds marks the octants that start a child.
 // (Sizes: the host count, or -- builds inside captured steps -- the level's node range
 // lvl[0] .. lvl[1] on the device, the kernel then covering cap entries and writing
 // zero counts past the frontier.)
@@ -187,8 +192,33 @@ __global__ void k_node_split(const int *__restrict__ front, int nfront_h, const 
             }
             b[k] = lo;
         }
-        for (int k = 0; k < 9; ++k) bounds[9 * w + k] = b[k];
-        for (int k = 0; k < 8; ++k) cnt += b[k + 1] > b[k] ? 1 : 0;
+        // children: a half of the cube (octants 4h .. 4h + 3) if it holds at most
+        // leaf_max particles, else its quarters (octant pairs) that do, else octants
+        int starts = 0;
+        auto first_in = [&](int k0, int k1) {  // first non-empty octant of [k0, k1)
+            int k = k0;
+            while (k < k1 && b[k + 1] == b[k]) ++k;
+            return k;
+        };
+        for (int q0 = 0; q0 < 8; q0 += 4) {
+            const int qn = b[q0 + 4] - b[q0];
+            if (qn <= leaf_max) {
+                if (qn > 0) starts |= 1 << first_in(q0, q0 + 4);
+                continue;
+            }
+            for (int p0 = q0; p0 < q0 + 4; p0 += 2) {
+                const int pn = b[p0 + 2] - b[p0];
+                if (pn <= leaf_max) {
+                    if (pn > 0) starts |= 1 << first_in(p0, p0 + 2);
+                    continue;
+                }
+                for (int k = p0; k < p0 + 2; ++k)
+                    if (b[k + 1] > b[k]) starts |= 1 << k;
+            }
+        }
+        cnt = __popc(starts);
+        for (int k = 0; k < 9; ++k) bounds[kBoundsW * w + k] = b[k];
+        bounds[kBoundsW * w + 9] = starts;
     }
     nkids[w] = (uint32_t)cnt;
     }
@@ -290,19 +320,32 @@ __global__ void k_make_children(const int *__restrict__ front, int nfront_h, Tre
     const uint32_t first = off[f], end = f + 1 < nfront ? off[f + 1] : total;
     if (end == first) continue;  // not refined: a leaf
     const int id = front[f];
-    const int *b = bounds + 9 * f;
+    const int *b = bounds + kBoundsW * f;
+    const int starts = b[9];
     TreeNode &t = nodes[id];
     int c = 0;
     for (int k = 0; k < 8; ++k) {
-        if (b[k + 1] <= b[k]) continue;
+        if (!((starts >> k) & 1)) continue;
+        // the child runs from octant k up to the next starting octant
+        int e = k + 1;
+        int octants = 1;
+        while (e < 8 && !((starts >> e) & 1)) {
+            octants += b[e + 1] > b[e] ? 1 : 0;
+            ++e;
+        }
         TreeNode ch;
         ch.lo = b[k];
-        ch.hi = b[k + 1];
+        ch.hi = b[e];
         ch.child = -1;
         ch.nchild = 0;
         ch.top = t.top;
-        ch.level = t.level + 1;
-        ch.prefix = (t.prefix << 3) | (uint64_t)k;
+        if (octants == 1) {  // one octant: its own cube
+            ch.level = t.level + 1;
+            ch.prefix = (t.prefix << 3) | (uint64_t)k;
+        } else {  // joined octants: the parent's cube
+            ch.level = t.level;
+            ch.prefix = t.prefix;
+        }
         ch.parent = id;
         const int cid = base + (int)first + c;
         nodes[cid] = ch;
@@ -638,6 +681,7 @@ struct WalkArgs {
     float *__restrict__ scale;         // fill: coordinate scale per leaf
     uint32_t *__restrict__ cnt;        // count: entries per leaf
     unsigned long long *overflow;
+    unsigned *ticket;  // device-sized builds: leaves beyond the first of each warp, handed out
 };
 
 template <bool COUNT>
@@ -756,9 +800,23 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_leaf_walk(WalkArgs a)
     __shared__ int2 stk[kWalkWarps][kWalkCap];
     if (!COUNT && a.skip_ovf && *a.skip_ovf) return;
     if (!COUNT && a.err && *a.err) return;
-    const int wib = threadIdx.x >> 5;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nl = a.nlp ? *a.nlp : a.nl;
-    for (int l = blockIdx.x * kWalkWarps + wib; l < nl; l += gridDim.x * kWalkWarps) {  // warp-uniform
+    const int first = blockIdx.x * kWalkWarps + wib, nw = gridDim.x * kWalkWarps;
+    if (!a.ticket) {  // one warp per leaf (host-sized launch)
+        for (int l = first; l < nl; l += nw) {
+            walk_leaf<COUNT>(a, l, stk[wib]);
+            __syncwarp();
+        }
+        return;
+    }
+    // persistent warps: the next leaf by ticket, taken one leaf ahead (walks differ
+    // widely in length)
+    unsigned tk = 0u;
+    if (lane == 0) tk = atomicAdd(a.ticket, 1u);
+    for (int l = first, nxt = 0; l < nl; l = nxt) {  // warp-uniform
+        nxt = nw + (int)__shfl_sync(kFull, tk, 0);
+        if (lane == 0 && nxt < nl) tk = atomicAdd(a.ticket, 1u);
         walk_leaf<COUNT>(a, l, stk[wib]);
         __syncwarp();
     }
@@ -799,6 +857,7 @@ __global__ void k_tree_begin(const int *__restrict__ cs, int64_t ntop, const uin
     tc->level_begin[0] = 0;
     tc->list_total = 0ull;
     tc->walk_ovf = 0ull;
+    tc->walk_ticket[0] = tc->walk_ticket[1] = 0u;
 }
 
 // children of level L: lb[L + 2] = lb[L + 1] + their count (none if they do not fit)
@@ -922,8 +981,9 @@ static int build_tree_device(sph_ctx *ctx, sph_particles *parts)
     SPH_LAUNCH(ctx, "leaf tiles");
     // neighbour lists: warp walks, or one-thread walks where a warp's stack overflowed
     const unsigned gw = (unsigned)(7 * sms);  // 7 blocks of 2 walking warps (32 KB stacks) per SM
-    WalkArgs wa{0, nlp, nullptr, nullptr, T.leaf_node, T.nodes, T.top_node, T.node_leaf, T.leaf_cen, ctx->d_boxes,
-                ctx->n_boxes, ctx->p.box_size, T.list_off, T.list, T.leaf_scale, T.list_off, &dc->walk_ovf};
+    WalkArgs wa{0,       nlp,           nullptr,          nullptr,     T.leaf_node,  T.nodes,
+                T.top_node, T.node_leaf, T.leaf_cen,    ctx->d_boxes, ctx->n_boxes, ctx->p.box_size,
+                T.list_off, T.list,      T.leaf_scale, T.list_off,   &dc->walk_ovf, &dc->walk_ticket[0]};
     k_leaf_walk<true><<<gw, 32 * kWalkWarps, 0, ctx->stream>>>(wa);
     SPH_LAUNCH(ctx, "leaf walk count");
     k_pairs_count<<<gp, 128, 0, ctx->stream>>>(0, nlp, &dc->walk_ovf, T.leaf_node, T.nodes, T.top_node, T.node_leaf,
@@ -938,6 +998,7 @@ static int build_tree_device(sph_ctx *ctx, sph_particles *parts)
     SPH_LAUNCH(ctx, "list check");
     wa.skip_ovf = &dc->walk_ovf;
     wa.err = &dc->err;
+    wa.ticket = &dc->walk_ticket[1];
     k_leaf_walk<false><<<gw, 32 * kWalkWarps, 0, ctx->stream>>>(wa);
     SPH_LAUNCH(ctx, "leaf walk fill");
     k_pairs_fill<<<gp, 128, 0, ctx->stream>>>(0, nlp, &dc->walk_ovf, &dc->err, T.leaf_node, T.nodes, T.top_node,
@@ -973,7 +1034,7 @@ int tree_prepare_device(sph_ctx *ctx, uint64_t *sig)
         (rc = grow(ctx, T.tord, T.cap_tord, n)) || (rc = grow(ctx, T.act_ord, T.cap_act_ord, n)) ||
         (rc = grow(ctx, T.top_node, T.cap_top, ntop + 1)) || (rc = grow(ctx, T.nodes, T.cap_nodes, an)) ||
         (rc = grow(ctx, T.node_leaf, T.cap_node_leaf, an)) || (rc = grow(ctx, T.front, T.cap_front, af)) ||
-        (rc = grow(ctx, T.front2, T.cap_front2, af)) || (rc = grow(ctx, T.bounds, T.cap_bounds, 9 * af)) ||
+        (rc = grow(ctx, T.front2, T.cap_front2, af)) || (rc = grow(ctx, T.bounds, T.cap_bounds, kBoundsW * af)) ||
         (rc = grow(ctx, T.nkids, T.cap_nkids, std::max(af, n + 2))) ||
         (rc = grow(ctx, T.leaf_node, T.cap_leaf_node, n + 1)) || (rc = grow(ctx, T.leaf_rng, T.cap_leaf_rng, n + 1)) ||
         (rc = grow(ctx, T.leaf_cen, T.cap_leaf_cen, 3 * n + 3)) || (rc = grow(ctx, T.leaf_h, T.cap_leaf_h, n + 1)) ||
@@ -1075,7 +1136,7 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
     const int64_t node_cap_need = (int64_t)nroot + 4 * (int64_t)n + 64;
     if ((rc = grow(ctx, T.nodes, T.cap_nodes, node_cap_need)) || (rc = grow(ctx, T.front, T.cap_front, node_cap_need)) ||
         (rc = grow(ctx, T.front2, T.cap_front2, node_cap_need)) ||
-        (rc = grow(ctx, T.bounds, T.cap_bounds, 9 * node_cap_need)) ||
+        (rc = grow(ctx, T.bounds, T.cap_bounds, kBoundsW * node_cap_need)) ||
         (rc = grow(ctx, T.nkids, T.cap_nkids, node_cap_need)) || (rc = grow(ctx, T.node_leaf, T.cap_node_leaf, node_cap_need)))
         return rc;
     k_roots<<<nblk(ntop, 256), 256, 0, ctx->stream>>>(ctx->cell_start, ntop, ctx->cell_tiles, T.nodes, T.top_node,
@@ -1191,7 +1252,7 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
         // neighbour lists: count, scan, fill (warp walks; one-thread walks if a warp's
         // stack overflowed)
         WalkArgs wa{nl, nullptr, nullptr, nullptr, T.leaf_node, T.nodes, T.top_node, T.node_leaf, T.leaf_cen, ctx->d_boxes, ctx->n_boxes,
-                    ctx->p.box_size, T.list_off, T.list, T.leaf_scale, T.list_off, ctx->counters + C_WALKOVF};
+                    ctx->p.box_size, T.list_off, T.list, T.leaf_scale, T.list_off, ctx->counters + C_WALKOVF, nullptr};
         SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_WALKOVF, 0, sizeof(unsigned long long), ctx->stream));
         k_leaf_walk<true><<<nblk(nl, kWalkWarps), 32 * kWalkWarps, 0, ctx->stream>>>(wa);
         SPH_LAUNCH(ctx, "leaf walk count");
