@@ -293,15 +293,17 @@ def run_ours(args):
     snap = {k: v.clone() for k, v in parts.t.items()}
     torch.cuda.synchronize()
 
-    def timed(fn):
+    def timed(fn, tag):
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(tag)  # profilers can select the timed launches
         e0.record(stream)
         res = fn()
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         ms_ = e0.elapsed_time(e1)
         if dist:
@@ -321,7 +323,7 @@ def run_ours(args):
             fl += cons["u_floors"]
         return fl
 
-    ms_plain, floors = timed(plain)
+    ms_plain, floors = timed(plain, "host_steps")
     st = ctx.stats()
 
     # production path: all K steps from one captured CUDA graph, no host sync between.
@@ -339,7 +341,7 @@ def run_ours(args):
         sampler.start()
         time.sleep(0.3)
     ctx.reset_stats()
-    ms, (dt_last, cons_g) = timed(lambda: ctx.steps(parts, args.steps))
+    ms, (dt_last, cons_g) = timed(lambda: ctx.steps(parts, args.steps), "graph_steps")
     clocks = sampler.stop() if sampler else None
     st_g = ctx.stats()
     sec = ms / 1e3
@@ -536,6 +538,7 @@ def run_adaptive(args):
         if sampler:
             sampler.start()
             time.sleep(0.3)
+        torch.cuda.nvtx.range_push("graph_steps" if graph else "host_steps")
         e0.record(stream)
         fl = 0
         if graph:
@@ -546,6 +549,7 @@ def run_adaptive(args):
                 _, cons = c.step(parts)
                 fl += cons["u_floors"]
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         clocks = sampler.stop() if sampler else None
         ms_ = e0.elapsed_time(e1)
