@@ -444,14 +444,16 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
     if (rc) return rc;
     if (ctx->adaptive) {
         // adaptive cells: a particle's neighbours lie in the 27 top cells around it,
-        // so the fixed top grid keeps a margin: sides >= 1.3 max h, planned at 1.6
+        // so the fixed top grid keeps a margin for h to grow during the run: sides
+        // >= 1.15 max h (larger top cells make slower trees: measured 7 % per step on
+        // the batched boxes at 1.6)
         bool good = ctx->planned;
         for (int b = 0; b < ctx->n_boxes && good; ++b)
-            if (ctx->box_off[b + 1] > ctx->box_off[b] && 1.3 * (double)ctx->h_box_hmax[b] > ctx->h_boxes[b].L64)
+            if (ctx->box_off[b + 1] > ctx->box_off[b] && 1.15 * (double)ctx->h_box_hmax[b] > ctx->h_boxes[b].L64)
                 good = false;
         if (!good) {
             const float cf = ctx->p.cell_factor;
-            ctx->p.cell_factor = std::max(cf, 1.6f);
+            ctx->p.cell_factor = std::max(cf, 1.15f);
             rc = plan_from_hmax(ctx);
             ctx->p.cell_factor = cf;
             if (rc) return rc;
