@@ -53,6 +53,21 @@ def _env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def _max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
+    """The largest of every rank's x (a time): the job ends with its slowest rank."""
+    if not dist:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _throughput(world: int, n: int, steps: int, seconds: float) -> float:
+    """Whole-job particles per second: every rank advances its own n particles."""
+    return world * n * steps / seconds
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -305,11 +320,7 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
-        ms_ = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms_], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_ = float(t.item())
+        ms_ = _max_over_ranks(e0.elapsed_time(e1), dist)
         return ms_, res
 
     # plain path: one sph_step call per step (host-driven passes), per-kernel events
@@ -345,7 +356,7 @@ def run_ours(args):
     clocks = sampler.stop() if sampler else None
     st_g = ctx.stats()
     sec = ms / 1e3
-    value = world * n * args.steps / sec
+    value = _throughput(world, n, args.steps, sec)
     pairs = st_g["density_pairs"] + st_g["force_pairs"]
 
     # roofline of the dominant pair kernel (plain FP32 ALU bound)
@@ -385,12 +396,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             ctx_h.step_host(hp)
-        t_e2e = time.perf_counter() - t0
-        if dist:
-            tt = torch.tensor([t_e2e], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e2e = float(tt.item())
-        e2e = {"value": world * n * args.steps / t_e2e, "unit": UNIT,
+        t_e2e = _max_over_ranks(time.perf_counter() - t0, dist)
+        e2e = {"value": _throughput(world, n, args.steps, t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": n * (6 * 8 + 8 * 4),
                "d2h_bytes_per_step": n * (6 * 8 + 14 * 4 + 4)}
         ctx_h.close()
@@ -404,7 +411,7 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "path": "graph-replayed steps (sph_steps): one captured KDK step, all boxes per launch",
-           "plain": {"value": world * n * args.steps / (ms_plain / 1e3), "unit": UNIT,
+           "plain": {"value": _throughput(world, n, args.steps, ms_plain / 1e3), "unit": UNIT,
                      "ms_per_step": ms_plain / args.steps,
                      "path": "one sph_step call per step, host-driven density passes"},
            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -552,11 +559,7 @@ def run_adaptive(args):
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         clocks = sampler.stop() if sampler else None
-        ms_ = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms_], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_ = float(t.item())
+        ms_ = _max_over_ranks(e0.elapsed_time(e1), dist)
         st = c.stats()
         c.close()
         return ms_, st, clocks, fl
@@ -572,7 +575,7 @@ def run_adaptive(args):
     else:
         ms_plain, st_plain = ms, st_g
     sec = ms / 1e3
-    value = world * n * args.steps / sec
+    value = _throughput(world, n, args.steps, sec)
     pairs = st_g["density_pairs"] + st_g["force_pairs"]
 
     props = torch.cuda.get_device_properties(local)
@@ -600,8 +603,8 @@ def run_adaptive(args):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             ctx_h.step_host(hp)
-        t_e2e = time.perf_counter() - t0
-        e2e = {"value": world * n * args.steps / t_e2e, "unit": UNIT,
+        t_e2e = _max_over_ranks(time.perf_counter() - t0, dist)
+        e2e = {"value": _throughput(world, n, args.steps, t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": n * (6 * 8 + 8 * 4), "d2h_bytes_per_step": n * (6 * 8 + 14 * 4 + 4)}
         ctx_h.close()
 
@@ -622,11 +625,11 @@ def run_adaptive(args):
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "path": ("graph-replayed steps (sph_steps) on adaptive cells, tree sizes on the device"
                     + (", learned h guess" if args.hpredict else "")),
-           "plain": {"value": world * n * args.steps / (ms_plain / 1e3), "unit": UNIT,
+           "plain": {"value": _throughput(world, n, args.steps, ms_plain / 1e3), "unit": UNIT,
                      "ms_per_step": ms_plain / args.steps,
                      "density_passes_per_step": st_plain["density_passes"] / args.steps,
                      "path": "graph-replayed steps, h iteration from the previous h"},
-           "host_steps": {"value": world * n * args.steps / (ms_host / 1e3), "unit": UNIT,
+           "host_steps": {"value": _throughput(world, n, args.steps, ms_host / 1e3), "unit": UNIT,
                           "ms_per_step": ms_host / args.steps,
                           "density_passes_per_step": st["density_passes"] / args.steps,
                           "rebuilds_per_step": st["rebuilds"] / args.steps,
