@@ -37,7 +37,9 @@ def _digest() -> str:
             h.update(f.encode() + fh.read())
     with open(os.path.join(INCLUDE, "sph.h"), "rb") as fh:
         h.update(fh.read())
-    h.update(" ".join(ARCH + FLAGS).encode())
+    # the flags without the include directory's absolute path, so that the digest
+    # names the sources and options, not the checkout's location
+    h.update(" ".join(ARCH + [f for f in FLAGS if f != INCLUDE]).encode())
     return h.hexdigest()[:16]
 
 
