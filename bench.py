@@ -153,7 +153,7 @@ def _gpu_id(dev: int) -> str:
 
 def _traffic(kernel: str):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
+    taken on the current sources of the pair kernels (else None)."""
     from paper_1508_00115_gb300 import build as b
     path = os.path.join(ROOT, "profiles", f"{kernel}_sedov128.md")
     try:
@@ -163,11 +163,11 @@ def _traffic(kernel: str):
     src = None
     val = None
     for line in text.splitlines():
-        if line.startswith("source_digest:"):
-            src = line.split(":", 1)[1].strip()
+        if line.startswith("kernel_digest:"):
+            src = line.split(":", 1)[1].split()[0]
         if line.startswith("dram_bytes_per_launch:"):
             val = float(line.split(":", 1)[1].split()[0])
-    if src is None or val is None or src != b._digest():
+    if src is None or val is None or src != b.pair_kernel_digest():
         return None
     return val
 

@@ -30,9 +30,15 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found (CUDA toolkit required to build libsph)")
 
 
-def _digest() -> str:
+# the translation unit of the pair kernels (k_density, k_force and their launches)
+PAIR_SOURCES = ["sph_pairs.cu", "sph_internal.cuh"]
+
+
+def _digest(files=None) -> str:
+    """Identity of the sources (all of csrc/, or the given files of it), sph.h and
+    the compile options."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(CSRC)):
+    for f in sorted(files if files is not None else os.listdir(CSRC)):
         with open(os.path.join(CSRC, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     with open(os.path.join(INCLUDE, "sph.h"), "rb") as fh:
@@ -41,6 +47,12 @@ def _digest() -> str:
     # names the sources and options, not the checkout's location
     h.update(" ".join(ARCH + [f for f in FLAGS if f != INCLUDE]).encode())
     return h.hexdigest()[:16]
+
+
+def pair_kernel_digest() -> str:
+    """Identity of the pair kernels' sources: ncu figures of k_density / k_force stay
+    valid while it is unchanged."""
+    return _digest(PAIR_SOURCES)
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:

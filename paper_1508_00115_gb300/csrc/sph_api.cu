@@ -948,6 +948,7 @@ void sph_destroy(sph_ctx *ctx)
     cudaFreeHost(ctx->h_box_hmax);
     cudaFree(ctx->d_box_off);
     if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     cudaFree(ctx->mirror_block);
     for (Timer &t : ctx->timers) {
         cudaEventDestroy(t.a);
