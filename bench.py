@@ -570,8 +570,16 @@ def run_adaptive(args):
     ms_host, st, _, _ = timed(base_t | hp_t, graph=False)
     # graph-replayed steps: the headline (and, with the learned guess, the plain one)
     ms, st_g, clocks, floors = timed(base_t | hp_t, graph=True)
+    learned = None
     if args.hpredict:
         ms_plain, st_plain, _, _ = timed(base_t, graph=True)
+        # the predictor's effect on the h iteration (host-driven steps iterate to
+        # convergence, so their passes and re-run targets show it)
+        ms_hp0, st_hp0, _, _ = timed(base_t, graph=False)
+        learned = {k: {"density_passes_per_step": s_["density_passes"] / args.steps,
+                       "targets_per_particle_per_step": s_["density_targets"] / (args.steps * n),
+                       "ms_per_step": m_ / args.steps}
+                   for k, (m_, s_) in (("plain", (ms_hp0, st_hp0)), ("learned", (ms_host, st)))}
     else:
         ms_plain, st_plain = ms, st_g
     sec = ms / 1e3
@@ -661,6 +669,8 @@ def run_adaptive(args):
                         "t_build_ms": st["t_build_ms"] / args.steps, "u_floors": floors / args.steps},
            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": int(st_g["kernel_launches"]), "clocks": clocks}
+    if learned:
+        out["learned_h"] = learned
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
