@@ -915,7 +915,13 @@ static int build_tree_device(sph_ctx *ctx, sph_particles *parts)
     int rc;
     int top_bits = 1;
     while ((1ll << top_bits) < ntop) ++top_bits;
-    if (n <= 0 || !dc) return fail(ctx, SPH_ERR_STATE, "device-sized tree build without prepared capacities");
+    if (n <= 0) {  // nothing to refine: no leaves, no tiles
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->n_tiles, 0, sizeof(int), ctx->stream));
+        ctx->built = true;
+        ctx->density_valid = false;
+        return SPH_OK;
+    }
+    if (!dc) return fail(ctx, SPH_ERR_STATE, "device-sized tree build without prepared capacities");
     const int sms = sm_count(ctx);
     const unsigned gp = (unsigned)(8 * sms);  // grid-stride launches
     k_tree_keys<<<nblk(n, 256), 256, 0, ctx->stream>>>(parts->x, parts->y, parts->z, n, ctx->n_boxes, ctx->p.box_size,
@@ -1068,6 +1074,12 @@ int tree_prepare_device(sph_ctx *ctx, uint64_t *sig)
 int tree_read_device(sph_ctx *ctx)
 {
     AdaptiveTree &T = ctx->tree;
+    if (ctx->n <= 0) {
+        T.n_nodes = T.n_leaves = 0;
+        T.n_entries = 0;
+        ctx->st.n_cells = 0;
+        return SPH_OK;
+    }
     if (!T.dc) return SPH_OK;
     SPH_CUDA(ctx, cudaMemcpyAsync(T.hc, T.dc, sizeof(TreeCounts), cudaMemcpyDeviceToHost, ctx->stream));
     SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1355,6 +1367,10 @@ int compact_active_leaf_tiles(sph_ctx *ctx)
 {
     AdaptiveTree &T = ctx->tree;
     if (T.device_sized) {  // counts on the device, capacities set by tree_prepare_device
+        if (ctx->n <= 0 || !T.dc) {
+            SPH_CUDA(ctx, cudaMemsetAsync(ctx->n_act_tiles, 0, sizeof(int), ctx->stream));
+            return SPH_OK;
+        }
         const int64_t capl = std::max<int64_t>(ctx->n, 1) + 1;
         const unsigned gp = (unsigned)(8 * sm_count(ctx));
         k_leaf_active<<<gp, 256, 0, ctx->stream>>>(T.leaf_rng, 0, &T.dc->nl, (int)capl, T.tord, ctx->active,

@@ -356,3 +356,43 @@ def test_boxes_512_sampled():
         t = _targets(sub, 100, b)
         check_density(sub, s, targets=t)
         check_force(sub, s, targets=t)
+
+
+def test_adaptive_graph_steps_edge_cases():
+    """Captured steps on adaptive cells: the empty set, a handful of particles (one
+    or two top cells per side), very small leaves (deep trees, many nodes), and a
+    batch with an empty box and a small one (h near a third of its side) -- each
+    against host steps."""
+    from paper_1508_00115_gb300 import binding
+    ctx0 = binding.Context(0, flags=_flags(False))
+    p0 = binding.Particles({k: np.zeros(0) for k in inputs.FIELDS})
+    ctx0.steps(p0, 2, 1e-3)
+    assert ctx0.stats()["n_cells"] == 0
+
+    def both(d, steps, **kw):
+        n = d["x"].size
+        dt = _half_cfl(d, h_tol=1e-6, **kw)
+        out = []
+        for mode in ("host", "graph"):
+            ctx = binding.Context(n, flags=_flags(False), h_tol=1e-6, **kw)
+            parts = binding.Particles(d)
+            if mode == "host":
+                for _ in range(steps):
+                    ctx.step(parts, dt)
+            else:
+                ctx.steps(parts, steps, dt)
+                assert ctx.stats()["graph_steps"] == steps
+            out.append((parts.numpy(), ctx.permutation()))
+        (g1, p1), (g2, p2) = out
+        _same_state(g1, g2, p1, p2, _RT_STEPS, _RT_RHO)
+
+    both(inputs.random_velocities(inputs.uniform(300, seed=50), 0.2, 51), 3)
+    both(_clustered(4000, 52, 3), 2, leaf_max=4)
+    boxes = [_clustered(2500, 53, 2), None, inputs.uniform(400, seed=54), inputs.uniform(700, seed=55)]
+    offs = [0]
+    for b in boxes:
+        offs.append(offs[-1] + (0 if b is None else b["x"].size))
+    parts_ = [b for b in boxes if b is not None]
+    d = {k: np.concatenate([b[k] for b in parts_]) for k in inputs.FIELDS}
+    d = inputs.random_velocities(d, 0.1, 56)
+    both(d, 2, box_offsets=offs)
