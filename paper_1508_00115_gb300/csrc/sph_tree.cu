@@ -170,57 +170,57 @@ __global__ void k_node_split(const int *__restrict__ front, int nfront_h, const 
     const int nfront = lvl ? lvl[1] - lvl[0] : nfront_h;
     const int end = lvl ? cap : nfront;
     for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < end; w += gridDim.x * blockDim.x) {
-    if (w >= nfront) {
-        nkids[w] = 0u;
-        continue;
-    }
-    const TreeNode t = nodes[front[w]];
-    const bool split = (t.hi - t.lo) > leaf_max && t.level < kMortonBits;
-    int cnt = 0;
-    if (split) {
-        // child boundaries: first slot whose next Morton digit is >= k (k = 1..7)
-        const int sh = 3 * (kMortonBits - 1 - t.level);
-        int b[9];
-        b[0] = t.lo;
-        b[8] = t.hi;
-        for (int k = 1; k < 8; ++k) {
-            int lo = b[k - 1], hi = t.hi;  // digits are sorted: search from the previous bound
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if ((int)((keys[mid] >> sh) & 7u) < k) lo = mid + 1;
-                else hi = mid;
-            }
-            b[k] = lo;
+        if (w >= nfront) {
+            nkids[w] = 0u;
+            continue;
         }
-        // children: a half of the cube (octants 4h .. 4h + 3) if it holds at most
-        // leaf_max particles, else its quarters (octant pairs) that do, else octants
-        int starts = 0;
-        auto first_in = [&](int k0, int k1) {  // first non-empty octant of [k0, k1)
-            int k = k0;
-            while (k < k1 && b[k + 1] == b[k]) ++k;
-            return k;
-        };
-        for (int q0 = 0; q0 < 8; q0 += 4) {
-            const int qn = b[q0 + 4] - b[q0];
-            if (qn <= leaf_max) {
-                if (qn > 0) starts |= 1 << first_in(q0, q0 + 4);
-                continue;
+        const TreeNode t = nodes[front[w]];
+        const bool split = (t.hi - t.lo) > leaf_max && t.level < kMortonBits;
+        int cnt = 0;
+        if (split) {
+            // child boundaries: first slot whose next Morton digit is >= k (k = 1..7)
+            const int sh = 3 * (kMortonBits - 1 - t.level);
+            int b[9];
+            b[0] = t.lo;
+            b[8] = t.hi;
+            for (int k = 1; k < 8; ++k) {
+                int lo = b[k - 1], hi = t.hi;  // digits are sorted: search from the previous bound
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if ((int)((keys[mid] >> sh) & 7u) < k) lo = mid + 1;
+                    else hi = mid;
+                }
+                b[k] = lo;
             }
-            for (int p0 = q0; p0 < q0 + 4; p0 += 2) {
-                const int pn = b[p0 + 2] - b[p0];
-                if (pn <= leaf_max) {
-                    if (pn > 0) starts |= 1 << first_in(p0, p0 + 2);
+            // children: a half of the cube (octants 4h .. 4h + 3) if it holds at most
+            // leaf_max particles, else its quarters (octant pairs) that do, else octants
+            int starts = 0;
+            auto first_in = [&](int k0, int k1) {  // first non-empty octant of [k0, k1)
+                int k = k0;
+                while (k < k1 && b[k + 1] == b[k]) ++k;
+                return k;
+            };
+            for (int q0 = 0; q0 < 8; q0 += 4) {
+                const int qn = b[q0 + 4] - b[q0];
+                if (qn <= leaf_max) {
+                    if (qn > 0) starts |= 1 << first_in(q0, q0 + 4);
                     continue;
                 }
-                for (int k = p0; k < p0 + 2; ++k)
-                    if (b[k + 1] > b[k]) starts |= 1 << k;
+                for (int p0 = q0; p0 < q0 + 4; p0 += 2) {
+                    const int pn = b[p0 + 2] - b[p0];
+                    if (pn <= leaf_max) {
+                        if (pn > 0) starts |= 1 << first_in(p0, p0 + 2);
+                        continue;
+                    }
+                    for (int k = p0; k < p0 + 2; ++k)
+                        if (b[k + 1] > b[k]) starts |= 1 << k;
+                }
             }
+            cnt = __popc(starts);
+            for (int k = 0; k < 9; ++k) bounds[kBoundsW * w + k] = b[k];
+            bounds[kBoundsW * w + 9] = starts;
         }
-        cnt = __popc(starts);
-        for (int k = 0; k < 9; ++k) bounds[kBoundsW * w + k] = b[k];
-        bounds[kBoundsW * w + 9] = starts;
-    }
-    nkids[w] = (uint32_t)cnt;
+        nkids[w] = (uint32_t)cnt;
     }
 }
 
@@ -234,44 +234,44 @@ __global__ void k_leaf_box(TreeNode *__restrict__ nodes, int n_nodes_h, const in
     const int n_nodes = np ? *np : n_nodes_h;
     const int lane = threadIdx.x & 31;
     for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n_nodes; w += (gridDim.x * blockDim.x) >> 5) {
-    TreeNode t = nodes[w];
-    if (t.child >= 0) continue;  // warp-uniform
-    const BoxDev g = bxs[nb == 1 ? 0 : tbox_of_cell(t.top, bxs, nb)];
-    const int loc = t.top - g.cell_off;
-    const double cx = ((double)(loc % g.nc) + 0.5) * g.L64, cy = ((double)((loc / g.nc) % g.nc) + 0.5) * g.L64,
-                 cz = ((double)(loc / (g.nc * g.nc)) + 0.5) * g.L64;
-    float hm = 0.f, x0 = 1e30f, y0 = 1e30f, z0 = 1e30f, x1 = -1e30f, y1 = -1e30f, z1 = -1e30f;
-    for (int p = t.lo + lane; p < t.hi; p += 32) {
-        hm = fmaxf(hm, h[p]);
-        const float px = (float)(x[p] - cx), py = (float)(y[p] - cy), pz = (float)(z[p] - cz);
-        x0 = fminf(x0, px);
-        x1 = fmaxf(x1, px);
-        y0 = fminf(y0, py);
-        y1 = fmaxf(y1, py);
-        z0 = fminf(z0, pz);
-        z1 = fmaxf(z1, pz);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        hm = fmaxf(hm, __shfl_xor_sync(kFull, hm, o));
-        x0 = fminf(x0, __shfl_xor_sync(kFull, x0, o));
-        x1 = fmaxf(x1, __shfl_xor_sync(kFull, x1, o));
-        y0 = fminf(y0, __shfl_xor_sync(kFull, y0, o));
-        y1 = fmaxf(y1, __shfl_xor_sync(kFull, y1, o));
-        z0 = fminf(z0, __shfl_xor_sync(kFull, z0, o));
-        z1 = fmaxf(z1, __shfl_xor_sync(kFull, z1, o));
-    }
-    if (lane == 0) {
-        const float pad = g.L32 * 1.2e-7f;
-        t.hmax = hm;
-        t.bx0 = x0 - pad;
-        t.by0 = y0 - pad;
-        t.bz0 = z0 - pad;
-        t.bx1 = x1 + pad;
-        t.by1 = y1 + pad;
-        t.bz1 = z1 + pad;
-        nodes[w] = t;
-    }
+        TreeNode t = nodes[w];
+        if (t.child >= 0) continue;  // warp-uniform
+        const BoxDev g = bxs[nb == 1 ? 0 : tbox_of_cell(t.top, bxs, nb)];
+        const int loc = t.top - g.cell_off;
+        const double cx = ((double)(loc % g.nc) + 0.5) * g.L64, cy = ((double)((loc / g.nc) % g.nc) + 0.5) * g.L64,
+                     cz = ((double)(loc / (g.nc * g.nc)) + 0.5) * g.L64;
+        float hm = 0.f, x0 = 1e30f, y0 = 1e30f, z0 = 1e30f, x1 = -1e30f, y1 = -1e30f, z1 = -1e30f;
+        for (int p = t.lo + lane; p < t.hi; p += 32) {
+            hm = fmaxf(hm, h[p]);
+            const float px = (float)(x[p] - cx), py = (float)(y[p] - cy), pz = (float)(z[p] - cz);
+            x0 = fminf(x0, px);
+            x1 = fmaxf(x1, px);
+            y0 = fminf(y0, py);
+            y1 = fmaxf(y1, py);
+            z0 = fminf(z0, pz);
+            z1 = fmaxf(z1, pz);
+        }
+    #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            hm = fmaxf(hm, __shfl_xor_sync(kFull, hm, o));
+            x0 = fminf(x0, __shfl_xor_sync(kFull, x0, o));
+            x1 = fmaxf(x1, __shfl_xor_sync(kFull, x1, o));
+            y0 = fminf(y0, __shfl_xor_sync(kFull, y0, o));
+            y1 = fmaxf(y1, __shfl_xor_sync(kFull, y1, o));
+            z0 = fminf(z0, __shfl_xor_sync(kFull, z0, o));
+            z1 = fmaxf(z1, __shfl_xor_sync(kFull, z1, o));
+        }
+        if (lane == 0) {
+            const float pad = g.L32 * 1.2e-7f;
+            t.hmax = hm;
+            t.bx0 = x0 - pad;
+            t.by0 = y0 - pad;
+            t.bz0 = z0 - pad;
+            t.bx1 = x1 + pad;
+            t.by1 = y1 + pad;
+            t.bz1 = z1 + pad;
+            nodes[w] = t;
+        }
     }
 }
 
@@ -281,27 +281,27 @@ __global__ void k_merge_children(TreeNode *__restrict__ nodes, int first_h, int 
 {
     const int first = lb ? lb[level] : first_h, last = lb ? lb[level + 1] : last_h;
     for (int id = first + blockIdx.x * blockDim.x + threadIdx.x; id < last; id += gridDim.x * blockDim.x) {
-    TreeNode t = nodes[id];
-    if (t.child < 0) continue;
-    float hm = 0.f, x0 = 1e30f, y0 = 1e30f, z0 = 1e30f, x1 = -1e30f, y1 = -1e30f, z1 = -1e30f;
-    for (int c = t.child; c < t.child + t.nchild; ++c) {
-        const TreeNode k = nodes[c];
-        hm = fmaxf(hm, k.hmax);
-        x0 = fminf(x0, k.bx0);
-        y0 = fminf(y0, k.by0);
-        z0 = fminf(z0, k.bz0);
-        x1 = fmaxf(x1, k.bx1);
-        y1 = fmaxf(y1, k.by1);
-        z1 = fmaxf(z1, k.bz1);
-    }
-    t.hmax = hm;
-    t.bx0 = x0;
-    t.by0 = y0;
-    t.bz0 = z0;
-    t.bx1 = x1;
-    t.by1 = y1;
-    t.bz1 = z1;
-    nodes[id] = t;
+        TreeNode t = nodes[id];
+        if (t.child < 0) continue;
+        float hm = 0.f, x0 = 1e30f, y0 = 1e30f, z0 = 1e30f, x1 = -1e30f, y1 = -1e30f, z1 = -1e30f;
+        for (int c = t.child; c < t.child + t.nchild; ++c) {
+            const TreeNode k = nodes[c];
+            hm = fmaxf(hm, k.hmax);
+            x0 = fminf(x0, k.bx0);
+            y0 = fminf(y0, k.by0);
+            z0 = fminf(z0, k.bz0);
+            x1 = fmaxf(x1, k.bx1);
+            y1 = fmaxf(y1, k.by1);
+            z1 = fmaxf(z1, k.bz1);
+        }
+        t.hmax = hm;
+        t.bx0 = x0;
+        t.by0 = y0;
+        t.bz0 = z0;
+        t.bx1 = x1;
+        t.by1 = y1;
+        t.bz1 = z1;
+        nodes[id] = t;
     }
 }
 
@@ -317,43 +317,43 @@ __global__ void k_make_children(const int *__restrict__ front, int nfront_h, Tre
     const int base = lvl ? lvl[1] : base_h;
     if (total == 0u) return;
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nfront; f += gridDim.x * blockDim.x) {
-    const uint32_t first = off[f], end = f + 1 < nfront ? off[f + 1] : total;
-    if (end == first) continue;  // not refined: a leaf
-    const int id = front[f];
-    const int *b = bounds + kBoundsW * f;
-    const int starts = b[9];
-    TreeNode &t = nodes[id];
-    int c = 0;
-    for (int k = 0; k < 8; ++k) {
-        if (!((starts >> k) & 1)) continue;
-        // the child runs from octant k up to the next starting octant
-        int e = k + 1;
-        int octants = 1;
-        while (e < 8 && !((starts >> e) & 1)) {
-            octants += b[e + 1] > b[e] ? 1 : 0;
-            ++e;
+        const uint32_t first = off[f], end = f + 1 < nfront ? off[f + 1] : total;
+        if (end == first) continue;  // not refined: a leaf
+        const int id = front[f];
+        const int *b = bounds + kBoundsW * f;
+        const int starts = b[9];
+        TreeNode &t = nodes[id];
+        int c = 0;
+        for (int k = 0; k < 8; ++k) {
+            if (!((starts >> k) & 1)) continue;
+            // the child runs from octant k up to the next starting octant
+            int e = k + 1;
+            int octants = 1;
+            while (e < 8 && !((starts >> e) & 1)) {
+                octants += b[e + 1] > b[e] ? 1 : 0;
+                ++e;
+            }
+            TreeNode ch;
+            ch.lo = b[k];
+            ch.hi = b[e];
+            ch.child = -1;
+            ch.nchild = 0;
+            ch.top = t.top;
+            if (octants == 1) {  // one octant: its own cube
+                ch.level = t.level + 1;
+                ch.prefix = (t.prefix << 3) | (uint64_t)k;
+            } else {  // joined octants: the parent's cube
+                ch.level = t.level;
+                ch.prefix = t.prefix;
+            }
+            ch.parent = id;
+            const int cid = base + (int)first + c;
+            nodes[cid] = ch;
+            next[first + c] = cid;
+            ++c;
         }
-        TreeNode ch;
-        ch.lo = b[k];
-        ch.hi = b[e];
-        ch.child = -1;
-        ch.nchild = 0;
-        ch.top = t.top;
-        if (octants == 1) {  // one octant: its own cube
-            ch.level = t.level + 1;
-            ch.prefix = (t.prefix << 3) | (uint64_t)k;
-        } else {  // joined octants: the parent's cube
-            ch.level = t.level;
-            ch.prefix = t.prefix;
-        }
-        ch.parent = id;
-        const int cid = base + (int)first + c;
-        nodes[cid] = ch;
-        next[first + c] = cid;
-        ++c;
-    }
-    t.child = base + (int)first;
-    t.nchild = c;
+        t.child = base + (int)first;
+        t.nchild = c;
     }
 }
 
