@@ -113,6 +113,10 @@ typedef struct {
                          /* copied by sph_init                                       */
     int32_t leaf_max;    /* SPH_FLAG_ADAPTIVE: refine nodes holding more particles   */
                          /* than this (1..4096; 0 = default 64)                     */
+    int64_t list_reserve; /* SPH_FLAG_ADAPTIVE, sph_steps: neighbour-list entries   */
+                         /* reserved for the captured builds (>= 0; 0 = twice the  */
+                         /* last host build's, at least 2^20); lists that outgrow  */
+                         /* it return SPH_ERR_CAPACITY                              */
 } sph_params;
 
 /*

@@ -60,7 +60,8 @@ class sph_params(ctypes.Structure):
                 ("max_h_iter", ctypes.c_int32), ("use_balsara", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("tile_width", ctypes.c_int32), ("n_boxes", ctypes.c_int32),
-                ("box_offsets", ctypes.c_void_p), ("leaf_max", ctypes.c_int32)]
+                ("box_offsets", ctypes.c_void_p), ("leaf_max", ctypes.c_int32),
+                ("list_reserve", ctypes.c_int64)]
 
 
 _PFIELDS = ["x", "y", "z", "vx", "vy", "vz", "m", "u", "h", "rho", "P", "c", "f", "divv", "curl",

@@ -131,6 +131,7 @@ static int check_params(const sph_params *p, std::string &why)
     else if (p->kernel != 0) why = "kernel must be 0 (cubic spline)";
     else if (p->tile_width != 0 && p->tile_width != 16 && p->tile_width != 32) why = "tile_width must be 0, 16 or 32";
     else if (p->leaf_max < 0 || p->leaf_max > 4096) why = "leaf_max must be in [0, 4096]";
+    else if (p->list_reserve < 0) why = "list_reserve must be >= 0";
     else if (p->n_boxes < 0) why = "n_boxes must be >= 0";
     else if (p->n_boxes > 1 && !p->box_offsets) why = "box_offsets required for n_boxes > 1";
     else if (p->n_boxes > 1 && (p->box_offsets[0] != 0 || p->box_offsets[p->n_boxes] != p->n)) why = "box_offsets must run from 0 to n";

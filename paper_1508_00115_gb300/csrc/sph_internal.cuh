@@ -126,7 +126,7 @@ struct AdaptiveTree {
     // graph-captured steps: counts on the device (dc) and their pinned host copy (hc),
     // fixed capacities of a frontier and of the node array, and the build mode
     TreeCounts *dc = nullptr, *hc = nullptr;
-    int64_t dev_capf = 0, dev_cap_nodes = 0;
+    int64_t dev_capf = 0, dev_cap_nodes = 0, dev_cap_list = 0;
     bool device_sized = false;   // build without host reads (set while a step is captured)
 };
 

@@ -1000,7 +1000,7 @@ static int build_tree_device(sph_ctx *ctx, sph_particles *parts)
     k_sum_u32<<<gp, 256, 0, ctx->stream>>>(T.list_off, (int)capl, &dc->list_total);
     SPH_LAUNCH(ctx, "list total");
     if ((rc = exclusive_scan_u32(ctx, T.list_off, T.list_off, capl))) return rc;  // list_off[nl] = total
-    k_list_check<<<1, 32, 0, ctx->stream>>>(dc, T.cap_list, ctx->n_tiles);
+    k_list_check<<<1, 32, 0, ctx->stream>>>(dc, T.dev_cap_list, ctx->n_tiles);
     SPH_LAUNCH(ctx, "list check");
     wa.skip_ovf = &dc->walk_ovf;
     wa.err = &dc->err;
@@ -1032,8 +1032,9 @@ int tree_prepare_device(sph_ctx *ctx, uint64_t *sig)
     // host builds between captured runs do not move them
     const int64_t host_nodes = ntop + 4 * n + 64;
     const int64_t an = std::max(cap_nodes, host_nodes), af = std::max(capf + 1, host_nodes);
-    // list reserve: twice the last build's entries, at least 2^20
-    const int64_t list_need = std::max<int64_t>(2 * T.n_entries, 1 << 20) + 1;
+    // list reserve: as asked, else twice the last build's entries, at least 2^20
+    const int64_t list_need =
+        (ctx->p.list_reserve > 0 ? ctx->p.list_reserve : std::max<int64_t>(2 * T.n_entries, 1 << 20)) + 1;
     int rc;
     if ((rc = grow(ctx, ctx->keys64, T.cap_keys, n)) || (rc = grow(ctx, ctx->keys64_alt, T.cap_keys2, n)) ||
         (rc = grow(ctx, T.leaf_of, T.cap_leaf_of, n)) || (rc = grow(ctx, T.node_at, T.cap_node_at, n)) ||
@@ -1052,12 +1053,13 @@ int tree_prepare_device(sph_ctx *ctx, uint64_t *sig)
     if (!T.hc) SPH_CUDA(ctx, cudaMallocHost(&T.hc, sizeof(TreeCounts)));
     T.dev_capf = capf;
     T.dev_cap_nodes = cap_nodes;
+    T.dev_cap_list = std::min<int64_t>(list_need - 1, T.cap_list);
     // FNV-1a over every array address and capacity the captured kernels see
     // (the sort's ping-pong pair in either order: captures may swap it)
     const void *ptrs[] = {std::min(ctx->keys64, ctx->keys64_alt), std::max(ctx->keys64, ctx->keys64_alt), T.leaf_of, T.node_at, T.tord, T.act_ord, T.top_node,
                           T.nodes, T.node_leaf, T.front, T.front2, T.bounds, T.nkids, T.leaf_node, T.leaf_rng,
                           T.leaf_cen, T.leaf_h, T.leaf_scale, T.nact_leaf, T.list_off, T.list, T.dc};
-    const int64_t caps[] = {capf, T.dev_cap_nodes, T.cap_list, ctx->leaf_max};
+    const int64_t caps[] = {capf, T.dev_cap_nodes, T.cap_list, T.dev_cap_list, ctx->leaf_max};
     uint64_t hsh = 1469598103934665603ull;
     auto mix = [&](uint64_t v) {
         for (int b = 0; b < 8; ++b) hsh = (hsh ^ ((v >> (8 * b)) & 0xffu)) * 1099511628211ull;

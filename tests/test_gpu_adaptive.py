@@ -396,3 +396,25 @@ def test_adaptive_graph_steps_edge_cases():
     d = {k: np.concatenate([b[k] for b in parts_]) for k in inputs.FIELDS}
     d = inputs.random_velocities(d, 0.1, 56)
     both(d, 2, box_offsets=offs)
+
+
+def test_adaptive_graph_list_reserve_overflow():
+    """Lists that outgrow the reserve of a captured build: the step does no pair work
+    (no entry is written past the reserve), the call returns SPH_ERR_CAPACITY, and
+    the context carries on with host steps."""
+    from paper_1508_00115_gb300 import binding
+    d = _clustered(5000, 57, 3)
+    n = d["x"].size
+    ctx = binding.Context(n, flags=_flags(False), list_reserve=1000)
+    parts = binding.Particles(d)
+    with pytest.raises(binding.SphError) as e:
+        ctx.steps(parts, 2, 1e-5)
+    assert e.value.code == binding.SPH_ERR_CAPACITY
+    ctx.step(parts, 1e-5)  # host-sized build: no reserve involved
+    g = parts.numpy()
+    assert np.all(np.isfinite(g["rho"])) and np.all(g["rho"] > 0)
+    # a reserve that holds the lists: the same call goes through
+    ctx2 = binding.Context(n, flags=_flags(False), list_reserve=50_000_000)
+    p2 = binding.Particles(d)
+    ctx2.steps(p2, 2, 1e-5)
+    assert ctx2.stats()["graph_steps"] == 2
