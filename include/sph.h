@@ -249,7 +249,7 @@ int sph_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_used, sph
  * (cells stay correct while every h stays within twice the planned cell side;
  * beyond that the call returns SPH_ERR_H_EXCEEDS_CELL; adaptive cells: the top
  * grid is kept while its sides are >= 1.15 max h, else planned at that margin,
- * and stays correct while every h stays within its top cell side and within 1.25
+ * and stays correct while every h stays within its top cell side and within 1.15
  * of its leaf's largest h at the step's build -- a Newton step is cut back to
  * that limit, and SPH_ERR_H_EXCEEDS_CELL reported if a root lies beyond); each density
  * evaluation runs a fixed number of passes, min(max_h_iter, 6) -- passes after

@@ -684,7 +684,7 @@ int hp_apply_step(sph_ctx *ctx, sph_particles *parts)
     int rc = hp_features(ctx, parts);
     if (rc) return rc;
     // growth is capped so that h stays within what the cells (lists) were built for
-    const float g_max = ctx->adaptive ? std::min(1.2f, ctx->p.cell_factor) : 1.2f;
+    const float g_max = ctx->adaptive ? std::min(std::min(1.2f, ctx->p.cell_factor), kTreeReach) : 1.2f;
     return hp_run(ctx, ctx->hp.feats, ctx->hp.h_prev, parts->h, ctx->n, logf(0.5f), logf(g_max));
 }
 

