@@ -352,16 +352,20 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
             for (int wd = 0; wd < nwords; ++wd) {
                 const int kend = min(32, nmax - 32 * wd);
                 const float4 *sw = sA + 32 * wd;
-                unsigned mw = 0u;
+                unsigned mw = 0u, bw = 0u;  // hits; pairs in the FP32 band, decided below
 #pragma unroll 4
                 for (int kk = 0; kk < kend; ++kk) {
                     const float4 s = sw[kk];
                     const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
                     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    bool in = r2 < lob;
-                    if (!in && r2 < hib)
-                        in = band_decide(a.x, a.y, a.z, i, __float_as_int(s.w), a.box, hi, hi) & 1u;
-                    mw |= (unsigned)in << kk;
+                    mw |= (unsigned)(r2 < lob) << kk;
+                    bw |= (unsigned)(r2 >= lob && r2 < hib) << kk;
+                }
+                // (rare) band pairs in FP64, out of the branch-free loop above
+                while (bw) {
+                    const int kk = __ffs(bw) - 1;
+                    bw &= bw - 1u;
+                    if (band_decide(a.x, a.y, a.z, i, __float_as_int(sw[kk].w), a.box, hi, hi) & 1u) mw |= 1u << kk;
                 }
                 m0 = wd == 0 ? mw : m0;
                 m1 = wd == 1 ? mw : m1;
@@ -793,7 +797,7 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
             for (int wd = 0; wd < nwords; ++wd) {
                 const int kend = min(32, nmax - 32 * wd);
                 const float4 *sw = sA + 32 * wd;
-                unsigned mw = 0u;
+                unsigned mw = 0u, bw = 0u;  // hits; pairs in the FP32 band, decided below
 #pragma unroll 4
                 for (int kk = 0; kk < kend; ++kk) {
                     const float4 s = sw[kk];
@@ -808,12 +812,15 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
                         m2x = fmaxf(hi2, s.w * s.w);
                         bm = bandmax;
                     }
-                    bool in = r2 < m2x - bm;
-                    if (!in && r2 < m2x + bm) {
-                        const unsigned d = band_decide(a.x, a.y, a.z, i, sI[32 * wd + kk], a.box, hi, s.w);
-                        in = d != 0u;
-                    }
-                    mw |= (unsigned)in << kk;
+                    const float d2 = r2 - m2x;
+                    mw |= (unsigned)(d2 < -bm) << kk;
+                    bw |= (unsigned)(d2 >= -bm && d2 < bm) << kk;
+                }
+                // (rare) band pairs in FP64, out of the branch-free loop above
+                while (bw) {
+                    const int kk = __ffs(bw) - 1;
+                    bw &= bw - 1u;
+                    if (band_decide(a.x, a.y, a.z, i, sI[32 * wd + kk], a.box, hi, sw[kk].w) != 0u) mw |= 1u << kk;
                 }
                 m0 = wd == 0 ? mw : m0;
                 m1 = wd == 1 ? mw : m1;
