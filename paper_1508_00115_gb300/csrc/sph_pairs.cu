@@ -340,8 +340,9 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
         int nst = 0;  // staged survivors of this tile (uniform within the tile)
 
         auto flush = [&]() {
-            const int nmax = __reduce_max_sync(kFull, (unsigned)nst);
-            // pad this tile's batch up to the warp's longest one (index 0 is a valid particle)
+            // pad this tile's batch up to the warp's longest one, rounded up to a
+            // multiple of 4 (index 0 is a valid particle; the pads are far away)
+            const int nmax = (int)((__reduce_max_sync(kFull, (unsigned)nst) + 3u) & ~3u);
             for (int k = nst + tl; k < nmax; k += TW) sA[k] = make_float4(-kFar, -kFar, -kFar, __int_as_float(0));
             __syncwarp();
             cand += (unsigned)nst;
@@ -350,16 +351,21 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
             const int nwords = (nmax + 31) >> 5;
 #pragma unroll 1
             for (int wd = 0; wd < nwords; ++wd) {
-                const int kend = min(32, nmax - 32 * wd);
+                const int kend = min(32, nmax - 32 * wd);  // a multiple of 4
                 const float4 *sw = sA + 32 * wd;
                 unsigned mw = 0u, bw = 0u;  // hits; pairs in the FP32 band, decided below
-#pragma unroll 4
-                for (int kk = 0; kk < kend; ++kk) {
-                    const float4 s = sw[kk];
-                    const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    mw |= (unsigned)(r2 < lob) << kk;
-                    bw |= (unsigned)(r2 >= lob && r2 < hib) << kk;
+                for (int k4 = 0; k4 < kend; k4 += 4) {
+                    unsigned mn = 0u, bn = 0u;  // the four tests of this group
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 s = sw[k4 + u];
+                        const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        mn |= (unsigned)(r2 < lob) << u;
+                        bn |= (unsigned)(r2 >= lob && r2 < hib) << u;
+                    }
+                    mw |= mn << k4;
+                    bw |= bn << k4;
                 }
                 // (rare) band pairs in FP64, out of the branch-free loop above
                 while (bw) {
@@ -783,8 +789,9 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
         };
 
         auto flush = [&]() {
-            const int nmax = __reduce_max_sync(kFull, (unsigned)nst);
-            // pad this tile's batch up to the warp's longest one (index 0 is a valid particle)
+            // pad this tile's batch up to the warp's longest one, rounded up to a
+            // multiple of 4 (index 0 is a valid particle; the pads are far away)
+            const int nmax = (int)((__reduce_max_sync(kFull, (unsigned)nst) + 3u) & ~3u);
             for (int k = nst + tl; k < nmax; k += TW) {
                 sA[k] = make_float4(-kFar, -kFar, -kFar, 0.f);
                 sI[k] = 0;
@@ -795,26 +802,31 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
             const int nwords = (nmax + 31) >> 5;
 #pragma unroll 1
             for (int wd = 0; wd < nwords; ++wd) {
-                const int kend = min(32, nmax - 32 * wd);
+                const int kend = min(32, nmax - 32 * wd);  // a multiple of 4
                 const float4 *sw = sA + 32 * wd;
                 unsigned mw = 0u, bw = 0u;  // hits; pairs in the FP32 band, decided below
-#pragma unroll 4
-                for (int kk = 0; kk < kend; ++kk) {
-                    const float4 s = sw[kk];
-                    const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    float m2x, bm;
-                    if (LIST) {  // band of this pair: h spans decades within a list
-                        const float mm = fmaxf(hi, s.w);
-                        m2x = mm * mm;
-                        bm = kBandK * mm * (mm + L);
-                    } else {
-                        m2x = fmaxf(hi2, s.w * s.w);
-                        bm = bandmax;
+                for (int k4 = 0; k4 < kend; k4 += 4) {
+                    unsigned mn = 0u, bn = 0u;  // the four tests of this group
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 s = sw[k4 + u];
+                        const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        float m2x, bm;
+                        if (LIST) {  // band of this pair: h spans decades within a list
+                            const float mm = fmaxf(hi, s.w);
+                            m2x = mm * mm;
+                            bm = kBandK * mm * (mm + L);
+                        } else {
+                            m2x = fmaxf(hi2, s.w * s.w);
+                            bm = bandmax;
+                        }
+                        const float d2 = r2 - m2x;
+                        mn |= (unsigned)(d2 < -bm) << u;
+                        bn |= (unsigned)(d2 >= -bm && d2 < bm) << u;
                     }
-                    const float d2 = r2 - m2x;
-                    mw |= (unsigned)(d2 < -bm) << kk;
-                    bw |= (unsigned)(d2 >= -bm && d2 < bm) << kk;
+                    mw |= mn << k4;
+                    bw |= bn << k4;
                 }
                 // (rare) band pairs in FP64, out of the branch-free loop above
                 while (bw) {
