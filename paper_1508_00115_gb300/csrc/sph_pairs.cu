@@ -969,27 +969,23 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
                     j = __float_as_int(e.y);
                     vq = sw_sg * e.x < sw_lim;
                 }
-                bool keep = false;
-                float4 pj, vj, tj;
-                int jj = 0;
-                if (vq) {
-                    pj = __ldg(a.pos4 + j);
-                    vj = __ldg(a.vel4 + j);
-                    tj = __ldg(a.thermo4 + j);
-                    jj = j;
-                    pj.x += shx;
-                    pj.y += shy;
-                    pj.z += shz;
-                    const float ex = fmaxf(fmaxf(lox - pj.x, pj.x - hix), 0.f);
-                    const float ey = fmaxf(fmaxf(loy - pj.y, pj.y - hiy), 0.f);
-                    const float ez = fmaxf(fmaxf(loz - pj.z, pj.z - hiz), 0.f);
-                    float r2max = reach2;
-                    if (LIST) {
-                        const float m = fmaxf(H, pj.w);
-                        r2max = m * m * (1.f + kPruneMargin) + 2.f * kBandK * m * (m + L);
-                    }
-                    keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < r2max;
+                // (no branch: a lane past the chunk's end reads slot 0 and keeps nothing)
+                const int jj = vq ? j : 0;
+                float4 pj = __ldg(a.pos4 + jj);
+                const float4 vj = __ldg(a.vel4 + jj);
+                const float4 tj = __ldg(a.thermo4 + jj);
+                pj.x += shx;
+                pj.y += shy;
+                pj.z += shz;
+                const float ex = fmaxf(fmaxf(lox - pj.x, pj.x - hix), 0.f);
+                const float ey = fmaxf(fmaxf(loy - pj.y, pj.y - hiy), 0.f);
+                const float ez = fmaxf(fmaxf(loz - pj.z, pj.z - hiz), 0.f);
+                float r2max = reach2;
+                if (LIST) {
+                    const float m = fmaxf(H, pj.w);
+                    r2max = m * m * (1.f + kPruneMargin) + 2.f * kBandK * m * (m + L);
                 }
+                const bool keep = vq && fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < r2max;
                 const unsigned mine = __ballot_sync(kFull, keep) & gmask;
                 if (keep) {
                     const int pos = nst + __popc(mine & lt);
