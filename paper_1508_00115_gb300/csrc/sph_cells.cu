@@ -321,20 +321,53 @@ struct WrapArgs {
     uint32_t *keys;
 };
 
+// Wrap of one coordinate: positions already inside the box (FP32 test with a margin)
+// are returned as they are; the others take the FP64 wrap.  Written back only if
+// it moved.
+__device__ __forceinline__ double wrap_coord(double *p, double box, float box_in)
+{
+    const double v = *p;
+    const float vf = (float)v;
+    if (vf > 0.f && vf < box_in) return v;
+    const double w = wrap64(v, box);
+    if (w != v) *p = w;
+    return w;
+}
+
+// Cell index along one axis, floor(v s) clamped, and whether v lies in the upper half
+// of that cell, v >= (c + 1/2) L -- as the FP64 forms cell_of / centre64 give them.
+// The FP32 product t carries a relative error below 2e-7; where t lies further than
+// eps = 1e-6 (t + 1) from an integer and from a half-integer both answers are those of
+// the FP64 forms, else they are computed in FP64.
+__device__ __forceinline__ int cell_half(double v, const BoxDev &g, float sf, unsigned &upper)
+{
+    const float t = __fmul_rn((float)v, sf);
+    const float fl = floorf(t);
+    const float fr = t - fl;
+    const float eps = fmaf(t, 1e-6f, 1e-6f);
+    if (fr > eps && fr < 1.f - eps && fabsf(fr - 0.5f) > eps && fl < (float)g.nc) {
+        upper = fr >= 0.5f ? 1u : 0u;
+        return (int)fl;
+    }
+    const int c = cell_of(v, g.s, g.nc);
+    upper = v >= centre64(c, g.L64) ? 1u : 0u;
+    return c;
+}
+
 __global__ void k_wrap_key(WrapArgs a)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const BoxDev g = a.bx[a.nb == 1 ? 0 : box_of_slot(i, a.bx, a.nb)];
-    double x = wrap64(a.x[i], a.box), y = wrap64(a.y[i], a.box), z = wrap64(a.z[i], a.box);
-    a.x[i] = x;
-    a.y[i] = y;
-    a.z[i] = z;
-    int ix = cell_of(x, g.s, g.nc), iy = cell_of(y, g.s, g.nc), iz = cell_of(z, g.s, g.nc);
+    const float box_in = (float)a.box * (1.f - 1e-6f);
+    const double x = wrap_coord(a.x + i, a.box, box_in), y = wrap_coord(a.y + i, a.box, box_in),
+                 z = wrap_coord(a.z + i, a.box, box_in);
+    const float sf = (float)g.s;
+    unsigned ux, uy, uz;
+    const int ix = cell_half(x, g, sf, ux), iy = cell_half(y, g, sf, uy), iz = cell_half(z, g, sf, uz);
     // key = cell * 8 + octant: inside a cell particles are grouped by octant (z
     // slowest), so the tiles of a cell split in two are each about half a cell
-    const unsigned oct = (x >= centre64(ix, g.L64) ? 1u : 0u) | (y >= centre64(iy, g.L64) ? 2u : 0u) |
-                         (z >= centre64(iz, g.L64) ? 4u : 0u);
+    const unsigned oct = ux | (uy << 1) | (uz << 2);
     a.keys[i] = ((uint32_t)(g.cell_off + (iz * g.nc + iy) * g.nc + ix) << 3) | oct;
 }
 
