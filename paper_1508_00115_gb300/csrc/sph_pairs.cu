@@ -1103,7 +1103,10 @@ __global__ void k_tile_scatter(const int4 *__restrict__ tiles, const uint32_t *_
 
 int compact_active_tiles(sph_ctx *ctx)
 {
-    const int64_t cap = ctx->tile_cap;
+    // every tile holds <= tile_w targets of one cell: at most n / tile_w + n_cells
+    // tiles (uniform grid), far fewer than the array's capacity
+    int64_t cap = ctx->tile_cap;
+    if (!ctx->adaptive) cap = std::min<int64_t>(cap, ctx->grid.n_cells + ctx->n / ctx->tile_w + 1);
     const unsigned blocks = (unsigned)((cap + 255) / 256);
     k_tile_flags<<<blocks, 256, 0, ctx->stream>>>(ctx->tiles, ctx->n_tiles, ctx->active,
                                                  ctx->adaptive ? ctx->tree.tord : nullptr, cap, ctx->tile_flag);
