@@ -115,6 +115,8 @@ struct AdaptiveTree {
     int *leaf_node = nullptr;
     int2 *leaf_rng = nullptr;  // particle slots of every leaf
     double *leaf_cen = nullptr; // absolute centre of every leaf (3 per leaf)
+    float4 *leaf_lo = nullptr, *leaf_hi = nullptr;  // leaf bounding box relative to its centre
+                                                    // (lo.w: the leaf's largest h at the build)
     float *leaf_h = nullptr;     // largest h per leaf when the tree was built
     float *leaf_scale = nullptr; // coordinate scale of the leaf's pair arithmetic (FP32 band width)
     uint32_t *list_off = nullptr; // neighbour-list offsets, n_leaves + 1
@@ -123,7 +125,8 @@ struct AdaptiveTree {
     int *h_i32 = nullptr;
     int64_t cap_keys = 0, cap_keys2 = 0, cap_leaf_of = 0, cap_tord = 0, cap_act_ord = 0, cap_nact_leaf = 0, cap_node_at = 0, cap_top = 0, cap_nodes = 0,
             cap_front = 0, cap_front2 = 0, cap_bounds = 0, cap_nkids = 0, cap_node_leaf = 0, cap_leaf_node = 0,
-            cap_leaf_rng = 0, cap_leaf_cen = 0, cap_leaf_h = 0, cap_leaf_scale = 0, cap_list_off = 0, cap_list = 0;
+            cap_leaf_rng = 0, cap_leaf_cen = 0, cap_leaf_h = 0, cap_leaf_scale = 0, cap_list_off = 0, cap_list = 0,
+            cap_leaf_lo = 0, cap_leaf_hi = 0;
     int n_nodes = 0, n_leaves = 0;
     int64_t n_entries = 0;
     // graph-captured steps: counts on the device (dc) and their pinned host copy (hc),

@@ -114,9 +114,16 @@ struct ListStream {
     float px = 0.f, py = 0.f, pz = 0.f;  // offset of this lane's entry
 
     // next window (warp-uniform); false once the longest list of the warp is done;
-    // *nchunk = the warp's largest chunk count of the window
-    __device__ __forceinline__ bool next(const float4 *__restrict__ list, const int2 *__restrict__ rng, uint32_t e0,
-                                         int ne, int ncell, int tl, int &nchunk)
+    // *nchunk = the warp's largest chunk count of the window.  An entry whose leaf box
+    // (moved by the entry's offset) lies beyond reach of the tile's box contributes no
+    // sources: the staging would reject every one of them.  Reach: sqrt(reach2) for the
+    // density (targets' h); for the force (FORCE) the larger of the targets' h and
+    // kTreeReach x the leaf's build-time h, which bounds its sources' h.
+    template <bool FORCE>
+    __device__ __forceinline__ bool next(const float4 *__restrict__ list, const int2 *__restrict__ rng,
+                                         const float4 *__restrict__ blo, const float4 *__restrict__ bhi, uint32_t e0,
+                                         int ne, int ncell, int tl, int &nchunk, float lox, float hix, float loy,
+                                         float hiy, float loz, float hiz, float reach2, float H, float L)
     {
         wb += TW;
         if (wb >= ncell) return false;
@@ -124,12 +131,39 @@ struct ListStream {
         px = py = pz = 0.f;
         if (wb + tl < ne) {
             const float4 en = list[e0 + (uint32_t)(wb + tl)];
-            const int2 r = rng[__float_as_int(en.w)];
+            const int lf = __float_as_int(en.w);
+            const int2 r = rng[lf];
             b = r.x;
             c = r.y - r.x;
             px = en.x;
             py = en.y;
             pz = en.z;
+            const float4 lo = blo[lf], hi = bhi[lf];
+            const float gx = fmaxf(fmaxf(lo.x + px - hix, lox - (hi.x + px)), 0.f);
+            const float gy = fmaxf(fmaxf(lo.y + py - hiy, loy - (hi.y + py)), 0.f);
+            const float gz = fmaxf(fmaxf(lo.z + pz - hiz, loz - (hi.z + pz)), 0.f);
+            float r2 = reach2;
+            if (FORCE) {
+                const float m = fmaxf(H, kTreeReach * lo.w * 1.00001f);
+                r2 = m * m * (1.f + kPruneMargin) + 2.f * kBandK * m * (m + L);
+            }
+            if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > r2 * 1.00001f) c = 0;
+        }
+        // the window's non-empty entries moved to the front (list order kept), so that
+        // the lookup below meets no empty entry before the last non-empty one
+        {
+            const int g = TW == 32 ? 0 : (int)(threadIdx.x & 31) / TW;
+            const unsigned gm = TW == 32 ? kFull : (((1u << TW) - 1u) << (TW * g));
+            const unsigned mine = __ballot_sync(kFull, c > 0) & gm;
+            const unsigned src = __fns(mine, (unsigned)(TW * g), tl + 1);
+            const bool has = src < 32u;
+            const int sl = has ? (int)src : (int)(threadIdx.x & 31);
+            c = __shfl_sync(kFull, c, sl);
+            b = __shfl_sync(kFull, b, sl);
+            px = __shfl_sync(kFull, px, sl);
+            py = __shfl_sync(kFull, py, sl);
+            pz = __shfl_sync(kFull, pz, sl);
+            if (!has) c = 0;
         }
         incl = c;
 #pragma unroll
@@ -191,6 +225,7 @@ struct DensityArgs {
     const float4 *__restrict__ list;
     const int2 *__restrict__ leaf_rng;
     const float *__restrict__ leaf_scale;
+    const float4 *__restrict__ leaf_lo, *__restrict__ leaf_hi;  // adaptive: leaf boxes (leaf frame)
     const float *__restrict__ leaf_hb;
     int hold_cells;  // list mode: the cells cannot be rebuilt during this iteration
     const int *__restrict__ tord;  // adaptive: targets of a leaf in ascending h (tiles index this)
@@ -473,7 +508,9 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
             ++ch;
             if (LIST) {
                 while (ch >= nchunk) {
-                    if (!ls.next(a.list, a.leaf_rng, e0, ne, ncell, tl, nchunk)) return false;
+                    if (!ls.template next<false>(a.list, a.leaf_rng, a.leaf_lo, a.leaf_hi, e0, ne, ncell, tl, nchunk,
+                                                 lox, hix, loy, hiy, loz, hiz, reach2, 0.f, L))
+                        return false;
                     ch = 0;
                 }
                 return true;
@@ -694,6 +731,7 @@ struct ForceArgs {
     const float4 *__restrict__ list;
     const int2 *__restrict__ leaf_rng;
     const float *__restrict__ leaf_scale;
+    const float4 *__restrict__ leaf_lo, *__restrict__ leaf_hi;  // adaptive: leaf boxes (leaf frame)
     const int *__restrict__ tord;
     const float2 *__restrict__ axis;
     int64_t axis_stride;
@@ -922,7 +960,9 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
         const float rlim = SWEEP ? sqrtf(reach2) : 0.f;
         for (;;) {
             if (LIST) {
-                while (ch >= nchunk && ls.next(a.list, a.leaf_rng, e0, ne, ncell, tl, nchunk)) ch = 0;
+                while (ch >= nchunk && ls.template next<true>(a.list, a.leaf_rng, a.leaf_lo, a.leaf_hi, e0, ne, ncell, tl,
+                                                              nchunk, lox, hix, loy, hiy, loz, hiz, reach2, H, L))
+                    ch = 0;
             }
             while (!LIST && ch >= nchunk && o < ncell - 1) {
                 ++o;
@@ -1151,6 +1191,8 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool ac
     a.list = ctx->tree.list;
     a.leaf_rng = ctx->tree.leaf_rng;
     a.leaf_scale = ctx->tree.leaf_scale;
+    a.leaf_lo = ctx->tree.leaf_lo;
+    a.leaf_hi = ctx->tree.leaf_hi;
     a.leaf_hb = ctx->tree.leaf_h;
     a.hold_cells = ctx->tree.device_sized ? 1 : 0;  // captured steps
     // adaptive cells: later passes run tiles of the active targets only (act_ord)
@@ -1206,6 +1248,8 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts)
     a.list = ctx->tree.list;
     a.leaf_rng = ctx->tree.leaf_rng;
     a.leaf_scale = ctx->tree.leaf_scale;
+    a.leaf_lo = ctx->tree.leaf_lo;
+    a.leaf_hi = ctx->tree.leaf_hi;
     a.tord = ctx->tree.tord;
     a.axis = (ctx->p.flags & SPH_FLAG_AXIS_SWEEP) && !ctx->adaptive ? ctx->axis : nullptr;
     a.axis_stride = std::max<int64_t>(ctx->cap, 1);

@@ -405,7 +405,7 @@ __global__ void k_leaves(const uint32_t *__restrict__ flag, const uint32_t *__re
                          const int *__restrict__ node_at, const TreeNode *__restrict__ nodes,
                          const BoxDev *__restrict__ bxs, int nb, int *__restrict__ leaf_of, int *__restrict__ leaf_node,
                          int *__restrict__ node_leaf, int2 *__restrict__ leaf_rng, double *__restrict__ leaf_cen,
-                         float *__restrict__ leaf_h)
+                         float *__restrict__ leaf_h, float4 *__restrict__ leaf_lo, float4 *__restrict__ leaf_hi)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -427,9 +427,18 @@ __global__ void k_leaves(const uint32_t *__restrict__ flag, const uint32_t *__re
     const double fine = g.L64 / (double)(1 << kMortonBits);
     const double sx = (double)compact3(pre) * fine, sy = (double)compact3(pre >> 1) * fine,
                  sz = (double)compact3(pre >> 2) * fine;
-    leaf_cen[3 * lid + 0] = (double)ix * g.L64 + sx + 0.5 * side;
-    leaf_cen[3 * lid + 1] = (double)iy * g.L64 + sy + 0.5 * side;
-    leaf_cen[3 * lid + 2] = (double)iz * g.L64 + sz + 0.5 * side;
+    const double lx = (double)ix * g.L64 + sx + 0.5 * side, ly = (double)iy * g.L64 + sy + 0.5 * side,
+                 lz = (double)iz * g.L64 + sz + 0.5 * side;
+    leaf_cen[3 * lid + 0] = lx;
+    leaf_cen[3 * lid + 1] = ly;
+    leaf_cen[3 * lid + 2] = lz;
+    // the node's box (relative to the top-cell centre) moved to the leaf centre, grown
+    // by two more FP32 ulps of the top cell for the rounding of the move
+    const float ox = (float)(((double)ix + 0.5) * g.L64 - lx), oy = (float)(((double)iy + 0.5) * g.L64 - ly),
+                oz = (float)(((double)iz + 0.5) * g.L64 - lz);
+    const float pad = g.L32 * 2.4e-7f;
+    leaf_lo[lid] = make_float4(t.bx0 + ox - pad, t.by0 + oy - pad, t.bz0 + oz - pad, t.hmax);
+    leaf_hi[lid] = make_float4(t.bx1 + ox + pad, t.by1 + oy + pad, t.bz1 + oz + pad, 0.f);
 }
 
 // positions relative to the leaf centre
@@ -969,7 +978,7 @@ static int build_tree_device(sph_ctx *ctx, sph_particles *parts)
     SPH_LAUNCH(ctx, "leaf count");
     k_leaves<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->keys, ctx->keys_alt, n, T.node_at, T.nodes, ctx->d_boxes,
                                                     ctx->n_boxes, T.leaf_of, T.leaf_node, T.node_leaf, T.leaf_rng,
-                                                    T.leaf_cen, T.leaf_h);
+                                                    T.leaf_cen, T.leaf_h, T.leaf_lo, T.leaf_hi);
     SPH_LAUNCH(ctx, "leaves");
     k_leaf_pos<<<nblk(n, 256), 256, 0, ctx->stream>>>(T.leaf_of, T.leaf_cen, parts->x, parts->y, parts->z, parts->h,
                                                       n, ctx->pos4);
@@ -1045,6 +1054,7 @@ int tree_prepare_device(sph_ctx *ctx, uint64_t *sig)
         (rc = grow(ctx, T.nkids, T.cap_nkids, std::max(af, n + 2))) ||
         (rc = grow(ctx, T.leaf_node, T.cap_leaf_node, n + 1)) || (rc = grow(ctx, T.leaf_rng, T.cap_leaf_rng, n + 1)) ||
         (rc = grow(ctx, T.leaf_cen, T.cap_leaf_cen, 3 * n + 3)) || (rc = grow(ctx, T.leaf_h, T.cap_leaf_h, n + 1)) ||
+        (rc = grow(ctx, T.leaf_lo, T.cap_leaf_lo, n + 1)) || (rc = grow(ctx, T.leaf_hi, T.cap_leaf_hi, n + 1)) ||
         (rc = grow(ctx, T.leaf_scale, T.cap_leaf_scale, n + 1)) ||
         (rc = grow(ctx, T.nact_leaf, T.cap_nact_leaf, n + 1)) || (rc = grow(ctx, T.list_off, T.cap_list_off, n + 2)) ||
         (rc = grow(ctx, T.list, T.cap_list, list_need)))
@@ -1058,7 +1068,8 @@ int tree_prepare_device(sph_ctx *ctx, uint64_t *sig)
     // (the sort's ping-pong pair in either order: captures may swap it)
     const void *ptrs[] = {std::min(ctx->keys64, ctx->keys64_alt), std::max(ctx->keys64, ctx->keys64_alt), T.leaf_of, T.node_at, T.tord, T.act_ord, T.top_node,
                           T.nodes, T.node_leaf, T.front, T.front2, T.bounds, T.nkids, T.leaf_node, T.leaf_rng,
-                          T.leaf_cen, T.leaf_h, T.leaf_scale, T.nact_leaf, T.list_off, T.list, T.dc};
+                          T.leaf_cen, T.leaf_h, T.leaf_scale, T.nact_leaf, T.list_off, T.list, T.dc,
+                          T.leaf_lo, T.leaf_hi};
     const int64_t caps[] = {capf, T.dev_cap_nodes, T.cap_list, T.dev_cap_list, ctx->leaf_max};
     uint64_t hsh = 1469598103934665603ull;
     auto mix = [&](uint64_t v) {
@@ -1239,12 +1250,13 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
     if ((rc = grow(ctx, T.leaf_node, T.cap_leaf_node, nl + 1)) || (rc = grow(ctx, T.leaf_rng, T.cap_leaf_rng, nl + 1)) ||
         (rc = grow(ctx, T.leaf_cen, T.cap_leaf_cen, 3 * (int64_t)nl + 3)) ||
         (rc = grow(ctx, T.leaf_h, T.cap_leaf_h, nl + 1)) || (rc = grow(ctx, T.leaf_scale, T.cap_leaf_scale, nl + 1)) ||
+        (rc = grow(ctx, T.leaf_lo, T.cap_leaf_lo, nl + 1)) || (rc = grow(ctx, T.leaf_hi, T.cap_leaf_hi, nl + 1)) ||
         (rc = grow(ctx, T.list_off, T.cap_list_off, nl + 2)))
         return rc;
     {
         k_leaves<<<nblk(n, 256), 256, 0, ctx->stream>>>(ctx->keys, ctx->keys_alt, n, T.node_at, T.nodes, ctx->d_boxes,
                                                         ctx->n_boxes, T.leaf_of, T.leaf_node, T.node_leaf, T.leaf_rng,
-                                                        T.leaf_cen, T.leaf_h);
+                                                        T.leaf_cen, T.leaf_h, T.leaf_lo, T.leaf_hi);
         SPH_LAUNCH(ctx, "leaves");
         k_leaf_pos<<<nblk(n, 256), 256, 0, ctx->stream>>>(T.leaf_of, T.leaf_cen, parts->x, parts->y, parts->z,
                                                           parts->h, n, ctx->pos4);
@@ -1415,7 +1427,7 @@ void free_tree(sph_ctx *ctx)
 {
     AdaptiveTree &T = ctx->tree;
     void *ptrs[] = {ctx->keys64, ctx->keys64_alt, T.leaf_of, T.tord, T.act_ord, T.nact_leaf, T.node_at, T.top_node, T.nodes, T.front, T.front2,
-                    T.bounds, T.nkids, T.node_leaf, T.leaf_node, T.leaf_rng, T.leaf_cen, T.leaf_h,
+                    T.bounds, T.nkids, T.node_leaf, T.leaf_node, T.leaf_rng, T.leaf_cen, T.leaf_h, T.leaf_lo, T.leaf_hi,
                     T.leaf_scale, T.list_off, T.list};
     for (void *p : ptrs) cudaFree(p);
     cudaFree(T.dc);
