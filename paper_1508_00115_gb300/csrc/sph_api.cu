@@ -286,7 +286,7 @@ static int do_force(sph_ctx *ctx, sph_particles *parts)
     if (ctx->n > 0) {
         // uniform grid: reach of every cell for r < max(h_i, h_j) (adaptive cells
         // prune every source with its own h)
-        int rc = ctx->adaptive ? SPH_OK : cell_reach(ctx);
+        int rc = ctx->adaptive ? tree_leaf_hcur(ctx, parts) : cell_reach(ctx);
         if (rc) return rc;
         rc = run_force_pass(ctx, parts);
         if (rc) return rc;
@@ -414,7 +414,7 @@ static int graph_step(sph_ctx *ctx, sph_particles *parts, double dt, int passes)
     SPH_LAUNCH(ctx, "step flags");
     rc = sync_h(ctx, parts);
     if (rc) return rc;
-    rc = ctx->adaptive ? SPH_OK : cell_reach(ctx);  // adaptive cells prune with each source's h
+    rc = ctx->adaptive ? tree_leaf_hcur(ctx, parts) : cell_reach(ctx);  // adaptive: sources' h per leaf
     if (rc) return rc;
     rc = run_force_pass(ctx, parts);
     if (rc) return rc;

@@ -312,6 +312,7 @@ int tree_prepare_device(sph_ctx *ctx, uint64_t *sig);           // sph_tree.cu (
 int tree_read_device(sph_ctx *ctx);                             // sph_tree.cu (after replays)
 int tree_cell_keys_out(sph_ctx *ctx, int32_t *dev_keys);        // sph_tree.cu
 int tree_shrink_count(sph_ctx *ctx, sph_particles *parts);      // sph_tree.cu
+int tree_leaf_hcur(sph_ctx *ctx, sph_particles *parts);         // sph_tree.cu (before a force pass)
 int reset_h_brackets(sph_ctx *ctx);                             // sph_pairs.cu
 // sph_hpredict.cu
 int hp_init(sph_ctx *ctx, uint64_t seed);

@@ -117,8 +117,8 @@ struct ListStream {
     // *nchunk = the warp's largest chunk count of the window.  An entry whose leaf box
     // (moved by the entry's offset) lies beyond reach of the tile's box contributes no
     // sources: the staging would reject every one of them.  Reach: sqrt(reach2) for the
-    // density (targets' h); for the force (FORCE) the larger of the targets' h and
-    // kTreeReach x the leaf's build-time h, which bounds its sources' h.
+    // density (targets' h); for the force (FORCE) the larger of the targets' h and the
+    // leaf's largest current h (set before the force pass).
     template <bool FORCE>
     __device__ __forceinline__ bool next(const float4 *__restrict__ list, const int2 *__restrict__ rng,
                                          const float4 *__restrict__ blo, const float4 *__restrict__ bhi, uint32_t e0,
@@ -144,7 +144,7 @@ struct ListStream {
             const float gz = fmaxf(fmaxf(lo.z + pz - hiz, loz - (hi.z + pz)), 0.f);
             float r2 = reach2;
             if (FORCE) {
-                const float m = fmaxf(H, kTreeReach * lo.w * 1.00001f);
+                const float m = fmaxf(H, lo.w);
                 r2 = m * m * (1.f + kPruneMargin) + 2.f * kBandK * m * (m + L);
             }
             if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > r2 * 1.00001f) c = 0;

@@ -1336,6 +1336,40 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
     return SPH_OK;
 }
 
+// Largest current h of every leaf into leaf_lo[].w (one warp per leaf; device count
+// when nlp is set): the force pass then prunes a leaf's list entry with the largest h
+// its sources have, not with kTreeReach x the build-time value.
+__global__ void k_leaf_hcur(const int2 *__restrict__ rng, int nl_h, const int *__restrict__ nlp,
+                            const float *__restrict__ h, float4 *__restrict__ leaf_lo)
+{
+    const int lane = threadIdx.x & 31;
+    const int nl = nlp ? *nlp : nl_h;
+    for (int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; l < nl; l += (gridDim.x * blockDim.x) >> 5) {
+        const int2 r = rng[l];  // warp-uniform
+        float m = 0.f;
+        for (int p = r.x + lane; p < r.y; p += 32) m = fmaxf(m, h[p]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, o));
+        if (lane == 0) leaf_lo[l].w = m;
+    }
+}
+
+int tree_leaf_hcur(sph_ctx *ctx, sph_particles *parts)
+{
+    AdaptiveTree &T = ctx->tree;
+    if (ctx->n <= 0) return SPH_OK;
+    if (T.device_sized) {
+        if (!T.dc) return SPH_OK;
+        k_leaf_hcur<<<8 * sm_count(ctx), 256, 0, ctx->stream>>>(T.leaf_rng, 0, &T.dc->nl, parts->h, T.leaf_lo);
+    } else {
+        if (T.n_leaves <= 0) return SPH_OK;
+        k_leaf_hcur<<<nblk((int64_t)T.n_leaves * 32, 256), 256, 0, ctx->stream>>>(T.leaf_rng, T.n_leaves, nullptr,
+                                                                                  parts->h, T.leaf_lo);
+    }
+    SPH_LAUNCH(ctx, "leaf current h");
+    return SPH_OK;
+}
+
 // leaves whose largest current h fell below kTreeShrink x their build value
 __global__ void k_leaf_shrink(const int2 *__restrict__ rng, int nl, const float *__restrict__ h,
                               const float *__restrict__ hb, unsigned long long *__restrict__ count)
