@@ -1117,12 +1117,14 @@ static int pair_grid(sph_ctx *ctx, int blocks_per_sm)
 // in their original order (flags, exclusive prefix sum, scatter): which tiles share
 // a warp, and so where a tile's staged batches end, is then the same on every run,
 // and with it every rounding.
+// (*unconv: the targets the last pass left active; none -- a captured step's passes
+// after convergence -- leaves nothing to flag, and the scatter below runs no tile)
 __global__ void k_tile_flags(const int4 *__restrict__ tiles, const int *__restrict__ n_tiles,
                              const uint8_t *__restrict__ active, const int *__restrict__ tord, int64_t cap,
-                             uint32_t *__restrict__ flag)
+                             const unsigned long long *__restrict__ unconv, uint32_t *__restrict__ flag)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= cap) return;
+    if (t >= cap || *unconv == 0ull) return;
     bool keep = false;
     if (t < *n_tiles) {
         const int4 tile = tiles[t];
@@ -1132,11 +1134,16 @@ __global__ void k_tile_flags(const int4 *__restrict__ tiles, const int *__restri
 }
 
 __global__ void k_tile_scatter(const int4 *__restrict__ tiles, const uint32_t *__restrict__ flag,
-                               const uint32_t *__restrict__ pos, int64_t cap, int4 *__restrict__ out,
+                               const uint32_t *__restrict__ pos, int64_t cap,
+                               const unsigned long long *__restrict__ unconv, int4 *__restrict__ out,
                                int *__restrict__ n_out)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= cap) return;
+    if (*unconv == 0ull) {
+        if (t == 0) *n_out = 0;
+        return;
+    }
     if (flag[t]) out[pos[t]] = tiles[t];
     if (t == cap - 1) *n_out = (int)(pos[t] + flag[t]);
 }
@@ -1149,12 +1156,13 @@ int compact_active_tiles(sph_ctx *ctx)
     if (!ctx->adaptive) cap = std::min<int64_t>(cap, ctx->grid.n_cells + ctx->n / ctx->tile_w + 1);
     const unsigned blocks = (unsigned)((cap + 255) / 256);
     k_tile_flags<<<blocks, 256, 0, ctx->stream>>>(ctx->tiles, ctx->n_tiles, ctx->active,
-                                                 ctx->adaptive ? ctx->tree.tord : nullptr, cap, ctx->tile_flag);
+                                                 ctx->adaptive ? ctx->tree.tord : nullptr, cap, ctx->counters + C_UNCONV,
+                                                 ctx->tile_flag);
     SPH_LAUNCH(ctx, "tile flags");
     int rc = exclusive_scan_u32(ctx, ctx->tile_flag, ctx->tile_pos, cap);
     if (rc) return rc;
-    k_tile_scatter<<<blocks, 256, 0, ctx->stream>>>(ctx->tiles, ctx->tile_flag, ctx->tile_pos, cap, ctx->act_tiles,
-                                                   ctx->n_act_tiles);
+    k_tile_scatter<<<blocks, 256, 0, ctx->stream>>>(ctx->tiles, ctx->tile_flag, ctx->tile_pos, cap,
+                                                   ctx->counters + C_UNCONV, ctx->act_tiles, ctx->n_act_tiles);
     SPH_LAUNCH(ctx, "compact tiles");
     return SPH_OK;
 }

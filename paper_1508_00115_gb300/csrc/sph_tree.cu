@@ -517,11 +517,15 @@ __global__ void k_leaf_tiles(const int2 *__restrict__ rng, const int *__restrict
 // Later density passes of adaptive cells: the still-active targets of every leaf,
 // packed to the front of its range in act_ord (in tord order, one warp per leaf),
 // and their tile counts; a tile then holds only targets that need the pass.
+// (*unconv, when given: the targets the last pass left active; none -- a captured
+// step's passes after convergence -- leaves nothing to do, and the tile kernel below
+// runs no tile)
 __global__ void k_leaf_active(const int2 *__restrict__ rng, int nl_h, const int *__restrict__ nlp, int cap,
                               const int *__restrict__ tord, const uint8_t *__restrict__ active, int tw,
-                              int *__restrict__ act_ord, uint32_t *__restrict__ ntiles_leaf,
-                              int *__restrict__ nact_leaf)
+                              const unsigned long long *__restrict__ unconv, int *__restrict__ act_ord,
+                              uint32_t *__restrict__ ntiles_leaf, int *__restrict__ nact_leaf)
 {
+    if (unconv && *unconv == 0ull) return;
     const int lane = threadIdx.x & 31;
     const int nl = nlp ? *nlp : nl_h;
     for (int l = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; l < nl; l += (gridDim.x * blockDim.x) >> 5) {
@@ -550,9 +554,10 @@ __global__ void k_leaf_active_tiles(const int2 *__restrict__ rng, const int *__r
                                     const TreeNode *__restrict__ nodes, int nl_h, const int *__restrict__ nlp, int tw,
                                     const uint32_t *__restrict__ off, const int *__restrict__ nact_leaf,
                                     const BoxDev *__restrict__ bxs, int nb, const int *__restrict__ err,
-                                    int4 *__restrict__ tiles, int *__restrict__ ntiles)
+                                    const unsigned long long *__restrict__ unconv, int4 *__restrict__ tiles,
+                                    int *__restrict__ ntiles)
 {
-    if (err && *err) {  // the lists did not fit: no tile runs
+    if ((err && *err) || (unconv && *unconv == 0ull)) {  // lists that did not fit, or nothing active
         if (blockIdx.x == 0 && threadIdx.x == 0) *ntiles = 0;
         return;
     }
@@ -1422,13 +1427,14 @@ int compact_active_leaf_tiles(sph_ctx *ctx)
         const int64_t capl = std::max<int64_t>(ctx->n, 1) + 1;
         const unsigned gp = (unsigned)(8 * sm_count(ctx));
         k_leaf_active<<<gp, 256, 0, ctx->stream>>>(T.leaf_rng, 0, &T.dc->nl, (int)capl, T.tord, ctx->active,
-                                                   ctx->tile_w, T.act_ord, T.nkids, T.nact_leaf);
+                                                   ctx->tile_w, ctx->counters + C_UNCONV, T.act_ord, T.nkids,
+                                                   T.nact_leaf);
         SPH_LAUNCH(ctx, "leaf active targets");
         int rc = exclusive_scan_u32(ctx, T.nkids, T.nkids, capl);
         if (rc) return rc;
         k_leaf_active_tiles<<<gp, 256, 0, ctx->stream>>>(T.leaf_rng, T.leaf_node, T.nodes, 0, &T.dc->nl, ctx->tile_w,
                                                          T.nkids, T.nact_leaf, ctx->d_boxes, ctx->n_boxes, &T.dc->err,
-                                                         ctx->act_tiles, ctx->n_act_tiles);
+                                                         ctx->counters + C_UNCONV, ctx->act_tiles, ctx->n_act_tiles);
         SPH_LAUNCH(ctx, "leaf active tiles");
         return SPH_OK;
     }
@@ -1443,16 +1449,15 @@ int compact_active_leaf_tiles(sph_ctx *ctx)
         return rc;
     // per-leaf tile counts in nkids (free outside the build; it holds >= n_leaves entries)
     k_leaf_active<<<nblk((int64_t)nl * 32, 256), 256, 0, ctx->stream>>>(T.leaf_rng, nl, nullptr, 0, T.tord,
-                                                                        ctx->active,
-                                                                        ctx->tile_w, T.act_ord, T.nkids,
-                                                                        T.nact_leaf);
+                                                                        ctx->active, ctx->tile_w, nullptr, T.act_ord,
+                                                                        T.nkids, T.nact_leaf);
     SPH_LAUNCH(ctx, "leaf active targets");
     rc = exclusive_scan_u32(ctx, T.nkids, T.nkids, nl);
     if (rc) return rc;
     k_leaf_active_tiles<<<nblk(nl, 256), 256, 0, ctx->stream>>>(T.leaf_rng, T.leaf_node, T.nodes, nl, nullptr,
                                                                ctx->tile_w,
                                                                T.nkids, T.nact_leaf, ctx->d_boxes, ctx->n_boxes,
-                                                               nullptr, ctx->act_tiles, ctx->n_act_tiles);
+                                                               nullptr, nullptr, ctx->act_tiles, ctx->n_act_tiles);
     SPH_LAUNCH(ctx, "leaf active tiles");
     return SPH_OK;
 }
