@@ -513,44 +513,44 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
                         return false;
                     ch = 0;
                 }
-                return true;
-            }
-            while (ch >= nchunk) {
-                if (o >= ncell - 1) return false;
-                ++o;
-                ch = 0;
-                {
-                    int ox, oy, oz;
-                    if (R == 1) {
-                        const int src = o < TW ? o : o - TW;
-                        bs = __shfl_sync(kFull, o < TW ? cs0 : cs1, src, TW);
-                        be = __shfl_sync(kFull, o < TW ? ce0 : ce1, src, TW);
-                        ox = kOrder[o][0];
-                        oy = kOrder[o][1];
-                        oz = kOrder[o][2];
-                    } else {
-                        ox = o < 27 ? kOrder[o][0] : kOuter[o - 27][0];
-                        oy = o < 27 ? kOrder[o][1] : kOuter[o - 27][1];
-                        oz = o < 27 ? kOrder[o][2] : kOuter[o - 27][2];
-                        bs = be = 0;
-                        if (live) {
-                            const int cb = bx.cell_off + (wrapc(iz + oz, nc) * nc + wrapc(iy + oy, nc)) * nc +
-                                           wrapc(ix + ox, nc);
-                            bs = a.cell_start[cb];
-                            be = a.cell_start[cb + 1];
+            } else {
+                while (ch >= nchunk) {
+                    if (o >= ncell - 1) return false;
+                    ++o;
+                    ch = 0;
+                    {
+                        int ox, oy, oz;
+                        if (R == 1) {
+                            const int src = o < TW ? o : o - TW;
+                            bs = __shfl_sync(kFull, o < TW ? cs0 : cs1, src, TW);
+                            be = __shfl_sync(kFull, o < TW ? ce0 : ce1, src, TW);
+                            ox = kOrder[o][0];
+                            oy = kOrder[o][1];
+                            oz = kOrder[o][2];
+                        } else {
+                            ox = o < 27 ? kOrder[o][0] : kOuter[o - 27][0];
+                            oy = o < 27 ? kOrder[o][1] : kOuter[o - 27][1];
+                            oz = o < 27 ? kOrder[o][2] : kOuter[o - 27][2];
+                            bs = be = 0;
+                            if (live) {
+                                const int cb = bx.cell_off + (wrapc(iz + oz, nc) * nc + wrapc(iy + oy, nc)) * nc +
+                                               wrapc(ix + ox, nc);
+                                bs = a.cell_start[cb];
+                                be = a.cell_start[cb + 1];
+                            }
+                        }
+                        shx = (float)ox * L;
+                        shy = (float)oy * L;
+                        shz = (float)oz * L;
+                        sw_d = -1;
+                        if (SWEEP && R == 1 && o > 0) {
+                            sw_d = kOrderAxis[o][0];
+                            sw_sg = (float)kOrderAxis[o][1];
+                            sw_lim = sweep_limit(o, L, rlim, lox, hix, loy, hiy, loz, hiz);
                         }
                     }
-                    shx = (float)ox * L;
-                    shy = (float)oy * L;
-                    shz = (float)oz * L;
-                    sw_d = -1;
-                    if (SWEEP && R == 1 && o > 0) {
-                        sw_d = kOrderAxis[o][0];
-                        sw_sg = (float)kOrderAxis[o][1];
-                        sw_lim = sweep_limit(o, L, rlim, lox, hix, loy, hiy, loz, hiz);
-                    }
+                    nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
                 }
-                nchunk = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
             }
             return true;
         };
