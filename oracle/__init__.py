@@ -16,7 +16,7 @@ hydrodynamics and gravity for cosmological simulations"):
   gradient"; the grad-h factor of the Gadget-2 formulation the paper adopts.
 * :func:`force` -- Sec. 2, Eq. 2 in the Gadget-2 form, with artificial
   viscosity.
-* :func:`step` -- Sec. 2, "particles are marched forward in time": a
+* :func:`step` -- Sec. 2, the time integration of the particles: a
   kick-drift-kick leapfrog (the integrator is not named in the paper).
 
 The arithmetic lives in ``sph_oracle.c`` (plain C, FP64, OpenMP over targets,

@@ -20,11 +20,12 @@
  *   - W(r,h) = h^-3 w(r/h), w = (8/pi){1-6q^2+6q^3 (q<=1/2); 2(1-q)^3 (1/2<q<=1)},
  *     the cubic spline of Monaghan & Lattanzio 1985 (not in the paper).
  *   - Eq. 1 density includes the self term j = i.
- *   - "h such that a given weighted number of particles contributes" (Sec. 2):
+ *   - h is set by a weighted neighbour count (Sec. 2, after Eq. 2):
  *     N_w(h) = (4 pi / 3) sum_j w(r_ij / h) = N_ngb.
- *   - The equation of state "from density and temperature": ideal gas,
+ *   - The equation of state (Sec. 2 gives pressure as a function of density and
+ *     temperature without naming one): ideal gas,
  *     P = (gamma-1) rho u, c = sqrt(gamma (gamma-1) u).
- *   - The "more accurate version used in Gadget 2" (Sec. 2, after Eq. 2): the
+ *   - The force law the paper defers to Gadget-2 (Sec. 2, after Eq. 2): the
  *     grad-h conservative equations of motion of Springel & Hernquist 2002 /
  *     Springel 2005, with the signal-velocity artificial viscosity
  *     (Monaghan 1997) and the Balsara 1995 switch.
@@ -42,7 +43,7 @@
 #define ORC_SIGMA (8.0 / ORC_PI) /* 3-D cubic-spline normalisation */
 #define ORC_FOUR_PI_3 (4.0 * ORC_PI / 3.0)
 
-/* ---- kernel shape (Sec. 2: "bell-shaped kernel with compact support") ---- */
+/* ---- kernel shape (Sec. 2: a bell-shaped kernel that vanishes beyond h) ---- */
 
 double orc_w(double q)
 {
@@ -67,7 +68,7 @@ double orc_dw(double q)
     return 0.0;
 }
 
-/* ---- periodic box (Sec. 2: "the simulated volume is periodically replicated") ---- */
+/* ---- periodic box (Sec. 2: the volume repeats periodically in every axis) ---- */
 
 /* Wrap into [0, box): positions already inside are returned unchanged; others are
  * shifted by box*floor(x/box), then corrected by one box if rounding left them
@@ -293,8 +294,8 @@ int orc_solve_h(int64_t n, double box, const double *x, const double *y, const d
 }
 
 /*
- * Quantities between the two passes ("we need to evaluate the density for each
- * particle before we can compute the pressure gradient", Sec. 2):
+ * Quantities between the two passes (Sec. 2: every density is needed before any
+ * pressure gradient can be formed):
  *   P = (gamma-1) rho u, c = sqrt(gamma (gamma-1) u),
  *   f = [1 + h/(3 rho) drho/dh]^-1   (grad-h term, Springel & Hernquist 2002),
  *   B = |div v| / (|div v| + |curl v| + 1e-4 c/h)  (Balsara 1995; 0 if the
