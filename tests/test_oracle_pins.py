@@ -167,6 +167,24 @@ def test_smoothing_length_root_unique(random_system):
     assert np.all(lo < 48.0) and np.all(hi > 48.0)
 
 
+def test_h_derivatives_match_finite_differences(random_system):
+    """dN_w/dh (the Newton slope) and drho/dh (the grad-h term) are the h-derivatives
+    of the sums themselves: central differences of N_w(h) and rho(h) at each
+    particle's h agree.  The spline is C2, so neighbours entering or leaving the
+    support within the step change nothing at this order."""
+    s, r = random_system
+    h = r["h"]
+    eps = 1e-5
+    d0 = oracle.density_at_h(s, h)
+    lo = oracle.density_at_h(s, h * (1 - eps))
+    hi = oracle.density_at_h(s, h * (1 + eps))
+    dh = 2 * eps * h
+    fd_nw = (hi["nw"] - lo["nw"]) / dh
+    fd_rho = (hi["rho"] - lo["rho"]) / dh
+    assert np.all(np.abs(fd_nw - d0["dnw_dh"]) <= 1e-7 * np.abs(d0["dnw_dh"]))
+    assert np.all(np.abs(fd_rho - d0["drho_dh"]) <= 1e-6 * np.abs(d0["rho"] / h))
+
+
 def test_translation_and_permutation_invariance(random_system):
     s, r = random_system
     rng = np.random.default_rng(5)
