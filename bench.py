@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -45,6 +46,7 @@ UNIT = "particles/s"
 # Kahan compensation included; rejected distance tests are NOT counted).
 FLOP_DENSITY_PAIR = 69
 FLOP_FORCE_PAIR = 86
+CPU_SAMPLE_S = 10.0  # least CPU time of the oracle sample behind cpu_baseline
 L2_BYTES = 129e6
 
 
@@ -216,12 +218,25 @@ def boxes_workload(n_boxes: int = 512, seed: int = 91):
 
 
 def oracle_sample(d: dict, n_force: int, seed: int = 5, label: str = "Sedov 128^3",
-                  local_radius: bool = False) -> dict:
+                  local_radius: bool = False, min_seconds: float = 0.0) -> dict:
     """Time the FP64 oracle on a bounded sample of the workload: n_force random
     targets get the full path (h solve + density for them and for every particle
     within 1.5 h of them, then the force sum), each brute-forced against all N.
     particles/s = 1 / (T_density/S_density + T_force/S_force).  local_radius: the
-    neighbourhood of a target is 2 x its own h (h spans decades), else 1.5 x max h."""
+    neighbourhood of a target is 2 x its own h (h spans decades), else 1.5 x max h.
+    min_seconds: if the sample took less CPU time than this, it is taken once more
+    with n_force scaled up to about that time (at most every particle), and that
+    second sample is the one reported."""
+    info = _oracle_sample_once(d, n_force, seed, label, local_radius)
+    n = d["x"].size
+    if info["seconds"] < min_seconds and n_force < n:
+        grow = 1.1 * min_seconds / max(info["seconds"], 1e-3)
+        info = _oracle_sample_once(d, min(n, int(math.ceil(n_force * grow))), seed, label,
+                                   local_radius)
+    return info
+
+
+def _oracle_sample_once(d: dict, n_force: int, seed: int, label: str, local_radius: bool) -> dict:
     import oracle
     n = d["x"].size
     s = oracle.State(**{k: d[k] for k in ("x", "y", "z", "vx", "vy", "vz", "m", "u", "h")})
@@ -264,7 +279,7 @@ def run_reference(args):
     vals = []
     info = None
     for k in range(args.warmup + args.steps):
-        info = oracle_sample(d, n_force=8, seed=100 + k)
+        info = oracle_sample(d, n_force=args.cpu_force_targets, seed=100 + k)
         if k >= args.warmup:
             vals.append(info["value"])
     v = float(np.median(vals)) if vals else 0.0
@@ -404,7 +419,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(d, n_force=args.cpu_force_targets)
+        cpu = oracle_sample(d, n_force=args.cpu_force_targets, min_seconds=CPU_SAMPLE_S)
         cpu.pop("seconds", None)
 
     work_mb = n * (6 * 8 + 14 * 4 + 4 + 3 * 16 + 4 + 8 + 8 + 16) / 1e6
@@ -626,7 +641,8 @@ def run_adaptive(args):
             lab = f"largest box (N={offs[b + 1] - offs[b]}) of the batched set"
         else:
             lab = label
-        cpu = oracle_sample(g, n_force=args.cpu_force_targets // 3, label=lab, local_radius=True)
+        cpu = oracle_sample(g, n_force=args.cpu_force_targets // 3, label=lab, local_radius=True,
+                            min_seconds=CPU_SAMPLE_S)
         cpu.pop("seconds", None)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
