@@ -56,12 +56,14 @@ typedef struct sph_ctx sph_ctx; /* opaque, library-owned */
 /* Flags for sph_params.flags */
 #define SPH_FLAG_TIMING 1u /* record CUDA events around the pair kernels */
 #define SPH_FLAG_NGB_HASH 2u /* density pass also writes a neighbour-set hash */
-#define SPH_FLAG_AUTOTUNE 4u /* before the first density pass, time one pass for each
-                                candidate schedule (tile width 16/32 x cell factor
-                                1.05/1.25/1.5; with SPH_FLAG_ADAPTIVE: tile width x
-                                leaf size 32/64/128) on the current particles and keep
-                                the fastest; overrides tile_width and cell_factor
-                                (leaf_max) */
+#define SPH_FLAG_AUTOTUNE 4u /* before the first density pass, time for each candidate
+                                schedule (tile width 16/32 x cell factor 1.05/1.25/1.5;
+                                with SPH_FLAG_ADAPTIVE: tile width x leaf size
+                                32/64/128) the cell build, one density pass and one
+                                force pass on the current particles and keep the
+                                fastest; overrides tile_width and cell_factor
+                                (leaf_max).  That first sph_density call also writes
+                                the force outputs (ax..vsig) of the probes. */
 #define SPH_FLAG_ADAPTIVE 8u /* adaptive cells (Sec. 3.1): the uniform grid becomes the
                                 top level of an octree refined while a node holds more
                                 than leaf_max particles; leaves are the work items,
@@ -227,7 +229,7 @@ int sph_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out);
  * Writes ax, ay, az, dudt, vsig.  Requires sph_density on the current state. */
 int sph_force(sph_ctx *ctx, sph_particles *parts);
 
-/* One kick-drift-kick step (Sec. 2 "marched forward in time"): kick v, u by dt/2
+/* One kick-drift-kick step (the time integration of Sec. 2): kick v, u by dt/2
  * with the current a, du/dt; drift x by dt (FP64) and wrap; rebuild cells; density
  * and force on v, u predicted to the end of the step; kick by dt/2 with the new
  * rates; u is floored at 0.  If no force pass ran on the current state, one runs
