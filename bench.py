@@ -466,6 +466,102 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------- individual time-steps
+
+
+def run_bins(args):
+    """Individual time-steps on the Sedov-Taylor workload: from one state, advance by
+    dt_max = 2^L x the global CFL step once with sph_step_bins (each particle on its
+    own power-of-two step) and once with global CFL steps (sph_step, the last one cut
+    to land on dt_max); report both times, the particle updates each needed, and
+    their total energies."""
+    import torch
+    from paper_1508_00115_gb300 import binding
+
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    binding.lib()
+    d = workload()
+    n = int(d["x"].size)
+    stream = torch.cuda.Stream()
+    sched = _schedule(args, binding)
+    ctx = binding.Context(n, device=local, stream=stream.cuda_stream, flags=sched.pop("flags"), **sched)
+    parts = binding.Particles(d)
+    cons = None
+    for _ in range(args.warmup):
+        _, cons = ctx.step(parts)
+    torch.cuda.synchronize()
+    dt0 = cons["dt_next"]
+    levels = args.levels
+    dt_max = dt0 * 2.0 ** levels
+    snap = {k: v.clone() for k, v in parts.t.items()}
+
+    def restore():
+        for k, v in snap.items():
+            parts.t[k].copy_(v)
+        torch.cuda.synchronize()
+
+    def timed(fn, tag):
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(tag)
+        e0.record(stream)
+        res = fn()
+        e1.record(stream)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        return _max_over_ranks(e0.elapsed_time(e1), dist), res
+
+    def global_steps():
+        t, k, c, dt = 0.0, 0, None, dt0
+        while t < dt_max * (1 - 1e-12):
+            dt = min(dt, dt_max - t)
+            used, c = ctx.step(parts, dt)
+            t += used
+            k += 1
+            dt = c["dt_next"]
+        return k, c
+
+    def binned():
+        return ctx.step_bins(parts, dt_max, levels)
+
+    binned()  # untimed first call (allocations)
+    restore()
+    ms_bins, (cons_b, st_b) = timed(binned, "bin_steps")
+    restore()
+    ms_glob, (n_glob, cons_g) = timed(global_steps, "global_steps")
+    e_start = float(np.sum(d["m"] * d["u"]))
+    out = {"metric": METRIC, "value": _throughput(world, n, n_glob, ms_bins / 1e3), "unit": UNIT,
+           "n_gpus": world, "steps": 1, "warmup": args.warmup, "ms_per_step": ms_bins,
+           "higher_is_better": True,
+           "path": (f"individual time-steps (sph_step_bins, {levels} levels) over dt_max = 2^{levels} x "
+                    "the global CFL step; value = particles x global steps covered / time"),
+           "global": {"value": _throughput(world, n, n_glob, ms_glob / 1e3), "unit": UNIT, "ms": ms_glob,
+                      "steps": n_glob, "updates": n_glob * n,
+                      "path": "sph_step at the global CFL dt to the same time"},
+           "speedup": ms_glob / ms_bins,
+           "bins": {"levels": levels, "dt_max": dt_max, "substeps": st_b["substeps"],
+                    "updates": st_b["updates"], "cfl_over": st_b["cfl_over"],
+                    "bin_count": [int(v) for v in st_b["bin_count"][:levels + 1]]},
+           "energy": {"start": e_start, "bins": cons_b["e_tot"], "global": cons_g["e_tot"]},
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "sedov-taylor 128^3 jittered lattice, individual time-steps",
+                      "n_particles": n, "n_ngb": 48, "levels": levels,
+                      "parallelism": f"replicas x{world}"}}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 # ------------------------------------------------- adaptive-cell workloads
 
 
@@ -704,9 +800,11 @@ def main():
     ap.add_argument("--cpu-force-targets", type=int, default=48)
     ap.add_argument("--tile-width", type=int, default=0, help="16 or 32 (0: autotuned)")
     ap.add_argument("--cell-factor", type=float, default=0.0, help=">= 1 (0: autotuned)")
-    ap.add_argument("--workload", choices=["sedov", "clustered", "boxes"], default="sedov",
+    ap.add_argument("--workload", choices=["sedov", "clustered", "boxes", "sedov-bins"], default="sedov",
                     help="sedov: Sedov-Taylor 128^3 (the headline); clustered: clustered halo field on "
-                         "adaptive cells; boxes: batched uneven boxes on adaptive cells")
+                         "adaptive cells; boxes: batched uneven boxes on adaptive cells; sedov-bins: "
+                         "individual time-steps against global steps on the Sedov workload")
+    ap.add_argument("--levels", type=int, default=8, help="sedov-bins: time-bin levels")
     ap.add_argument("--side", type=int, default=256, help="clustered: particles per side")
     ap.add_argument("--n-boxes", type=int, default=512, help="boxes: number of boxes")
     ap.add_argument("--leaf-max", type=int, default=0, help="adaptive: leaf size (0: autotuned)")
@@ -719,6 +817,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "sedov-bins":
+        run_bins(args)
     elif args.workload != "sedov":
         run_adaptive(args)
     else:

@@ -156,6 +156,16 @@ typedef struct {
     int64_t u_floors;   /* kicks that drove u below 0 (clamped to 0) */
 } sph_conserved;
 
+/* Individual time-steps (sph_step_bins): deepest bin, and what one call reports. */
+#define SPH_MAX_BINS 24
+typedef struct {
+    int64_t substeps;                    /* step ends visited (drift + update events)   */
+    int64_t updates;                     /* particle updates: sum of active counts      */
+    int64_t cfl_over;                    /* steps whose CFL step was below the smallest  */
+                                         /* bin's, taken at the smallest bin anyway     */
+    int64_t bin_count[SPH_MAX_BINS + 1]; /* particles per bin, for their last step      */
+} sph_bin_stats;
+
 /* Counters since the last sph_reset_stats (sph_get_stats synchronises the stream). */
 typedef struct {
     int32_t nc;                /* cells per side of the grid of box 0                */
@@ -262,6 +272,31 @@ int sph_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_used, sph
  * the stream at entry (max h, first dt) and at the end. */
 int sph_steps(sph_ctx *ctx, sph_particles *parts, int32_t n_steps, double dt, double *dt_last,
               sph_conserved *out);
+
+/* Individual time-steps: advances by dt_max with each particle on its own step
+ * dt_max / 2^b, b in [0, n_bins] (0 <= n_bins <= SPH_MAX_BINS).  The paper is silent
+ * on time-stepping; this is the power-of-two scheme of the Gadget-2 line its force
+ * law comes from, each particle following the leapfrog of sph_step.  Time runs on
+ * a grid of dt_max / 2^n_bins.  A particle starting a step at time s takes the
+ * largest dt_max / 2^b not above its CFL step cfl h / vsig (b = n_bins, counted in
+ * cfl_over, if even that is above it), made smaller until s is a multiple of it.
+ * All particles open a step at 0 (half kick); at each later step end every particle
+ * drifts, the cells are rebuilt, and the particles whose step ends there get the
+ * density (h iteration) and force against all particles -- every particle's v and
+ * u predicted to that time from the middle of its own step, v_half + a (t - t_mid),
+ * the others keeping h, rho, P, c, f, Balsara B, a, du/dt and vsig from their last
+ * update -- then their closing half kick, a new bin and, before dt_max, their
+ * next opening half kick.  On return every particle is synchronised at dt_max with
+ * current a, du/dt, vsig (n_bins = 0 is exactly sph_step with dt = dt_max).  Runs
+ * a hydro pass first if the current state has none (or SPH_FLAG_AUTOTUNE has not
+ * tuned yet).  *out and *stats may be NULL.  Errors as sph_step; on an error the
+ * particles are left part-way through the interval.  Host reads at every step end. */
+int sph_step_bins(sph_ctx *ctx, sph_particles *parts, double dt_max, int32_t n_bins, sph_conserved *out,
+                  sph_bin_stats *stats);
+
+/* Bin of every slot after the last sph_step_bins (device, int8, length n, the
+ * current slot order). */
+int sph_get_bins(sph_ctx *ctx, int8_t *dev_bins);
 
 /* sph_step on HOST arrays (pinned memory recommended): copies x..h, vx..vz, m, u,
  * ax, ay, az, dudt, vsig to library-owned device buffers, steps, and copies every

@@ -18,6 +18,9 @@ hydrodynamics and gravity for cosmological simulations"):
   viscosity.
 * :func:`step` -- Sec. 2, the time integration of the particles: a
   kick-drift-kick leapfrog (the integrator is not named in the paper).
+* :func:`time_bins`, :func:`step_bins` -- the same leapfrog with individual,
+  power-of-two time-steps (the Gadget-2 scheme the paper's force law comes from;
+  the paper itself is silent on time-stepping).
 
 The arithmetic lives in ``sph_oracle.c`` (plain C, FP64, OpenMP over targets,
 ``-ffp-contract=off``); this file only marshals arrays and composes the step.
@@ -329,3 +332,120 @@ def step(s: State, acc: dict, dt: float, p: Params = Params()) -> tuple[State, d
     floors += int(np.sum(n2.u < 0))
     n2.u = np.maximum(n2.u, 0.0)
     return n2, res, floors
+
+
+def time_bins(h, vsig, dt_max: float, n_bins: int, s_now: int, cfl: float = 0.1):
+    """Time bins of particles that start a step at integer time s_now (unit
+    dt_max / 2^n_bins).  Bin b means a step of dt_max / 2^b: the largest such step not
+    above the particle's CFL step cfl h / vsig (bin n_bins if even that one is
+    above it; those are counted), then made smaller until s_now is a multiple of
+    the step's length, so that every step starts and ends on its own grid.
+    Returns (bins, number of particles whose CFL step is below the smallest bin,
+    margin): margin is the smallest distance, in log2, of a CFL step from a bin
+    boundary dt_max / 2^k inside the range of bins (inf if none), i.e. how far the
+    decisions are from flipping."""
+    h = _f64(h)
+    v = _f64(vsig)
+    dtc = np.full(h.size, np.inf)
+    ok = v > 0
+    dtc[ok] = cfl * h[ok] / v[ok]
+    b = np.full(h.size, n_bins, dtype=np.int64)
+    for k in range(n_bins, -1, -1):  # ends at the smallest k that fits
+        b = np.where(dt_max * 2.0 ** (-k) <= dtc, k, b)
+    over = int(np.sum(dt_max * 2.0 ** (-n_bins) > dtc))
+    lg = np.log2(dt_max / dtc[ok]) if ok.any() else np.zeros(0)
+    lg = lg[(lg > -1.0) & (lg < n_bins + 1.0)]
+    margin = float(np.min(np.abs(lg - np.rint(lg)))) if lg.size else float("inf")
+    for i in range(h.size):
+        while b[i] < n_bins and s_now % (1 << (n_bins - b[i])) != 0:
+            b[i] += 1
+    return b, over, margin
+
+
+def step_bins(s: State, acc: dict, dt_max: float, n_bins: int,
+              p: Params = Params()) -> tuple[State, dict, dict]:
+    """Advance by dt_max with individual time-steps: the kick-drift-kick leapfrog of
+    :func:`step` per particle, each on its own power-of-two step (:func:`time_bins`).
+
+    ``acc`` is the hydro result of a synchronised state (keys a, dudt, vsig, h, rho,
+    P, c, f, B).  Time runs on an integer grid of dt_max / 2^n_bins.  At the start
+    every particle takes its opening half kick.  Then, from one step end to the
+    next: all particles drift; the particles whose step ends now are active; the
+    density (with the h solve) and the force are evaluated for the active ones only,
+    against every particle at its drifted position, with velocities and internal
+    energies predicted to the current time (v_half + a (t - t_mid), t_mid the middle
+    of the particle's own step), while the inactive particles keep h, rho, P, c, f
+    and B from their last evaluation; the active ones take their closing half
+    kick, a new bin, and (before dt_max is reached) the opening half kick of their
+    next step.  At dt_max every particle is synchronised again.
+
+    Returns (state, hydro dict of the final synchronised state, stats with
+    floors, substeps, active (particle updates), over (CFL steps below the
+    smallest bin), margin (the closest any bin decision came to a boundary, in
+    log2) and bins (the bins of the last steps))."""
+    B = int(n_bins)
+    unit = dt_max / 2.0 ** B
+    end = 1 << B
+    n2 = s.copy()
+    st = {k: np.array(acc[k], dtype=np.float64) for k in ("h", "rho", "P", "c", "f", "B", "dudt", "vsig")}
+    st["a"] = np.array(acc["a"], dtype=np.float64)
+    n2.h = st["h"].copy()
+    floors = 0
+
+    def kick(idx, bins):
+        nonlocal floors
+        half = 0.5 * ((1 << (B - bins[idx])).astype(np.float64) * unit)
+        n2.vx[idx] = n2.vx[idx] + st["a"][idx, 0] * half
+        n2.vy[idx] = n2.vy[idx] + st["a"][idx, 1] * half
+        n2.vz[idx] = n2.vz[idx] + st["a"][idx, 2] * half
+        u = n2.u[idx] + st["dudt"][idx] * half
+        floors += int(np.sum(u < 0))
+        n2.u[idx] = np.maximum(u, 0.0)
+
+    everyone = np.arange(s.n)
+    bins, over, margin = time_bins(st["h"], st["vsig"], dt_max, B, 0, p.cfl)
+    kick(everyone, bins)
+    S = 0
+    substeps = 0
+    updates = 0
+    while S < end:
+        dmin = 1 << (B - int(bins.max()))
+        S_next = (S // dmin + 1) * dmin
+        dt = (S_next - S) * unit
+        n2.x = wrap(n2.x + n2.vx * dt, s.box)
+        n2.y = wrap(n2.y + n2.vy * dt, s.box)
+        n2.z = wrap(n2.z + n2.vz * dt, s.box)
+        S = S_next
+        substeps += 1
+        D = np.left_shift(1, B - bins)
+        act = (S % D) == 0
+        idx = np.nonzero(act)[0]
+        updates += int(idx.size)
+        s0 = np.where(act, S - D, S - S % D)
+        tau = 0.5 * ((2 * (S - s0) - D).astype(np.float64) * unit)
+        pred = n2.copy()
+        pred.vx = n2.vx + st["a"][:, 0] * tau
+        pred.vy = n2.vy + st["a"][:, 1] * tau
+        pred.vz = n2.vz + st["a"][:, 2] * tau
+        pred.u = np.maximum(n2.u + st["dudt"] * tau, 0.0)
+        d = solve_h(pred, h_guess=st["h"], n_ngb=p.n_ngb, tol=p.h_tol, targets=idx)
+        g = ghost(d["rho"], d["drho_dh"], d["divv"], d["curl_abs"], pred.u[idx], d["h"], p.gamma,
+                  p.use_balsara)
+        st["h"][idx] = d["h"]
+        st["rho"][idx] = d["rho"]
+        for k in ("P", "c", "f", "B"):
+            st[k][idx] = g[k]
+        fr = force(pred, st["h"], st["rho"], st["P"], st["c"], st["f"], st["B"], p.alpha, targets=idx)
+        st["a"][idx] = fr["a"]
+        st["dudt"][idx] = fr["dudt"]
+        st["vsig"][idx] = fr["vsig"]
+        n2.h[idx] = d["h"]
+        kick(idx, bins)  # closing half kick on the step that ends now
+        nb, o, mg = time_bins(st["h"][idx], st["vsig"][idx], dt_max, B, S, p.cfl)
+        over += o
+        margin = min(margin, mg)
+        bins[idx] = nb
+        if S < end:
+            kick(idx, bins)  # opening half kick of the next step
+    stats = dict(floors=floors, substeps=substeps, active=updates, over=over, margin=margin, bins=bins)
+    return n2, st, stats

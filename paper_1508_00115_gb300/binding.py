@@ -78,6 +78,14 @@ class sph_conserved(ctypes.Structure):
                 ("u_floors", ctypes.c_int64)]
 
 
+SPH_MAX_BINS = 24
+
+
+class sph_bin_stats(ctypes.Structure):
+    _fields_ = [("substeps", ctypes.c_int64), ("updates", ctypes.c_int64), ("cfl_over", ctypes.c_int64),
+                ("bin_count", ctypes.c_int64 * (SPH_MAX_BINS + 1))]
+
+
 class sph_stats(ctypes.Structure):
     _fields_ = [("nc", ctypes.c_int32), ("rebuilds", ctypes.c_int32), ("n_cells", ctypes.c_int64),
                 ("cell_size", ctypes.c_double), ("density_passes", ctypes.c_int64),
@@ -123,6 +131,9 @@ def lib(build_if_missing: bool = True):
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(sph_conserved)]),
             "sph_steps": (C, [P, ctypes.POINTER(sph_particles), ctypes.c_int32, ctypes.c_double,
                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(sph_conserved)]),
+            "sph_step_bins": (C, [P, ctypes.POINTER(sph_particles), ctypes.c_double, ctypes.c_int32,
+                                  ctypes.POINTER(sph_conserved), ctypes.POINTER(sph_bin_stats)]),
+            "sph_get_bins": (C, [P, P]),
             "sph_get_permutation": (C, [P, P]),
             "sph_reset_ids": (C, [P]),
             "sph_get_cell_keys": (C, [P, P]),
@@ -221,6 +232,16 @@ def sph_step_host(ctx, parts: sph_particles, dt: float = 0.0):
     _check(lib().sph_step_host(ctx, ctypes.byref(parts), float(dt), ctypes.byref(used),
                                ctypes.byref(cons)), ctx)
     return float(used.value), _cons_dict(cons)
+
+
+def sph_step_bins(ctx, parts: sph_particles, dt_max: float, n_bins: int):
+    cons = sph_conserved()
+    bs = sph_bin_stats()
+    _check(lib().sph_step_bins(ctx, ctypes.byref(parts), float(dt_max), int(n_bins), ctypes.byref(cons),
+                               ctypes.byref(bs)), ctx)
+    stats = dict(substeps=int(bs.substeps), updates=int(bs.updates), cfl_over=int(bs.cfl_over),
+                 bin_count=np.array(list(bs.bin_count), dtype=np.int64))
+    return _cons_dict(cons), stats
 
 
 def _cons_dict(c: sph_conserved) -> dict:
@@ -373,6 +394,18 @@ class Context:
 
     def steps(self, parts: Particles, n_steps: int, dt: float = 0.0, allow=()):
         return sph_steps(self.h, parts.struct(), n_steps, dt, allow)
+
+    def step_bins(self, parts: Particles, dt_max: float, n_bins: int):
+        """Individual time-steps over dt_max: (conserved dict, bin stats dict)."""
+        return sph_step_bins(self.h, parts.struct(), dt_max, n_bins)
+
+    def bins(self) -> np.ndarray:
+        import torch
+        n = int(self.params.n)
+        t = torch.empty(max(n, 1), dtype=torch.int8, device="cuda")
+        _check(lib().sph_get_bins(self.h, ctypes.c_void_p(t.data_ptr())), self.h)
+        torch.cuda.synchronize()
+        return t[:n].cpu().numpy()
 
     def step_host(self, parts: Particles, dt: float = 0.0):
         return sph_step_host(self.h, parts.struct(), dt)

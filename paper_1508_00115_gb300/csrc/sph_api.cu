@@ -108,6 +108,31 @@ static int alloc_particles(sph_ctx *c, int64_t cap)
     return SPH_OK;
 }
 
+// individual time-steps: per-particle state of sph_step_bins, allocated on first use
+static void free_bins(sph_ctx *c)
+{
+    void *ptrs[] = {c->bins, c->bins_tmp, c->bin_active, c->bin_active_tmp, c->bin_s32};
+    for (void *p : ptrs) cudaFree(p);
+    c->bins = c->bins_tmp = nullptr;
+    c->bin_active = c->bin_active_tmp = nullptr;
+    c->bin_s32 = nullptr;
+    c->bin_cap = 0;
+}
+
+static int alloc_bins(sph_ctx *c)
+{
+    if (c->bin_cap >= c->cap && c->bins) return SPH_OK;
+    free_bins(c);
+    const int64_t cap = std::max<int64_t>(c->cap, 1);
+    SPH_CUDA(c, cudaMalloc(&c->bins, cap));
+    SPH_CUDA(c, cudaMalloc(&c->bins_tmp, cap));
+    SPH_CUDA(c, cudaMalloc(&c->bin_active, cap));
+    SPH_CUDA(c, cudaMalloc(&c->bin_active_tmp, cap));
+    SPH_CUDA(c, cudaMalloc(&c->bin_s32, sizeof(float) * 5 * cap));
+    c->bin_cap = cap;
+    return SPH_OK;
+}
+
 static bool parts_ok(const sph_particles *p)
 {
     const void *a[] = {p->x,   p->y, p->z, p->vx,   p->vy,    p->vz, p->m,  p->u,  p->h,  p->rho, p->P,
@@ -218,6 +243,18 @@ static int autotune(sph_ctx *ctx, sph_particles *parts)
 // long); each restarts the h iteration with a fresh pass budget
 constexpr int kMaxRebins = 32;
 
+// Density targets of a call: every particle, or inside sph_step_bins the particles
+// whose step ends now.
+static int init_active(sph_ctx *ctx)
+{
+    const int64_t n = ctx->n;
+    if (ctx->bin_mode)
+        SPH_CUDA(ctx, cudaMemcpyAsync(ctx->active, ctx->bin_active, n, cudaMemcpyDeviceToDevice, ctx->stream));
+    else
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, n, ctx->stream));
+    return SPH_OK;
+}
+
 static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
 {
     if (!ctx->built) return fail(ctx, SPH_ERR_STATE, "sph_density needs sph_build_cells on the current positions");
@@ -227,12 +264,20 @@ static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
     int rebinned = 0;  // re-binnings in this call
     unsigned long long unconv = 0;
     if (n > 0 && (ctx->p.flags & SPH_FLAG_AUTOTUNE) && !ctx->tuned) {
-        int rc = autotune(ctx, parts);
+        // the schedules are timed at converged smoothing lengths, where the passes of
+        // later steps run (an initial guess far from the root favoured schedules that
+        // are slower in every later step): converge h with the current schedule first
+        ctx->tuned = true;  // the inner call does not tune
+        int rc = do_density(ctx, parts, nullptr);
+        ctx->tuned = false;
+        if (rc && rc != SPH_ERR_NOT_CONVERGED) return rc;
+        rc = autotune(ctx, parts);
         if (rc) return rc;
     }
     if (n > 0) {
-        SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, n, ctx->stream));
-        int rc = reset_h_brackets(ctx);
+        int rc = init_active(ctx);
+        if (rc) return rc;
+        rc = reset_h_brackets(ctx);
         if (rc) return rc;
         bool all_tiles = true;  // first pass (and after a rebuild): every tile
         for (;;) {
@@ -269,7 +314,8 @@ static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
                 ctx->st.rebuilds++;
                 ++rebinned;
                 since = 0;
-                SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, n, ctx->stream));
+                rc = init_active(ctx);
+                if (rc) return rc;
                 rc = reset_h_brackets(ctx);  // slots were permuted
                 if (rc) return rc;
                 all_tiles = true;
@@ -371,6 +417,110 @@ static int do_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_use
     rc = kick(ctx, parts);
     if (rc) return rc;
     if (dt_used) *dt_used = dt;
+    if (out) {
+        rc = conserved_device(ctx, parts);
+        if (rc) return rc;
+        rc = conserved_read(ctx, out);
+        if (rc) return rc;
+        rc = cfl_dt(ctx, parts, &out->dt_next);
+        if (rc) return rc;
+    }
+    return SPH_OK;
+}
+
+// ------------------------------------------------------- individual time-steps
+
+// Advance by dt_max with each particle on its own power-of-two step (the leapfrog of
+// do_step per particle).  Time runs on an integer grid of unit dt_max / 2^L.  All
+// particles open a step at 0; then, from one step end to the next: every particle
+// drifts; the cells are built (the build also carries the bins and the kept density
+// outputs along, and predicts every particle's v and u to the current time); the
+// particles whose step ends now get density (with the h iteration) and force
+// against all particles, take their closing half kick, a new bin, and (before
+// dt_max) the opening half kick of their next step.  The others keep h, rho, P, c,
+// f, B, a, du/dt and vsig from their last update.  At dt_max every particle is
+// synchronised again, with current a and du/dt.
+static int do_step_bins(sph_ctx *ctx, sph_particles *parts, double dt_max, int levels, sph_conserved *out,
+                        sph_bin_stats *bs)
+{
+    int rc;
+    ctx->predict = false;
+    // a synchronised start with current accelerations, and the schedule tuned before
+    // (the tuner's probe passes would overwrite what inactive particles keep)
+    if (!ctx->hydro_valid || ((ctx->p.flags & SPH_FLAG_AUTOTUNE) && !ctx->tuned)) {
+        rc = hydro(ctx, parts);
+        if (rc) return rc;
+    }
+    rc = alloc_bins(ctx);
+    if (rc) return rc;
+    const int64_t end = (int64_t)1 << levels;
+    const double unit = ldexp(dt_max, -levels);
+    ctx->bin_levels = levels;
+    ctx->bin_unit = unit;
+    ctx->bin_now = 0;
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_FLOORS, 0, sizeof(unsigned long long), ctx->stream));
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_BINOVER, 0, sizeof(unsigned long long), ctx->stream));
+    int64_t substeps = 0, updates = 0;
+    ctx->bin_mode = true;
+    auto body = [&]() -> int {
+        int r = bin_assign(ctx, parts, true, dt_max);
+        if (r) return r;
+        r = bin_kick(ctx, parts, true);  // every particle opens a step
+        if (r) return r;
+        int64_t s = 0;
+        while (s < end) {
+            int deepest = 0;
+            unsigned long long over = 0;
+            r = bin_max_read(ctx, &deepest, &over);
+            if (r) return r;
+            const int64_t dmin = (int64_t)1 << (levels - deepest);
+            const int64_t s_next = (s / dmin + 1) * dmin;
+            r = set_dt(ctx, (double)(s_next - s) * unit);
+            if (r) return r;
+            r = drift(ctx, parts);
+            if (r) return r;
+            s = s_next;
+            ctx->bin_now = s;
+            unsigned long long n_act = 0;
+            r = bin_active(ctx, &n_act);
+            if (r) return r;
+            ++substeps;
+            updates += (int64_t)n_act;
+            r = do_build(ctx, parts);
+            if (r) return r;
+            r = do_density(ctx, parts, nullptr);
+            if (r) return r;
+            r = do_force(ctx, parts);
+            if (r) return r;
+            r = bin_kick(ctx, parts, false);  // closing half kick of the steps that end now
+            if (r) return r;
+            r = bin_assign(ctx, parts, false, dt_max);
+            if (r) return r;
+            if (s < end) {
+                r = bin_kick(ctx, parts, false);  // opening half kick of their next steps
+                if (r) return r;
+            }
+        }
+        return SPH_OK;
+    };
+    rc = body();
+    ctx->bin_mode = false;
+    if (rc) return rc;
+    ctx->hydro_valid = true;  // all particles were active at dt_max
+    if (bs) {
+        memset(bs, 0, sizeof *bs);
+        bs->substeps = substeps;
+        bs->updates = updates;
+        std::vector<int8_t> hb((size_t)std::max<int64_t>(ctx->n, 1));
+        if (ctx->n > 0)
+            SPH_CUDA(ctx, cudaMemcpyAsync(hb.data(), ctx->bins, (size_t)ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+        int deepest = 0;
+        unsigned long long over = 0;
+        rc = bin_max_read(ctx, &deepest, &over);  // synchronises the stream
+        if (rc) return rc;
+        bs->cfl_over = (int64_t)over;
+        for (int64_t i = 0; i < ctx->n; ++i) bs->bin_count[hb[(size_t)i]]++;
+    }
     if (out) {
         rc = conserved_device(ctx, parts);
         if (rc) return rc;
@@ -709,6 +859,25 @@ int sph_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_used, sph
     return do_step(ctx, parts, dt, dt_used, out);
 }
 
+int sph_step_bins(sph_ctx *ctx, sph_particles *parts, double dt_max, int32_t n_bins, sph_conserved *out,
+                  sph_bin_stats *stats)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!parts || (ctx->n > 0 && !parts_ok(parts))) return fail(ctx, SPH_ERR_INVALID_ARG, "null particle array");
+    if (!(dt_max > 0) || !isfinite(dt_max)) return fail(ctx, SPH_ERR_INVALID_ARG, "dt_max must be finite and > 0");
+    if (n_bins < 0 || n_bins > SPH_MAX_BINS) return fail(ctx, SPH_ERR_INVALID_ARG, "n_bins must be in [0, SPH_MAX_BINS]");
+    return do_step_bins(ctx, parts, dt_max, n_bins, out, stats);
+}
+
+int sph_get_bins(sph_ctx *ctx, int8_t *dev_bins)
+{
+    if (!ctx || !dev_bins) return SPH_ERR_INVALID_ARG;
+    if (!ctx->bins) return fail(ctx, SPH_ERR_STATE, "no sph_step_bins call yet");
+    if (ctx->n > 0)
+        SPH_CUDA(ctx, cudaMemcpyAsync(dev_bins, ctx->bins, (size_t)ctx->n, cudaMemcpyDeviceToDevice, ctx->stream));
+    return SPH_OK;
+}
+
 int sph_steps(sph_ctx *ctx, sph_particles *parts, int32_t n_steps, double dt, double *dt_last, sph_conserved *out)
 {
     if (!ctx) return SPH_ERR_INVALID_ARG;
@@ -940,6 +1109,7 @@ void sph_destroy(sph_ctx *ctx)
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
     free_particles(ctx);
+    free_bins(ctx);
     free_tree(ctx);
     cudaFree(ctx->axis);
     hp_free(ctx);

@@ -711,6 +711,8 @@ int permute_particles(sph_ctx *ctx, sph_particles *parts, bool cell_pos)
                                                              ctx->cap, n);
     SPH_LAUNCH(ctx, "copy back");
     ctx->ids_valid = true;
+    // individual time-steps: bins, kept density outputs and per-particle prediction
+    if (ctx->bin_mode) return bin_permute(ctx, parts);
     return SPH_OK;
 }
 

@@ -50,6 +50,9 @@ enum Counter {
     C_WALKOVF = 10,   // adaptive: leaf walks whose stack overflowed
     C_LISTTOT = 11,   // adaptive: neighbour-list entries (64-bit total)
     C_TICKET = 12,    // pair kernels: next tile group to hand out (reset before each launch)
+    C_BINACT = 13,    // individual time-steps: particles whose step ends at the current time
+    C_BINMAX = 14,    // individual time-steps: deepest bin in use
+    C_BINOVER = 15,   // individual time-steps: CFL steps below the smallest bin's step
     C_NCOUNTERS = 16
 };
 
@@ -267,6 +270,18 @@ struct sph_ctx {
     uint32_t *g_keys = nullptr, *g_keys_alt = nullptr, *g_vals = nullptr, *g_vals_alt = nullptr;
     uint64_t *g_keys64 = nullptr, *g_keys64_alt = nullptr;
 
+    // individual time-steps (sph_step_bins), allocated on first use: each particle's
+    // bin and whether its step ends at the current time (slot order, permuted with
+    // the particles), and scratch for the quantities inactive particles keep
+    int8_t *bins = nullptr, *bins_tmp = nullptr;
+    uint8_t *bin_active = nullptr, *bin_active_tmp = nullptr;
+    float *bin_s32 = nullptr;  // 5 * cap: rho, P, c, f, curl while permuting
+    int64_t bin_cap = 0;
+    bool bin_mode = false;     // inside sph_step_bins: builds also permute the above
+    int bin_levels = 0;        // n_bins of the running call
+    int64_t bin_now = 0;       // current time in units of dt_max / 2^n_bins
+    double bin_unit = 0.0;
+
     // statistics
     sph_stats st{};
     std::vector<sph::Timer> timers;
@@ -314,6 +329,12 @@ int tree_cell_keys_out(sph_ctx *ctx, int32_t *dev_keys);        // sph_tree.cu
 int tree_shrink_count(sph_ctx *ctx, sph_particles *parts);      // sph_tree.cu
 int tree_leaf_hcur(sph_ctx *ctx, sph_particles *parts);         // sph_tree.cu (before a force pass)
 int reset_h_brackets(sph_ctx *ctx);                             // sph_pairs.cu
+// individual time-steps, sph_integrate.cu
+int bin_permute(sph_ctx *ctx, sph_particles *parts);  // after each permutation: bins, kept state, prediction
+int bin_active(sph_ctx *ctx, unsigned long long *n_active);  // active mask at ctx->bin_now (host read)
+int bin_kick(sph_ctx *ctx, sph_particles *parts, bool all);  // half of each particle's own step
+int bin_assign(sph_ctx *ctx, sph_particles *parts, bool all, double dt_max);  // new bins from the CFL step
+int bin_max_read(sph_ctx *ctx, int *max_bin, unsigned long long *over);  // deepest bin in use (host read)
 // sph_hpredict.cu
 int hp_init(sph_ctx *ctx, uint64_t seed);
 int hp_load(sph_ctx *ctx, const uint16_t *w_bf16, const float *f32);

@@ -725,6 +725,7 @@ struct ForceArgs {
     const double *__restrict__ z;
     const float *__restrict__ cell_reach;  // per cell: max h of anything that can reach it
     float *ax, *ay, *az, *dudt, *vsig;
+    const uint8_t *__restrict__ fmask;  // individual time-steps: targets to update (null: all)
     unsigned long long *counters;
     const BoxDev *__restrict__ boxes;
     const uint32_t *__restrict__ list_off;
@@ -774,8 +775,9 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
         if (lane == 0 && g_after < ngroups) tk = atomicAdd(ticket, 1u);
         const int t = grp * TPW + sub;
         const int4 tile = t < ntiles ? a.tiles[t] : make_int4(0, 0, 0, 0);
-        const bool act = tl < tile.z;
-        const int i = LIST ? (act ? a.tord[tile.y + tl] : 0) : tile.y + tl;
+        const bool inr = tl < tile.z;
+        const int i = LIST ? (inr ? a.tord[tile.y + tl] : 0) : tile.y + tl;
+        const bool act = inr && (a.fmask == nullptr || a.fmask[i]);
         const unsigned amask = __ballot_sync(kFull, act);
         const bool live = (amask & gmask) != 0;
         // lanes without a target sit far away so that no distance test passes
@@ -1266,6 +1268,7 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts)
     a.az = parts->az;
     a.dudt = parts->dudt;
     a.vsig = parts->vsig;
+    a.fmask = ctx->bin_mode ? ctx->bin_active : nullptr;
     a.counters = ctx->counters;
     a.boxes = ctx->d_boxes;
     a.box = ctx->p.box_size;
