@@ -255,6 +255,15 @@ static int init_active(sph_ctx *ctx)
     return SPH_OK;
 }
 
+// Tiles holding a target of ctx->active (the compaction runs only when the
+// unconverged counter is nonzero: it is set to 1 here).
+static int compact_bin_targets(sph_ctx *ctx)
+{
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_UNCONV, 0, sizeof(unsigned long long), ctx->stream));
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_UNCONV, 1, 1, ctx->stream));
+    return ctx->adaptive ? compact_active_leaf_tiles(ctx) : compact_active_tiles(ctx);
+}
+
 static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
 {
     if (!ctx->built) return fail(ctx, SPH_ERR_STATE, "sph_density needs sph_build_cells on the current positions");
@@ -280,6 +289,11 @@ static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
         rc = reset_h_brackets(ctx);
         if (rc) return rc;
         bool all_tiles = true;  // first pass (and after a rebuild): every tile
+        if (ctx->bin_mode) {    // individual time-steps: only tiles with a target whose step ends
+            rc = compact_bin_targets(ctx);
+            if (rc) return rc;
+            all_tiles = false;
+        }
         for (;;) {
             const bool last = since == ctx->p.max_h_iter - 1;
             SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_UNCONV, 0, 2 * sizeof(unsigned long long),
@@ -319,6 +333,11 @@ static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
                 rc = reset_h_brackets(ctx);  // slots were permuted
                 if (rc) return rc;
                 all_tiles = true;
+                if (ctx->bin_mode) {
+                    rc = compact_bin_targets(ctx);
+                    if (rc) return rc;
+                    all_tiles = false;
+                }
             } else {
                 rc = ctx->adaptive ? compact_active_leaf_tiles(ctx) : compact_active_tiles(ctx);
                 if (rc) return rc;
@@ -347,7 +366,13 @@ static int do_force(sph_ctx *ctx, sph_particles *parts)
         // prune every source with its own h)
         int rc = ctx->adaptive ? tree_leaf_hcur(ctx, parts) : cell_reach(ctx);
         if (rc) return rc;
-        rc = run_force_pass(ctx, parts);
+        if (ctx->bin_mode) {  // individual time-steps: the tiles of the targets whose step ends
+            rc = init_active(ctx);
+            if (rc) return rc;
+            rc = compact_bin_targets(ctx);
+            if (rc) return rc;
+        }
+        rc = run_force_pass(ctx, parts, ctx->bin_mode);
         if (rc) return rc;
     }
     ctx->hydro_valid = true;

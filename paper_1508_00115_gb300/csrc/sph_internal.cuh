@@ -354,7 +354,7 @@ int cell_keys_out(sph_ctx *ctx, int32_t *dev_keys);             // sph_cells.cu
 int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool active_list);  // sph_pairs.cu
 int compact_active_tiles(sph_ctx *ctx);                                    // sph_pairs.cu
 int compact_active_leaf_tiles(sph_ctx *ctx);  // adaptive cells: tiles of active targets only  // sph_tree.cu
-int run_force_pass(sph_ctx *ctx, sph_particles *parts);                    // sph_pairs.cu
+int run_force_pass(sph_ctx *ctx, sph_particles *parts, bool active_list = false);  // sph_pairs.cu
 int sync_h(sph_ctx *ctx, sph_particles *parts);                            // sph_pairs.cu
 int kick(sph_ctx *ctx, sph_particles *parts);    // by *d_dt / 2           // sph_integrate.cu
 int drift(sph_ctx *ctx, sph_particles *parts);   // by *d_dt               // sph_integrate.cu

@@ -1241,15 +1241,16 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool ac
     return SPH_OK;
 }
 
-int run_force_pass(sph_ctx *ctx, sph_particles *parts)
+// active_list: the tiles compacted from ctx->active (individual time-steps)
+int run_force_pass(sph_ctx *ctx, sph_particles *parts, bool active_list)
 {
     ForceArgs a{};
     a.pos4 = ctx->pos4;
     a.vel4 = ctx->vel4;
     a.thermo4 = ctx->thermo4;
     a.cell_start = ctx->cell_start;
-    a.tiles = ctx->tiles;
-    a.n_tiles = ctx->n_tiles;
+    a.tiles = active_list ? ctx->act_tiles : ctx->tiles;
+    a.n_tiles = active_list ? ctx->n_act_tiles : ctx->n_tiles;
     a.x = parts->x;
     a.y = parts->y;
     a.z = parts->z;
@@ -1260,7 +1261,7 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts)
     a.leaf_scale = ctx->tree.leaf_scale;
     a.leaf_lo = ctx->tree.leaf_lo;
     a.leaf_hi = ctx->tree.leaf_hi;
-    a.tord = ctx->tree.tord;
+    a.tord = ctx->adaptive && active_list ? ctx->tree.act_ord : ctx->tree.tord;
     a.axis = (ctx->p.flags & SPH_FLAG_AXIS_SWEEP) && !ctx->adaptive ? ctx->axis : nullptr;
     a.axis_stride = std::max<int64_t>(ctx->cap, 1);
     a.ax = parts->ax;
