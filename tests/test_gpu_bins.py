@@ -118,3 +118,22 @@ def test_hierarchical_bins_match_oracle():
     # momentum is not conserved exactly by individual steps; energy stays close
     e0 = float(np.sum(s.m * (0.5 * (s.vx ** 2 + s.vy ** 2 + s.vz ** 2) + s.u)))
     assert abs(cons["e_tot"] - e0) < 1e-2 * e0
+
+
+def test_bins_edge_cases():
+    from paper_1508_00115_gb300 import binding
+    d = inputs.uniform(500, seed=4)
+    ctx, parts = _hydro_ctx(d)
+    with pytest.raises(binding.SphError) as e:  # no binned step yet
+        ctx.bins()
+    assert e.value.code == binding.SPH_ERR_STATE
+    for dt, levels in ((0.0, 2), (-1.0, 2), (float("nan"), 2), (1e-3, -1), (1e-3, binding.SPH_MAX_BINS + 1)):
+        with pytest.raises(binding.SphError) as e:
+            ctx.step_bins(parts, dt, levels)
+        assert e.value.code == binding.SPH_ERR_INVALID_ARG
+    # empty set: one step end, nothing to update
+    ctx0 = binding.Context(0)
+    p0 = binding.Particles({k: np.zeros(0) for k in inputs.FIELDS})
+    cons, st = ctx0.step_bins(p0, 1e-3, 3)
+    assert st["substeps"] == 1 and st["updates"] == 0 and cons["e_tot"] == 0.0
+    assert ctx0.bins().size == 0
