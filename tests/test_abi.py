@@ -3,6 +3,7 @@ the library builds for sm_103a, loads, exports every entry point include/sph.h
 declares, and its structs have the layout the Python binding assumes."""
 import ctypes
 import os
+import pathlib
 import subprocess
 
 import pytest
@@ -25,15 +26,18 @@ def test_library_exports_every_declared_symbol(L):
     assert not missing, missing
 
 
-def test_struct_layout_matches_header(tmp_path):
+def test_struct_layout_matches_header():
     """Compile a probe against include/sph.h with gcc and compare sizeof/offsetof
     with the ctypes mirrors."""
-    src = tmp_path / "probe.c"
+    scratch = pathlib.Path(ROOT) / "tests" / "_build"  # git-ignored
+    scratch.mkdir(exist_ok=True)
+    src = scratch / "probe.c"
     fields = {
         "sph_params": [f for f, _ in binding.sph_params._fields_],
         "sph_particles": [f for f, _ in binding.sph_particles._fields_],
         "sph_conserved": [f for f, _ in binding.sph_conserved._fields_],
         "sph_stats": [f for f, _ in binding.sph_stats._fields_],
+        "sph_bin_stats": [f for f, _ in binding.sph_bin_stats._fields_],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sph.h"', "int main(void){"]
     for s, fs in fields.items():
@@ -42,7 +46,7 @@ def test_struct_layout_matches_header(tmp_path):
             lines.append(f'printf("{s}.{f} %zu\\n", offsetof({s}, {f}));')
     lines.append("return 0;}")
     src.write_text("\n".join(lines))
-    exe = tmp_path / "probe"
+    exe = scratch / "probe"
     subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src),
                            "-o", str(exe)])
     out = dict(l.rsplit(" ", 1) for l in subprocess.check_output([str(exe)], text=True).split("\n")
@@ -95,3 +99,16 @@ def test_oracle_and_library_share_no_code():
         if f.endswith((".py", ".c")):
             text = open(os.path.join(ROOT, "oracle", f)).read()
             assert "paper_1508_00115_gb300" not in text.replace("paper_1508_00115_gb300/inputs.py", "")
+
+
+def test_header_constants_match_binding():
+    """Flags, status codes and SPH_MAX_BINS: the header's values are the binding's."""
+    import re
+    text = open(os.path.join(ROOT, "include", "sph.h")).read()
+    defs = dict(re.findall(r"#define (SPH_\w+) (\d+)u?\b", text))
+    defs.update(re.findall(r"^\s*(SPH_(?:OK|ERR_\w+)) = (\d+)", text, flags=re.M))
+    assert len(defs) >= 17, defs
+    for name, value in defs.items():
+        if hasattr(binding, name):
+            assert getattr(binding, name) == int(value), name
+    assert int(defs["SPH_MAX_BINS"]) == binding.SPH_MAX_BINS
