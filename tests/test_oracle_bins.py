@@ -119,3 +119,14 @@ def test_groups_that_do_not_interact_evolve_alone():
             x = getattr(rb, k)[sl]
             y = getattr(r1, k)
             assert np.abs(x - y).max() <= 1e-12 * max(1.0, np.abs(y).max()), k
+
+
+def test_all_in_the_top_bin_is_one_global_step(moving_hydro):
+    """Every CFL step above dt_max: every particle takes bin 0 whatever the depth of
+    the grid, and the call is one global step of dt_max."""
+    s, acc = moving_hydro
+    dt = 0.5 * oracle.cfl_dt(acc["h"], acc["vsig"])
+    g, _, _ = oracle.step(s, acc, dt)
+    b, _, st = oracle.step_bins(s, acc, dt, 5)
+    assert np.all(st["bins"] == 0) and st["substeps"] == 1 and st["active"] == s.n
+    _same(b, g, 1e-13)
