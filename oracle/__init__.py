@@ -24,7 +24,8 @@ hydrodynamics and gravity for cosmological simulations"):
 
 The arithmetic lives in ``sph_oracle.c`` (plain C, FP64, OpenMP over targets,
 ``-ffp-contract=off``); this file only marshals arrays and composes the step.
-Parity pins: ``tests/test_oracle_pins.py`` (no function here is unpinned).
+Parity pins: ``tests/test_oracle_pins.py`` and, for the individual time-steps,
+``tests/test_oracle_bins.py`` (no function here is unpinned).
 """
 from __future__ import annotations
 
