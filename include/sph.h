@@ -47,9 +47,23 @@ typedef enum {
     SPH_ERR_NAN = 6,            /* a non-finite input or result was detected     */
     SPH_ERR_STATE = 7,          /* call order violated (e.g. force before        */
                                 /* density on the current positions)             */
-    SPH_ERR_CAPACITY = 8        /* a size limit was exceeded (adaptive cells:    */
+    SPH_ERR_CAPACITY = 8,       /* a size limit was exceeded (adaptive cells:    */
                                 /* more than 2^32 - 2 neighbour-list entries)    */
+    SPH_ERR_PRECISION = 9       /* uniform grid: some converged h is below cell  */
+                                /* side / SPH_FRAME_RATIO, where FP32 positions  */
+                                /* relative to the cell centre cannot hold the   */
+                                /* 1e-5 density tolerance (results are written;  */
+                                /* use SPH_FLAG_ADAPTIVE for such h ranges)      */
 } sph_status;
+
+/* Largest cell side / h the uniform grid accepts (SPH_ERR_PRECISION beyond).  The
+ * pair arithmetic takes positions relative to the cell centre in FP32: each
+ * separation component is off by at most ~3.4 x 2^-24 L (the two positions, the
+ * cell side and the shifted sum), which bounds the density error by ~2e-6 L/h when
+ * every rounding points the same way; the roundings of the ~50 neighbours of a sum
+ * are independent and partly cancel, and the largest error measured over clustered
+ * fields is ~2e-8 L/h (2e-5 at L/h = 960).  At the limit that is ~1.3e-6. */
+#define SPH_FRAME_RATIO 64
 
 typedef struct sph_ctx sph_ctx; /* opaque, library-owned */
 
@@ -232,7 +246,9 @@ int sph_build_cells(sph_ctx *ctx, sph_particles *parts);
  * (SPH_ERR_NOT_CONVERGED beyond that).
  * Writes h, rho, P, c, f, divv, curl, n_ngb.  *iters_out (may be NULL) = passes
  * run.  Requires sph_build_cells on the current positions.  Host read: the
- * unconverged count after each pass. */
+ * unconverged count after each pass.  On the uniform grid, SPH_ERR_PRECISION if a
+ * converged h is below cell side / SPH_FRAME_RATIO (results are written, and the
+ * state counts as having densities, so that sph_force may follow). */
 int sph_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out);
 
 /* Eq. 2 (Gadget-2 form) with artificial viscosity over pairs r_ij < max(h_i, h_j).
@@ -376,23 +392,40 @@ int sph_hpredict_collect(sph_ctx *ctx, float *dev_feats, float *dev_target, int6
  * accounting), or that must not allocate in the middle of a time step.  The paper
  * has no counterpart; it is a deployment convenience.
  *   keys_in   device uint32[n], read only, need not be sorted
- *   keys_out  device uint32[n], caller-owned: keys in ascending order, equal keys
- *             in input order
+ *   keys_out  device uint32[n], caller-owned: the input keys (all their bits) in
+ *             ascending order of their low key_bits bits, equal ones in input order
  *   perm_out  device uint32[n], caller-owned: perm_out[k] = index in keys_in of
  *             the key now in slot k
- *   key_bits  significant low bits of every key, 1..32 (bits above are ignored)
+ *   key_bits  significant low bits of every key, 1..32; bits above them take no
+ *             part in the order
+ * The three buffers must not overlap (an in-place sort is not supported):
+ * overlapping ranges return SPH_ERR_INVALID_ARG before any GPU work.
  * The scratch is a fixed static device buffer of about 2.2 MB, held on every GPU
  * that loads the library until the process exits; n above SPH_SORT_STATIC_MAX_N
  * returns SPH_ERR_INVALID_ARG before any GPU work.  Nothing is allocated or freed.
- * The first call on a device looks up the buffer's device address (make it before
- * any stream capture).  Work is enqueued on `cuda_stream` (a cudaStream_t) on the
+ * Every call looks up the buffer's device address on the current device; the first
+ * call on a device also loads the library's GPU code there (make it before any
+ * stream capture).  Work is enqueued on `cuda_stream` (a cudaStream_t) on the
  * current device and the call returns without synchronising.  All calls share the
  * one buffer: calls whose GPU work overlaps (different streams, or several host
  * threads) race and must be serialised by the caller.  Returns SPH_OK,
- * SPH_ERR_INVALID_ARG or SPH_ERR_CUDA (no context, so no sph_last_error text). */
+ * SPH_ERR_INVALID_ARG or SPH_ERR_CUDA (no context, so no sph_last_error text):
+ * SPH_ERR_CUDA also when a CUDA error from earlier work is still pending on entry
+ * (it is left pending for its owner, and nothing is launched). */
 #define SPH_SORT_STATIC_MAX_N 262144
 int sph_sort_keys_static(const uint32_t *keys_in, uint32_t *keys_out, uint32_t *perm_out, int64_t n,
                          int32_t key_bits, void *cuda_stream);
+
+/* Throughput of the plain FP32 FMA pipes on the current device: the ceiling of the
+ * pair kernels, whose sums are not dense contractions (the tensor cores do not
+ * apply).  Not in the paper; it measures the denominator of their roofline.  Runs
+ * `reps` timed launches (after one untimed) of a kernel in which every thread
+ * carries 16 independent FMA recurrences for `iters` rounds, 8 blocks of 256 threads
+ * per SM, on `cuda_stream` (a cudaStream_t), and synchronises.  *tflops_out (host)
+ * = 2 x FMAs / the fastest launch's CUDA-event time; *ms_out (may be NULL) = that
+ * time.  Allocates nothing.  SPH_ERR_INVALID_ARG for iters < 1, reps < 1 or a null
+ * tflops_out; SPH_ERR_CUDA if a CUDA call fails. */
+int sph_fp32_peak(void *cuda_stream, int32_t iters, int32_t reps, double *tflops_out, float *ms_out);
 
 int sph_get_stats(sph_ctx *ctx, sph_stats *s);
 int sph_reset_stats(sph_ctx *ctx);

@@ -28,6 +28,8 @@ SPH_ERR_TIMEOUT = 5
 SPH_ERR_NAN = 6
 SPH_ERR_STATE = 7
 SPH_ERR_CAPACITY = 8
+SPH_ERR_PRECISION = 9
+SPH_FRAME_RATIO = 64
 SPH_FLAG_TIMING = 1
 SPH_FLAG_NGB_HASH = 2
 SPH_FLAG_AUTOTUNE = 4
@@ -42,7 +44,7 @@ SPH_SORT_STATIC_MAX_N = 262144
 
 _NAMES = {0: "SPH_OK", 1: "SPH_ERR_INVALID_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_NOT_CONVERGED",
           4: "SPH_ERR_H_EXCEEDS_CELL", 5: "SPH_ERR_TIMEOUT", 6: "SPH_ERR_NAN", 7: "SPH_ERR_STATE",
-          8: "SPH_ERR_CAPACITY"}
+          8: "SPH_ERR_CAPACITY", 9: "SPH_ERR_PRECISION"}
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "sph.h")
 
@@ -149,6 +151,8 @@ def lib(build_if_missing: bool = True):
             "sph_hpredict_train": (C, [P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64,
                                        ctypes.POINTER(ctypes.c_float)]),
             "sph_hpredict_collect": (C, [P, P, P, ctypes.c_int64]),
+            "sph_fp32_peak": (C, [P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_float)]),
             "sph_get_stats": (C, [P, ctypes.POINTER(sph_stats)]),
             "sph_reset_stats": (C, [P]),
             "sph_last_error": (ctypes.c_char_p, [P]),
@@ -301,6 +305,16 @@ def sph_hpredict_train(ctx, feats, target, n: int, epochs: int, lr: float, seed:
 def sph_hpredict_collect(ctx, feats, target, capacity: int) -> int:
     return _check(lib().sph_hpredict_collect(ctx, _ptr(feats) if feats is not None else None,
                                              _ptr(target) if target is not None else None, int(capacity)), ctx)
+
+
+def sph_fp32_peak(stream: int | None = None, iters: int = 1 << 15, reps: int = 3) -> tuple[float, float]:
+    """Measured FP32 FMA throughput of the current device: (TFLOP/s, ms of the
+    fastest launch)."""
+    tf = ctypes.c_double(0)
+    ms = ctypes.c_float(0)
+    _check(lib().sph_fp32_peak(ctypes.c_void_p(stream or 0), int(iters), int(reps), ctypes.byref(tf),
+                               ctypes.byref(ms)))
+    return float(tf.value), float(ms.value)
 
 
 def sph_get_stats(ctx) -> dict:

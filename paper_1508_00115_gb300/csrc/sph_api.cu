@@ -188,7 +188,10 @@ static int autotune(sph_ctx *ctx, sph_particles *parts)
     const int leaves[3] = {32, 64, 128};  // adaptive cells: leaf sizes instead of cell factors
     cudaEvent_t ev[4];
     for (int i = 0; i < 4; ++i) SPH_CUDA(ctx, cudaEventCreate(&ev[i]));
+    // schedules whose cells are too large for the FP32 frame of the smallest h (uniform
+    // grid, SPH_FRAME_RATIO) rank behind every schedule that holds it
     float best = 1e30f;
+    bool best_fits = false;
     int best_tw = ctx->tile_w;
     float best_cf = ctx->p.cell_factor;
     int best_leaf = ctx->leaf_max;
@@ -208,6 +211,7 @@ static int autotune(sph_ctx *ctx, sph_particles *parts)
             }
             if (rc) break;
             SPH_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
+            SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_PREC, 0, sizeof(unsigned long long), ctx->stream));
             for (int r = 0; r < 2 && rc == SPH_OK; ++r) {
                 SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, ctx->n, ctx->stream));
                 rc = run_density_pass(ctx, parts, true, false);
@@ -222,8 +226,12 @@ static int autotune(sph_ctx *ctx, sph_particles *parts)
             SPH_CUDA(ctx, cudaEventElapsedTime(&t_1, ev[1], ev[2]));
             SPH_CUDA(ctx, cudaEventElapsedTime(&t_2, ev[2], ev[3]));
             const float ms = t_build + std::min(t_1, t_2);
-            if (ms < best) {
+            rc = read_counters(ctx);
+            if (rc) break;
+            const bool fits = ctx->h_counters[C_PREC] == 0;
+            if ((fits && !best_fits) || (fits == best_fits && ms < best)) {
                 best = ms;
+                best_fits = fits;
                 best_tw = tws[a];
                 best_cf = ctx->p.cell_factor;
                 best_leaf = ctx->leaf_max;
@@ -279,7 +287,7 @@ static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
         ctx->tuned = true;  // the inner call does not tune
         int rc = do_density(ctx, parts, nullptr);
         ctx->tuned = false;
-        if (rc && rc != SPH_ERR_NOT_CONVERGED) return rc;
+        if (rc && rc != SPH_ERR_NOT_CONVERGED && rc != SPH_ERR_PRECISION) return rc;
         rc = autotune(ctx, parts);
         if (rc) return rc;
     }
@@ -294,6 +302,7 @@ static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
             if (rc) return rc;
             all_tiles = false;
         }
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_PREC, 0, sizeof(unsigned long long), ctx->stream));
         for (;;) {
             const bool last = since == ctx->p.max_h_iter - 1;
             SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_UNCONV, 0, 2 * sizeof(unsigned long long),
@@ -332,6 +341,7 @@ static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
                 if (rc) return rc;
                 rc = reset_h_brackets(ctx);  // slots were permuted
                 if (rc) return rc;
+                SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_PREC, 0, sizeof(unsigned long long), ctx->stream));
                 all_tiles = true;
                 if (ctx->bin_mode) {
                     rc = compact_bin_targets(ctx);
@@ -354,6 +364,13 @@ static int do_density(sph_ctx *ctx, sph_particles *parts, int32_t *iters_out)
         char buf[160];
         snprintf(buf, sizeof buf, "%llu smoothing lengths not converged after %d passes", unconv, iters);
         return fail(ctx, SPH_ERR_NOT_CONVERGED, buf);
+    }
+    if (n > 0 && ctx->h_counters[C_PREC]) {
+        char buf[200];
+        snprintf(buf, sizeof buf,
+                 "uniform grid: some h is below cell side / %d, beyond what FP32 cell-relative positions "
+                 "resolve at the density tolerance (use SPH_FLAG_ADAPTIVE)", SPH_FRAME_RATIO);
+        return fail(ctx, SPH_ERR_PRECISION, buf);
     }
     return SPH_OK;
 }
@@ -389,6 +406,25 @@ static int do_build(sph_ctx *ctx, sph_particles *parts)
     return rc;
 }
 
+// do_density inside a compound call: SPH_ERR_PRECISION leaves written results that
+// only miss the density tolerance, so the call goes on and reports it at its end
+static int density_in_call(sph_ctx *ctx, sph_particles *parts)
+{
+    const int rc = do_density(ctx, parts, nullptr);
+    if (rc != SPH_ERR_PRECISION) return rc;
+    ctx->soft_rc = rc;
+    ctx->soft_msg = ctx->err;
+    return SPH_OK;
+}
+
+// the status of a compound call: its own error, else the deferred one
+static int finish_call(sph_ctx *ctx, int rc)
+{
+    if (rc == SPH_OK && ctx->soft_rc) rc = fail(ctx, ctx->soft_rc, ctx->soft_msg);
+    ctx->soft_rc = 0;
+    return rc;
+}
+
 // build -> density -> force.  in_step: the hydro pass inside a step, where the
 // previous pass's outputs feed the learned h guess and the sample collection.
 static int hydro(sph_ctx *ctx, sph_particles *parts, bool in_step = false)
@@ -404,7 +440,7 @@ static int hydro(sph_ctx *ctx, sph_particles *parts, bool in_step = false)
         rc = hp_features(ctx, parts);
         if (rc) return rc;
     }
-    rc = do_density(ctx, parts, nullptr);
+    rc = density_in_call(ctx, parts);
     if (rc) return rc;
     if (collect) {
         rc = hp_collect(ctx, parts);
@@ -513,7 +549,7 @@ static int do_step_bins(sph_ctx *ctx, sph_particles *parts, double dt_max, int l
             updates += (int64_t)n_act;
             r = do_build(ctx, parts);
             if (r) return r;
-            r = do_density(ctx, parts, nullptr);
+            r = density_in_call(ctx, parts);
             if (r) return r;
             r = do_force(ctx, parts);
             if (r) return r;
@@ -565,6 +601,7 @@ __global__ void k_step_flags(unsigned long long *c)
     unsigned long long f = 0;
     if (c[C_UNCONV]) f |= 1ull;
     if (c[C_HFLAG]) f |= 2ull;
+    if (c[C_PREC]) f |= 4ull;
     c[C_GFLAGS] |= f;
 }
 
@@ -589,6 +626,7 @@ static int graph_step(sph_ctx *ctx, sph_particles *parts, double dt, int passes)
     rc = reset_h_brackets(ctx);
     if (rc) return rc;
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_UNCONV, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_PREC, 0, sizeof(unsigned long long), ctx->stream));
     for (int p = 0; p < passes; ++p) {
         if (p > 0) {
             rc = ctx->adaptive ? compact_active_leaf_tiles(ctx) : compact_active_tiles(ctx);
@@ -752,6 +790,7 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
     const unsigned long long gf = ctx->h_counters[C_GFLAGS];
     if (gf & 2ull) return fail(ctx, SPH_ERR_H_EXCEEDS_CELL, "some h grew beyond twice the planned cell side");
     if (gf & 1ull) return fail(ctx, SPH_ERR_NOT_CONVERGED, "smoothing lengths not converged in a captured step");
+    if (gf & 4ull) return fail(ctx, SPH_ERR_PRECISION, "uniform grid: some h fell below cell side / SPH_FRAME_RATIO");
     return SPH_OK;
 }
 
@@ -881,7 +920,8 @@ int sph_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_used, sph
     if (!isfinite(dt)) return fail(ctx, SPH_ERR_INVALID_ARG, "dt must be finite");
     if ((ctx->p.flags & SPH_FLAG_HPREDICT) && !ctx->hp.ready)
         return fail(ctx, SPH_ERR_STATE, "SPH_FLAG_HPREDICT without predictor weights");
-    return do_step(ctx, parts, dt, dt_used, out);
+    ctx->soft_rc = 0;
+    return finish_call(ctx, do_step(ctx, parts, dt, dt_used, out));
 }
 
 int sph_step_bins(sph_ctx *ctx, sph_particles *parts, double dt_max, int32_t n_bins, sph_conserved *out,
@@ -891,7 +931,8 @@ int sph_step_bins(sph_ctx *ctx, sph_particles *parts, double dt_max, int32_t n_b
     if (!parts || (ctx->n > 0 && !parts_ok(parts))) return fail(ctx, SPH_ERR_INVALID_ARG, "null particle array");
     if (!(dt_max > 0) || !isfinite(dt_max)) return fail(ctx, SPH_ERR_INVALID_ARG, "dt_max must be finite and > 0");
     if (n_bins < 0 || n_bins > SPH_MAX_BINS) return fail(ctx, SPH_ERR_INVALID_ARG, "n_bins must be in [0, SPH_MAX_BINS]");
-    return do_step_bins(ctx, parts, dt_max, n_bins, out, stats);
+    ctx->soft_rc = 0;
+    return finish_call(ctx, do_step_bins(ctx, parts, dt_max, n_bins, out, stats));
 }
 
 int sph_get_bins(sph_ctx *ctx, int8_t *dev_bins)
@@ -911,7 +952,8 @@ int sph_steps(sph_ctx *ctx, sph_particles *parts, int32_t n_steps, double dt, do
     if (n_steps < 0) return fail(ctx, SPH_ERR_INVALID_ARG, "n_steps must be >= 0");
     if ((ctx->p.flags & SPH_FLAG_HPREDICT) && !ctx->hp.ready)
         return fail(ctx, SPH_ERR_STATE, "SPH_FLAG_HPREDICT without predictor weights");
-    return do_steps(ctx, parts, n_steps, dt, dt_last, out);
+    ctx->soft_rc = 0;
+    return finish_call(ctx, do_steps(ctx, parts, n_steps, dt, dt_last, out));
 }
 
 int sph_step_host(sph_ctx *ctx, sph_particles *hp, double dt, double *dt_used, sph_conserved *out)
@@ -956,8 +998,12 @@ int sph_step_host(sph_ctx *ctx, sph_particles *hp, double dt, double *dt_used, s
     for (auto &q : in32) SPH_CUDA(ctx, cudaMemcpyAsync(q[0], q[1], b4, cudaMemcpyHostToDevice, s));
     // the device copies replace whatever the context held: cells must be rebuilt
     ctx->built = ctx->density_valid = false;
+    ctx->soft_rc = 0;
     int rc = do_step(ctx, &d, dt, dt_used, out);
-    if (rc) return rc;
+    if (rc) {
+        ctx->soft_rc = 0;
+        return rc;
+    }
     for (auto &q : in64) SPH_CUDA(ctx, cudaMemcpyAsync(q[1], q[0], b8, cudaMemcpyDeviceToHost, s));
     for (auto &q : in32) SPH_CUDA(ctx, cudaMemcpyAsync(q[1], q[0], b4, cudaMemcpyDeviceToHost, s));
     float *out32[][2] = {{d.rho, hp->rho}, {d.P, hp->P}, {d.c, hp->c}, {d.f, hp->f}, {d.divv, hp->divv},
@@ -965,7 +1011,7 @@ int sph_step_host(sph_ctx *ctx, sph_particles *hp, double dt, double *dt_used, s
     for (auto &q : out32) SPH_CUDA(ctx, cudaMemcpyAsync(q[1], q[0], b4, cudaMemcpyDeviceToHost, s));
     SPH_CUDA(ctx, cudaMemcpyAsync(hp->n_ngb, d.n_ngb, b4, cudaMemcpyDeviceToHost, s));
     SPH_CUDA(ctx, cudaStreamSynchronize(s));
-    return SPH_OK;
+    return finish_call(ctx, SPH_OK);
 }
 
 int sph_get_permutation(sph_ctx *ctx, int64_t *dev_perm)

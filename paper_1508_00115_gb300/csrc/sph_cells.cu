@@ -6,7 +6,6 @@
 #include <math.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "sph_internal.cuh"
 
@@ -128,9 +127,12 @@ constexpr int kRsItems = 16;
 constexpr int kRsTile = kRsThreads * kRsItems;  // 4096
 constexpr int kRsWarps = kRsThreads / 32;
 
+// dmask: the bits of the digit that take part (255, or fewer in the last pass of a
+// sort whose key_bits is not a multiple of 8)
 template <typename K>
 __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const K *__restrict__ keys, int n, int shift,
-                                                           uint32_t *__restrict__ hist, int ntiles)
+                                                           uint32_t *__restrict__ hist, int ntiles,
+                                                           uint32_t dmask = 255u)
 {
     __shared__ uint32_t cnt[256];
     cnt[threadIdx.x] = 0;
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_hist(const K *__restrict__
 #pragma unroll 4
     for (int k = 0; k < kRsItems; ++k) {
         int64_t i = base + k * kRsThreads + threadIdx.x;
-        if (i < n) atomicAdd(&cnt[(uint32_t)(keys[i] >> shift) & 255u], 1u);
+        if (i < n) atomicAdd(&cnt[(uint32_t)(keys[i] >> shift) & dmask], 1u);
     }
     __syncthreads();
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
@@ -150,7 +152,8 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const K *__restric
                                                               const uint32_t *__restrict__ vin,
                                                               K *__restrict__ kout,
                                                               uint32_t *__restrict__ vout, int n, int shift,
-                                                              const uint32_t *__restrict__ offs, int ntiles)
+                                                              const uint32_t *__restrict__ offs, int ntiles,
+                                                              uint32_t dmask = 255u)
 {
     __shared__ uint32_t wcnt[kRsWarps][256];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const K *__restric
         K k = ok ? kin[i] : (K)0;
         key[it] = k;
         val[it] = ok ? (vin ? vin[i] : (uint32_t)i) : 0u;
-        uint32_t d = ok ? ((uint32_t)(k >> shift) & 255u) : 256u;
+        uint32_t d = ok ? ((uint32_t)(k >> shift) & dmask) : 256u;
         unsigned peers = __match_any_sync(kFull, d);
         uint32_t before = ok ? wcnt[w][d] : 0u;
         rank[it] = (uint16_t)(before + __popc(peers & lt));
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const K *__restric
     for (int it = 0; it < kRsItems; ++it) {
         int64_t i = base + it * 32 + lane;
         if (i < n) {
-            uint32_t d = (uint32_t)(key[it] >> shift) & 255u;
+            uint32_t d = (uint32_t)(key[it] >> shift) & dmask;
             uint32_t dst = offs[(int64_t)d * ntiles + blockIdx.x] + woff[w][d] + rank[it];
             kout[dst] = key[it];
             vout[dst] = val[it];
@@ -845,27 +848,24 @@ constexpr int64_t kStaticWords = 2 * SPH_SORT_STATIC_MAX_N + kStaticHist + kStat
 
 static __device__ __align__(256) uint32_t g_sort_scratch[kStaticWords];
 
-constexpr int kStaticMaxDevices = 64;
-static uint32_t *g_sort_scratch_addr[kStaticMaxDevices];
-static std::mutex g_sort_scratch_mu;
-
-// Device address of g_sort_scratch on the current device (looked up once per
-// device; the host-side symbol is only a stand-in and must never reach a kernel).
+// Device address of g_sort_scratch on the current device.  The host-side symbol is
+// only a stand-in and must never reach a kernel.  The lookup runs on every call (it
+// is a table lookup once the module is loaded), so an address can never outlive a
+// cudaDeviceReset; the first call on a device loads the module.
 static cudaError_t static_scratch(uint32_t **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_sort_scratch_mu);
-    if (!g_sort_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_sort_scratch);
-        if (e != cudaSuccess) return e;
-        g_sort_scratch_addr[dev] = (uint32_t *)p;
-    }
-    *out = g_sort_scratch_addr[dev];
+    *out = (uint32_t *)p;
     return cudaSuccess;
+}
+
+// [a, a + bytes) and [b, b + bytes) share a byte
+static bool overlap(const void *a, const void *b, size_t bytes)
+{
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + bytes && y < x + bytes;
 }
 
 }  // namespace sph
@@ -877,6 +877,14 @@ extern "C" int sph_sort_keys_static(const uint32_t *keys_in, uint32_t *keys_out,
     if (n < 0 || n > SPH_SORT_STATIC_MAX_N || key_bits < 1 || key_bits > 32) return SPH_ERR_INVALID_ARG;
     if (n == 0) return SPH_OK;
     if (!keys_in || !keys_out || !perm_out) return SPH_ERR_INVALID_ARG;
+    // a pass reads keys that other blocks of the same pass may already have overwritten
+    // if the outputs alias the input or each other
+    const size_t bytes = sizeof(uint32_t) * (size_t)n;
+    if (overlap(keys_in, keys_out, bytes) || overlap(keys_in, perm_out, bytes) || overlap(keys_out, perm_out, bytes))
+        return SPH_ERR_INVALID_ARG;
+    // an error left pending by earlier, unrelated work is not this call's to report or
+    // to clear: refuse to run on top of it
+    if (cudaPeekAtLastError() != cudaSuccess) return SPH_ERR_CUDA;
     uint32_t *scratch = nullptr;
     if (static_scratch(&scratch) != cudaSuccess) return SPH_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -895,13 +903,21 @@ extern "C" int sph_sort_keys_static(const uint32_t *keys_in, uint32_t *keys_out,
         const bool to_out = ((passes - 1 - p) % 2) == 0;
         uint32_t *kout = to_out ? keys_out : sk, *vout = to_out ? perm_out : sv;
         const int shift = 8 * p;
-        k_radix_hist<uint32_t><<<ntiles, kRsThreads, 0, st>>>(kin, nn, shift, hist, ntiles);
+        // the last digit keeps only the bits below key_bits: higher bits take no part
+        const int top = key_bits - shift;  // 1..8 in the last pass
+        const uint32_t dmask = top >= 8 ? 255u : (1u << top) - 1u;
+        k_radix_hist<uint32_t><<<ntiles, kRsThreads, 0, st>>>(kin, nn, shift, hist, ntiles, dmask);
+        if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
         k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, st>>>(hist, nh, aux);
+        if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
         k_scan_top<<<1, kScanThreads, 0, st>>>(aux, nb);
+        if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
         k_scan_down<<<(unsigned)nb, kScanThreads, 0, st>>>(hist, hist, nh, aux);
-        k_radix_scatter<uint32_t><<<ntiles, kRsThreads, 0, st>>>(kin, vin, kout, vout, nn, shift, hist, ntiles);
+        if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
+        k_radix_scatter<uint32_t><<<ntiles, kRsThreads, 0, st>>>(kin, vin, kout, vout, nn, shift, hist, ntiles, dmask);
+        if (cudaGetLastError() != cudaSuccess) return SPH_ERR_CUDA;
         kin = kout;
         vin = vout;
     }
-    return cudaGetLastError() == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+    return SPH_OK;
 }

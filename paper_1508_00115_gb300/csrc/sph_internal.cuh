@@ -45,7 +45,8 @@ enum Counter {
     C_FCAND = 5,      // force candidate tests
     C_FLOORS = 6,     // u floors
     C_DTARGETS = 7,   // active density targets
-    C_GFLAGS = 8,     // multi-step run: OR of per-step flags (1: unconverged, 2: h beyond cells)
+    C_GFLAGS = 8,     // multi-step run: OR of per-step flags (1: unconverged, 2: h beyond cells,
+                      // 4: h below what the uniform grid's FP32 frame resolves)
     C_SHRINK = 9,     // adaptive: leaves whose largest h fell below kTreeShrink x its build value
     C_WALKOVF = 10,   // adaptive: leaf walks whose stack overflowed
     C_LISTTOT = 11,   // adaptive: neighbour-list entries (64-bit total)
@@ -53,7 +54,8 @@ enum Counter {
     C_BINACT = 13,    // individual time-steps: particles whose step ends at the current time
     C_BINMAX = 14,    // individual time-steps: deepest bin in use
     C_BINOVER = 15,   // individual time-steps: CFL steps below the smallest bin's step
-    C_NCOUNTERS = 16
+    C_PREC = 16,      // uniform grid: a converged h below cell side / SPH_FRAME_RATIO
+    C_NCOUNTERS = 17
 };
 
 // Cell grid of one periodic box (every box has side box_size; boxes are batched
@@ -281,6 +283,12 @@ struct sph_ctx {
     int bin_levels = 0;        // n_bins of the running call
     int64_t bin_now = 0;       // current time in units of dt_max / 2^n_bins
     double bin_unit = 0.0;
+
+    // a status that does not stop a compound call (sph_step, sph_steps, sph_step_bins,
+    // sph_step_host): SPH_ERR_PRECISION from a density pass whose results were
+    // written; the call finishes and returns it (with its message) at the end
+    int soft_rc = 0;
+    std::string soft_msg;
 
     // statistics
     sph_stats st{};

@@ -675,6 +675,9 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
                 a.h_hi[i] = up;
             } else {
                 if (!conv) flag = 1u;
+                // uniform grid: FP32 cell-relative positions resolve h only down to
+                // cell side / SPH_FRAME_RATIO at the density tolerance
+                if (!LIST && bx.L32 > (float)SPH_FRAME_RATIO * hi) flag |= 4u;
                 a.active[i] = 0;
                 // quantities needed before the pressure gradient (EOS, grad-h, Balsara)
                 const float u = a.upred[i];
@@ -700,7 +703,7 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
             }
         }
         acc_unc += flag & 1u;
-        acc_hf |= flag & 2u;
+        acc_hf |= flag & 6u;
     }
     const unsigned long long tp = warp_sum_ull(acc_pairs), tc = warp_sum_ull(acc_cand);  // 64-bit sums
     const unsigned tu = __reduce_add_sync(kFull, acc_unc), th = __reduce_or_sync(kFull, acc_hf);
@@ -709,7 +712,8 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
         if (tc) atomicAdd(a.counters + C_DCAND, tc);
         if (acc_targets) atomicAdd(a.counters + C_DTARGETS, (unsigned long long)acc_targets);
         if (tu) atomicAdd(a.counters + C_UNCONV, (unsigned long long)tu);
-        if (th) atomicOr(a.counters + C_HFLAG, 1ull);
+        if (th & 2u) atomicOr(a.counters + C_HFLAG, 1ull);
+        if (th & 4u) atomicOr(a.counters + C_PREC, 1ull);
     }
 }
 

@@ -112,3 +112,18 @@ def test_header_constants_match_binding():
         if hasattr(binding, name):
             assert getattr(binding, name) == int(value), name
     assert int(defs["SPH_MAX_BINS"]) == binding.SPH_MAX_BINS
+
+
+def test_static_sort_rejects_overlapping_buffers_without_gpu_work(L):
+    """sph_sort_keys_static cannot sort in place: any overlap of keys_in, keys_out and
+    perm_out is refused before anything touches a device (the addresses below are
+    never dereferenced)."""
+    n = 1000
+    base = 1 << 40
+    cases = [(base, base, base + 8 * n),             # keys_out == keys_in
+             (base, base + 8 * n, base + 4),          # perm_out inside keys_in
+             (base, base + 8 * n, base + 8 * n + 4)]  # perm_out overlaps keys_out
+    for kin, kout, pout in cases:
+        rc = L.sph_sort_keys_static(ctypes.c_void_p(kin), ctypes.c_void_p(kout), ctypes.c_void_p(pout), n,
+                                    32, None)
+        assert rc == binding.SPH_ERR_INVALID_ARG, (kin, kout, pout)

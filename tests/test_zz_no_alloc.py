@@ -62,6 +62,38 @@ def test_static_sort_matches_build_on_two_calls_in_a_row():
         assert np.array_equal(po.astype(np.int64), perm)
 
 
+@pytest.mark.parametrize("bits", [8, 13, 16, 24, 32])
+def test_static_sort_random_keys_match_stable_argsort(bits):
+    """Random keys, every pass count (1-4 passes: an odd count writes the outputs in
+    the first pass straight from the input), keys with stray bits above key_bits
+    (they must take no part in the order), two calls in a row."""
+    rng = np.random.default_rng(100 + bits)
+    mask = np.uint32((1 << bits) - 1)
+    for n in (1, 4095, 4097, 50001):
+        keys = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+        # half the keys take few distinct low values, so that stability decides many
+        # slots; their high bits stay random
+        half = n // 2
+        keys[:half] = (keys[:half] & ~mask) | ((keys[:half] & mask) % np.uint32(7))
+        low = keys & mask
+        want = np.argsort(low, kind="stable")
+        for _ in range(2):
+            ko, po = _static_sort(keys, bits)
+            assert np.array_equal(po.astype(np.int64), want)
+            assert np.array_equal(ko, keys[want])
+
+
+def test_static_sort_at_the_size_limit():
+    n = binding.SPH_SORT_STATIC_MAX_N
+    rng = np.random.default_rng(7)
+    keys = rng.integers(0, 1 << 20, n, dtype=np.uint32)
+    want = np.argsort(keys, kind="stable")
+    for bits in (20, 24):
+        ko, po = _static_sort(keys, bits)
+        assert np.array_equal(po.astype(np.int64), want)
+        assert np.array_equal(ko, keys[want])
+
+
 def test_static_sort_rejects_oversize_without_gpu_work():
     L = binding.lib()
     rc = L.sph_sort_keys_static(None, None, None, binding.SPH_SORT_STATIC_MAX_N + 1, 16, None)
