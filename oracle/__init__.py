@@ -21,11 +21,15 @@ hydrodynamics and gravity for cosmological simulations"):
 * :func:`time_bins`, :func:`step_bins` -- the same leapfrog with individual,
   power-of-two time-steps (the Gadget-2 scheme the paper's force law comes from;
   the paper itself is silent on time-stepping).
+* :func:`grav_p2p` -- Sec. 3.2, Eq. 3: the near-field gravity tasks in which all
+  particles of a cell interact with all particles of the adjacent cells
+  (softened, minimal image).
 
 The arithmetic lives in ``sph_oracle.c`` (plain C, FP64, OpenMP over targets,
 ``-ffp-contract=off``); this file only marshals arrays and composes the step.
-Parity pins: ``tests/test_oracle_pins.py`` and, for the individual time-steps,
-``tests/test_oracle_bins.py`` (no function here is unpinned).
+Parity pins: ``tests/test_oracle_pins.py``, for the individual time-steps
+``tests/test_oracle_bins.py``, for the gravity near field
+``tests/test_oracle_gravity.py`` (no function here is unpinned).
 """
 from __future__ import annotations
 
@@ -90,6 +94,8 @@ def _load():
         lib.orc_force.restype = ctypes.c_int
         lib.orc_force.argtypes = ([i64, d] + [P] * 7 + [P] * 6 + [d, i64, P]
                                   + [P] * 6)
+        lib.orc_grav_p2p.restype = ctypes.c_int
+        lib.orc_grav_p2p.argtypes = [i64, d, P, P, P, P, i64, d, d, i64, P, P, P, P, P]
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_num_threads.argtypes = []
         _lib = lib
@@ -450,3 +456,18 @@ def step_bins(s: State, acc: dict, dt_max: float, n_bins: int,
             kick(idx, bins)  # opening half kick of the next step
     stats = dict(floors=floors, substeps=substeps, active=updates, over=over, margin=margin, bins=bins)
     return n2, st, stats
+
+
+def grav_p2p(s: State, nc: int, G: float = 1.0, eps: float = 0.0, targets=None) -> dict:
+    """Near-field gravity of Sec. 3.2 (Eq. 3, Plummer-softened, minimal image): for
+    each target, the sum over every other particle in its own cell and the 26
+    adjacent cells of the periodic nc^3 grid.  Returns a (nt, 3) and phi (nt)."""
+    lib = _load()
+    t, nt = _targets(s.n, targets)
+    a = np.zeros((3, nt))
+    phi = np.zeros(nt)
+    rc = lib.orc_grav_p2p(s.n, float(s.box), _p(_f64(s.x)), _p(_f64(s.y)), _p(_f64(s.z)), _p(_f64(s.m)),
+                          int(nc), float(G), float(eps), nt, _p(t), _p(a[0]), _p(a[1]), _p(a[2]), _p(phi))
+    if rc:
+        raise RuntimeError(f"orc_grav_p2p failed ({rc})")
+    return {"a": np.ascontiguousarray(a.T), "phi": phi}

@@ -3,7 +3,8 @@
  *
  * A plain, slow, FP64, brute-force O(N^2) CPU restatement of the SPH sums of
  * Theuns, Chalk, Schaller & Gonnet 2015 ("Swift: task-based hydrodynamics and
- * gravity for cosmological simulations"), Sec. 2.  Only tests/, the smoke check
+ * gravity for cosmological simulations"), Sec. 2, and of the near-field part of
+ * its gravity (Sec. 3.2, Eq. 3; see orc_grav_p2p).  Only tests/, the smoke check
  * of __graft_entry__ and the CPU-baseline leg of bench.py may load this file.
  * The CUDA library never includes, links or calls it, and it shares no code
  * with the CUDA library.
@@ -380,6 +381,79 @@ int orc_force(int64_t n, double box, const double *x, const double *y, const dou
         vsig[t] = vs;
         if (n_pairs) n_pairs[t] = cnt;
     }
+    return 0;
+}
+
+/* ---- gravity near field (Sec. 3.2, Eq. 3) ----
+ * The tree walk of Sec. 3.2 ends in two kinds of tasks: a node against the
+ * multipole of a distant node, and "all particles in one node interact with all
+ * particles in a nearby node".  This is the second kind, with readings (not in the
+ * paper): the nodes are the cells of the periodic nc^3 grid of orc_cell_key, and a
+ * particle's nearby nodes are its own cell and the 26 cells adjacent to it (each
+ * cell index differs by 0 or 1 modulo nc; for nc <= 3 that is every cell); each
+ * pair takes the minimal-image separation (the periodic replicas Eq. 3 mentions);
+ * Eq. 3 is softened with the Plummer length eps (eps = 0 is Eq. 3 as printed, and
+ * then a pair at zero separation contributes nothing):
+ *   a_i   = -G sum_{j != i, near} m_j (r_i - r_j) / (|r_i - r_j|^2 + eps^2)^(3/2)
+ *   phi_i = -G sum_{j != i, near} m_j / (|r_i - r_j|^2 + eps^2)^(1/2)
+ * Every target runs over ALL j in index order and tests the pair's cells. */
+static inline int cell_adjacent(int64_t a, int64_t b, int64_t nc)
+{
+    int64_t d = a - b;
+    if (d < 0) d = -d;
+    return d == 0 || d == 1 || d == nc - 1;
+}
+
+int orc_grav_p2p(int64_t n, double box, const double *x, const double *y, const double *z, const double *m,
+                 int64_t nc, double G, double eps, int64_t nt, const int64_t *targets, double *ax, double *ay,
+                 double *az, double *phi)
+{
+    if (nc < 1) return 1;
+    int64_t *cx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *cy = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *cz = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!cx || !cy || !cz) {
+        free(cx);
+        free(cy);
+        free(cz);
+        return 2;
+    }
+    for (int64_t j = 0; j < n; ++j) {
+        const int64_t k = orc_cell_key(x[j], y[j], z[j], box, nc);
+        cx[j] = k % nc;
+        cy[j] = (k / nc) % nc;
+        cz[j] = k / (nc * nc);
+    }
+    const double eps2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; ++t) {
+        const int64_t i = targets ? targets[t] : t;
+        double sx = 0.0, sy = 0.0, sz = 0.0, sp = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            if (!cell_adjacent(cx[i], cx[j], nc) || !cell_adjacent(cy[i], cy[j], nc) ||
+                !cell_adjacent(cz[i], cz[j], nc))
+                continue;
+            const double dx = min_image(x[i] - x[j], box);
+            const double dy = min_image(y[i] - y[j], box);
+            const double dz = min_image(z[i] - z[j], box);
+            const double r2 = dx * dx + dy * dy + dz * dz + eps2;
+            if (r2 == 0.0) continue; /* eps = 0, coincident particles */
+            const double rinv = 1.0 / sqrt(r2);
+            const double rinv3 = rinv * rinv * rinv;
+            sx -= G * m[j] * dx * rinv3;
+            sy -= G * m[j] * dy * rinv3;
+            sz -= G * m[j] * dz * rinv3;
+            sp -= G * m[j] * rinv;
+        }
+        ax[t] = sx;
+        ay[t] = sy;
+        az[t] = sz;
+        phi[t] = sp;
+    }
+    free(cx);
+    free(cy);
+    free(cz);
     return 0;
 }
 
