@@ -588,6 +588,87 @@ def run_bins(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------- gravity near field
+
+
+FLOP_GRAV_PAIR = 20  # 3 FADD + 3 FFMA (r^2) + rsqrt + FMUL + FADD (phi) + 2 FMUL + 3 FFMA (a); FFMA = 2
+
+
+def run_gravity(args):
+    """Near-field gravity (sph_gravity_p2p, Sec. 3.2, Eq. 3) on the Sedov-Taylor
+    128^3 particles and the SPH path's own cell grid (cell side 1.25 x max h): every
+    particle against every other particle of its own and the 26 adjacent cells.
+    L2 is flushed (a 256 MB write) before every timed launch; each launch is timed
+    by CUDA events on the library's stream."""
+    import torch
+    from paper_1508_00115_gb300 import binding
+
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    binding.lib()
+    d = workload()
+    n = int(d["x"].size)
+    stream = torch.cuda.Stream()
+    ctx = binding.Context(n, device=local, stream=stream.cuda_stream, flags=binding.SPH_FLAG_TIMING,
+                          tile_width=args.tile_width or 32, cell_factor=args.cell_factor or 1.25)
+    parts = binding.Particles(d)
+    ctx.build_cells(parts)
+    out = None
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            out = ctx.gravity(1.0, 0.0, out)
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    sampler = ClockSampler(_gpu_id(local)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    ms = 0.0
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.gravity(1.0, 0.0, out)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    clocks = sampler.stop() if sampler else None
+    ms = _max_over_ranks(ms, dist)
+    st = ctx.stats()
+    pairs = st["grav_pairs"] / args.steps
+    sec = ms / 1e3
+    props = torch.cuda.get_device_properties(local)
+    peak, peak_how = fp32_peak_tflops(props.multi_processor_count, _peaks(), stream.cuda_stream)
+    achieved = pairs * FLOP_GRAV_PAIR * args.steps / sec / 1e12
+    res = {"metric": "gravity near-field pair interactions/s (Sec. 3.2 node-node tasks), 1 GB300",
+           "value": world * pairs * args.steps / sec, "unit": "pair interactions/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "particles_per_s": world * n * args.steps / sec,
+           "path": "sph_gravity_p2p: one launch per step over all tiles of the uniform grid",
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "Sedov-Taylor 128^3 jittered lattice, near-field gravity on the SPH cell grid",
+                      "n_particles": n, "nc": int(st["nc"]), "pairs_per_particle": pairs / n,
+                      "tile_width": int(st["tile_width"]), "eps": 0.0, "l2": "flushed before every launch",
+                      "parallelism": f"replicas x{world}"},
+           "roofline": {"bound": "alu", "kernel": "k_gravity", "achieved": achieved, "peak": peak,
+                        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_how,
+                        "flop_per_pair": FLOP_GRAV_PAIR, "launches": args.steps,
+                        "avg_launch_ms": ms / args.steps},
+           "gpu_launches": int(st["kernel_launches"]), "clocks": clocks}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 # ------------------------------------------------- adaptive-cell workloads
 
 
@@ -826,7 +907,7 @@ def main():
     ap.add_argument("--cpu-force-targets", type=int, default=48)
     ap.add_argument("--tile-width", type=int, default=0, help="16 or 32 (0: autotuned)")
     ap.add_argument("--cell-factor", type=float, default=0.0, help=">= 1 (0: autotuned)")
-    ap.add_argument("--workload", choices=["sedov", "clustered", "boxes", "sedov-bins"], default="sedov",
+    ap.add_argument("--workload", choices=["sedov", "clustered", "boxes", "sedov-bins", "gravity"], default="sedov",
                     help="sedov: Sedov-Taylor 128^3 (the headline); clustered: clustered halo field on "
                          "adaptive cells; boxes: batched uneven boxes on adaptive cells; sedov-bins: "
                          "individual time-steps against global steps on the Sedov workload")
@@ -845,6 +926,8 @@ def main():
         run_reference(args)
     elif args.workload == "sedov-bins":
         run_bins(args)
+    elif args.workload == "gravity":
+        run_gravity(args)
     elif args.workload != "sedov":
         run_adaptive(args)
     else:

@@ -203,6 +203,9 @@ typedef struct {
     int64_t graph_steps;       /* steps replayed from a captured graph (sph_steps)   */
     int32_t leaf_max;          /* adaptive cells: leaf size in use (0: uniform grid) */
     int64_t hp_samples;        /* learned h: (features, target) pairs collected so far */
+    int64_t grav_passes;       /* gravity near-field launches (sph_gravity_p2p)       */
+    int64_t grav_pairs;        /* gravity near-field pair interactions (j != i)        */
+    double t_grav_ms;          /* summed device time of gravity launches (TIMING)     */
 } sph_stats;
 
 /* Fill *p with the defaults: gamma 5/3, n_ngb 48, h_tol 1e-4, alpha 0.8, cfl 0.1,
@@ -415,6 +418,29 @@ int sph_hpredict_collect(sph_ctx *ctx, float *dev_feats, float *dev_target, int6
 #define SPH_SORT_STATIC_MAX_N 262144
 int sph_sort_keys_static(const uint32_t *keys_in, uint32_t *keys_out, uint32_t *perm_out, int64_t n,
                          int32_t key_bits, void *cuda_stream);
+
+/* Near-field gravity (Sec. 3.2, Eq. 3): the node-node tasks of the paper's tree walk
+ * in which all particles of one node interact with all particles of a nearby node,
+ * run on the cells of the current uniform grid.  For every particle i,
+ *   a_i   = -G sum_j m_j (r_i - r_j) / (|r_i - r_j|^2 + eps^2)^(3/2)
+ *   phi_i = -G sum_j m_j / (|r_i - r_j|^2 + eps^2)^(1/2)
+ * over every j != i in i's own cell and the 26 cells adjacent to it (periodic, the
+ * minimal-image separation; with 3 cells per side that is every particle of the
+ * box).  eps is the Plummer softening length; eps = 0 is Eq. 3 as printed, and then
+ * a pair at zero separation contributes nothing.  The far field (multipoles of
+ * non-adjacent cells) is not computed.  Batched boxes: each box on its own grid.
+ *   ax, ay, az  device FP32[n], caller-owned: the acceleration of every slot, in
+ *               the current cell order (that of sph_build_cells)
+ *   phi         device FP32[n] or NULL: the potential
+ * FP32 arithmetic on the cell-relative positions of the last build, masses from m
+ * at that build; the 27 cell sums of a particle are added with compensation.  A
+ * separation component is off by up to ~3.5 x 2^-24 x cell side, so a softened
+ * pair's force by at most m_j x that / eps^3, an unsoftened one by ~2 x that / r of
+ * itself: close unsoftened pairs carry large relative errors.
+ * Requires sph_build_cells on the current positions, uniform grid (SPH_ERR_STATE
+ * otherwise, or with SPH_FLAG_ADAPTIVE); SPH_ERR_INVALID_ARG for eps < 0, non-finite
+ * G or eps, or null outputs.  Asynchronous. */
+int sph_gravity_p2p(sph_ctx *ctx, double G, double eps, float *ax, float *ay, float *az, float *phi);
 
 /* Throughput of the plain FP32 FMA pipes on the current device: the ceiling of the
  * pair kernels, whose sums are not dense contractions (the tensor cores do not

@@ -98,7 +98,8 @@ class sph_stats(ctypes.Structure):
                 ("t_build_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("tile_width", ctypes.c_int32), ("cell_factor", ctypes.c_float),
                 ("graph_steps", ctypes.c_int64), ("leaf_max", ctypes.c_int32),
-                ("hp_samples", ctypes.c_int64)]
+                ("hp_samples", ctypes.c_int64), ("grav_passes", ctypes.c_int64),
+                ("grav_pairs", ctypes.c_int64), ("t_grav_ms", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -151,6 +152,7 @@ def lib(build_if_missing: bool = True):
             "sph_hpredict_train": (C, [P, P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64,
                                        ctypes.POINTER(ctypes.c_float)]),
             "sph_hpredict_collect": (C, [P, P, P, ctypes.c_int64]),
+            "sph_gravity_p2p": (C, [P, ctypes.c_double, ctypes.c_double, P, P, P, P]),
             "sph_fp32_peak": (C, [P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_float)]),
             "sph_get_stats": (C, [P, ctypes.POINTER(sph_stats)]),
@@ -307,6 +309,11 @@ def sph_hpredict_collect(ctx, feats, target, capacity: int) -> int:
                                              _ptr(target) if target is not None else None, int(capacity)), ctx)
 
 
+def sph_gravity_p2p(ctx, G: float, eps: float, ax, ay, az, phi=None) -> int:
+    return _check(lib().sph_gravity_p2p(ctx, float(G), float(eps), _ptr(ax), _ptr(ay), _ptr(az),
+                                        _ptr(phi) if phi is not None else None), ctx)
+
+
 def sph_fp32_peak(stream: int | None = None, iters: int = 1 << 15, reps: int = 3) -> tuple[float, float]:
     """Measured FP32 FMA throughput of the current device: (TFLOP/s, ms of the
     fastest launch)."""
@@ -423,6 +430,17 @@ class Context:
 
     def step_host(self, parts: Particles, dt: float = 0.0):
         return sph_step_host(self.h, parts.struct(), dt)
+
+    def gravity(self, G: float = 1.0, eps: float = 0.0, out=None, with_phi: bool = True):
+        """Near-field gravity on the current cells (sph_gravity_p2p) into device
+        tensors (a dict ax, ay, az, phi of FP32 CUDA tensors, allocated if None);
+        returns that dict."""
+        import torch
+        n = int(self.params.n)
+        if out is None:
+            out = {k: torch.zeros(max(n, 1), dtype=torch.float32, device="cuda") for k in ("ax", "ay", "az", "phi")}
+        sph_gravity_p2p(self.h, G, eps, out["ax"], out["ay"], out["az"], out["phi"] if with_phi else None)
+        return out
 
     def permutation(self) -> np.ndarray:
         import torch

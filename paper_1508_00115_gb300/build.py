@@ -18,7 +18,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsph.so")
 SOURCES = ["sph_api.cu", "sph_cells.cu", "sph_pairs.cu", "sph_integrate.cu", "sph_tree.cu", "sph_hpredict.cu",
-           "sph_probe.cu"]
+           "sph_gravity.cu", "sph_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "--extended-lambda",
          "-I", INCLUDE]

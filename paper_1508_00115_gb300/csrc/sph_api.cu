@@ -1014,6 +1014,19 @@ int sph_step_host(sph_ctx *ctx, sph_particles *hp, double dt, double *dt_used, s
     return finish_call(ctx, SPH_OK);
 }
 
+int sph_gravity_p2p(sph_ctx *ctx, double G, double eps, float *ax, float *ay, float *az, float *phi)
+{
+    if (!ctx) return SPH_ERR_INVALID_ARG;
+    if (!isfinite(G) || !isfinite(eps) || eps < 0.0)
+        return fail(ctx, SPH_ERR_INVALID_ARG, "G and eps must be finite, eps >= 0");
+    if (ctx->n > 0 && (!ax || !ay || !az)) return fail(ctx, SPH_ERR_INVALID_ARG, "null acceleration array");
+    if (ctx->adaptive)
+        return fail(ctx, SPH_ERR_STATE, "the gravity near field runs on the uniform grid (not SPH_FLAG_ADAPTIVE)");
+    if (!ctx->built) return fail(ctx, SPH_ERR_STATE, "sph_gravity_p2p needs sph_build_cells on the current positions");
+    if (ctx->n == 0) return SPH_OK;
+    return run_gravity_pass(ctx, G, eps, ax, ay, az, phi);
+}
+
 int sph_get_permutation(sph_ctx *ctx, int64_t *dev_perm)
 {
     if (!ctx || !dev_perm) return SPH_ERR_INVALID_ARG;
@@ -1051,7 +1064,7 @@ int sph_get_stats(sph_ctx *ctx, sph_stats *s)
     if (!ctx || !s) return SPH_ERR_INVALID_ARG;
     int rc = read_counters(ctx);
     if (rc) return rc;
-    double t[3] = {0, 0, 0};
+    double t[4] = {0, 0, 0, 0};
     for (Timer &tm : ctx->timers) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, tm.a, tm.b) == cudaSuccess) t[tm.kind] += ms;
@@ -1065,6 +1078,8 @@ int sph_get_stats(sph_ctx *ctx, sph_stats *s)
     st.t_density_ms = t[0];
     st.t_force_ms = t[1];
     st.t_build_ms = t[2];
+    st.t_grav_ms = t[3];
+    st.grav_pairs = (int64_t)ctx->h_counters[C_GPAIRS];
     st.tile_width = ctx->tile_w;
     st.cell_factor = ctx->p.cell_factor;
     st.leaf_max = ctx->adaptive ? ctx->leaf_max : 0;
@@ -1080,6 +1095,7 @@ int sph_reset_stats(sph_ctx *ctx)
     for (Timer &t : ctx->timers) ctx->free_timers.push_back(t);
     ctx->timers.clear();
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_DPAIRS, 0, 6 * sizeof(unsigned long long), ctx->stream));
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_GPAIRS, 0, sizeof(unsigned long long), ctx->stream));
     int nc = ctx->st.nc;
     int64_t ncell = ctx->st.n_cells;
     double cs = ctx->st.cell_size;

@@ -55,7 +55,8 @@ enum Counter {
     C_BINMAX = 14,    // individual time-steps: deepest bin in use
     C_BINOVER = 15,   // individual time-steps: CFL steps below the smallest bin's step
     C_PREC = 16,      // uniform grid: a converged h below cell side / SPH_FRAME_RATIO
-    C_NCOUNTERS = 17
+    C_GPAIRS = 17,    // gravity near field: pair interactions
+    C_NCOUNTERS = 18
 };
 
 // Cell grid of one periodic box (every box has side box_size; boxes are batched
@@ -169,7 +170,7 @@ struct Grid {
 
 struct Timer {
     cudaEvent_t a, b;
-    int kind;  // 0 density, 1 force, 2 build
+    int kind;  // 0 density, 1 force, 2 build, 3 gravity
 };
 
 }  // namespace sph
@@ -363,6 +364,7 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool ac
 int compact_active_tiles(sph_ctx *ctx);                                    // sph_pairs.cu
 int compact_active_leaf_tiles(sph_ctx *ctx);  // adaptive cells: tiles of active targets only  // sph_tree.cu
 int run_force_pass(sph_ctx *ctx, sph_particles *parts, bool active_list = false);  // sph_pairs.cu
+int run_gravity_pass(sph_ctx *ctx, double G, double eps, float *ax, float *ay, float *az, float *phi);  // sph_gravity.cu
 int sync_h(sph_ctx *ctx, sph_particles *parts);                            // sph_pairs.cu
 int kick(sph_ctx *ctx, sph_particles *parts);    // by *d_dt / 2           // sph_integrate.cu
 int drift(sph_ctx *ctx, sph_particles *parts);   // by *d_dt               // sph_integrate.cu
