@@ -180,11 +180,12 @@ def _gpu_id(dev: int) -> str:
         return vis.split(",")[dev] if vis else str(dev)
 
 
-def _traffic(kernel: str):
+def _traffic(kernel: str, summary: str | None = None):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if it was
-    taken on the current sources of the pair kernels (else None)."""
+    taken on the current sources of that kernel (else None)."""
     from paper_1508_00115_gb300 import build as b
-    path = os.path.join(ROOT, "profiles", f"{kernel}_sedov128.md")
+    path = os.path.join(ROOT, "profiles", summary or f"{kernel}_sedov128.md")
+    digest = b.gravity_kernel_digest() if kernel == "gravity" else b.pair_kernel_digest()
     try:
         text = open(path).read()
     except OSError:
@@ -196,7 +197,7 @@ def _traffic(kernel: str):
             src = line.split(":", 1)[1].split()[0]
         if line.startswith("dram_bytes_per_launch:"):
             val = float(line.split(":", 1)[1].split()[0])
-    if src is None or val is None or src != b.pair_kernel_digest():
+    if src is None or val is None or src != digest:
         return None
     return val
 
@@ -619,9 +620,12 @@ def run_gravity(args):
     ctx.build_cells(parts)
     out = None
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    # Plummer softening: by default 1/25 of the mean interparticle spacing (a common
+    # choice in cosmological runs); --eps 0 runs Eq. 3 unsoftened
+    eps = args.eps if args.eps >= 0 else (1.0 / n) ** (1.0 / 3.0) / 25.0
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            out = ctx.gravity(1.0, 0.0, out)
+            out = ctx.gravity(1.0, eps, out)
     torch.cuda.synchronize()
     ctx.reset_stats()
     sampler = ClockSampler(_gpu_id(local)) if rank == 0 else None
@@ -635,7 +639,7 @@ def run_gravity(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ctx.gravity(1.0, 0.0, out)
+            ctx.gravity(1.0, eps, out)
             e1.record(stream)
         torch.cuda.synchronize()
         ms += e0.elapsed_time(e1)
@@ -655,10 +659,12 @@ def run_gravity(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "Sedov-Taylor 128^3 jittered lattice, near-field gravity on the SPH cell grid",
                       "n_particles": n, "nc": int(st["nc"]), "pairs_per_particle": pairs / n,
-                      "tile_width": int(st["tile_width"]), "eps": 0.0, "l2": "flushed before every launch",
+                      "tile_width": int(st["tile_width"]), "eps": eps, "l2": "flushed before every launch",
                       "parallelism": f"replicas x{world}"},
            "roofline": {"bound": "alu", "kernel": "k_gravity", "achieved": achieved, "peak": peak,
-                        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_how,
+                        "unit": "TFLOP/s", "frac": achieved / peak,
+                        "traffic": _traffic("gravity", "gravity_sedov128.md") if abs(eps - 3.125e-4) < 1e-9
+                        and int(st["tile_width"]) == 32 else None, "peak_source": peak_how,
                         "flop_per_pair": FLOP_GRAV_PAIR, "launches": args.steps,
                         "avg_launch_ms": ms / args.steps},
            "gpu_launches": int(st["kernel_launches"]), "clocks": clocks}
@@ -912,6 +918,8 @@ def main():
                          "adaptive cells; boxes: batched uneven boxes on adaptive cells; sedov-bins: "
                          "individual time-steps against global steps on the Sedov workload")
     ap.add_argument("--levels", type=int, default=8, help="sedov-bins: time-bin levels")
+    ap.add_argument("--eps", type=float, default=-1.0,
+                    help="gravity: Plummer softening (default: 1/25 of the mean spacing; 0: unsoftened)")
     ap.add_argument("--side", type=int, default=256, help="clustered: particles per side")
     ap.add_argument("--n-boxes", type=int, default=512, help="boxes: number of boxes")
     ap.add_argument("--leaf-max", type=int, default=0, help="adaptive: leaf size (0: autotuned)")

@@ -427,7 +427,7 @@ int sph_sort_keys_static(const uint32_t *keys_in, uint32_t *keys_out, uint32_t *
  * over every j != i in i's own cell and the 26 cells adjacent to it (periodic, the
  * minimal-image separation; with 3 cells per side that is every particle of the
  * box).  eps is the Plummer softening length; eps = 0 is Eq. 3 as printed, and then
- * a pair at zero separation contributes nothing.  The far field (multipoles of
+ * a pair at zero separation contributes nothing (below 1e-15 box units in FP32).  The far field (multipoles of
  * non-adjacent cells) is not computed.  Batched boxes: each box on its own grid.
  *   ax, ay, az  device FP32[n], caller-owned: the acceleration of every slot, in
  *               the current cell order (that of sph_build_cells)

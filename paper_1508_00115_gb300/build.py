@@ -50,6 +50,14 @@ def _digest(files=None) -> str:
     return h.hexdigest()[:16]
 
 
+GRAVITY_SOURCES = ["sph_gravity.cu", "sph_internal.cuh"]
+
+
+def gravity_kernel_digest() -> str:
+    """Identity of the gravity kernel's sources (ncu figures of k_gravity)."""
+    return _digest(GRAVITY_SOURCES)
+
+
 def pair_kernel_digest() -> str:
     """Identity of the pair kernels' sources: ncu figures of k_density / k_force stay
     valid while it is unchanged."""

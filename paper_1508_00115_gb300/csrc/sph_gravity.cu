@@ -7,14 +7,16 @@
 // particle of its own cell and of the 26 adjacent cells (periodic, minimal image).
 //
 // Work decomposition: the SPH path's tiles (up to TW targets of one cell, one lane
-// per target) handed out by the same ticket counter.  For each of the 27 cells a
-// tile's lanes load TW sources at a time (one coalesced float4 each), shifted into
-// the tile's cell frame, into shared memory; every lane then runs over all staged
-// sources (broadcast reads).  No distance test, no pruning: each staged source is an
-// interaction, so the inner loop is straight-line FP32 arithmetic -- 3 FADD, 6 FFMA,
-// 3 FMUL, 1 FADD and one MUFU reciprocal square root per pair.  The terms of one
-// cell are summed plainly and the 27 cell sums added with Kahan compensation; the
-// summation order of a target never depends on which warp runs its tile.
+// per target) handed out by the same ticket counter.  The 27 cells' particles form
+// one source stream per tile; its lanes load TW stream positions at a time (one
+// coalesced float4 each, across cell boundaries, so that only the stream's last
+// chunk has pads), shifted into the tile's cell frame, into shared memory; every
+// lane then runs over all staged sources (broadcast reads).  No distance test, no
+// pruning: each staged source is an interaction, so the inner loop is straight-line
+// FP32 arithmetic -- 3 FADD, 3 FFMA for r^2, one MUFU reciprocal square root, 3 FMUL,
+// 1 FADD and 3 FFMA per pair.  The terms of 128 staged sources are summed plainly and
+// the batch sums added with Kahan compensation; the summation order of a target
+// never depends on which warp runs its tile.
 #include <algorithm>
 
 #include "sph_internal.cuh"
@@ -24,6 +26,10 @@ namespace sph {
 constexpr int kGravThreads = 256;
 // staging pads: far away (r^2 overflows to +inf, so rsqrt gives 0) and massless
 constexpr float kGravFar = 1e30f;
+// smallest squared separation (box units) an unsoftened pair contributes at, and the
+// smallest eps^2 the softened kernel runs with: FP32 positions relative to a cell
+// centre cannot resolve separations near 1e-15 anyway
+constexpr float kGravMinR2 = 1e-30f;
 
 struct GravArgs {
     const float4 *__restrict__ pos4;  // {x, y, z} relative to the cell centre, h
@@ -39,13 +45,26 @@ struct GravArgs {
 
 __device__ __forceinline__ int wrapg(int j, int nc) { return j < 0 ? j + nc : (j >= nc ? j - nc : j); }
 
-// SOFT: eps > 0 (the target's own term is masked by its staged index); otherwise
-// pairs at zero separation (the target itself, coincident particles) are dropped by
-// their r^2
+// 1/sqrt(x) as the one MUFU instruction, with denormal inputs and results flushed
+// to zero: the squared separations here are at least eps^2 >= kGravMinR2 (softened)
+// or, unsoftened, taken only above kGravMinR2 -- never denormal -- so nothing else is
+// needed around it; rsqrt(+inf) = 0 keeps the staging pads inert.
+__device__ __forceinline__ float rsqrt_mufu(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// SOFT: eps^2 >= kGravMinR2 -- every staged source enters the sums, and the target's
+// own term (exactly m_i / eps: its separation is exactly 0) is taken out once at the
+// end; otherwise pairs closer than sqrt(kGravMinR2) (the target itself, coincident
+// particles) are dropped by their r^2.
 template <int TW, bool SOFT>
 __global__ void __launch_bounds__(kGravThreads) k_gravity(GravArgs a)
 {
     constexpr int TPW = 32 / TW;
+    constexpr int kFlush = 128 / TW;  // chunks per compensated batch (128 sources)
     __shared__ float4 stage[kGravThreads / 32][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int sub = lane / TW, tl = lane % TW;
@@ -71,74 +90,100 @@ __global__ void __launch_bounds__(kGravThreads) k_gravity(GravArgs a)
         const float L = bx.L32;
         const int ca = tile.x - bx.cell_off;
         const int ix = ca % nc, iy = (ca / nc) % nc, iz = ca / (nc * nc);
-        // the 27 cell ranges, fetched at once: lane tl holds cells tl and tl + TW;
-        // cell o is at offset (o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1), o = 13 its own
-        int cs0 = 0, ce0 = 0, cs1 = 0, ce1 = 0;
-        if (tile.z > 0) {
-            if (tl < 27) {
-                const int cb = bx.cell_off + (wrapg(iz + tl / 9 - 1, nc) * nc + wrapg(iy + (tl / 3) % 3 - 1, nc)) * nc +
-                               wrapg(ix + tl % 3 - 1, nc);
-                cs0 = a.cell_start[cb];
-                ce0 = a.cell_start[cb + 1];
+        // The sources of a tile as one stream: the 27 cells in order o = 0..26 (cell o
+        // at offset (o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1), o = 13 the tile's own),
+        // each cell's particles in slot order.  Lane tl describes cell tl (and, for
+        // TW = 16, cell tl + 16): where the cell ends in the stream, and slot - stream
+        // position for its particles.
+        int endA = 0, offA = 0, endB = 0, offB = 0;
+        {
+            int bsA = 0, cA = 0, bsB = 0, cB = 0;
+            if (tile.z > 0) {
+                if (tl < 27) {
+                    const int cb = bx.cell_off +
+                                   (wrapg(iz + tl / 9 - 1, nc) * nc + wrapg(iy + (tl / 3) % 3 - 1, nc)) * nc +
+                                   wrapg(ix + tl % 3 - 1, nc);
+                    bsA = a.cell_start[cb];
+                    cA = a.cell_start[cb + 1] - bsA;
+                }
+                if (tl + TW < 27) {
+                    const int o2 = tl + TW;
+                    const int cb = bx.cell_off +
+                                   (wrapg(iz + o2 / 9 - 1, nc) * nc + wrapg(iy + (o2 / 3) % 3 - 1, nc)) * nc +
+                                   wrapg(ix + o2 % 3 - 1, nc);
+                    bsB = a.cell_start[cb];
+                    cB = a.cell_start[cb + 1] - bsB;
+                }
             }
-            if (tl + TW < 27) {
-                const int o2 = tl + TW;
-                const int cb = bx.cell_off + (wrapg(iz + o2 / 9 - 1, nc) * nc + wrapg(iy + (o2 / 3) % 3 - 1, nc)) * nc +
-                               wrapg(ix + o2 % 3 - 1, nc);
-                cs1 = a.cell_start[cb];
-                ce1 = a.cell_start[cb + 1];
+            endA = cA;
+            endB = cB;
+#pragma unroll
+            for (int d = 1; d < TW; d <<= 1) {
+                const int vA = __shfl_up_sync(kFull, endA, d, TW), vB = __shfl_up_sync(kFull, endB, d, TW);
+                if (tl >= d) {
+                    endA += vA;
+                    endB += vB;
+                }
             }
+            endB += __shfl_sync(kFull, endA, TW - 1, TW);
+            offA = bsA - (endA - cA);
+            offB = bsB - (endB - cB);
         }
+        const int total = __shfl_sync(kFull, TW == 32 ? endA : endB, TW - 1, TW);
+        // this lane's cursor: stream cell cur, its end and slot offset
+        int cur = 0;
+        int cend = __shfl_sync(kFull, endA, 0, TW), coff = __shfl_sync(kFull, offA, 0, TW);
         float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f, sz = 0.f, cz = 0.f, sp = 0.f, cp = 0.f;
-        int nsrc = 0;
-        for (int o = 0; o < 27; ++o) {
-            const int src = o < TW ? o : o - TW;
-            const int bs = __shfl_sync(kFull, o < TW ? cs0 : cs1, src, TW);
-            const int be = __shfl_sync(kFull, o < TW ? ce0 : ce1, src, TW);
-            nsrc += be - bs;
-            const float shx = (float)(o % 3 - 1) * L, shy = (float)((o / 3) % 3 - 1) * L,
-                        shz = (float)(o / 9 - 1) * L;
-            const int nch = (int)__reduce_max_sync(kFull, (unsigned)((be - bs + TW - 1) / TW));
-            float bxs = 0.f, bys = 0.f, bzs = 0.f, bps = 0.f;  // this cell's terms
-            // the sum over the staged sources: straight-line, or with the target's own
-            // slot masked (own cell, softened: its term would be m_i / eps)
-            auto sum = [&](int self) {
-#pragma unroll 8
-                for (int k = 0; k < TW; ++k) {
-                    const float4 q = sA[k];
-                    const float dx = q.x - pi.x, dy = q.y - pi.y, dz = q.z - pi.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, a.eps2)));
-                    float inv = rsqrtf(r2);
-                    if (!SOFT) inv = r2 > 0.f ? inv : 0.f;
-                    const float mj = (SOFT && k == self) ? 0.f : q.w;
-                    const float mi = mj * inv;
-                    bps += mi;
-                    const float mi3 = mi * inv * inv;
-                    bxs = fmaf(mi3, dx, bxs);
-                    bys = fmaf(mi3, dy, bys);
-                    bzs = fmaf(mi3, dz, bzs);
-                }
-            };
-            for (int ch = 0; ch < nch; ++ch) {
-                const int j = bs + ch * TW + tl;
-                float4 s = make_float4(kGravFar, kGravFar, kGravFar, 0.f);
-                if (j < be) {
-                    const float4 p = __ldg(a.pos4 + j);
-                    s = make_float4(p.x + shx, p.y + shy, p.z + shz, __ldg(&a.vel4[j].w));
-                }
-                __syncwarp();
-                sA[tl] = s;
-                __syncwarp();
-                if (SOFT && o == 13) sum(i - (bs + ch * TW));
-                else sum(-1);
+        float bxs = 0.f, bys = 0.f, bzs = 0.f, bps = 0.f;  // terms of the current batch
+        const int nch = (int)__reduce_max_sync(kFull, (unsigned)((total + TW - 1) / TW));
+        for (int ch = 0; ch < nch; ++ch) {
+            const int q = ch * TW + tl;
+            // move the cursor to the cell holding stream position q (skipping empty cells)
+            while (__any_sync(kFull, q < total && q >= cend)) {
+                if (q < total && q >= cend) ++cur;
+                const int src = cur < TW ? cur : cur - TW;
+                const int eA = __shfl_sync(kFull, endA, src, TW), eB = __shfl_sync(kFull, endB, src, TW);
+                const int fA = __shfl_sync(kFull, offA, src, TW), fB = __shfl_sync(kFull, offB, src, TW);
+                cend = cur < TW ? eA : eB;
+                coff = cur < TW ? fA : fB;
             }
-            kahan_add(sx, cx, bxs);
-            kahan_add(sy, cy, bys);
-            kahan_add(sz, cz, bzs);
-            kahan_add(sp, cp, bps);
+            float4 sv = make_float4(kGravFar, kGravFar, kGravFar, 0.f);
+            if (q < total) {
+                const int j = coff + q;
+                const float4 p = __ldg(a.pos4 + j);
+                sv = make_float4(p.x + (float)(cur % 3 - 1) * L, p.y + (float)((cur / 3) % 3 - 1) * L,
+                                 p.z + (float)(cur / 9 - 1) * L, __ldg(&a.vel4[j].w));
+            }
+            __syncwarp();
+            sA[tl] = sv;
+            __syncwarp();
+#pragma unroll 8
+            for (int k = 0; k < TW; ++k) {
+                const float4 qk = sA[k];
+                const float dx = qk.x - pi.x, dy = qk.y - pi.y, dz = qk.z - pi.z;
+                const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, a.eps2)));
+                float inv = rsqrt_mufu(r2);
+                if (!SOFT) inv = r2 > kGravMinR2 ? inv : 0.f;
+                const float mi = qk.w * inv;
+                bps += mi;
+                const float mi3 = mi * inv * inv;
+                bxs = fmaf(mi3, dx, bxs);
+                bys = fmaf(mi3, dy, bys);
+                bzs = fmaf(mi3, dz, bzs);
+            }
+            if ((ch + 1) % kFlush == 0 || ch == nch - 1) {
+                kahan_add(sx, cx, bxs);
+                kahan_add(sy, cy, bys);
+                kahan_add(sz, cz, bzs);
+                kahan_add(sp, cp, bps);
+                bxs = bys = bzs = bps = 0.f;
+            }
         }
         if (!valid) continue;
-        acc_pairs += (unsigned long long)(nsrc - 1);
+        // the target's own term: zero separation, so exactly m_i rsqrt(eps^2) in phi
+        // and nothing in a
+        if (SOFT) kahan_add(sp, cp, -(__ldg(&a.vel4[i].w) * rsqrt_mufu(a.eps2)));
+        acc_pairs += (unsigned long long)(total - 1);
         // a_i = -G sum m_j (r_i - r_j) / (r^2 + eps^2)^(3/2): the sums above run over
         // r_j - r_i, hence +G
         a.ax[i] = a.G * (sx - cx);
@@ -189,7 +234,7 @@ int run_gravity_pass(sph_ctx *ctx, double G, double eps, float *ax, float *ay, f
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_TICKET, 0, sizeof(unsigned long long), ctx->stream));
     cudaEvent_t end = nullptr;
     timer_begin(ctx, 3, &end);
-    const bool soft = eps > 0.0;
+    const bool soft = a.eps2 >= kGravMinR2;
     int rc;
     if (ctx->tile_w == 32) rc = soft ? launch_gravity<32, true>(ctx, a) : launch_gravity<32, false>(ctx, a);
     else rc = soft ? launch_gravity<16, true>(ctx, a) : launch_gravity<16, false>(ctx, a);
