@@ -1,13 +1,20 @@
-"""Benchmark of the SPH hot path on GB300: KDK steps of the Sedov-Taylor workload.
+"""Benchmark of the SPH hot path on GB300: KDK steps, learned h + batched vs plain.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload sedov|clustered|boxes] [--hpredict]
+                    [--workload headline|sedov|clustered|boxes|sedov-bins|gravity]
 
 One step = one pass of the whole hot path over the particle set: kick, drift,
-cell binning (wrap, key, radix sort, permute), density with the smoothing-length
-iteration, force, kick, and the global reductions (CFL dt, conserved sums).
-Workload: Sedov-Taylor blast on a 128^3 jittered lattice (2,097,152 particles),
-the configuration the throughput is quoted on; inputs resident in HBM.
+cell binning (wrap, key, radix sort, permute, adaptive refinement and neighbour
+lists), density with the smoothing-length iteration, force, kick, and the global
+reductions (CFL dt, conserved sums).
+
+Default (headline) workload: 512 independent periodic boxes of uneven occupancy
+(N log-uniform in [1e3, 2e5], 17.45 M particles, each a uniform background plus
+Plummer spheres) on adaptive cells.  value = the learned-h + batched form (all
+boxes in one context, graph-replayed steps, h iteration from a learned guess
+trained before the timed region); beside it the batched form without the guess
+and the unbatched plain form (one context and host-driven steps per box), from
+the same state at the same h tolerance; inputs resident in HBM.
 
 Prints ONE JSON line (rank 0).  value = particles advanced per second over all
 ranks; the device time is taken with CUDA events on the library's stream,
@@ -18,10 +25,9 @@ rank steps its own replica (the path does not shard across GPUs here).
 bounded sample of the same workload (the oracle is the only other
 implementation of this path), extrapolated to particles/s.
 
---workload clustered / boxes measure the adaptive-cell path on the clustered halo
-field (256^3) and on 512 batched boxes of uneven occupancy; --hpredict adds the
-learned initial h (trained on another seed before the timed region).  These are
-secondary lines: the default run is the Sedov headline.
+Secondary lines: --workload sedov (Sedov-Taylor 128^3 on the uniform grid),
+clustered (256^3 clustered halo field), boxes (the batched boxes, optionally with
+--hpredict), sedov-bins (individual time-steps), gravity (near-field gravity).
 """
 from __future__ import annotations
 
@@ -226,20 +232,32 @@ def clustered_workload(n_side: int = 256, seed: int = 77):
     return d
 
 
+def boxes_sizes(n_boxes: int = 512, seed: int = 91) -> np.ndarray:
+    """Particle counts of the batched boxes: N log-uniform in [1e3, 2e5]."""
+    rng = np.random.default_rng(seed)
+    return np.exp(rng.uniform(np.log(1e3), np.log(2e5), n_boxes)).astype(np.int64)
+
+
+def box_particles(b: int, nb: int, seed: int = 91) -> dict:
+    """Box b of the batched set: a uniform-plus-Plummer mix (70% in max(1, N/1000)
+    halos), masses 1/N, Gaussian velocities of dispersion 0.05."""
+    from paper_1508_00115_gb300 import inputs
+    d = inputs.plummer_mix(int(nb), seed=seed + 10 + b, n_halos=max(1, int(nb) // 1000))
+    return inputs.random_velocities(d, 0.05, seed + 5000 + b)
+
+
 def boxes_workload(n_boxes: int = 512, seed: int = 91):
     """Independent periodic unit boxes, N log-uniform in [1e3, 2e5]; each a
     uniform-plus-Plummer mix (70% in max(1, N/1000) halos), masses 1/N per box."""
     from paper_1508_00115_gb300 import inputs
-    rng = np.random.default_rng(seed)
-    sizes = np.exp(rng.uniform(np.log(1e3), np.log(2e5), n_boxes)).astype(np.int64)
-    parts, offs = [], [0]
+    sizes = boxes_sizes(n_boxes, seed)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    d = {k: np.empty(int(offs[-1])) for k in inputs.FIELDS}
     for b, nb in enumerate(sizes):
-        d = inputs.plummer_mix(int(nb), seed=seed + 10 + b, n_halos=max(1, int(nb) // 1000))
-        d = inputs.random_velocities(d, 0.05, seed + 5000 + b)
-        parts.append(d)
-        offs.append(offs[-1] + int(nb))
-    d = {k: np.concatenate([p[k] for p in parts]) for k in inputs.FIELDS}
-    return d, offs
+        bd = box_particles(b, int(nb), seed)
+        for k in inputs.FIELDS:
+            d[k][offs[b]:offs[b + 1]] = bd[k]
+    return d, [int(o) for o in offs]
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -300,14 +318,28 @@ def _oracle_sample_once(d: dict, n_force: int, seed: int, label: str, local_radi
 
 
 def run_reference(args):
+    """The oracle as it stands, timed on this host's cores: each step a bounded sample
+    of the workload the default arm runs (the largest of the 512 batched boxes, built
+    alone; --workload sedov: the Sedov-Taylor 128^3 particles), extrapolated to
+    particles/s."""
     rank, world, _ = _env_rank()
     if world > 1 and rank != 0:
         return
-    d = workload()
+    if args.workload == "sedov":
+        d = workload()
+        label, local, nf = "Sedov 128^3", False, args.cpu_force_targets
+        wl = "sedov-taylor 128^3 jittered lattice (2097152 particles), bounded oracle sample per step"
+    else:
+        sizes = boxes_sizes(args.n_boxes)
+        b = int(np.argmax(sizes))
+        d = box_particles(b, int(sizes[b]))
+        label, local, nf = f"largest box (N={int(sizes[b])}) of the batched set", True, args.cpu_force_targets // 3
+        wl = (f"{args.n_boxes} periodic boxes, N log-uniform in [1e3, 2e5] (uniform + Plummer mix): bounded oracle "
+              f"sample of the largest box (N={int(sizes[b])}) per step")
     vals = []
     info = None
     for k in range(args.warmup + args.steps):
-        info = oracle_sample(d, n_force=args.cpu_force_targets, seed=100 + k)
+        info = oracle_sample(d, n_force=nf, seed=100 + k, label=label, local_radius=local)
         if k >= args.warmup:
             vals.append(info["value"])
     v = float(np.median(vals)) if vals else 0.0
@@ -315,8 +347,7 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": "sedov-taylor 128^3 jittered lattice (2097152 particles), "
-                                  "bounded oracle sample per step", "n_particles": int(d["x"].size)},
+           "config": {"workload": wl, "n_particles": int(d["x"].size)},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
                             "sample": info["sample"]},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -902,6 +933,302 @@ def run_adaptive(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------- the headline: learned h + batched vs plain
+
+
+def _train_boxes_predictor(binding, n_boxes, local, stream):
+    """Learned h guess for the batched boxes, trained before the timed region on
+    another realisation of the workload (seed 92, a quarter of the boxes): the
+    (features, converged log h ratio) pairs of two steps at h_tol 1e-6, six epochs
+    of Adam.  Returns (weights, floats) and a description."""
+    import torch
+    d, offs = boxes_workload(max(8, n_boxes // 4), seed=92)
+    n = int(d["x"].size)
+    t0 = time.perf_counter()
+    ctx = binding.Context(n, device=local, stream=stream.cuda_stream, box_offsets=offs, h_tol=1e-6, leaf_max=128,
+                          tile_width=32, flags=binding.SPH_FLAG_ADAPTIVE | binding.SPH_FLAG_TREE_H_GUESS)
+    parts = binding.Particles(d)
+    # at h_tol 1e-6 a handful of the ~5 M smoothing lengths may end a step at their
+    # last iterate (the step completes); their targets are noise among millions
+    ok = (binding.SPH_ERR_NOT_CONVERGED,)
+    ctx.step(parts, allow=ok)
+    F = torch.zeros((2 * n, 6), dtype=torch.float32, device="cuda")
+    T = torch.zeros(2 * n, dtype=torch.float32, device="cuda")
+    ctx.hp_collect(F, T, 2 * n)
+    ctx.step(parts, allow=ok)
+    ctx.step(parts, allow=ok)
+    ctx.hp_collect(None, None, 0)
+    ctx.hp_init(1)
+    loss = None
+    for ep in range(6):
+        loss = ctx.hp_train(F, T, epochs=1, lr=1e-3 if ep < 4 else 3e-4, seed=ep + 1)
+    wf = ctx.hp_save()
+    ctx.close()
+    del F, T, parts
+    torch.cuda.empty_cache()
+    return wf, {"trained_on": f"{len(offs) - 1} boxes of seed 92 ({n} particles), two steps at h_tol 1e-6",
+                "samples": 2 * n, "epochs": 6, "final_loss": loss, "seconds": time.perf_counter() - t0}
+
+
+def run_headline(args):
+    """The metric on the largest single-GPU configuration: 512 independent periodic
+    boxes of uneven occupancy (N log-uniform in [1e3, 2e5], clustered: Plummer
+    spheres in a uniform background; 17.45 M particles), KDK steps on adaptive cells.
+
+    value   learned h + batched: every box in one context (one persistent launch per
+            pass for all boxes), whole steps replayed from a CUDA graph, each step's h
+            iteration started from the learned guess (trained before the timed
+            region on another realisation).
+    plain   the same batched graph without the learned guess (the previous h).
+    plain_unbatched  no batching, no learned guess: one context per box, one
+            sph_step call per box and step (the box's own launches, host-driven).
+    All three start from the same state, at the same h_tol (1e-4); the first two
+    alternate over --repeats runs (median reported)."""
+    import torch
+    from paper_1508_00115_gb300 import binding
+
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    binding.lib()
+    t_setup = time.perf_counter()
+    stream = torch.cuda.Stream()
+    wf, pred_info = _train_boxes_predictor(binding, args.n_boxes, local, stream)
+    d, offs = boxes_workload(args.n_boxes)
+    n = int(d["x"].size)
+    nb = len(offs) - 1
+    base = binding.SPH_FLAG_ADAPTIVE | binding.SPH_FLAG_TREE_H_GUESS
+    # warm-up steps on the batched context (the autotuner picks tile width x leaf
+    # size on the first density pass); their end state is every arm's start
+    ctx = binding.Context(n, device=local, stream=stream.cuda_stream, box_offsets=offs,
+                          flags=base | binding.SPH_FLAG_AUTOTUNE)
+    parts = binding.Particles(d)
+    for _ in range(args.warmup):
+        ctx.step(parts)
+    st0 = ctx.stats()
+    tuned = {"tile_width": int(st0["tile_width"]), "leaf_max": int(st0["leaf_max"])}
+    snap = {k: v.clone() for k, v in parts.t.items()}
+    ctx.close()
+    torch.cuda.synchronize()
+    A = binding.SPH_FLAG_ADAPTIVE
+
+    def restore():
+        for k, v in snap.items():
+            parts.t[k].copy_(v)
+
+    def run(flags, graph, steps, sample_clocks=False):
+        restore()
+        c = binding.Context(n, device=local, stream=stream.cuda_stream, box_offsets=offs,
+                            flags=flags | (0 if graph else binding.SPH_FLAG_TIMING), **tuned)
+        if flags & binding.SPH_FLAG_HPREDICT:
+            c.hp_load(*wf)
+        # the first hydro pass on the snapshot (and, for replayed steps, the capture)
+        # outside the timed region
+        if graph:
+            c.steps(parts, 0)
+        else:
+            c.step(parts)
+        c.reset_stats()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        sampler = ClockSampler(_gpu_id(local)) if (sample_clocks and rank == 0) else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fl = 0
+        if graph:
+            _, cons = c.steps(parts, steps)
+            fl = cons["u_floors"]
+        else:
+            for _ in range(steps):
+                _, cons = c.step(parts)
+                fl += cons["u_floors"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        ms_ = _max_over_ranks(e0.elapsed_time(e1), dist)
+        st = c.stats()
+        c.close()
+        return ms_, st, clocks, fl
+
+    learned_ms, plain_ms = [], []
+    st_learned = st_plain = clocks = None
+    floors = 0
+    for r in range(args.repeats):
+        m1, s1, ck, fl = run(A | binding.SPH_FLAG_HPREDICT, True, args.steps, sample_clocks=(r == 0))
+        m2, s2, _, _ = run(A, True, args.steps)
+        learned_ms.append(m1)
+        plain_ms.append(m2)
+        if r == 0:
+            st_learned, st_plain, clocks, floors = s1, s2, ck, fl
+    ms = float(np.median(learned_ms))
+    ms_plain = float(np.median(plain_ms))
+    sec = ms / 1e3
+    value = _throughput(world, n, args.steps, sec)
+    pairs = st_learned["density_pairs"] + st_learned["force_pairs"]
+
+    # host-driven steps with timed kernels: the per-kernel times of the roofline and
+    # the effect of the guess on the h iteration (passes and re-run targets)
+    ms_hl, st_hl, _, _ = run(A | binding.SPH_FLAG_HPREDICT, False, args.steps)
+    ms_hp, st_hp, _, _ = run(A, False, args.steps)
+    learned = {k: {"density_passes_per_step": s_["density_passes"] / args.steps,
+                   "density_targets_per_particle_per_step": s_["density_targets"] / (args.steps * n),
+                   "t_density_ms_per_step": s_["t_density_ms"] / args.steps,
+                   "ms_per_step": m_ / args.steps}
+               for k, (m_, s_) in (("plain", (ms_hp, st_hp)), ("learned", (ms_hl, st_hl)))}
+
+    # plain, unbatched: one context per box, host-driven steps
+    unb = None
+    if args.unbatched_steps > 0:
+        restore()
+        snap_np = {k: v.cpu().numpy() for k, v in snap.items()}
+        ctxs, bparts = [], []
+        for b in range(nb):
+            sl = slice(offs[b], offs[b + 1])
+            cb = binding.Context(offs[b + 1] - offs[b], device=local, stream=stream.cuda_stream, flags=A, **tuned)
+            pb = binding.Particles({k: v[sl] for k, v in snap_np.items()})
+            cb.build_cells(pb)
+            cb.density(pb)
+            cb.force(pb)
+            ctxs.append(cb)
+            bparts.append(pb)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.unbatched_steps):
+            for cb, pb in zip(ctxs, bparts):
+                cb.step(pb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_u = _max_over_ranks(e0.elapsed_time(e1), dist)
+        launches_u = sum(c.stats()["kernel_launches"] for c in ctxs)
+        for cb in ctxs:
+            cb.close()
+        del bparts
+        unb = {"value": _throughput(world, n, args.unbatched_steps, ms_u / 1e3), "unit": UNIT,
+               "ms_per_step": ms_u / args.unbatched_steps, "steps": args.unbatched_steps,
+               "kernel_launches_per_step": launches_u / args.unbatched_steps,
+               "path": f"{nb} contexts, one sph_step per box and step (host-driven passes), previous-h guess"}
+
+    props = torch.cuda.get_device_properties(local)
+    peak, peak_how = fp32_peak_tflops(props.multi_processor_count, _peaks(), stream.cuda_stream)
+    kernels = {"density": (st_hl["t_density_ms"], st_hl["density_pairs"] * FLOP_DENSITY_PAIR,
+                           st_hl["density_passes"]),
+               "force": (st_hl["t_force_ms"], st_hl["force_pairs"] * FLOP_FORCE_PAIR, st_hl["force_passes"])}
+    dom = max(kernels, key=lambda k: kernels[k][0])
+    t_ms, flops, launches = kernels[dom]
+    achieved = flops / (t_ms / 1e3) / 1e12 if t_ms > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": f"k_{dom} (list mode)", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": _boxes_traffic(dom, launches, st_hl, n),
+                "peak_source": peak_how, "launches": launches, "avg_launch_ms": t_ms / max(launches, 1),
+                "timing": "CUDA events around every launch of host-driven learned-h steps (same state, "
+                          "schedule and h_tol as the replayed ones)",
+                "other_kernel": {k: {"ms_total": v[0], "tflops": (v[1] / (v[0] / 1e3) / 1e12 if v[0] > 0 else 0)}
+                                 for k, v in kernels.items() if k != dom}}
+
+    e2e = None
+    if not args.no_e2e:
+        restore()
+        ctx_h = binding.Context(n, device=local, stream=stream.cuda_stream, box_offsets=offs,
+                                flags=A | binding.SPH_FLAG_HPREDICT, **tuned)
+        ctx_h.hp_load(*wf)
+        hp = binding.Particles({k: snap[k].cpu().numpy() for k in snap}, device="cpu", pin=True)
+        ctx_h.step_host(hp)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx_h.step_host(hp)
+        t_e2e = _max_over_ranks(time.perf_counter() - t0, dist)
+        e2e = {"value": _throughput(world, n, args.steps, t_e2e), "unit": UNIT,
+               "h2d_bytes_per_step": n * (6 * 8 + 8 * 4), "d2h_bytes_per_step": n * (6 * 8 + 14 * 4 + 4),
+               "path": "sph_step_host (pinned host buffers, learned h, all boxes batched, host-driven passes)"}
+        ctx_h.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        b = int(np.argmax(np.diff(offs)))
+        g = {k: snap[k][offs[b]:offs[b + 1]].cpu().numpy().astype(np.float64)
+             for k in ("x", "y", "z", "vx", "vy", "vz", "m", "u", "h")}
+        cpu = oracle_sample(g, n_force=args.cpu_force_targets // 3,
+                            label=f"largest box (N={offs[b + 1] - offs[b]}) of the batched set",
+                            local_radius=True, min_seconds=CPU_SAMPLE_S)
+        cpu.pop("seconds", None)
+
+    spread = lambda v: [float(x) / args.steps for x in v]
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "path": "learned h + batched: all boxes in one context, graph-replayed steps (sph_steps), h iteration "
+                   "from the learned guess",
+           "plain": {"value": _throughput(world, n, args.steps, ms_plain / 1e3), "unit": UNIT,
+                     "ms_per_step": ms_plain / args.steps,
+                     "path": "batched, graph-replayed, h iteration from the previous h (no learned guess)"},
+           "plain_unbatched": unb,
+           "ratios": {"learned_batched_vs_plain_batched": ms_plain / ms,
+                      "learned_batched_vs_plain_unbatched": (unb["ms_per_step"] / (ms / args.steps)) if unb else None},
+           "repeats": {"n": args.repeats, "learned_ms_per_step": spread(learned_ms),
+                       "plain_ms_per_step": spread(plain_ms)},
+           "learned_h": learned, "predictor": pred_info,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "dtype_detail": "FP32 pair arithmetic on leaf-relative positions with compensated sums; FP64 positions, "
+                           "kicks/drifts, wrap and global reductions; BF16/FP32 MLP",
+           "data": "synthetic",
+           "config": {"workload": f"{nb} periodic boxes, N log-uniform in [1e3, 2e5] (uniform + Plummer mix), "
+                                  "batched, learned h",
+                      "n_particles": n, "n_boxes": nb, "n_ngb": 48, "h_tol": 1e-4,
+                      "tile_width": tuned["tile_width"], "leaf_max": tuned["leaf_max"], "schedule": "autotuned",
+                      "l2": "inputs larger than L2 (~7 GB resident)", "parallelism": f"replicas x{world}"},
+           "pair_interactions_per_s": world * pairs / sec,
+           "per_step": {"graph_density_passes": st_learned["density_passes"] / args.steps,
+                        "graph_density_pairs": st_learned["density_pairs"] / args.steps,
+                        "force_pairs": st_learned["force_pairs"] / args.steps,
+                        "leaves": st_learned["n_cells"],
+                        "density_candidates": st_hl["density_candidates"] / args.steps,
+                        "force_candidates": st_hl["force_candidates"] / args.steps,
+                        "t_density_ms": st_hl["t_density_ms"] / args.steps,
+                        "t_force_ms": st_hl["t_force_ms"] / args.steps,
+                        "t_build_ms": st_hl["t_build_ms"] / args.steps, "u_floors": floors / args.steps},
+           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+           "gpu_launches": int(st_learned["kernel_launches"]), "clocks": clocks,
+           "setup_s": time.perf_counter() - t_setup}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _boxes_traffic(kernel, launches, st, n):
+    """DRAM bytes per launch of the list-mode kernel, scaled to this workload from the
+    committed ncu summary of a smaller batched set (profiles/<kernel>_boxes.md: bytes
+    per unit of work -- per target for the density, per particle for the force),
+    while the pair kernels' sources are those it was taken on; else None."""
+    from paper_1508_00115_gb300 import build as b
+    path = os.path.join(ROOT, "profiles", f"{kernel}_boxes.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    src = per = None
+    for line in text.splitlines():
+        if line.startswith("kernel_digest:"):
+            src = line.split(":", 1)[1].split()[0]
+        if line.startswith("dram_bytes_per_unit:"):
+            per = float(line.split(":", 1)[1].split()[0])
+    if src is None or per is None or src != b.pair_kernel_digest():
+        return None
+    units = st["density_targets"] if kernel == "density" else n * launches
+    return per * units / max(launches, 1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -913,10 +1240,16 @@ def main():
     ap.add_argument("--cpu-force-targets", type=int, default=48)
     ap.add_argument("--tile-width", type=int, default=0, help="16 or 32 (0: autotuned)")
     ap.add_argument("--cell-factor", type=float, default=0.0, help=">= 1 (0: autotuned)")
-    ap.add_argument("--workload", choices=["sedov", "clustered", "boxes", "sedov-bins", "gravity"], default="sedov",
-                    help="sedov: Sedov-Taylor 128^3 (the headline); clustered: clustered halo field on "
+    ap.add_argument("--workload", choices=["headline", "sedov", "clustered", "boxes", "sedov-bins", "gravity"],
+                    default="headline",
+                    help="headline: 512 uneven clustered boxes, learned h + batched against plain (the metric); "
+                         "sedov: Sedov-Taylor 128^3 on the uniform grid; clustered: clustered halo field on "
                          "adaptive cells; boxes: batched uneven boxes on adaptive cells; sedov-bins: "
-                         "individual time-steps against global steps on the Sedov workload")
+                         "individual time-steps against global steps on the Sedov workload; gravity: near-field "
+                         "gravity on the Sedov particles")
+    ap.add_argument("--repeats", type=int, default=3, help="headline: alternating learned / plain runs")
+    ap.add_argument("--unbatched-steps", type=int, default=2,
+                    help="headline: steps of the unbatched plain arm (0: skip it)")
     ap.add_argument("--levels", type=int, default=8, help="sedov-bins: time-bin levels")
     ap.add_argument("--eps", type=float, default=-1.0,
                     help="gravity: Plummer softening (default: 1/25 of the mean spacing; 0: unsoftened)")
@@ -936,6 +1269,8 @@ def main():
         run_bins(args)
     elif args.workload == "gravity":
         run_gravity(args)
+    elif args.workload == "headline":
+        run_headline(args)
     elif args.workload != "sedov":
         run_adaptive(args)
     else:

@@ -264,7 +264,10 @@ int sph_force(sph_ctx *ctx, sph_particles *parts);
  * rates; u is floored at 0.  If no force pass ran on the current state, one runs
  * first.  dt <= 0 selects the CFL step from the current vsig.  *dt_used and *out
  * (either may be NULL) receive the step taken and the conserved quantities.
- * Host read: dt and the reductions. */
+ * SPH_ERR_NOT_CONVERGED (h iteration over its pass budget: those particles keep
+ * their last iterate) and SPH_ERR_PRECISION do not stop the step: it completes and
+ * returns the first of them at its end (also sph_steps, sph_step_bins and
+ * sph_step_host).  Host read: dt and the reductions. */
 int sph_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_used, sph_conserved *out);
 
 /* n_steps KDK steps (as sph_step) with no host synchronisation between them: the

@@ -216,11 +216,11 @@ def sph_force(ctx, parts: sph_particles) -> int:
     return _check(lib().sph_force(ctx, ctypes.byref(parts)), ctx)
 
 
-def sph_step(ctx, parts: sph_particles, dt: float = 0.0):
+def sph_step(ctx, parts: sph_particles, dt: float = 0.0, allow=()):
     used = ctypes.c_double(0)
     cons = sph_conserved()
     _check(lib().sph_step(ctx, ctypes.byref(parts), float(dt), ctypes.byref(used),
-                          ctypes.byref(cons)), ctx)
+                          ctypes.byref(cons)), ctx, allow)
     return float(used.value), _cons_dict(cons)
 
 
@@ -410,8 +410,10 @@ class Context:
     def force(self, parts: Particles):
         return sph_force(self.h, parts.struct())
 
-    def step(self, parts: Particles, dt: float = 0.0):
-        return sph_step(self.h, parts.struct(), dt)
+    def step(self, parts: Particles, dt: float = 0.0, allow=()):
+        """One KDK step; `allow`: statuses returned instead of raised (the step
+        completes under SPH_ERR_NOT_CONVERGED and SPH_ERR_PRECISION)."""
+        return sph_step(self.h, parts.struct(), dt, allow)
 
     def steps(self, parts: Particles, n_steps: int, dt: float = 0.0, allow=()):
         return sph_steps(self.h, parts.struct(), n_steps, dt, allow)

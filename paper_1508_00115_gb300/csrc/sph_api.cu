@@ -407,13 +407,19 @@ static int do_build(sph_ctx *ctx, sph_particles *parts)
 }
 
 // do_density inside a compound call: SPH_ERR_PRECISION leaves written results that
-// only miss the density tolerance, so the call goes on and reports it at its end
+// only miss the density tolerance, and SPH_ERR_NOT_CONVERGED after the pass budget
+// leaves every particle with results at its last iterate inside cells that hold it,
+// so the call goes on (a step completes, with a consistent state) and reports the
+// status at its end.  h beyond the cells after the re-binnings stops the call.
 static int density_in_call(sph_ctx *ctx, sph_particles *parts)
 {
     const int rc = do_density(ctx, parts, nullptr);
-    if (rc != SPH_ERR_PRECISION) return rc;
-    ctx->soft_rc = rc;
-    ctx->soft_msg = ctx->err;
+    const bool soft = rc == SPH_ERR_PRECISION || (rc == SPH_ERR_NOT_CONVERGED && ctx->h_counters[C_HFLAG] == 0);
+    if (!soft) return rc;
+    if (!ctx->soft_rc) {
+        ctx->soft_rc = rc;
+        ctx->soft_msg = ctx->err;
+    }
     return SPH_OK;
 }
 

@@ -286,8 +286,9 @@ struct sph_ctx {
     double bin_unit = 0.0;
 
     // a status that does not stop a compound call (sph_step, sph_steps, sph_step_bins,
-    // sph_step_host): SPH_ERR_PRECISION from a density pass whose results were
-    // written; the call finishes and returns it (with its message) at the end
+    // sph_step_host): SPH_ERR_PRECISION, or SPH_ERR_NOT_CONVERGED after the pass budget,
+    // from a density pass whose results were written; the call finishes and returns
+    // the first such status (with its message) at the end
     int soft_rc = 0;
     std::string soft_msg;
 

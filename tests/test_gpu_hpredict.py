@@ -168,6 +168,37 @@ def test_hp_steps_reach_the_same_root(graph):
     _state_close(g1, g2, p1, p2, 1e-5)
 
 
+def test_hp_batched_adaptive_graph_steps_reach_the_same_root():
+    """Learned guess + batched boxes on adaptive cells, steps replayed from a CUDA
+    graph (the headline form): same smoothing lengths, positions and velocities as
+    the same steps without the guess."""
+    from paper_1508_00115_gb300 import binding
+    boxes = []
+    for b, nb in enumerate((4000, 900, 2500 + 3)):
+        d = inputs.plummer_mix(nb, seed=60 + b, n_halos=max(1, nb // 1000))
+        boxes.append(inputs.random_velocities(d, 0.05, 70 + b))
+    offs = [0]
+    for b in boxes:
+        offs.append(offs[-1] + b["x"].size)
+    d = {k: np.concatenate([b[k] for b in boxes]) for k in inputs.FIELDS}
+    norm = _norm()
+    norm[12], norm[13] = 0.0, 0.02
+    w, f = hp.to_library(hp.glorot(31), norm)
+    out = []
+    for flags in (binding.SPH_FLAG_ADAPTIVE, binding.SPH_FLAG_ADAPTIVE | binding.SPH_FLAG_HPREDICT):
+        ctx = binding.Context(d["x"].size, h_tol=1e-6, flags=flags | binding.SPH_FLAG_TREE_H_GUESS,
+                              box_offsets=offs)
+        if flags & binding.SPH_FLAG_HPREDICT:
+            ctx.hp_load(w, f)
+        parts = binding.Particles(d)
+        ctx.steps(parts, 3, 2e-4)
+        assert ctx.stats()["graph_steps"] == 3
+        out.append((parts.numpy(), ctx.permutation()))
+        ctx.close()
+    (g1, p1), (g2, p2) = out
+    _state_close(g1, g2, p1, p2, 1e-5)
+
+
 def test_hp_collect_samples_during_steps():
     from paper_1508_00115_gb300 import binding
     n = 5000

@@ -165,6 +165,21 @@ def test_edge_cases():
     with pytest.raises(binding.SphError) as e:
         ctx.density(parts)
     assert e.value.code == binding.SPH_ERR_NOT_CONVERGED
+    # a step over the pass budget completes (force and closing kick included) and
+    # reports the status at its end: the state stays consistent for the next call
+    ctx.force(parts)
+    before = parts.numpy()
+    perm0 = ctx.permutation()
+    dt = 1e-4
+    ctx.step(parts, dt, allow=(binding.SPH_ERR_NOT_CONVERGED,))
+    after = parts.numpy()
+    assert all(np.all(np.isfinite(after[k])) for k in ("x", "vx", "ax", "rho", "h"))
+    i0, i1 = np.argsort(perm0), np.argsort(ctx.permutation())
+    dx = after["x"][i1] - before["x"][i0] - (before["vx"][i0] + before["ax"][i0].astype(np.float64) * dt / 2) * dt
+    assert np.abs(dx - np.rint(dx)).max() < 1e-12  # drifted by (v + a dt/2) dt
+    with pytest.raises(binding.SphError) as e:
+        ctx.step(parts, dt)
+    assert e.value.code == binding.SPH_ERR_NOT_CONVERGED
     # force before density on the current positions
     ctx.build_cells(parts)
     with pytest.raises(binding.SphError) as e:
