@@ -475,6 +475,28 @@ def run_ours(args):
                "d2h_bytes_per_step": n * (6 * 8 + 14 * 4 + 4)}
         ctx_h.close()
 
+    # the force pass in its two forms on the same state and schedule: gather (each
+    # pair from both sides) and symmetric (each unordered pair once)
+    forms = {}
+    for name, fl in (("gather", 0), ("symmetric", binding.SPH_FLAG_SYMMETRIC)):
+        for k, v in snap.items():
+            parts.t[k].copy_(v)
+        cf_ = binding.Context(n, device=local, stream=stream.cuda_stream,
+                              flags=binding.SPH_FLAG_TIMING | fl, **tuned)
+        cf_.build_cells(parts)
+        cf_.density(parts)
+        cf_.force(parts)  # untimed first launch
+        cf_.reset_stats()
+        for _ in range(5):
+            cf_.force(parts)
+        sf = cf_.stats()
+        forms[name] = {"ms_per_pass": sf["t_force_ms"] / max(sf["force_passes"], 1),
+                       "pairs_per_pass": sf["force_pairs"] / max(sf["force_passes"], 1),
+                       "candidates_per_pass": sf["force_candidates"] / max(sf["force_passes"], 1)}
+        cf_.close()
+    for k, v in snap.items():
+        parts.t[k].copy_(v)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(d, n_force=args.cpu_force_targets, min_seconds=CPU_SAMPLE_S)
@@ -516,6 +538,7 @@ def run_ours(args):
                         "t_build_ms": st["t_build_ms"] / args.steps,
                         "u_floors": floors / args.steps},
            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+           "force_forms": forms, "force_symmetric_chosen": int(st["force_symmetric"]),
            "gpu_launches": int(st_g["kernel_launches"]), "clocks": clocks}
     ctx.close()
     if rank == 0:

@@ -105,6 +105,15 @@ typedef struct sph_ctx sph_ctx; /* opaque, library-owned */
                                 already exceeds the cutoff (exact: projected distance
                                 <= distance).  Default off: the tile bounding-box test
                                 alone prunes the same pairs */
+#define SPH_FLAG_SYMMETRIC 128u /* uniform grid: the force pass evaluates each unordered pair
+                                once (the paper's pair tasks update both cells, Sec. 3.1): one
+                                warp per cell sums its own cell in gather form and the 13 cells
+                                of a half stencil symmetrically, the far side's terms reduced
+                                per source in a fixed order into per-direction slots that a
+                                last pass adds up -- deterministic, no atomics on the sums.
+                                Where some h needs the radius-2 stencil, and in individual
+                                time-steps, the gather form runs.  SPH_FLAG_AUTOTUNE times both
+                                forms and keeps the faster (sph_stats.force_symmetric) */
 
 typedef struct {
     int64_t n;           /* particles; 0 <= n < 2^31                                  */
@@ -206,6 +215,7 @@ typedef struct {
     int64_t grav_passes;       /* gravity near-field launches (sph_gravity_p2p)       */
     int64_t grav_pairs;        /* gravity near-field pair interactions (j != i)        */
     double t_grav_ms;          /* summed device time of gravity launches (TIMING)     */
+    int32_t force_symmetric;   /* force pass in use: 1 symmetric variant, 0 gather     */
 } sph_stats;
 
 /* Fill *p with the defaults: gamma 5/3, n_ngb 48, h_tol 1e-4, alpha 0.8, cfl 0.1,

@@ -37,6 +37,7 @@ SPH_FLAG_ADAPTIVE = 8
 SPH_FLAG_TREE_H_GUESS = 16
 SPH_FLAG_HPREDICT = 32
 SPH_FLAG_AXIS_SWEEP = 64
+SPH_FLAG_SYMMETRIC = 128
 SPH_HP_NBF16 = 4544
 SPH_HP_NF32 = 143
 SPH_HP_NPARAM = 4673
@@ -99,7 +100,8 @@ class sph_stats(ctypes.Structure):
                 ("tile_width", ctypes.c_int32), ("cell_factor", ctypes.c_float),
                 ("graph_steps", ctypes.c_int64), ("leaf_max", ctypes.c_int32),
                 ("hp_samples", ctypes.c_int64), ("grav_passes", ctypes.c_int64),
-                ("grav_pairs", ctypes.c_int64), ("t_grav_ms", ctypes.c_double)]
+                ("grav_pairs", ctypes.c_int64), ("t_grav_ms", ctypes.c_double),
+                ("force_symmetric", ctypes.c_int32)]
 
 
 _lock = threading.Lock()

@@ -59,8 +59,11 @@ static void free_particles(sph_ctx *c)
 {
     void *ptrs[] = {c->pos4, c->vel4, c->thermo4, c->upred, c->h_lo, c->h_hi, c->active, c->ids, c->ids_tmp, c->ngb_hash,
                     c->keys, c->keys_alt, c->vals, c->vals_alt, c->hist, c->s64, c->s32, c->tiles,
-                    c->act_tiles, c->tile_flag, c->tile_pos};
+                    c->act_tiles, c->tile_flag, c->tile_pos, c->sym_slot, c->sym_vsig};
     for (void *p : ptrs) cudaFree(p);
+    c->sym_slot = nullptr;
+    c->sym_vsig = nullptr;
+    c->sym_cap = 0;
     c->pos4 = c->vel4 = c->thermo4 = nullptr;
     c->upred = nullptr;
     c->h_lo = c->h_hi = nullptr;
@@ -237,14 +240,41 @@ static int autotune(sph_ctx *ctx, sph_particles *parts)
                 best_leaf = ctx->leaf_max;
             }
         }
-    for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
     ctx->p.flags = flags;
-    if (rc) return rc;
+    if (rc) {
+        for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+        return rc;
+    }
     ctx->tile_w = best_tw;
     ctx->p.cell_factor = best_cf;
     ctx->leaf_max = best_leaf;
     ctx->tuned = true;
-    return build_cells(ctx, parts);
+    rc = build_cells(ctx, parts);
+    if (rc == SPH_OK && !ctx->adaptive) {
+        // force pass: gather form or the symmetric variant (each unordered pair once),
+        // each timed twice at these smoothing lengths, the faster repetition counting
+        ctx->p.flags &= ~SPH_FLAG_TIMING;
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, ctx->n, ctx->stream));
+        rc = run_density_pass(ctx, parts, true, false);
+        if (rc == SPH_OK) rc = cell_reach(ctx);
+        float t[2] = {1e30f, 1e30f};
+        for (int v = 0; v < 2 && rc == SPH_OK; ++v) {
+            ctx->sym_force = v == 1;
+            for (int r = 0; r < 2 && rc == SPH_OK; ++r) {
+                SPH_CUDA(ctx, cudaEventRecord(ev[0], ctx->stream));
+                rc = run_force_pass(ctx, parts);
+                SPH_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
+                SPH_CUDA(ctx, cudaEventSynchronize(ev[1]));
+                float ms = 0.f;
+                SPH_CUDA(ctx, cudaEventElapsedTime(&ms, ev[0], ev[1]));
+                t[v] = std::min(t[v], ms);
+            }
+        }
+        ctx->sym_force = t[1] < t[0];
+        ctx->p.flags = flags;
+    }
+    for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+    return rc;
 }
 
 // re-binnings of one density call (h outgrew the cells, or adaptive lists far too
@@ -711,8 +741,12 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
     // stream, which cannot be captured); the graph is then launched on the caller's
     // stream.  The timing flag is suspended while capturing.  A graph captured for
     // the same arrays, dt mode and launch shapes is reused.
+    if (ctx->sym_force && !ctx->adaptive) {  // the symmetric force pass's slots, before any capture
+        rc = ensure_sym(ctx);
+        if (rc) return rc;
+    }
     sph_ctx::GraphKey key{*parts, dt > 0 ? dt : 0.0, ctx->n, ctx->grid.n_cells, ctx->grid.key_bits, passes, ctx->tile_w,
-                          tree_sig};
+                          tree_sig, ctx->sym_force};
     if (!ctx->step_exec || !(key == ctx->graph_key)) {
         if (!ctx->cap_stream) SPH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
         const uint32_t flags = ctx->p.flags;
@@ -839,6 +873,7 @@ int sph_init(sph_ctx **out, const sph_params *p, int device, void *cuda_stream)
     c->n = p->n;
     c->tile_w = p->tile_width == 32 ? 32 : 16;
     c->adaptive = (p->flags & SPH_FLAG_ADAPTIVE) != 0;
+    c->sym_force = (p->flags & SPH_FLAG_SYMMETRIC) != 0 && !c->adaptive;
     c->leaf_max = p->leaf_max > 0 ? p->leaf_max : 64;
     c->h_guess_pending = c->adaptive && (p->flags & SPH_FLAG_TREE_H_GUESS);
     c->n_boxes = p->n_boxes > 1 ? p->n_boxes : 1;
@@ -1086,6 +1121,7 @@ int sph_get_stats(sph_ctx *ctx, sph_stats *s)
     st.t_build_ms = t[2];
     st.t_grav_ms = t[3];
     st.grav_pairs = (int64_t)ctx->h_counters[C_GPAIRS];
+    st.force_symmetric = ctx->sym_force ? 1 : 0;
     st.tile_width = ctx->tile_w;
     st.cell_factor = ctx->p.cell_factor;
     st.leaf_max = ctx->adaptive ? ctx->leaf_max : 0;

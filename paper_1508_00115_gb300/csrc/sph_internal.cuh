@@ -56,7 +56,8 @@ enum Counter {
     C_BINOVER = 15,   // individual time-steps: CFL steps below the smallest bin's step
     C_PREC = 16,      // uniform grid: a converged h below cell side / SPH_FRAME_RATIO
     C_GPAIRS = 17,    // gravity near field: pair interactions
-    C_NCOUNTERS = 18
+    C_SYMGATHER = 18, // symmetric force pass: some cell needs the radius-2 stencil (gather runs instead)
+    C_NCOUNTERS = 19
 };
 
 // Cell grid of one periodic box (every box has side box_size; boxes are batched
@@ -261,10 +262,12 @@ struct sph_ctx {
         int64_t n, n_cells;
         int key_bits, passes, tile_w;
         uint64_t tree_sig;  // adaptive cells: arrays and capacities the captured build uses
+        bool sym;           // symmetric force pass
         bool operator==(const GraphKey &o) const
         {
             return memcmp(&parts, &o.parts, sizeof parts) == 0 && dt == o.dt && n == o.n && n_cells == o.n_cells &&
-                   key_bits == o.key_bits && passes == o.passes && tile_w == o.tile_w && tree_sig == o.tree_sig;
+                   key_bits == o.key_bits && passes == o.passes && tile_w == o.tile_w && tree_sig == o.tree_sig &&
+                   sym == o.sym;
         }
     } graph_key{};
     int64_t graph_launches = 0;  // kernels in one captured step
@@ -291,6 +294,13 @@ struct sph_ctx {
     // the first such status (with its message) at the end
     int soft_rc = 0;
     std::string soft_msg;
+
+    // symmetric force pass (SPH_FLAG_SYMMETRIC or the autotuner's choice): source-side
+    // slots, 13 float4 per particle, and the source-side v_sig maxima
+    bool sym_force = false;
+    float4 *sym_slot = nullptr;
+    unsigned *sym_vsig = nullptr;
+    int64_t sym_cap = 0;
 
     // statistics
     sph_stats st{};
@@ -366,6 +376,7 @@ int compact_active_tiles(sph_ctx *ctx);                                    // sp
 int compact_active_leaf_tiles(sph_ctx *ctx);  // adaptive cells: tiles of active targets only  // sph_tree.cu
 int run_force_pass(sph_ctx *ctx, sph_particles *parts, bool active_list = false);  // sph_pairs.cu
 int run_gravity_pass(sph_ctx *ctx, double G, double eps, float *ax, float *ay, float *az, float *phi);  // sph_gravity.cu
+int ensure_sym(sph_ctx *ctx);  // slot arrays of the symmetric force pass           // sph_pairs.cu
 int sync_h(sph_ctx *ctx, sph_particles *parts);                            // sph_pairs.cu
 int kick(sph_ctx *ctx, sph_particles *parts);    // by *d_dt / 2           // sph_integrate.cu
 int drift(sph_ctx *ctx, sph_particles *parts);   // by *d_dt               // sph_integrate.cu

@@ -730,6 +730,7 @@ struct ForceArgs {
     const float *__restrict__ cell_reach;  // per cell: max h of anything that can reach it
     float *ax, *ay, *az, *dudt, *vsig;
     const uint8_t *__restrict__ fmask;  // individual time-steps: targets to update (null: all)
+    const unsigned long long *__restrict__ run_if;  // non-null: run only if *run_if != 0
     unsigned long long *counters;
     const BoxDev *__restrict__ boxes;
     const uint32_t *__restrict__ list_off;
@@ -747,6 +748,7 @@ struct ForceArgs {
 template <int TW, int MODE>
 __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs a)
 {
+    if (a.run_if && *a.run_if == 0ull) return;  // the symmetric pass ran instead
     constexpr bool LIST = MODE == 1, SWEEP = MODE == 2;
     constexpr int TPW = 32 / TW;
     constexpr int B = kBatchF;
@@ -1065,6 +1067,376 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force(ForceArgs 
     }
 }
 
+// ------------------------------------------------ symmetric force pass (f4)
+// Each unordered cell pair once (the paper's pair tasks, Sec. 3.1, which update both
+// cells): one warp owns a cell, takes its particles as targets in groups of 32, and
+// visits its own cell in gather form (every target sums over every other particle of
+// the cell) and the 13 cells of a half stencil (kOrder[1], kOrder[3], ..., kOrder[25]:
+// one of each pair +d, -d) symmetrically: each pair (i, j) with j in neighbour cell
+// B = A + d is evaluated once, and its term goes to i (the target, in registers)
+// and to j (the source).  Determinism without atomics on the sums: within a round of
+// the hit walk, lanes that hit the same source form a group (match_any) whose terms
+// the lowest lane adds in lane order into the batch's per-source sum; after the
+// batch, the warp adds those into slot s of j (s = 1..13, the direction index), a
+// slot only the warp of cell B - d_s ever writes, in a fixed order (groups, then
+// batches).  A final pass adds the 13 slots to the target-side sums in slot order.
+// v_sig is a maximum (order-free): an atomic max on its bits.
+// Needs every cell's reach within one cell side (no radius-2 stencil): otherwise
+// *need_gather is set beforehand and the gather kernel runs the pass instead.
+
+constexpr int kSymSlots = 13;
+
+struct ForceSymArgs {
+    const float4 *__restrict__ pos4;
+    const float4 *__restrict__ vel4;
+    const float4 *__restrict__ thermo4;
+    const int *__restrict__ cell_start;
+    const double *__restrict__ x;
+    const double *__restrict__ y;
+    const double *__restrict__ z;
+    const float *__restrict__ cell_reach;
+    const BoxDev *__restrict__ boxes;
+    float *ax, *ay, *az, *dudt, *vsig;    // target-side sums (plain stores)
+    float4 *slot;                         // kSymSlots x n: source-side sums {a, du/dt}
+    unsigned *vsig_src;                   // n: source-side max v_sig (float bits)
+    const unsigned long long *need_gather;
+    unsigned long long *counters;
+    int64_t n_cells, n;
+    int nb;
+    double box;
+    float alpha;
+};
+
+__device__ __forceinline__ int sym_box_of_cell(int c, const BoxDev *__restrict__ bx, int nb)
+{
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bx[mid].cell_off <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force_sym(ForceSymArgs a)
+{
+    if (*a.need_gather) return;
+    constexpr int TW = 32;
+    constexpr int B = kBatchF;
+    constexpr int SLOT = B + 1;
+    extern __shared__ float4 smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nwb = blockDim.x >> 5;
+    float4 *sA = smem + (size_t)wib * (4 * SLOT);  // {x, y, z, h_j} in the target frame
+    float4 *sB = sA + SLOT;                         // {vx, vy, vz, m}
+    float4 *sC = sB + SLOT;                         // {rho, A, c, B}
+    float4 *sS = sC + SLOT;                         // source-side sums of the batch
+    int *sI = (int *)(smem + (size_t)nwb * (4 * SLOT)) + (size_t)wib * SLOT;  // slot * 16 + stencil index
+    float *sV = (float *)(smem + (size_t)nwb * (4 * SLOT)) + (size_t)nwb * SLOT + (size_t)wib * SLOT;  // max v_sig
+    const unsigned lt = (1u << lane) - 1u;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int ncells = (int)a.n_cells;
+    const float inf = __int_as_float(0x7f800000);
+    unsigned acc_pairs = 0u, acc_cand = 0u;
+    unsigned *ticket = reinterpret_cast<unsigned *>(a.counters + C_TICKET);
+    unsigned tk = 0u;
+    if (lane == 0) tk = atomicAdd(ticket, 1u);
+    for (int c = gw, c_after = 0; c < ncells; c = c_after) {
+        c_after = nw + (int)__shfl_sync(kFull, tk, 0);
+        if (lane == 0 && c_after < ncells) tk = atomicAdd(ticket, 1u);
+        const int cs = a.cell_start[c], ce = a.cell_start[c + 1];
+        if (cs == ce) continue;
+        const BoxDev bx = a.boxes[a.nb == 1 ? 0 : sym_box_of_cell(c, a.boxes, a.nb)];
+        const int nc = bx.nc;
+        const float L = bx.L32;
+        const int ca = c - bx.cell_off;
+        const int ix = ca % nc, iy = (ca / nc) % nc, iz = ca / (nc * nc);
+        // ranges of the 14 cells: lane s < 14 holds stencil entry s (0 = own cell,
+        // s >= 1: kOrder[2 s - 1])
+        int csl = 0, cel = 0;
+        if (lane < 14) {
+            const int o = lane == 0 ? 0 : 2 * lane - 1;
+            const int cb = bx.cell_off + (wrapc(iz + kOrder[o][2], nc) * nc + wrapc(iy + kOrder[o][1], nc)) * nc +
+                           wrapc(ix + kOrder[o][0], nc);
+            csl = a.cell_start[cb];
+            cel = a.cell_start[cb + 1];
+        }
+        const float hreach = a.cell_reach[c];
+        for (int g0 = cs; g0 < ce; g0 += TW) {
+            const int i = g0 + lane;
+            const bool act = i < ce;
+            float4 pi = make_float4(kFar, kFar, kFar, 0.f), vi = make_float4(0.f, 0.f, 0.f, 0.f),
+                   ti = make_float4(1.f, 0.f, 0.f, 0.f);
+            if (act) {
+                pi = a.pos4[i];
+                vi = a.vel4[i];
+                ti = a.thermo4[i];
+            }
+            const float lox = tile_min<TW>(act ? pi.x : inf), hix = tile_max<TW>(act ? pi.x : -inf);
+            const float loy = tile_min<TW>(act ? pi.y : inf), hiy = tile_max<TW>(act ? pi.y : -inf);
+            const float loz = tile_min<TW>(act ? pi.z : inf), hiz = tile_max<TW>(act ? pi.z : -inf);
+            const float hi = pi.w;
+            const float H = fmaxf(tile_max<TW>(hi), hreach);
+            const float bandmax = 2.f * kBandK * H * (H + L);
+            const float reach2 = H * H * (1.f + kPruneMargin) + bandmax;
+            const float hi2 = hi * hi;
+            const float hinv = act ? 1.f / hi : 0.f;
+            const float hinv4 = hinv * hinv * hinv * hinv;
+            const float band_i = kBandK * hi * (hi + L);
+            const float mi_ = vi.w;
+            float sx_ = 0.f, sxc = 0.f, sy_ = 0.f, syc = 0.f, sz_ = 0.f, szc = 0.f, su = 0.f, suc = 0.f;
+            float vs = 0.f;
+            int cnt = 0;
+            unsigned cand = 0;
+            int nst = 0;
+
+            auto flush = [&]() {
+                const int nmax = (int)((__reduce_max_sync(kFull, (unsigned)nst) + 3u) & ~3u);
+                for (int k = nst + lane; k < nmax; k += TW) {
+                    sA[k] = make_float4(-kFar, -kFar, -kFar, 0.f);
+                    sI[k] = 0;
+                }
+                for (int k = lane; k < nmax; k += TW) {
+                    sS[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    sV[k] = 0.f;
+                }
+                __syncwarp();
+                cand += (unsigned)nst;
+                unsigned m0 = 0u, m1 = 0u, m2 = 0u, m3 = 0u;
+                const int nwords = (nmax + 31) >> 5;
+#pragma unroll 1
+                for (int wd = 0; wd < nwords; ++wd) {
+                    const int kend = min(32, nmax - 32 * wd);
+                    const float4 *sw = sA + 32 * wd;
+                    unsigned mw = 0u, bw = 0u;
+                    for (int k4 = 0; k4 < kend; k4 += 4) {
+                        unsigned mn = 0u, bn = 0u;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float4 s = sw[k4 + u];
+                            const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            const float d2 = r2 - fmaxf(hi2, s.w * s.w);
+                            mn |= (unsigned)(d2 < -bandmax) << u;
+                            bn |= (unsigned)(d2 >= -bandmax && d2 < bandmax) << u;
+                        }
+                        mw |= mn << k4;
+                        bw |= bn << k4;
+                    }
+                    while (bw) {
+                        const int kk = __ffs(bw) - 1;
+                        bw &= bw - 1u;
+                        if (band_decide(a.x, a.y, a.z, i, sI[32 * wd + kk] >> 4, a.box, hi, sw[kk].w) != 0u)
+                            mw |= 1u << kk;
+                    }
+                    m0 = wd == 0 ? mw : m0;
+                    m1 = wd == 1 ? mw : m1;
+                    m2 = wd == 2 ? mw : m2;
+                    m3 = wd == 3 ? mw : m3;
+                }
+                float bx_ = 0.f, by_ = 0.f, bz_ = 0.f, bu = 0.f;
+                while (__any_sync(kFull, (m0 | m1 | m2 | m3) != 0u)) {
+                    // this round: each lane's next hit (lowest staged index first)
+                    int k = -1;
+                    float cx = 0.f, cy = 0.f, cz = 0.f, cu = 0.f, cv = 0.f;
+                    bool src = false;
+                    if (m0 | m1 | m2 | m3) {
+                        k = pop_bit(m0, m1, m2, m3);
+                        const float4 s = sA[k];
+                        const float4 vj = sB[k];
+                        const float4 tj = sC[k];
+                        const int code = sI[k];
+                        const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        src = (code & 15) != 0;
+                        cnt += src ? 2 : 1;
+                        if (r2 > 0.f) {
+                            const float hj2 = s.w * s.w;
+                            bool in_i = r2 < hi2, in_j = r2 < hj2;
+                            const float band_j = kBandK * s.w * (s.w + L);
+                            if (fabsf(r2 - hi2) <= band_i || fabsf(r2 - hj2) <= band_j) {
+                                const unsigned dd = band_decide(a.x, a.y, a.z, i, code >> 4, a.box, hi, s.w);
+                                in_i = dd & 1u;
+                                in_j = dd & 2u;
+                            }
+                            const float rinv = rsqrtf(r2);
+                            const float r = r2 * rinv;
+                            const float hjinv = __fdividef(1.f, s.w);
+                            const float hj2inv = hjinv * hjinv;
+                            const float dWi = in_i ? kSigma * spline_dw_u(r * hinv) * hinv4 : 0.f;
+                            const float dWj = in_j ? kSigma * spline_dw_u(r * hjinv) * (hj2inv * hj2inv) : 0.f;
+                            const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+                            const float mu = fmaf(vx, dx, fmaf(vy, dy, vz * dz)) * rinv;
+                            const float muc = fminf(mu, 0.f);
+                            const float vsig_ij = ti.z + tj.z - 3.f * muc;
+                            const float Pi = -a.alpha * vsig_ij * muc * (0.5f * (ti.w + tj.w)) *
+                                             __fdividef(1.f, ti.x + tj.x);
+                            const float pdw = 0.5f * Pi * (0.5f * (dWi + dWj));  // (1/2) Pi dW-bar
+                            const float X = fmaf(ti.y, dWi, fmaf(tj.y, dWj, 2.f * pdw)) * rinv;
+                            const float mj = vj.w;
+                            bx_ = fmaf(-mj * X, dx, bx_);
+                            by_ = fmaf(-mj * X, dy, by_);
+                            bz_ = fmaf(-mj * X, dz, bz_);
+                            bu = fmaf(mj * mu, fmaf(ti.y, dWi, pdw), bu);
+                            vs = fmaxf(vs, vsig_ij);
+                            if (src) {  // the same pair seen from j: d_ji = -d_ij, same mu
+                                const float mX = mi_ * X;
+                                cx = mX * dx;
+                                cy = mX * dy;
+                                cz = mX * dz;
+                                cu = mi_ * mu * fmaf(tj.y, dWj, pdw);
+                                cv = vsig_ij;
+                            }
+                        } else if (src) {
+                            cv = 0.f;
+                        }
+                    }
+                    // the lanes that hit the same source: the lowest adds the group's
+                    // terms in lane order into the batch's sum for that source
+                    const unsigned peers = __match_any_sync(kFull, src ? k : -1 - lane);
+                    const int leader = __ffs(peers) - 1;
+                    const unsigned others = peers & ~(1u << leader);
+                    const int nothers = lane == leader ? __popc(others) : 0;
+                    const int mo = (int)__reduce_max_sync(kFull, (unsigned)nothers);
+                    float gx = cx, gy = cy, gz = cz, gu = cu, gv = cv;
+                    for (int t = 0; t < mo; ++t) {
+                        const int from = t < nothers ? (int)__fns(others, 0u, t + 1) : lane;
+                        const float ox = __shfl_sync(kFull, cx, from), oy = __shfl_sync(kFull, cy, from);
+                        const float oz = __shfl_sync(kFull, cz, from), ou = __shfl_sync(kFull, cu, from);
+                        const float ov = __shfl_sync(kFull, cv, from);
+                        if (t < nothers) {
+                            gx += ox;
+                            gy += oy;
+                            gz += oz;
+                            gu += ou;
+                            gv = fmaxf(gv, ov);
+                        }
+                    }
+                    if (src && lane == leader) {
+                        float4 acc = sS[k];
+                        acc.x += gx;
+                        acc.y += gy;
+                        acc.z += gz;
+                        acc.w += gu;
+                        sS[k] = acc;
+                        sV[k] = fmaxf(sV[k], gv);
+                    }
+                    __syncwarp();
+                }
+                kahan_add(sx_, sxc, bx_);
+                kahan_add(sy_, syc, by_);
+                kahan_add(sz_, szc, bz_);
+                kahan_add(su, suc, bu);
+                // the batch's source sums into the slots of their particles (one writer
+                // per slot: this warp, in batch order)
+                for (int k = lane; k < nst; k += TW) {
+                    const int code = sI[k];
+                    const int s = code & 15;
+                    if (s == 0) continue;
+                    const int j = code >> 4;
+                    const float4 v = sS[k];
+                    float4 *dst = a.slot + (size_t)(s - 1) * (size_t)a.n + j;
+                    float4 o = *dst;
+                    o.x += v.x;
+                    o.y += v.y;
+                    o.z += v.z;
+                    o.w += v.w;
+                    *dst = o;
+                    if (sV[k] > 0.f) atomicMax(a.vsig_src + j, __float_as_uint(sV[k]));
+                }
+                nst = 0;
+                __syncwarp();
+            };
+
+            // stream the 14 cells, TW sources at a time; box-prune against the group
+            for (int s = 0; s < 14; ++s) {
+                const int bs = __shfl_sync(kFull, csl, s), be = __shfl_sync(kFull, cel, s);
+                const int o = s == 0 ? 0 : 2 * s - 1;
+                const float shx = (float)kOrder[o][0] * L, shy = (float)kOrder[o][1] * L,
+                            shz = (float)kOrder[o][2] * L;
+                for (int base = bs; base < be; base += TW) {
+                    const int j = base + lane;
+                    const bool vq = j < be;
+                    const int jj = vq ? j : bs;
+                    float4 pj = __ldg(a.pos4 + jj);
+                    const float4 vj = __ldg(a.vel4 + jj);
+                    const float4 tj = __ldg(a.thermo4 + jj);
+                    pj.x += shx;
+                    pj.y += shy;
+                    pj.z += shz;
+                    const float ex = fmaxf(fmaxf(lox - pj.x, pj.x - hix), 0.f);
+                    const float ey = fmaxf(fmaxf(loy - pj.y, pj.y - hiy), 0.f);
+                    const float ez = fmaxf(fmaxf(loz - pj.z, pj.z - hiz), 0.f);
+                    const bool keep = vq && fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < reach2;
+                    const unsigned mine = __ballot_sync(kFull, keep);
+                    if (keep) {
+                        const int pos = nst + __popc(mine & lt);
+                        sA[pos] = pj;
+                        sB[pos] = vj;
+                        sC[pos] = tj;
+                        sI[pos] = (jj << 4) | s;
+                    }
+                    nst += __popc(mine);
+                    if (nst > B - TW) flush();
+                }
+            }
+            if (nst > 0) flush();
+            const int nself = act ? 1 : 0;
+            acc_pairs += (unsigned)(cnt - nself);
+            const unsigned am = __ballot_sync(kFull, act);
+            if (lane == 0) acc_cand += cand * (unsigned)__popc(am);
+            if (act) {
+                a.ax[i] = sx_ - sxc;
+                a.ay[i] = sy_ - syc;
+                a.az[i] = sz_ - szc;
+                a.dudt[i] = su - suc;
+                a.vsig[i] = vs;
+            }
+        }
+    }
+    const unsigned long long tp = warp_sum_ull(acc_pairs), tc = warp_sum_ull(acc_cand);
+    if (lane == 0) {
+        if (tp) atomicAdd(a.counters + C_FPAIRS, tp);
+        if (tc) atomicAdd(a.counters + C_FCAND, tc);
+    }
+}
+
+// Whether some cell's reach exceeds its side (the symmetric pass covers one cell
+// around each cell only): sets *flag.
+__global__ void k_sym_check(const float *__restrict__ reach, const BoxDev *__restrict__ bx, int nb, int64_t ncells,
+                            unsigned long long *flag)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    const float L = bx[nb == 1 ? 0 : sym_box_of_cell((int)c, bx, nb)].L32;
+    if (reach[c] * (1.f + kPruneMargin) > L) atomicOr(flag, 1ull);
+}
+
+// target-side sums + the 13 source-side slots (slot order) and the two v_sig maxima
+__global__ void k_sym_reduce(const float4 *__restrict__ slot, const unsigned *__restrict__ vsig_src, int64_t n,
+                             const unsigned long long *__restrict__ need_gather, float *ax, float *ay, float *az,
+                             float *dudt, float *vsig)
+{
+    if (*need_gather) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float x = ax[i], y = ay[i], z = az[i], u = dudt[i];
+#pragma unroll
+    for (int s = 0; s < kSymSlots; ++s) {
+        const float4 v = slot[(size_t)s * (size_t)n + i];
+        x += v.x;
+        y += v.y;
+        z += v.z;
+        u += v.w;
+    }
+    ax[i] = x;
+    ay[i] = y;
+    az[i] = z;
+    dudt[i] = u;
+    vsig[i] = fmaxf(vsig[i], __uint_as_float(vsig_src[i]));
+}
+
 __global__ void k_sync_h(const float *__restrict__ h, float4 *__restrict__ pos4, int n)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1081,6 +1453,12 @@ static size_t force_smem()
 {
     const size_t slots = (size_t)(kPairThreads / 32) * (32 / TW) * (kBatchF + 1);
     return slots * (3 * sizeof(float4) + sizeof(int));
+}
+
+static size_t force_sym_smem()
+{
+    const size_t slots = (size_t)(kPairThreads / 32) * (kBatchF + 1);
+    return slots * (4 * sizeof(float4) + sizeof(int) + sizeof(float));
 }
 
 // Opt the pair kernels into more than 48 KB of dynamic shared memory (once per process;
@@ -1103,6 +1481,7 @@ static int smem_optin(sph_ctx *ctx)
     SPH_OPT_D(1)
     SPH_OPT_D(2)
 #undef SPH_OPT_D
+    SPH_CUDA(ctx, cudaFuncSetAttribute(k_force_sym, at, (int)force_sym_smem()));
     done = true;
     return SPH_OK;
 }
@@ -1281,6 +1660,57 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts, bool active_list)
     int rc = smem_optin(ctx);
     if (rc) return rc;
     const int g = pair_grid(ctx, kForceBlocks);
+    // symmetric variant (uniform grid, every target, radius-1 reach): the gather
+    // kernel below then runs only if some cell needs the radius-2 stencil
+    const bool sym = ctx->sym_force && !ctx->adaptive && !a.fmask && !a.axis && !active_list &&
+                     ctx->n < ((int64_t)1 << 27);
+    if (sym) {
+        rc = ensure_sym(ctx);
+        if (rc) return rc;
+        const int64_t nc = ctx->grid.n_cells, n = ctx->n;
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_SYMGATHER, 0, sizeof(unsigned long long), ctx->stream));
+        k_sym_check<<<(unsigned)((nc + 255) / 256), 256, 0, ctx->stream>>>(ctx->cell_tmp, ctx->d_boxes, ctx->n_boxes,
+                                                                         nc, ctx->counters + C_SYMGATHER);
+        SPH_LAUNCH(ctx, "symmetric force check");
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->sym_slot, 0, sizeof(float4) * kSymSlots * (size_t)n, ctx->stream));
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->sym_vsig, 0, sizeof(unsigned) * (size_t)n, ctx->stream));
+        ForceSymArgs sa{};
+        sa.pos4 = ctx->pos4;
+        sa.vel4 = ctx->vel4;
+        sa.thermo4 = ctx->thermo4;
+        sa.cell_start = ctx->cell_start;
+        sa.x = parts->x;
+        sa.y = parts->y;
+        sa.z = parts->z;
+        sa.cell_reach = ctx->cell_tmp;
+        sa.boxes = ctx->d_boxes;
+        sa.ax = parts->ax;
+        sa.ay = parts->ay;
+        sa.az = parts->az;
+        sa.dudt = parts->dudt;
+        sa.vsig = parts->vsig;
+        sa.slot = ctx->sym_slot;
+        sa.vsig_src = ctx->sym_vsig;
+        sa.need_gather = ctx->counters + C_SYMGATHER;
+        sa.counters = ctx->counters;
+        sa.n_cells = nc;
+        sa.n = n;
+        sa.nb = ctx->n_boxes;
+        sa.box = ctx->p.box_size;
+        sa.alpha = ctx->p.alpha_visc;
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+        if (sms <= 0) sms = 148;
+        const int gs = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * kForceBlocks,
+                                                                    nc / (kPairThreads / 32) + 1));
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_TICKET, 0, sizeof(unsigned long long), ctx->stream));
+        cudaEvent_t end = nullptr;
+        timer_begin(ctx, 1, &end);
+        k_force_sym<<<gs, kPairThreads, force_sym_smem(), ctx->stream>>>(sa);
+        timer_end(ctx, end);
+        SPH_LAUNCH(ctx, "symmetric force kernel");
+        a.run_if = ctx->counters + C_SYMGATHER;
+    }
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_TICKET, 0, sizeof(unsigned long long), ctx->stream));
     cudaEvent_t end = nullptr;
     timer_begin(ctx, 1, &end);
@@ -1295,7 +1725,30 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts, bool active_list)
 #undef SPH_LAUNCH_F
     timer_end(ctx, end);
     SPH_LAUNCH(ctx, "force kernel");
+    if (sym) {
+        const int64_t n = ctx->n;
+        k_sym_reduce<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
+            ctx->sym_slot, ctx->sym_vsig, n, ctx->counters + C_SYMGATHER, parts->ax, parts->ay, parts->az,
+            parts->dudt, parts->vsig);
+        SPH_LAUNCH(ctx, "symmetric force sums");
+    }
     ctx->st.force_passes++;
+    return SPH_OK;
+}
+
+// slot arrays of the symmetric force pass (allocated on first use, outside captures)
+int ensure_sym(sph_ctx *ctx)
+{
+    const int64_t need = std::max<int64_t>(ctx->cap, 1);
+    if (ctx->sym_cap >= need) return SPH_OK;
+    cudaFree(ctx->sym_slot);
+    cudaFree(ctx->sym_vsig);
+    ctx->sym_slot = nullptr;
+    ctx->sym_vsig = nullptr;
+    ctx->sym_cap = 0;
+    SPH_CUDA(ctx, cudaMalloc(&ctx->sym_slot, sizeof(float4) * kSymSlots * (size_t)need));
+    SPH_CUDA(ctx, cudaMalloc(&ctx->sym_vsig, sizeof(unsigned) * (size_t)need));
+    ctx->sym_cap = need;
     return SPH_OK;
 }
 
