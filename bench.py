@@ -1217,6 +1217,11 @@ def run_headline(args):
                         "leaves": st_learned["n_cells"],
                         "density_candidates": st_hl["density_candidates"] / args.steps,
                         "force_candidates": st_hl["force_candidates"] / args.steps,
+                        "density_streamed": st_hl["density_streamed"] / args.steps,
+                        "density_staged": st_hl["density_staged"] / args.steps,
+                        "force_streamed": st_hl["force_streamed"] / args.steps,
+                        "force_staged": st_hl["force_staged"] / args.steps,
+                        "density_pairs_host": st_hl["density_pairs"] / args.steps,
                         "t_density_ms": st_hl["t_density_ms"] / args.steps,
                         "t_force_ms": st_hl["t_force_ms"] / args.steps,
                         "t_build_ms": st_hl["t_build_ms"] / args.steps, "u_floors": floors / args.steps},

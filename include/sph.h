@@ -216,6 +216,11 @@ typedef struct {
     int64_t grav_pairs;        /* gravity near-field pair interactions (j != i)        */
     double t_grav_ms;          /* summed device time of gravity launches (TIMING)     */
     int32_t force_symmetric;   /* force pass in use: 1 symmetric variant, 0 gather     */
+    int64_t density_streamed;  /* density: sources read from the leaf lists, all tiles */
+                               /* (adaptive cells; 0 on the uniform grid)             */
+    int64_t density_staged;    /* density: of those, staged past the tile's box test   */
+    int64_t force_streamed;    /* force: sources read (adaptive cells)                 */
+    int64_t force_staged;      /* force: sources staged                                */
 } sph_stats;
 
 /* Fill *p with the defaults: gamma 5/3, n_ngb 48, h_tol 1e-4, alpha 0.8, cfl 0.1,

@@ -1122,6 +1122,10 @@ int sph_get_stats(sph_ctx *ctx, sph_stats *s)
     st.t_grav_ms = t[3];
     st.grav_pairs = (int64_t)ctx->h_counters[C_GPAIRS];
     st.force_symmetric = ctx->sym_force ? 1 : 0;
+    st.density_streamed = (int64_t)ctx->h_counters[C_DSTREAM];
+    st.density_staged = (int64_t)ctx->h_counters[C_DSTAGED];
+    st.force_streamed = (int64_t)ctx->h_counters[C_FSTREAM];
+    st.force_staged = (int64_t)ctx->h_counters[C_FSTAGED];
     st.tile_width = ctx->tile_w;
     st.cell_factor = ctx->p.cell_factor;
     st.leaf_max = ctx->adaptive ? ctx->leaf_max : 0;
@@ -1138,6 +1142,7 @@ int sph_reset_stats(sph_ctx *ctx)
     ctx->timers.clear();
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_DPAIRS, 0, 6 * sizeof(unsigned long long), ctx->stream));
     SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_GPAIRS, 0, sizeof(unsigned long long), ctx->stream));
+    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_DSTREAM, 0, 4 * sizeof(unsigned long long), ctx->stream));
     int nc = ctx->st.nc;
     int64_t ncell = ctx->st.n_cells;
     double cs = ctx->st.cell_size;

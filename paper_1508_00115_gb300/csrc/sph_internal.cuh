@@ -57,7 +57,11 @@ enum Counter {
     C_PREC = 16,      // uniform grid: a converged h below cell side / SPH_FRAME_RATIO
     C_GPAIRS = 17,    // gravity near field: pair interactions
     C_SYMGATHER = 18, // symmetric force pass: some cell needs the radius-2 stencil (gather runs instead)
-    C_NCOUNTERS = 19
+    C_DSTREAM = 19,   // density: sources read from the cells / lists (before the box test)
+    C_DSTAGED = 20,   // density: sources staged for the distance tests (per tile)
+    C_FSTREAM = 21,   // force: sources read
+    C_FSTAGED = 22,   // force: sources staged
+    C_NCOUNTERS = 23
 };
 
 // Cell grid of one periodic box (every box has side box_size; boxes are batched
