@@ -135,9 +135,10 @@ __global__ void __launch_bounds__(kRedThreads) k_conserved_part(sph_particles P,
     for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = s[k];
     __syncthreads();
     for (int w = kRedThreads / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w)
+        if ((int)threadIdx.x < w) {
 #pragma unroll
             for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        }
         __syncthreads();
     }
     if (threadIdx.x < 5) part[threadIdx.x * kRedBlocks + blockIdx.x] = sh[threadIdx.x][0];

@@ -32,6 +32,7 @@ namespace sph {
 
 constexpr int kBatchD = 128;  // staged survivors per tile, density (4 hit-mask words)
 constexpr int kBatchF = 128;  // staged survivors per tile, force
+constexpr int kSlotF = 132;   // floats per staged-coordinate array (>= kBatchD, even: 8-byte aligned pairs)
 constexpr int kPairThreads = 256;
 // Adaptive cells (leaf lists): a batch's hits are walked as one compacted warp-wide
 // list when they sit on fewer than this many lanes' worth (total hits < kCompactLanes
@@ -885,6 +886,13 @@ __global__ void __launch_bounds__(kPairThreads, MODE == 1 ? kForceBlocks : kForc
     float4 *sC = sB + TPW * SLOT;                                      // {rho, A, c, B}
     int *sI = (int *)(smem + (size_t)(blockDim.x >> 5) * (3 * TPW * SLOT)) + (size_t)wib * TPW * SLOT +
               sub * SLOT;
+    // list mode, for the distance tests, as arrays (pairs of sources per instruction):
+    // the staged x, y, z, and each source's cutoff thresholds h_j^2 -/+ its FP32 band
+    // (h spans decades within a list, so each pair has its own band)
+    const size_t nwb = blockDim.x >> 5;
+    float *sX = (float *)((int *)(smem + nwb * (3 * TPW * SLOT)) + nwb * TPW * SLOT) +
+                ((size_t)wib * TPW + sub) * 5 * kSlotF;  // (list mode only: not allocated otherwise)
+    float *sY = sX + kSlotF, *sZ = sY + kSlotF, *sLo = sZ + kSlotF, *sHi = sLo + kSlotF;
     const unsigned gmask = TW == 32 ? kFull : (((1u << TW) - 1u) << (sub * TW));
     const unsigned lt = (1u << lane) - 1u;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -938,6 +946,10 @@ __global__ void __launch_bounds__(kPairThreads, MODE == 1 ? kForceBlocks : kForc
         const float hinv = act ? 1.f / hi : 0.f;
         const float hinv4 = hinv * hinv * hinv * hinv;
         const float band_i = kBandK * hi * (hi + L);
+        // list mode: r^2 below max(tlo_i, tlo_j): neighbour; at or above max(thi_i, thi_j):
+        // not; in between decided in FP64 (h^2 -/+ the band, of the pair's larger h: the
+        // band grows with h, so the pair's thresholds are the larger of the two particles')
+        const float tlo_i = act ? hi2 - band_i : -1.f, thi_i = act ? hi2 + band_i : -1.f;
         const int ca = tile.x - bx.cell_off;
         const int ix = ca % nc, iy = (ca / nc) % nc, iz = ca / (nc * nc);
         float sx_ = 0.f, sxc = 0.f, sy_ = 0.f, syc = 0.f, sz_ = 0.f, szc = 0.f, su = 0.f, suc = 0.f;
@@ -966,10 +978,19 @@ __global__ void __launch_bounds__(kPairThreads, MODE == 1 ? kForceBlocks : kForc
             for (int k = nst + tl; k < nmax; k += TW) {
                 sA[k] = make_float4(-kFar, -kFar, -kFar, 0.f);
                 sI[k] = 0;
+                if constexpr (LIST) {
+                    sX[k] = -kFar;
+                    sY[k] = -kFar;
+                    sZ[k] = -kFar;
+                    sLo[k] = -1.f;
+                    sHi[k] = -1.f;
+                }
             }
             __syncwarp();
             cand += (unsigned)nst;
             unsigned m0 = 0u, m1 = 0u, m2 = 0u, m3 = 0u;
+            const float2 px2 = make_float2(pi.x, pi.x), py2 = make_float2(pi.y, pi.y), pz2 = make_float2(pi.z, pi.z);
+            const float2 mone = make_float2(-1.f, -1.f);
             const int nwords = (nmax + 31) >> 5;
 #pragma unroll 1
             for (int wd = 0; wd < nwords; ++wd) {
@@ -978,23 +999,33 @@ __global__ void __launch_bounds__(kPairThreads, MODE == 1 ? kForceBlocks : kForc
                 unsigned mw = 0u, bw = 0u;  // hits; pairs in the FP32 band, decided below
                 for (int k4 = 0; k4 < kend; k4 += 4) {
                     unsigned mn = 0u, bn = 0u;  // the four tests of this group
+                    if constexpr (!LIST) {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const float4 s = sw[k4 + u];
-                        const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        float m2x, bm;
-                        if (LIST) {  // band of this pair: h spans decades within a list
-                            const float mm = fmaxf(hi, s.w);
-                            m2x = mm * mm;
-                            bm = kBandK * mm * (mm + L);
-                        } else {
-                            m2x = fmaxf(hi2, s.w * s.w);
-                            bm = bandmax;
+                        for (int u = 0; u < 4; ++u) {
+                            const float4 s = sw[k4 + u];
+                            const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            const float d2 = r2 - fmaxf(hi2, s.w * s.w);
+                            mn |= (unsigned)(d2 < -bandmax) << u;
+                            bn |= (unsigned)(d2 >= -bandmax && d2 < bandmax) << u;
                         }
-                        const float d2 = r2 - m2x;
-                        mn |= (unsigned)(d2 < -bm) << u;
-                        bn |= (unsigned)(d2 >= -bm && d2 < bm) << u;
+                    } else {
+#pragma unroll
+                    for (int u = 0; u < 4; u += 2) {
+                        const int k = 32 * wd + k4 + u;  // two sources per instruction (FP32x2)
+                        const float2 x2 = *reinterpret_cast<const float2 *>(sX + k);
+                        const float2 y2 = *reinterpret_cast<const float2 *>(sY + k);
+                        const float2 z2 = *reinterpret_cast<const float2 *>(sZ + k);
+                        const float2 lo2 = *reinterpret_cast<const float2 *>(sLo + k);
+                        const float2 hi2v = *reinterpret_cast<const float2 *>(sHi + k);
+                        const float2 dx2 = __ffma2_rn(x2, mone, px2), dy2 = __ffma2_rn(y2, mone, py2);
+                        const float2 dz2 = __ffma2_rn(z2, mone, pz2);
+                        const float2 r2 = __ffma2_rn(dx2, dx2, __ffma2_rn(dy2, dy2, __fmul2_rn(dz2, dz2)));
+                        const float l0 = fmaxf(tlo_i, lo2.x), l1 = fmaxf(tlo_i, lo2.y);
+                        const float h0 = fmaxf(thi_i, hi2v.x), h1 = fmaxf(thi_i, hi2v.y);
+                        mn |= ((unsigned)(r2.x < l0) << u) | ((unsigned)(r2.y < l1) << (u + 1));
+                        bn |= ((unsigned)(r2.x >= l0 && r2.x < h0) << u) | ((unsigned)(r2.y >= l1 && r2.y < h1) << (u + 1));
+                    }
                     }
                     mw |= mn << k4;
                     bw |= bn << k4;
@@ -1281,6 +1312,14 @@ __global__ void __launch_bounds__(kPairThreads, MODE == 1 ? kForceBlocks : kForc
                     sB[pos] = vj;
                     sC[pos] = tj;
                     sI[pos] = jj;
+                    if constexpr (LIST) {
+                        sX[pos] = pj.x;
+                        sY[pos] = pj.y;
+                        sZ[pos] = pj.z;
+                        const float hj2 = pj.w * pj.w, bj = kBandK * pj.w * (pj.w + L);
+                        sLo[pos] = hj2 - bj;
+                        sHi[pos] = hj2 + bj;
+                    }
                 }
                 nst += __popc(mine);
                 ++ch;
@@ -1693,10 +1732,11 @@ static size_t density_smem()
     return (size_t)(kPairThreads / 32) * 2 * (32 / TW) * (kBatchD + 1) * sizeof(float4);
 }
 template <int TW>
-static size_t force_smem()
+static size_t force_smem(bool list)
 {
     const size_t slots = (size_t)(kPairThreads / 32) * (32 / TW) * (kBatchF + 1);
-    return slots * (3 * sizeof(float4) + sizeof(int));
+    const size_t tiles = (size_t)(kPairThreads / 32) * (32 / TW);
+    return slots * (3 * sizeof(float4) + sizeof(int)) + (list ? tiles * 5 * kSlotF * sizeof(float) : 0);
 }
 
 static size_t force_sym_smem()
@@ -1712,7 +1752,7 @@ static int smem_optin(sph_ctx *ctx)
     static bool done = false;
     if (done) return SPH_OK;
     const int d16 = (int)density_smem<16>(), d32 = (int)density_smem<32>();
-    const int f16 = (int)force_smem<16>(), f32 = (int)force_smem<32>();
+    const int f16 = (int)force_smem<16>(true), f32 = (int)force_smem<32>(true);
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
 #define SPH_OPT_D(M)                                                              \
     SPH_CUDA(ctx, cudaFuncSetAttribute(k_density<16, false, M>, at, d16));        \
@@ -1959,7 +1999,7 @@ int run_force_pass(sph_ctx *ctx, sph_particles *parts, bool active_list)
     cudaEvent_t end = nullptr;
     timer_begin(ctx, 1, &end);
     const int mode = ctx->adaptive ? 1 : (a.axis ? 2 : 0);
-    const size_t smf = ctx->tile_w == 32 ? force_smem<32>() : force_smem<16>();
+    const size_t smf = ctx->tile_w == 32 ? force_smem<32>(ctx->adaptive) : force_smem<16>(ctx->adaptive);
 #define SPH_LAUNCH_F(TWv, Mv) k_force<TWv, Mv><<<g, kPairThreads, smf, ctx->stream>>>(a)
     if (ctx->tile_w == 32) {
         if (mode == 1) SPH_LAUNCH_F(32, 1); else if (mode == 2) SPH_LAUNCH_F(32, 2); else SPH_LAUNCH_F(32, 0);
