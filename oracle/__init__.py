@@ -369,27 +369,96 @@ def time_bins(h, vsig, dt_max: float, n_bins: int, s_now: int, cfl: float = 0.1)
     return b, over, margin
 
 
+def _neighbours(s: State, h, idx):
+    """For each particle i of idx, every j != i with r_ij < max(h_i, h_j) (the pairs
+    of the force sum, Eq. 8), r_ij^2 in the operation order of the plain definition:
+    dx = x_i - x_j, minimal image dx - box rint(dx / box), r^2 = (dx^2 + dy^2) + dz^2."""
+    out = []
+    for i in idx:
+        d = []
+        for c in ("x", "y", "z"):
+            v = getattr(s, c)
+            dd = v[i] - v
+            dd = dd - s.box * np.rint(dd / s.box)
+            d.append(dd)
+        r2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]
+        hh = np.maximum(h[i] * h[i], h * h)
+        nb = np.nonzero(r2 < hh)[0]
+        out.append(nb[nb != i])
+    return out
+
+
+def limit_bins(s: State, h, bins, active, T, s_now: int, n_bins: int, levels: int = 2):
+    """Time-step limiter with wake-up (Saitoh & Makino 2009; the paper is silent on
+    time-stepping) at integer time s_now, after the particles whose step ends there
+    (``active``) took their CFL bins.
+
+    Neighbours are the pairs of the force sum, r_ij < max(h_i, h_j).  The bins are
+    raised to the least fixed point, reached by Jacobi sweeps from the given ones, of
+      active i:    b_i = max(b_i, max over all neighbours j of b_j - levels)
+      inactive j:  b_j = max(b_j, max over active neighbours i of b_i - levels),
+    so that afterwards no pair with an active member has bins more than ``levels``
+    apart.  (An active particle's bin already divides s_now, and a larger bin still
+    does.)  An inactive particle whose raised bin's step D' = 2^(n_bins - b) ends
+    before its current step, at T' = (s_now // D' + 1) D' < T, is woken: its step is
+    cut to end at T'.
+
+    Returns (bins, T, limited: active particles whose bin was raised, woken: mask of
+    the particles whose step was cut).  The caller corrects the cut particles'
+    opening half kick by (T' - T) / 2."""
+    bins = np.array(bins, dtype=np.int64)
+    T = np.array(T, dtype=np.int64)
+    act = np.asarray(active, dtype=bool)
+    everyone = np.arange(s.n)
+    ngb = _neighbours(s, h, everyone)
+    start = bins.copy()
+    while True:
+        prev = bins.copy()
+        for i in everyone:
+            g = ngb[i] if act[i] else ngb[i][act[ngb[i]]]
+            if g.size:
+                bins[i] = max(prev[i], int(prev[g].max()) - levels)
+        if np.array_equal(bins, prev):
+            break
+    limited = int(np.sum(act & (bins != start)))
+    D = np.left_shift(1, n_bins - bins)
+    Tn = (s_now // D + 1) * D
+    woken = ~act & (Tn < T)
+    T[woken] = Tn[woken]
+    return bins, T, limited, woken
+
+
 def step_bins(s: State, acc: dict, dt_max: float, n_bins: int,
-              p: Params = Params()) -> tuple[State, dict, dict]:
+              p: Params = Params(), limiter: int | None = None) -> tuple[State, dict, dict]:
     """Advance by dt_max with individual time-steps: the kick-drift-kick leapfrog of
     :func:`step` per particle, each on its own power-of-two step (:func:`time_bins`).
 
     ``acc`` is the hydro result of a synchronised state (keys a, dudt, vsig, h, rho,
-    P, c, f, B).  Time runs on an integer grid of dt_max / 2^n_bins.  At the start
-    every particle takes its opening half kick.  Then, from one step end to the
-    next: all particles drift; the particles whose step ends now are active; the
+    P, c, f, B).  Time runs on an integer grid of dt_max / 2^n_bins; every particle
+    carries the start s0 and end T of its current step.  At the start every particle
+    takes its opening half kick.  Then, from one step end to the next: all particles
+    drift to the smallest T; the particles whose step ends there are active; the
     density (with the h solve) and the force are evaluated for the active ones only,
     against every particle at its drifted position, with velocities and internal
-    energies predicted to the current time (v_half + a (t - t_mid), t_mid the middle
-    of the particle's own step), while the inactive particles keep h, rho, P, c, f
-    and B from their last evaluation; the active ones take their closing half
-    kick, a new bin, and (before dt_max is reached) the opening half kick of their
-    next step.  At dt_max every particle is synchronised again.
+    energies predicted to the current time (v_half + a (t - t_mid), t_mid = (s0 + T)
+    / 2 the middle of the particle's own step), while the inactive particles keep h,
+    rho, P, c, f and B from their last evaluation; the active ones take their closing
+    half kick (T - s0) / 2, a new bin, and (before dt_max is reached) the opening half
+    kick of their next step.  At dt_max every particle is synchronised again.
+
+    ``limiter`` (levels, e.g. 2: no step more than 4 times a neighbour's): after the
+    active particles (all of them at the start) take their CFL bins, the bins are
+    raised by :func:`limit_bins` (Saitoh & Makino 2009), and every inactive particle
+    whose step it cut takes the difference of its opening half kick, v += a (T' - T)
+    dt-unit / 2 and u likewise (floored at 0, counted).
+    ``limiter=None`` is the scheme without them.
 
     Returns (state, hydro dict of the final synchronised state, stats with
     floors, substeps, active (particle updates), over (CFL steps below the
     smallest bin), margin (the closest any bin decision came to a boundary, in
-    log2) and bins (the bins of the last steps))."""
+    log2), bins (the bins of the last steps), kicked (each particle's half-kick
+    lengths summed, in units: 2^(n_bins + 1) when its steps tile the interval), and
+    with a limiter limited (bins raised by it) and woken (wake-ups))."""
     B = int(n_bins)
     unit = dt_max / 2.0 ** B
     end = 1 << B
@@ -398,10 +467,15 @@ def step_bins(s: State, acc: dict, dt_max: float, n_bins: int,
     st["a"] = np.array(acc["a"], dtype=np.float64)
     n2.h = st["h"].copy()
     floors = 0
+    limited = 0
+    woken = 0
+    kicked = np.zeros(s.n, dtype=np.int64)  # each particle's half-kick lengths, summed
 
-    def kick(idx, bins):
+    def kick(idx, length):
+        """v += a L/2 dt-unit, u likewise (floored), for the particles idx."""
         nonlocal floors
-        half = 0.5 * ((1 << (B - bins[idx])).astype(np.float64) * unit)
+        kicked[idx] += np.asarray(length, dtype=np.int64)
+        half = 0.5 * (np.asarray(length, dtype=np.int64).astype(np.float64) * unit)
         n2.vx[idx] = n2.vx[idx] + st["a"][idx, 0] * half
         n2.vy[idx] = n2.vy[idx] + st["a"][idx, 1] * half
         n2.vz[idx] = n2.vz[idx] + st["a"][idx, 2] * half
@@ -409,27 +483,42 @@ def step_bins(s: State, acc: dict, dt_max: float, n_bins: int,
         floors += int(np.sum(u < 0))
         n2.u[idx] = np.maximum(u, 0.0)
 
+    def limit(act, bins, S):
+        """The limiter and wake-up at S (:func:`limit_bins`); the cut steps' opening
+        half kicks corrected to their new length."""
+        nonlocal limited, woken, T
+        if limiter is None:
+            return bins
+        bins, Tn, nl, wk = limit_bins(n2, st["h"], bins, act, T, S, B, limiter)
+        idx = np.nonzero(wk)[0]
+        kick(idx, Tn[idx] - T[idx])
+        T = Tn
+        limited += nl
+        woken += int(idx.size)
+        return bins
+
     everyone = np.arange(s.n)
     bins, over, margin = time_bins(st["h"], st["vsig"], dt_max, B, 0, p.cfl)
-    kick(everyone, bins)
+    s0 = np.zeros(s.n, dtype=np.int64)
+    T = np.zeros(s.n, dtype=np.int64)
+    bins = limit(np.ones(s.n, dtype=bool), bins, 0)
+    T[:] = np.left_shift(1, B - bins)
+    kick(everyone, T - s0)
     S = 0
     substeps = 0
     updates = 0
     while S < end:
-        dmin = 1 << (B - int(bins.max()))
-        S_next = (S // dmin + 1) * dmin
+        S_next = int(T.min())
         dt = (S_next - S) * unit
         n2.x = wrap(n2.x + n2.vx * dt, s.box)
         n2.y = wrap(n2.y + n2.vy * dt, s.box)
         n2.z = wrap(n2.z + n2.vz * dt, s.box)
         S = S_next
         substeps += 1
-        D = np.left_shift(1, B - bins)
-        act = (S % D) == 0
+        act = T == S
         idx = np.nonzero(act)[0]
         updates += int(idx.size)
-        s0 = np.where(act, S - D, S - S % D)
-        tau = 0.5 * ((2 * (S - s0) - D).astype(np.float64) * unit)
+        tau = 0.5 * ((2 * S - s0 - T).astype(np.float64) * unit)
         pred = n2.copy()
         pred.vx = n2.vx + st["a"][:, 0] * tau
         pred.vy = n2.vy + st["a"][:, 1] * tau
@@ -447,14 +536,20 @@ def step_bins(s: State, acc: dict, dt_max: float, n_bins: int,
         st["dudt"][idx] = fr["dudt"]
         st["vsig"][idx] = fr["vsig"]
         n2.h[idx] = d["h"]
-        kick(idx, bins)  # closing half kick on the step that ends now
+        kick(idx, T[idx] - s0[idx])  # closing half kick on the step that ends now
         nb, o, mg = time_bins(st["h"][idx], st["vsig"][idx], dt_max, B, S, p.cfl)
         over += o
         margin = min(margin, mg)
         bins[idx] = nb
         if S < end:
-            kick(idx, bins)  # opening half kick of the next step
-    stats = dict(floors=floors, substeps=substeps, active=updates, over=over, margin=margin, bins=bins)
+            bins = limit(act, bins, S)
+            s0[idx] = S
+            T[idx] = S + np.left_shift(1, B - bins[idx])
+            kick(idx, T[idx] - s0[idx])  # opening half kick of the next step
+    stats = dict(floors=floors, substeps=substeps, active=updates, over=over, margin=margin, bins=bins,
+                 kicked=kicked)
+    if limiter is not None:
+        stats.update(limited=limited, woken=woken)
     return n2, st, stats
 
 
