@@ -552,10 +552,10 @@ def run_ours(args):
 
 def run_bins(args):
     """Individual time-steps on the Sedov-Taylor workload: from one state, advance by
-    dt_max = 2^L x the global CFL step once with sph_step_bins (each particle on its
-    own power-of-two step) and once with global CFL steps (sph_step, the last one cut
-    to land on dt_max); report both times, the particle updates each needed, and
-    their total energies."""
+    dt_max = 2^L x the global CFL step with sph_step_bins (each particle on its own
+    power-of-two step), without and with the time-step limiter (SPH_FLAG_BIN_LIMITER),
+    and with global CFL steps (sph_step, the last one cut to land on dt_max); report
+    the times, the particle updates each needed, and their total energies."""
     import torch
     from paper_1508_00115_gb300 import binding
 
@@ -570,7 +570,8 @@ def run_bins(args):
     n = int(d["x"].size)
     stream = torch.cuda.Stream()
     sched = _schedule(args, binding)
-    ctx = binding.Context(n, device=local, stream=stream.cuda_stream, flags=sched.pop("flags"), **sched)
+    flags = sched.pop("flags")
+    ctx = binding.Context(n, device=local, stream=stream.cuda_stream, flags=flags, **sched)
     parts = binding.Particles(d)
     cons = None
     for _ in range(args.warmup):
@@ -618,6 +619,25 @@ def run_bins(args):
     ms_bins, (cons_b, st_b) = timed(binned, "bin_steps")
     restore()
     ms_glob, (n_glob, cons_g) = timed(global_steps, "global_steps")
+    # the same from the same state with the time-step limiter: its own context (the
+    # flag is a context parameter), on the warmed-up state
+    restore()
+    ctx_l = binding.Context(n, device=local, stream=stream.cuda_stream, flags=flags | binding.SPH_FLAG_BIN_LIMITER,
+                            **sched)
+    ctx_l.build_cells(parts)
+    ctx_l.density(parts)
+    ctx_l.force(parts)
+    torch.cuda.synchronize()
+    snap_l = {k: v.clone() for k, v in parts.t.items()}
+
+    def binned_lim():
+        return ctx_l.step_bins(parts, dt_max, levels)
+
+    binned_lim()  # untimed first call (allocations)
+    for k, v in snap_l.items():
+        parts.t[k].copy_(v)
+    ms_lim, (cons_l, st_l) = timed(binned_lim, "bin_steps_limiter")
+    ctx_l.close()
     e_start = float(np.sum(d["m"] * d["u"]))
     out = {"metric": METRIC, "value": _throughput(world, n, n_glob, ms_bins / 1e3), "unit": UNIT,
            "n_gpus": world, "steps": 1, "warmup": args.warmup, "ms_per_step": ms_bins,
@@ -631,7 +651,14 @@ def run_bins(args):
            "bins": {"levels": levels, "dt_max": dt_max, "substeps": st_b["substeps"],
                     "updates": st_b["updates"], "cfl_over": st_b["cfl_over"],
                     "bin_count": [int(v) for v in st_b["bin_count"][:levels + 1]]},
-           "energy": {"start": e_start, "bins": cons_b["e_tot"], "global": cons_g["e_tot"]},
+           "limiter": {"ms": ms_lim, "speedup_vs_global": ms_glob / ms_lim,
+                       "levels": binding.SPH_BIN_LIMIT_LEVELS, "substeps": st_l["substeps"],
+                       "updates": st_l["updates"], "limited": st_l["limited"], "woken": st_l["woken"],
+                       "passes": st_l["limit_sweeps"],
+                       "bin_count": [int(v) for v in st_l["bin_count"][:levels + 1]],
+                       "path": "sph_step_bins with SPH_FLAG_BIN_LIMITER (Saitoh & Makino 2009, factor 4)"},
+           "energy": {"start": e_start, "bins": cons_b["e_tot"], "bins_limiter": cons_l["e_tot"],
+                      "global": cons_g["e_tot"]},
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "sedov-taylor 128^3 jittered lattice, individual time-steps",
                       "n_particles": n, "n_ngb": 48, "levels": levels,

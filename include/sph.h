@@ -114,6 +114,14 @@ typedef struct sph_ctx sph_ctx; /* opaque, library-owned */
                                 Where some h needs the radius-2 stencil, and in individual
                                 time-steps, the gather form runs.  SPH_FLAG_AUTOTUNE times both
                                 forms and keeps the faster (sph_stats.force_symmetric) */
+#define SPH_FLAG_BIN_LIMITER 256u /* sph_step_bins: time-step limiter with wake-up (Saitoh &
+                                Makino 2009; the paper is silent on time-stepping): no pair
+                                r_ij < max(h_i, h_j) with a particle whose step ends now is
+                                left more than SPH_BIN_LIMIT_LEVELS bins apart, and a
+                                sleeping particle whose raised bin's step ends earlier than
+                                its own is woken (its step cut, its opening half kick
+                                corrected) */
+#define SPH_BIN_LIMIT_LEVELS 2  /* bins a neighbour may be coarser: steps within a factor 4 */
 
 typedef struct {
     int64_t n;           /* particles; 0 <= n < 2^31                                  */
@@ -187,6 +195,10 @@ typedef struct {
     int64_t cfl_over;                    /* steps whose CFL step was below the smallest  */
                                          /* bin's, taken at the smallest bin anyway     */
     int64_t bin_count[SPH_MAX_BINS + 1]; /* particles per bin, for their last step      */
+    int64_t limited;                     /* SPH_FLAG_BIN_LIMITER: starting steps whose  */
+                                         /* bin the limiter raised above the CFL bin    */
+    int64_t woken;                       /* SPH_FLAG_BIN_LIMITER: steps cut by wake-ups */
+    int64_t limit_sweeps;                /* SPH_FLAG_BIN_LIMITER: limiter passes run    */
 } sph_bin_stats;
 
 /* Counters since the last sph_reset_stats (sph_get_stats synchronises the stream). */
@@ -323,7 +335,16 @@ int sph_steps(sph_ctx *ctx, sph_particles *parts, int32_t n_steps, double dt, do
  * u predicted to that time from the middle of its own step, v_half + a (t - t_mid),
  * the others keeping h, rho, P, c, f, Balsara B, a, du/dt and vsig from their last
  * update -- then their closing half kick, a new bin and, before dt_max, their
- * next opening half kick.  On return every particle is synchronised at dt_max with
+ * next opening half kick.  With SPH_FLAG_BIN_LIMITER the new bins (all of them at
+ * 0) are then raised, in passes over the particles until none changes, to the
+ * least fixed point of: a particle whose step ends now takes at least the largest
+ * bin of its neighbours (r_ij < max(h_i, h_j), decided in FP64 from the positions)
+ * minus SPH_BIN_LIMIT_LEVELS, a sleeping one at least the largest bin of its
+ * neighbours whose step ends now minus SPH_BIN_LIMIT_LEVELS; a sleeping particle
+ * whose raised bin's step, counted from the grid, ends at T' before its own step
+ * end T is woken -- its step now ends at T', its opening half kick corrected by
+ * (T' - T) / 2 -- and the others open their steps.  Each particle's step start and
+ * end are kept as integers.  On return every particle is synchronised at dt_max with
  * current a, du/dt, vsig (n_bins = 0 is exactly sph_step with dt = dt_max).  Runs
  * a hydro pass first if the current state has none (or SPH_FLAG_AUTOTUNE has not
  * tuned yet).  *out and *stats may be NULL.  Errors as sph_step; on an error the

@@ -38,6 +38,8 @@ SPH_FLAG_TREE_H_GUESS = 16
 SPH_FLAG_HPREDICT = 32
 SPH_FLAG_AXIS_SWEEP = 64
 SPH_FLAG_SYMMETRIC = 128
+SPH_FLAG_BIN_LIMITER = 256
+SPH_BIN_LIMIT_LEVELS = 2
 SPH_HP_NBF16 = 4544
 SPH_HP_NF32 = 143
 SPH_HP_NPARAM = 4673
@@ -86,7 +88,8 @@ SPH_MAX_BINS = 24
 
 class sph_bin_stats(ctypes.Structure):
     _fields_ = [("substeps", ctypes.c_int64), ("updates", ctypes.c_int64), ("cfl_over", ctypes.c_int64),
-                ("bin_count", ctypes.c_int64 * (SPH_MAX_BINS + 1))]
+                ("bin_count", ctypes.c_int64 * (SPH_MAX_BINS + 1)), ("limited", ctypes.c_int64),
+                ("woken", ctypes.c_int64), ("limit_sweeps", ctypes.c_int64)]
 
 
 class sph_stats(ctypes.Structure):
@@ -250,7 +253,8 @@ def sph_step_bins(ctx, parts: sph_particles, dt_max: float, n_bins: int):
     _check(lib().sph_step_bins(ctx, ctypes.byref(parts), float(dt_max), int(n_bins), ctypes.byref(cons),
                                ctypes.byref(bs)), ctx)
     stats = dict(substeps=int(bs.substeps), updates=int(bs.updates), cfl_over=int(bs.cfl_over),
-                 bin_count=np.array(list(bs.bin_count), dtype=np.int64))
+                 bin_count=np.array(list(bs.bin_count), dtype=np.int64), limited=int(bs.limited),
+                 woken=int(bs.woken), limit_sweeps=int(bs.limit_sweeps))
     return _cons_dict(cons), stats
 
 

@@ -114,11 +114,19 @@ static int alloc_particles(sph_ctx *c, int64_t cap)
 // individual time-steps: per-particle state of sph_step_bins, allocated on first use
 static void free_bins(sph_ctx *c)
 {
-    void *ptrs[] = {c->bins, c->bins_tmp, c->bin_active, c->bin_active_tmp, c->bin_s32};
+    void *ptrs[] = {c->bins, c->bins_tmp, c->bin_active, c->bin_active_tmp, c->bin_s32,
+                    c->bin_st, c->bin_st_tmp, c->bins_cfl, c->lim_cell, c->lim_want, c->lim_list, c->lim_cmax};
     for (void *p : ptrs) cudaFree(p);
     c->bins = c->bins_tmp = nullptr;
     c->bin_active = c->bin_active_tmp = nullptr;
     c->bin_s32 = nullptr;
+    c->bin_st = c->bin_st_tmp = nullptr;
+    c->bins_cfl = nullptr;
+    c->lim_cell = nullptr;
+    c->lim_want = nullptr;
+    c->lim_list = nullptr;
+    c->lim_cmax = nullptr;
+    c->lim_cmax_cap = 0;
     c->bin_cap = 0;
 }
 
@@ -132,6 +140,12 @@ static int alloc_bins(sph_ctx *c)
     SPH_CUDA(c, cudaMalloc(&c->bin_active, cap));
     SPH_CUDA(c, cudaMalloc(&c->bin_active_tmp, cap));
     SPH_CUDA(c, cudaMalloc(&c->bin_s32, sizeof(float) * 5 * cap));
+    SPH_CUDA(c, cudaMalloc(&c->bin_st, sizeof(int2) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->bin_st_tmp, sizeof(int2) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->bins_cfl, cap));
+    SPH_CUDA(c, cudaMalloc(&c->lim_cell, sizeof(int32_t) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->lim_want, sizeof(int) * cap));
+    SPH_CUDA(c, cudaMalloc(&c->lim_list, sizeof(int) * cap));
     c->bin_cap = cap;
     return SPH_OK;
 }
@@ -529,14 +543,16 @@ static int do_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_use
 
 // Advance by dt_max with each particle on its own power-of-two step (the leapfrog of
 // do_step per particle).  Time runs on an integer grid of unit dt_max / 2^L.  All
-// particles open a step at 0; then, from one step end to the next: every particle
-// drifts; the cells are built (the build also carries the bins and the kept density
-// outputs along, and predicts every particle's v and u to the current time); the
-// particles whose step ends now get density (with the h iteration) and force
-// against all particles, take their closing half kick, a new bin, and (before
-// dt_max) the opening half kick of their next step.  The others keep h, rho, P, c,
-// f, B, a, du/dt and vsig from their last update.  At dt_max every particle is
-// synchronised again, with current a and du/dt.
+// particles open a step at 0; then, from one step end to the next (the earliest
+// step end over the particles): every particle drifts; the cells are built (the
+// build also carries the bins, the steps and the kept density outputs along, and
+// predicts every particle's v and u to the current time); the particles whose step
+// ends now get density (with the h iteration) and force against all particles,
+// take their closing half kick, a new bin (raised by the limiter, which may also
+// wake sleeping neighbours, with SPH_FLAG_BIN_LIMITER), and (before dt_max) open
+// their next step with its half kick.  The others keep h, rho, P, c, f, B, a,
+// du/dt and vsig from their last update.  At dt_max every particle is synchronised
+// again, with current a and du/dt.
 static int do_step_bins(sph_ctx *ctx, sph_particles *parts, double dt_max, int levels, sph_conserved *out,
                         sph_bin_stats *bs)
 {
@@ -550,28 +566,49 @@ static int do_step_bins(sph_ctx *ctx, sph_particles *parts, double dt_max, int l
     }
     rc = alloc_bins(ctx);
     if (rc) return rc;
+    const bool limiter = (ctx->p.flags & SPH_FLAG_BIN_LIMITER) != 0;
     const int64_t end = (int64_t)1 << levels;
     const double unit = ldexp(dt_max, -levels);
     ctx->bin_levels = levels;
     ctx->bin_unit = unit;
     ctx->bin_now = 0;
-    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_FLOORS, 0, sizeof(unsigned long long), ctx->stream));
-    SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + C_BINOVER, 0, sizeof(unsigned long long), ctx->stream));
-    int64_t substeps = 0, updates = 0;
+    const Counter zeroed[] = {C_FLOORS, C_BINOVER, C_LIMITED, C_WOKEN};
+    for (Counter k : zeroed)
+        SPH_CUDA(ctx, cudaMemsetAsync(ctx->counters + k, 0, sizeof(unsigned long long), ctx->stream));
+    int64_t substeps = 0, updates = 0, sweeps = 0;
     ctx->bin_mode = true;
     auto body = [&]() -> int {
-        int r = bin_assign(ctx, parts, true, dt_max);
+        // every particle opens a step at 0
+        int r;
+        if (limiter && ctx->n > 0) {
+            // the limiter's neighbourhoods come from the cells: build them on the
+            // positions as they are now (the kept density outputs follow the
+            // permutation; every step is still empty, so nothing is predicted)
+            SPH_CUDA(ctx, cudaMemsetAsync(ctx->bin_st, 0, sizeof(int2) * (size_t)ctx->n, ctx->stream));
+            SPH_CUDA(ctx, cudaMemsetAsync(ctx->bin_active, 0, (size_t)ctx->n, ctx->stream));
+            SPH_CUDA(ctx, cudaMemsetAsync(ctx->bins, 0, (size_t)ctx->n, ctx->stream));
+            r = do_build(ctx, parts);
+            if (r) return r;
+        }
+        r = bin_assign(ctx, parts, true, dt_max);
         if (r) return r;
-        r = bin_kick(ctx, parts, true);  // every particle opens a step
+        if (limiter) {
+            r = bin_limit(ctx, parts, true, &sweeps);
+            if (r) return r;
+        }
+        r = bin_open(ctx, parts, true, limiter);
+        if (r) return r;
+        r = bin_kick(ctx, parts, true);
         if (r) return r;
         int64_t s = 0;
         while (s < end) {
             int deepest = 0;
             unsigned long long over = 0;
-            r = bin_max_read(ctx, &deepest, &over);
+            int64_t s_next = end;
+            r = bin_max_read(ctx, &deepest, &over, &s_next);
             if (r) return r;
-            const int64_t dmin = (int64_t)1 << (levels - deepest);
-            const int64_t s_next = (s / dmin + 1) * dmin;
+            if (ctx->n == 0) s_next = end;  // nothing steps: one step end, at dt_max
+            if (s_next <= s || s_next > end) return fail(ctx, SPH_ERR_STATE, "individual time-steps: bad step end");
             r = set_dt(ctx, (double)(s_next - s) * unit);
             if (r) return r;
             r = drift(ctx, parts);
@@ -594,6 +631,12 @@ static int do_step_bins(sph_ctx *ctx, sph_particles *parts, double dt_max, int l
             r = bin_assign(ctx, parts, false, dt_max);
             if (r) return r;
             if (s < end) {
+                if (limiter) {
+                    r = bin_limit(ctx, parts, false, &sweeps);
+                    if (r) return r;
+                }
+                r = bin_open(ctx, parts, false, limiter);
+                if (r) return r;
                 r = bin_kick(ctx, parts, false);  // opening half kick of their next steps
                 if (r) return r;
             }
@@ -613,9 +656,15 @@ static int do_step_bins(sph_ctx *ctx, sph_particles *parts, double dt_max, int l
             SPH_CUDA(ctx, cudaMemcpyAsync(hb.data(), ctx->bins, (size_t)ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
         int deepest = 0;
         unsigned long long over = 0;
-        rc = bin_max_read(ctx, &deepest, &over);  // synchronises the stream
+        rc = bin_max_read(ctx, &deepest, &over, nullptr);  // synchronises the stream
         if (rc) return rc;
         bs->cfl_over = (int64_t)over;
+        SPH_CUDA(ctx, cudaMemcpyAsync(ctx->h_counters + C_LIMITED, ctx->counters + C_LIMITED,
+                                      2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+        SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        bs->limited = (int64_t)ctx->h_counters[C_LIMITED];
+        bs->woken = (int64_t)ctx->h_counters[C_WOKEN];
+        bs->limit_sweeps = sweeps;
         for (int64_t i = 0; i < ctx->n; ++i) bs->bin_count[hb[(size_t)i]]++;
     }
     if (out) {

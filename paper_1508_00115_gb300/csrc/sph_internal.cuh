@@ -61,7 +61,12 @@ enum Counter {
     C_DSTAGED = 20,   // density: sources staged for the distance tests (per tile)
     C_FSTREAM = 21,   // force: sources read
     C_FSTAGED = 22,   // force: sources staged
-    C_NCOUNTERS = 23
+    C_LIMCHG = 23,    // time-step limiter: bins one pass changed
+    C_LIMITED = 24,   // time-step limiter: starting steps whose bin it raised
+    C_WOKEN = 25,     // time-step limiter: steps cut by wake-ups
+    C_TMIN = 26,      // individual time-steps: earliest step end
+    C_LIMACT = 27,    // time-step limiter: particles in the active list
+    C_NCOUNTERS = 28
 };
 
 // Cell grid of one periodic box (every box has side box_size; boxes are batched
@@ -285,6 +290,14 @@ struct sph_ctx {
     // the particles), and scratch for the quantities inactive particles keep
     int8_t *bins = nullptr, *bins_tmp = nullptr;
     uint8_t *bin_active = nullptr, *bin_active_tmp = nullptr;
+    int2 *bin_st = nullptr, *bin_st_tmp = nullptr;  // {start, end} of each particle's current step
+    int8_t *bins_cfl = nullptr;   // SPH_FLAG_BIN_LIMITER: the bins before the limiter's passes
+    int32_t *lim_cell = nullptr;  // SPH_FLAG_BIN_LIMITER: (top-level) cell of each slot
+    int *lim_want = nullptr;      // SPH_FLAG_BIN_LIMITER: bins gathered by / scattered to each particle
+    int *lim_list = nullptr;      // SPH_FLAG_BIN_LIMITER: the active slots
+    int *lim_cmax = nullptr;      // SPH_FLAG_BIN_LIMITER: per cell largest bin, smallest sleeping bin,
+                                  // then 2 x cells of changed-cell flags
+    int64_t lim_cmax_cap = 0;
     float *bin_s32 = nullptr;  // 5 * cap: rho, P, c, f, curl while permuting
     int64_t bin_cap = 0;
     bool bin_mode = false;     // inside sph_step_bins: builds also permute the above
@@ -358,7 +371,10 @@ int bin_permute(sph_ctx *ctx, sph_particles *parts);  // after each permutation:
 int bin_active(sph_ctx *ctx, unsigned long long *n_active);  // active mask at ctx->bin_now (host read)
 int bin_kick(sph_ctx *ctx, sph_particles *parts, bool all);  // half of each particle's own step
 int bin_assign(sph_ctx *ctx, sph_particles *parts, bool all, double dt_max);  // new bins from the CFL step
-int bin_max_read(sph_ctx *ctx, int *max_bin, unsigned long long *over);  // deepest bin in use (host read)
+int bin_max_read(sph_ctx *ctx, int *max_bin, unsigned long long *over,
+                 int64_t *t_min);  // deepest bin in use, earliest step end (host read)
+int bin_limit(sph_ctx *ctx, sph_particles *parts, bool all, int64_t *sweeps);  // limiter passes (host reads)
+int bin_open(sph_ctx *ctx, sph_particles *parts, bool all, bool limiter);    // open steps; wake-ups
 // sph_hpredict.cu
 int hp_init(sph_ctx *ctx, uint64_t seed);
 int hp_load(sph_ctx *ctx, const uint16_t *w_bf16, const float *f32);

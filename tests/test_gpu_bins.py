@@ -137,3 +137,91 @@ def test_bins_edge_cases():
     cons, st = ctx0.step_bins(p0, 1e-3, 3)
     assert st["substeps"] == 1 and st["updates"] == 0 and cons["e_tot"] == 0.0
     assert ctx0.bins().size == 0
+
+
+def _blast(n, seed, lattice=False):
+    """A hot sphere (u = 10) in cold gas at rest (u = 1e-4): CFL steps ~350x apart.
+    lattice: n^3 particles on a jittered lattice (nearly equal h), else n random."""
+    if lattice:
+        d = inputs.lattice(n, 1.0, jitter=0.3, seed=seed, u0=1e-4)
+        n = d["x"].size
+    else:
+        d = inputs.uniform(n, seed=seed)
+    for k in ("vx", "vy", "vz"):
+        d[k] = np.zeros(n)
+    d["u"] = np.full(n, 1e-4)
+    r2 = (d["x"] - 0.5) ** 2 + (d["y"] - 0.5) ** 2 + (d["z"] - 0.5) ** 2
+    d["u"][r2 < (0.15 if lattice else 0.12) ** 2] = 10.0
+    return d
+
+
+@pytest.mark.parametrize("grid", ["uniform", "adaptive", "uniform-wide"])
+def test_limiter_matches_oracle(grid):
+    """The time-step limiter with wake-up against oracle.step_bins(limiter=2) on a blast
+    into cold gas: the same bins, substeps, particle updates, raised bins and
+    wake-ups (all integers), and the state within the tolerances above.  The limiter's
+    neighbour decisions are FP64 on both sides; the pairs that decide a raise sit
+    next to a jump of several bins, far from the h boundary in this setup.
+    uniform-wide: a 12^3 jittered lattice, the grid planned from h guesses 1.8x below
+    the converged h (between 1.4 and 1.6 cell sides, within the 1.8 up to which the
+    plan is kept): every cutoff exceeds the cell side, and the limiter searches the
+    125 cells around each particle."""
+    from paper_1508_00115_gb300 import binding
+    levels = 8
+    d = _blast(12, 41, lattice=True) if grid == "uniform-wide" else _blast(1200, 41)
+    n = int(d["x"].size)
+    s = oracle.State(**{k: np.asarray(d[k], np.float64) for k in inputs.FIELDS})
+    acc = oracle.hydro(s)
+    dtc = 0.1 * acc["h"] / acc["vsig"]
+    dt_max = 16.0 * dtc.min()
+    for _ in range(40):
+        ref, racc, rst = oracle.step_bins(s, acc, dt_max, levels, limiter=binding.SPH_BIN_LIMIT_LEVELS)
+        if rst["margin"] > 5e-5:
+            break
+        dt_max *= 1.0173
+    else:
+        pytest.fail("no dt_max with clear bin decisions")
+    assert rst["limited"] > 0 and rst["woken"] > 0
+    flags = binding.SPH_FLAG_BIN_LIMITER | (binding.SPH_FLAG_ADAPTIVE if grid == "adaptive" else 0)
+    ctx = binding.Context(n, h_tol=1e-6, flags=flags)
+    if grid == "uniform-wide":
+        d = dict(d, h=acc["h"] / 1.8)
+    parts = binding.Particles(d)
+    ctx.build_cells(parts)
+    if grid == "uniform-wide":
+        L = ctx.stats()["cell_size"]
+        assert acc["h"].min() > 1.05 * L and acc["h"].max() < 1.8 * L
+    ctx.density(parts)
+    ctx.force(parts)
+    cons, st = ctx.step_bins(parts, dt_max, levels)
+    g = parts.numpy()
+    idx = ctx.permutation()
+    assert np.array_equal(ctx.bins(), rst["bins"][idx])
+    assert st["substeps"] == rst["substeps"] and st["updates"] == rst["active"]
+    assert st["limited"] == rst["limited"] and st["woken"] == rst["woken"]
+    assert st["cfl_over"] == rst["over"] and st["limit_sweeps"] >= st["substeps"]
+    for k in ("x", "y", "z"):
+        dx = g[k] - getattr(ref, k)[idx]
+        dx -= np.rint(dx)
+        assert np.abs(dx).max() < 1e-7, k
+    vscale = np.sqrt(np.mean(ref.vx ** 2 + ref.vy ** 2 + ref.vz ** 2))
+    for k in ("vx", "vy", "vz"):
+        assert np.abs(g[k] - getattr(ref, k)[idx]).max() < 1e-4 * vscale, k
+    assert (np.abs(g["u"] - ref.u[idx]) / ref.u[idx]).max() < 1e-4
+    assert (np.abs(g["h"] - ref.h[idx]) / ref.h[idx]).max() < 1e-4
+
+
+def test_limiter_off_is_unchanged_and_on_is_a_no_op_in_one_bin():
+    """Every particle in one bin: the limiter finds nothing to raise or wake, and the
+    run is bit for bit the one without it (and both the repeated global step)."""
+    from paper_1508_00115_gb300 import binding
+    d = inputs.random_velocities(inputs.lattice(16, 1.0, jitter=0.1, seed=8, u0=1.0), 0.02, 9)
+    c1, p1 = _hydro_ctx(d)
+    c2, p2 = _hydro_ctx(d, flags=binding.SPH_FLAG_BIN_LIMITER)
+    g = p1.numpy()
+    dt_max = 2.9 * float(np.min(0.1 * g["h"].astype(np.float64) / g["vsig"].astype(np.float64)))
+    _, s1 = c1.step_bins(p1, dt_max, 4)
+    _, s2 = c2.step_bins(p2, dt_max, 4)
+    assert s2["limited"] == 0 and s2["woken"] == 0 and s2["limit_sweeps"] == s2["substeps"]
+    assert s1["limit_sweeps"] == 0
+    _equal(p1.numpy(), p2.numpy())
