@@ -394,6 +394,7 @@ int cell_keys_out(sph_ctx *ctx, int32_t *dev_keys);             // sph_cells.cu
 int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool active_list);  // sph_pairs.cu
 int compact_active_tiles(sph_ctx *ctx);                                    // sph_pairs.cu
 int compact_active_leaf_tiles(sph_ctx *ctx);  // adaptive cells: tiles of active targets only  // sph_tree.cu
+int order_tiles(sph_ctx *ctx, int4 *tiles, const int *n_tiles);  // adaptive: longest-first tile groups  // sph_tree.cu
 int run_force_pass(sph_ctx *ctx, sph_particles *parts, bool active_list = false);  // sph_pairs.cu
 int run_gravity_pass(sph_ctx *ctx, double G, double eps, float *ax, float *ay, float *az, float *phi);  // sph_gravity.cu
 int ensure_sym(sph_ctx *ctx);  // slot arrays of the symmetric force pass           // sph_pairs.cu

@@ -1025,6 +1025,7 @@ static int build_tree_device(sph_ctx *ctx, sph_particles *parts)
                                               T.node_leaf, T.leaf_cen, ctx->d_boxes, ctx->n_boxes, ctx->p.box_size,
                                               T.list_off, T.list, T.leaf_scale);
     SPH_LAUNCH(ctx, "pair fill");
+    if ((rc = order_tiles(ctx, ctx->tiles, ctx->n_tiles))) return rc;
     ctx->built = true;
     ctx->density_valid = false;
     return SPH_OK;
@@ -1332,6 +1333,7 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
                                                                 ctx->p.box_size, T.list_off, T.list, T.leaf_scale);
             SPH_LAUNCH(ctx, "pair fill");
         }
+        if ((rc = order_tiles(ctx, ctx->tiles, ctx->n_tiles))) return rc;
     } else {
         SPH_CUDA(ctx, cudaMemsetAsync(ctx->n_tiles, 0, sizeof(int), ctx->stream));
     }
@@ -1416,6 +1418,104 @@ int tree_cell_keys_out(sph_ctx *ctx, int32_t *dev_keys)
     return SPH_OK;
 }
 
+// ------------------------------------------------ work order of the pair passes
+// A pass hands its tile groups out by a ticket, in array order.  On uneven batched
+// boxes the costliest tiles take ~40 % of a warp's share of a pass, and one of them
+// taken late leaves its SM working alone at the end (measured: the last SM busy
+// ~30 % past the others).  So the groups are put in descending order of cost --
+// longest first, as in list scheduling -- estimated as the sources their leaf's list
+// streams, by octaves: a counting sort on log2 of the cost.  The order within an
+// octave is whatever the atomics give; a tile's sums do not depend on when it runs.
+// Groups of 32 / TW tiles move together (TW = 16: two tiles share a warp's batches),
+// and a partial last group keeps its place.
+constexpr int kOrderOctaves = 32;
+
+__global__ void k_order_key(const int4 *__restrict__ tiles, const int *__restrict__ n_tiles, int tpw,
+                            const uint32_t *__restrict__ list_off, const float4 *__restrict__ list,
+                            const int2 *__restrict__ rng, uint32_t *__restrict__ key, unsigned *__restrict__ hist)
+{
+    __shared__ unsigned sh[kOrderOctaves];
+    if (threadIdx.x < kOrderOctaves) sh[threadIdx.x] = 0u;
+    __syncthreads();
+    const int ng = *n_tiles / tpw;  // whole groups
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        unsigned cost = 1u;
+        for (int s = 0; s < tpw; ++s) {
+            const int lf = tiles[g * tpw + s].x;
+            unsigned c = 0u;
+            for (uint32_t e = list_off[lf], e1 = list_off[lf + 1]; e < e1; ++e) {
+                const int2 r = rng[__float_as_int(list[e].w)];
+                c += (unsigned)(r.y - r.x);
+            }
+            cost = max(cost, c);
+        }
+        const unsigned b = 31u - __clz(cost);
+        key[g] = b;
+        atomicAdd(&sh[b], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < kOrderOctaves && sh[threadIdx.x]) atomicAdd(&hist[threadIdx.x], sh[threadIdx.x]);
+}
+
+// hist[0..31]: groups per octave -> hist[32 + b]: first position of octave b, the
+// largest octave first (one warp)
+__global__ void k_order_base(unsigned *hist)
+{
+    const int lane = threadIdx.x & 31, b = 31 - lane;
+    const unsigned v = hist[b];
+    unsigned incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned u = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += u;
+    }
+    hist[32 + b] = incl - v;
+}
+
+__global__ void k_order_scatter(const int4 *__restrict__ tiles, const int *__restrict__ n_tiles, int tpw,
+                                const uint32_t *__restrict__ key, unsigned *__restrict__ cursor,
+                                int4 *__restrict__ out)
+{
+    const int nt = *n_tiles, ng = nt / tpw;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        const unsigned pos = atomicAdd(&cursor[key[g]], 1u);
+        for (int s = 0; s < tpw; ++s) out[pos * tpw + s] = tiles[g * tpw + s];
+    }
+    const int t = ng * tpw + blockIdx.x * blockDim.x + threadIdx.x;  // the partial group, in place
+    if (t < nt) out[t] = tiles[t];
+}
+
+__global__ void k_copy_tiles(const int4 *__restrict__ src, const int *__restrict__ n_tiles, int4 *__restrict__ dst)
+{
+    const int nt = *n_tiles;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) dst[t] = src[t];
+}
+
+// Longest-first order of the tile groups of `tiles` (adaptive cells; device count).
+// Scratch: the uniform grid's tile flags and positions (unused with adaptive cells)
+// and the build's gather scratch (free once the cells are built).
+int order_tiles(sph_ctx *ctx, int4 *tiles, const int *n_tiles)
+{
+    AdaptiveTree &T = ctx->tree;
+    if (!ctx->adaptive || ctx->n <= 0 || !T.list_off || !T.list) return SPH_OK;
+    if ((int64_t)sizeof(double) * 6 * ctx->cap < (int64_t)sizeof(int4) * ctx->tile_cap) return SPH_OK;  // tiny sets
+    const int tpw = 32 / ctx->tile_w;
+    unsigned *hist = ctx->tile_pos;
+    int4 *out = reinterpret_cast<int4 *>(ctx->s64);
+    const unsigned gp = (unsigned)(8 * sm_count(ctx));
+    SPH_CUDA(ctx, cudaMemsetAsync(hist, 0, sizeof(unsigned) * 2 * kOrderOctaves, ctx->stream));
+    k_order_key<<<gp, 256, 0, ctx->stream>>>(tiles, n_tiles, tpw, T.list_off, T.list, T.leaf_rng, ctx->tile_flag,
+                                             hist);
+    SPH_LAUNCH(ctx, "tile order keys");
+    k_order_base<<<1, 32, 0, ctx->stream>>>(hist);
+    SPH_LAUNCH(ctx, "tile order octaves");
+    k_order_scatter<<<gp, 256, 0, ctx->stream>>>(tiles, n_tiles, tpw, ctx->tile_flag, hist + kOrderOctaves, out);
+    SPH_LAUNCH(ctx, "tile order scatter");
+    k_copy_tiles<<<gp, 256, 0, ctx->stream>>>(out, n_tiles, tiles);
+    SPH_LAUNCH(ctx, "tile order copy");
+    return SPH_OK;
+}
+
 int compact_active_leaf_tiles(sph_ctx *ctx)
 {
     AdaptiveTree &T = ctx->tree;
@@ -1436,7 +1536,7 @@ int compact_active_leaf_tiles(sph_ctx *ctx)
                                                          T.nkids, T.nact_leaf, ctx->d_boxes, ctx->n_boxes, &T.dc->err,
                                                          ctx->counters + C_UNCONV, ctx->act_tiles, ctx->n_act_tiles);
         SPH_LAUNCH(ctx, "leaf active tiles");
-        return SPH_OK;
+        return order_tiles(ctx, ctx->act_tiles, ctx->n_act_tiles);
     }
     const int nl = T.n_leaves;
     if (nl <= 0) {
@@ -1459,7 +1559,7 @@ int compact_active_leaf_tiles(sph_ctx *ctx)
                                                                T.nkids, T.nact_leaf, ctx->d_boxes, ctx->n_boxes,
                                                                nullptr, nullptr, ctx->act_tiles, ctx->n_act_tiles);
     SPH_LAUNCH(ctx, "leaf active tiles");
-    return SPH_OK;
+    return order_tiles(ctx, ctx->act_tiles, ctx->n_act_tiles);
 }
 
 void free_tree(sph_ctx *ctx)
