@@ -680,13 +680,16 @@ static int do_step_bins(sph_ctx *ctx, sph_particles *parts, double dt_max, int l
 
 // --------------------------------------------------------- graph-captured steps
 
-// flags of one step, ORed into C_GFLAGS: 1 = unconverged h, 2 = h beyond the cells
+// flags of one step, ORed into C_GFLAGS: 1 = unconverged h, 2 = h beyond the cells,
+// 4 = h below what the uniform grid's FP32 frame resolves, 8 = a tensor-core wait of
+// the learned-h inference ran out
 __global__ void k_step_flags(unsigned long long *c)
 {
     unsigned long long f = 0;
     if (c[C_UNCONV]) f |= 1ull;
     if (c[C_HFLAG]) f |= 2ull;
     if (c[C_PREC]) f |= 4ull;
+    if (c[C_TCERR]) f |= 8ull;
     c[C_GFLAGS] |= f;
 }
 
@@ -877,6 +880,7 @@ static int do_steps(sph_ctx *ctx, sph_particles *parts, int n_steps, double dt, 
         if (rc) return rc;
     }
     const unsigned long long gf = ctx->h_counters[C_GFLAGS];
+    if (gf & 8ull) return fail(ctx, SPH_ERR_TIMEOUT, "predictor: a tensor-core wait ran out in a captured step");
     if (gf & 2ull) return fail(ctx, SPH_ERR_H_EXCEEDS_CELL, "some h grew beyond twice the planned cell side");
     if (gf & 1ull) return fail(ctx, SPH_ERR_NOT_CONVERGED, "smoothing lengths not converged in a captured step");
     if (gf & 4ull) return fail(ctx, SPH_ERR_PRECISION, "uniform grid: some h fell below cell side / SPH_FRAME_RATIO");

@@ -17,8 +17,9 @@
 //   model: z = (f - mean) / sd;  y = W3 silu(W2 silu(W1 z + b1) + b2) + b3
 //          (6 -> 64 -> 64 -> 1, SiLU); log(h0 / h_prev) = y * sd_y + mean_y,
 //          clamped to [log 1/2, log g_max]
-//   inference: BF16 weights and activations, FP32 accumulation, on the tensor
-//          cores (mma.sync m16n8k16, 16 particles per warp and step)
+//   inference: BF16 weights and activations, FP32 accumulation, on the 5th-
+//          generation tensor cores: tcgen05.mma with operands in shared memory and
+//          the accumulators in tensor memory, 128 particles per MMA tile
 //   training: MSE on the normalised target, Adam, FP32 master weights; per block
 //          partial gradients reduced in a fixed order (deterministic)
 #include <cuda_bf16.h>
@@ -53,9 +54,11 @@ constexpr int kNBf = kBfW3 + kHid;
 constexpr int kTrThreads = 256, kTrS = 64, kTrSub = 4, kTrBlocks = 64;
 constexpr int kTrBatch = kTrBlocks * kTrSub * kTrS;  // 16384
 
-constexpr int kHpThreads = 256;  // inference: 8 warps, 16 particles per warp step
 
 __device__ __forceinline__ float silu(float x) { return x / (1.f + __expf(-x)); }
+// inference: the quotient by the fast reciprocal (the activations are rounded to
+// BF16, 2^-9, far above its couple of FP32 ulps)
+__device__ __forceinline__ float silu_fast(float x) { return __fdividef(x, 1.f + __expf(-x)); }
 __device__ __forceinline__ float silu_grad(float x)
 {
     const float s = 1.f / (1.f + __expf(-x));
@@ -68,16 +71,6 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
-// D += A * B, A 16x16 (row), B 16x8 (col), BF16 in, FP32 accumulate
-__device__ __forceinline__ void mma16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
 
 // ------------------------------------------------------------------ features
 
@@ -153,101 +146,240 @@ struct ApplyArgs {
     float *out;             // n: h0, or the log-ratio
     int n;
     float log_lo, log_hi;   // clamp of log(h0 / h_prev)
+    unsigned long long *err;  // set to 1 if a tensor-core wait ran out
 };
 
-__global__ void __launch_bounds__(kHpThreads) k_hp_apply(ApplyArgs a)
+// One CTA of 4 warps takes tiles of 128 particles, the M of the MMAs.  Tensor memory
+// holds the FP32 accumulator, 64 columns: lane r = particle r of the tile, layer 2
+// reusing layer 1's columns once its epilogue has read them; warp w reads lanes
+// 32w..32w+31, so that in the epilogues every thread owns one particle.  64 columns
+// and ~27 KB of shared memory (the features share the buffer of the layer-2
+// operand) let 8 CTAs share an SM, whose epilogues hide one another's MMA and
+// barrier latencies.  One thread issues the MMAs:
+//   layer 1  D1[128 x 64] = Z[128 x 16] W1^T      (one MMA, K = 16: 6 features, zeros)
+//   layer 2  D2[128 x 64] = S1[128 x 64] W2^T     (four MMAs, K = 16 each, accumulating)
+// with S1 = bf16(silu(D1 + b1)) written back to shared memory by the epilogue of
+// layer 1, and y = w3 . silu(D2 + b2) + b3 in the epilogue of layer 2.
+constexpr int kTcM = 128, kTcThreads = 128, kTcCols = 64, kTcPerSm = 8;
+constexpr int kTcSpin = 1 << 22;  // mbarrier polls before a wait counts as run out
+
+// Operands in shared memory, K-major, no swizzle: 8-row x 16-byte core matrices of
+// 128 contiguous bytes, row r at byte 16 (r % 8); element (r, k) of a matrix with kc
+// core matrices per 8-row group at ((r / 8) kc + k / 8) 128 + (r % 8) 16 + (k % 8) 2.
+// Descriptor strides: next core matrix along K 128 bytes (leading byte offset),
+// next 8-row group kc x 128 bytes (stride byte offset).
+__device__ __forceinline__ uint32_t canon_off(int r, int k, int kc)
 {
-    __shared__ uint32_t sW1[kHid * kW1Row / 2];
-    __shared__ uint32_t sW2[kHid * kW2Row / 2];
-    __shared__ float sW3[kHid], sB1[kHid], sB2[kHid];
-    __shared__ float sNorm[kNNorm];
-    const uint32_t *gw = reinterpret_cast<const uint32_t *>(a.wbf);
-    for (int k = threadIdx.x; k < kHid * kW1Row / 2; k += blockDim.x) sW1[k] = gw[kBfW1 / 2 + k];
-    for (int k = threadIdx.x; k < kHid * kW2Row / 2; k += blockDim.x) sW2[k] = gw[kBfW2 / 2 + k];
-    for (int k = threadIdx.x; k < kHid; k += blockDim.x) {
-        const __nv_bfloat16 w = reinterpret_cast<const __nv_bfloat16 *>(a.wbf)[kBfW3 + k];
-        sW3[k] = __bfloat162float(w);
-        sB1[k] = a.params[kOffB1 + k];
-        sB2[k] = a.params[kOffB2 + k];
+    return (uint32_t)((((r >> 3) * kc + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+// shared-memory matrix descriptor: start >> 4 (bits 0-13), leading byte offset >> 4
+// (16-29), stride byte offset >> 4 (32-45), the fixed 0b001 of this descriptor
+// version (46-48), base offset 0, swizzle none (61-63 = 0)
+__device__ __forceinline__ uint64_t umma_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
+           ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
+// BF16 (7-9 = 1, 10-12 = 1), both K-major (15, 16 = 0), N >> 3 (17-22), M >> 4 (24-28)
+constexpr uint32_t kIdescM128N64 = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %3, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %4, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(accumulate), "r"(kIdescM128N64));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+// bounded wait on an mbarrier phase; false if it ran out
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    for (int it = 0; it < kTcSpin; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
     }
-    if (threadIdx.x < kNNorm) sNorm[threadIdx.x] = a.norm[threadIdx.x];
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this warp's 32 lanes (one per thread), waited for
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(kTcThreads) k_hp_apply(ApplyArgs a)
+{
+    // layer-1 activations; its first 4 KB hold the normalised features (K = 16) until
+    // the layer-1 MMA has read them
+    __shared__ __align__(1024) uint8_t sA2[kTcM * kHid * 2];
+    uint8_t *const sA1 = sA2;
+    __shared__ __align__(1024) uint8_t sB1[kHid * 16 * 2];   // W1 (out x in), in padded to 16
+    __shared__ __align__(1024) uint8_t sB2[kHid * kHid * 2]; // W2 (out x in)
+    __shared__ float sW3[kHid], sB1v[kHid], sB2v[kHid], sNorm[kNNorm];
+    __shared__ __align__(8) uint64_t sBar;
+    __shared__ uint32_t sTmem;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(a.wbf);
+    // weights into the canonical layouts (zero padding), biases, normalisation
+    for (int e = tid; e < kHid * 16; e += kTcThreads) {
+        const int o = e >> 4, k = e & 15;
+        const __nv_bfloat16 v = k < kW1Row ? wb[kBfW1 + o * kW1Row + k] : __float2bfloat16_rn(0.f);
+        *reinterpret_cast<__nv_bfloat16 *>(sB1 + canon_off(o, k, 2)) = v;
+    }
+    for (int e = tid; e < kHid * kHid; e += kTcThreads) {
+        const int o = e >> 6, k = e & 63;
+        *reinterpret_cast<__nv_bfloat16 *>(sB2 + canon_off(o, k, 8)) = wb[kBfW2 + o * kW2Row + k];
+    }
+    for (int k = tid; k < kHid; k += kTcThreads) {
+        sW3[k] = __bfloat162float(wb[kBfW3 + k]);
+        sB1v[k] = a.params[kOffB1 + k];
+        sB2v[k] = a.params[kOffB2 + k];
+    }
+    if (tid < kNNorm) sNorm[tid] = a.norm[tid];
+    const uint32_t bar = smem_u32(&sBar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {  // tensor memory: 64 columns x 128 lanes of FP32
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sTmem)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    async_proxy_fence();
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sTmem;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lanes
     const float b3 = a.params[kOffB3];
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int gw_id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int base = gw_id * 16; base < a.n; base += nwarps * 16) {
-        const int r0 = base + g, r1 = base + g + 8;
-        // layer 1: A = normalised features (k 0..5; k 6..15 zero)
-        uint32_t a0 = 0u, a1 = 0u;
-        if (t < 3) {
-            const int k = 2 * t;
-            const float m0 = sNorm[k], m1 = sNorm[k + 1];
-            const float s0 = 1.f / sNorm[kF + k], s1 = 1.f / sNorm[kF + k + 1];
-            float x00 = 0.f, x01 = 0.f, x10 = 0.f, x11 = 0.f;
-            if (r0 < a.n) {
-                x00 = (a.feats[(size_t)6 * r0 + k] - m0) * s0;
-                x01 = (a.feats[(size_t)6 * r0 + k + 1] - m1) * s1;
+    const uint32_t a1 = smem_u32(sA1), a2 = smem_u32(sA2), b1 = smem_u32(sB1), b2 = smem_u32(sB2);
+    uint32_t parity = 0u;
+    bool ok = true;
+    const int ntile = (a.n + kTcM - 1) / kTcM;
+    for (int tile = blockIdx.x; tile < ntile && ok; tile += gridDim.x) {
+        const int p = tile * kTcM + tid;  // this thread's particle (row tid of the tile)
+        // layer-1 operand: (f - mean) / sd in BF16, columns 6-15 zero
+        {
+            __nv_bfloat16 z[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) z[k] = __float2bfloat16_rn(0.f);
+            if (p < a.n) {
+#pragma unroll
+                for (int k = 0; k < kF; ++k)
+                    z[k] = __float2bfloat16_rn((a.feats[(size_t)kF * p + k] - sNorm[k]) * (1.f / sNorm[kF + k]));
             }
-            if (r1 < a.n) {
-                x10 = (a.feats[(size_t)6 * r1 + k] - m0) * s0;
-                x11 = (a.feats[(size_t)6 * r1 + k + 1] - m1) * s1;
-            }
-            a0 = pack_bf16(x00, x01);
-            a1 = pack_bf16(x10, x11);
+            *reinterpret_cast<uint4 *>(sA1 + canon_off(tid, 0, 2)) = *reinterpret_cast<const uint4 *>(&z[0]);
+            *reinterpret_cast<uint4 *>(sA1 + canon_off(tid, 8, 2)) = *reinterpret_cast<const uint4 *>(&z[8]);
         }
-        float c1[8][4];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            c1[j][0] = c1[j][1] = c1[j][2] = c1[j][3] = 0.f;
-            mma16816(c1[j], a0, a1, 0u, 0u, sW1[(8 * j + g) * (kW1Row / 2) + t], 0u);
+        async_proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            umma_bf16(tmem, umma_sdesc(a1, 128, 256), umma_sdesc(b1, 128, 256), 0u);
+            umma_commit(bar);
         }
-        // bias, SiLU, repack as the A operand of layer 2 (two n-tiles = one k-tile)
-        uint32_t A2[4][4];
+        ok = __syncthreads_and(mbar_wait(bar, parity)) != 0;
+        parity ^= 1u;
+        if (!ok) break;
+        tc_fence_after();
+        // epilogue 1: bias, SiLU, BF16 -> the layer-2 operand
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int u = 8 * j + 2 * t;
-            const float v0 = silu(c1[j][0] + sB1[u]), v1 = silu(c1[j][1] + sB1[u + 1]);
-            const float v2 = silu(c1[j][2] + sB1[u]), v3 = silu(c1[j][3] + sB1[u + 1]);
-            A2[j >> 1][(j & 1) * 2 + 0] = pack_bf16(v0, v1);
-            A2[j >> 1][(j & 1) * 2 + 1] = pack_bf16(v2, v3);
-        }
-        // layer 2: 4 k-tiles x 8 n-tiles
-        float c2[8][4];
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tmem_ld32(tmem + lane_base + (uint32_t)(32 * h), v);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            c2[j][0] = c2[j][1] = c2[j][2] = c2[j][3] = 0.f;
-            const uint32_t *row = sW2 + (8 * j + g) * (kW2Row / 2);
+            for (int c = 0; c < 4; ++c) {
+                __nv_bfloat16 s8[8];
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-                mma16816(c2[j], A2[kk][0], A2[kk][1], A2[kk][2], A2[kk][3], row[8 * kk + t], row[8 * kk + 4 + t]);
-        }
-        // layer 3: dot with W3, reduced over the 4 lanes of a row group
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int u = 8 * j + 2 * t;
-            s0 = fmaf(silu(c2[j][0] + sB2[u]), sW3[u], s0);
-            s0 = fmaf(silu(c2[j][1] + sB2[u + 1]), sW3[u + 1], s0);
-            s1 = fmaf(silu(c2[j][2] + sB2[u]), sW3[u], s1);
-            s1 = fmaf(silu(c2[j][3] + sB2[u + 1]), sW3[u + 1], s1);
-        }
-        s0 += __shfl_xor_sync(kFull, s0, 1);
-        s0 += __shfl_xor_sync(kFull, s0, 2);
-        s1 += __shfl_xor_sync(kFull, s1, 1);
-        s1 += __shfl_xor_sync(kFull, s1, 2);
-        if (t == 0) {
-            const float ym = sNorm[2 * kF], ys = sNorm[2 * kF + 1];
-            if (r0 < a.n) {
-                const float y = fminf(fmaxf((s0 + b3) * ys + ym, a.log_lo), a.log_hi);
-                a.out[r0] = a.h_prev ? a.h_prev[r0] * __expf(y) : y;
-            }
-            if (r1 < a.n) {
-                const float y = fminf(fmaxf((s1 + b3) * ys + ym, a.log_lo), a.log_hi);
-                a.out[r1] = a.h_prev ? a.h_prev[r1] * __expf(y) : y;
+                for (int e = 0; e < 8; ++e) {
+                    const int j = 32 * h + 8 * c + e;
+                    s8[e] = __float2bfloat16_rn(silu_fast(v[8 * c + e] + sB1v[j]));
+                }
+                *reinterpret_cast<uint4 *>(sA2 + canon_off(tid, 32 * h + 8 * c, 8)) =
+                    *reinterpret_cast<const uint4 *>(s8);
             }
         }
+        async_proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)  // K = 16 per MMA: two core matrices along K
+                umma_bf16(tmem, umma_sdesc(a2 + 256 * kk, 128, 1024), umma_sdesc(b2 + 256 * kk, 128, 1024),
+                          kk > 0 ? 1u : 0u);
+            umma_commit(bar);
+        }
+        ok = __syncthreads_and(mbar_wait(bar, parity)) != 0;
+        parity ^= 1u;
+        if (!ok) break;
+        tc_fence_after();
+        // epilogue 2: bias, SiLU, dot with W3 (FP32), de-normalise, clamp
+        float s = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tmem_ld32(tmem + lane_base + (uint32_t)(32 * h), v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) s = fmaf(silu_fast(v[e] + sB2v[32 * h + e]), sW3[32 * h + e], s);
+        }
+        if (p < a.n) {
+            const float y = fminf(fmaxf((s + b3) * sNorm[2 * kF + 1] + sNorm[2 * kF], a.log_lo), a.log_hi);
+            a.out[p] = a.h_prev ? a.h_prev[p] * __expf(y) : y;
+        }
+        tc_fence_before();
+        __syncthreads();  // every lane read its columns before the next tile's MMAs
     }
+    if (!ok) {
+        if (tid == 0) atomicOr(a.err, 1ull);
+        // an MMA may still be in flight: give it one more bounded wait before the
+        // tensor memory is released
+        __syncthreads_and(mbar_wait(bar, parity ^ 1u));
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
 }
 
 // FP32 parameters -> BF16 inference copy (padding zero)
@@ -658,13 +790,14 @@ int hp_features(sph_ctx *ctx, sph_particles *parts)
     return SPH_OK;
 }
 
+// persistent grid: at most 8 CTAs per SM (8 x 64 of the 512 tensor-memory columns)
 static int hp_grid(sph_ctx *ctx, int64_t n)
 {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (sms <= 0) sms = 148;
-    const int64_t want = (n + 16 * (kHpThreads / 32) - 1) / (16 * (kHpThreads / 32));
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
+    const int64_t want = (n + kTcM - 1) / kTcM;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * kTcPerSm));
 }
 
 // MLP on arbitrary features: out = log-ratio (h_prev null) or h_prev * exp(log-ratio)
@@ -672,9 +805,20 @@ int hp_run(sph_ctx *ctx, const float *feats, const float *h_prev, float *out, in
 {
     if (!ctx->hp.ready) return fail(ctx, SPH_ERR_STATE, "no predictor weights (init, load or train first)");
     if (n <= 0) return SPH_OK;
-    ApplyArgs a{feats, ctx->hp.wbf, ctx->hp.params, ctx->hp.norm, h_prev, out, (int)n, log_lo, log_hi};
-    k_hp_apply<<<hp_grid(ctx, n), kHpThreads, 0, ctx->stream>>>(a);
+    ApplyArgs a{feats, ctx->hp.wbf, ctx->hp.params, ctx->hp.norm, h_prev, out, (int)n, log_lo, log_hi,
+                ctx->counters + C_TCERR};
+    k_hp_apply<<<hp_grid(ctx, n), kTcThreads, 0, ctx->stream>>>(a);
     SPH_LAUNCH(ctx, "predictor mlp");
+    // outside a capture the run-out flag is read here; captured steps fold it into
+    // the step flags
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    SPH_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+        SPH_CUDA(ctx, cudaMemcpyAsync(ctx->h_counters + C_TCERR, ctx->counters + C_TCERR, sizeof(unsigned long long),
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+        SPH_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (ctx->h_counters[C_TCERR]) return fail(ctx, SPH_ERR_TIMEOUT, "predictor: a tensor-core wait ran out");
+    }
     return SPH_OK;
 }
 

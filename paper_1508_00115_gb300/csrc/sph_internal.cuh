@@ -46,7 +46,8 @@ enum Counter {
     C_FLOORS = 6,     // u floors
     C_DTARGETS = 7,   // active density targets
     C_GFLAGS = 8,     // multi-step run: OR of per-step flags (1: unconverged, 2: h beyond cells,
-                      // 4: h below what the uniform grid's FP32 frame resolves)
+                      // 4: h below what the uniform grid's FP32 frame resolves, 8: a
+                      // tensor-core wait of the learned-h inference ran out)
     C_SHRINK = 9,     // adaptive: leaves whose largest h fell below kTreeShrink x its build value
     C_WALKOVF = 10,   // adaptive: leaf walks whose stack overflowed
     C_LISTTOT = 11,   // adaptive: neighbour-list entries (64-bit total)
@@ -66,7 +67,8 @@ enum Counter {
     C_WOKEN = 25,     // time-step limiter: steps cut by wake-ups
     C_TMIN = 26,      // individual time-steps: earliest step end
     C_LIMACT = 27,    // time-step limiter: particles in the active list
-    C_NCOUNTERS = 28
+    C_TCERR = 28,     // learned h: a tensor-core (mbarrier) wait of the inference ran out
+    C_NCOUNTERS = 29
 };
 
 // Cell grid of one periodic box (every box has side box_size; boxes are batched
