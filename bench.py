@@ -1091,6 +1091,9 @@ def run_headline(args):
             time.sleep(0.3)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        # named range of the timed region (lets a profiler take just these launches)
+        torch.cuda.nvtx.range_push(("headline_learned" if flags & binding.SPH_FLAG_HPREDICT else "headline_plain") +
+                                   ("_graph" if graph else "_host"))
         e0.record(stream)
         fl = 0
         if graph:
@@ -1101,6 +1104,7 @@ def run_headline(args):
                 _, cons = c.step(parts)
                 fl += cons["u_floors"]
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         clocks = sampler.stop() if sampler else None
         ms_ = _max_over_ranks(e0.elapsed_time(e1), dist)
