@@ -520,7 +520,9 @@ def run_ours(args):
                       "cell_factor": round(float(st["cell_factor"]), 3),
                       "schedule": "autotuned" if args.tile_width == 0 and args.cell_factor == 0
                                   else "fixed",
-                      "pruning": "axis sweep + tile box" if args.axis_sweep else "tile box",
+                      "pruning": "axis sweep + tile box" if st["axis_sweep"] else "tile box",
+                      "pruning_chosen_by": "autotuner" if args.tile_width == 0 and args.cell_factor == 0
+                                           else "--axis-sweep",
                       "l2": f"inputs larger than L2 (~{work_mb:.0f} MB resident per step > 129 MB)",
                       "parallelism": f"replicas x{world}"},
            "pair_interactions_per_s": world * pairs / sec,

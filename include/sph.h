@@ -76,8 +76,13 @@ typedef struct sph_ctx sph_ctx; /* opaque, library-owned */
                                 32/64/128) the cell build, one density pass and one
                                 force pass on the current particles and keep the
                                 fastest; overrides tile_width and cell_factor
-                                (leaf_max).  That first sph_density call also writes
-                                the force outputs (ax..vsig) of the probes. */
+                                (leaf_max).  On the uniform grid it then times, at
+                                that schedule, the staging with and without
+                                SPH_FLAG_AXIS_SWEEP (build + density + force) and the
+                                force pass in gather and symmetric form, and keeps
+                                the faster of each (sph_stats.axis_sweep,
+                                force_symmetric).  That first sph_density call also
+                                writes the force outputs (ax..vsig) of the probes. */
 #define SPH_FLAG_ADAPTIVE 8u /* adaptive cells (Sec. 3.1): the uniform grid becomes the
                                 top level of an octree refined while a node holds more
                                 than leaf_max particles; leaves are the work items,
@@ -228,6 +233,7 @@ typedef struct {
     int64_t grav_pairs;        /* gravity near-field pair interactions (j != i)        */
     double t_grav_ms;          /* summed device time of gravity launches (TIMING)     */
     int32_t force_symmetric;   /* force pass in use: 1 symmetric variant, 0 gather     */
+    int32_t axis_sweep;        /* staging in use: 1 per-axis sorted sweep, 0 box test  */
     int64_t density_streamed;  /* density: sources read from the leaf lists, all tiles */
                                /* (adaptive cells; 0 on the uniform grid)             */
     int64_t density_staged;    /* density: of those, staged past the tile's box test   */

@@ -104,7 +104,8 @@ class sph_stats(ctypes.Structure):
                 ("graph_steps", ctypes.c_int64), ("leaf_max", ctypes.c_int32),
                 ("hp_samples", ctypes.c_int64), ("grav_passes", ctypes.c_int64),
                 ("grav_pairs", ctypes.c_int64), ("t_grav_ms", ctypes.c_double),
-                ("force_symmetric", ctypes.c_int32), ("density_streamed", ctypes.c_int64),
+                ("force_symmetric", ctypes.c_int32), ("axis_sweep", ctypes.c_int32),
+                ("density_streamed", ctypes.c_int64),
                 ("density_staged", ctypes.c_int64), ("force_streamed", ctypes.c_int64),
                 ("force_staged", ctypes.c_int64)]
 

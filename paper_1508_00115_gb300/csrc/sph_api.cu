@@ -212,7 +212,7 @@ static int autotune(sph_ctx *ctx, sph_particles *parts)
     int best_tw = ctx->tile_w;
     float best_cf = ctx->p.cell_factor;
     int best_leaf = ctx->leaf_max;
-    const uint32_t flags = ctx->p.flags;
+    uint32_t flags = ctx->p.flags;
     ctx->p.flags &= ~SPH_FLAG_TIMING;  // probes are not part of the statistics
     int rc = SPH_OK;
     for (int a = 0; a < 2 && rc == SPH_OK; ++a)
@@ -263,7 +263,37 @@ static int autotune(sph_ctx *ctx, sph_particles *parts)
     ctx->p.cell_factor = best_cf;
     ctx->leaf_max = best_leaf;
     ctx->tuned = true;
-    rc = build_cells(ctx, parts);
+    if (!ctx->adaptive) {
+        // staging of the pair passes: tile-box pruning alone, or after the per-axis
+        // sorted sweep (SPH_FLAG_AXIS_SWEEP; Sec. 3.1, sorting) -- each a build (with
+        // its 13 per-cell sorts) plus a density and a force pass, timed twice, the
+        // faster repetition counting
+        ctx->p.flags &= ~SPH_FLAG_TIMING;
+        float ts[2] = {1e30f, 1e30f};
+        for (int v = 0; v < 2 && rc == SPH_OK; ++v) {
+            if (v) ctx->p.flags |= SPH_FLAG_AXIS_SWEEP;
+            else ctx->p.flags &= ~SPH_FLAG_AXIS_SWEEP;
+            for (int r = 0; r < 2 && rc == SPH_OK; ++r) {
+                SPH_CUDA(ctx, cudaEventRecord(ev[0], ctx->stream));
+                rc = build_cells(ctx, parts);
+                if (rc) break;
+                SPH_CUDA(ctx, cudaMemsetAsync(ctx->active, 1, ctx->n, ctx->stream));
+                rc = run_density_pass(ctx, parts, true, false);
+                if (rc == SPH_OK) rc = cell_reach(ctx);
+                if (rc == SPH_OK) rc = run_force_pass(ctx, parts);
+                if (rc) break;
+                SPH_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
+                SPH_CUDA(ctx, cudaEventSynchronize(ev[1]));
+                float ms = 0.f;
+                SPH_CUDA(ctx, cudaEventElapsedTime(&ms, ev[0], ev[1]));
+                ts[v] = std::min(ts[v], ms);
+            }
+        }
+        const uint32_t sweep = ts[1] < ts[0] ? SPH_FLAG_AXIS_SWEEP : 0u;
+        flags = (flags & ~SPH_FLAG_AXIS_SWEEP) | sweep;
+        ctx->p.flags = (ctx->p.flags & ~SPH_FLAG_AXIS_SWEEP) | sweep;
+    }
+    if (rc == SPH_OK) rc = build_cells(ctx, parts);
     if (rc == SPH_OK && !ctx->adaptive) {
         // force pass: gather form or the symmetric variant (each unordered pair once),
         // each timed twice at these smoothing lengths, the faster repetition counting
@@ -1175,6 +1205,7 @@ int sph_get_stats(sph_ctx *ctx, sph_stats *s)
     st.t_grav_ms = t[3];
     st.grav_pairs = (int64_t)ctx->h_counters[C_GPAIRS];
     st.force_symmetric = ctx->sym_force ? 1 : 0;
+    st.axis_sweep = (ctx->p.flags & SPH_FLAG_AXIS_SWEEP) && !ctx->adaptive ? 1 : 0;
     st.density_streamed = (int64_t)ctx->h_counters[C_DSTREAM];
     st.density_staged = (int64_t)ctx->h_counters[C_DSTAGED];
     st.force_streamed = (int64_t)ctx->h_counters[C_FSTREAM];

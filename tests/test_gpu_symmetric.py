@@ -117,4 +117,5 @@ def test_autotuner_chooses_a_force_form():
     d = _moving(30000, 19)
     ctx, parts, g = gpu_hydro(d, flags=binding.SPH_FLAG_AUTOTUNE)
     assert g["stats"]["force_symmetric"] in (0, 1)
+    assert g["stats"]["axis_sweep"] in (0, 1)  # the staging it timed and kept
     check_force(g, oracle_state(g))
