@@ -34,15 +34,18 @@ constexpr int kBatchD = 128;  // staged survivors per tile, density (4 hit-mask 
 constexpr int kBatchF = 128;  // staged survivors per tile, force
 constexpr int kSlotF = 132;   // floats per staged-coordinate array (>= kBatchD, even: 8-byte aligned pairs)
 constexpr int kPairThreads = 256;
-// Adaptive cells (leaf lists): a batch's hits are walked as one compacted warp-wide
-// list when they sit on fewer than this many lanes' worth (total hits < kCompactLanes
-// x the largest lane count): the list costs ~6 warp instructions per hit, the
-// lane-by-lane walk ~70 (density) or ~100 (force) per hit of its busiest lane.  The
-// uniform grid's batches mix cells on both sides of the tile, so their hits spread
-// over the lanes: its kernels are compiled without the compacted walk (measured on
-// Sedov 128^3: the extra code alone cost 5-8 %, never taking it).
-constexpr int kCompactLanesD = 8;
-constexpr int kCompactLanesF = 12;
+// Adaptive cells (leaf lists): a batch's hits are walked lane by lane -- each lane its
+// own target's hits, one (force) or two (density) per round -- while at least
+// kWalkBusy lanes still have one; what is left is then laid out as one compacted
+// warp-wide list, 32 hits per round.  A lane-by-lane round costs the same whatever
+// the number of busy lanes, a compacted hit adds the shuffles of the list and of the
+// segmented scan; the thresholds are measured on uneven batched boxes (8 and 10 of
+// 32 lanes: 4/8, 6/10, 6/12, 8/12, 12/16, 16/20 and 20/24 were up to 5 % slower).
+// The uniform grid's batches mix cells on both sides of the tile, so their hits
+// spread over the lanes: its kernels are compiled without the compacted walk
+// (measured on Sedov 128^3: the extra code alone cost 5-8 %, never taking it).
+constexpr int kWalkBusyD = 8;
+constexpr int kWalkBusyF = 10;
 constexpr int kDensityBlocks = 2;  // resident blocks per SM the density kernel is compiled for
 constexpr int kForceBlocks = 2;      // leaf lists (adaptive cells): the compacted walk needs the registers
 constexpr int kForceBlocksU = 3;     // uniform grid: a third block per SM outweighs a few spilled values
@@ -451,117 +454,120 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
                 cy = fmaf(fr, fmaf(v.z, d.x, -v.x * d.z), cy);
                 cz = fmaf(fr, fmaf(v.x, d.y, -v.y * d.x), cz);
             };
-            // Where the batch's hits sit on a few lanes (its sources lie next to a few of
-            // the targets), walking them lane by lane leaves most lanes idle: then the
-            // hits are laid out as one warp-wide list -- lane order, ascending staged
-            // index within a lane -- and taken 32 per round, one per lane, every target's
-            // terms of the round summed by a segmented scan and fetched by its own lane.
-            const int nh = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
-            int hincl = nh;
-#pragma unroll
-            for (int dd = 1; dd < 32; dd <<= 1) {
-                const int v = __shfl_up_sync(kFull, hincl, dd);
-                if (lane >= dd) hincl += v;
-            }
-            const int htot = __shfl_sync(kFull, hincl, 31);
-            const int hoff = hincl - nh;
-            const int hmax = (int)__reduce_max_sync(kFull, (unsigned)nh);
-            if constexpr (LIST) if (htot < kCompactLanesD * hmax) {
-                cnt += nh;
-                if (HASH) {  // integer sums: any order gives the same bits
-                    unsigned h0 = m0, h1 = m1, h2 = m2, h3 = m3;
-                    while (h0 | h1 | h2 | h3) hh += mix64((uint64_t)a.ids[__float_as_int(sA[pop_bit(h0, h1, h2, h3)].w)]);
-                }
-                float4 *wbase = smem + (size_t)wib * (2 * TPW * SLOT);
-                for (int base = 0; base < htot; base += 32) {
-                    const int hq = base + lane;
-                    const bool hv = hq < htot;
-                    // owner lane of hit hq: the last lane whose list starts at or before it
-                    int t = 0;
-#pragma unroll
-                    for (int st = 16; st > 0; st >>= 1)
-                        if (__shfl_sync(kFull, hoff, t + st) <= hq) t += st;
-                    int r = hq - __shfl_sync(kFull, hoff, t);
-                    const unsigned w0 = __shfl_sync(kFull, m0, t), w1 = __shfl_sync(kFull, m1, t);
-                    const unsigned w2 = __shfl_sync(kFull, m2, t), w3 = __shfl_sync(kFull, m3, t);
-                    const float tx = __shfl_sync(kFull, pi.x, t), ty = __shfl_sync(kFull, pi.y, t);
-                    const float tz = __shfl_sync(kFull, pi.z, t), tvx = __shfl_sync(kFull, vi.x, t);
-                    const float tvy = __shfl_sync(kFull, vi.y, t), tvz = __shfl_sync(kFull, vi.z, t);
-                    const float thinv = __shfl_sync(kFull, hinv, t);
-                    float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f, c4 = 0.f, c5 = 0.f, c6 = 0.f, c7 = 0.f;
-                    if (hv) {
-                        int k;
-                        const int p0 = __popc(w0), p1 = __popc(w1), p2 = __popc(w2);
-                        if (r < p0) k = (int)__fns(w0, 0u, r + 1);
-                        else if ((r -= p0) < p1) k = 32 + (int)__fns(w1, 0u, r + 1);
-                        else if ((r -= p1) < p2) k = 64 + (int)__fns(w2, 0u, r + 1);
-                        else k = 96 + (int)__fns(w3, 0u, r - p2 + 1);
-                        k = (unsigned)k < (unsigned)B ? k : 0;  // (never taken: a hit lies in the batch)
-                        const float4 *sAt = wbase + (t / TW) * SLOT;
-                        const float4 sk = sAt[k];
-                        const float4 vj = sAt[TPW * SLOT + k];
-                        const float dx = tx - sk.x, dy = ty - sk.y, dz = tz - sk.z;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                        const float q = r2 * rinv * thinv;
-                        float w, dw;
-                        spline_u(q, w, dw);
-                        const float mj = vj.w;
-                        const float fr = mj * dw * rinv;
-                        const float vx = tvx - vj.x, vy = tvy - vj.y, vz = tvz - vj.z;
-                        c0 = mj * w;
-                        c1 = w;
-                        c2 = q * dw;
-                        c3 = mj * fmaf(q, dw, 3.f * w);
-                        c4 = fr * fmaf(vx, dx, fmaf(vy, dy, vz * dz));
-                        c5 = fr * fmaf(vy, dz, -vz * dy);
-                        c6 = fr * fmaf(vz, dx, -vx * dz);
-                        c7 = fr * fmaf(vx, dy, -vy * dx);
-                    }
-                    // inclusive scan within runs of equal owner (runs are contiguous)
+            // Lane-by-lane rounds, two hits per round (independent instruction streams;
+            // a lane's terms are still added in ascending staged order, so its sums are
+            // those of one at a time), while enough lanes have a hit left.  Then
+            // (adaptive cells) the rest -- the few lanes whose sources lie next to many
+            // hits -- are laid out as one warp-wide list, lane order and ascending
+            // staged index within a lane, and taken 32 per round, one per lane, every
+            // target's terms of the round summed by a segmented scan and fetched by
+            // its own lane.
+            for (;;) {
+                const unsigned busy = __ballot_sync(kFull, (m0 | m1 | m2 | m3) != 0u);
+                if (busy == 0u) break;
+                if constexpr (LIST) if (__popc(busy) < kWalkBusyD) {
+                    const int nh = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
+                    int hincl = nh;
 #pragma unroll
                     for (int dd = 1; dd < 32; dd <<= 1) {
-                        const int tu = __shfl_up_sync(kFull, t, dd);  // every lane takes part
-                        const bool same = lane >= dd && tu == t;
-                        const float u0 = __shfl_up_sync(kFull, c0, dd), u1 = __shfl_up_sync(kFull, c1, dd);
-                        const float u2 = __shfl_up_sync(kFull, c2, dd), u3 = __shfl_up_sync(kFull, c3, dd);
-                        const float u4 = __shfl_up_sync(kFull, c4, dd), u5 = __shfl_up_sync(kFull, c5, dd);
-                        const float u6 = __shfl_up_sync(kFull, c6, dd), u7 = __shfl_up_sync(kFull, c7, dd);
-                        if (same) {
-                            c0 += u0;
-                            c1 += u1;
-                            c2 += u2;
-                            c3 += u3;
-                            c4 += u4;
-                            c5 += u5;
-                            c6 += u6;
-                            c7 += u7;
+                        const int v = __shfl_up_sync(kFull, hincl, dd);
+                        if (lane >= dd) hincl += v;
+                    }
+                    const int htot = __shfl_sync(kFull, hincl, 31);
+                    const int hoff = hincl - nh;
+                    cnt += nh;
+                    if (HASH) {  // integer sums: any order gives the same bits
+                        unsigned h0 = m0, h1 = m1, h2 = m2, h3 = m3;
+                        while (h0 | h1 | h2 | h3) hh += mix64((uint64_t)a.ids[__float_as_int(sA[pop_bit(h0, h1, h2, h3)].w)]);
+                    }
+                    float4 *wbase = smem + (size_t)wib * (2 * TPW * SLOT);
+                    for (int base = 0; base < htot; base += 32) {
+                        const int hq = base + lane;
+                        const bool hv = hq < htot;
+                        // owner lane of hit hq: the last lane whose list starts at or before it
+                        int t = 0;
+#pragma unroll
+                        for (int st = 16; st > 0; st >>= 1)
+                            if (__shfl_sync(kFull, hoff, t + st) <= hq) t += st;
+                        int r = hq - __shfl_sync(kFull, hoff, t);
+                        const unsigned w0 = __shfl_sync(kFull, m0, t), w1 = __shfl_sync(kFull, m1, t);
+                        const unsigned w2 = __shfl_sync(kFull, m2, t), w3 = __shfl_sync(kFull, m3, t);
+                        const float tx = __shfl_sync(kFull, pi.x, t), ty = __shfl_sync(kFull, pi.y, t);
+                        const float tz = __shfl_sync(kFull, pi.z, t), tvx = __shfl_sync(kFull, vi.x, t);
+                        const float tvy = __shfl_sync(kFull, vi.y, t), tvz = __shfl_sync(kFull, vi.z, t);
+                        const float thinv = __shfl_sync(kFull, hinv, t);
+                        float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f, c4 = 0.f, c5 = 0.f, c6 = 0.f, c7 = 0.f;
+                        if (hv) {
+                            int k;
+                            const int p0 = __popc(w0), p1 = __popc(w1), p2 = __popc(w2);
+                            if (r < p0) k = (int)__fns(w0, 0u, r + 1);
+                            else if ((r -= p0) < p1) k = 32 + (int)__fns(w1, 0u, r + 1);
+                            else if ((r -= p1) < p2) k = 64 + (int)__fns(w2, 0u, r + 1);
+                            else k = 96 + (int)__fns(w3, 0u, r - p2 + 1);
+                            k = (unsigned)k < (unsigned)B ? k : 0;  // (never taken: a hit lies in the batch)
+                            const float4 *sAt = wbase + (t / TW) * SLOT;
+                            const float4 sk = sAt[k];
+                            const float4 vj = sAt[TPW * SLOT + k];
+                            const float dx = tx - sk.x, dy = ty - sk.y, dz = tz - sk.z;
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                            const float q = r2 * rinv * thinv;
+                            float w, dw;
+                            spline_u(q, w, dw);
+                            const float mj = vj.w;
+                            const float fr = mj * dw * rinv;
+                            const float vx = tvx - vj.x, vy = tvy - vj.y, vz = tvz - vj.z;
+                            c0 = mj * w;
+                            c1 = w;
+                            c2 = q * dw;
+                            c3 = mj * fmaf(q, dw, 3.f * w);
+                            c4 = fr * fmaf(vx, dx, fmaf(vy, dy, vz * dz));
+                            c5 = fr * fmaf(vy, dz, -vz * dy);
+                            c6 = fr * fmaf(vz, dx, -vx * dz);
+                            c7 = fr * fmaf(vx, dy, -vy * dx);
+                        }
+                        // inclusive scan within runs of equal owner (runs are contiguous)
+#pragma unroll
+                        for (int dd = 1; dd < 32; dd <<= 1) {
+                            const int tu = __shfl_up_sync(kFull, t, dd);  // every lane takes part
+                            const bool same = lane >= dd && tu == t;
+                            const float u0 = __shfl_up_sync(kFull, c0, dd), u1 = __shfl_up_sync(kFull, c1, dd);
+                            const float u2 = __shfl_up_sync(kFull, c2, dd), u3 = __shfl_up_sync(kFull, c3, dd);
+                            const float u4 = __shfl_up_sync(kFull, c4, dd), u5 = __shfl_up_sync(kFull, c5, dd);
+                            const float u6 = __shfl_up_sync(kFull, c6, dd), u7 = __shfl_up_sync(kFull, c7, dd);
+                            if (same) {
+                                c0 += u0;
+                                c1 += u1;
+                                c2 += u2;
+                                c3 += u3;
+                                c4 += u4;
+                                c5 += u5;
+                                c6 += u6;
+                                c7 += u7;
+                            }
+                        }
+                        // each lane fetches the end of its own run in this round
+                        const int lo = hoff - base, hi_ = hoff + nh - base;
+                        const bool mine = nh > 0 && hi_ > 0 && lo < 32;
+                        const int src = mine ? min(hi_, 32) - 1 : lane;
+                        const float g0 = __shfl_sync(kFull, c0, src), g1 = __shfl_sync(kFull, c1, src);
+                        const float g2 = __shfl_sync(kFull, c2, src), g3 = __shfl_sync(kFull, c3, src);
+                        const float g4 = __shfl_sync(kFull, c4, src), g5 = __shfl_sync(kFull, c5, src);
+                        const float g6 = __shfl_sync(kFull, c6, src), g7 = __shfl_sync(kFull, c7, src);
+                        if (mine) {
+                            rb += g0;
+                            wb += g1;
+                            sqdw += g2;
+                            drho += g3;
+                            dv += g4;
+                            cx += g5;
+                            cy += g6;
+                            cz += g7;
                         }
                     }
-                    // each lane fetches the end of its own run in this round
-                    const int lo = hoff - base, hi_ = hoff + nh - base;
-                    const bool mine = nh > 0 && hi_ > 0 && lo < 32;
-                    const int src = mine ? min(hi_, 32) - 1 : lane;
-                    const float g0 = __shfl_sync(kFull, c0, src), g1 = __shfl_sync(kFull, c1, src);
-                    const float g2 = __shfl_sync(kFull, c2, src), g3 = __shfl_sync(kFull, c3, src);
-                    const float g4 = __shfl_sync(kFull, c4, src), g5 = __shfl_sync(kFull, c5, src);
-                    const float g6 = __shfl_sync(kFull, c6, src), g7 = __shfl_sync(kFull, c7, src);
-                    if (mine) {
-                        rb += g0;
-                        wb += g1;
-                        sqdw += g2;
-                        drho += g3;
-                        dv += g4;
-                        cx += g5;
-                        cy += g6;
-                        cz += g7;
-                    }
+                    m0 = m1 = m2 = m3 = 0u;
+                    break;
                 }
-                m0 = m1 = m2 = m3 = 0u;
-            }
-            // two hits per round (independent instruction streams; the terms are still
-            // added in ascending staged order, so the sums are those of one at a time)
-            while (__any_sync(kFull, (m0 | m1 | m2 | m3) != 0u)) {
                 if (m0 | m1 | m2 | m3) {
                     const int k1 = pop_bit(m0, m1, m2, m3);
                     const bool two = (m0 | m1 | m2 | m3) != 0u;
@@ -1043,121 +1049,124 @@ __global__ void __launch_bounds__(kPairThreads, MODE == 1 ? kForceBlocks : kForc
             }
             // batch sums plain, compensated across batches
             float bx = 0.f, by = 0.f, bz = 0.f, bu = 0.f;
-            // hits on few lanes: one compacted warp-wide list, 32 pairs per round (as in
+            // lane-by-lane rounds while enough lanes have a hit left, then (adaptive
+            // cells) the rest as one compacted warp-wide list, 32 pairs per round (as in
             // the density pass); every target's terms come back by a segmented scan
-            const int nh = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
-            int hincl = nh;
-#pragma unroll
-            for (int dd = 1; dd < 32; dd <<= 1) {
-                const int v = __shfl_up_sync(kFull, hincl, dd);
-                if (lane >= dd) hincl += v;
-            }
-            const int htot = __shfl_sync(kFull, hincl, 31);
-            const int hoff = hincl - nh;
-            const int hmax = (int)__reduce_max_sync(kFull, (unsigned)nh);
-            if constexpr (LIST) if (htot < kCompactLanesF * hmax) {
-                cnt += nh;
-                float4 *wbase = smem + (size_t)wib * (3 * TPW * SLOT);
-                const int *ibase = (const int *)(smem + (size_t)(blockDim.x >> 5) * (3 * TPW * SLOT)) +
-                                   (size_t)wib * TPW * SLOT;
-                for (int base = 0; base < htot; base += 32) {
-                    const int hq = base + lane;
-                    const bool hv = hq < htot;
-                    int t = 0;
-#pragma unroll
-                    for (int st = 16; st > 0; st >>= 1)
-                        if (__shfl_sync(kFull, hoff, t + st) <= hq) t += st;
-                    int r = hq - __shfl_sync(kFull, hoff, t);
-                    const unsigned w0 = __shfl_sync(kFull, m0, t), w1 = __shfl_sync(kFull, m1, t);
-                    const unsigned w2 = __shfl_sync(kFull, m2, t), w3 = __shfl_sync(kFull, m3, t);
-                    const float tx = __shfl_sync(kFull, pi.x, t), ty = __shfl_sync(kFull, pi.y, t);
-                    const float tz = __shfl_sync(kFull, pi.z, t), th = __shfl_sync(kFull, pi.w, t);
-                    const float thinv = __shfl_sync(kFull, hinv, t), tL = __shfl_sync(kFull, L, t);
-                    const float tvx = __shfl_sync(kFull, vi.x, t), tvy = __shfl_sync(kFull, vi.y, t);
-                    const float tvz = __shfl_sync(kFull, vi.z, t);
-                    const float ttx = __shfl_sync(kFull, ti.x, t), tty = __shfl_sync(kFull, ti.y, t);
-                    const float ttz = __shfl_sync(kFull, ti.z, t), ttw = __shfl_sync(kFull, ti.w, t);
-                    const int ti_ = __shfl_sync(kFull, i, t);
-                    float gx = 0.f, gy = 0.f, gz = 0.f, gu = 0.f, gv = 0.f;
-                    if (hv) {
-                        int k;
-                        const int p0 = __popc(w0), p1 = __popc(w1), p2 = __popc(w2);
-                        if (r < p0) k = (int)__fns(w0, 0u, r + 1);
-                        else if ((r -= p0) < p1) k = 32 + (int)__fns(w1, 0u, r + 1);
-                        else if ((r -= p1) < p2) k = 64 + (int)__fns(w2, 0u, r + 1);
-                        else k = 96 + (int)__fns(w3, 0u, r - p2 + 1);
-                        k = (unsigned)k < (unsigned)B ? k : 0;  // (never taken: a hit lies in the batch)
-                        const float4 *sAt = wbase + (t / TW) * SLOT;
-                        const float4 s = sAt[k];
-                        const float4 vj = sAt[TPW * SLOT + k];
-                        const float4 tj = sAt[2 * TPW * SLOT + k];
-                        const float dx = tx - s.x, dy = ty - s.y, dz = tz - s.z;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        if (r2 > 0.f) {
-                            const float hi2t = th * th, hj2 = s.w * s.w;
-                            bool in_i = r2 < hi2t, in_j = r2 < hj2;
-                            if (fabsf(r2 - hi2t) <= kBandK * th * (th + tL) ||
-                                fabsf(r2 - hj2) <= kBandK * s.w * (s.w + tL)) {
-                                const unsigned dd2 = band_decide(a.x, a.y, a.z, ti_, ibase[(t / TW) * SLOT + k], a.box,
-                                                                 th, s.w);
-                                in_i = dd2 & 1u;
-                                in_j = dd2 & 2u;
-                            }
-                            const float rinv = rsqrtf(r2);
-                            const float rr = r2 * rinv;
-                            const float hjinv = __fdividef(1.f, s.w);
-                            const float hj2inv = hjinv * hjinv;
-                            const float thinv2 = thinv * thinv;
-                            const float dWi = in_i ? kSigma * spline_dw_u(rr * thinv) * (thinv2 * thinv2) : 0.f;
-                            const float dWj = in_j ? kSigma * spline_dw_u(rr * hjinv) * (hj2inv * hj2inv) : 0.f;
-                            const float vx = tvx - vj.x, vy = tvy - vj.y, vz = tvz - vj.z;
-                            const float mu = fmaf(vx, dx, fmaf(vy, dy, vz * dz)) * rinv;
-                            const float muc = fminf(mu, 0.f);
-                            const float vsig_ij = ttz + tj.z - 3.f * muc;
-                            const float Pi = -a.alpha * vsig_ij * muc * (0.5f * (ttw + tj.w)) *
-                                             __fdividef(1.f, ttx + tj.x);
-                            const float dWbar = 0.5f * (dWi + dWj);
-                            const float mj = vj.w;
-                            const float sc = mj * fmaf(tty, dWi, fmaf(tj.y, dWj, Pi * dWbar)) * rinv;
-                            gx = -sc * dx;
-                            gy = -sc * dy;
-                            gz = -sc * dz;
-                            gu = mj * mu * fmaf(tty, dWi, 0.5f * Pi * dWbar);
-                            gv = vsig_ij;
-                        }
-                    }
+            for (;;) {
+                const unsigned busy = __ballot_sync(kFull, (m0 | m1 | m2 | m3) != 0u);
+                if (busy == 0u) break;
+                if constexpr (LIST) if (__popc(busy) < kWalkBusyF) {
+                    const int nh = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
+                    int hincl = nh;
 #pragma unroll
                     for (int dd = 1; dd < 32; dd <<= 1) {
-                        const int tu = __shfl_up_sync(kFull, t, dd);  // every lane takes part
-                        const bool same = lane >= dd && tu == t;
-                        const float ux = __shfl_up_sync(kFull, gx, dd), uy = __shfl_up_sync(kFull, gy, dd);
-                        const float uz = __shfl_up_sync(kFull, gz, dd), uu = __shfl_up_sync(kFull, gu, dd);
-                        const float uv = __shfl_up_sync(kFull, gv, dd);
-                        if (same) {
-                            gx += ux;
-                            gy += uy;
-                            gz += uz;
-                            gu += uu;
-                            gv = fmaxf(gv, uv);
+                        const int v = __shfl_up_sync(kFull, hincl, dd);
+                        if (lane >= dd) hincl += v;
+                    }
+                    const int htot = __shfl_sync(kFull, hincl, 31);
+                    const int hoff = hincl - nh;
+                    cnt += nh;
+                    float4 *wbase = smem + (size_t)wib * (3 * TPW * SLOT);
+                    const int *ibase = (const int *)(smem + (size_t)(blockDim.x >> 5) * (3 * TPW * SLOT)) +
+                                       (size_t)wib * TPW * SLOT;
+                    for (int base = 0; base < htot; base += 32) {
+                        const int hq = base + lane;
+                        const bool hv = hq < htot;
+                        int t = 0;
+#pragma unroll
+                        for (int st = 16; st > 0; st >>= 1)
+                            if (__shfl_sync(kFull, hoff, t + st) <= hq) t += st;
+                        int r = hq - __shfl_sync(kFull, hoff, t);
+                        const unsigned w0 = __shfl_sync(kFull, m0, t), w1 = __shfl_sync(kFull, m1, t);
+                        const unsigned w2 = __shfl_sync(kFull, m2, t), w3 = __shfl_sync(kFull, m3, t);
+                        const float tx = __shfl_sync(kFull, pi.x, t), ty = __shfl_sync(kFull, pi.y, t);
+                        const float tz = __shfl_sync(kFull, pi.z, t), th = __shfl_sync(kFull, pi.w, t);
+                        const float thinv = __shfl_sync(kFull, hinv, t), tL = __shfl_sync(kFull, L, t);
+                        const float tvx = __shfl_sync(kFull, vi.x, t), tvy = __shfl_sync(kFull, vi.y, t);
+                        const float tvz = __shfl_sync(kFull, vi.z, t);
+                        const float ttx = __shfl_sync(kFull, ti.x, t), tty = __shfl_sync(kFull, ti.y, t);
+                        const float ttz = __shfl_sync(kFull, ti.z, t), ttw = __shfl_sync(kFull, ti.w, t);
+                        const int ti_ = __shfl_sync(kFull, i, t);
+                        float gx = 0.f, gy = 0.f, gz = 0.f, gu = 0.f, gv = 0.f;
+                        if (hv) {
+                            int k;
+                            const int p0 = __popc(w0), p1 = __popc(w1), p2 = __popc(w2);
+                            if (r < p0) k = (int)__fns(w0, 0u, r + 1);
+                            else if ((r -= p0) < p1) k = 32 + (int)__fns(w1, 0u, r + 1);
+                            else if ((r -= p1) < p2) k = 64 + (int)__fns(w2, 0u, r + 1);
+                            else k = 96 + (int)__fns(w3, 0u, r - p2 + 1);
+                            k = (unsigned)k < (unsigned)B ? k : 0;  // (never taken: a hit lies in the batch)
+                            const float4 *sAt = wbase + (t / TW) * SLOT;
+                            const float4 s = sAt[k];
+                            const float4 vj = sAt[TPW * SLOT + k];
+                            const float4 tj = sAt[2 * TPW * SLOT + k];
+                            const float dx = tx - s.x, dy = ty - s.y, dz = tz - s.z;
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            if (r2 > 0.f) {
+                                const float hi2t = th * th, hj2 = s.w * s.w;
+                                bool in_i = r2 < hi2t, in_j = r2 < hj2;
+                                if (fabsf(r2 - hi2t) <= kBandK * th * (th + tL) ||
+                                    fabsf(r2 - hj2) <= kBandK * s.w * (s.w + tL)) {
+                                    const unsigned dd2 = band_decide(a.x, a.y, a.z, ti_, ibase[(t / TW) * SLOT + k], a.box,
+                                                                     th, s.w);
+                                    in_i = dd2 & 1u;
+                                    in_j = dd2 & 2u;
+                                }
+                                const float rinv = rsqrtf(r2);
+                                const float rr = r2 * rinv;
+                                const float hjinv = __fdividef(1.f, s.w);
+                                const float hj2inv = hjinv * hjinv;
+                                const float thinv2 = thinv * thinv;
+                                const float dWi = in_i ? kSigma * spline_dw_u(rr * thinv) * (thinv2 * thinv2) : 0.f;
+                                const float dWj = in_j ? kSigma * spline_dw_u(rr * hjinv) * (hj2inv * hj2inv) : 0.f;
+                                const float vx = tvx - vj.x, vy = tvy - vj.y, vz = tvz - vj.z;
+                                const float mu = fmaf(vx, dx, fmaf(vy, dy, vz * dz)) * rinv;
+                                const float muc = fminf(mu, 0.f);
+                                const float vsig_ij = ttz + tj.z - 3.f * muc;
+                                const float Pi = -a.alpha * vsig_ij * muc * (0.5f * (ttw + tj.w)) *
+                                                 __fdividef(1.f, ttx + tj.x);
+                                const float dWbar = 0.5f * (dWi + dWj);
+                                const float mj = vj.w;
+                                const float sc = mj * fmaf(tty, dWi, fmaf(tj.y, dWj, Pi * dWbar)) * rinv;
+                                gx = -sc * dx;
+                                gy = -sc * dy;
+                                gz = -sc * dz;
+                                gu = mj * mu * fmaf(tty, dWi, 0.5f * Pi * dWbar);
+                                gv = vsig_ij;
+                            }
+                        }
+#pragma unroll
+                        for (int dd = 1; dd < 32; dd <<= 1) {
+                            const int tu = __shfl_up_sync(kFull, t, dd);  // every lane takes part
+                            const bool same = lane >= dd && tu == t;
+                            const float ux = __shfl_up_sync(kFull, gx, dd), uy = __shfl_up_sync(kFull, gy, dd);
+                            const float uz = __shfl_up_sync(kFull, gz, dd), uu = __shfl_up_sync(kFull, gu, dd);
+                            const float uv = __shfl_up_sync(kFull, gv, dd);
+                            if (same) {
+                                gx += ux;
+                                gy += uy;
+                                gz += uz;
+                                gu += uu;
+                                gv = fmaxf(gv, uv);
+                            }
+                        }
+                        const int lo = hoff - base, hi_ = hoff + nh - base;
+                        const bool mine = nh > 0 && hi_ > 0 && lo < 32;
+                        const int src = mine ? min(hi_, 32) - 1 : lane;
+                        const float fx = __shfl_sync(kFull, gx, src), fy = __shfl_sync(kFull, gy, src);
+                        const float fz = __shfl_sync(kFull, gz, src), fu = __shfl_sync(kFull, gu, src);
+                        const float fv = __shfl_sync(kFull, gv, src);
+                        if (mine) {
+                            bx += fx;
+                            by += fy;
+                            bz += fz;
+                            bu += fu;
+                            vs = fmaxf(vs, fv);
                         }
                     }
-                    const int lo = hoff - base, hi_ = hoff + nh - base;
-                    const bool mine = nh > 0 && hi_ > 0 && lo < 32;
-                    const int src = mine ? min(hi_, 32) - 1 : lane;
-                    const float fx = __shfl_sync(kFull, gx, src), fy = __shfl_sync(kFull, gy, src);
-                    const float fz = __shfl_sync(kFull, gz, src), fu = __shfl_sync(kFull, gu, src);
-                    const float fv = __shfl_sync(kFull, gv, src);
-                    if (mine) {
-                        bx += fx;
-                        by += fy;
-                        bz += fz;
-                        bu += fu;
-                        vs = fmaxf(vs, fv);
-                    }
+                    m0 = m1 = m2 = m3 = 0u;
+                    break;
                 }
-                m0 = m1 = m2 = m3 = 0u;
-            }
-            while (__any_sync(kFull, (m0 | m1 | m2 | m3) != 0u)) {
                 if (m0 | m1 | m2 | m3) {
                     const int k = pop_bit(m0, m1, m2, m3);
                     const float4 s = sA[k];
