@@ -1477,9 +1477,24 @@ __global__ void k_order_scatter(const int4 *__restrict__ tiles, const int *__res
                                 int4 *__restrict__ out)
 {
     const int nt = *n_tiles, ng = nt / tpw;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
-        const unsigned pos = atomicAdd(&cursor[key[g]], 1u);
-        for (int s = 0; s < tpw; ++s) out[pos * tpw + s] = tiles[g * tpw + s];
+    const int lane = threadIdx.x & 31;
+    // warp-uniform trip count; the lanes of one octave take their positions with one
+    // atomic (a pass's groups fall into a few octaves: per-lane atomics on one counter
+    // would serialise)
+    const int stride = gridDim.x * blockDim.x;
+    for (int g0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); g0 < ng; g0 += stride) {
+        const int g = g0 + lane;
+        const bool in = g < ng;
+        const unsigned b = in ? key[g] : 0xffffffffu;
+        const unsigned peers = __match_any_sync(kFull, b);
+        const int leader = __ffs(peers) - 1;
+        unsigned base = 0u;
+        if (in && lane == leader) base = atomicAdd(&cursor[b], (unsigned)__popc(peers));
+        base = __shfl_sync(kFull, base, leader);
+        if (in) {
+            const unsigned pos = base + (unsigned)__popc(peers & ((1u << lane) - 1u));
+            for (int s = 0; s < tpw; ++s) out[pos * tpw + s] = tiles[g * tpw + s];
+        }
     }
     const int t = ng * tpw + blockIdx.x * blockDim.x + threadIdx.x;  // the partial group, in place
     if (t < nt) out[t] = tiles[t];
