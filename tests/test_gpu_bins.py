@@ -225,3 +225,52 @@ def test_limiter_off_is_unchanged_and_on_is_a_no_op_in_one_bin():
     assert s2["limited"] == 0 and s2["woken"] == 0 and s2["limit_sweeps"] == s2["substeps"]
     assert s1["limit_sweeps"] == 0
     _equal(p1.numpy(), p2.numpy())
+
+
+def test_limiter_batched_boxes_match_each_box_alone():
+    """Two blasts in two periodic boxes of one context (one limiter pass over all
+    boxes) against each box in a context of its own: the same bins, updates, raised
+    bins and wake-ups, and the same state up to rounding -- a batched run also
+    drifts each box at the other box's step ends, which splits its drifts and
+    moves its FP32 sums by an ulp."""
+    from paper_1508_00115_gb300 import binding
+    levels = 7
+    ds = [_blast(900, 51), _blast(1400, 52)]
+    runs = []
+    for d in ds:
+        ctx, parts = _hydro_ctx(d, flags=binding.SPH_FLAG_BIN_LIMITER)
+        runs.append((ctx, parts))
+    g0 = runs[0][1].numpy()
+    dt_max = 16.0 * float(np.min(0.1 * g0["h"].astype(np.float64) / g0["vsig"].astype(np.float64)))
+    alone = []
+    for ctx, parts in runs:
+        _, st = ctx.step_bins(parts, dt_max, levels)
+        alone.append((st, parts.numpy(), ctx.bins(), ctx.permutation()))
+        assert st["limited"] > 0 and st["woken"] > 0
+    sizes = [d["x"].size for d in ds]
+    offs = np.array([0, sizes[0], sizes[0] + sizes[1]], dtype=np.int64)
+    db = {k: np.concatenate([d[k] for d in ds]) for k in inputs.FIELDS}
+    ctx = binding.Context(int(offs[-1]), box_offsets=offs, flags=binding.SPH_FLAG_BIN_LIMITER)
+    parts = binding.Particles(db)
+    ctx.build_cells(parts)
+    ctx.density(parts)
+    ctx.force(parts)
+    _, stb = ctx.step_bins(parts, dt_max, levels)
+    gb, bb, pb = parts.numpy(), ctx.bins(), ctx.permutation()
+    # step ends: those of either box (their union)
+    assert max(a[0]["substeps"] for a in alone) <= stb["substeps"] <= sum(a[0]["substeps"] for a in alone)
+    assert stb["updates"] == sum(a[0]["updates"] for a in alone)
+    assert stb["limited"] == sum(a[0]["limited"] for a in alone)
+    assert stb["woken"] == sum(a[0]["woken"] for a in alone)
+    for b, (st, g, bins, perm) in enumerate(alone):
+        sl = slice(int(offs[b]), int(offs[b + 1]))
+        ib = np.argsort(pb[sl] - offs[b])
+        ia = np.argsort(perm)
+        assert np.array_equal(bb[sl][ib], bins[ia])
+        for k in ("x", "y", "z"):
+            dx = gb[k][sl][ib] - g[k][ia]
+            dx -= np.rint(dx)
+            assert np.abs(dx).max() < 1e-8, k
+        for k in ("vx", "vy", "vz", "u", "h"):
+            x, y = gb[k][sl][ib], g[k][ia]
+            assert np.abs(x - y).max() <= 1e-5 * np.abs(y).max(), k

@@ -223,3 +223,22 @@ def test_hp_collect_samples_during_steps():
     g = parts.numpy()
     assert np.all(np.abs(t[2 * n:]) < 0.2)
     assert np.all(g["h"] > 0)
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 311373])
+def test_hp_inference_ragged_tiles(n):
+    """Tensor-core inference takes 128 particles per tile and loops over tiles in a
+    persistent grid: a single particle, one short of a tile, a whole tile, one over,
+    and more than two waves of the grid's CTAs (8 per SM), against the oracle."""
+    ctx = _ctx()
+    w, f = hp.to_library(hp.glorot(31), _norm())
+    ctx.hp_load(w, f)
+    P, norm = hp.from_library(w, f)
+    X, _ = _data(n, 32)
+    out = ctx.hp_eval(torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+    ref = hp.forward(P, norm, X, bf16=True)
+    err = np.abs(out - ref)
+    assert out.shape == (n,)
+    assert err.max() <= 1e-4, err.max()
+    if n >= 1000:
+        assert np.quantile(err, 0.999) <= 1e-6
