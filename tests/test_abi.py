@@ -58,6 +58,26 @@ def test_struct_layout_matches_header():
             assert int(out[f"{s}.{f}"]) == getattr(cls, f).offset, (s, f)
 
 
+def test_constants_match_header():
+    """Every SPH_* constant the binding mirrors (macros and enumerators) has the
+    header's value."""
+    names = [k for k in dir(binding) if k.startswith("SPH_") and isinstance(getattr(binding, k), int)]
+    scratch = pathlib.Path(ROOT) / "tests" / "_build"  # git-ignored
+    scratch.mkdir(exist_ok=True)
+    src = scratch / "consts.c"
+    lines = ['#include <stdio.h>', '#include "sph.h"', "int main(void){"]
+    for k in names:
+        lines.append(f'printf("{k} %lld\\n", (long long)({k}));')  # (a name the header lacks fails to compile)
+    lines.append("return 0;}")
+    src.write_text("\n".join(lines))
+    exe = scratch / "consts"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = dict(l.rsplit(" ", 1) for l in subprocess.check_output([str(exe)], text=True).split("\n") if l)
+    assert sorted(out) == sorted(names)
+    for k, v in out.items():
+        assert int(v) == getattr(binding, k), k
+
+
 def test_default_params(L):
     p = binding.sph_default_params()
     assert p.n_ngb == 48.0 and abs(p.gamma - 5 / 3) < 1e-7 and p.kernel == 0
