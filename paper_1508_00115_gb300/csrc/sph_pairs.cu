@@ -34,20 +34,19 @@ constexpr int kBatchD = 128;  // staged survivors per tile, density (4 hit-mask 
 constexpr int kBatchF = 128;  // staged survivors per tile, force
 constexpr int kSlotF = 132;   // floats per staged-coordinate array (>= kBatchD, even: 8-byte aligned pairs)
 constexpr int kPairThreads = 256;
-// Adaptive cells (leaf lists): a batch's hits are walked lane by lane -- each lane its
-// own target's hits, one (force) or two (density) per round -- while at least
-// kWalkBusy lanes still have one; what is left is then laid out as one compacted
-// warp-wide list, 32 hits per round.  A lane-by-lane round costs the same whatever
-// the number of busy lanes, a compacted hit adds the shuffles of the list and of the
-// segmented scan; the thresholds are measured on uneven batched boxes (8 and 10 of
-// 32 lanes: 4/8, 6/10, 6/12, 8/12, 12/16, 16/20 and 20/24 were up to 5 % slower).
-// The uniform grid's batches mix cells on both sides of the tile, so their hits
-// spread over the lanes: its kernels are compiled without the compacted walk
-// (measured on Sedov 128^3: the extra code alone cost 5-8 %, never taking it).
-constexpr int kWalkBusyD = 8;
-constexpr int kWalkBusyF = 10;
+// Adaptive cells (leaf lists): the tiles' targets span a range of h, so their hit
+// counts in a batch differ widely.  The density and force passes therefore cut a
+// batch's hits into equal contiguous ranges, one per lane (the balanced walk of
+// k_density and k_force), with the tile's targets in shared memory for the lanes that
+// move from one target's hits to the next; measured on the 512 uneven boxes against
+// the earlier walk (lane by lane while enough lanes had a hit left, then one
+// compacted warp-wide list with a segmented scan): force 7.5 % faster.  The uniform
+// grid's batches mix cells on both sides of the tile, so their hits spread over the
+// lanes: its kernels walk lane by lane only.
+constexpr int kWalkBytesD = 148;  // density pass, list mode: the balanced walk's scratch per target
+constexpr int kWalkBytes = 132;   // force pass, list mode: the balanced walk's scratch per target
 constexpr int kDensityBlocks = 2;  // resident blocks per SM the density kernel is compiled for
-constexpr int kForceBlocks = 2;      // leaf lists (adaptive cells): the compacted walk needs the registers
+constexpr int kForceBlocks = 2;      // leaf lists (adaptive cells): 3 would spill (328 B at 80 registers)
 constexpr int kForceBlocksU = 3;     // uniform grid: a third block per SM outweighs a few spilled values
 // Padding sources sit at -kFar and target-less lanes at +kFar: the squared distance
 // between either and anything else overflows to +inf, so no test can pass.
@@ -289,6 +288,28 @@ __device__ __forceinline__ int pop_bit(unsigned &m0, unsigned &m1, unsigned &m2,
     return base + __ffs(m) - 1;
 }
 
+// Clear the r lowest set bits of the 128-bit mask M (r below its population).
+__device__ __forceinline__ unsigned keep_after(unsigned w, int r)
+{
+    return r == 0 ? w : w & ~((1u << __fns(w, 0u, r + 1)) - 1u);
+}
+__device__ __forceinline__ void drop_hits(uint4 &M, int r)
+{
+    int c = __popc(M.x);
+    if (r < c) { M.x = keep_after(M.x, r); return; }
+    r -= c;
+    M.x = 0u;
+    c = __popc(M.y);
+    if (r < c) { M.y = keep_after(M.y, r); return; }
+    r -= c;
+    M.y = 0u;
+    c = __popc(M.z);
+    if (r < c) { M.z = keep_after(M.z, r); return; }
+    r -= c;
+    M.z = 0u;
+    M.w = keep_after(M.w, r);
+}
+
 // Cubic spline of support 1 without its normalisation sigma, in truncated-power form:
 // w/sigma = 2(1-q)^3_+ - 8(1/2-q)^3_+,  (dw/dq)/sigma = -6(1-q)^2_+ + 24(1/2-q)^2_+
 // (identical to the piecewise polynomial; branch-free).
@@ -305,6 +326,61 @@ __device__ __forceinline__ float spline_dw_u(float q)
     return fmaf(24.f * b, b, -6.f * a * a);
 }
 
+// Partial force sums of one target: a, du/dt and the largest v_sig.
+struct ForceSum {
+    float x = 0.f, y = 0.f, z = 0.f, u = 0.f, v = 0.f;
+    // store into slot idx (sums into the float4, v_sig beside) and start again
+    __device__ __forceinline__ void put(float4 *s4, float *sv, int idx)
+    {
+        s4[idx] = make_float4(x, y, z, u);
+        sv[idx] = v;
+        x = y = z = u = v = 0.f;
+    }
+};
+
+// Partial density sums of one target: {sum m w, sum w, sum q w', sum m (3 w + q w')}
+// and {sum (v_ij . d) m w'/r, the three components of the curl sum}.
+struct DensSum {
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = make_float4(0.f, 0.f, 0.f, 0.f);
+    // store into slot idx (two float4) and start again
+    __device__ __forceinline__ void put(float4 *s, int idx)
+    {
+        s[2 * idx] = a;
+        s[2 * idx + 1] = b;
+        a = b = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+};
+
+// The pair term of the force pass (Sec. 2: the grad-h pressure force with the
+// Monaghan viscosity and its Balsara switch, and du/dt) of target i (1/h_i, 1/h_i^4,
+// v_i, thermo_i = {rho, f P / rho^2, c, B}) and source j (h_j, {v_j, m_j}, thermo_j)
+// at d = p_i - p_j, r2 = |d|^2 > 0; in_i, in_j: r < h_i, r < h_j.
+__device__ __forceinline__ void force_term(float dx, float dy, float dz, float r2, bool in_i, bool in_j, float hinv,
+                                           float hinv4, const float4 vi, const float4 ti, float hj, const float4 vj,
+                                           const float4 tj, float alpha, ForceSum &f)
+{
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float hjinv = __fdividef(1.f, hj);
+    const float hj2inv = hjinv * hjinv;
+    const float dWi = in_i ? kSigma * spline_dw_u(r * hinv) * hinv4 : 0.f;
+    const float dWj = in_j ? kSigma * spline_dw_u(r * hjinv) * (hj2inv * hj2inv) : 0.f;
+    const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+    const float mu = fmaf(vx, dx, fmaf(vy, dy, vz * dz)) * rinv;
+    // viscosity only on approach (mu < 0): branch-free, Pi = 0 otherwise
+    const float muc = fminf(mu, 0.f);
+    const float vsig_ij = ti.z + tj.z - 3.f * muc;
+    const float Pi = -alpha * vsig_ij * muc * (0.5f * (ti.w + tj.w)) * __fdividef(1.f, ti.x + tj.x);
+    const float dWbar = 0.5f * (dWi + dWj);
+    const float mj = vj.w;
+    const float sc = mj * fmaf(ti.y, dWi, fmaf(tj.y, dWj, Pi * dWbar)) * rinv;
+    f.x = fmaf(-sc, dx, f.x);
+    f.y = fmaf(-sc, dy, f.y);
+    f.z = fmaf(-sc, dz, f.z);
+    f.u = fmaf(mj * mu, fmaf(ti.y, dWi, 0.5f * Pi * dWbar), f.u);
+    f.v = fmaxf(f.v, vsig_ij);
+}
+
 // MODE: 0 = uniform grid, 1 = adaptive cells (leaf lists), 2 = uniform grid with the
 // per-axis sweep (SPH_FLAG_AXIS_SWEEP)
 template <int TW, bool HASH, int MODE>
@@ -319,6 +395,16 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
     const int sub = lane / TW, tl = lane % TW;
     float4 *sA = smem + (size_t)wib * (2 * TPW * SLOT) + sub * SLOT;  // {x, y, z, j} in target frame
     float4 *sB = sA + TPW * SLOT;                                      // {vx, vy, vz, m}
+    // list mode, the balanced hit walk's scratch per tile (kWalkBytesD x TW): the
+    // targets' hit masks, the partial sums (two float4) of each lane's first target (F),
+    // last target (E) and of the targets inside its range (D), the tile's targets
+    // ({x, y, z, 1/h}, {v, m}) and their first hit's position
+    char *const wt = reinterpret_cast<char *>(smem + (size_t)(blockDim.x >> 5) * (2 * TPW * SLOT)) +
+                     ((size_t)wib * TPW + sub) * TW * kWalkBytesD;
+    uint4 *wM = reinterpret_cast<uint4 *>(wt);
+    float4 *wF = reinterpret_cast<float4 *>(wt + TW * 16), *wE = wF + 2 * TW, *wD = wE + 2 * TW;
+    float4 *wP = wD + 2 * TW, *wV = wP + TW;
+    int *wOff = reinterpret_cast<int *>(wV + TW);
     const unsigned gmask = TW == 32 ? kFull : (((1u << TW) - 1u) << (sub * TW));
     const unsigned lt = (1u << lane) - 1u;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -374,6 +460,10 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
         const float hi2 = act ? hi * hi : -1.f;
         const float lob = hi2 - band, hib = hi2 + band;
         const float hinv = act ? 1.f / hi : 0.f;
+        if constexpr (LIST) {  // for the balanced walk (read after the flush's first __syncwarp)
+            wP[tl] = make_float4(pi.x, pi.y, pi.z, hinv);
+            wV[tl] = vi;
+        }
         const int ca = tile.x - bx.cell_off;
         const int ix = ca % nc, iy = (ca / nc) % nc, iz = ca / (nc * nc);
 
@@ -454,135 +544,137 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
                 cy = fmaf(fr, fmaf(v.z, d.x, -v.x * d.z), cy);
                 cz = fmaf(fr, fmaf(v.x, d.y, -v.y * d.x), cz);
             };
-            // Lane-by-lane rounds, two hits per round (independent instruction streams;
-            // a lane's terms are still added in ascending staged order, so its sums are
-            // those of one at a time), while enough lanes have a hit left.  Then
-            // (adaptive cells) the rest -- the few lanes whose sources lie next to many
-            // hits -- are laid out as one warp-wide list, lane order and ascending
-            // staged index within a lane, and taken 32 per round, one per lane, every
-            // target's terms of the round summed by a segmented scan and fetched by
-            // its own lane.
-            for (;;) {
-                const unsigned busy = __ballot_sync(kFull, (m0 | m1 | m2 | m3) != 0u);
-                if (busy == 0u) break;
-                if constexpr (LIST) if (__popc(busy) < kWalkBusyD) {
-                    const int nh = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
-                    int hincl = nh;
+            if constexpr (LIST) {
+                // Balanced walk, as in the force pass (k_force): the tile's H hits, in lane
+                // order, cut into TW contiguous ranges, one per lane; each lane sums its
+                // targets' terms in order, and a target whose hits cross ranges adds the
+                // pieces in lane order (the same order on every run).
+                const int nh = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
+                int hincl = nh;
 #pragma unroll
-                    for (int dd = 1; dd < 32; dd <<= 1) {
-                        const int v = __shfl_up_sync(kFull, hincl, dd);
-                        if (lane >= dd) hincl += v;
-                    }
-                    const int htot = __shfl_sync(kFull, hincl, 31);
-                    const int hoff = hincl - nh;
-                    cnt += nh;
-                    if (HASH) {  // integer sums: any order gives the same bits
-                        unsigned h0 = m0, h1 = m1, h2 = m2, h3 = m3;
-                        while (h0 | h1 | h2 | h3) hh += mix64((uint64_t)a.ids[__float_as_int(sA[pop_bit(h0, h1, h2, h3)].w)]);
-                    }
-                    float4 *wbase = smem + (size_t)wib * (2 * TPW * SLOT);
-                    for (int base = 0; base < htot; base += 32) {
-                        const int hq = base + lane;
-                        const bool hv = hq < htot;
-                        // owner lane of hit hq: the last lane whose list starts at or before it
-                        int t = 0;
-#pragma unroll
-                        for (int st = 16; st > 0; st >>= 1)
-                            if (__shfl_sync(kFull, hoff, t + st) <= hq) t += st;
-                        int r = hq - __shfl_sync(kFull, hoff, t);
-                        const unsigned w0 = __shfl_sync(kFull, m0, t), w1 = __shfl_sync(kFull, m1, t);
-                        const unsigned w2 = __shfl_sync(kFull, m2, t), w3 = __shfl_sync(kFull, m3, t);
-                        const float tx = __shfl_sync(kFull, pi.x, t), ty = __shfl_sync(kFull, pi.y, t);
-                        const float tz = __shfl_sync(kFull, pi.z, t), tvx = __shfl_sync(kFull, vi.x, t);
-                        const float tvy = __shfl_sync(kFull, vi.y, t), tvz = __shfl_sync(kFull, vi.z, t);
-                        const float thinv = __shfl_sync(kFull, hinv, t);
-                        float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f, c4 = 0.f, c5 = 0.f, c6 = 0.f, c7 = 0.f;
-                        if (hv) {
-                            int k;
-                            const int p0 = __popc(w0), p1 = __popc(w1), p2 = __popc(w2);
-                            if (r < p0) k = (int)__fns(w0, 0u, r + 1);
-                            else if ((r -= p0) < p1) k = 32 + (int)__fns(w1, 0u, r + 1);
-                            else if ((r -= p1) < p2) k = 64 + (int)__fns(w2, 0u, r + 1);
-                            else k = 96 + (int)__fns(w3, 0u, r - p2 + 1);
-                            k = (unsigned)k < (unsigned)B ? k : 0;  // (never taken: a hit lies in the batch)
-                            const float4 *sAt = wbase + (t / TW) * SLOT;
-                            const float4 sk = sAt[k];
-                            const float4 vj = sAt[TPW * SLOT + k];
-                            const float dx = tx - sk.x, dy = ty - sk.y, dz = tz - sk.z;
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                            const float q = r2 * rinv * thinv;
-                            float w, dw;
-                            spline_u(q, w, dw);
-                            const float mj = vj.w;
-                            const float fr = mj * dw * rinv;
-                            const float vx = tvx - vj.x, vy = tvy - vj.y, vz = tvz - vj.z;
-                            c0 = mj * w;
-                            c1 = w;
-                            c2 = q * dw;
-                            c3 = mj * fmaf(q, dw, 3.f * w);
-                            c4 = fr * fmaf(vx, dx, fmaf(vy, dy, vz * dz));
-                            c5 = fr * fmaf(vy, dz, -vz * dy);
-                            c6 = fr * fmaf(vz, dx, -vx * dz);
-                            c7 = fr * fmaf(vx, dy, -vy * dx);
-                        }
-                        // inclusive scan within runs of equal owner (runs are contiguous)
-#pragma unroll
-                        for (int dd = 1; dd < 32; dd <<= 1) {
-                            const int tu = __shfl_up_sync(kFull, t, dd);  // every lane takes part
-                            const bool same = lane >= dd && tu == t;
-                            const float u0 = __shfl_up_sync(kFull, c0, dd), u1 = __shfl_up_sync(kFull, c1, dd);
-                            const float u2 = __shfl_up_sync(kFull, c2, dd), u3 = __shfl_up_sync(kFull, c3, dd);
-                            const float u4 = __shfl_up_sync(kFull, c4, dd), u5 = __shfl_up_sync(kFull, c5, dd);
-                            const float u6 = __shfl_up_sync(kFull, c6, dd), u7 = __shfl_up_sync(kFull, c7, dd);
-                            if (same) {
-                                c0 += u0;
-                                c1 += u1;
-                                c2 += u2;
-                                c3 += u3;
-                                c4 += u4;
-                                c5 += u5;
-                                c6 += u6;
-                                c7 += u7;
-                            }
-                        }
-                        // each lane fetches the end of its own run in this round
-                        const int lo = hoff - base, hi_ = hoff + nh - base;
-                        const bool mine = nh > 0 && hi_ > 0 && lo < 32;
-                        const int src = mine ? min(hi_, 32) - 1 : lane;
-                        const float g0 = __shfl_sync(kFull, c0, src), g1 = __shfl_sync(kFull, c1, src);
-                        const float g2 = __shfl_sync(kFull, c2, src), g3 = __shfl_sync(kFull, c3, src);
-                        const float g4 = __shfl_sync(kFull, c4, src), g5 = __shfl_sync(kFull, c5, src);
-                        const float g6 = __shfl_sync(kFull, c6, src), g7 = __shfl_sync(kFull, c7, src);
-                        if (mine) {
-                            rb += g0;
-                            wb += g1;
-                            sqdw += g2;
-                            drho += g3;
-                            dv += g4;
-                            cx += g5;
-                            cy += g6;
-                            cz += g7;
-                        }
-                    }
-                    m0 = m1 = m2 = m3 = 0u;
-                    break;
+                for (int dd = 1; dd < TW; dd <<= 1) {
+                    const int v = __shfl_up_sync(kFull, hincl, dd, TW);
+                    if (tl >= dd) hincl += v;
                 }
-                if (m0 | m1 | m2 | m3) {
-                    const int k1 = pop_bit(m0, m1, m2, m3);
-                    const bool two = (m0 | m1 | m2 | m3) != 0u;
-                    int k2 = k1;
-                    if (two) k2 = pop_bit(m0, m1, m2, m3);
-                    float w1, dw1, q1, fr1, mj1, w2, dw2, q2, fr2, mj2;
-                    float3 d1, v1, d2, v2;
-                    term(k1, w1, dw1, q1, fr1, mj1, d1, v1);
-                    term(k2, w2, dw2, q2, fr2, mj2, d2, v2);
-                    accumulate(w1, dw1, q1, fr1, mj1, d1, v1);
-                    if (two) accumulate(w2, dw2, q2, fr2, mj2, d2, v2);
-                    cnt += two ? 2 : 1;
-                    if (HASH) {
-                        hh += mix64((uint64_t)a.ids[__float_as_int(sA[k1].w)]);
-                        if (two) hh += mix64((uint64_t)a.ids[__float_as_int(sA[k2].w)]);
+                const int H = __shfl_sync(kFull, hincl, TW - 1, TW);
+                const int hoff = hincl - nh;
+                cnt += nh;
+                if (HASH) {  // integer sums: any order gives the same bits
+                    unsigned h0 = m0, h1 = m1, h2 = m2, h3 = m3;
+                    while (h0 | h1 | h2 | h3) hh += mix64((uint64_t)a.ids[__float_as_int(sA[pop_bit(h0, h1, h2, h3)].w)]);
+                }
+                wM[tl] = make_uint4(m0, m1, m2, m3);
+                wOff[tl] = hoff;
+                __syncwarp();
+                const int rb_ = (tl * H) / TW, re_ = ((tl + 1) * H) / TW;
+                if (rb_ < re_) {
+                    int o = 0;
+#pragma unroll
+                    for (int st = TW / 2; st > 0; st >>= 1)
+                        if (wOff[o + st] <= rb_) o += st;
+                    uint4 M = wM[o];
+                    drop_hits(M, rb_ - wOff[o]);  // those belong to the ranges before
+                    float4 po = wP[o];            // {x, y, z, 1/h}
+                    float4 vo = wV[o];
+                    DensSum part;
+                    bool first = true;
+                    for (int p = rb_; p < re_; ++p) {
+                        if ((M.x | M.y | M.z | M.w) == 0u) {  // the owner's hits end here
+                            if (first) part.put(wF, tl);
+                            else part.put(wD, o);  // a target inside this range: only this lane
+                            first = false;
+                            do {
+                                ++o;
+                                M = wM[o];
+                            } while ((M.x | M.y | M.z | M.w) == 0u);
+                            po = wP[o];
+                            vo = wV[o];
+                        }
+                        const int k = pop_bit(M.x, M.y, M.z, M.w);
+                        const float4 sk = sA[k];
+                        const float4 vj = sB[k];
+                        const float dx = po.x - sk.x, dy = po.y - sk.y, dz = po.z - sk.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                        const float q = r2 * rinv * po.w;
+                        float w, dw;
+                        spline_u(q, w, dw);
+                        const float mj = vj.w;
+                        const float fr = mj * dw * rinv;
+                        const float vx = vo.x - vj.x, vy = vo.y - vj.y, vz = vo.z - vj.z;
+                        part.a.x = fmaf(mj, w, part.a.x);
+                        part.a.y += w;
+                        part.a.z = fmaf(q, dw, part.a.z);
+                        part.a.w = fmaf(mj, fmaf(q, dw, 3.f * w), part.a.w);
+                        part.b.x = fmaf(fr, fmaf(vx, dx, fmaf(vy, dy, vz * dz)), part.b.x);
+                        part.b.y = fmaf(fr, fmaf(vy, dz, -vz * dy), part.b.y);
+                        part.b.z = fmaf(fr, fmaf(vz, dx, -vx * dz), part.b.z);
+                        part.b.w = fmaf(fr, fmaf(vx, dy, -vy * dx), part.b.w);
+                    }
+                    if (first) {
+                        part.put(wF, tl);
+                        wE[2 * tl] = wE[2 * tl + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    } else {
+                        part.put(wE, tl);
+                    }
+                } else {
+                    wF[2 * tl] = wF[2 * tl + 1] = wE[2 * tl] = wE[2 * tl + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                __syncwarp();
+                if (nh > 0) {
+                    // the ranges La..Lb hold this target's hits hoff..hoff + nh - 1
+                    const int p0 = hoff, p1 = hoff + nh - 1;
+                    const int La = min(TW - 1, ((p0 + 1) * TW - 1) / H);
+                    const int Lb = min(TW - 1, ((p1 + 1) * TW - 1) / H);
+                    const int bA = (La * H) / TW, eA = ((La + 1) * H) / TW;
+                    const float4 *src = (La == Lb && p0 != bA && p1 + 1 != eA) ? wD + 2 * tl
+                                        : (p0 == bA ? wF + 2 * La : wE + 2 * La);
+                    float4 ta = src[0], tb = src[1];
+                    for (int Lx = La + 1; Lx <= Lb; ++Lx) {  // ranges that start inside its hits
+                        const float4 fa = wF[2 * Lx], fb = wF[2 * Lx + 1];
+                        ta.x += fa.x;
+                        ta.y += fa.y;
+                        ta.z += fa.z;
+                        ta.w += fa.w;
+                        tb.x += fb.x;
+                        tb.y += fb.y;
+                        tb.z += fb.z;
+                        tb.w += fb.w;
+                    }
+                    rb += ta.x;
+                    wb += ta.y;
+                    sqdw += ta.z;
+                    drho += ta.w;
+                    dv += tb.x;
+                    cx += tb.y;
+                    cy += tb.z;
+                    cz += tb.w;
+                }
+                __syncwarp();  // the scratch is rewritten by the next batch
+                m0 = m1 = m2 = m3 = 0u;
+            } else {
+                // Lane-by-lane rounds, two hits per round (independent instruction streams;
+                // a lane's terms are still added in ascending staged order, so its sums are
+                // those of one at a time).
+                for (;;) {
+                    const unsigned busy = __ballot_sync(kFull, (m0 | m1 | m2 | m3) != 0u);
+                    if (busy == 0u) break;
+                    if (m0 | m1 | m2 | m3) {
+                        const int k1 = pop_bit(m0, m1, m2, m3);
+                        const bool two = (m0 | m1 | m2 | m3) != 0u;
+                        int k2 = k1;
+                        if (two) k2 = pop_bit(m0, m1, m2, m3);
+                        float w1, dw1, q1, fr1, mj1, w2, dw2, q2, fr2, mj2;
+                        float3 d1, v1, d2, v2;
+                        term(k1, w1, dw1, q1, fr1, mj1, d1, v1);
+                        term(k2, w2, dw2, q2, fr2, mj2, d2, v2);
+                        accumulate(w1, dw1, q1, fr1, mj1, d1, v1);
+                        if (two) accumulate(w2, dw2, q2, fr2, mj2, d2, v2);
+                        cnt += two ? 2 : 1;
+                        if (HASH) {
+                            hh += mix64((uint64_t)a.ids[__float_as_int(sA[k1].w)]);
+                            if (two) hh += mix64((uint64_t)a.ids[__float_as_int(sA[k2].w)]);
+                        }
                     }
                 }
             }
@@ -899,6 +991,19 @@ __global__ void __launch_bounds__(kPairThreads, MODE == 1 ? kForceBlocks : kForc
     float *sX = (float *)((int *)(smem + nwb * (3 * TPW * SLOT)) + nwb * TPW * SLOT) +
                 ((size_t)wib * TPW + sub) * 5 * kSlotF;  // (list mode only: not allocated otherwise)
     float *sY = sX + kSlotF, *sZ = sY + kSlotF, *sLo = sZ + kSlotF, *sHi = sLo + kSlotF;
+    // list mode, the balanced hit walk's scratch per tile (kWalkBytes x TW): the targets'
+    // hit masks, their first hit's position, the partial sums of each lane's first
+    // target (F), last target (E) and of the targets inside its range (D), and the
+    // tile's targets ({x, y, z, h}, {v, m}, thermo, index)
+    char *const wt = reinterpret_cast<char *>(smem) + (size_t)nwb * (3 * TPW * SLOT) * sizeof(float4) +
+                     (size_t)nwb * TPW * SLOT * sizeof(int) + (size_t)nwb * TPW * 5 * kSlotF * sizeof(float) +
+                     ((size_t)wib * TPW + sub) * TW * kWalkBytes;
+    uint4 *wM = reinterpret_cast<uint4 *>(wt);
+    float4 *wF = reinterpret_cast<float4 *>(wt + TW * 16), *wE = wF + TW, *wD = wE + TW;
+    int *wOff = reinterpret_cast<int *>(wt + TW * 64);
+    float *wFv = reinterpret_cast<float *>(wOff + TW), *wEv = wFv + TW, *wDv = wEv + TW;
+    float4 *wP = reinterpret_cast<float4 *>(wt + TW * 80), *wV = wP + TW, *wT = wV + TW;
+    int *wI = reinterpret_cast<int *>(wT + TW);
     const unsigned gmask = TW == 32 ? kFull : (((1u << TW) - 1u) << (sub * TW));
     const unsigned lt = (1u << lane) - 1u;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -932,6 +1037,12 @@ __global__ void __launch_bounds__(kPairThreads, MODE == 1 ? kForceBlocks : kForc
             pi = a.pos4[i];
             vi = a.vel4[i];
             ti = a.thermo4[i];
+        }
+        if constexpr (LIST) {  // for the balanced walk (read after the flush's first __syncwarp)
+            wP[tl] = pi;
+            wV[tl] = vi;
+            wT[tl] = ti;
+            wI[tl] = i;
         }
         const float lox = tile_min<TW>(act ? pi.x : inf), hix = tile_max<TW>(act ? pi.x : -inf);
         const float loy = tile_min<TW>(act ? pi.y : inf), hiy = tile_max<TW>(act ? pi.y : -inf);
@@ -1049,156 +1160,165 @@ __global__ void __launch_bounds__(kPairThreads, MODE == 1 ? kForceBlocks : kForc
             }
             // batch sums plain, compensated across batches
             float bx = 0.f, by = 0.f, bz = 0.f, bu = 0.f;
-            // lane-by-lane rounds while enough lanes have a hit left, then (adaptive
-            // cells) the rest as one compacted warp-wide list, 32 pairs per round (as in
-            // the density pass); every target's terms come back by a segmented scan
-            for (;;) {
-                const unsigned busy = __ballot_sync(kFull, (m0 | m1 | m2 | m3) != 0u);
-                if (busy == 0u) break;
-                if constexpr (LIST) if (__popc(busy) < kWalkBusyF) {
-                    const int nh = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
-                    int hincl = nh;
+            if constexpr (LIST) {
+                // Balanced walk (adaptive cells, where a tile's targets span a range of h
+                // and their hit counts differ widely): the tile's H hits, laid out in
+                // lane order (each target's in ascending staged index), are cut into TW
+                // contiguous ranges, one per lane; a lane walks its range, moving to the
+                // next target where one's hits end, and sums each target's terms in
+                // order.  A target whose hits lie inside one range takes its sum from that
+                // lane; one whose hits cross ranges adds the pieces in lane order -- the
+                // same order on every run.
+                const int nh = __popc(m0) + __popc(m1) + __popc(m2) + __popc(m3);
+                int hincl = nh;
 #pragma unroll
-                    for (int dd = 1; dd < 32; dd <<= 1) {
-                        const int v = __shfl_up_sync(kFull, hincl, dd);
-                        if (lane >= dd) hincl += v;
-                    }
-                    const int htot = __shfl_sync(kFull, hincl, 31);
-                    const int hoff = hincl - nh;
-                    cnt += nh;
-                    float4 *wbase = smem + (size_t)wib * (3 * TPW * SLOT);
-                    const int *ibase = (const int *)(smem + (size_t)(blockDim.x >> 5) * (3 * TPW * SLOT)) +
-                                       (size_t)wib * TPW * SLOT;
-                    for (int base = 0; base < htot; base += 32) {
-                        const int hq = base + lane;
-                        const bool hv = hq < htot;
-                        int t = 0;
-#pragma unroll
-                        for (int st = 16; st > 0; st >>= 1)
-                            if (__shfl_sync(kFull, hoff, t + st) <= hq) t += st;
-                        int r = hq - __shfl_sync(kFull, hoff, t);
-                        const unsigned w0 = __shfl_sync(kFull, m0, t), w1 = __shfl_sync(kFull, m1, t);
-                        const unsigned w2 = __shfl_sync(kFull, m2, t), w3 = __shfl_sync(kFull, m3, t);
-                        const float tx = __shfl_sync(kFull, pi.x, t), ty = __shfl_sync(kFull, pi.y, t);
-                        const float tz = __shfl_sync(kFull, pi.z, t), th = __shfl_sync(kFull, pi.w, t);
-                        const float thinv = __shfl_sync(kFull, hinv, t), tL = __shfl_sync(kFull, L, t);
-                        const float tvx = __shfl_sync(kFull, vi.x, t), tvy = __shfl_sync(kFull, vi.y, t);
-                        const float tvz = __shfl_sync(kFull, vi.z, t);
-                        const float ttx = __shfl_sync(kFull, ti.x, t), tty = __shfl_sync(kFull, ti.y, t);
-                        const float ttz = __shfl_sync(kFull, ti.z, t), ttw = __shfl_sync(kFull, ti.w, t);
-                        const int ti_ = __shfl_sync(kFull, i, t);
-                        float gx = 0.f, gy = 0.f, gz = 0.f, gu = 0.f, gv = 0.f;
-                        if (hv) {
-                            int k;
-                            const int p0 = __popc(w0), p1 = __popc(w1), p2 = __popc(w2);
-                            if (r < p0) k = (int)__fns(w0, 0u, r + 1);
-                            else if ((r -= p0) < p1) k = 32 + (int)__fns(w1, 0u, r + 1);
-                            else if ((r -= p1) < p2) k = 64 + (int)__fns(w2, 0u, r + 1);
-                            else k = 96 + (int)__fns(w3, 0u, r - p2 + 1);
-                            k = (unsigned)k < (unsigned)B ? k : 0;  // (never taken: a hit lies in the batch)
-                            const float4 *sAt = wbase + (t / TW) * SLOT;
-                            const float4 s = sAt[k];
-                            const float4 vj = sAt[TPW * SLOT + k];
-                            const float4 tj = sAt[2 * TPW * SLOT + k];
-                            const float dx = tx - s.x, dy = ty - s.y, dz = tz - s.z;
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            if (r2 > 0.f) {
-                                const float hi2t = th * th, hj2 = s.w * s.w;
-                                bool in_i = r2 < hi2t, in_j = r2 < hj2;
-                                if (fabsf(r2 - hi2t) <= kBandK * th * (th + tL) ||
-                                    fabsf(r2 - hj2) <= kBandK * s.w * (s.w + tL)) {
-                                    const unsigned dd2 = band_decide(a.x, a.y, a.z, ti_, ibase[(t / TW) * SLOT + k], a.box,
-                                                                     th, s.w);
-                                    in_i = dd2 & 1u;
-                                    in_j = dd2 & 2u;
-                                }
-                                const float rinv = rsqrtf(r2);
-                                const float rr = r2 * rinv;
-                                const float hjinv = __fdividef(1.f, s.w);
-                                const float hj2inv = hjinv * hjinv;
-                                const float thinv2 = thinv * thinv;
-                                const float dWi = in_i ? kSigma * spline_dw_u(rr * thinv) * (thinv2 * thinv2) : 0.f;
-                                const float dWj = in_j ? kSigma * spline_dw_u(rr * hjinv) * (hj2inv * hj2inv) : 0.f;
-                                const float vx = tvx - vj.x, vy = tvy - vj.y, vz = tvz - vj.z;
-                                const float mu = fmaf(vx, dx, fmaf(vy, dy, vz * dz)) * rinv;
-                                const float muc = fminf(mu, 0.f);
-                                const float vsig_ij = ttz + tj.z - 3.f * muc;
-                                const float Pi = -a.alpha * vsig_ij * muc * (0.5f * (ttw + tj.w)) *
-                                                 __fdividef(1.f, ttx + tj.x);
-                                const float dWbar = 0.5f * (dWi + dWj);
-                                const float mj = vj.w;
-                                const float sc = mj * fmaf(tty, dWi, fmaf(tj.y, dWj, Pi * dWbar)) * rinv;
-                                gx = -sc * dx;
-                                gy = -sc * dy;
-                                gz = -sc * dz;
-                                gu = mj * mu * fmaf(tty, dWi, 0.5f * Pi * dWbar);
-                                gv = vsig_ij;
-                            }
-                        }
-#pragma unroll
-                        for (int dd = 1; dd < 32; dd <<= 1) {
-                            const int tu = __shfl_up_sync(kFull, t, dd);  // every lane takes part
-                            const bool same = lane >= dd && tu == t;
-                            const float ux = __shfl_up_sync(kFull, gx, dd), uy = __shfl_up_sync(kFull, gy, dd);
-                            const float uz = __shfl_up_sync(kFull, gz, dd), uu = __shfl_up_sync(kFull, gu, dd);
-                            const float uv = __shfl_up_sync(kFull, gv, dd);
-                            if (same) {
-                                gx += ux;
-                                gy += uy;
-                                gz += uz;
-                                gu += uu;
-                                gv = fmaxf(gv, uv);
-                            }
-                        }
-                        const int lo = hoff - base, hi_ = hoff + nh - base;
-                        const bool mine = nh > 0 && hi_ > 0 && lo < 32;
-                        const int src = mine ? min(hi_, 32) - 1 : lane;
-                        const float fx = __shfl_sync(kFull, gx, src), fy = __shfl_sync(kFull, gy, src);
-                        const float fz = __shfl_sync(kFull, gz, src), fu = __shfl_sync(kFull, gu, src);
-                        const float fv = __shfl_sync(kFull, gv, src);
-                        if (mine) {
-                            bx += fx;
-                            by += fy;
-                            bz += fz;
-                            bu += fu;
-                            vs = fmaxf(vs, fv);
-                        }
-                    }
-                    m0 = m1 = m2 = m3 = 0u;
-                    break;
+                for (int dd = 1; dd < TW; dd <<= 1) {
+                    const int v = __shfl_up_sync(kFull, hincl, dd, TW);
+                    if (tl >= dd) hincl += v;
                 }
-                if (m0 | m1 | m2 | m3) {
-                    const int k = pop_bit(m0, m1, m2, m3);
-                    const float4 s = sA[k];
-                    const float4 vj = sB[k];
-                    const float4 tj = sC[k];
-                    const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    ++cnt;
-                    if (r2 > 0.f) {  // the pair (i, i), and coincident pairs, have no direction
-                        bool in_i, in_j;
-                        decide(r2, s.w, sI + k, in_i, in_j);
-                        const float rinv = rsqrtf(r2);
-                        const float r = r2 * rinv;
-                        const float hjinv = __fdividef(1.f, s.w);
-                        const float hj2inv = hjinv * hjinv;
-                        const float dWi = in_i ? kSigma * spline_dw_u(r * hinv) * hinv4 : 0.f;
-                        const float dWj = in_j ? kSigma * spline_dw_u(r * hjinv) * (hj2inv * hj2inv) : 0.f;
-                        const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
-                        const float mu = fmaf(vx, dx, fmaf(vy, dy, vz * dz)) * rinv;
-                        // viscosity only on approach (mu < 0): branch-free, Pi = 0 otherwise
-                        const float muc = fminf(mu, 0.f);
-                        const float vsig_ij = ti.z + tj.z - 3.f * muc;
-                        const float Pi = -a.alpha * vsig_ij * muc * (0.5f * (ti.w + tj.w)) *
-                                         __fdividef(1.f, ti.x + tj.x);
-                        const float dWbar = 0.5f * (dWi + dWj);
-                        const float mj = vj.w;
-                        const float sc = mj * fmaf(ti.y, dWi, fmaf(tj.y, dWj, Pi * dWbar)) * rinv;
-                        bx = fmaf(-sc, dx, bx);
-                        by = fmaf(-sc, dy, by);
-                        bz = fmaf(-sc, dz, bz);
-                        bu = fmaf(mj * mu, fmaf(ti.y, dWi, 0.5f * Pi * dWbar), bu);
-                        vs = fmaxf(vs, vsig_ij);
+                const int H = __shfl_sync(kFull, hincl, TW - 1, TW);
+                const int hoff = hincl - nh;
+                cnt += nh;
+                wM[tl] = make_uint4(m0, m1, m2, m3);
+                wOff[tl] = hoff;
+                __syncwarp();
+                const int rb = (tl * H) / TW, re = ((tl + 1) * H) / TW;
+                if (rb < re) {
+                    // owner of position rb: the last target whose hits start at or before it
+                    int o = 0;
+#pragma unroll
+                    for (int st = TW / 2; st > 0; st >>= 1)
+                        if (wOff[o + st] <= rb) o += st;
+                    uint4 M = wM[o];
+                    drop_hits(M, rb - wOff[o]);  // those belong to the ranges before
+                    int io = 0;
+                    float4 po, vo, to;
+                    float ho = 0.f, hinv_o = 0.f, hinv4_o = 0.f, ho2 = 0.f, band_o = 0.f;
+                    auto owner = [&]() {
+                        io = wI[o];
+                        po = wP[o];
+                        vo = wV[o];
+                        to = wT[o];
+                        ho = po.w;
+                        hinv_o = 1.f / ho;
+                        hinv4_o = hinv_o * hinv_o * hinv_o * hinv_o;
+                        ho2 = ho * ho;
+                        band_o = kBandK * ho * (ho + L);
+                    };
+                    owner();
+                    ForceSum part;
+                    bool first = true;
+                    for (int p = rb; p < re; ++p) {
+                        if ((M.x | M.y | M.z | M.w) == 0u) {  // the owner's hits end here
+                            if (first) part.put(wF, wFv, tl);
+                            else part.put(wD, wDv, o);  // a target inside this range: only this lane
+                            first = false;
+                            do {
+                                ++o;
+                                M = wM[o];
+                            } while ((M.x | M.y | M.z | M.w) == 0u);
+                            owner();
+                        }
+                        const int k = pop_bit(M.x, M.y, M.z, M.w);
+                        const float4 s = sA[k];
+                        const float dx = po.x - s.x, dy = po.y - s.y, dz = po.z - s.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        if (r2 > 0.f) {  // the pair (i, i), and coincident pairs, have no direction
+                            const float hj2 = s.w * s.w;
+                            bool in_i = r2 < ho2, in_j = r2 < hj2;
+                            if (fabsf(r2 - ho2) <= band_o || fabsf(r2 - hj2) <= kBandK * s.w * (s.w + L)) {
+                                const unsigned d = band_decide(a.x, a.y, a.z, io, sI[k], a.box, ho, s.w);
+                                in_i = d & 1u;
+                                in_j = d & 2u;
+                            }
+                            force_term(dx, dy, dz, r2, in_i, in_j, hinv_o, hinv4_o, vo, to, s.w, sB[k], sC[k],
+                                       a.alpha, part);
+                        }
+                    }
+                    if (first) {
+                        part.put(wF, wFv, tl);
+                        wE[tl] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        wEv[tl] = 0.f;
+                    } else {
+                        part.put(wE, wEv, tl);
+                    }
+                } else {
+                    wF[tl] = wE[tl] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    wFv[tl] = wEv[tl] = 0.f;
+                }
+                __syncwarp();
+                if (nh > 0) {
+                    // the ranges La..Lb hold this target's hits hoff..hoff + nh - 1
+                    const int p0 = hoff, p1 = hoff + nh - 1;
+                    const int La = min(TW - 1, ((p0 + 1) * TW - 1) / H);
+                    const int Lb = min(TW - 1, ((p1 + 1) * TW - 1) / H);
+                    const int bA = (La * H) / TW, eA = ((La + 1) * H) / TW;
+                    float4 t4;
+                    float tv;
+                    if (La == Lb && p0 != bA && p1 + 1 != eA) {
+                        t4 = wD[tl];
+                        tv = wDv[tl];
+                    } else if (p0 == bA) {  // the first target of range La
+                        t4 = wF[La];
+                        tv = wFv[La];
+                    } else {  // the last one
+                        t4 = wE[La];
+                        tv = wEv[La];
+                    }
+                    for (int Lx = La + 1; Lx <= Lb; ++Lx) {  // ranges that start inside its hits
+                        const float4 f = wF[Lx];
+                        t4.x += f.x;
+                        t4.y += f.y;
+                        t4.z += f.z;
+                        t4.w += f.w;
+                        tv = fmaxf(tv, wFv[Lx]);
+                    }
+                    bx = t4.x;
+                    by = t4.y;
+                    bz = t4.z;
+                    bu = t4.w;
+                    vs = fmaxf(vs, tv);
+                }
+                __syncwarp();  // the scratch is rewritten by the next batch
+                m0 = m1 = m2 = m3 = 0u;
+            } else {
+                // lane by lane (uniform grid: a cell's targets have similar hit counts)
+                for (;;) {
+                    const unsigned busy = __ballot_sync(kFull, (m0 | m1 | m2 | m3) != 0u);
+                    if (busy == 0u) break;
+                    if (m0 | m1 | m2 | m3) {
+                        const int k = pop_bit(m0, m1, m2, m3);
+                        const float4 s = sA[k];
+                        const float4 vj = sB[k];
+                        const float4 tj = sC[k];
+                        const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        ++cnt;
+                        if (r2 > 0.f) {  // the pair (i, i), and coincident pairs, have no direction
+                            bool in_i, in_j;
+                            decide(r2, s.w, sI + k, in_i, in_j);
+                            const float rinv = rsqrtf(r2);
+                            const float r = r2 * rinv;
+                            const float hjinv = __fdividef(1.f, s.w);
+                            const float hj2inv = hjinv * hjinv;
+                            const float dWi = in_i ? kSigma * spline_dw_u(r * hinv) * hinv4 : 0.f;
+                            const float dWj = in_j ? kSigma * spline_dw_u(r * hjinv) * (hj2inv * hj2inv) : 0.f;
+                            const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+                            const float mu = fmaf(vx, dx, fmaf(vy, dy, vz * dz)) * rinv;
+                            // viscosity only on approach (mu < 0): branch-free, Pi = 0 otherwise
+                            const float muc = fminf(mu, 0.f);
+                            const float vsig_ij = ti.z + tj.z - 3.f * muc;
+                            const float Pi = -a.alpha * vsig_ij * muc * (0.5f * (ti.w + tj.w)) *
+                                             __fdividef(1.f, ti.x + tj.x);
+                            const float dWbar = 0.5f * (dWi + dWj);
+                            const float mj = vj.w;
+                            const float sc = mj * fmaf(ti.y, dWi, fmaf(tj.y, dWj, Pi * dWbar)) * rinv;
+                            bx = fmaf(-sc, dx, bx);
+                            by = fmaf(-sc, dy, by);
+                            bz = fmaf(-sc, dz, bz);
+                            bu = fmaf(mj * mu, fmaf(ti.y, dWi, 0.5f * Pi * dWbar), bu);
+                            vs = fmaxf(vs, vsig_ij);
+                        }
                     }
                 }
             }
@@ -1736,16 +1856,18 @@ __global__ void k_sync_h(const float *__restrict__ h, float4 *__restrict__ pos4,
 }
 
 template <int TW>
-static size_t density_smem()
+static size_t density_smem(bool list)
 {
-    return (size_t)(kPairThreads / 32) * 2 * (32 / TW) * (kBatchD + 1) * sizeof(float4);
+    return (size_t)(kPairThreads / 32) * 2 * (32 / TW) * (kBatchD + 1) * sizeof(float4) +
+           (list ? (size_t)(kPairThreads / 32) * 32 * kWalkBytesD : 0);
 }
 template <int TW>
 static size_t force_smem(bool list)
 {
     const size_t slots = (size_t)(kPairThreads / 32) * (32 / TW) * (kBatchF + 1);
     const size_t tiles = (size_t)(kPairThreads / 32) * (32 / TW);
-    return slots * (3 * sizeof(float4) + sizeof(int)) + (list ? tiles * 5 * kSlotF * sizeof(float) : 0);
+    return slots * (3 * sizeof(float4) + sizeof(int)) +
+           (list ? tiles * (5 * kSlotF * sizeof(float) + (size_t)TW * kWalkBytes) : 0);
 }
 
 static size_t force_sym_smem()
@@ -1760,7 +1882,7 @@ static int smem_optin(sph_ctx *ctx)
 {
     static bool done = false;
     if (done) return SPH_OK;
-    const int d16 = (int)density_smem<16>(), d32 = (int)density_smem<32>();
+    const int d16 = (int)density_smem<16>(true), d32 = (int)density_smem<32>(true);
     const int f16 = (int)force_smem<16>(true), f32 = (int)force_smem<32>(true);
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
 #define SPH_OPT_D(M)                                                              \
@@ -1899,7 +2021,7 @@ int run_density_pass(sph_ctx *ctx, sph_particles *parts, bool last_pass, bool ac
     cudaEvent_t end = nullptr;
     timer_begin(ctx, 0, &end);
     const int mode = ctx->adaptive ? 1 : (a.axis ? 2 : 0);
-    const size_t sm = ctx->tile_w == 32 ? density_smem<32>() : density_smem<16>();
+    const size_t sm = ctx->tile_w == 32 ? density_smem<32>(ctx->adaptive) : density_smem<16>(ctx->adaptive);
 #define SPH_LAUNCH_D(TWv, Hv, Mv) k_density<TWv, Hv, Mv><<<g, kPairThreads, sm, ctx->stream>>>(a)
     if (ctx->tile_w == 32) {
         if (mode == 1) { if (hash) SPH_LAUNCH_D(32, true, 1); else SPH_LAUNCH_D(32, false, 1); }
