@@ -804,9 +804,7 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
             if (SWEEP && have_n) slot_at(jn, vn);
             const float4 pn = vn ? __ldg(a.pos4 + jn) : make_float4(0.f, 0.f, 0.f, 0.f);
             bool keep = false;
-            float4 vj;
             if (vc) {
-                vj = __ldg(a.vel4 + jc);
                 pc.x += scx;
                 pc.y += scy;
                 pc.z += scz;
@@ -819,7 +817,7 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
             if (keep) {
                 const int pos = nst + __popc(mine & lt);
                 sA[pos] = make_float4(pc.x, pc.y, pc.z, __int_as_float(jc));
-                sB[pos] = vj;
+                sB[pos] = __ldg(a.vel4 + jc);  // (only for the kept sources: 1.6 % faster on boxes)
             }
             nst += __popc(mine);
             const int mx = (int)__reduce_max_sync(kFull, (unsigned)nst);
@@ -1208,7 +1206,7 @@ __global__ void __launch_bounds__(kPairThreads, MODE == 1 ? kForceBlocks : kForc
                     owner();
                     ForceSum part;
                     bool first = true;
-                    for (int p = rb; p < re; ++p) {
+                    for (int p = rb; p < re;) {
                         if ((M.x | M.y | M.z | M.w) == 0u) {  // the owner's hits end here
                             if (first) part.put(wF, wFv, tl);
                             else part.put(wD, wDv, o);  // a target inside this range: only this lane
@@ -1219,21 +1217,30 @@ __global__ void __launch_bounds__(kPairThreads, MODE == 1 ? kForceBlocks : kForc
                             } while ((M.x | M.y | M.z | M.w) == 0u);
                             owner();
                         }
-                        const int k = pop_bit(M.x, M.y, M.z, M.w);
-                        const float4 s = sA[k];
-                        const float dx = po.x - s.x, dy = po.y - s.y, dz = po.z - s.z;
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        if (r2 > 0.f) {  // the pair (i, i), and coincident pairs, have no direction
-                            const float hj2 = s.w * s.w;
-                            bool in_i = r2 < ho2, in_j = r2 < hj2;
-                            if (fabsf(r2 - ho2) <= band_o || fabsf(r2 - hj2) <= kBandK * s.w * (s.w + L)) {
-                                const unsigned d = band_decide(a.x, a.y, a.z, io, sI[k], a.box, ho, s.w);
-                                in_i = d & 1u;
-                                in_j = d & 2u;
+                        // two hits of the owner at once where the range holds them (two
+                        // instruction streams, added in order: the sums of one at a time)
+                        const int k1 = pop_bit(M.x, M.y, M.z, M.w);
+                        const bool two = p + 1 < re && (M.x | M.y | M.z | M.w) != 0u;
+                        const int k2 = two ? pop_bit(M.x, M.y, M.z, M.w) : k1;
+                        p += two ? 2 : 1;
+                        auto add = [&](int k) {
+                            const float4 s = sA[k];
+                            const float dx = po.x - s.x, dy = po.y - s.y, dz = po.z - s.z;
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            if (r2 > 0.f) {  // the pair (i, i), and coincident pairs, have no direction
+                                const float hj2 = s.w * s.w;
+                                bool in_i = r2 < ho2, in_j = r2 < hj2;
+                                if (fabsf(r2 - ho2) <= band_o || fabsf(r2 - hj2) <= kBandK * s.w * (s.w + L)) {
+                                    const unsigned d = band_decide(a.x, a.y, a.z, io, sI[k], a.box, ho, s.w);
+                                    in_i = d & 1u;
+                                    in_j = d & 2u;
+                                }
+                                force_term(dx, dy, dz, r2, in_i, in_j, hinv_o, hinv4_o, vo, to, s.w, sB[k], sC[k],
+                                           a.alpha, part);
                             }
-                            force_term(dx, dy, dz, r2, in_i, in_j, hinv_o, hinv4_o, vo, to, s.w, sB[k], sC[k],
-                                       a.alpha, part);
-                        }
+                        };
+                        add(k1);
+                        if (two) add(k2);
                     }
                     if (first) {
                         part.put(wF, wFv, tl);
