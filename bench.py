@@ -900,8 +900,12 @@ def run_adaptive(args):
     dom = max(kernels, key=lambda k: kernels[k][0])
     t_ms, flops, launches = kernels[dom]
     achieved = flops / (t_ms / 1e3) / 1e12 if t_ms > 0 else 0.0
+    # DRAM bytes per launch: the batched boxes from the committed summary of the same
+    # kernel on a smaller set of them, scaled by the units of work (no summary is kept
+    # for the clustered field)
+    traffic = _boxes_traffic(dom, launches, st, n) if offs is not None else None
     roofline = {"bound": "alu", "kernel": f"k_{dom} (list mode)", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "peak_source": peak_how,
                 "launches": launches, "avg_launch_ms": t_ms / max(launches, 1)}
 
