@@ -73,7 +73,7 @@ typedef struct sph_ctx sph_ctx; /* opaque, library-owned */
 #define SPH_FLAG_AUTOTUNE 4u /* before the first density pass, time for each candidate
                                 schedule (tile width 16/32 x cell factor 1.05/1.25/1.5;
                                 with SPH_FLAG_ADAPTIVE: tile width x leaf size
-                                32/64/128) the cell build, one density pass and one
+                                64/128/256) the cell build, one density pass and one
                                 force pass on the current particles and keep the
                                 fastest; overrides tile_width and cell_factor
                                 (leaf_max).  On the uniform grid it then times, at

@@ -202,7 +202,7 @@ static int autotune(sph_ctx *ctx, sph_particles *parts)
 {
     const int tws[2] = {16, 32};
     const float cfs[3] = {1.05f, 1.25f, 1.5f};
-    const int leaves[3] = {32, 64, 128};  // adaptive cells: leaf sizes instead of cell factors
+    const int leaves[3] = {64, 128, 256};  // adaptive cells: leaf sizes instead of cell factors
     cudaEvent_t ev[4];
     for (int i = 0; i < 4; ++i) SPH_CUDA(ctx, cudaEventCreate(&ev[i]));
     // schedules whose cells are too large for the FP32 frame of the smallest h (uniform

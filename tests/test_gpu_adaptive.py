@@ -81,6 +81,20 @@ def test_adaptive_uniform_ragged(n, seed, tw):
     check_force(g, s)
 
 
+@pytest.mark.parametrize("leaf", [256])
+def test_adaptive_clustered_large_leaves(leaf):
+    """Leaves of up to 256 particles (the largest size the autotuner tries; their
+    targets are still put in ascending h): eight tiles of 32 per full leaf."""
+    d = _clustered(30000, 27, 12)
+    ctx, parts, g = gpu_hydro(d, flags=_flags(), tile_width=32, leaf_max=leaf)
+    assert g["stats"]["leaf_max"] == leaf
+    s = oracle_state(g)
+    t = _targets(g, 300, 3)
+    dd = check_density(g, s, targets=t)
+    check_ghost(g, s, dd, t)
+    check_force(g, s, targets=t)
+
+
 def test_adaptive_top_cell_keys_bit_exact():
     d = _clustered(20000, 22, 10)
     ctx, parts, g = gpu_hydro(d, flags=_flags())
