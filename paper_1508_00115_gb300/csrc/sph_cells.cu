@@ -205,6 +205,99 @@ __global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const K *__restric
     }
 }
 
+// The same pass written through shared memory: the tile's keys are first placed in
+// their order within the tile (the digit runs one after another, each run in the
+// stable order above), then written out run by run, consecutive threads writing
+// consecutive addresses (the plain scatter writes each key where it ranks, 256 runs
+// interleaved).  Every key lands where k_radix_scatter puts it.
+template <typename K>
+__global__ void __launch_bounds__(kRsThreads) k_radix_scatter_c(const K *__restrict__ kin,
+                                                                const uint32_t *__restrict__ vin,
+                                                                K *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                                int n, int shift, const uint32_t *__restrict__ offs,
+                                                                int ntiles)
+{
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    K *sk = reinterpret_cast<K *>(rs_smem);                     // kRsTile keys in tile order
+    uint32_t *sv = reinterpret_cast<uint32_t *>(sk + kRsTile);  // and their values
+    __shared__ uint32_t wcnt[kRsWarps][256];
+    __shared__ uint32_t woff[kRsWarps][256];
+    __shared__ uint32_t dstart[256];  // tile-local start of each digit's run
+    __shared__ uint32_t gbase[256];   // global start of this tile's run of each digit
+    __shared__ uint32_t wtot[kRsWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = lane; d < 256; d += 32) wcnt[w][d] = 0;
+    __syncwarp();
+    const int64_t base = (int64_t)blockIdx.x * kRsTile + (int64_t)w * (kRsItems * 32);
+    const unsigned lt = (1u << lane) - 1u;
+    K key[kRsItems];
+    uint32_t val[kRsItems];
+    uint16_t rank[kRsItems];
+#pragma unroll
+    for (int it = 0; it < kRsItems; ++it) {
+        int64_t i = base + it * 32 + lane;
+        bool ok = i < n;
+        K k = ok ? kin[i] : (K)0;
+        key[it] = k;
+        val[it] = ok ? (vin ? vin[i] : (uint32_t)i) : 0u;
+        uint32_t d = ok ? ((uint32_t)(k >> shift) & 255u) : 256u;
+        unsigned peers = __match_any_sync(kFull, d);
+        uint32_t before = ok ? wcnt[w][d] : 0u;
+        rank[it] = (uint16_t)(before + __popc(peers & lt));
+        __syncwarp();
+        int leader = 31 - __clz(peers);
+        if (ok && lane == leader) wcnt[w][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        // per digit (one thread each): warp-order offsets, the tile's count, and an
+        // exclusive prefix of the counts over the digits (warp scans, then the warps')
+        const int d = threadIdx.x;
+        uint32_t c = 0;
+#pragma unroll
+        for (int ww = 0; ww < kRsWarps; ++ww) {
+            woff[ww][d] = c;
+            c += wcnt[ww][d];
+        }
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wtot[w] = incl;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int ww = 0; ww < w; ++ww) before += wtot[ww];
+        dstart[d] = before + incl - c;
+        gbase[d] = offs[(int64_t)d * ntiles + blockIdx.x];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kRsItems; ++it) {
+        int64_t i = base + it * 32 + lane;
+        if (i < n) {
+            const uint32_t d = (uint32_t)(key[it] >> shift) & 255u;
+            const uint32_t p = dstart[d] + woff[w][d] + rank[it];
+            sk[p] = key[it];
+            sv[p] = val[it];
+        }
+    }
+    __syncthreads();
+    const int m = (int)min((int64_t)kRsTile, (int64_t)n - (int64_t)blockIdx.x * kRsTile);
+    for (int p = threadIdx.x; p < m; p += kRsThreads) {
+        const K k = sk[p];
+        const uint32_t d = (uint32_t)(k >> shift) & 255u;
+        const uint32_t dst = gbase[d] + ((uint32_t)p - dstart[d]);
+        kout[dst] = k;
+        vout[dst] = sv[p];
+    }
+}
+
+template <typename K>
+static size_t scatter_c_smem() { return (size_t)kRsTile * (sizeof(K) + sizeof(uint32_t)); }
+
 // Stable LSD sort of keys[] (n entries, key_bits significant) with source slots as
 // values (identity at the start); the sorted keys and slots end in keys[] / vals[]
 // (the buffers are swapped on the host when the pass count is odd).
@@ -212,6 +305,14 @@ template <typename K>
 static int radix_sort_any(sph_ctx *ctx, int n, int key_bits, K *&keys, K *&keys_alt)
 {
     int ntiles = (n + kRsTile - 1) / kRsTile;
+    static bool optin = false;  // (per function, once per process)
+    if (!optin) {
+        SPH_CUDA(ctx, cudaFuncSetAttribute(k_radix_scatter_c<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)scatter_c_smem<uint32_t>()));
+        SPH_CUDA(ctx, cudaFuncSetAttribute(k_radix_scatter_c<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)scatter_c_smem<uint64_t>()));
+        optin = true;
+    }
     K *kin = keys, *kout = keys_alt;
     uint32_t *vin = nullptr, *vout = ctx->vals_alt;
     int passes = std::max(1, (key_bits + 7) / 8);
@@ -221,8 +322,8 @@ static int radix_sort_any(sph_ctx *ctx, int n, int key_bits, K *&keys, K *&keys_
         SPH_LAUNCH(ctx, "radix histogram");
         int rc = exclusive_scan_u32(ctx, ctx->hist, ctx->hist, (int64_t)256 * ntiles);
         if (rc) return rc;
-        k_radix_scatter<K><<<ntiles, kRsThreads, 0, ctx->stream>>>(kin, vin, kout, vout, n, shift, ctx->hist,
-                                                                  ntiles);
+        k_radix_scatter_c<K><<<ntiles, kRsThreads, scatter_c_smem<K>(), ctx->stream>>>(kin, vin, kout, vout, n, shift,
+                                                                                   ctx->hist, ntiles);
         SPH_LAUNCH(ctx, "radix scatter");
         std::swap(kin, kout);
         vin = vout;
