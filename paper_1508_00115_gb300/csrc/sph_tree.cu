@@ -455,7 +455,9 @@ __global__ void k_leaf_pos(const int *__restrict__ leaf_of, const double *__rest
 
 // Targets of every leaf in ascending h (ties by slot), so that a tile holds targets of
 // similar h: its reach -- and with it the candidates of every target -- is not set by
-// one large-h particle among small ones.  One warp per leaf; leaves above kSortMax
+// one large-h particle among small ones.  One warp per leaf: a bitonic sort in shared
+// memory of the keys (bits of h, which order as h does for h >= 0; slot within the leaf),
+// padded to a power of two with keys above every real one.  Leaves above kSortMax
 // particles keep their order.
 constexpr int kSortMax = 256;
 constexpr int kSortWarps = 4;
@@ -463,8 +465,9 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_leaf_hsort(const int2 *__re
                                                                 const int *__restrict__ nlp,
                                                                 const float *__restrict__ h, int *__restrict__ tord)
 {
-    __shared__ float sh[kSortWarps][kSortMax];
+    __shared__ unsigned long long sk[kSortWarps][kSortMax];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned long long *k2 = sk[wib];
     const int nl = nlp ? *nlp : nl_h;
     for (int l = blockIdx.x * kSortWarps + wib; l < nl; l += gridDim.x * kSortWarps) {  // warp-uniform
         const int lo = rng[l].x, c = rng[l].y - lo;
@@ -472,18 +475,26 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_leaf_hsort(const int2 *__re
             for (int k = lane; k < c; k += 32) tord[lo + k] = lo + k;
             continue;
         }
+        int P = 1;
+        while (P < c) P <<= 1;
         __syncwarp();
-        for (int k = lane; k < c; k += 32) sh[wib][k] = h[lo + k];
+        for (int k = lane; k < P; k += 32)
+            k2[k] = k < c ? ((unsigned long long)__float_as_uint(h[lo + k]) << 32) | (unsigned)k : ~0ull;
         __syncwarp();
-        for (int k = lane; k < c; k += 32) {
-            const float hk = sh[wib][k];
-            int rank = 0;
-            for (int m = 0; m < c; ++m) {
-                const float hm = sh[wib][m];
-                rank += (hm < hk || (hm == hk && m < k)) ? 1 : 0;
+        for (int size = 2; size <= P; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = lane; t < (P >> 1); t += 32) {
+                    const int i = 2 * t - (t & (stride - 1));  // lower element of the t-th pair
+                    const unsigned long long a = k2[i], b = k2[i + stride];
+                    if ((a > b) == ((i & size) == 0)) {  // ascending where (i & size) == 0
+                        k2[i] = b;
+                        k2[i + stride] = a;
+                    }
+                }
+                __syncwarp();
             }
-            tord[lo + rank] = lo + k;
         }
+        for (int k = lane; k < c; k += 32) tord[lo + k] = lo + (int)(unsigned)(k2[k] & 0xffffffffull);
     }
 }
 
