@@ -457,17 +457,26 @@ __global__ void k_leaf_pos(const int *__restrict__ leaf_of, const double *__rest
 // similar h: its reach -- and with it the candidates of every target -- is not set by
 // one large-h particle among small ones.  One warp per leaf: a bitonic sort in shared
 // memory of the keys (bits of h, which order as h does for h >= 0; slot within the leaf),
-// padded to a power of two with keys above every real one.  Leaves above kSortMax
-// particles keep their order.
+// padded to a power of two with keys above every real one.  Then each run of two tiles'
+// worth (2 tw targets of similar h) is sorted along the longest side of its bounding box
+// (the coordinate's FP32 bits: positions lie in [0, box)), so that each of its two tiles
+// covers half of it: 2-3 % fewer pair-pass time on the uneven boxes (a second, finer
+// split of runs of four tiles was slower).  Leaves above kSortMax particles keep their
+// order.
 constexpr int kSortMax = 256;
 constexpr int kSortWarps = 4;
 __global__ void __launch_bounds__(32 * kSortWarps) k_leaf_hsort(const int2 *__restrict__ rng, int nl_h,
                                                                 const int *__restrict__ nlp,
-                                                                const float *__restrict__ h, int *__restrict__ tord)
+                                                                const float *__restrict__ h, int *__restrict__ tord,
+                                                                const double *__restrict__ x,
+                                                                const double *__restrict__ y,
+                                                                const double *__restrict__ z, int tw)
 {
     __shared__ unsigned long long sk[kSortWarps][kSortMax];
+    __shared__ unsigned long long sg[kSortWarps][64];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned long long *k2 = sk[wib];
+    unsigned long long *g2 = sg[wib];
     const int nl = nlp ? *nlp : nl_h;
     for (int l = blockIdx.x * kSortWarps + wib; l < nl; l += gridDim.x * kSortWarps) {  // warp-uniform
         const int lo = rng[l].x, c = rng[l].y - lo;
@@ -493,6 +502,62 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_leaf_hsort(const int2 *__re
                 }
                 __syncwarp();
             }
+        }
+        // groups of two tiles of similar h: each split in two halves along the longest
+        // side of the group's box, so that each tile covers half of it
+        const int gs = 2 * tw;
+        for (int g0 = 0; g0 < c; g0 += gs) {
+            const int gc = min(gs, c - g0);
+            if (gc <= tw) break;
+            float mn0 = 3e38f, mn1 = 3e38f, mn2 = 3e38f, mx0 = -3e38f, mx1 = -3e38f, mx2 = -3e38f;
+            for (int k = lane; k < gc; k += 32) {
+                const int s_ = lo + (int)(unsigned)(k2[g0 + k] & 0xffffffffull);
+                const float px = (float)x[s_], py = (float)y[s_], pz = (float)z[s_];
+                mn0 = fminf(mn0, px);
+                mx0 = fmaxf(mx0, px);
+                mn1 = fminf(mn1, py);
+                mx1 = fmaxf(mx1, py);
+                mn2 = fminf(mn2, pz);
+                mx2 = fmaxf(mx2, pz);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mn0 = fminf(mn0, __shfl_xor_sync(kFull, mn0, o));
+                mx0 = fmaxf(mx0, __shfl_xor_sync(kFull, mx0, o));
+                mn1 = fminf(mn1, __shfl_xor_sync(kFull, mn1, o));
+                mx1 = fmaxf(mx1, __shfl_xor_sync(kFull, mx1, o));
+                mn2 = fminf(mn2, __shfl_xor_sync(kFull, mn2, o));
+                mx2 = fmaxf(mx2, __shfl_xor_sync(kFull, mx2, o));
+            }
+            const int ax = (mx0 - mn0 >= mx1 - mn1 && mx0 - mn0 >= mx2 - mn2) ? 0 : (mx1 - mn1 >= mx2 - mn2 ? 1 : 2);
+            int P2 = 1;
+            while (P2 < gc) P2 <<= 1;
+            __syncwarp();
+            for (int k = lane; k < P2; k += 32) {
+                unsigned long long key = ~0ull;
+                if (k < gc) {
+                    const unsigned s_ = (unsigned)(k2[g0 + k] & 0xffffffffull);
+                    const double v = ax == 0 ? x[lo + s_] : (ax == 1 ? y[lo + s_] : z[lo + s_]);
+                    key = ((unsigned long long)__float_as_uint((float)v) << 32) | s_;
+                }
+                g2[k] = key;
+            }
+            __syncwarp();
+            for (int size = 2; size <= P2; size <<= 1) {
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    for (int t = lane; t < (P2 >> 1); t += 32) {
+                        const int i = 2 * t - (t & (stride - 1));
+                        const unsigned long long a = g2[i], b = g2[i + stride];
+                        if ((a > b) == ((i & size) == 0)) {
+                            g2[i] = b;
+                            g2[i + stride] = a;
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+            for (int k = lane; k < gc; k += 32) k2[g0 + k] = g2[k];
+            __syncwarp();
         }
         for (int k = lane; k < c; k += 32) tord[lo + k] = lo + (int)(unsigned)(k2[k] & 0xffffffffull);
     }
@@ -1002,7 +1067,8 @@ static int build_tree_device(sph_ctx *ctx, sph_particles *parts)
     // tiles (the leaf arrays hold n + 1 entries: nl <= n)
     const int *nlp = &dc->nl;
     const int64_t capl = (int64_t)n + 1;
-    k_leaf_hsort<<<gp, 32 * kSortWarps, 0, ctx->stream>>>(T.leaf_rng, 0, nlp, parts->h, T.tord);
+    k_leaf_hsort<<<gp, 32 * kSortWarps, 0, ctx->stream>>>(T.leaf_rng, 0, nlp, parts->h, T.tord, parts->x, parts->y,
+                                                          parts->z, ctx->tile_w);
     SPH_LAUNCH(ctx, "leaf h order");
     k_leaf_tiles_n<<<gp, 256, 0, ctx->stream>>>(T.leaf_rng, 0, nlp, (int)capl, ctx->tile_w, T.list_off);
     SPH_LAUNCH(ctx, "leaf tile counts");
@@ -1282,7 +1348,8 @@ int build_tree(sph_ctx *ctx, sph_particles *parts)
     // tiles
     if (nl > 0) {
         k_leaf_hsort<<<nblk(nl, kSortWarps), 32 * kSortWarps, 0, ctx->stream>>>(T.leaf_rng, nl, nullptr, parts->h,
-                                                                                 T.tord);
+                                                                                 T.tord, parts->x, parts->y, parts->z,
+                                                                                 ctx->tile_w);
         SPH_LAUNCH(ctx, "leaf h order");
         k_leaf_tiles_n<<<nblk(nl, 256), 256, 0, ctx->stream>>>(T.leaf_rng, nl, nullptr, 0, ctx->tile_w, T.list_off);
         SPH_LAUNCH(ctx, "leaf tile counts");
