@@ -31,8 +31,9 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found (CUDA toolkit required to build libsph)")
 
 
-# the translation unit of the pair kernels (k_density, k_force and their launches)
-PAIR_SOURCES = ["sph_pairs.cu", "sph_internal.cuh"]
+# the pair kernels (k_density, k_force and their launches) and the cell and tree builds
+# that lay out their work (cell order, leaves, the tiles' targets)
+PAIR_SOURCES = ["sph_pairs.cu", "sph_internal.cuh", "sph_cells.cu", "sph_tree.cu"]
 
 
 def _digest(files=None) -> str:
@@ -59,8 +60,8 @@ def gravity_kernel_digest() -> str:
 
 
 def pair_kernel_digest() -> str:
-    """Identity of the pair kernels' sources: ncu figures of k_density / k_force stay
-    valid while it is unchanged."""
+    """Identity of the pair kernels' sources and of the builds that lay out their work:
+    ncu figures of k_density / k_force stay valid while it is unchanged."""
     return _digest(PAIR_SOURCES)
 
 
