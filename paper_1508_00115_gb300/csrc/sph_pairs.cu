@@ -502,12 +502,14 @@ __global__ void __launch_bounds__(kPairThreads, kDensityBlocks) k_density(Densit
                         const float dx = pi.x - s.x, dy = pi.y - s.y, dz = pi.z - s.z;
                         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                         mn |= (unsigned)(r2 < lob) << u;
-                        bn |= (unsigned)(r2 >= lob && r2 < hib) << u;
+                        bn |= (unsigned)(r2 < hib) << u;  // (below the band's top; the hits are removed after)
                     }
                     mw |= mn << k4;
                     bw |= bn << k4;
                 }
-                // (rare) band pairs in FP64, out of the branch-free loop above
+                // (rare) band pairs in FP64, out of the branch-free loop above: below the
+                // band's top and not a hit
+                bw &= ~mw;
                 while (bw) {
                     const int kk = __ffs(bw) - 1;
                     bw &= bw - 1u;
@@ -1125,7 +1127,7 @@ __global__ void __launch_bounds__(kPairThreads, MODE == 1 ? kForceBlocks : kForc
                             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                             const float d2 = r2 - fmaxf(hi2, s.w * s.w);
                             mn |= (unsigned)(d2 < -bandmax) << u;
-                            bn |= (unsigned)(d2 >= -bandmax && d2 < bandmax) << u;
+                            bn |= (unsigned)(d2 < bandmax) << u;
                         }
                     } else {
 #pragma unroll
@@ -1142,13 +1144,15 @@ __global__ void __launch_bounds__(kPairThreads, MODE == 1 ? kForceBlocks : kForc
                         const float l0 = fmaxf(tlo_i, lo2.x), l1 = fmaxf(tlo_i, lo2.y);
                         const float h0 = fmaxf(thi_i, hi2v.x), h1 = fmaxf(thi_i, hi2v.y);
                         mn |= ((unsigned)(r2.x < l0) << u) | ((unsigned)(r2.y < l1) << (u + 1));
-                        bn |= ((unsigned)(r2.x >= l0 && r2.x < h0) << u) | ((unsigned)(r2.y >= l1 && r2.y < h1) << (u + 1));
+                        bn |= ((unsigned)(r2.x < h0) << u) | ((unsigned)(r2.y < h1) << (u + 1));
                     }
                     }
                     mw |= mn << k4;
                     bw |= bn << k4;
                 }
-                // (rare) band pairs in FP64, out of the branch-free loop above
+                // (rare) band pairs in FP64, out of the branch-free loop above: below the
+                // band's top and not a hit
+                bw &= ~mw;
                 while (bw) {
                     const int kk = __ffs(bw) - 1;
                     bw &= bw - 1u;
@@ -1642,11 +1646,12 @@ __global__ void __launch_bounds__(kPairThreads, kForceBlocks) k_force_sym(ForceS
                             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                             const float d2 = r2 - fmaxf(hi2, s.w * s.w);
                             mn |= (unsigned)(d2 < -bandmax) << u;
-                            bn |= (unsigned)(d2 >= -bandmax && d2 < bandmax) << u;
+                            bn |= (unsigned)(d2 < bandmax) << u;
                         }
                         mw |= mn << k4;
                         bw |= bn << k4;
                     }
+                    bw &= ~mw;  // below the band's top and not a hit
                     while (bw) {
                         const int kk = __ffs(bw) - 1;
                         bw &= bw - 1u;
