@@ -507,6 +507,34 @@ static int finish_call(sph_ctx *ctx, int rc)
 
 // build -> density -> force.  in_step: the hydro pass inside a step, where the
 // previous pass's outputs feed the learned h guess and the sample collection.
+// Inside sph_step_host: the device-to-host copies of the results the rest of the step
+// no longer writes, issued on the copy stream behind an event of the compute stream,
+// so that they overlap the passes that follow.  After the density passes (and any
+// re-binning they caused) the order, positions, masses, h and the density outputs are
+// final; after the force pass the accelerations, du/dt and v_sig.
+static int early_copies(sph_ctx *ctx, const sph_particles *d, int stage)
+{
+    sph_particles *hp = ctx->host_out;
+    if (!hp || ctx->n <= 0) return SPH_OK;
+    const size_t b8 = 8 * (size_t)ctx->n, b4 = 4 * (size_t)ctx->n;
+    cudaStream_t cs = ctx->copy_stream;
+    SPH_CUDA(ctx, cudaEventRecord(ctx->copy_ev, ctx->stream));
+    SPH_CUDA(ctx, cudaStreamWaitEvent(cs, ctx->copy_ev, 0));
+    if (stage == 0) {
+        double *s64[][2] = {{hp->x, d->x}, {hp->y, d->y}, {hp->z, d->z}};
+        for (auto &q : s64) SPH_CUDA(ctx, cudaMemcpyAsync(q[0], q[1], b8, cudaMemcpyDeviceToHost, cs));
+        float *s32[][2] = {{hp->m, d->m}, {hp->h, d->h},     {hp->rho, d->rho}, {hp->P, d->P},
+                           {hp->c, d->c}, {hp->f, d->f}, {hp->divv, d->divv}, {hp->curl, d->curl}};
+        for (auto &q : s32) SPH_CUDA(ctx, cudaMemcpyAsync(q[0], q[1], b4, cudaMemcpyDeviceToHost, cs));
+        SPH_CUDA(ctx, cudaMemcpyAsync(hp->n_ngb, d->n_ngb, b4, cudaMemcpyDeviceToHost, cs));
+    } else {
+        float *s32[][2] = {{hp->ax, d->ax}, {hp->ay, d->ay}, {hp->az, d->az}, {hp->dudt, d->dudt},
+                           {hp->vsig, d->vsig}};
+        for (auto &q : s32) SPH_CUDA(ctx, cudaMemcpyAsync(q[0], q[1], b4, cudaMemcpyDeviceToHost, cs));
+    }
+    return SPH_OK;
+}
+
 static int hydro(sph_ctx *ctx, sph_particles *parts, bool in_step = false)
 {
     int rc = do_build(ctx, parts);
@@ -526,7 +554,13 @@ static int hydro(sph_ctx *ctx, sph_particles *parts, bool in_step = false)
         rc = hp_collect(ctx, parts);
         if (rc) return rc;
     }
-    return do_force(ctx, parts);
+    if (in_step) {
+        rc = early_copies(ctx, parts, 0);
+        if (rc) return rc;
+    }
+    rc = do_force(ctx, parts);
+    if (rc) return rc;
+    return in_step ? early_copies(ctx, parts, 1) : SPH_OK;
 }
 
 static int do_step(sph_ctx *ctx, sph_particles *parts, double dt, double *dt_used, sph_conserved *out)
@@ -1111,6 +1145,10 @@ int sph_step_host(sph_ctx *ctx, sph_particles *hp, double dt, double *dt_used, s
         m.n_ngb = (int32_t *)take(4 * cap);
         ctx->mirror_cap = cap;
     }
+    if (!ctx->copy_stream) {
+        SPH_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        SPH_CUDA(ctx, cudaEventCreateWithFlags(&ctx->copy_ev, cudaEventDisableTiming));
+    }
     sph_particles &d = ctx->dev_mirror;
     cudaStream_t s = ctx->stream;
     const size_t b8 = 8 * (size_t)n, b4 = 4 * (size_t)n;
@@ -1123,18 +1161,21 @@ int sph_step_host(sph_ctx *ctx, sph_particles *hp, double dt, double *dt_used, s
     // the device copies replace whatever the context held: cells must be rebuilt
     ctx->built = ctx->density_valid = false;
     ctx->soft_rc = 0;
+    // results go back as soon as the step is done with them (the copy stream), the
+    // velocities and u (closing kick) at the end
+    ctx->host_out = hp;
     int rc = do_step(ctx, &d, dt, dt_used, out);
+    ctx->host_out = nullptr;
     if (rc) {
+        cudaStreamSynchronize(ctx->copy_stream);  // (nothing in flight is left reading the mirror)
         ctx->soft_rc = 0;
         return rc;
     }
-    for (auto &q : in64) SPH_CUDA(ctx, cudaMemcpyAsync(q[1], q[0], b8, cudaMemcpyDeviceToHost, s));
-    for (auto &q : in32) SPH_CUDA(ctx, cudaMemcpyAsync(q[1], q[0], b4, cudaMemcpyDeviceToHost, s));
-    float *out32[][2] = {{d.rho, hp->rho}, {d.P, hp->P}, {d.c, hp->c}, {d.f, hp->f}, {d.divv, hp->divv},
-                         {d.curl, hp->curl}};
-    for (auto &q : out32) SPH_CUDA(ctx, cudaMemcpyAsync(q[1], q[0], b4, cudaMemcpyDeviceToHost, s));
-    SPH_CUDA(ctx, cudaMemcpyAsync(hp->n_ngb, d.n_ngb, b4, cudaMemcpyDeviceToHost, s));
+    double *end64[][2] = {{d.vx, hp->vx}, {d.vy, hp->vy}, {d.vz, hp->vz}};
+    for (auto &q : end64) SPH_CUDA(ctx, cudaMemcpyAsync(q[1], q[0], b8, cudaMemcpyDeviceToHost, s));
+    SPH_CUDA(ctx, cudaMemcpyAsync(hp->u, d.u, b4, cudaMemcpyDeviceToHost, s));
     SPH_CUDA(ctx, cudaStreamSynchronize(s));
+    SPH_CUDA(ctx, cudaStreamSynchronize(ctx->copy_stream));
     return finish_call(ctx, SPH_OK);
 }
 
@@ -1351,6 +1392,8 @@ void sph_destroy(sph_ctx *ctx)
     cudaFree(ctx->d_box_off);
     if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->copy_ev) cudaEventDestroy(ctx->copy_ev);
     cudaFree(ctx->mirror_block);
     for (Timer &t : ctx->timers) {
         cudaEventDestroy(t.a);

@@ -255,6 +255,11 @@ struct sph_ctx {
     sph_particles dev_mirror{};
     int64_t mirror_cap = 0;
     void *mirror_block = nullptr;
+    // inside sph_step_host: the caller's arrays, and a second stream on which each
+    // result goes back to the host once the step has finished with it
+    sph_particles *host_out = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_ev = nullptr;
 
     bool ids_valid = false;   // ids hold a permutation
     bool built = false;       // cells match the current positions

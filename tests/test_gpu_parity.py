@@ -367,17 +367,22 @@ def test_axis_sweep_parity(tw):
         ctx.step(parts, 2e-4)
 
 
-@pytest.mark.parametrize("pin", [True, False])
-def test_step_host_matches_device_step(pin):
-    """sph_step_host (host arrays, copies inside the call) gives exactly what
-    sph_step gives on device arrays: the same kernels in the same order."""
+@pytest.mark.parametrize("pin,adaptive", [(True, False), (False, False), (True, True)])
+def test_step_host_matches_device_step(pin, adaptive):
+    """sph_step_host (host arrays, copies inside the call -- the results go back on a
+    second stream as soon as the step is done with them) gives exactly what sph_step
+    gives on device arrays: the same kernels in the same order."""
     from paper_1508_00115_gb300 import binding
-    d = _uniform_moving(5000, 91)
+    if adaptive:
+        d = inputs.random_velocities(inputs.plummer_mix(8000, seed=93, n_halos=4), 0.2, 94)
+    else:
+        d = _uniform_moving(5000, 91)
     n = d["x"].size
     dt = 3e-4
-    ctx_d = binding.Context(n, h_tol=1e-6)
+    fl = binding.SPH_FLAG_ADAPTIVE if adaptive else 0
+    ctx_d = binding.Context(n, h_tol=1e-6, flags=fl)
     pd = binding.Particles(d)
-    ctx_h = binding.Context(n, h_tol=1e-6)
+    ctx_h = binding.Context(n, h_tol=1e-6, flags=fl)
     ph = binding.Particles(d, device="cpu", pin=pin)
     for k in range(3):
         used_d, cons_d = ctx_d.step(pd, dt if k else 0.0)
